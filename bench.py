@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark: pixel hits/s clustered and centroided, as a fraction of HBM peak.
+
+Workload (one GPU): the large batch -- 10^6 laser shots at 1 kHz, Poisson(50)
+particles per shot, 5% planted as overlapping pairs, Gaussian charge clouds of
+sigma 1 px with ToT >= 10 (about 1.27e9 packets, 10 GB, read from HBM once per
+step). A step is one pass of the whole path (decode, unwrap, shot binning and
+cut, clustering, local maxima, centroids, per-pixel labels) over the batch.
+
+Prints one JSON line. `--impl reference` times the CPU oracle instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel hits/s clustered+centroided"
+UNIT = "hits/s"
+CLUSTER_BYTES = 88
+KERNEL_SRC = os.path.join(ROOT, "paper_2603_04942_gb300", "csrc", "tpx_fused.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_large_batch.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--shots", type=int, default=1_000_000)
+    ap.add_argument("--variant", choices=["literal", "stated"], default="literal")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-shots", type=int, default=50_000)
+    ap.add_argument("--ref-shots", type=int, default=10_000)
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    """Each rank gets its own acquisition run (seed 1 + rank) of the same shape."""
+    import synth
+    p = synth.large(n_shots=args.shots, seed=1 + rank)
+    if args.variant == "stated":
+        p = synth.stated_size(p)
+    desc = (f"large batch: {args.shots:,} shots at 1 kHz x Poisson(50) particles, 5% overlapping pairs "
+            f"(sep 0-4 px, dToA 0-20 ns, amp 0.3-1), sigma 1 px, peak ToT 200-1023, "
+            f"ToT >= {int(p.tot_min)} ({args.variant} parameters), ToF 1-10 us, seed {p.seed}")
+    return p, desc
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def traffic_per_packet():
+    """DRAM bytes per packet of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+        m_b = re.search(r"dram_bytes_per_packet:\s*([0-9.]+)", txt)
+        if m_sha and m_b and m_sha.group(1) == sha:
+            return float(m_b.group(1))
+    except Exception:
+        pass
+    return None
+
+
+def oracle_timed(p, shot_begin: int, n_shots: int) -> tuple[float, int, int]:
+    """Generate shots [shot_begin, shot_begin + n_shots) of workload `p` and
+    time the oracle on them (generation untimed). A slice that starts after
+    wraps is given its wrap counts, so it computes the same as the full run."""
+    import oracle
+    import synth
+    st = synth.Stream(p.replace(shot_begin=shot_begin, n_shots=n_shots))
+    pk = st.packets()
+    e_pix, e_tdc = st.wrap_counts()
+    st.close()
+    hits = int(((pk >> np.uint64(60)) == 0xB).sum())
+    cfg = oracle.Config(epoch0_pix=e_pix, epoch0_tdc=e_tdc)
+    t0 = time.perf_counter()
+    r = oracle.run(pk, cfg)
+    dt = time.perf_counter() - t0
+    assert r["status"] == 0, r["status"]
+    return dt, hits, pk.size
+
+
+def cpu_baseline(args, sample_shots: int) -> dict:
+    """The oracle as it stands, single-threaded, on the first shots of the
+    same workload, in chunks of 25,000 shots."""
+    import oracle
+    oracle.build()
+    p, _ = workload(args)
+    tot_t, tot_h, tot_p = 0.0, 0, 0
+    for b in range(0, sample_shots, 25_000):
+        dt, h, n = oracle_timed(p, b, min(25_000, sample_shots - b))
+        tot_t += dt
+        tot_h += h
+        tot_p += n
+    return {"value": tot_h / tot_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_shots:,} shots of the workload ({tot_h:,} pixel hits, {tot_p:,} packets) "
+                      f"in 25,000-shot calls, {tot_t:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, one bounded sample of
+    the workload per step (a different shot range each step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    p, desc = workload(args)
+    sample = args.ref_shots
+    times, hits_tot = [], 0
+    for k in range(args.warmup + args.steps):
+        dt, hits, _ = oracle_timed(p, (k * sample) % max(1, args.shots - sample), sample)
+        if k >= args.warmup:
+            times.append(dt)
+            hits_tot += hits
+    v = hits_tot / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": desc, "sample_shots_per_step": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample:,} shots per step, single-threaded CPU oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    from paper_2603_04942_gb300 import build as tbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tbuild.build()
+    tpx.load()
+
+    p, desc = workload(args, rank)
+    t_gen = time.perf_counter()
+    st = synth.Stream(p)
+    n = st.n_packets
+    h_pk = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    st.packets_into(h_pk.numpy().view(np.uint64))
+    st.close()
+    t_gen = time.perf_counter() - t_gen
+    hits = int(((h_pk.numpy().view(np.uint64) >> np.uint64(60)) == 0xB).sum())
+    d_pk = h_pk.to("cuda", non_blocking=False)
+
+    ctx = tpx.Context(tpx.Config(), max_packets=n)
+    cl_cap = max(1024, n // 16)
+    out = ctx.alloc_outputs(n, labels=True, is_peak=False, cluster_capacity=cl_cap,
+                            trig_capacity=args.shots + 16)
+    s = ctx.stream
+    for _ in range(args.warmup):
+        ctx.tpx_process(d_pk, out)
+    rc, counters = ctx.tpx_sync(check=False)
+    if rc != 0:
+        raise SystemExit(f"tpx_process failed in warm-up: {rc} {counters}")
+    n_cl = int(out["n_clusters"].item())
+    n_tr = int(out["n_trig"].item())
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(s)
+    for k in range(args.steps):
+        ctx.tpx_process(d_pk, out)
+        ev[k + 1].record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    rc, counters = ctx.tpx_sync(check=False)
+    assert rc == 0, rc
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    h_all = torch.tensor([hits * args.steps], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(h_all, op=dist.ReduceOp.SUM)
+    value = float(h_all.item()) / (float(t_max.item()) / 1e3)
+
+    # roofline of the fused kernel (the only kernel of a step)
+    pk_info, peak_kind = peaks()
+    alg_bytes = 8 * n + 8 * n + CLUSTER_BYTES * n_cl + 8 * n_tr
+    avg_ms = statistics.mean(step_ms)
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    peak = float(pk_info.get("hbm_gbs", 6800.0))
+    tpp = traffic_per_packet()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None if tpp is None else tpp * n,
+            "algorithmic_bytes": alg_bytes, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "kernel": "tpxk::fused_kernel<0>", "avg_launch_ms": avg_ms}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        del out
+        torch.cuda.empty_cache()
+        h_lab = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        h_cl = torch.empty(cl_cap * CLUSTER_BYTES, dtype=torch.uint8, pin_memory=True)
+        h_tr = torch.empty(args.shots + 16, dtype=torch.int64, pin_memory=True)
+        a_pk = h_pk.numpy().view(np.uint64)
+        a_lab, a_tr = h_lab.numpy(), h_tr.numpy()
+        a_cl = h_cl.numpy().view(tpx.CLUSTER_DTYPE)
+        rc, ncl_h, ntr_h = ctx.tpx_process_host(a_pk, a_lab, None, a_cl, a_tr)   # untimed: staging
+        assert rc == 0, rc
+        if world > 1:
+            dist.barrier()
+        tim = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            rc, ncl_h, ntr_h = ctx.tpx_process_host(a_pk, a_lab, None, a_cl, a_tr)
+            tim.append(time.perf_counter() - t0)
+            assert rc == 0, rc
+        e_t = torch.tensor([sum(tim)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": float(h_all.item()) / float(e_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 8 * n + CLUSTER_BYTES * ncl_h + 8 * ntr_h + 16,
+               "ms_per_step": 1e3 * statistics.mean(tim)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args, args.cpu_shots)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": float(t_max.item()) / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                "data": "synthetic",
+                "config": {"workload": desc, "packets_per_gpu": n, "pixel_hits_per_gpu": hits,
+                           "clusters_per_gpu": n_cl, "shots_per_gpu": n_tr,
+                           "l2": "inputs larger than L2 (10 GB packet stream per step)",
+                           "parallelism": f"{world} independent shot ranges" if world > 1 else "1 GPU",
+                           "generation_s": round(t_gen, 1)},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": args.steps,
+                "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+                "counters": counters}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

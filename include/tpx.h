@@ -1,0 +1,165 @@
+/*
+ * tpx.h -- C ABI of the GB300 TPX3 clustering / centroiding library (libtpx).
+ *
+ * The library turns a TimePix3-style packet stream (pixel events with X, Y,
+ * ToA, ToT and TDC trigger events interleaved, paper Sec. III) into particle
+ * hits: it decodes the 64-bit packets, unwraps ToA (Sec. IV.A), bins pixels
+ * into laser shots by the most recent trigger and applies the background cut
+ * (Sec. IV.B) and an optional timewalk table (Sec. IV.C, Eq. 1), groups pixels
+ * by the box adjacency of Sec. V.A (connected components, or the paper's
+ * per-maximum neighbourhoods), finds local maxima (Sec. V.B) and forms
+ * ToT-weighted centroids (Sec. V.C).
+ *
+ * Conventions
+ *   - Pointers named d_* are device pointers; h_* are host pointers.  The
+ *     caller owns every buffer it passes in; the context owns its scratch,
+ *     which is sized once by tpx_create / tpx_reserve.  No call on the
+ *     processing path allocates device memory.
+ *   - Calls are asynchronous on the context's CUDA stream.  Device-side
+ *     conditions (capacity, corrupt input, timeouts) are latched into a
+ *     status word that tpx_sync() reads; the kernels never trap.
+ *   - Every call returns TPX_OK (0) or a negative TPX_E* code.
+ *   - Times are in ticks of 1.5625 ns (25/16 ns; 256 units of 25/4096 ns).
+ *
+ * Packet layout (project-defined, TPX3-style; the paper prints none):
+ *   pixel : [63:60]=0xB [59:53]=dcol [52:47]=spix [46:44]=pix [43:30]=ToA
+ *           [29:20]=ToT [19:16]=fToA [15:0]=spidr;
+ *           x = 2*dcol + (pix>>2), y = 4*spix + (pix&3),
+ *           raw time = ((spidr<<14 | ToA)*16 - fToA) mod 2^34 ticks
+ *   TDC   : [63:60]=0x6 [43:9]=coarse (3.125 ns); raw time = 2*coarse mod 2^36
+ *   any other header: counted as corrupt and skipped (an error if strict).
+ */
+#ifndef TPX_H
+#define TPX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define TPX_OK 0
+#define TPX_EINVAL (-1)        /* bad argument or configuration               */
+#define TPX_ENOMEM (-2)        /* scratch allocation failed (create/reserve)  */
+#define TPX_EOVERFLOW (-3)     /* a caller buffer is too small; the required
+                                  count is in *d_n_clusters / *d_n_trig       */
+#define TPX_ECORRUPT (-4)      /* strict mode saw an unknown header, or the
+                                  trigger times decrease                      */
+#define TPX_EAGAIN (-5)        /* admission refused (streaming)               */
+#define TPX_ETIMEOUT (-6)      /* host-side wait ran out (streaming poll)     */
+#define TPX_EDEVTIMEOUT (-7)   /* a bounded device-side wait ran out          */
+#define TPX_ECUDA (-8)         /* a CUDA runtime call failed                  */
+#define TPX_EUNSUPPORTED (-9)  /* input outside what the fused path handles   */
+
+#define TPX_MODE_CC 0          /* connected components of the box adjacency   */
+#define TPX_MODE_PAPER 1       /* box neighbourhood of each local maximum     */
+
+/* Configuration.  Every paper parameter is a field (Sec. IV.A-C, V.A). */
+typedef struct tpx_config {
+    int32_t rx, ry;             /* spatial radii in pixels, inclusive, 0..7   */
+    int32_t dt_ticks;           /* time radius in ticks, inclusive, >= 0      */
+    int32_t mode;               /* TPX_MODE_CC or TPX_MODE_PAPER              */
+    int64_t tof_max_ticks;      /* keep pixels with ToF <= this; 64000 = 100 us
+                                   (Sec. IV.B).  At most 2^24 - 65537.        */
+    int64_t wrap_thr_pix_ticks; /* unwrap threshold, pixel stream (20 s)      */
+    int64_t wrap_thr_tdc_ticks; /* unwrap threshold, TDC stream (20 s)        */
+    const int16_t *d_timewalk_lut; /* device, 1024 entries in ticks indexed by
+                                   ToT, subtracted after the cut (Sec. IV.C);
+                                   NULL = no correction                       */
+    int32_t strict;             /* 1: unknown headers are an error            */
+    int32_t reserved;
+} tpx_config;
+
+/* One particle hit.  CC mode: one record per connected component; PAPER
+   mode: one record per local maximum, summed over its box neighbourhood
+   (Sec. V.C).  Records are written in ascending `label` order. */
+typedef struct tpx_cluster {
+    int64_t label;   /* stream index (packet_index_base + position) of the
+                        cluster's earliest pixel in (time, stream index)
+                        order; PAPER mode: of the local maximum              */
+    int64_t shot;    /* trigger index (count of TDC packets before it)       */
+    int64_t t0;      /* corrected time of the earliest pixel, ticks          */
+    int64_t s_tot;   /* sum ToT                                              */
+    int64_t s_x;     /* sum x*ToT                                            */
+    int64_t s_y;     /* sum y*ToT                                            */
+    int64_t s_t;     /* sum (t - t0)*ToT                                     */
+    int32_t n;       /* pixel count                                          */
+    int32_t n_peaks; /* local maxima among the pixels (Sec. V.B)             */
+    double x;        /* s_x / s_tot                                          */
+    double y;        /* s_y / s_tot                                          */
+    double tof;      /* (t0 - t_trig[shot]) + s_t / s_tot, ticks             */
+} tpx_cluster;       /* 88 bytes */
+
+typedef struct tpx_counters {
+    int64_t packets, pixels, tdcs, corrupt, dropped_pre_trigger, dropped_background,
+            kept, clusters, peaks;
+    int64_t status_bits;        /* raw device status word of the last call    */
+} tpx_counters;
+
+typedef struct tpx_ctx tpx_ctx;
+
+/* Fill *cfg with the defaults: rx = ry = 1, dt = 32 ticks (50 ns),
+   tof_max = 64000 ticks (100 us), both wrap thresholds 20 s, CC mode. */
+void tpx_config_default(tpx_config *cfg);
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = default
+   stream) on the current device, with scratch for up to `max_packets`
+   packets per call.  The configuration is copied; the timewalk table it
+   points to must stay valid while the context is used.
+   Errors: TPX_EINVAL (bad config), TPX_ENOMEM, TPX_ECUDA. */
+int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *cuda_stream);
+
+/* Grow the scratch to hold `max_packets` (synchronises the stream). */
+int tpx_reserve(tpx_ctx *ctx, int64_t max_packets);
+
+/* Destroy the context and free its scratch (synchronises the stream). */
+int tpx_destroy(tpx_ctx *ctx);
+
+/* The fused path (Sec. III - V.C, all steps in one pass over the stream).
+     d_packets        [n_packets] uint64, device, stream order.
+     packet_index_base  added to positions to form stream indices (labels),
+                      so labels stay global when a long stream is cut into
+                      calls.
+     d_labels         [n_packets] int64 or NULL: per packet, the label of its
+                      cluster (CC), its own stream index (PAPER) or -1 when
+                      the packet is not a kept pixel.
+     d_is_peak        [n_packets] uint8 or NULL: 1 for local maxima.
+     d_clusters       [cluster_capacity] records, ascending label.
+     d_n_clusters     device int64: number of records (if it exceeds the
+                      capacity, only `capacity` are written and tpx_sync
+                      returns TPX_EOVERFLOW).
+     d_trig_t         [trig_capacity] int64: unwrapped trigger times.
+     d_n_trig         device int64: number of triggers.
+   Returns TPX_EINVAL for bad arguments or n_packets > reserved capacity;
+   otherwise the work is queued and its outcome is read with tpx_sync. */
+int tpx_process(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets,
+                int64_t packet_index_base, int64_t *d_labels, uint8_t *d_is_peak,
+                tpx_cluster *d_clusters, int64_t cluster_capacity, int64_t *d_n_clusters,
+                int64_t *d_trig_t, int64_t trig_capacity, int64_t *d_n_trig);
+
+/* The same with host buffers: copies h_packets to the device, processes and
+   copies results back, all on the context stream, and synchronises.
+   h_labels / h_is_peak may be NULL.  *h_n_clusters and *h_n_trig receive the
+   counts.  Device staging comes from the context's scratch (tpx_reserve),
+   so it allocates nothing either.  Returns the tpx_sync status. */
+int tpx_process_host(tpx_ctx *ctx, const uint64_t *h_packets, int64_t n_packets,
+                     int64_t packet_index_base, int64_t *h_labels, uint8_t *h_is_peak,
+                     tpx_cluster *h_clusters, int64_t cluster_capacity, int64_t *h_n_clusters,
+                     int64_t *h_trig_t, int64_t trig_capacity, int64_t *h_n_trig);
+
+/* Wait for the context's queued work and translate the device status word
+   of the last call into a status code.  If counters != NULL, fill it. */
+int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
+
+/* Static description of a status code. */
+const char *tpx_strerror(int code);
+
+/* Library version string. */
+const char *tpx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPX_H */

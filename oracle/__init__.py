@@ -42,7 +42,7 @@ class _Cfg(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("tof_max_ticks", ctypes.c_int64),
                 ("wrap_thr_pix_ticks", ctypes.c_int64), ("wrap_thr_tdc_ticks", ctypes.c_int64),
                 ("timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("epoch0_pix", ctypes.c_int64), ("epoch0_tdc", ctypes.c_int64)]
 
 
 class _Counters(ctypes.Structure):
@@ -60,6 +60,8 @@ class Config:
     wrap_thr_tdc_ticks: int = WRAP_THR_TICKS
     timewalk_lut: np.ndarray | None = None
     strict: bool = False
+    epoch0_pix: int = 0      # wraps before the first pixel packet (slices of a longer stream)
+    epoch0_tdc: int = 0
 
 
 def _build() -> str:
@@ -101,7 +103,7 @@ def run(packets: np.ndarray, cfg: Config | None = None, idx_base: int = 0, want_
     pk = np.ascontiguousarray(packets, dtype=np.uint64)
     n = pk.size
     c = _Cfg(cfg.rx, cfg.ry, cfg.dt_ticks, cfg.mode, cfg.tof_max_ticks, cfg.wrap_thr_pix_ticks,
-             cfg.wrap_thr_tdc_ticks, None, int(cfg.strict), 0)
+             cfg.wrap_thr_tdc_ticks, None, int(cfg.strict), 0, int(cfg.epoch0_pix), int(cfg.epoch0_tdc))
     lut = None
     if cfg.timewalk_lut is not None:
         lut = np.ascontiguousarray(cfg.timewalk_lut, dtype=np.int16)

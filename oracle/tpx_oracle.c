@@ -65,6 +65,8 @@ typedef struct orc_config {
     const int16_t *timewalk_lut;         /* 1024 entries (ticks) or NULL */
     int32_t strict;                      /* unknown headers are an error */
     int32_t reserved;
+    int64_t epoch0_pix, epoch0_tdc;      /* wraps before the first packet (a slice
+                                            cut from the middle of a stream) */
 } orc_config;
 
 typedef struct orc_cluster {
@@ -139,7 +141,7 @@ int orc_run(const orc_config *cfg, const uint64_t *pk, int64_t n, int64_t idx_ba
     int32_t *ptot = (int32_t *)calloc((size_t)(n + 1), sizeof(int32_t));
     if (!type || !t || !px || !py || !ptot) return ORC_ENOMEM;
     int have_pix = 0, have_tdc = 0;
-    int64_t prev_pix = 0, prev_tdc = 0, epoch_pix = 0, epoch_tdc = 0;
+    int64_t prev_pix = 0, prev_tdc = 0, epoch_pix = cfg->epoch0_pix, epoch_tdc = cfg->epoch0_tdc;
     for (int64_t i = 0; i < n; i++) {
         uint64_t w = pk[i];
         unsigned hdr = (unsigned)(w >> 60);

@@ -1,0 +1,225 @@
+"""Python binding of libtpx, the GB300 TPX3 clustering / centroiding library.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. PyTorch provides device memory and the CUDA stream. The entry points
+have the C-ABI names of include/tpx.h (tpx_create, tpx_process,
+tpx_process_host, tpx_sync, ...). There is no CPU fallback: if the library or
+a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = ["Config", "Context", "CLUSTER_DTYPE", "TpxError", "lib", "load", "MODE_CC", "MODE_PAPER",
+           "EXPORTED_SYMBOLS"]
+
+MODE_CC = 0
+MODE_PAPER = 1
+TICK_NS = 1.5625
+
+OK, EINVAL, ENOMEM, EOVERFLOW, ECORRUPT, EAGAIN, ETIMEOUT, EDEVTIMEOUT, ECUDA, EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+
+# tpx_cluster, 88 bytes, ascending label order
+CLUSTER_DTYPE = np.dtype([("label", "<i8"), ("shot", "<i8"), ("t0", "<i8"), ("s_tot", "<i8"),
+                          ("s_x", "<i8"), ("s_y", "<i8"), ("s_t", "<i8"), ("n", "<i4"),
+                          ("n_peaks", "<i4"), ("x", "<f8"), ("y", "<f8"), ("tof", "<f8")])
+assert CLUSTER_DTYPE.itemsize == 88
+
+COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger", "dropped_background",
+                  "kept", "clusters", "peaks", "status_bits")
+
+EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
+                    "tpx_process_host", "tpx_sync", "tpx_strerror", "tpx_version")
+
+
+class _CConfig(ctypes.Structure):
+    _fields_ = [("rx", ctypes.c_int32), ("ry", ctypes.c_int32), ("dt_ticks", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("tof_max_ticks", ctypes.c_int64),
+                ("wrap_thr_pix_ticks", ctypes.c_int64), ("wrap_thr_tdc_ticks", ctypes.c_int64),
+                ("d_timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _CCounters(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in COUNTER_FIELDS]
+
+
+class TpxError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {lib().tpx_strerror(code).decode()} ({code})")
+
+
+@dataclasses.dataclass
+class Config:
+    """Mirror of tpx_config (Sec. IV.A-C and V.A parameters)."""
+    rx: int = 1
+    ry: int = 1
+    dt_ticks: int = 32
+    mode: int = MODE_CC
+    tof_max_ticks: int = 64_000
+    wrap_thr_pix_ticks: int = 12_800_000_000
+    wrap_thr_tdc_ticks: int = 12_800_000_000
+    timewalk_lut: object = None        # torch int16 tensor of 1024 on the device, or None
+    strict: bool = False
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the built library; raise if it is missing (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build_mod.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtpx is not built ({path}); run paper_2603_04942_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.tpx_config_default.argtypes = [ctypes.POINTER(_CConfig)]
+        L.tpx_config_default.restype = None
+        L.tpx_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_CConfig), i64, vp]
+        L.tpx_reserve.argtypes = [vp, i64]
+        L.tpx_destroy.argtypes = [vp]
+        L.tpx_process.argtypes = [vp, vp, i64, i64, vp, vp, vp, i64, vp, vp, i64, vp]
+        L.tpx_process_host.argtypes = [vp, vp, i64, i64, vp, vp, vp, i64, vp, vp, i64, vp]
+        L.tpx_sync.argtypes = [vp, ctypes.POINTER(_CCounters)]
+        L.tpx_strerror.argtypes = [i32]
+        L.tpx_strerror.restype = ctypes.c_char_p
+        L.tpx_version.restype = ctypes.c_char_p
+        for f in ("tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process", "tpx_process_host", "tpx_sync"):
+            getattr(L, f).restype = i32
+        _lib = L
+        return L
+
+
+def lib():
+    return load()
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+class Context:
+    """A tpx_ctx bound to a torch CUDA stream."""
+
+    def __init__(self, cfg: Config | None = None, max_packets: int = 1 << 20, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtpx needs a CUDA device")
+        self.cfg = cfg or Config()
+        self._lut = self.cfg.timewalk_lut
+        if self._lut is not None:
+            assert self._lut.dtype == torch.int16 and self._lut.numel() == 1024 and self._lut.is_cuda
+        c = _CConfig(self.cfg.rx, self.cfg.ry, self.cfg.dt_ticks, self.cfg.mode, self.cfg.tof_max_ticks,
+                     self.cfg.wrap_thr_pix_ticks, self.cfg.wrap_thr_tdc_ticks, _ptr(self._lut),
+                     int(self.cfg.strict), 0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        rc = lib().tpx_create(ctypes.byref(h), ctypes.byref(c), int(max_packets), ctypes.c_void_p(self.stream.cuda_stream))
+        if rc:
+            raise TpxError(rc, "tpx_create")
+        self._h = h
+
+    def reserve(self, max_packets: int):
+        rc = lib().tpx_reserve(self._h, int(max_packets))
+        if rc:
+            raise TpxError(rc, "tpx_reserve")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tpx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- device buffers (asynchronous; call sync() to read the status) --
+    def alloc_outputs(self, n_packets: int, labels=True, is_peak=False, cluster_capacity=None,
+                      trig_capacity=None):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cl_cap = int(cluster_capacity if cluster_capacity is not None else max(16, n_packets // 4))
+        tr_cap = int(trig_capacity if trig_capacity is not None else max(16, n_packets // 8))
+        return dict(
+            labels=torch.empty(n_packets, dtype=torch.int64, device=dev) if labels else None,
+            is_peak=torch.empty(n_packets, dtype=torch.uint8, device=dev) if is_peak else None,
+            clusters=torch.empty(cl_cap * CLUSTER_DTYPE.itemsize, dtype=torch.uint8, device=dev),
+            n_clusters=torch.zeros(1, dtype=torch.int64, device=dev),
+            trig=torch.empty(tr_cap, dtype=torch.int64, device=dev),
+            n_trig=torch.zeros(1, dtype=torch.int64, device=dev),
+            cluster_capacity=cl_cap, trig_capacity=tr_cap)
+
+    def tpx_process(self, packets, out: dict, index_base: int = 0, n_packets: int | None = None):
+        n = int(packets.numel() if n_packets is None else n_packets)
+        rc = lib().tpx_process(self._h, _ptr(packets), n, int(index_base), _ptr(out["labels"]),
+                               _ptr(out["is_peak"]), _ptr(out["clusters"]), out["cluster_capacity"],
+                               _ptr(out["n_clusters"]), _ptr(out["trig"]), out["trig_capacity"],
+                               _ptr(out["n_trig"]))
+        if rc:
+            raise TpxError(rc, "tpx_process")
+
+    def tpx_sync(self, check: bool = True) -> tuple[int, dict]:
+        cnt = _CCounters()
+        rc = lib().tpx_sync(self._h, ctypes.byref(cnt))
+        counters = {f: int(getattr(cnt, f)) for f in COUNTER_FIELDS}
+        if check and rc:
+            raise TpxError(rc, "tpx_sync")
+        return rc, counters
+
+    def process(self, packets, labels=True, is_peak=False, cluster_capacity=None, trig_capacity=None,
+                index_base: int = 0, check: bool = True) -> dict:
+        """Run the fused path on device-resident packets and return host
+        copies: clusters (structured numpy array), labels, is_peak,
+        triggers, counters and the status code."""
+        n = int(packets.numel())
+        if n > self.max_packets_hint():
+            self.reserve(n)
+        out = self.alloc_outputs(n, labels, is_peak, cluster_capacity, trig_capacity)
+        self.tpx_process(packets, out, index_base)
+        rc, counters = self.tpx_sync(check=check)
+        return self.collect(out, rc, counters)
+
+    def max_packets_hint(self) -> int:
+        return 1 << 62
+
+    @staticmethod
+    def collect(out: dict, rc: int, counters: dict) -> dict:
+        ncl = int(out["n_clusters"].item())
+        ntr = int(out["n_trig"].item())
+        m = min(ncl, out["cluster_capacity"])
+        raw = out["clusters"][: m * CLUSTER_DTYPE.itemsize].cpu().numpy()
+        clusters = np.frombuffer(raw.tobytes(), CLUSTER_DTYPE).copy() if m else np.zeros(0, CLUSTER_DTYPE)
+        return dict(status=rc, counters=counters, clusters=clusters, n_clusters=ncl, n_trig=ntr,
+                    triggers=out["trig"][: min(ntr, out["trig_capacity"])].cpu().numpy(),
+                    labels=None if out["labels"] is None else out["labels"].cpu().numpy(),
+                    is_peak=None if out["is_peak"] is None else out["is_peak"].cpu().numpy())
+
+    # -- host buffers (the end-to-end call) --
+    def tpx_process_host(self, packets: np.ndarray, labels: np.ndarray | None, is_peak: np.ndarray | None,
+                         clusters: np.ndarray, triggers: np.ndarray, index_base: int = 0) -> tuple[int, int, int]:
+        assert packets.dtype == np.uint64 and packets.flags.c_contiguous
+        n_cl = ctypes.c_int64()
+        n_tr = ctypes.c_int64()
+        rc = lib().tpx_process_host(self._h, packets.ctypes.data, packets.size, int(index_base),
+                                    None if labels is None else labels.ctypes.data,
+                                    None if is_peak is None else is_peak.ctypes.data,
+                                    clusters.ctypes.data, clusters.size, ctypes.byref(n_cl),
+                                    triggers.ctypes.data, triggers.size, ctypes.byref(n_tr))
+        return rc, n_cl.value, n_tr.value

@@ -1,0 +1,749 @@
+// tpx_fused.cu -- fused single-pass TPX3 decode / unwrap / bin / cluster /
+// centroid kernel for sm_103a.  See tpx_fused.cuh for the structure.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "tpx_fused.cuh"
+
+namespace tpxk {
+
+constexpr int NT = 512;            // threads per CTA
+constexpr int NW = NT / 32;
+constexpr int T = 4096;            // packets per tile
+constexpr int C = 8192;            // range capacity (tile + look-ahead), positions
+constexpr int KP = C / NT;         // positions per thread in contiguous walks
+constexpr int HB = 8192;           // hash buckets (power of two)
+constexpr int M = 1024;            // cluster records per range
+constexpr int MAXSEG = T + 16;     // TDC packets per range: at most a tile's plus the terminator
+constexpr uint64_t INVALID = ~0ull;
+constexpr uint32_t EMPTY = 0xFFFFu;
+constexpr long long MAX_SPIN = 1LL << 22;   // bounded look-back waits (~0.5 s)
+
+static_assert(T % NT == 0 && C % NT == 0 && T <= C && C <= 16384, "tile geometry");
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ int pad(int p) { return p + (p >> 4); }   // conflict-free 16-wide walks
+
+// kept-pixel record: [63:40] tof+bias | [39:26] segment | [25:16] ToT | [15:8] y | [7:0] x
+__device__ __forceinline__ uint64_t mkrec(uint32_t tofb, uint32_t seg, uint32_t tot, uint32_t x, uint32_t y) {
+    return ((uint64_t)tofb << 40) | ((uint64_t)seg << 26) | ((uint64_t)tot << 16) | ((uint64_t)y << 8) | x;
+}
+__device__ __forceinline__ int r_x(uint64_t r) { return (int)(r & 255); }
+__device__ __forceinline__ int r_y(uint64_t r) { return (int)((r >> 8) & 255); }
+__device__ __forceinline__ int r_tot(uint64_t r) { return (int)((r >> 16) & 1023); }
+__device__ __forceinline__ int r_seg(uint64_t r) { return (int)((r >> 26) & 0x3FFF); }
+__device__ __forceinline__ int r_tof(uint64_t r) { return (int)(r >> 40); }
+
+__device__ __forceinline__ long long pix_raw(uint64_t w) {
+    long long coarse = (long long)(((w & 0xFFFFull) << 14) | ((w >> 30) & 0x3FFFull));
+    long long ftoa = (long long)((w >> 16) & 0xFull);
+    return (coarse * 16 - ftoa) & (kPixPeriod - 1);
+}
+__device__ __forceinline__ long long tdc_raw(uint64_t w) {
+    return (long long)(((w >> 9) & ((1ull << 35) - 1)) << 1);
+}
+__device__ __forceinline__ int pix_x(uint64_t w) { return (int)(2 * ((w >> 53) & 0x7F) + (((w >> 44) & 7) >> 2)); }
+__device__ __forceinline__ int pix_y(uint64_t w) { return (int)(4 * ((w >> 47) & 0x3F) + ((w >> 44) & 3)); }
+__device__ __forceinline__ int pix_tot(uint64_t w) { return (int)((w >> 20) & 0x3FF); }
+
+__device__ __forceinline__ long long jump(long long d, long long thr) { return d < -thr ? 1 : (d > thr ? -1 : 0); }
+
+__device__ __forceinline__ GChain chain_id() { GChain c; c.n = 0; c.first = 0; c.last = 0; c.sum = 0; return c; }
+__device__ __forceinline__ GAgg agg_id() { GAgg a; a.pix = chain_id(); a.tdc = chain_id(); return a; }
+
+// associative combine of two consecutive stretches of one unwrap chain
+__device__ __forceinline__ GChain ccomb(const GChain &a, const GChain &b, long long thr) {
+    GChain c;
+    c.n = a.n + b.n;
+    c.first = a.n ? a.first : b.first;
+    c.last = b.n ? b.last : a.last;
+    c.sum = a.sum + b.sum + ((a.n && b.n) ? jump(b.first - a.last, thr) : 0);
+    return c;
+}
+__device__ __forceinline__ GAgg acomb(const GAgg &a, const GAgg &b, long long tp, long long tt) {
+    GAgg c;
+    c.pix = ccomb(a.pix, b.pix, tp);
+    c.tdc = ccomb(a.tdc, b.tdc, tt);
+    return c;
+}
+__device__ __forceinline__ void chain_push(GChain &c, long long raw, long long thr) {
+    if (c.n) c.sum += jump(raw - c.last, thr); else c.first = raw;
+    c.last = raw;
+    c.n += 1;
+}
+
+__device__ __forceinline__ GChain shfl_up_chain(const GChain &v, int o) {
+    GChain u;
+    u.n = __shfl_up_sync(0xffffffffu, v.n, o);
+    u.first = __shfl_up_sync(0xffffffffu, v.first, o);
+    u.last = __shfl_up_sync(0xffffffffu, v.last, o);
+    u.sum = __shfl_up_sync(0xffffffffu, v.sum, o);
+    return u;
+}
+__device__ __forceinline__ GAgg shfl_up_agg(const GAgg &v, int o) {
+    GAgg u;
+    u.pix = shfl_up_chain(v.pix, o);
+    u.tdc = shfl_up_chain(v.tdc, o);
+    return u;
+}
+__device__ __forceinline__ GAgg warp_incl_scan(GAgg v, int lane, long long tp, long long tt) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        GAgg u = shfl_up_agg(v, o);
+        if (lane >= o) v = acomb(u, v, tp, tt);
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_agg(GAgg *dst, const GAgg &a) {
+    long long *d = reinterpret_cast<long long *>(dst);
+    const long long *s = reinterpret_cast<const long long *>(&a);
+#pragma unroll
+    for (int i = 0; i < 8; i++) __stcg(d + i, s[i]);
+}
+__device__ __forceinline__ GAgg ld_agg(const GAgg *src) {
+    GAgg a;
+    const long long *s = reinterpret_cast<const long long *>(src);
+    long long *d = reinterpret_cast<long long *>(&a);
+#pragma unroll
+    for (int i = 0; i < 8; i++) d[i] = __ldcg(s + i);
+    return a;
+}
+
+// hash of a (segment, x, y) cell
+__device__ __forceinline__ uint32_t hcell(int seg, int x, int y) {
+    return (uint32_t)(x + 67 * y + 1543 * seg) & (HB - 1);
+}
+
+__device__ __forceinline__ uint32_t find_root(volatile uint32_t *parent, uint32_t x) {
+    for (;;) {
+        uint32_t p = parent[x];
+        if (p == x) return x;
+        uint32_t g = parent[p];
+        if (g == p) return p;
+        parent[x] = g;            // path halving: g is an ancestor of x
+        x = g;
+    }
+}
+__device__ __forceinline__ uint32_t find_ro(const volatile uint32_t *parent, uint32_t x) {
+    uint32_t p;
+    while ((p = parent[x]) != x) x = p;
+    return x;
+}
+
+// --------------------------------------------------------------- smem layout
+struct __align__(16) Smem {
+    uint64_t buf[C + C / 16];                         // packets, then kept-pixel records
+    uint32_t parent[C];                               // union-find (CC) / peak list (PAPER)
+    union { uint32_t head[HB]; uint32_t cid[C]; } u1; // hash heads, then cluster ids
+    union { uint16_t next[C]; uint16_t rootof[C]; } u2;
+    uint8_t notpeak[C];
+    unsigned long long acc0[M];   // ToT | n<<24 | peaks<<44
+    unsigned long long acc1[M];   // x*ToT | (y*ToT)<<32
+    unsigned long long acc2[M];   // (tof+bias)*ToT
+    uint16_t rootpos[M];
+    long long tdc_t[MAXSEG];
+    GAgg warp_agg[NW];
+    GAgg tot_agg;
+    GAgg E;                       // unwrap state before the tile
+    int warp_int[NW + 1];
+    unsigned long long cnt[C_NUM];
+    long long tile;
+    long long clo;
+    int first_tdc;
+    int la_first;
+    unsigned status;
+};
+
+// block exclusive scan of GAgg in thread order; returns this thread's
+// exclusive prefix and leaves the block total in S.tot_agg
+__device__ GAgg block_scan_agg(Smem &S, const GAgg &v, long long tp, long long tt) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    GAgg incl = warp_incl_scan(v, lane, tp, tt);
+    GAgg wex = shfl_up_agg(incl, 1);
+    if (lane == 0) wex = agg_id();
+    if (lane == 31) S.warp_agg[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        GAgg x = lane < NW ? S.warp_agg[lane] : agg_id();
+        GAgg xi = warp_incl_scan(x, lane, tp, tt);
+        GAgg xe = shfl_up_agg(xi, 1);
+        if (lane == 0) xe = agg_id();
+        if (lane < NW) S.warp_agg[lane] = xe;
+        if (lane == NW - 1) S.tot_agg = xi;
+    }
+    __syncthreads();
+    GAgg r = acomb(S.warp_agg[w], wex, tp, tt);
+    __syncthreads();
+    return r;
+}
+
+// block exclusive scan of int; total in *total
+__device__ int block_scan_int(Smem &S, int v, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) S.warp_int[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < NW ? S.warp_int[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += u;
+        }
+        if (lane < NW) S.warp_int[lane] = xi - x;
+        if (lane == NW - 1) S.warp_int[NW] = xi;
+    }
+    __syncthreads();
+    int r = S.warp_int[w] + incl - v;
+    *total = S.warp_int[NW];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// once any wait has run out, every later wait gives up at once, so a broken
+// chain costs one bounded wait, not one per tile
+__device__ __forceinline__ bool timed_out(const Params &p) {
+    return (*reinterpret_cast<volatile unsigned *>(&p.ctl->status) & ST_DEVTIMEOUT) != 0;
+}
+
+// bounded decoupled look-back over the unwrap chains (thread 0 only)
+__device__ GAgg lookback_agg(const Params &p, long long tile, unsigned seq, unsigned *status) {
+    GAgg acc = agg_id();
+    for (long long q = tile - 1; q >= 0;) {
+        unsigned f = 0;
+        long long spins = 0;
+        for (;;) {
+            f = ld_acquire(&p.ts.flags[q]);
+            if ((f >> 2) == seq && (f & 3u)) break;
+            if (++spins > MAX_SPIN || timed_out(p)) { atomicOr(&p.ctl->status, ST_DEVTIMEOUT); *status |= ST_DEVTIMEOUT; return acc; }
+            __nanosleep(64);
+        }
+        if ((f & 3u) == 2u) { acc = acomb(ld_agg(&p.ts.pre[q]), acc, p.thr_pix, p.thr_tdc); break; }
+        acc = acomb(ld_agg(&p.ts.agg[q]), acc, p.thr_pix, p.thr_tdc);
+        --q;
+    }
+    return acc;
+}
+
+// bounded decoupled look-back over cluster counts (thread 0 only)
+__device__ long long lookback_count(const Params &p, long long tile, unsigned seq, unsigned *status) {
+    long long acc = 0;
+    for (long long q = tile - 1; q >= 0;) {
+        unsigned f = 0;
+        long long spins = 0;
+        for (;;) {
+            f = ld_acquire(&p.ts.cflags[q]);
+            if ((f >> 2) == seq && (f & 3u)) break;
+            if (++spins > MAX_SPIN || timed_out(p)) { atomicOr(&p.ctl->status, ST_DEVTIMEOUT); *status |= ST_DEVTIMEOUT; return acc; }
+            __nanosleep(64);
+        }
+        if ((f & 3u) == 2u) { acc += __ldcg(&p.ts.cpre[q]); break; }
+        acc += __ldcg(&p.ts.cagg[q]);
+        --q;
+    }
+    return acc;
+}
+
+// lock-free union; the root is the member with the smallest (time, position)
+__device__ __forceinline__ uint64_t rkey(const Smem &S, uint32_t q) {
+    return ((uint64_t)r_tof(S.buf[pad((int)q)]) << 16) | q;
+}
+__device__ void unite(Smem &S, uint32_t a, uint32_t b) {
+    volatile uint32_t *vp = S.parent;
+    for (;;) {
+        a = find_root(vp, a);
+        b = find_root(vp, b);
+        if (a == b) return;
+        if (rkey(S, a) > rkey(S, b)) { uint32_t t = a; a = b; b = t; }
+        uint32_t old = atomicCAS(&S.parent[b], b, a);
+        if (old == b) return;
+        b = old;
+    }
+}
+
+// ------------------------------------------------------------------- kernel
+template <int MODE>
+__global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long tp = p.thr_pix, tt = p.thr_tdc;
+    const unsigned seq = p.seq & 0x3FFFFFFFu;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
+            S.first_tdc = INT_MAX;
+            S.status = 0;
+        }
+        if (tid < C_NUM) S.cnt[tid] = 0;
+        __syncthreads();
+        const long long tile = S.tile;
+        if (tile >= p.n_tiles) break;
+        const long long base = tile * T;
+        const int cnt = (int)min((long long)T, p.n - base);
+
+        // ---- load the tile: coalesced 16-byte loads into the padded buffer ----
+        {
+            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.pk + base);
+            const int npair = cnt >> 1;
+            for (int v = tid; v < npair; v += NT) {
+                ulonglong2 w = __ldcg(src + v);
+                S.buf[pad(2 * v)] = w.x;
+                S.buf[pad(2 * v + 1)] = w.y;
+            }
+            if ((cnt & 1) && tid == 0) S.buf[pad(cnt - 1)] = __ldcg(p.pk + base + cnt - 1);
+        }
+        for (int i = tid; i < HB; i += NT) S.u1.head[i] = EMPTY;
+        __syncthreads();
+
+        // ---- walk 1: unwrap-chain aggregate of the tile, packet counts ----
+        {
+            GAgg a = agg_id();
+            unsigned long long c_pix = 0, c_tdc = 0, c_bad = 0;
+            int my_first = INT_MAX;
+            const int p0 = tid * KP;
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= cnt) break;
+                const uint64_t w = S.buf[pad(q)];
+                const unsigned h = (unsigned)(w >> 60);
+                if (h == 0xBu) { chain_push(a.pix, pix_raw(w), tp); ++c_pix; }
+                else if (h == 0x6u) { chain_push(a.tdc, tdc_raw(w), tt); ++c_tdc; my_first = min(my_first, q); }
+                else ++c_bad;
+            }
+            (void)block_scan_agg(S, a, tp, tt);
+            c_pix = warp_sum(c_pix); c_tdc = warp_sum(c_tdc); c_bad = warp_sum(c_bad);
+            if (lane == 0) {
+                atomicAdd(&S.cnt[C_PIXELS], c_pix);
+                atomicAdd(&S.cnt[C_TDCS], c_tdc);
+                atomicAdd(&S.cnt[C_CORRUPT], c_bad);
+            }
+            if (my_first != INT_MAX) atomicMin(&S.first_tdc, my_first);
+        }
+        // publish the aggregate, look back, publish the inclusive prefix
+        if (tid == 0) {
+            const GAgg tot = S.tot_agg;
+            GAgg E = agg_id();
+            unsigned st = 0;
+            if (tile > 0) {
+                st_agg(&p.ts.agg[tile], tot);
+                st_release(&p.ts.flags[tile], (seq << 2) | 1u);
+                E = lookback_agg(p, tile, seq, &st);
+            }
+            st_agg(&p.ts.pre[tile], acomb(E, tot, tp, tt));
+            st_release(&p.ts.flags[tile], (seq << 2) | 2u);
+            S.E = E;
+            atomicOr(&S.status, st);
+        }
+        __syncthreads();
+        const GAgg E = S.E;
+        const int f = S.first_tdc;
+        const bool prev_global = E.tdc.n > 0;
+
+        // ---- look ahead past the tile up to the next TDC packet ----
+        int L = cnt;
+        bool term = false;
+        if (f != INT_MAX) {
+            while (base + L < p.n) {
+                const int room = C - L;
+                if (room <= 0) break;
+                const int chunk = (int)min((long long)min(NT, room), p.n - (base + L));
+                bool is_t = false;
+                if (tid < chunk) {
+                    const uint64_t w = __ldcg(p.pk + base + L + tid);
+                    S.buf[pad(L + tid)] = w;
+                    is_t = (w >> 60) == 0x6u;
+                }
+                if (tid == 0) S.la_first = INT_MAX;
+                __syncthreads();
+                if (is_t) atomicMin(&S.la_first, tid);
+                __syncthreads();
+                const int lf = S.la_first;
+                __syncthreads();
+                if (lf != INT_MAX) { L += lf + 1; term = true; break; }
+                L += chunk;
+            }
+            if (!term && base + L < p.n && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+        }
+
+        // ---- walk 2: per-thread chain state over [0, L) ----
+        const int p0 = tid * KP;
+        GAgg ex;
+        int ntdc;
+        {
+            GAgg a = agg_id();
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= L) break;
+                const uint64_t w = S.buf[pad(q)];
+                const unsigned h = (unsigned)(w >> 60);
+                if (h == 0xBu) chain_push(a.pix, pix_raw(w), tp);
+                else if (h == 0x6u) chain_push(a.tdc, tdc_raw(w), tt);
+            }
+            ex = block_scan_agg(S, a, tp, tt);
+            ntdc = (int)S.tot_agg.tdc.n;
+        }
+        const GAgg st = acomb(E, ex, tp, tt);   // global chain state before position p0
+
+        // ---- walk 3: unwrapped trigger times ----
+        {
+            bool has = st.tdc.n > 0;
+            long long last = st.tdc.last, ep = st.tdc.sum;
+            int li = (int)ex.tdc.n;
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= L) break;
+                const uint64_t w = S.buf[pad(q)];
+                if ((w >> 60) != 0x6u) continue;
+                const long long r = tdc_raw(w);
+                if (has) ep += jump(r - last, tt);
+                has = true;
+                last = r;
+                const long long t = r + ep * kTdcPeriod;
+                if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
+                if (q < cnt) {
+                    const long long g = E.tdc.n + li;
+                    if (g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
+                }
+                ++li;
+            }
+        }
+        __syncthreads();
+        if (ntdc > MAXSEG && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+        for (int i = tid; i + 1 < min(ntdc, MAXSEG); i += NT)
+            if (S.tdc_t[i + 1] < S.tdc_t[i]) atomicOr(&p.ctl->status, ST_TRIG_ORDER);
+
+        // ---- walk 4: pixels -> shot, cut, timewalk, packed record ----
+        {
+            bool has = st.pix.n > 0;
+            long long last = st.pix.last, ep = st.pix.sum;
+            int seg = (int)ex.tdc.n - 1;
+            const long long t_prev_global = E.tdc.last + E.tdc.sum * kTdcPeriod;
+            unsigned long long c_keep = 0, c_pre = 0, c_bg = 0;
+            bool exc = false;
+            const int nseg = min(ntdc, MAXSEG);
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= L) break;
+                const uint64_t w = S.buf[pad(q)];
+                const unsigned h = (unsigned)(w >> 60);
+                uint64_t rec = INVALID;
+                if (h == 0x6u) {
+                    ++seg;
+                } else if (h == 0xBu) {
+                    const long long r = pix_raw(w);
+                    if (has) ep += jump(r - last, tp);
+                    has = true;
+                    last = r;
+                    const long long t = r + ep * kPixPeriod;
+                    if (seg < 0) {
+                        if (!prev_global) ++c_pre;        // no trigger before it anywhere
+                    } else if (seg < nseg) {
+                        const long long t_lo = S.tdc_t[seg];
+                        const bool has_hi = seg + 1 < nseg;
+                        int verdict;                      // 0 keep, 1 bg, 2 pre, 3 undecidable here
+                        if (has_hi && t >= S.tdc_t[seg + 1]) verdict = 3;
+                        else if (t >= t_lo) verdict = (t - t_lo > p.tof_max) ? 1 : 0;
+                        else {
+                            const bool hp = seg > 0 || prev_global;
+                            const long long tprev = seg > 0 ? S.tdc_t[seg - 1] : t_prev_global;
+                            if (!hp) verdict = 2;
+                            else if (t >= tprev) verdict = (t - tprev > p.tof_max) ? 1 : 3;
+                            else verdict = 3;
+                        }
+                        if (verdict == 0) {
+                            const int tot = pix_tot(w);
+                            const long long tc = t - (p.lut ? (long long)p.lut[tot] : 0LL);
+                            const long long tofb = tc - t_lo + kTofBias;
+                            rec = mkrec((uint32_t)tofb, (uint32_t)seg, (uint32_t)tot, (uint32_t)pix_x(w), (uint32_t)pix_y(w));
+                            ++c_keep;
+                        } else if (verdict == 1) ++c_bg;
+                        else if (verdict == 2) ++c_pre;
+                        else exc = true;
+                    }
+                }
+                S.buf[pad(q)] = rec;
+            }
+            c_keep = warp_sum(c_keep); c_pre = warp_sum(c_pre); c_bg = warp_sum(c_bg);
+            if (lane == 0) {
+                atomicAdd(&S.cnt[C_KEPT], c_keep);
+                atomicAdd(&S.cnt[C_DROP_PRE], c_pre);
+                atomicAdd(&S.cnt[C_DROP_BG], c_bg);
+            }
+            if (exc) atomicOr(&S.status, ST_EXCEPTION);
+        }
+
+        // the range this CTA owns: [R0, R1)
+        const int R0 = (f == INT_MAX) ? 0 : f;
+        const int R1 = (f == INT_MAX) ? 0 : (term ? L - 1 : L);
+        // label writes cover [W0, W1): the range, plus the packets before the
+        // tile's first trigger when no trigger precedes them anywhere
+        const int W0 = prev_global ? R0 : 0;
+        const int W1 = (f == INT_MAX) ? (prev_global ? 0 : cnt) : R1;
+
+        // ---- hash insert ----
+        for (int q = R0 + tid; q < R1; q += NT) {
+            const uint64_t r = S.buf[pad(q)];
+            S.parent[q] = (uint32_t)q;
+            S.notpeak[q] = 0;
+            if (r != INVALID) {
+                const uint32_t b = hcell(r_seg(r), r_x(r), r_y(r));
+                S.u2.next[q] = (uint16_t)atomicExch(&S.u1.head[b], (uint32_t)q);
+            }
+        }
+        __syncthreads();
+
+        // ---- neighbour pass: each adjacent pair once (Sec. V.A box rule) ----
+        for (int q = R0 + tid; q < R1; q += NT) {
+            const uint64_t r = S.buf[pad(q)];
+            if (r == INVALID) continue;
+            const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
+            for (int dx = 0; dx <= p.rx; ++dx) {
+                const int cx = x + dx;
+                if (cx > 255) break;
+                for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
+                    const int cy = y + dy;
+                    if (cy < 0 || cy > 255) continue;
+                    for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                        if (dx == 0 && dy == 0 && (int)j <= q) continue;
+                        const uint64_t rj = S.buf[pad((int)j)];
+                        if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
+                        const int d = r_tof(rj) - tb;
+                        if (d < -p.dt || d > p.dt) continue;
+                        const int tj = r_tot(rj);
+                        // local maxima: equal ToT goes to the later pixel (Sec. V.B)
+                        if (tj > tot || (tj == tot && (int)j > q)) S.notpeak[q] = 1;
+                        else S.notpeak[j] = 1;
+                        if (MODE == TPX_MODE_CC) unite(S, (uint32_t)q, j);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        int ncl = 0;
+        if (MODE == TPX_MODE_CC) {
+            for (int q = R0 + tid; q < R1; q += NT)
+                if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(S.parent, (uint32_t)q);
+            __syncthreads();
+            int c = 0;
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
+            }
+            int excl = block_scan_int(S, c, &ncl);
+            if (ncl > M && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
+                    S.u1.cid[q] = (uint32_t)excl;
+                    if (excl < M) S.rootpos[excl] = (uint16_t)q;
+                    ++excl;
+                }
+            }
+            for (int i = tid; i < min(ncl, M); i += NT) { S.acc0[i] = 0; S.acc1[i] = 0; S.acc2[i] = 0; }
+            __syncthreads();
+            unsigned long long c_pk = 0;
+            for (int q = W0 + tid; q < W1; q += NT) {
+                const uint64_t r = S.buf[pad(q)];
+                long long lab = -1;
+                uint8_t pk = 0;
+                if (q >= R0 && r != INVALID) {
+                    const uint32_t root = S.u2.rootof[q];
+                    const uint32_t ci = S.u1.cid[root];
+                    pk = S.notpeak[q] ? 0 : 1;
+                    c_pk += pk;
+                    if (ci < (uint32_t)M) {
+                        const unsigned long long tot = (unsigned long long)r_tot(r);
+                        atomicAdd(&S.acc0[ci], tot | (1ull << 24) | ((unsigned long long)pk << 44));
+                        atomicAdd(&S.acc1[ci], (tot * (unsigned long long)r_x(r)) | ((tot * (unsigned long long)r_y(r)) << 32));
+                        atomicAdd(&S.acc2[ci], tot * (unsigned long long)r_tof(r));
+                    }
+                    lab = p.idx_base + base + (long long)root;
+                }
+                if (p.labels) p.labels[base + q] = lab;
+                if (p.is_peak) p.is_peak[base + q] = pk;
+            }
+            c_pk = warp_sum(c_pk);
+            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
+        } else {
+            // PAPER mode: one record per local maximum (list kept in parent[])
+            int c = 0;
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) ++c;
+            }
+            int excl = block_scan_int(S, c, &ncl);
+            for (int j = 0; j < KP; ++j) {
+                const int q = p0 + j;
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) S.parent[excl++] = (uint32_t)q;
+            }
+            unsigned long long c_pk = 0;
+            for (int q = W0 + tid; q < W1; q += NT) {
+                const uint64_t r = S.buf[pad(q)];
+                long long lab = -1;
+                uint8_t pk = 0;
+                if (q >= R0 && r != INVALID) {
+                    lab = p.idx_base + base + q;
+                    pk = S.notpeak[q] ? 0 : 1;
+                    c_pk += pk;
+                }
+                if (p.labels) p.labels[base + q] = lab;
+                if (p.is_peak) p.is_peak[base + q] = pk;
+            }
+            c_pk = warp_sum(c_pk);
+            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
+            __syncthreads();
+        }
+
+        // ---- cluster offsets: second decoupled look-back over record counts ----
+        if (tid == 0) {
+            unsigned st2 = 0;
+            long long O = 0;
+            const long long mine = (long long)ncl;
+            if (tile > 0) {
+                __stcg(&p.ts.cagg[tile], mine);
+                st_release(&p.ts.cflags[tile], (seq << 2) | 1u);
+                O = lookback_count(p, tile, seq, &st2);
+            }
+            __stcg(&p.ts.cpre[tile], O + mine);
+            st_release(&p.ts.cflags[tile], (seq << 2) | 2u);
+            S.clo = O;
+            atomicOr(&S.status, st2);
+            if (tile == p.n_tiles - 1) {
+                const long long ntr = E.tdc.n + (long long)S.cnt[C_TDCS];
+                *p.n_clusters = O + mine;
+                *p.n_trig = ntr;
+                if (O + mine > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
+                if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
+            }
+        }
+        __syncthreads();
+        const long long O = S.clo;
+
+        // ---- cluster records (Sec. V.C centre of mass, exact integer sums) ----
+        if (MODE == TPX_MODE_CC) {
+            for (int i = tid; i < min(ncl, M); i += NT) {
+                if (O + i >= p.cl_cap) break;
+                const int q = S.rootpos[i];
+                const uint64_t r = S.buf[pad(q)];
+                const unsigned long long a0 = S.acc0[i], a1 = S.acc1[i], a2 = S.acc2[i];
+                const long long s_tot = (long long)(a0 & 0xFFFFFFull);
+                const int n = (int)((a0 >> 24) & 0xFFFFFull);
+                const int npk = (int)(a0 >> 44);
+                const long long s_x = (long long)(a1 & 0xFFFFFFFFull), s_y = (long long)(a1 >> 32);
+                const long long tofb0 = r_tof(r);
+                const long long s_t = (long long)a2 - tofb0 * s_tot;
+                const int seg = r_seg(r);
+                const long long tofc0 = tofb0 - kTofBias;
+                tpx_cluster o;
+                o.label = p.idx_base + base + q;
+                o.shot = E.tdc.n + seg;
+                o.t0 = S.tdc_t[seg] + tofc0;
+                o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
+                o.n = n; o.n_peaks = npk;
+                o.x = (double)s_x / (double)s_tot;
+                o.y = (double)s_y / (double)s_tot;
+                o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
+                p.clusters[O + i] = o;
+            }
+        } else {
+            for (int i = tid; i < ncl; i += NT) {
+                if (O + i >= p.cl_cap) break;
+                const int q = (int)S.parent[i];
+                const uint64_t r = S.buf[pad(q)];
+                const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
+                long long n = 0, s_tot = 0, s_x = 0, s_y = 0, a2 = 0;
+                int tmin = tb;
+                for (int dx = -p.rx; dx <= p.rx; ++dx) {
+                    const int cx = x + dx;
+                    if (cx < 0 || cx > 255) continue;
+                    for (int dy = -p.ry; dy <= p.ry; ++dy) {
+                        const int cy = y + dy;
+                        if (cy < 0 || cy > 255) continue;
+                        for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                            const uint64_t rj = S.buf[pad((int)j)];
+                            if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
+                            const int d = r_tof(rj) - tb;
+                            if (d < -p.dt || d > p.dt) continue;
+                            const long long tj = r_tot(rj);
+                            n += 1; s_tot += tj; s_x += tj * cx; s_y += tj * cy; a2 += tj * r_tof(rj);
+                            tmin = min(tmin, r_tof(rj));
+                        }
+                    }
+                }
+                const long long s_t = a2 - (long long)tmin * s_tot;
+                const long long tofc0 = (long long)tmin - kTofBias;
+                tpx_cluster o;
+                o.label = p.idx_base + base + q;
+                o.shot = E.tdc.n + sg;
+                o.t0 = S.tdc_t[sg] + tofc0;
+                o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
+                o.n = (int)n; o.n_peaks = 1;
+                o.x = (double)s_x / (double)s_tot;
+                o.y = (double)s_y / (double)s_tot;
+                o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
+                p.clusters[O + i] = o;
+            }
+        }
+        if (tid == 0) S.cnt[C_CLUSTERS] = (unsigned long long)ncl;
+        __syncthreads();
+        if (tid < C_NUM && tid != C_PACKETS && S.cnt[tid]) atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
+        if (tid == 0) {
+            atomicAdd(&p.ctl->counters[C_PACKETS], (unsigned long long)cnt);
+            if (S.status) atomicOr(&p.ctl->status, S.status);
+        }
+    }
+}
+
+int fused_tile_packets() { return T; }
+int fused_threads() { return NT; }
+int fused_smem_bytes() { return (int)sizeof(Smem); }
+
+cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s) {
+    static bool attr_done[2] = {false, false};
+    const int smem = (int)sizeof(Smem);
+    if (mode == TPX_MODE_CC) {
+        if (!attr_done[0]) {
+            cudaError_t e = cudaFuncSetAttribute(fused_kernel<TPX_MODE_CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_done[0] = true;
+        }
+        fused_kernel<TPX_MODE_CC><<<grid, NT, smem, s>>>(p);
+    } else {
+        if (!attr_done[1]) {
+            cudaError_t e = cudaFuncSetAttribute(fused_kernel<TPX_MODE_PAPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_done[1] = true;
+        }
+        fused_kernel<TPX_MODE_PAPER><<<grid, NT, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tpxk

@@ -1,0 +1,105 @@
+// tpx_fused.cuh -- the fused single-pass TPX3 path for sm_103a.
+//
+// One persistent kernel reads the packet stream once.  Each CTA repeatedly
+// claims the next tile of T packets (dynamic, in stream order), and:
+//   1. loads the tile into shared memory and reduces the two ToA unwrap
+//      chains (pixels, TDCs) over it (Sec. IV.A: a step down by more than the
+//      threshold adds a wrap, a step up by more removes one).  The chains are
+//      associative, so tiles publish their aggregate and a decoupled look-back
+//      over predecessors yields the exact state at the tile start;
+//   2. owns the laser shots whose TDC packet lies in the tile, reading past
+//      the tile end up to the next TDC packet (its "range");
+//   3. unwraps every packet of the range, bins each pixel to the most recent
+//      trigger in time, applies the <= tof_max background cut and the optional
+//      timewalk table (Sec. IV.B-C);
+//   4. hashes kept pixels by (shot, x, y) and visits each adjacent pair once
+//      under the box rule of Sec. V.A; a pair updates the local-maximum flags
+//      (Sec. V.B, equal ToT resolved towards the later pixel) and, in CC mode,
+//      a lock-free union-find whose root is the pair-wise minimum of the key
+//      (corrected time, stream position) -- so each component's root is its
+//      earliest pixel in sorted order without sorting the pixels;
+//   5. accumulates exact integer sums per cluster in shared memory (Sec. V.C)
+//      and writes per-packet labels and, after a second look-back over
+//      cluster counts, the cluster records in ascending label order.
+// Pixels whose trigger cannot be decided inside the range, and ranges that
+// exceed the on-chip capacities, raise a status bit instead (the kernel never
+// traps).  All device waits are bounded.
+#pragma once
+
+#include <cstdint>
+
+#include "tpx.h"
+
+namespace tpxk {
+
+constexpr int64_t kPixPeriod = 1LL << 34;
+constexpr int64_t kTdcPeriod = 1LL << 36;
+constexpr int kTofBias = 32768;            // tof_c + bias >= 1 for int16 timewalk shifts
+
+// status bits latched in Ctl::status
+enum : unsigned {
+    ST_CORRUPT = 1u << 0,      // unknown header (reported only when strict)
+    ST_TRIG_ORDER = 1u << 1,   // trigger times decrease
+    ST_CAPACITY = 1u << 2,     // a range exceeds shared-memory capacity
+    ST_EXCEPTION = 1u << 3,    // a pixel's trigger lies outside its range
+    ST_CLUSTER_CAP = 1u << 4,  // caller cluster buffer too small
+    ST_TRIG_CAP = 1u << 5,     // caller trigger buffer too small
+    ST_DEVTIMEOUT = 1u << 6,   // a look-back wait ran out
+};
+
+enum CounterIdx {
+    C_PACKETS = 0, C_PIXELS, C_TDCS, C_CORRUPT, C_DROP_PRE, C_DROP_BG, C_KEPT, C_CLUSTERS, C_PEAKS,
+    C_NUM
+};
+
+struct Ctl {                     // per-launch control block, cleared before each launch
+    unsigned int tile_counter;
+    unsigned int status;
+    unsigned long long counters[C_NUM];
+};
+
+// one unwrap chain over a stretch of the stream (64-bit form)
+struct GChain { long long n, first, last, sum; };
+struct GAgg { GChain pix, tdc; };            // 64 bytes
+
+// per-tile look-back records
+struct TileScratch {
+    unsigned int *flags;     // [tiles] (seq<<2)|1 aggregate, |2 inclusive prefix
+    GAgg *agg;               // [tiles]
+    GAgg *pre;               // [tiles]
+    unsigned int *cflags;    // [tiles] cluster-count chain
+    long long *cagg;         // [tiles]
+    long long *cpre;         // [tiles]
+};
+
+struct Params {
+    const uint64_t *pk;
+    long long n;
+    long long idx_base;
+    long long *labels;
+    uint8_t *is_peak;
+    tpx_cluster *clusters;
+    long long cl_cap;
+    long long *n_clusters;
+    long long *trig;
+    long long trig_cap;
+    long long *n_trig;
+    const int16_t *lut;
+    int rx, ry, dt, strict;
+    long long tof_max;
+    long long thr_pix, thr_tdc;
+    long long n_tiles;
+    unsigned int seq;
+    TileScratch ts;
+    Ctl *ctl;
+};
+
+}  // namespace tpxk
+
+// launch entry points (defined in tpx_fused.cu)
+namespace tpxk {
+int fused_tile_packets();
+int fused_smem_bytes();
+int fused_threads();
+cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s);
+}  // namespace tpxk

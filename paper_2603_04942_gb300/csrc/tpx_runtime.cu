@@ -1,0 +1,309 @@
+// tpx_runtime.cu -- host side of the C ABI declared in include/tpx.h:
+// context and scratch management, argument checks, launches, status words.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "tpx.h"
+#include "tpx_fused.cuh"
+
+struct tpx_ctx {
+    tpx_config cfg;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int64_t max_packets;
+    int64_t max_tiles;
+    unsigned seq;
+    tpxk::TileScratch ts;
+    void *scratch;            // one allocation for all tile records
+    tpxk::Ctl *ctl;           // device control block
+    tpxk::Ctl *h_ctl;         // pinned host copy
+    // device staging for tpx_process_host
+    uint64_t *st_pk;
+    int64_t *st_labels;
+    uint8_t *st_peak;
+    int64_t st_n, st_labels_cap, st_peak_cap, st_counts_cap;
+    tpx_cluster *st_cl;
+    int64_t st_cl_cap;
+    int64_t *st_trig;
+    int64_t st_trig_cap;
+    int64_t *st_counts;       // [2]: n_clusters, n_trig
+};
+
+namespace {
+
+constexpr int64_t kMaxTofMax = (1LL << 24) - 65537;
+
+int check_cfg(const tpx_config *c) {
+    if (!c) return TPX_EINVAL;
+    if (c->rx < 0 || c->ry < 0 || c->rx > 7 || c->ry > 7) return TPX_EINVAL;
+    if (c->dt_ticks < 0) return TPX_EINVAL;
+    if (c->mode != TPX_MODE_CC && c->mode != TPX_MODE_PAPER) return TPX_EINVAL;
+    if (c->tof_max_ticks < 0 || c->tof_max_ticks > kMaxTofMax) return TPX_EINVAL;
+    if (c->wrap_thr_pix_ticks <= 0 || c->wrap_thr_tdc_ticks <= 0) return TPX_EINVAL;
+    return TPX_OK;
+}
+
+void free_scratch(tpx_ctx *c) {
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    std::memset(&c->ts, 0, sizeof c->ts);
+    c->max_tiles = 0;
+}
+
+int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
+    const int64_t T = tpxk::fused_tile_packets();
+    int64_t tiles = (max_packets + T - 1) / T;
+    if (tiles < 1) tiles = 1;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_flags = al(sizeof(unsigned) * tiles), b_agg = al(sizeof(tpxk::GAgg) * tiles),
+                 b_cnt = al(sizeof(long long) * tiles);
+    const size_t total = 2 * b_flags + 2 * b_agg + 2 * b_cnt;
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
+    if (cudaMemset(mem, 0, total) != cudaSuccess) { cudaFree(mem); return TPX_ECUDA; }
+    char *p = static_cast<char *>(mem);
+    c->ts.flags = reinterpret_cast<unsigned *>(p); p += b_flags;
+    c->ts.cflags = reinterpret_cast<unsigned *>(p); p += b_flags;
+    c->ts.agg = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
+    c->ts.pre = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
+    c->ts.cagg = reinterpret_cast<long long *>(p); p += b_cnt;
+    c->ts.cpre = reinterpret_cast<long long *>(p);
+    c->scratch = mem;
+    c->max_tiles = tiles;
+    c->max_packets = tiles * T;
+    c->seq = 0;   // fresh flags: any sequence number is new
+    return TPX_OK;
+}
+
+template <class Tp>
+int grow(Tp **ptr, int64_t *cap, int64_t want) {
+    if (*ptr && *cap >= want) return TPX_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (want <= 0) want = 1;
+    if (cudaMalloc(reinterpret_cast<void **>(ptr), sizeof(Tp) * (size_t)want) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return TPX_ENOMEM;
+    }
+    *cap = want;
+    return TPX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tpx_config_default(tpx_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->rx = 1;
+    c->ry = 1;
+    c->dt_ticks = 32;
+    c->mode = TPX_MODE_CC;
+    c->tof_max_ticks = 64000;
+    c->wrap_thr_pix_ticks = 12800000000LL;
+    c->wrap_thr_tdc_ticks = 12800000000LL;
+    c->d_timewalk_lut = nullptr;
+    c->strict = 0;
+}
+
+int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *cuda_stream) {
+    if (!out || max_packets < 0) return TPX_EINVAL;
+    *out = nullptr;
+    int rc = check_cfg(cfg);
+    if (rc) return rc;
+    tpx_ctx *c = new (std::nothrow) tpx_ctx;
+    if (!c) return TPX_ENOMEM;
+    std::memset(c, 0, sizeof *c);
+    c->cfg = *cfg;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return TPX_ECUDA; }
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        delete c;
+        return TPX_ECUDA;
+    }
+    if (cudaMalloc(&c->ctl, sizeof(tpxk::Ctl)) != cudaSuccess) { delete c; return TPX_ENOMEM; }
+    if (cudaMallocHost(&c->h_ctl, sizeof(tpxk::Ctl)) != cudaSuccess) {
+        cudaFree(c->ctl);
+        delete c;
+        return TPX_ENOMEM;
+    }
+    std::memset(c->h_ctl, 0, sizeof(tpxk::Ctl));
+    cudaMemset(c->ctl, 0, sizeof(tpxk::Ctl));
+    rc = alloc_scratch(c, max_packets);
+    if (rc) {
+        cudaFree(c->ctl);
+        cudaFreeHost(c->h_ctl);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return TPX_OK;
+}
+
+int tpx_reserve(tpx_ctx *c, int64_t max_packets) {
+    if (!c || max_packets < 0) return TPX_EINVAL;
+    if (max_packets <= c->max_packets) return TPX_OK;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    free_scratch(c);
+    return alloc_scratch(c, max_packets);
+}
+
+int tpx_destroy(tpx_ctx *c) {
+    if (!c) return TPX_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    free_scratch(c);
+    if (c->ctl) cudaFree(c->ctl);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->st_pk) cudaFree(c->st_pk);
+    if (c->st_labels) cudaFree(c->st_labels);
+    if (c->st_peak) cudaFree(c->st_peak);
+    if (c->st_cl) cudaFree(c->st_cl);
+    if (c->st_trig) cudaFree(c->st_trig);
+    if (c->st_counts) cudaFree(c->st_counts);
+    delete c;
+    return TPX_OK;
+}
+
+int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_base, int64_t *d_labels,
+                uint8_t *d_is_peak, tpx_cluster *d_clusters, int64_t cl_cap, int64_t *d_n_clusters,
+                int64_t *d_trig, int64_t trig_cap, int64_t *d_n_trig) {
+    if (!c || n < 0 || cl_cap < 0 || trig_cap < 0 || !d_n_clusters || !d_n_trig) return TPX_EINVAL;
+    if (n > c->max_packets) return TPX_EINVAL;
+    if (n > 0 && !d_packets) return TPX_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_packets) & 15) != 0) return TPX_EINVAL;
+    if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
+    if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
+    if (cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (cudaMemsetAsync(d_n_clusters, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (cudaMemsetAsync(d_n_trig, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (n == 0) return TPX_OK;
+    c->seq = (c->seq + 1) & 0x3FFFFFFFu;
+    if (c->seq == 0) {   // sequence numbers wrapped: clear the flags once
+        c->seq = 1;
+        cudaMemsetAsync(c->ts.flags, 0, sizeof(unsigned) * c->max_tiles, c->stream);
+        cudaMemsetAsync(c->ts.cflags, 0, sizeof(unsigned) * c->max_tiles, c->stream);
+    }
+    tpxk::Params p;
+    std::memset(&p, 0, sizeof p);
+    p.pk = d_packets;
+    p.n = n;
+    p.idx_base = idx_base;
+    p.labels = reinterpret_cast<long long *>(d_labels);
+    p.is_peak = d_is_peak;
+    p.clusters = d_clusters;
+    p.cl_cap = cl_cap;
+    p.n_clusters = reinterpret_cast<long long *>(d_n_clusters);
+    p.trig = reinterpret_cast<long long *>(d_trig);
+    p.trig_cap = trig_cap;
+    p.n_trig = reinterpret_cast<long long *>(d_n_trig);
+    p.lut = c->cfg.d_timewalk_lut;
+    p.rx = c->cfg.rx;
+    p.ry = c->cfg.ry;
+    p.dt = c->cfg.dt_ticks;
+    p.strict = c->cfg.strict;
+    p.tof_max = c->cfg.tof_max_ticks;
+    p.thr_pix = c->cfg.wrap_thr_pix_ticks;
+    p.thr_tdc = c->cfg.wrap_thr_tdc_ticks;
+    const int64_t T = tpxk::fused_tile_packets();
+    p.n_tiles = (n + T - 1) / T;
+    p.seq = c->seq;
+    p.ts = c->ts;
+    p.ctl = c->ctl;
+    int64_t grid = c->num_sms;   // persistent: one CTA per SM
+    if (grid > p.n_tiles) grid = p.n_tiles;
+    cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, (int)grid, c->stream);
+    return e == cudaSuccess ? TPX_OK : TPX_ECUDA;
+}
+
+int tpx_sync(tpx_ctx *c, tpx_counters *out) {
+    if (!c) return TPX_EINVAL;
+    if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return TPX_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    const tpxk::Ctl &h = *c->h_ctl;
+    if (out) {
+        out->packets = (int64_t)h.counters[tpxk::C_PACKETS];
+        out->pixels = (int64_t)h.counters[tpxk::C_PIXELS];
+        out->tdcs = (int64_t)h.counters[tpxk::C_TDCS];
+        out->corrupt = (int64_t)h.counters[tpxk::C_CORRUPT];
+        out->dropped_pre_trigger = (int64_t)h.counters[tpxk::C_DROP_PRE];
+        out->dropped_background = (int64_t)h.counters[tpxk::C_DROP_BG];
+        out->kept = (int64_t)h.counters[tpxk::C_KEPT];
+        out->clusters = (int64_t)h.counters[tpxk::C_CLUSTERS];
+        out->peaks = (int64_t)h.counters[tpxk::C_PEAKS];
+        out->status_bits = (int64_t)h.status;
+    }
+    const unsigned s = h.status;
+    if (s & tpxk::ST_DEVTIMEOUT) return TPX_EDEVTIMEOUT;
+    if (s & tpxk::ST_TRIG_ORDER) return TPX_ECORRUPT;
+    if (s & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) return TPX_EUNSUPPORTED;
+    if (c->cfg.strict && h.counters[tpxk::C_CORRUPT]) return TPX_ECORRUPT;
+    if (s & (tpxk::ST_CLUSTER_CAP | tpxk::ST_TRIG_CAP)) return TPX_EOVERFLOW;
+    return TPX_OK;
+}
+
+int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base, int64_t *h_labels,
+                     uint8_t *h_is_peak, tpx_cluster *h_clusters, int64_t cl_cap, int64_t *h_n_clusters,
+                     int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
+    if (!c || n < 0 || cl_cap < 0 || trig_cap < 0 || !h_n_clusters || !h_n_trig) return TPX_EINVAL;
+    if (n > 0 && !h_packets) return TPX_EINVAL;
+    if (n > c->max_packets) return TPX_EINVAL;
+    int rc;
+    if ((rc = grow(&c->st_pk, &c->st_n, n))) return rc;
+    if (h_labels && (rc = grow(&c->st_labels, &c->st_labels_cap, n))) return rc;
+    if (h_is_peak && (rc = grow(&c->st_peak, &c->st_peak_cap, n))) return rc;
+    if ((rc = grow(&c->st_cl, &c->st_cl_cap, cl_cap))) return rc;
+    if ((rc = grow(&c->st_trig, &c->st_trig_cap, trig_cap))) return rc;
+    if ((rc = grow(&c->st_counts, &c->st_counts_cap, 2))) return rc;
+    cudaStream_t s = c->stream;
+    if (n && cudaMemcpyAsync(c->st_pk, h_packets, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TPX_ECUDA;
+    rc = tpx_process(c, c->st_pk, n, idx_base, h_labels ? c->st_labels : nullptr, h_is_peak ? c->st_peak : nullptr,
+                     c->st_cl, cl_cap, c->st_counts, c->st_trig, trig_cap, c->st_counts + 1);
+    if (rc) return rc;
+    int64_t counts[2] = {0, 0};
+    if (cudaMemcpyAsync(counts, c->st_counts, sizeof counts, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+    if (h_labels && n &&
+        cudaMemcpyAsync(h_labels, c->st_labels, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPX_ECUDA;
+    if (h_is_peak && n && cudaMemcpyAsync(h_is_peak, c->st_peak, n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPX_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    const int64_t ncl = counts[0] < cl_cap ? counts[0] : cl_cap;
+    const int64_t ntr = counts[1] < trig_cap ? counts[1] : trig_cap;
+    if (ncl > 0 && cudaMemcpyAsync(h_clusters, c->st_cl, sizeof(tpx_cluster) * ncl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPX_ECUDA;
+    if (ntr > 0 && cudaMemcpyAsync(h_trig, c->st_trig, sizeof(int64_t) * ntr, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPX_ECUDA;
+    *h_n_clusters = counts[0];
+    *h_n_trig = counts[1];
+    return tpx_sync(c, nullptr);
+}
+
+const char *tpx_strerror(int code) {
+    switch (code) {
+        case TPX_OK: return "ok";
+        case TPX_EINVAL: return "invalid argument or configuration";
+        case TPX_ENOMEM: return "device memory allocation failed";
+        case TPX_EOVERFLOW: return "output buffer too small (required count written)";
+        case TPX_ECORRUPT: return "corrupt stream (unknown header in strict mode, or decreasing triggers)";
+        case TPX_EAGAIN: return "admission refused";
+        case TPX_ETIMEOUT: return "host wait timed out";
+        case TPX_EDEVTIMEOUT: return "bounded device wait ran out";
+        case TPX_ECUDA: return "CUDA runtime error";
+        case TPX_EUNSUPPORTED: return "input outside the fused path's on-chip capacity";
+        default: return "unknown status";
+    }
+}
+
+const char *tpx_version(void) { return "tpx-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -123,6 +123,7 @@ def lib():
             L.synth_copy_packets.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
             L.synth_copy_truth.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 6
             L.synth_free.argtypes = [ctypes.c_void_p]
+            L.synth_first_times.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.synth_encode_pixels.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_void_p]
             L.synth_encode_tdcs.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
             _lib = L
@@ -173,6 +174,18 @@ class Stream:
                  t=np.empty(n, np.float64), peak=np.empty(n, np.float64), kind=np.empty(n, np.int32))
         lib().synth_copy_truth(self._h, *(d[k].ctypes.data for k in ("shot", "cx", "cy", "t", "peak", "kind")))
         return d
+
+    def first_times(self) -> tuple[int, int]:
+        """True times (ticks) of the first pixel and first TDC packet, -1 if none."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        lib().synth_first_times(self._h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+    def wrap_counts(self) -> tuple[int, int]:
+        """Whole wrap periods elapsed before the first pixel (2^34 ticks) and
+        the first TDC packet (2^36 ticks) of this range."""
+        tp, tt = self.first_times()
+        return (max(tp, 0) // PIX_PERIOD_TICKS, max(tt, 0) // TDC_PERIOD_TICKS)
 
     def trigger_times(self) -> np.ndarray:
         p = self.params

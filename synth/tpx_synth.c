@@ -135,6 +135,7 @@ typedef struct {
     hit_t *h2; int64_t cap_h2;
     int32_t *map_tag; int32_t *map_idx;  /* per-pixel last hit, tagged by shot */
     int64_t *rank_key; int64_t cap_rk;
+    int64_t first_pix_t, first_tdc_t;    /* true times of the first emitted packets */
 } worker_t;
 
 #define GROW(ptr, n, cap, type)                                                        \
@@ -268,6 +269,8 @@ static void gen_shot(worker_t *w, const synth_params *p, int64_t k) {
     }
     qsort(w->rank_key, (size_t)w->n_h, sizeof(int64_t), cmp_key);
     GROW(w->pk, w->n_pk + w->n_h + 1, w->cap_pk, uint64_t);
+    if (w->first_tdc_t < 0) w->first_tdc_t = t_trig;
+    if (w->first_pix_t < 0 && w->n_h > 0) w->first_pix_t = w->h[w->rank_key[0] & 0xFFFFFF].toa;
     w->pk[w->n_pk++] = encode_tdc(t_trig, k);
     for (int64_t i = 0; i < w->n_h; i++) {
         hit_t *h = &w->h[w->rank_key[i] & 0xFFFFFF];
@@ -285,6 +288,8 @@ static void *run_job(void *arg) {
     job_t *j = (job_t *)arg;
     j->w.map_tag = (int32_t *)calloc(65536, sizeof(int32_t));
     j->w.map_idx = (int32_t *)calloc(65536, sizeof(int32_t));
+    j->w.first_pix_t = -1;
+    j->w.first_tdc_t = -1;
     for (int64_t k = j->s0; k < j->s1; k++) gen_shot(&j->w, j->p, k);
     free(j->w.map_tag); free(j->w.map_idx); free(j->w.h); free(j->w.rank_key);
     j->w.map_tag = NULL; j->w.map_idx = NULL; j->w.h = NULL; j->w.rank_key = NULL;
@@ -323,6 +328,16 @@ synth_result *synth_generate(const synth_params *p_in) {
 }
 
 int64_t synth_n_packets(const synth_result *r) { return r->n_packets; }
+
+/* true times of the first pixel and first TDC packet of the generated range
+   (-1 if none): a slice's wrap counts before its first packet follow from them */
+void synth_first_times(const synth_result *r, int64_t *pix_t, int64_t *tdc_t) {
+    *pix_t = -1; *tdc_t = -1;
+    for (int i = 0; i < r->n_jobs; i++) {
+        if (*pix_t < 0 && r->jobs[i].w.first_pix_t >= 0) *pix_t = r->jobs[i].w.first_pix_t;
+        if (*tdc_t < 0 && r->jobs[i].w.first_tdc_t >= 0) *tdc_t = r->jobs[i].w.first_tdc_t;
+    }
+}
 int64_t synth_n_particles(const synth_result *r) { return r->n_particles; }
 
 typedef struct { uint64_t *dst; const uint64_t *src; int64_t n; } cp_t;

@@ -345,3 +345,29 @@ def test_empty_and_degenerate_inputs():
         b.pix(1, 1, 1, 1)         # no trigger at all
     r = oracle.run(b.packets())
     assert r["counters"]["dropped_pre_trigger"] == 3 and r["clusters"].size == 0
+
+
+def test_slice_with_initial_epochs_matches_full_stream():
+    """A slice cut from the middle of a stream, given the number of wraps
+    before it, reproduces the full stream's times and clusters for its shots."""
+    p = synth.small(n_shots=40, shot_begin=480)
+    full, _, trig = synth.generate(p)
+    rf = oracle.run(full, want_info=True)
+    tdc_pos = np.flatnonzero((full >> np.uint64(60)) == 6)
+    k = 25
+    sl = full[tdc_pos[k]:tdc_pos[k + 1]]
+    tk = int(trig[k])
+    P, PT = 1 << 34, 1 << 36
+    # first pixel: the epoch whose time lies within half a period of the trigger
+    w = int(sl[1])
+    raw = ((((w & 0xFFFF) << 14) | ((w >> 30) & 0x3FFF)) * 16 - ((w >> 16) & 0xF)) % P
+    e_pix = round((tk - raw) / P)
+    cfg = oracle.Config(epoch0_pix=e_pix, epoch0_tdc=tk // PT)
+    rs = oracle.run(sl, cfg, idx_base=int(tdc_pos[k]), want_info=True)
+    assert rs["triggers"][0] == tk
+    assert np.array_equal(rs["info"]["t"], rf["info"]["t"][tdc_pos[k]:tdc_pos[k + 1]])
+    cf = rf["clusters"][rf["clusters"]["shot"] == k]
+    cs = rs["clusters"].copy()
+    cs["shot"] += k
+    assert np.array_equal(cf, cs)
+    assert np.array_equal(rs["labels"], rf["labels"][tdc_pos[k]:tdc_pos[k + 1]])
