@@ -125,19 +125,34 @@ __device__ __forceinline__ uint32_t hcell(int seg, int x, int y) {
     return (uint32_t)(x + 67 * y + 1543 * seg) & (HB - 1);
 }
 
-__device__ __forceinline__ uint32_t find_root(volatile uint32_t *parent, uint32_t x) {
+// Union-find over a shared-memory parent array, addressed explicitly in the
+// shared window (32-bit addresses, ld/st.volatile.shared, atom.shared.cas).
+__device__ __forceinline__ uint32_t sh_ld(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sh_st(uint32_t a, uint32_t v) {
+    asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t sh_cas(uint32_t a, uint32_t cmp, uint32_t v) {
+    uint32_t o;
+    asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(o) : "r"(a), "r"(cmp), "r"(v) : "memory");
+    return o;
+}
+__device__ __forceinline__ uint32_t find_root(uint32_t pbase, uint32_t x) {
     for (;;) {
-        uint32_t p = parent[x];
+        const uint32_t p = sh_ld(pbase + 4 * x);
         if (p == x) return x;
-        uint32_t g = parent[p];
+        const uint32_t g = sh_ld(pbase + 4 * p);
         if (g == p) return p;
-        parent[x] = g;            // path halving: g is an ancestor of x
+        sh_st(pbase + 4 * x, g);   // path halving: g is an ancestor of x
         x = g;
     }
 }
-__device__ __forceinline__ uint32_t find_ro(const volatile uint32_t *parent, uint32_t x) {
+__device__ __forceinline__ uint32_t find_ro(uint32_t pbase, uint32_t x) {
     uint32_t p;
-    while ((p = parent[x]) != x) x = p;
+    while ((p = sh_ld(pbase + 4 * x)) != x) x = p;
     return x;
 }
 
@@ -271,14 +286,51 @@ __device__ long long lookback_count(const Params &p, long long tile, unsigned se
 __device__ __forceinline__ uint64_t rkey(const Smem &S, uint32_t q) {
     return ((uint64_t)r_tof(S.buf[pad((int)q)]) << 16) | q;
 }
-__device__ void unite(Smem &S, uint32_t a, uint32_t b) {
-    volatile uint32_t *vp = S.parent;
+// Warp-synchronous union of (a, b) for every lane with `have`: each trip of
+// the loop advances every active lane by one step -- a find hop (with path
+// halving) on a or b, or one linking attempt once both are roots -- so the
+// lanes stay converged.  The root of the smaller key (time, position) wins,
+// making each component's root its earliest pixel.  Returns the root reached
+// on a's side (a hint for the next union of the same pixel).
+__device__ __forceinline__ uint32_t unite_ws(const Smem &S, uint32_t pbase, bool have, uint32_t a, uint32_t b) {
+    bool active = have;
+    while (__any_sync(0xffffffffu, active)) {
+        if (active) {
+            const uint32_t pa = sh_ld(pbase + 4 * a);
+            const uint32_t pb = sh_ld(pbase + 4 * b);
+            if (pa != a || pb != b) {
+                if (pa != a) {
+                    const uint32_t ga = sh_ld(pbase + 4 * pa);
+                    if (ga != pa) sh_st(pbase + 4 * a, ga);
+                    a = ga;
+                }
+                if (pb != b) {
+                    const uint32_t gb = sh_ld(pbase + 4 * pb);
+                    if (gb != pb) sh_st(pbase + 4 * b, gb);
+                    b = gb;
+                }
+            } else if (a == b) {
+                active = false;
+            } else {
+                uint32_t lo = a, hi = b;
+                if (rkey(S, a) > rkey(S, b)) { lo = b; hi = a; }
+                const uint32_t old = sh_cas(pbase + 4 * hi, hi, lo);
+                if (old == hi) active = false;
+                else b = old;           // hi was linked meanwhile: continue above it
+                a = lo;
+            }
+        }
+    }
+    return a;
+}
+
+__device__ void unite_one(const Smem &S, uint32_t pbase, uint32_t a, uint32_t b) {
     for (;;) {
-        a = find_root(vp, a);
-        b = find_root(vp, b);
+        a = find_root(pbase, a);
+        b = find_root(pbase, b);
         if (a == b) return;
         if (rkey(S, a) > rkey(S, b)) { uint32_t t = a; a = b; b = t; }
-        uint32_t old = atomicCAS(&S.parent[b], b, a);
+        const uint32_t old = sh_cas(pbase + 4 * b, b, a);
         if (old == b) return;
         b = old;
     }
@@ -292,6 +344,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
     const int tid = threadIdx.x, lane = tid & 31;
     const long long tp = p.thr_pix, tt = p.thr_tdc;
     const unsigned seq = p.seq & 0x3FFFFFFFu;
+    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(S.parent);
 
     for (;;) {
         __syncthreads();
@@ -497,6 +550,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             }
             if (exc) atomicOr(&S.status, ST_EXCEPTION);
         }
+        __syncthreads();   // records written per contiguous chunk are read strided below
 
         // the range this CTA owns: [R0, R1)
         const int R0 = (f == INT_MAX) ? 0 : f;
@@ -519,27 +573,86 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         __syncthreads();
 
         // ---- neighbour pass: each adjacent pair once (Sec. V.A box rule) ----
-        for (int q = R0 + tid; q < R1; q += NT) {
-            const uint64_t r = S.buf[pad(q)];
-            if (r == INVALID) continue;
-            const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
-            for (int dx = 0; dx <= p.rx; ++dx) {
-                const int cx = x + dx;
-                if (cx > 255) break;
-                for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
-                    const int cy = y + dy;
-                    if (cy < 0 || cy > 255) continue;
-                    for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
-                        if (dx == 0 && dy == 0 && (int)j <= q) continue;
-                        const uint64_t rj = S.buf[pad((int)j)];
-                        if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
-                        const int d = r_tof(rj) - tb;
-                        if (d < -p.dt || d > p.dt) continue;
-                        const int tj = r_tot(rj);
-                        // local maxima: equal ToT goes to the later pixel (Sec. V.B)
-                        if (tj > tot || (tj == tot && (int)j > q)) S.notpeak[q] = 1;
-                        else S.notpeak[j] = 1;
-                        if (MODE == TPX_MODE_CC) unite(S, (uint32_t)q, j);
+        // Warp-synchronous: the warp walks 32 consecutive positions at a time;
+        // one trip of the lookup loop advances every lane by one hash-chain
+        // node or one neighbour cell, and the unions run afterwards, also one
+        // step per trip (nested data-dependent loops would serialise lanes).
+        {
+            const int ndir = (p.ry + 1) + p.rx * (2 * p.ry + 1);   // forward half of the box
+            for (int qb = R0 + (tid & ~31); qb < R1; qb += NT) {
+                const int q = qb + lane;
+                const uint64_t r = q < R1 ? S.buf[pad(q)] : INVALID;
+                bool active = r != INVALID;
+                const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
+                uint64_t eb0 = 0, eb1 = 0;
+                int ne = 0, di = -1, cx = 0, cy = 0;
+                bool dim = false, own = false;
+                uint32_t j = EMPTY;
+                while (__any_sync(0xffffffffu, active)) {
+                    if (active) {
+                        if (j == EMPTY) {
+                            ++di;
+                            if (di >= ndir) {
+                                active = false;
+                            } else {
+                                int dx, dy;
+                                if (di <= p.ry) { dx = 0; dy = di; }
+                                else { const int k = di - (p.ry + 1); dx = 1 + k / (2 * p.ry + 1); dy = k % (2 * p.ry + 1) - p.ry; }
+                                cx = x + dx;
+                                cy = y + dy;
+                                own = (dx == 0 && dy == 0);
+                                j = (cx <= 255 && cy >= 0 && cy <= 255) ? S.u1.head[hcell(sg, cx, cy)] : EMPTY;
+                            }
+                        } else {
+                            const uint64_t rj = S.buf[pad((int)j)];
+                            const uint32_t jn = S.u2.next[j];
+                            const int d = r_tof(rj) - tb;
+                            if (!(own && (int)j <= q) && r_x(rj) == cx && r_y(rj) == cy && r_seg(rj) == sg &&
+                                d >= -p.dt && d <= p.dt) {
+                                const int tj = r_tot(rj);
+                                // local maxima: equal ToT goes to the later pixel (Sec. V.B)
+                                if (tj > tot || (tj == tot && (int)j > q)) dim = true;
+                                else S.notpeak[j] = 1;
+                                if (MODE == TPX_MODE_CC && ne < 8) {
+                                    if (ne < 4) eb0 |= (uint64_t)j << (16 * ne);
+                                    else eb1 |= (uint64_t)j << (16 * (ne - 4));
+                                    ++ne;
+                                }
+                            }
+                            j = jn;
+                        }
+                    }
+                }
+                if (dim) S.notpeak[q] = 1;
+                if (MODE == TPX_MODE_CC) {
+                    if (__any_sync(0xffffffffu, ne >= 8)) {
+                        // more than 8 partners (only with larger radii): unite in
+                        // the slow nested form, one lane at a time
+                        for (int l = 0; l < 32; ++l) {
+                            if (__shfl_sync(0xffffffffu, ne, l) >= 8 && lane == l) {
+                                for (int dx = 0; dx <= p.rx; ++dx)
+                                    for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
+                                        const int ux = x + dx, uy = y + dy;
+                                        if (ux > 255 || uy < 0 || uy > 255) continue;
+                                        for (uint32_t jj = S.u1.head[hcell(sg, ux, uy)]; jj != EMPTY; jj = S.u2.next[jj]) {
+                                            if (dx == 0 && dy == 0 && (int)jj <= q) continue;
+                                            const uint64_t rj = S.buf[pad((int)jj)];
+                                            if (r_x(rj) != ux || r_y(rj) != uy || r_seg(rj) != sg) continue;
+                                            const int d = r_tof(rj) - tb;
+                                            if (d < -p.dt || d > p.dt) continue;
+                                            unite_one(S, pbase, (uint32_t)q, jj);
+                                        }
+                                    }
+                                ne = 0;
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)ne);
+                    uint32_t rq = (uint32_t)(q < R1 ? q : 0);
+                    for (int k = 0; k < kmax; ++k) {
+                        const uint64_t w = k < 4 ? eb0 : eb1;
+                        rq = unite_ws(S, pbase, k < ne, rq, (uint32_t)((w >> (16 * (k & 3))) & 0xFFFF));
                     }
                 }
             }
@@ -549,48 +662,19 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         int ncl = 0;
         if (MODE == TPX_MODE_CC) {
             for (int q = R0 + tid; q < R1; q += NT)
-                if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(S.parent, (uint32_t)q);
+                if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(pbase, (uint32_t)q);
             __syncthreads();
+            // cluster ids in ascending root position (= ascending label)
             int c = 0;
             for (int j = 0; j < KP; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
             }
             int excl = block_scan_int(S, c, &ncl);
-            if (ncl > M && tid == 0) atomicOr(&S.status, ST_CAPACITY);
             for (int j = 0; j < KP; ++j) {
                 const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
-                    S.u1.cid[q] = (uint32_t)excl;
-                    if (excl < M) S.rootpos[excl] = (uint16_t)q;
-                    ++excl;
-                }
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) S.u1.cid[q] = (uint32_t)excl++;
             }
-            for (int i = tid; i < min(ncl, M); i += NT) { S.acc0[i] = 0; S.acc1[i] = 0; S.acc2[i] = 0; }
-            __syncthreads();
-            unsigned long long c_pk = 0;
-            for (int q = W0 + tid; q < W1; q += NT) {
-                const uint64_t r = S.buf[pad(q)];
-                long long lab = -1;
-                uint8_t pk = 0;
-                if (q >= R0 && r != INVALID) {
-                    const uint32_t root = S.u2.rootof[q];
-                    const uint32_t ci = S.u1.cid[root];
-                    pk = S.notpeak[q] ? 0 : 1;
-                    c_pk += pk;
-                    if (ci < (uint32_t)M) {
-                        const unsigned long long tot = (unsigned long long)r_tot(r);
-                        atomicAdd(&S.acc0[ci], tot | (1ull << 24) | ((unsigned long long)pk << 44));
-                        atomicAdd(&S.acc1[ci], (tot * (unsigned long long)r_x(r)) | ((tot * (unsigned long long)r_y(r)) << 32));
-                        atomicAdd(&S.acc2[ci], tot * (unsigned long long)r_tof(r));
-                    }
-                    lab = p.idx_base + base + (long long)root;
-                }
-                if (p.labels) p.labels[base + q] = lab;
-                if (p.is_peak) p.is_peak[base + q] = pk;
-            }
-            c_pk = warp_sum(c_pk);
-            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
         } else {
             // PAPER mode: one record per local maximum (list kept in parent[])
             int c = 0;
@@ -603,25 +687,10 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) S.parent[excl++] = (uint32_t)q;
             }
-            unsigned long long c_pk = 0;
-            for (int q = W0 + tid; q < W1; q += NT) {
-                const uint64_t r = S.buf[pad(q)];
-                long long lab = -1;
-                uint8_t pk = 0;
-                if (q >= R0 && r != INVALID) {
-                    lab = p.idx_base + base + q;
-                    pk = S.notpeak[q] ? 0 : 1;
-                    c_pk += pk;
-                }
-                if (p.labels) p.labels[base + q] = lab;
-                if (p.is_peak) p.is_peak[base + q] = pk;
-            }
-            c_pk = warp_sum(c_pk);
-            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
-            __syncthreads();
         }
 
-        // ---- cluster offsets: second decoupled look-back over record counts ----
+        // ---- record offsets: second decoupled look-back over record counts,
+        //      published as soon as the count is known ----
         if (tid == 0) {
             unsigned st2 = 0;
             long long O = 0;
@@ -646,33 +715,85 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         __syncthreads();
         const long long O = S.clo;
 
-        // ---- cluster records (Sec. V.C centre of mass, exact integer sums) ----
         if (MODE == TPX_MODE_CC) {
-            for (int i = tid; i < min(ncl, M); i += NT) {
-                if (O + i >= p.cl_cap) break;
-                const int q = S.rootpos[i];
-                const uint64_t r = S.buf[pad(q)];
-                const unsigned long long a0 = S.acc0[i], a1 = S.acc1[i], a2 = S.acc2[i];
-                const long long s_tot = (long long)(a0 & 0xFFFFFFull);
-                const int n = (int)((a0 >> 24) & 0xFFFFFull);
-                const int npk = (int)(a0 >> 44);
-                const long long s_x = (long long)(a1 & 0xFFFFFFFFull), s_y = (long long)(a1 >> 32);
-                const long long tofb0 = r_tof(r);
-                const long long s_t = (long long)a2 - tofb0 * s_tot;
-                const int seg = r_seg(r);
-                const long long tofc0 = tofb0 - kTofBias;
-                tpx_cluster o;
-                o.label = p.idx_base + base + q;
-                o.shot = E.tdc.n + seg;
-                o.t0 = S.tdc_t[seg] + tofc0;
-                o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
-                o.n = n; o.n_peaks = npk;
-                o.x = (double)s_x / (double)s_tot;
-                o.y = (double)s_y / (double)s_tot;
-                o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
-                p.clusters[O + i] = o;
+            // accumulate in batches of M cluster ids (one batch in normal data);
+            // the first batch also writes the per-packet outputs
+            unsigned long long c_pk = 0;
+            for (int c0 = 0; c0 == 0 || c0 < ncl; c0 += M) {
+                const int nb = min(M, ncl - c0);
+                for (int i = tid; i < nb; i += NT) { S.acc0[i] = 0; S.acc1[i] = 0; S.acc2[i] = 0; }
+                __syncthreads();
+                for (int q = W0 + tid; q < W1; q += NT) {
+                    const uint64_t r = S.buf[pad(q)];
+                    const bool kept = q >= R0 && r != INVALID;
+                    uint32_t root = 0;
+                    int ci = -1;
+                    uint8_t pk = 0;
+                    if (kept) {
+                        root = S.u2.rootof[q];
+                        ci = (int)S.u1.cid[root] - c0;
+                        pk = S.notpeak[q] ? 0 : 1;
+                        if (ci >= 0 && ci < nb) {
+                            const unsigned long long tot = (unsigned long long)r_tot(r);
+                            atomicAdd(&S.acc0[ci], tot | (1ull << 24) | ((unsigned long long)pk << 44));
+                            atomicAdd(&S.acc1[ci], (tot * (unsigned long long)r_x(r)) | ((tot * (unsigned long long)r_y(r)) << 32));
+                            atomicAdd(&S.acc2[ci], tot * (unsigned long long)r_tof(r));
+                            if (root == (uint32_t)q) S.rootpos[ci] = (uint16_t)q;
+                        }
+                    }
+                    if (c0 == 0) {
+                        c_pk += pk;
+                        if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)root : -1LL;
+                        if (p.is_peak) p.is_peak[base + q] = pk;
+                    }
+                }
+                __syncthreads();
+                // cluster records (Sec. V.C centre of mass from exact integer sums)
+                for (int i = tid; i < nb; i += NT) {
+                    if (O + c0 + i >= p.cl_cap) break;
+                    const int q = S.rootpos[i];
+                    const uint64_t r = S.buf[pad(q)];
+                    const unsigned long long a0 = S.acc0[i], a1 = S.acc1[i], a2 = S.acc2[i];
+                    const long long s_tot = (long long)(a0 & 0xFFFFFFull);
+                    const int n = (int)((a0 >> 24) & 0xFFFFFull);
+                    const int npk = (int)(a0 >> 44);
+                    const long long s_x = (long long)(a1 & 0xFFFFFFFFull), s_y = (long long)(a1 >> 32);
+                    const long long tofb0 = r_tof(r);
+                    const long long s_t = (long long)a2 - tofb0 * s_tot;
+                    const int seg = r_seg(r);
+                    const long long tofc0 = tofb0 - kTofBias;
+                    tpx_cluster o;
+                    o.label = p.idx_base + base + q;
+                    o.shot = E.tdc.n + seg;
+                    o.t0 = S.tdc_t[seg] + tofc0;
+                    o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
+                    o.n = n; o.n_peaks = npk;
+                    o.x = (double)s_x / (double)s_tot;
+                    o.y = (double)s_y / (double)s_tot;
+                    o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
+                    p.clusters[O + c0 + i] = o;
+                }
+                __syncthreads();
             }
+            c_pk = warp_sum(c_pk);
+            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
         } else {
+            unsigned long long c_pk = 0;
+            for (int q = W0 + tid; q < W1; q += NT) {
+                const uint64_t r = S.buf[pad(q)];
+                long long lab = -1;
+                uint8_t pk = 0;
+                if (q >= R0 && r != INVALID) {
+                    lab = p.idx_base + base + q;
+                    pk = S.notpeak[q] ? 0 : 1;
+                    c_pk += pk;
+                }
+                if (p.labels) p.labels[base + q] = lab;
+                if (p.is_peak) p.is_peak[base + q] = pk;
+            }
+            c_pk = warp_sum(c_pk);
+            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
+            // records: box neighbourhood sums of each local maximum (Sec. V.C)
             for (int i = tid; i < ncl; i += NT) {
                 if (O + i >= p.cl_cap) break;
                 const int q = (int)S.parent[i];
