@@ -152,6 +152,33 @@ int tpx_process_host(tpx_ctx *ctx, const uint64_t *h_packets, int64_t n_packets,
    of the last call into a status code.  If counters != NULL, fill it. */
 int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
 
+/* Upper bound on n_packets for tpx_process_noalloc (2^26 packets, 512 MB of
+   input): the size of its fixed scratch array. */
+#define TPX_NOALLOC_MAX_PACKETS (1LL << 26)
+
+/* The fused path without any device allocation (no counterpart in the paper;
+   it serves callers that cannot call cudaMalloc where they process data --
+   code running while a CUDA graph is captured, real-time acquisition loops that
+   must not block in the allocator, hosts that fix the library's memory up
+   front).  Same inputs, outputs and results as tpx_process, but no context:
+   the configuration and the CUDA stream are passed directly, and the
+   look-back scratch is one fixed array in device memory that is part of the
+   library (about 2.4 MB per device that loads it, held until exit).
+   The first call on each device, with that device current, looks up the
+   array's device address (cudaGetSymbolAddress); make that first call before
+   any stream capture.  All calls on a device share the array and it keeps the
+   last call's contents (the per-call control block is cleared first): calls
+   that overlap on the GPU race and must not be made.  The call synchronises
+   the stream and returns the status that tpx_sync would; if h_counters is not
+   NULL it receives the counters.
+   Errors: TPX_EINVAL for a bad configuration or argument, or n_packets above
+   TPX_NOALLOC_MAX_PACKETS; then the status codes of tpx_sync. */
+int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t *d_packets,
+                        int64_t n_packets, int64_t packet_index_base, int64_t *d_labels,
+                        uint8_t *d_is_peak, tpx_cluster *d_clusters, int64_t cluster_capacity,
+                        int64_t *d_n_clusters, int64_t *d_trig_t, int64_t trig_capacity,
+                        int64_t *d_n_trig, tpx_counters *h_counters);
+
 /* Static description of a status code. */
 const char *tpx_strerror(int code);
 

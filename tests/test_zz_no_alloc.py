@@ -1,0 +1,98 @@
+"""tpx_process_noalloc: the fused path for callers that cannot allocate
+device memory where they process data (for example code running during CUDA
+graph capture, or acquisition loops that must not block in the allocator).
+
+Called through the C ABI, its output must match tpx_process on the same input
+on two calls in a row (the shared fixed scratch keeps the previous call's
+contents, which must not leak into the next result). Collected last so that a
+stop-at-first-failure run has already run every other test; it passes alone
+in a fresh process as well.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import TOL, INT_FIELDS, FLOAT_FIELDS, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+NOALLOC_MAX_PACKETS = 1 << 26
+
+
+def _lib():
+    import paper_2603_04942_gb300 as tpx
+    from paper_2603_04942_gb300 import build as b
+    b.build()
+    L = tpx.load()
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.tpx_process_noalloc.argtypes = [ctypes.POINTER(tpx._CConfig), vp, vp, i64, i64, vp, vp, vp, i64, vp, vp,
+                                      i64, vp, ctypes.POINTER(tpx._CCounters)]
+    L.tpx_process_noalloc.restype = ctypes.c_int
+    return tpx, L
+
+
+def _noalloc_run(tpx, L, pk, cfg, index_base=0):
+    import torch
+    n = pk.size
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    cl_cap, tr_cap = max(16, n), max(16, n)
+    labels = torch.full((n,), -7, dtype=torch.int64, device="cuda")
+    is_peak = torch.full((n,), 9, dtype=torch.uint8, device="cuda")
+    clusters = torch.zeros(cl_cap * tpx.CLUSTER_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    trig = torch.zeros(tr_cap, dtype=torch.int64, device="cuda")
+    n_cl = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n_tr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = tpx._CCounters()
+    torch.cuda.synchronize()
+    rc = L.tpx_process_noalloc(ctypes.byref(cfg), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                               d.data_ptr(), n, index_base, labels.data_ptr(), is_peak.data_ptr(),
+                               clusters.data_ptr(), cl_cap, n_cl.data_ptr(), trig.data_ptr(), tr_cap,
+                               n_tr.data_ptr(), ctypes.byref(cnt))
+    ncl, ntr = int(n_cl.item()), int(n_tr.item())
+    raw = clusters[: ncl * tpx.CLUSTER_DTYPE.itemsize].cpu().numpy()
+    return dict(status=rc, labels=labels.cpu().numpy(), is_peak=is_peak.cpu().numpy(),
+                clusters=np.frombuffer(raw.tobytes(), tpx.CLUSTER_DTYPE).copy(), n_clusters=ncl,
+                triggers=trig[:ntr].cpu().numpy(), counters={f: int(getattr(cnt, f)) for f in
+                                                             ("kept", "clusters", "peaks", "pixels")})
+
+
+def _same(a, b):
+    assert a["status"] == 0 and b["status"] == 0
+    assert np.array_equal(a["labels"], b["labels"])
+    assert np.array_equal(a["is_peak"], b["is_peak"])
+    assert np.array_equal(a["triggers"], b["triggers"])
+    assert a["n_clusters"] == b["n_clusters"] == a["clusters"].size == b["clusters"].size
+    for f in INT_FIELDS:
+        assert np.array_equal(a["clusters"][f], b["clusters"][f]), f
+    for f in FLOAT_FIELDS:
+        assert np.all(np.abs(a["clusters"][f] - b["clusters"][f]) <= TOL), f
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_noalloc_matches_tpx_process_twice(mode):
+    tpx, L = _lib()
+    pk = synth.generate(synth.large(n_shots=300, dark_per_shot=2.0))[0]
+    ref = gpu_run(pk, mode=mode, index_base=5)
+    cfg = tpx._CConfig()
+    L.tpx_config_default(ctypes.byref(cfg))
+    cfg.mode = mode
+    first = _noalloc_run(tpx, L, pk, cfg, index_base=5)
+    second = _noalloc_run(tpx, L, pk, cfg, index_base=5)
+    _same(first, ref)
+    _same(second, ref)
+    assert first["counters"]["kept"] == ref["counters"]["kept"]
+    # a different, smaller input right after: nothing of the previous call leaks
+    pk2 = pk[: 3 * 4096 + 11]
+    _same(_noalloc_run(tpx, L, pk2, cfg), gpu_run(pk2, mode=mode))
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    tpx, L = _lib()
+    cfg = tpx._CConfig()
+    L.tpx_config_default(ctypes.byref(cfg))
+    dummy = ctypes.c_int64()
+    rc = L.tpx_process_noalloc(ctypes.byref(cfg), None, None, NOALLOC_MAX_PACKETS + 1, 0, None, None, None, 0,
+                               ctypes.addressof(dummy), None, 0, ctypes.addressof(dummy), None)
+    assert rc == tpx.EINVAL
