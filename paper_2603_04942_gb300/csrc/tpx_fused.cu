@@ -9,7 +9,7 @@
 
 namespace tpxk {
 
-constexpr int NT = 512;            // threads per CTA
+constexpr int NT = 1024;           // threads per CTA
 constexpr int NW = NT / 32;
 constexpr int T = 4096;            // packets per tile
 constexpr int C = 8192;            // range capacity (tile + look-ahead), positions
@@ -24,7 +24,7 @@ constexpr long long MAX_SPIN = 1LL << 22;   // bounded look-back waits (~0.5 s)
 static_assert(T % NT == 0 && C % NT == 0 && T <= C && C <= 16384, "tile geometry");
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ int pad(int p) { return p + (p >> 4); }   // conflict-free 16-wide walks
+__device__ __forceinline__ int pad(int p) { return p + (p >> 3); }   // conflict-free 8-wide walks
 
 // kept-pixel record: [63:40] tof+bias | [39:26] segment | [25:16] ToT | [15:8] y | [7:0] x
 __device__ __forceinline__ uint64_t mkrec(uint32_t tofb, uint32_t seg, uint32_t tot, uint32_t x, uint32_t y) {
@@ -158,18 +158,22 @@ __device__ __forceinline__ uint32_t find_ro(uint32_t pbase, uint32_t x) {
 
 // --------------------------------------------------------------- smem layout
 struct __align__(16) Smem {
-    uint64_t buf[C + C / 16];                         // packets, then kept-pixel records
+    uint64_t buf[C + C / 8];                          // packets, then kept-pixel records
     uint32_t parent[C];                               // union-find (CC) / peak list (PAPER)
     union { uint32_t head[HB]; uint32_t cid[C]; } u1; // hash heads, then cluster ids
     union { uint16_t next[C]; uint16_t rootof[C]; } u2;
     uint8_t notpeak[C];
-    unsigned long long acc0[M];   // ToT | n<<24 | peaks<<44
-    unsigned long long acc1[M];   // x*ToT | (y*ToT)<<32
-    unsigned long long acc2[M];   // (tof+bias)*ToT
+    uint32_t a_tot[M];            // sum ToT
+    uint32_t a_np[M];             // pixel count | local maxima << 16
+    uint32_t a_x[M];              // sum x*ToT
+    uint32_t a_y[M];              // sum y*ToT
+    uint32_t a_dt[M];             // sum (t - t0)*ToT, low 32 bits
+    uint32_t a_dth[M];            // its high 32 bits (carries)
     uint16_t rootpos[M];
     long long tdc_t[MAXSEG];
     GAgg warp_agg[NW];
     GAgg tot_agg;
+    GAgg tile_agg;                // this tile's chain aggregate
     GAgg E;                       // unwrap state before the tile
     int warp_int[NW + 1];
     unsigned long long cnt[C_NUM];
@@ -244,40 +248,99 @@ __device__ __forceinline__ bool timed_out(const Params &p) {
     return (*reinterpret_cast<volatile unsigned *>(&p.ctl->status) & ST_DEVTIMEOUT) != 0;
 }
 
-// bounded decoupled look-back over the unwrap chains (thread 0 only)
-__device__ GAgg lookback_agg(const Params &p, long long tile, unsigned seq, unsigned *status) {
+__device__ __forceinline__ GChain shfl_down_chain(const GChain &v, int o) {
+    GChain u;
+    u.n = __shfl_down_sync(0xffffffffu, v.n, o);
+    u.first = __shfl_down_sync(0xffffffffu, v.first, o);
+    u.last = __shfl_down_sync(0xffffffffu, v.last, o);
+    u.sum = __shfl_down_sync(0xffffffffu, v.sum, o);
+    return u;
+}
+
+// Bounded decoupled look-back over the unwrap chains, one warp: each trip
+// reads the flags of 32 predecessors at once, combines the aggregates in
+// stream order up to the nearest inclusive prefix, and stops there.
+// Called by all lanes of one warp; every lane returns the exclusive prefix.
+__device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
+    const int lane = threadIdx.x & 31;
     GAgg acc = agg_id();
-    for (long long q = tile - 1; q >= 0;) {
+    for (long long hi = tile - 1; hi >= 0; hi -= 32) {
+        const long long q = hi - lane;
         unsigned f = 0;
         long long spins = 0;
         for (;;) {
-            f = ld_acquire(&p.ts.flags[q]);
-            if ((f >> 2) == seq && (f & 3u)) break;
-            if (++spins > MAX_SPIN || timed_out(p)) { atomicOr(&p.ctl->status, ST_DEVTIMEOUT); *status |= ST_DEVTIMEOUT; return acc; }
+            bool ready = true;
+            if (q >= 0) {
+                f = ld_acquire(&p.ts.flags[q]);
+                ready = (f >> 2) == seq && (f & 3u);
+            }
+            if (__all_sync(0xffffffffu, ready)) break;
+            if (++spins > MAX_SPIN || timed_out(p)) {
+                if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
+                *status |= ST_DEVTIMEOUT;
+                return acc;
+            }
             __nanosleep(64);
         }
-        if ((f & 3u) == 2u) { acc = acomb(ld_agg(&p.ts.pre[q]), acc, p.thr_pix, p.thr_tdc); break; }
-        acc = acomb(ld_agg(&p.ts.agg[q]), acc, p.thr_pix, p.thr_tdc);
-        --q;
+        const unsigned pm = __ballot_sync(0xffffffffu, q >= 0 && (f & 3u) == 2u);
+        const int stop = pm ? __ffs(pm) - 1 : 31;
+        GAgg v = agg_id();
+        if (q >= 0 && lane <= stop) v = ld_agg((pm && lane == stop) ? &p.ts.pre[q] : &p.ts.agg[q]);
+        // lane L holds tile hi-L: combine earlier tiles (higher lanes) on the left
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            GAgg u;
+            u.pix = shfl_down_chain(v.pix, o);
+            u.tdc = shfl_down_chain(v.tdc, o);
+            if (lane + o < 32) v = acomb(u, v, p.thr_pix, p.thr_tdc);
+        }
+        GAgg r;
+        r.pix = shfl_down_chain(v.pix, 0);
+        r.tdc = shfl_down_chain(v.tdc, 0);
+        r.pix.n = __shfl_sync(0xffffffffu, v.pix.n, 0);
+        r.pix.first = __shfl_sync(0xffffffffu, v.pix.first, 0);
+        r.pix.last = __shfl_sync(0xffffffffu, v.pix.last, 0);
+        r.pix.sum = __shfl_sync(0xffffffffu, v.pix.sum, 0);
+        r.tdc.n = __shfl_sync(0xffffffffu, v.tdc.n, 0);
+        r.tdc.first = __shfl_sync(0xffffffffu, v.tdc.first, 0);
+        r.tdc.last = __shfl_sync(0xffffffffu, v.tdc.last, 0);
+        r.tdc.sum = __shfl_sync(0xffffffffu, v.tdc.sum, 0);
+        acc = acomb(r, acc, p.thr_pix, p.thr_tdc);
+        if (pm) break;
     }
     return acc;
 }
 
-// bounded decoupled look-back over cluster counts (thread 0 only)
-__device__ long long lookback_count(const Params &p, long long tile, unsigned seq, unsigned *status) {
+// The same over the record counts of the tiles.
+__device__ long long lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
+    const int lane = threadIdx.x & 31;
     long long acc = 0;
-    for (long long q = tile - 1; q >= 0;) {
+    for (long long hi = tile - 1; hi >= 0; hi -= 32) {
+        const long long q = hi - lane;
         unsigned f = 0;
         long long spins = 0;
         for (;;) {
-            f = ld_acquire(&p.ts.cflags[q]);
-            if ((f >> 2) == seq && (f & 3u)) break;
-            if (++spins > MAX_SPIN || timed_out(p)) { atomicOr(&p.ctl->status, ST_DEVTIMEOUT); *status |= ST_DEVTIMEOUT; return acc; }
+            bool ready = true;
+            if (q >= 0) {
+                f = ld_acquire(&p.ts.cflags[q]);
+                ready = (f >> 2) == seq && (f & 3u);
+            }
+            if (__all_sync(0xffffffffu, ready)) break;
+            if (++spins > MAX_SPIN || timed_out(p)) {
+                if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
+                *status |= ST_DEVTIMEOUT;
+                return acc;
+            }
             __nanosleep(64);
         }
-        if ((f & 3u) == 2u) { acc += __ldcg(&p.ts.cpre[q]); break; }
-        acc += __ldcg(&p.ts.cagg[q]);
-        --q;
+        const unsigned pm = __ballot_sync(0xffffffffu, q >= 0 && (f & 3u) == 2u);
+        const int stop = pm ? __ffs(pm) - 1 : 31;
+        long long v = 0;
+        if (q >= 0 && lane <= stop) v = __ldcg((pm && lane == stop) ? &p.ts.cpre[q] : &p.ts.cagg[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc += v;
+        if (pm) break;
     }
     return acc;
 }
@@ -398,25 +461,20 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             }
             if (my_first != INT_MAX) atomicMin(&S.first_tdc, my_first);
         }
-        // publish the aggregate, look back, publish the inclusive prefix
+        // publish the tile's aggregate now; the look-back waits until after the
+        // read-ahead and the block scan, which do not need it
         if (tid == 0) {
-            const GAgg tot = S.tot_agg;
-            GAgg E = agg_id();
-            unsigned st = 0;
+            S.tile_agg = S.tot_agg;
             if (tile > 0) {
-                st_agg(&p.ts.agg[tile], tot);
+                st_agg(&p.ts.agg[tile], S.tot_agg);
                 st_release(&p.ts.flags[tile], (seq << 2) | 1u);
-                E = lookback_agg(p, tile, seq, &st);
+            } else {
+                st_agg(&p.ts.pre[0], S.tot_agg);
+                st_release(&p.ts.flags[0], (seq << 2) | 2u);
             }
-            st_agg(&p.ts.pre[tile], acomb(E, tot, tp, tt));
-            st_release(&p.ts.flags[tile], (seq << 2) | 2u);
-            S.E = E;
-            atomicOr(&S.status, st);
         }
         __syncthreads();
-        const GAgg E = S.E;
         const int f = S.first_tdc;
-        const bool prev_global = E.tdc.n > 0;
 
         // ---- look ahead past the tile up to the next TDC packet ----
         int L = cnt;
@@ -461,6 +519,23 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             ex = block_scan_agg(S, a, tp, tt);
             ntdc = (int)S.tot_agg.tdc.n;
         }
+        // ---- unwrap state before the tile: warp-parallel look-back ----
+        if (tid < 32) {
+            unsigned stl = 0;
+            GAgg Ew = agg_id();
+            if (tile > 0) Ew = lookback_agg_warp(p, tile, seq, &stl);
+            if (tid == 0) {
+                if (tile > 0) {
+                    st_agg(&p.ts.pre[tile], acomb(Ew, S.tile_agg, tp, tt));
+                    st_release(&p.ts.flags[tile], (seq << 2) | 2u);
+                }
+                S.E = Ew;
+                if (stl) atomicOr(&S.status, stl);
+            }
+        }
+        __syncthreads();
+        const GAgg E = S.E;
+        const bool prev_global = E.tdc.n > 0;
         const GAgg st = acomb(E, ex, tp, tt);   // global chain state before position p0
 
         // ---- walk 3: unwrapped trigger times ----
@@ -573,82 +648,71 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         __syncthreads();
 
         // ---- neighbour pass: each adjacent pair once (Sec. V.A box rule) ----
-        // Warp-synchronous: the warp walks 32 consecutive positions at a time;
-        // one trip of the lookup loop advances every lane by one hash-chain
-        // node or one neighbour cell, and the unions run afterwards, also one
-        // step per trip (nested data-dependent loops would serialise lanes).
+        // The warp walks 32 consecutive positions at a time. Each lane first
+        // gathers its pixel's partners in the forward half of the box (packed
+        // 16-bit positions in two registers); the unions then run
+        // warp-synchronously, one find hop or link attempt per loop trip, so
+        // the lanes stay converged (retry loops nested in the lookups would
+        // serialise them).
         {
-            const int ndir = (p.ry + 1) + p.rx * (2 * p.ry + 1);   // forward half of the box
             for (int qb = R0 + (tid & ~31); qb < R1; qb += NT) {
                 const int q = qb + lane;
                 const uint64_t r = q < R1 ? S.buf[pad(q)] : INVALID;
-                bool active = r != INVALID;
-                const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
                 uint64_t eb0 = 0, eb1 = 0;
-                int ne = 0, di = -1, cx = 0, cy = 0;
-                bool dim = false, own = false;
-                uint32_t j = EMPTY;
-                while (__any_sync(0xffffffffu, active)) {
-                    if (active) {
-                        if (j == EMPTY) {
-                            ++di;
-                            if (di >= ndir) {
-                                active = false;
-                            } else {
-                                int dx, dy;
-                                if (di <= p.ry) { dx = 0; dy = di; }
-                                else { const int k = di - (p.ry + 1); dx = 1 + k / (2 * p.ry + 1); dy = k % (2 * p.ry + 1) - p.ry; }
-                                cx = x + dx;
-                                cy = y + dy;
-                                own = (dx == 0 && dy == 0);
-                                j = (cx <= 255 && cy >= 0 && cy <= 255) ? S.u1.head[hcell(sg, cx, cy)] : EMPTY;
-                            }
-                        } else {
-                            const uint64_t rj = S.buf[pad((int)j)];
-                            const uint32_t jn = S.u2.next[j];
-                            const int d = r_tof(rj) - tb;
-                            if (!(own && (int)j <= q) && r_x(rj) == cx && r_y(rj) == cy && r_seg(rj) == sg &&
-                                d >= -p.dt && d <= p.dt) {
+                int ne = 0;
+                bool overflow = false;
+                if (r != INVALID) {
+                    const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
+                    bool dim = false;
+                    for (int dx = 0; dx <= p.rx; ++dx) {
+                        const int cx = x + dx;
+                        if (cx > 255) break;
+                        for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
+                            const int cy = y + dy;
+                            if (cy < 0 || cy > 255) continue;
+                            for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                                if (dx == 0 && dy == 0 && (int)j <= q) continue;
+                                const uint64_t rj = S.buf[pad((int)j)];
+                                if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
+                                const int d = r_tof(rj) - tb;
+                                if (d < -p.dt || d > p.dt) continue;
                                 const int tj = r_tot(rj);
                                 // local maxima: equal ToT goes to the later pixel (Sec. V.B)
                                 if (tj > tot || (tj == tot && (int)j > q)) dim = true;
                                 else S.notpeak[j] = 1;
-                                if (MODE == TPX_MODE_CC && ne < 8) {
+                                if (MODE == TPX_MODE_CC) {
                                     if (ne < 4) eb0 |= (uint64_t)j << (16 * ne);
-                                    else eb1 |= (uint64_t)j << (16 * (ne - 4));
+                                    else if (ne < 8) eb1 |= (uint64_t)j << (16 * (ne - 4));
+                                    else overflow = true;
                                     ++ne;
                                 }
                             }
-                            j = jn;
                         }
                     }
+                    if (dim) S.notpeak[q] = 1;
                 }
-                if (dim) S.notpeak[q] = 1;
                 if (MODE == TPX_MODE_CC) {
-                    if (__any_sync(0xffffffffu, ne >= 8)) {
-                        // more than 8 partners (only with larger radii): unite in
-                        // the slow nested form, one lane at a time
-                        for (int l = 0; l < 32; ++l) {
-                            if (__shfl_sync(0xffffffffu, ne, l) >= 8 && lane == l) {
-                                for (int dx = 0; dx <= p.rx; ++dx)
-                                    for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
-                                        const int ux = x + dx, uy = y + dy;
-                                        if (ux > 255 || uy < 0 || uy > 255) continue;
-                                        for (uint32_t jj = S.u1.head[hcell(sg, ux, uy)]; jj != EMPTY; jj = S.u2.next[jj]) {
-                                            if (dx == 0 && dy == 0 && (int)jj <= q) continue;
-                                            const uint64_t rj = S.buf[pad((int)jj)];
-                                            if (r_x(rj) != ux || r_y(rj) != uy || r_seg(rj) != sg) continue;
-                                            const int d = r_tof(rj) - tb;
-                                            if (d < -p.dt || d > p.dt) continue;
-                                            unite_one(S, pbase, (uint32_t)q, jj);
-                                        }
-                                    }
-                                ne = 0;
+                    if (overflow) {
+                        // more than 8 partners (possible with larger radii): unite
+                        // this pixel's pairs one at a time
+                        const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
+                        for (int dx = 0; dx <= p.rx; ++dx)
+                            for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
+                                const int ux = x + dx, uy = y + dy;
+                                if (ux > 255 || uy < 0 || uy > 255) continue;
+                                for (uint32_t jj = S.u1.head[hcell(sg, ux, uy)]; jj != EMPTY; jj = S.u2.next[jj]) {
+                                    if (dx == 0 && dy == 0 && (int)jj <= q) continue;
+                                    const uint64_t rj = S.buf[pad((int)jj)];
+                                    if (r_x(rj) != ux || r_y(rj) != uy || r_seg(rj) != sg) continue;
+                                    const int d = r_tof(rj) - tb;
+                                    if (d < -p.dt || d > p.dt) continue;
+                                    unite_one(S, pbase, (uint32_t)q, jj);
+                                }
                             }
-                            __syncwarp();
-                        }
+                        ne = 0;
                     }
-                    const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)ne);
+                    __syncwarp();
+                    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)ne);
                     uint32_t rq = (uint32_t)(q < R1 ? q : 0);
                     for (int k = 0; k < kmax; ++k) {
                         const uint64_t w = k < 4 ? eb0 : eb1;
@@ -689,31 +753,39 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             }
         }
 
-        // ---- record offsets: second decoupled look-back over record counts,
-        //      published as soon as the count is known ----
+        // ---- record offsets: publish this tile's count now, look back later ----
         if (tid == 0) {
-            unsigned st2 = 0;
-            long long O = 0;
-            const long long mine = (long long)ncl;
             if (tile > 0) {
-                __stcg(&p.ts.cagg[tile], mine);
+                __stcg(&p.ts.cagg[tile], (long long)ncl);
                 st_release(&p.ts.cflags[tile], (seq << 2) | 1u);
-                O = lookback_count(p, tile, seq, &st2);
-            }
-            __stcg(&p.ts.cpre[tile], O + mine);
-            st_release(&p.ts.cflags[tile], (seq << 2) | 2u);
-            S.clo = O;
-            atomicOr(&S.status, st2);
-            if (tile == p.n_tiles - 1) {
-                const long long ntr = E.tdc.n + (long long)S.cnt[C_TDCS];
-                *p.n_clusters = O + mine;
-                *p.n_trig = ntr;
-                if (O + mine > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
-                if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
+            } else {
+                __stcg(&p.ts.cpre[0], (long long)ncl);
+                st_release(&p.ts.cflags[0], (seq << 2) | 2u);
             }
         }
-        __syncthreads();
-        const long long O = S.clo;
+        // warp 0 resolves the record offset of this tile (decoupled look-back)
+        auto resolve_offset = [&]() {
+            if (tid < 32) {
+                unsigned st2 = 0;
+                long long Ow = 0;
+                if (tile > 0) Ow = lookback_count_warp(p, tile, seq, &st2);
+                if (tid == 0) {
+                    if (tile > 0) {
+                        __stcg(&p.ts.cpre[tile], Ow + (long long)ncl);
+                        st_release(&p.ts.cflags[tile], (seq << 2) | 2u);
+                    }
+                    S.clo = Ow;
+                    if (st2) atomicOr(&S.status, st2);
+                    if (tile == p.n_tiles - 1) {
+                        const long long ntr = E.tdc.n + (long long)S.cnt[C_TDCS];
+                        *p.n_clusters = Ow + ncl;
+                        *p.n_trig = ntr;
+                        if (Ow + ncl > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
+                        if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
+                    }
+                }
+            }
+        };
 
         if (MODE == TPX_MODE_CC) {
             // accumulate in batches of M cluster ids (one batch in normal data);
@@ -721,7 +793,9 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             unsigned long long c_pk = 0;
             for (int c0 = 0; c0 == 0 || c0 < ncl; c0 += M) {
                 const int nb = min(M, ncl - c0);
-                for (int i = tid; i < nb; i += NT) { S.acc0[i] = 0; S.acc1[i] = 0; S.acc2[i] = 0; }
+                for (int i = tid; i < nb; i += NT) {
+                    S.a_tot[i] = 0; S.a_np[i] = 0; S.a_x[i] = 0; S.a_y[i] = 0; S.a_dt[i] = 0; S.a_dth[i] = 0;
+                }
                 __syncthreads();
                 for (int q = W0 + tid; q < W1; q += NT) {
                     const uint64_t r = S.buf[pad(q)];
@@ -734,10 +808,18 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                         ci = (int)S.u1.cid[root] - c0;
                         pk = S.notpeak[q] ? 0 : 1;
                         if (ci >= 0 && ci < nb) {
-                            const unsigned long long tot = (unsigned long long)r_tot(r);
-                            atomicAdd(&S.acc0[ci], tot | (1ull << 24) | ((unsigned long long)pk << 44));
-                            atomicAdd(&S.acc1[ci], (tot * (unsigned long long)r_x(r)) | ((tot * (unsigned long long)r_y(r)) << 32));
-                            atomicAdd(&S.acc2[ci], tot * (unsigned long long)r_tof(r));
+                            // exact sums with 32-bit shared atomics: the time moment is
+                            // taken relative to the root (the earliest pixel), and its
+                            // carries out of 32 bits are counted from the returned value
+                            const uint32_t tot = (uint32_t)r_tot(r);
+                            const uint64_t v = (uint64_t)(uint32_t)(r_tof(r) - r_tof(S.buf[pad((int)root)])) * tot;
+                            atomicAdd(&S.a_tot[ci], tot);
+                            atomicAdd(&S.a_np[ci], 1u | ((uint32_t)pk << 16));
+                            atomicAdd(&S.a_x[ci], tot * (uint32_t)r_x(r));
+                            atomicAdd(&S.a_y[ci], tot * (uint32_t)r_y(r));
+                            const uint32_t lo = (uint32_t)v, old = atomicAdd(&S.a_dt[ci], lo);
+                            const uint32_t hi = (uint32_t)(v >> 32) + ((uint32_t)(old + lo) < old ? 1u : 0u);
+                            if (hi) atomicAdd(&S.a_dth[ci], hi);
                             if (root == (uint32_t)q) S.rootpos[ci] = (uint16_t)q;
                         }
                     }
@@ -747,19 +829,21 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                         if (p.is_peak) p.is_peak[base + q] = pk;
                     }
                 }
+                if (c0 == 0) resolve_offset();
                 __syncthreads();
+                const long long O = S.clo;
                 // cluster records (Sec. V.C centre of mass from exact integer sums)
                 for (int i = tid; i < nb; i += NT) {
                     if (O + c0 + i >= p.cl_cap) break;
                     const int q = S.rootpos[i];
                     const uint64_t r = S.buf[pad(q)];
-                    const unsigned long long a0 = S.acc0[i], a1 = S.acc1[i], a2 = S.acc2[i];
-                    const long long s_tot = (long long)(a0 & 0xFFFFFFull);
-                    const int n = (int)((a0 >> 24) & 0xFFFFFull);
-                    const int npk = (int)(a0 >> 44);
-                    const long long s_x = (long long)(a1 & 0xFFFFFFFFull), s_y = (long long)(a1 >> 32);
+                    const long long s_tot = (long long)S.a_tot[i];
+                    const uint32_t np = S.a_np[i];
+                    const int n = (int)(np & 0xFFFFu);
+                    const int npk = (int)(np >> 16);
+                    const long long s_x = (long long)S.a_x[i], s_y = (long long)S.a_y[i];
                     const long long tofb0 = r_tof(r);
-                    const long long s_t = (long long)a2 - tofb0 * s_tot;
+                    const long long s_t = (long long)(((uint64_t)S.a_dth[i] << 32) | (uint64_t)S.a_dt[i]);
                     const int seg = r_seg(r);
                     const long long tofc0 = tofb0 - kTofBias;
                     tpx_cluster o;
@@ -793,6 +877,9 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             }
             c_pk = warp_sum(c_pk);
             if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
+            resolve_offset();
+            __syncthreads();
+            const long long O = S.clo;
             // records: box neighbourhood sums of each local maximum (Sec. V.C)
             for (int i = tid; i < ncl; i += NT) {
                 if (O + i >= p.cl_cap) break;
