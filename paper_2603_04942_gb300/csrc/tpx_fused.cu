@@ -15,7 +15,6 @@ constexpr int T = 4096;            // packets per tile
 constexpr int C = 8192;            // range capacity (tile + look-ahead), positions
 constexpr int KP = C / NT;         // positions per thread in contiguous walks
 constexpr int HB = 8192;           // hash buckets (power of two)
-constexpr int M = 1024;            // cluster records per range
 constexpr int MAXSEG = T + 16;     // TDC packets per range: at most a tile's plus the terminator
 constexpr uint64_t INVALID = ~0ull;
 constexpr uint32_t EMPTY = 0xFFFFu;
@@ -159,17 +158,11 @@ __device__ __forceinline__ uint32_t find_ro(uint32_t pbase, uint32_t x) {
 // --------------------------------------------------------------- smem layout
 struct __align__(16) Smem {
     uint64_t buf[C + C / 8];                          // packets, then kept-pixel records
-    uint32_t parent[C];                               // union-find (CC) / peak list (PAPER)
-    union { uint32_t head[HB]; uint32_t cid[C]; } u1; // hash heads, then cluster ids
+    uint32_t parent[C];                               // union-find; then member links and
+                                                      // root positions (CC) / peak list (PAPER)
+    union { uint32_t head[HB]; uint32_t mhead[C]; } u1; // hash heads, then member-list heads
     union { uint16_t next[C]; uint16_t rootof[C]; } u2;
     uint8_t notpeak[C];
-    uint32_t a_tot[M];            // sum ToT
-    uint32_t a_np[M];             // pixel count | local maxima << 16
-    uint32_t a_x[M];              // sum x*ToT
-    uint32_t a_y[M];              // sum y*ToT
-    uint32_t a_dt[M];             // sum (t - t0)*ToT, low 32 bits
-    uint32_t a_dth[M];            // its high 32 bits (carries)
-    uint16_t rootpos[M];
     long long tdc_t[MAXSEG];
     GAgg warp_agg[NW];
     GAgg tot_agg;
@@ -349,44 +342,6 @@ __device__ long long lookback_count_warp(const Params &p, long long tile, unsign
 __device__ __forceinline__ uint64_t rkey(const Smem &S, uint32_t q) {
     return ((uint64_t)r_tof(S.buf[pad((int)q)]) << 16) | q;
 }
-// Warp-synchronous union of (a, b) for every lane with `have`: each trip of
-// the loop advances every active lane by one step -- a find hop (with path
-// halving) on a or b, or one linking attempt once both are roots -- so the
-// lanes stay converged.  The root of the smaller key (time, position) wins,
-// making each component's root its earliest pixel.  Returns the root reached
-// on a's side (a hint for the next union of the same pixel).
-__device__ __forceinline__ uint32_t unite_ws(const Smem &S, uint32_t pbase, bool have, uint32_t a, uint32_t b) {
-    bool active = have;
-    while (__any_sync(0xffffffffu, active)) {
-        if (active) {
-            const uint32_t pa = sh_ld(pbase + 4 * a);
-            const uint32_t pb = sh_ld(pbase + 4 * b);
-            if (pa != a || pb != b) {
-                if (pa != a) {
-                    const uint32_t ga = sh_ld(pbase + 4 * pa);
-                    if (ga != pa) sh_st(pbase + 4 * a, ga);
-                    a = ga;
-                }
-                if (pb != b) {
-                    const uint32_t gb = sh_ld(pbase + 4 * pb);
-                    if (gb != pb) sh_st(pbase + 4 * b, gb);
-                    b = gb;
-                }
-            } else if (a == b) {
-                active = false;
-            } else {
-                uint32_t lo = a, hi = b;
-                if (rkey(S, a) > rkey(S, b)) { lo = b; hi = a; }
-                const uint32_t old = sh_cas(pbase + 4 * hi, hi, lo);
-                if (old == hi) active = false;
-                else b = old;           // hi was linked meanwhile: continue above it
-                a = lo;
-            }
-        }
-    }
-    return a;
-}
-
 __device__ void unite_one(const Smem &S, uint32_t pbase, uint32_t a, uint32_t b) {
     for (;;) {
         a = find_root(pbase, a);
@@ -711,12 +666,49 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                             }
                         ne = 0;
                     }
+                    // warp-synchronous unions: each trip advances every active lane by
+                    // one step (a find hop with path halving on either side, or one
+                    // link attempt); a lane moves to its next partner as soon as its
+                    // current union is done
                     __syncwarp();
-                    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)ne);
-                    uint32_t rq = (uint32_t)(q < R1 ? q : 0);
-                    for (int k = 0; k < kmax; ++k) {
-                        const uint64_t w = k < 4 ? eb0 : eb1;
-                        rq = unite_ws(S, pbase, k < ne, rq, (uint32_t)((w >> (16 * (k & 3))) & 0xFFFF));
+                    int k = 0;
+                    uint32_t a = (uint32_t)(q < R1 ? q : 0), b = (uint32_t)(eb0 & 0xFFFF);
+                    bool active = ne > 0;
+                    while (__any_sync(0xffffffffu, active)) {
+                        if (active) {
+                            bool done = false;
+                            const uint32_t pa = sh_ld(pbase + 4 * a);
+                            const uint32_t pb = sh_ld(pbase + 4 * b);
+                            if (pa != a || pb != b) {
+                                if (pa != a) {
+                                    const uint32_t ga = sh_ld(pbase + 4 * pa);
+                                    if (ga != pa) sh_st(pbase + 4 * a, ga);
+                                    a = ga;
+                                }
+                                if (pb != b) {
+                                    const uint32_t gb = sh_ld(pbase + 4 * pb);
+                                    if (gb != pb) sh_st(pbase + 4 * b, gb);
+                                    b = gb;
+                                }
+                            } else if (a == b) {
+                                done = true;
+                            } else {
+                                uint32_t lo = a, hi = b;
+                                if (rkey(S, a) > rkey(S, b)) { lo = b; hi = a; }
+                                const uint32_t old = sh_cas(pbase + 4 * hi, hi, lo);
+                                if (old == hi) done = true;
+                                else b = old;      // hi was linked meanwhile: continue above it
+                                a = lo;
+                            }
+                            if (done) {
+                                if (++k < ne) {
+                                    const uint64_t w = k < 4 ? eb0 : eb1;
+                                    b = (uint32_t)((w >> (16 * (k & 3))) & 0xFFFF);
+                                } else {
+                                    active = false;
+                                }
+                            }
+                        }
                     }
                 }
             }
@@ -735,9 +727,15 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
             }
             int excl = block_scan_int(S, c, &ncl);
+            // the union-find array is free now: it holds the member links
+            // (first half) and the root position of each cluster id (second half)
+            uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
             for (int j = 0; j < KP; ++j) {
                 const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) S.u1.cid[q] = (uint32_t)excl++;
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
+                    rootpos[excl++] = (uint16_t)q;
+                    S.u1.mhead[q] = EMPTY;
+                }
             }
         } else {
             // PAPER mode: one record per local maximum (list kept in parent[])
@@ -788,79 +786,64 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         };
 
         if (MODE == TPX_MODE_CC) {
-            // accumulate in batches of M cluster ids (one batch in normal data);
-            // the first batch also writes the per-packet outputs
+            // Each kept pixel joins its cluster's member list (one exchange per
+            // pixel) and writes its label; then one thread per cluster walks the
+            // list and forms the exact integer moments in registers (Sec. V.C).
+            uint16_t *mnext = reinterpret_cast<uint16_t *>(S.parent);
+            const uint16_t *rootpos = mnext + C;
+            __syncthreads();
             unsigned long long c_pk = 0;
-            for (int c0 = 0; c0 == 0 || c0 < ncl; c0 += M) {
-                const int nb = min(M, ncl - c0);
-                for (int i = tid; i < nb; i += NT) {
-                    S.a_tot[i] = 0; S.a_np[i] = 0; S.a_x[i] = 0; S.a_y[i] = 0; S.a_dt[i] = 0; S.a_dth[i] = 0;
+            for (int q = W0 + tid; q < W1; q += NT) {
+                const uint64_t r = S.buf[pad(q)];
+                const bool kept = q >= R0 && r != INVALID;
+                uint32_t root = 0;
+                uint8_t pk = 0;
+                if (kept) {
+                    root = S.u2.rootof[q];
+                    pk = S.notpeak[q] ? 0 : 1;
+                    c_pk += pk;
+                    mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[root], (uint32_t)q);
                 }
-                __syncthreads();
-                for (int q = W0 + tid; q < W1; q += NT) {
-                    const uint64_t r = S.buf[pad(q)];
-                    const bool kept = q >= R0 && r != INVALID;
-                    uint32_t root = 0;
-                    int ci = -1;
-                    uint8_t pk = 0;
-                    if (kept) {
-                        root = S.u2.rootof[q];
-                        ci = (int)S.u1.cid[root] - c0;
-                        pk = S.notpeak[q] ? 0 : 1;
-                        if (ci >= 0 && ci < nb) {
-                            // exact sums with 32-bit shared atomics: the time moment is
-                            // taken relative to the root (the earliest pixel), and its
-                            // carries out of 32 bits are counted from the returned value
-                            const uint32_t tot = (uint32_t)r_tot(r);
-                            const uint64_t v = (uint64_t)(uint32_t)(r_tof(r) - r_tof(S.buf[pad((int)root)])) * tot;
-                            atomicAdd(&S.a_tot[ci], tot);
-                            atomicAdd(&S.a_np[ci], 1u | ((uint32_t)pk << 16));
-                            atomicAdd(&S.a_x[ci], tot * (uint32_t)r_x(r));
-                            atomicAdd(&S.a_y[ci], tot * (uint32_t)r_y(r));
-                            const uint32_t lo = (uint32_t)v, old = atomicAdd(&S.a_dt[ci], lo);
-                            const uint32_t hi = (uint32_t)(v >> 32) + ((uint32_t)(old + lo) < old ? 1u : 0u);
-                            if (hi) atomicAdd(&S.a_dth[ci], hi);
-                            if (root == (uint32_t)q) S.rootpos[ci] = (uint16_t)q;
-                        }
-                    }
-                    if (c0 == 0) {
-                        c_pk += pk;
-                        if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)root : -1LL;
-                        if (p.is_peak) p.is_peak[base + q] = pk;
-                    }
-                }
-                if (c0 == 0) resolve_offset();
-                __syncthreads();
-                const long long O = S.clo;
-                // cluster records (Sec. V.C centre of mass from exact integer sums)
-                for (int i = tid; i < nb; i += NT) {
-                    if (O + c0 + i >= p.cl_cap) break;
-                    const int q = S.rootpos[i];
-                    const uint64_t r = S.buf[pad(q)];
-                    const long long s_tot = (long long)S.a_tot[i];
-                    const uint32_t np = S.a_np[i];
-                    const int n = (int)(np & 0xFFFFu);
-                    const int npk = (int)(np >> 16);
-                    const long long s_x = (long long)S.a_x[i], s_y = (long long)S.a_y[i];
-                    const long long tofb0 = r_tof(r);
-                    const long long s_t = (long long)(((uint64_t)S.a_dth[i] << 32) | (uint64_t)S.a_dt[i]);
-                    const int seg = r_seg(r);
-                    const long long tofc0 = tofb0 - kTofBias;
-                    tpx_cluster o;
-                    o.label = p.idx_base + base + q;
-                    o.shot = E.tdc.n + seg;
-                    o.t0 = S.tdc_t[seg] + tofc0;
-                    o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
-                    o.n = n; o.n_peaks = npk;
-                    o.x = (double)s_x / (double)s_tot;
-                    o.y = (double)s_y / (double)s_tot;
-                    o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
-                    p.clusters[O + c0 + i] = o;
-                }
-                __syncthreads();
+                if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)root : -1LL;
+                if (p.is_peak) p.is_peak[base + q] = pk;
             }
             c_pk = warp_sum(c_pk);
             if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
+            resolve_offset();
+            __syncthreads();
+            const long long O = S.clo;
+            // records: one thread per cluster walks its member list and forms
+            // the exact integer moments in registers (Sec. V.C)
+            for (int i = tid; i < ncl; i += NT) {
+                if (O + i >= p.cl_cap) break;
+                const int q = rootpos[i];
+                const uint64_t r = S.buf[pad(q)];
+                const int tofb0 = r_tof(r);
+                long long s_tot = 0, s_x = 0, s_y = 0, s_t = 0;
+                int n = 0, npk = 0;
+                for (uint32_t m = S.u1.mhead[q]; m != EMPTY; m = mnext[m]) {
+                    const uint64_t rm = S.buf[pad((int)m)];
+                    const long long tot = r_tot(rm);
+                    n += 1;
+                    npk += S.notpeak[m] ? 0 : 1;
+                    s_tot += tot;
+                    s_x += tot * r_x(rm);
+                    s_y += tot * r_y(rm);
+                    s_t += tot * (long long)(r_tof(rm) - tofb0);
+                }
+                const int seg = r_seg(r);
+                const long long tofc0 = (long long)tofb0 - kTofBias;
+                tpx_cluster o;
+                o.label = p.idx_base + base + q;
+                o.shot = E.tdc.n + seg;
+                o.t0 = S.tdc_t[seg] + tofc0;
+                o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
+                o.n = n; o.n_peaks = npk;
+                o.x = (double)s_x / (double)s_tot;
+                o.y = (double)s_y / (double)s_tot;
+                o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
+                p.clusters[O + i] = o;
+            }
         } else {
             unsigned long long c_pk = 0;
             for (int q = W0 + tid; q < W1; q += NT) {
