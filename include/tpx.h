@@ -74,7 +74,7 @@ typedef struct tpx_config {
 /* One particle hit.  CC mode: one record per connected component; PAPER
    mode: one record per local maximum, summed over its box neighbourhood
    (Sec. V.C).  Records are written in ascending `label` order. */
-typedef struct tpx_cluster {
+typedef struct tpx_record {
     int64_t label;   /* stream index (packet_index_base + position) of the
                         cluster's earliest pixel in (time, stream index)
                         order; PAPER mode: of the local maximum              */
@@ -89,12 +89,14 @@ typedef struct tpx_cluster {
     double x;        /* s_x / s_tot                                          */
     double y;        /* s_y / s_tot                                          */
     double tof;      /* (t0 - t_trig[shot]) + s_t / s_tot, ticks             */
-} tpx_cluster;       /* 88 bytes */
+} tpx_record;        /* 88 bytes */
 
 typedef struct tpx_counters {
     int64_t packets, pixels, tdcs, corrupt, dropped_pre_trigger, dropped_background,
             kept, clusters, peaks;
     int64_t status_bits;        /* raw device status word of the last call    */
+    int64_t redone;             /* 1 if tpx_sync redid the last tpx_process
+                                   call with the general path                 */
 } tpx_counters;
 
 typedef struct tpx_ctx tpx_ctx;
@@ -135,7 +137,7 @@ int tpx_destroy(tpx_ctx *ctx);
    otherwise the work is queued and its outcome is read with tpx_sync. */
 int tpx_process(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets,
                 int64_t packet_index_base, int64_t *d_labels, uint8_t *d_is_peak,
-                tpx_cluster *d_clusters, int64_t cluster_capacity, int64_t *d_n_clusters,
+                tpx_record *d_clusters, int64_t cluster_capacity, int64_t *d_n_clusters,
                 int64_t *d_trig_t, int64_t trig_capacity, int64_t *d_n_trig);
 
 /* The same with host buffers: copies h_packets to the device, processes and
@@ -145,11 +147,62 @@ int tpx_process(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets,
    so it allocates nothing either.  Returns the tpx_sync status. */
 int tpx_process_host(tpx_ctx *ctx, const uint64_t *h_packets, int64_t n_packets,
                      int64_t packet_index_base, int64_t *h_labels, uint8_t *h_is_peak,
-                     tpx_cluster *h_clusters, int64_t cluster_capacity, int64_t *h_n_clusters,
+                     tpx_record *h_clusters, int64_t cluster_capacity, int64_t *h_n_clusters,
                      int64_t *h_trig_t, int64_t trig_capacity, int64_t *h_n_trig);
 
+/* Kept pixels in stream order, as device arrays of one common capacity
+   (structure of arrays, caller-owned), produced by tpx_decode. */
+typedef struct tpx_hits {
+    int64_t *index;   /* stream index: packet_index_base + packet position    */
+    int64_t *shot;    /* trigger index (most recent trigger in time)          */
+    int64_t *t;       /* unwrapped time after the timewalk table, ticks       */
+    int32_t *tof;     /* t - t_trig[shot], ticks                              */
+    uint8_t *x;
+    uint8_t *y;
+    uint16_t *tot;    /* time over threshold, 25 ns units                     */
+} tpx_hits;
+
+/* The same path in three separate calls, through global memory (no shot or
+   range size limit; at most 2^31 - 1 kept pixels per call).  Each call
+   queues its work on the context stream; scratch is taken from the
+   context's general scratch, which these calls grow on first use (they may
+   allocate, unlike tpx_process).
+
+   tpx_decode: decode packets, unwrap ToA per stream (Sec. IV.A), bin each
+   pixel to the most recent trigger in time and keep it if its ToF does not
+   exceed tof_max (Sec. IV.B), subtract the timewalk table (Sec. IV.C).
+     hits, hits_capacity   output arrays; kept pixels in stream order
+     d_n_hits              device int64: number of kept pixels (if it exceeds
+                           the capacity, only `capacity` are written and
+                           tpx_sync returns TPX_EOVERFLOW)
+     d_trig_t, d_n_trig    unwrapped trigger times and their number */
+int tpx_decode(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets, int64_t packet_index_base,
+               const tpx_hits *hits, int64_t hits_capacity, int64_t *d_n_hits,
+               int64_t *d_trig_t, int64_t trig_capacity, int64_t *d_n_trig);
+
+/* tpx_cluster: order the hits by ToA -- a stable device radix sort on
+   (shot, corrected ToF), ties in stream order -- then join adjacent hits
+   (Sec. V.A box rule) by union-find in that order, so that each cluster's
+   root is its earliest hit; find the local maxima (Sec. V.B).
+     n_hits        host count (read d_n_hits after tpx_decode)
+     d_labels      [n_hits] int64: per hit, the stream index of its cluster's
+                   earliest hit (CC mode) or its own stream index (PAPER mode)
+     d_is_peak     [n_hits] uint8 or NULL: 1 for local maxima */
+int tpx_cluster(tpx_ctx *ctx, const tpx_hits *hits, int64_t n_hits, int64_t *d_labels, uint8_t *d_is_peak);
+
+/* tpx_centroid: cluster records in ascending label order (Sec. V.C).  CC
+   mode: moments over the hits sharing a label; PAPER mode: over the box
+   neighbourhood of each local maximum (d_is_peak required).  Same record
+   layout and count/overflow rules as tpx_process. */
+int tpx_centroid(tpx_ctx *ctx, const tpx_hits *hits, const int64_t *d_labels, const uint8_t *d_is_peak,
+                 int64_t n_hits, tpx_record *d_clusters, int64_t cluster_capacity, int64_t *d_n_clusters);
+
 /* Wait for the context's queued work and translate the device status word
-   of the last call into a status code.  If counters != NULL, fill it. */
+   of the last call into a status code.  If counters != NULL, fill it.
+   When the last call was tpx_process and the fused kernel met an input it
+   cannot hold on chip (a range longer than 8192 packets, or a pixel whose
+   trigger lies outside its range), tpx_sync redoes that call exactly with the
+   general path before returning (this may allocate general scratch). */
 int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
 
 /* Upper bound on n_packets for tpx_process_noalloc (2^26 packets, 512 MB of
@@ -175,7 +228,7 @@ int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
    TPX_NOALLOC_MAX_PACKETS; then the status codes of tpx_sync. */
 int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t *d_packets,
                         int64_t n_packets, int64_t packet_index_base, int64_t *d_labels,
-                        uint8_t *d_is_peak, tpx_cluster *d_clusters, int64_t cluster_capacity,
+                        uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cluster_capacity,
                         int64_t *d_n_clusters, int64_t *d_trig_t, int64_t trig_capacity,
                         int64_t *d_n_trig, tpx_counters *h_counters);
 

@@ -27,17 +27,18 @@ TICK_NS = 1.5625
 OK, EINVAL, ENOMEM, EOVERFLOW, ECORRUPT, EAGAIN, ETIMEOUT, EDEVTIMEOUT, ECUDA, EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 
-# tpx_cluster, 88 bytes, ascending label order
+# tpx_record, 88 bytes, ascending label order
 CLUSTER_DTYPE = np.dtype([("label", "<i8"), ("shot", "<i8"), ("t0", "<i8"), ("s_tot", "<i8"),
                           ("s_x", "<i8"), ("s_y", "<i8"), ("s_t", "<i8"), ("n", "<i4"),
                           ("n_peaks", "<i4"), ("x", "<f8"), ("y", "<f8"), ("tof", "<f8")])
 assert CLUSTER_DTYPE.itemsize == 88
 
 COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger", "dropped_background",
-                  "kept", "clusters", "peaks", "status_bits")
+                  "kept", "clusters", "peaks", "status_bits", "redone")
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
-                    "tpx_process_host", "tpx_sync", "tpx_strerror", "tpx_version")
+                    "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
+                    "tpx_centroid", "tpx_strerror", "tpx_version")
 
 
 class _CConfig(ctypes.Structure):
@@ -49,6 +50,10 @@ class _CConfig(ctypes.Structure):
 
 class _CCounters(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in COUNTER_FIELDS]
+
+
+class _CHits(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in ("index", "shot", "t", "tof", "x", "y", "tot")]
 
 
 class TpxError(RuntimeError):
@@ -97,7 +102,11 @@ def load(path: str | None = None):
         L.tpx_strerror.argtypes = [i32]
         L.tpx_strerror.restype = ctypes.c_char_p
         L.tpx_version.restype = ctypes.c_char_p
-        for f in ("tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process", "tpx_process_host", "tpx_sync"):
+        L.tpx_decode.argtypes = [vp, vp, i64, i64, ctypes.POINTER(_CHits), i64, vp, vp, i64, vp]
+        L.tpx_cluster.argtypes = [vp, ctypes.POINTER(_CHits), i64, vp, vp]
+        L.tpx_centroid.argtypes = [vp, ctypes.POINTER(_CHits), vp, vp, i64, vp, i64, vp]
+        for f in ("tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process", "tpx_process_host", "tpx_sync",
+                  "tpx_decode", "tpx_cluster", "tpx_centroid"):
             getattr(L, f).restype = i32
         _lib = L
         return L
@@ -223,3 +232,58 @@ class Context:
                                     clusters.ctypes.data, clusters.size, ctypes.byref(n_cl),
                                     triggers.ctypes.data, triggers.size, ctypes.byref(n_tr))
         return rc, n_cl.value, n_tr.value
+
+    # -- the same path in three calls (global memory, no range size limit) --
+    def tpx_decode(self, packets, hits_capacity: int | None = None, trig_capacity: int | None = None,
+                   index_base: int = 0, n_packets: int | None = None) -> dict:
+        """Kept pixels in stream order (device tensors) and the trigger times."""
+        import torch
+        n = int(packets.numel() if n_packets is None else n_packets)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cap = int(hits_capacity if hits_capacity is not None else max(1, n))
+        tcap = int(trig_capacity if trig_capacity is not None else max(16, n))
+        h = dict(index=torch.empty(cap, dtype=torch.int64, device=dev),
+                 shot=torch.empty(cap, dtype=torch.int64, device=dev),
+                 t=torch.empty(cap, dtype=torch.int64, device=dev),
+                 tof=torch.empty(cap, dtype=torch.int32, device=dev),
+                 x=torch.empty(cap, dtype=torch.uint8, device=dev),
+                 y=torch.empty(cap, dtype=torch.uint8, device=dev),
+                 tot=torch.empty(cap, dtype=torch.int16, device=dev))
+        n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
+        trig = torch.empty(tcap, dtype=torch.int64, device=dev)
+        n_trig = torch.zeros(1, dtype=torch.int64, device=dev)
+        ch = _CHits(*(_ptr(h[f]) for f in ("index", "shot", "t", "tof", "x", "y", "tot")))
+        rc = lib().tpx_decode(self._h, _ptr(packets), n, int(index_base), ctypes.byref(ch), cap, _ptr(n_hits),
+                              _ptr(trig), tcap, _ptr(n_trig))
+        if rc:
+            raise TpxError(rc, "tpx_decode")
+        return dict(hits=h, n_hits=n_hits, trig=trig, n_trig=n_trig, hits_capacity=cap, trig_capacity=tcap)
+
+    @staticmethod
+    def _chits(h: dict) -> _CHits:
+        return _CHits(*(_ptr(h[f]) for f in ("index", "shot", "t", "tof", "x", "y", "tot")))
+
+    def tpx_cluster(self, hits: dict, n_hits: int, is_peak: bool = True) -> dict:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        labels = torch.empty(max(1, n_hits), dtype=torch.int64, device=dev)
+        pk = torch.empty(max(1, n_hits), dtype=torch.uint8, device=dev) if is_peak else None
+        ch = self._chits(hits)
+        rc = lib().tpx_cluster(self._h, ctypes.byref(ch), int(n_hits), _ptr(labels), _ptr(pk))
+        if rc:
+            raise TpxError(rc, "tpx_cluster")
+        return dict(labels=labels, is_peak=pk)
+
+    def tpx_centroid(self, hits: dict, labels, is_peak, n_hits: int, cluster_capacity: int | None = None) -> dict:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cap = int(cluster_capacity if cluster_capacity is not None else max(16, n_hits))
+        cl = torch.empty(cap * CLUSTER_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        n_cl = torch.zeros(1, dtype=torch.int64, device=dev)
+        ch = self._chits(hits)
+        rc = lib().tpx_centroid(self._h, ctypes.byref(ch), _ptr(labels), _ptr(is_peak), int(n_hits), _ptr(cl), cap,
+                                _ptr(n_cl))
+        if rc:
+            raise TpxError(rc, "tpx_centroid")
+        return dict(clusters=cl, n_clusters=n_cl, cluster_capacity=cap)
+

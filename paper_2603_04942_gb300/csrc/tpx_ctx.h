@@ -1,0 +1,60 @@
+// tpx_ctx.h -- the context behind the opaque tpx_ctx handle (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tpx.h"
+#include "tpx_fused.cuh"
+
+struct tpx_ctx {
+    tpx_config cfg;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int64_t max_packets;
+    int64_t max_tiles;
+    unsigned seq;
+    tpxk::TileScratch ts;
+    void *scratch;            // one allocation for all tile records
+    tpxk::Ctl *ctl;           // device control block
+    tpxk::Ctl *h_ctl;         // pinned host copy
+    // device staging for tpx_process_host
+    uint64_t *st_pk;
+    int64_t *st_labels;
+    uint8_t *st_peak;
+    int64_t st_n, st_labels_cap, st_peak_cap, st_counts_cap;
+    tpx_record *st_cl;
+    int64_t st_cl_cap;
+    int64_t *st_trig;
+    int64_t st_trig_cap;
+    int64_t *st_counts;       // [2]: n_clusters, n_trig
+    // scratch of the general (global-memory) path, grown on demand
+    void *g_mem;
+    size_t g_bytes;
+    // the last tpx_process call, kept so tpx_sync can redo it exactly with the
+    // general path when the fused kernel reports an input it cannot hold
+    struct {
+        bool valid;
+        const uint64_t *pk;
+        int64_t n, base;
+        int64_t *labels;
+        uint8_t *is_peak;
+        tpx_record *cl;
+        int64_t cl_cap;
+        int64_t *n_cl;
+        int64_t *trig;
+        int64_t trig_cap;
+        int64_t *n_trig;
+    } last;
+};
+
+// general (global-memory) path, tpx_general.cu
+namespace tpxg {
+// grow the context's general scratch to at least `bytes` (synchronises)
+int reserve(tpx_ctx *c, size_t bytes);
+// exact redo of the last tpx_process call with the general path; returns
+// the status of the redone call
+int redo_last(tpx_ctx *c);
+}  // namespace tpxg

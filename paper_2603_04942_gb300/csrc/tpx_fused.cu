@@ -5,6 +5,7 @@
 #include <climits>
 #include <cstdint>
 
+#include "tpx_common.cuh"
 #include "tpx_fused.cuh"
 
 namespace tpxk {
@@ -34,67 +35,6 @@ __device__ __forceinline__ int r_y(uint64_t r) { return (int)((r >> 8) & 255); }
 __device__ __forceinline__ int r_tot(uint64_t r) { return (int)((r >> 16) & 1023); }
 __device__ __forceinline__ int r_seg(uint64_t r) { return (int)((r >> 26) & 0x3FFF); }
 __device__ __forceinline__ int r_tof(uint64_t r) { return (int)(r >> 40); }
-
-__device__ __forceinline__ long long pix_raw(uint64_t w) {
-    long long coarse = (long long)(((w & 0xFFFFull) << 14) | ((w >> 30) & 0x3FFFull));
-    long long ftoa = (long long)((w >> 16) & 0xFull);
-    return (coarse * 16 - ftoa) & (kPixPeriod - 1);
-}
-__device__ __forceinline__ long long tdc_raw(uint64_t w) {
-    return (long long)(((w >> 9) & ((1ull << 35) - 1)) << 1);
-}
-__device__ __forceinline__ int pix_x(uint64_t w) { return (int)(2 * ((w >> 53) & 0x7F) + (((w >> 44) & 7) >> 2)); }
-__device__ __forceinline__ int pix_y(uint64_t w) { return (int)(4 * ((w >> 47) & 0x3F) + ((w >> 44) & 3)); }
-__device__ __forceinline__ int pix_tot(uint64_t w) { return (int)((w >> 20) & 0x3FF); }
-
-__device__ __forceinline__ long long jump(long long d, long long thr) { return d < -thr ? 1 : (d > thr ? -1 : 0); }
-
-__device__ __forceinline__ GChain chain_id() { GChain c; c.n = 0; c.first = 0; c.last = 0; c.sum = 0; return c; }
-__device__ __forceinline__ GAgg agg_id() { GAgg a; a.pix = chain_id(); a.tdc = chain_id(); return a; }
-
-// associative combine of two consecutive stretches of one unwrap chain
-__device__ __forceinline__ GChain ccomb(const GChain &a, const GChain &b, long long thr) {
-    GChain c;
-    c.n = a.n + b.n;
-    c.first = a.n ? a.first : b.first;
-    c.last = b.n ? b.last : a.last;
-    c.sum = a.sum + b.sum + ((a.n && b.n) ? jump(b.first - a.last, thr) : 0);
-    return c;
-}
-__device__ __forceinline__ GAgg acomb(const GAgg &a, const GAgg &b, long long tp, long long tt) {
-    GAgg c;
-    c.pix = ccomb(a.pix, b.pix, tp);
-    c.tdc = ccomb(a.tdc, b.tdc, tt);
-    return c;
-}
-__device__ __forceinline__ void chain_push(GChain &c, long long raw, long long thr) {
-    if (c.n) c.sum += jump(raw - c.last, thr); else c.first = raw;
-    c.last = raw;
-    c.n += 1;
-}
-
-__device__ __forceinline__ GChain shfl_up_chain(const GChain &v, int o) {
-    GChain u;
-    u.n = __shfl_up_sync(0xffffffffu, v.n, o);
-    u.first = __shfl_up_sync(0xffffffffu, v.first, o);
-    u.last = __shfl_up_sync(0xffffffffu, v.last, o);
-    u.sum = __shfl_up_sync(0xffffffffu, v.sum, o);
-    return u;
-}
-__device__ __forceinline__ GAgg shfl_up_agg(const GAgg &v, int o) {
-    GAgg u;
-    u.pix = shfl_up_chain(v.pix, o);
-    u.tdc = shfl_up_chain(v.tdc, o);
-    return u;
-}
-__device__ __forceinline__ GAgg warp_incl_scan(GAgg v, int lane, long long tp, long long tt) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        GAgg u = shfl_up_agg(v, o);
-        if (lane >= o) v = acomb(u, v, tp, tt);
-    }
-    return v;
-}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -833,7 +773,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 }
                 const int seg = r_seg(r);
                 const long long tofc0 = (long long)tofb0 - kTofBias;
-                tpx_cluster o;
+                tpx_record o;
                 o.label = p.idx_base + base + q;
                 o.shot = E.tdc.n + seg;
                 o.t0 = S.tdc_t[seg] + tofc0;
@@ -890,7 +830,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 }
                 const long long s_t = a2 - (long long)tmin * s_tot;
                 const long long tofc0 = (long long)tmin - kTofBias;
-                tpx_cluster o;
+                tpx_record o;
                 o.label = p.idx_base + base + q;
                 o.shot = E.tdc.n + sg;
                 o.t0 = S.tdc_t[sg] + tofc0;

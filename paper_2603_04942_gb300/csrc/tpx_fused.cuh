@@ -78,7 +78,7 @@ struct Params {
     long long idx_base;
     long long *labels;
     uint8_t *is_peak;
-    tpx_cluster *clusters;
+    tpx_record *clusters;
     long long cl_cap;
     long long *n_clusters;
     long long *trig;

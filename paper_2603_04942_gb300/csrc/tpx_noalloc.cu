@@ -66,7 +66,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 
 extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t *d_packets,
                                    int64_t n, int64_t idx_base, int64_t *d_labels, uint8_t *d_is_peak,
-                                   tpx_cluster *d_clusters, int64_t cl_cap, int64_t *d_n_clusters,
+                                   tpx_record *d_clusters, int64_t cl_cap, int64_t *d_n_clusters,
                                    int64_t *d_trig, int64_t trig_cap, int64_t *d_n_trig,
                                    tpx_counters *h_counters) {
     int rc = noalloc_check_cfg(cfg);
@@ -165,6 +165,7 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
         h_counters->clusters = (int64_t)h.counters[tpxk::C_CLUSTERS];
         h_counters->peaks = (int64_t)h.counters[tpxk::C_PEAKS];
         h_counters->status_bits = (int64_t)h.status;
+        h_counters->redone = 0;
     }
     const unsigned st = h.status;
     if (st & tpxk::ST_DEVTIMEOUT) return TPX_EDEVTIMEOUT;

@@ -8,31 +8,9 @@
 #include <new>
 
 #include "tpx.h"
+#include "tpx_ctx.h"
 #include "tpx_fused.cuh"
 
-struct tpx_ctx {
-    tpx_config cfg;
-    cudaStream_t stream;
-    int device;
-    int num_sms;
-    int64_t max_packets;
-    int64_t max_tiles;
-    unsigned seq;
-    tpxk::TileScratch ts;
-    void *scratch;            // one allocation for all tile records
-    tpxk::Ctl *ctl;           // device control block
-    tpxk::Ctl *h_ctl;         // pinned host copy
-    // device staging for tpx_process_host
-    uint64_t *st_pk;
-    int64_t *st_labels;
-    uint8_t *st_peak;
-    int64_t st_n, st_labels_cap, st_peak_cap, st_counts_cap;
-    tpx_cluster *st_cl;
-    int64_t st_cl_cap;
-    int64_t *st_trig;
-    int64_t st_trig_cap;
-    int64_t *st_counts;       // [2]: n_clusters, n_trig
-};
 
 namespace {
 
@@ -168,12 +146,13 @@ int tpx_destroy(tpx_ctx *c) {
     if (c->st_cl) cudaFree(c->st_cl);
     if (c->st_trig) cudaFree(c->st_trig);
     if (c->st_counts) cudaFree(c->st_counts);
+    if (c->g_mem) cudaFree(c->g_mem);
     delete c;
     return TPX_OK;
 }
 
 int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_base, int64_t *d_labels,
-                uint8_t *d_is_peak, tpx_cluster *d_clusters, int64_t cl_cap, int64_t *d_n_clusters,
+                uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cl_cap, int64_t *d_n_clusters,
                 int64_t *d_trig, int64_t trig_cap, int64_t *d_n_trig) {
     if (!c || n < 0 || cl_cap < 0 || trig_cap < 0 || !d_n_clusters || !d_n_trig) return TPX_EINVAL;
     if (n > c->max_packets) return TPX_EINVAL;
@@ -181,6 +160,18 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     if ((reinterpret_cast<uintptr_t>(d_packets) & 15) != 0) return TPX_EINVAL;
     if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
+    c->last.valid = true;
+    c->last.pk = d_packets;
+    c->last.n = n;
+    c->last.base = idx_base;
+    c->last.labels = d_labels;
+    c->last.is_peak = d_is_peak;
+    c->last.cl = d_clusters;
+    c->last.cl_cap = cl_cap;
+    c->last.n_cl = d_n_clusters;
+    c->last.trig = d_trig;
+    c->last.trig_cap = trig_cap;
+    c->last.n_trig = d_n_trig;
     if (cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), c->stream) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_clusters, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_trig, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
@@ -225,9 +216,22 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
 
 int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     if (!c) return TPX_EINVAL;
+    int64_t redone = 0;
     if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return TPX_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    if ((c->h_ctl->status & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) && !(c->h_ctl->status & tpxk::ST_DEVTIMEOUT) &&
+        c->last.valid) {
+        // the fused kernel met an input it cannot hold on chip: redo the call
+        // exactly with the general path, then report that run
+        const int rc = tpxg::redo_last(c);
+        c->last.valid = false;
+        redone = 1;
+        if (rc) return rc;
+        if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return TPX_ECUDA;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    }
     const tpxk::Ctl &h = *c->h_ctl;
     if (out) {
         out->packets = (int64_t)h.counters[tpxk::C_PACKETS];
@@ -240,6 +244,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
         out->clusters = (int64_t)h.counters[tpxk::C_CLUSTERS];
         out->peaks = (int64_t)h.counters[tpxk::C_PEAKS];
         out->status_bits = (int64_t)h.status;
+        out->redone = redone;
     }
     const unsigned s = h.status;
     if (s & tpxk::ST_DEVTIMEOUT) return TPX_EDEVTIMEOUT;
@@ -251,7 +256,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
 }
 
 int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base, int64_t *h_labels,
-                     uint8_t *h_is_peak, tpx_cluster *h_clusters, int64_t cl_cap, int64_t *h_n_clusters,
+                     uint8_t *h_is_peak, tpx_record *h_clusters, int64_t cl_cap, int64_t *h_n_clusters,
                      int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
     if (!c || n < 0 || cl_cap < 0 || trig_cap < 0 || !h_n_clusters || !h_n_trig) return TPX_EINVAL;
     if (n > 0 && !h_packets) return TPX_EINVAL;
@@ -279,7 +284,7 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
     const int64_t ncl = counts[0] < cl_cap ? counts[0] : cl_cap;
     const int64_t ntr = counts[1] < trig_cap ? counts[1] : trig_cap;
-    if (ncl > 0 && cudaMemcpyAsync(h_clusters, c->st_cl, sizeof(tpx_cluster) * ncl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (ncl > 0 && cudaMemcpyAsync(h_clusters, c->st_cl, sizeof(tpx_record) * ncl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;
     if (ntr > 0 && cudaMemcpyAsync(h_trig, c->st_trig, sizeof(int64_t) * ntr, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;

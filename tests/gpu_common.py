@@ -58,7 +58,7 @@ def assert_clusters_equal(gc: np.ndarray, oc: np.ndarray):
 
 
 COUNTERS = ("pixels", "tdcs", "corrupt", "dropped_pre_trigger", "dropped_background", "kept", "clusters",
-            "peaks")
+            "peaks")  # "redone" and "status_bits" describe the path, not the result
 
 
 def assert_parity(g: dict, o: dict, check_counters=True):

@@ -63,7 +63,7 @@ def test_build_targets_sm103a_only():
 def test_cluster_record_layout():
     assert tpx.CLUSTER_DTYPE.itemsize == 88
     src = open(HDR).read()
-    assert "} tpx_cluster;       /* 88 bytes */" in src
+    assert "} tpx_record;        /* 88 bytes */" in src
 
 
 def test_product_path_has_no_oracle_import():
