@@ -68,7 +68,13 @@ typedef struct tpx_config {
                                    ToT, subtracted after the cut (Sec. IV.C);
                                    NULL = no correction                       */
     int32_t strict;             /* 1: unknown headers are an error            */
-    int32_t reserved;
+    int32_t chain;              /* 1: each tpx_process / tpx_decode continues
+                                   the unwrap state and trigger count where
+                                   the previous call on the context ended
+                                   (kept on the device: a long stream can be
+                                   fed in consecutive calls, each starting at
+                                   a trigger packet); 0: each call starts a
+                                   new stream unless tpx_set_state was used   */
 } tpx_config;
 
 /* One particle hit.  CC mode: one record per connected component; PAPER
@@ -100,6 +106,20 @@ typedef struct tpx_counters {
 } tpx_counters;
 
 typedef struct tpx_ctx tpx_ctx;
+
+/* Unwrap state and trigger count before (or after) a call: what a call needs
+   to continue a stream cut into several calls (Sec. IV.A wrap counting).  A
+   call given a state behaves exactly as if the packets before it had been in
+   the call, except that pixels before its first trigger packet are dropped
+   (they belong to the previous call's last shot). */
+typedef struct tpx_stream_state {
+    int64_t pixels;        /* pixel packets before the call (0: none)         */
+    int64_t pix_last_raw;  /* raw time of the last of them, ticks mod 2^34    */
+    int64_t pix_wraps;     /* pixel wraps counted so far                      */
+    int64_t triggers;      /* TDC packets before the call: trigger index base */
+    int64_t tdc_last_raw;  /* raw time of the last of them, ticks mod 2^36    */
+    int64_t tdc_wraps;     /* TDC wraps counted so far                        */
+} tpx_stream_state;
 
 /* Fill *cfg with the defaults: rx = ry = 1, dt = 32 ticks (50 ns),
    tof_max = 64000 ticks (100 us), both wrap thresholds 20 s, CC mode. */
@@ -231,6 +251,13 @@ int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t
                         uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cluster_capacity,
                         int64_t *d_n_clusters, int64_t *d_trig_t, int64_t trig_capacity,
                         int64_t *d_n_trig, tpx_counters *h_counters);
+
+/* The next tpx_process / tpx_decode on the context starts from *state
+   (NULL: the start of a stream).  Asynchronous on the context stream. */
+int tpx_set_state(tpx_ctx *ctx, const tpx_stream_state *state);
+
+/* The state after the last tpx_process / tpx_decode (synchronises). */
+int tpx_get_state(tpx_ctx *ctx, tpx_stream_state *state);
 
 /* Static description of a status code. */
 const char *tpx_strerror(int code);

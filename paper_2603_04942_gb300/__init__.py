@@ -38,14 +38,21 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_strerror", "tpx_version")
+                    "tpx_centroid", "tpx_set_state", "tpx_get_state", "tpx_strerror", "tpx_version")
 
 
 class _CConfig(ctypes.Structure):
     _fields_ = [("rx", ctypes.c_int32), ("ry", ctypes.c_int32), ("dt_ticks", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("tof_max_ticks", ctypes.c_int64),
                 ("wrap_thr_pix_ticks", ctypes.c_int64), ("wrap_thr_tdc_ticks", ctypes.c_int64),
-                ("d_timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("d_timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32), ("chain", ctypes.c_int32)]
+
+
+STATE_FIELDS = ("pixels", "pix_last_raw", "pix_wraps", "triggers", "tdc_last_raw", "tdc_wraps")
+
+
+class _CState(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in STATE_FIELDS]
 
 
 class _CCounters(ctypes.Structure):
@@ -74,6 +81,7 @@ class Config:
     wrap_thr_tdc_ticks: int = 12_800_000_000
     timewalk_lut: object = None        # torch int16 tensor of 1024 on the device, or None
     strict: bool = False
+    chain: bool = False                # each call continues where the previous one ended
 
 
 _lock = threading.Lock()
@@ -102,6 +110,10 @@ def load(path: str | None = None):
         L.tpx_strerror.argtypes = [i32]
         L.tpx_strerror.restype = ctypes.c_char_p
         L.tpx_version.restype = ctypes.c_char_p
+        L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
+        L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
+        L.tpx_set_state.restype = i32
+        L.tpx_get_state.restype = i32
         L.tpx_decode.argtypes = [vp, vp, i64, i64, ctypes.POINTER(_CHits), i64, vp, vp, i64, vp]
         L.tpx_cluster.argtypes = [vp, ctypes.POINTER(_CHits), i64, vp, vp]
         L.tpx_centroid.argtypes = [vp, ctypes.POINTER(_CHits), vp, vp, i64, vp, i64, vp]
@@ -135,7 +147,7 @@ class Context:
             assert self._lut.dtype == torch.int16 and self._lut.numel() == 1024 and self._lut.is_cuda
         c = _CConfig(self.cfg.rx, self.cfg.ry, self.cfg.dt_ticks, self.cfg.mode, self.cfg.tof_max_ticks,
                      self.cfg.wrap_thr_pix_ticks, self.cfg.wrap_thr_tdc_ticks, _ptr(self._lut),
-                     int(self.cfg.strict), 0)
+                     int(self.cfg.strict), int(self.cfg.chain))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         rc = lib().tpx_create(ctypes.byref(h), ctypes.byref(c), int(max_packets), ctypes.c_void_p(self.stream.cuda_stream))
@@ -147,6 +159,19 @@ class Context:
         rc = lib().tpx_reserve(self._h, int(max_packets))
         if rc:
             raise TpxError(rc, "tpx_reserve")
+
+    def tpx_set_state(self, state: dict | None):
+        st = None if state is None else _CState(*(int(state[f]) for f in STATE_FIELDS))
+        rc = lib().tpx_set_state(self._h, ctypes.byref(st) if st is not None else None)
+        if rc:
+            raise TpxError(rc, "tpx_set_state")
+
+    def tpx_get_state(self) -> dict:
+        st = _CState()
+        rc = lib().tpx_get_state(self._h, ctypes.byref(st))
+        if rc:
+            raise TpxError(rc, "tpx_get_state")
+        return {f: int(getattr(st, f)) for f in STATE_FIELDS}
 
     def close(self):
         if getattr(self, "_h", None):

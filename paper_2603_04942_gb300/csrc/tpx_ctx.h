@@ -30,6 +30,11 @@ struct tpx_ctx {
     int64_t *st_trig;
     int64_t st_trig_cap;
     int64_t *st_counts;       // [2]: n_clusters, n_trig
+    // unwrap state before / after a call, on the device (ping-pong)
+    tpxk::GAgg *d_state;      // [2]
+    int cur;                  // d_state[cur]: state for the next call
+    bool state_once;          // tpx_set_state was called for the next call
+    tpxk::GAgg h_state;       // host staging for tpx_set_state / tpx_get_state
     // scratch of the general (global-memory) path, grown on demand
     void *g_mem;
     size_t g_bytes;
@@ -47,8 +52,14 @@ struct tpx_ctx {
         int64_t *trig;
         int64_t trig_cap;
         int64_t *n_trig;
+        const tpxk::GAgg *E0;
+        tpxk::GAgg *state_out;
     } last;
 };
+
+// state for the next call and where it leaves its final state (advances the
+// ping-pong; tpx_runtime.cu)
+void take_state(tpx_ctx *c, const tpxk::GAgg **E0, tpxk::GAgg **out);
 
 // general (global-memory) path, tpx_general.cu
 namespace tpxg {
@@ -57,4 +68,7 @@ int reserve(tpx_ctx *c, size_t bytes);
 // exact redo of the last tpx_process call with the general path; returns
 // the status of the redone call
 int redo_last(tpx_ctx *c);
+int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const tpx_hits &h, int64_t cap,
+                int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
+                const tpxk::GAgg *E0, tpxk::GAgg *state_out);
 }  // namespace tpxg

@@ -364,7 +364,9 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 st_agg(&p.ts.agg[tile], S.tot_agg);
                 st_release(&p.ts.flags[tile], (seq << 2) | 1u);
             } else {
-                st_agg(&p.ts.pre[0], S.tot_agg);
+                const GAgg e0 = p.E0 ? *p.E0 : agg_id();
+                S.E = e0;
+                st_agg(&p.ts.pre[0], acomb(e0, S.tot_agg, tp, tt));
                 st_release(&p.ts.flags[0], (seq << 2) | 2u);
             }
         }
@@ -419,18 +421,22 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             unsigned stl = 0;
             GAgg Ew = agg_id();
             if (tile > 0) Ew = lookback_agg_warp(p, tile, seq, &stl);
+            else Ew = p.E0 ? *p.E0 : agg_id();
             if (tid == 0) {
                 if (tile > 0) {
                     st_agg(&p.ts.pre[tile], acomb(Ew, S.tile_agg, tp, tt));
                     st_release(&p.ts.flags[tile], (seq << 2) | 2u);
                 }
+                if (tile == p.n_tiles - 1 && p.state_out) *p.state_out = acomb(Ew, S.tile_agg, tp, tt);
                 S.E = Ew;
                 if (stl) atomicOr(&S.status, stl);
             }
         }
         __syncthreads();
         const GAgg E = S.E;
-        const bool prev_global = E.tdc.n > 0;
+        // a call sees only its own triggers: "earlier" means earlier in this call
+        const long long trig_base = p.E0 ? p.E0->tdc.n : 0;
+        const bool prev_global = E.tdc.n > trig_base;
         const GAgg st = acomb(E, ex, tp, tt);   // global chain state before position p0
 
         // ---- walk 3: unwrapped trigger times ----
@@ -450,7 +456,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 const long long t = r + ep * kTdcPeriod;
                 if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
                 if (q < cnt) {
-                    const long long g = E.tdc.n + li;
+                    const long long g = E.tdc.n - trig_base + li;
                     if (g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
                 }
                 ++li;
@@ -715,7 +721,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                     S.clo = Ow;
                     if (st2) atomicOr(&S.status, st2);
                     if (tile == p.n_tiles - 1) {
-                        const long long ntr = E.tdc.n + (long long)S.cnt[C_TDCS];
+                        const long long ntr = E.tdc.n - trig_base + (long long)S.cnt[C_TDCS];
                         *p.n_clusters = Ow + ncl;
                         *p.n_trig = ntr;
                         if (Ow + ncl > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);

@@ -92,6 +92,8 @@ struct Params {
     unsigned int seq;
     TileScratch ts;
     Ctl *ctl;
+    const GAgg *E0;          // unwrap state before the call (NULL: stream start)
+    GAgg *state_out;         // state after the call, written by the last tile (or NULL)
 };
 
 }  // namespace tpxk

@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(GT) k_tile_agg(const uint64_t *pk, long long n
 
 // exclusive prefix over tiles (one thread: this path is not on the benchmark)
 __global__ void k_tile_prefix(const GAgg *tagg, GAgg *tpre, const long long *tcnt, long long *toff, long long tiles,
-                              long long tp, long long tt, long long *n_trig_out) {
-    GAgg acc = agg_id();
+                              long long tp, long long tt, long long *n_trig_out, const GAgg *E0, GAgg *state_out) {
+    GAgg acc = E0 ? *E0 : agg_id();
     long long off = 0;
     for (long long t = 0; t < tiles; ++t) {
         tpre[t] = acc;
@@ -124,6 +124,7 @@ __global__ void k_tile_prefix(const GAgg *tagg, GAgg *tpre, const long long *tcn
     }
     toff[tiles] = off;
     *n_trig_out = off;
+    if (state_out) *state_out = acc;
 }
 
 __global__ void __launch_bounds__(GT) k_unwrap(const uint64_t *pk, long long n, const GAgg *tpre, const long long *toff,
@@ -245,7 +246,8 @@ __global__ void k_serial_prefix(const long long *cnt, long long *off, long long 
 __global__ void __launch_bounds__(GT) k_compact(const uint64_t *pk, long long n, long long idx_base, const long long *t_all,
                                                 const long long *trig, long long ntr, long long tof_max,
                                                 const int16_t *lut, const long long *tile_off, tpx_hits hits,
-                                                long long cap, unsigned *status) {
+                                                long long cap, unsigned *status, const GAgg *E0) {
+    const long long trig_base = E0 ? E0->tdc.n : 0;
     __shared__ long long s_w[GW];
     __shared__ long long s_tot;
     const long long tile = blockIdx.x, q0 = tile * GTILE + threadIdx.x * GK;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(GT) k_compact(const uint64_t *pk, long long n,
             const int tot = pix_tot(w);
             const long long corr = lut ? (long long)lut[tot] : 0LL;
             hits.index[o] = idx_base + q;
-            hits.shot[o] = s;
+            hits.shot[o] = s + trig_base;
             hits.t[o] = t_all[q] - corr;
             hits.tof[o] = (int32_t)(f - corr);
             hits.x[o] = (uint8_t)pix_x(w);
@@ -621,7 +623,8 @@ int sort_hits(tpx_ctx *c, Arena &a, const tpx_hits &h, long long n, unsigned **v
 }
 
 int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const tpx_hits &h, int64_t cap,
-                int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl) {
+                int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
+                const GAgg *E0, GAgg *state_out) {
     cudaStream_t s = c->stream;
     const long long tiles = (n + GTILE - 1) / GTILE;
     const size_t need = sz(tiles, sizeof(GAgg)) * 2 + sz(tiles + 1, 8) * 4 + sz(n, 8) + 4096;
@@ -635,10 +638,15 @@ int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const t
     if (clear_ctl && cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_hits, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_n_trig, 0, 8, s) != cudaSuccess)
         return TPX_ECUDA;
-    if (n == 0) return TPX_OK;
+    if (n == 0) {   // the state passes through unchanged
+        if (!state_out) return TPX_OK;
+        if (E0) return ck(cudaMemcpyAsync(state_out, E0, sizeof(GAgg), cudaMemcpyDeviceToDevice, s));
+        return ck(cudaMemsetAsync(state_out, 0, sizeof(GAgg), s));
+    }
     const long long tp = c->cfg.wrap_thr_pix_ticks, tt = c->cfg.wrap_thr_tdc_ticks;
     k_tile_agg<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tp, tt, tagg, tcnt);
-    k_tile_prefix<<<1, 1, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, reinterpret_cast<long long *>(d_n_trig));
+    k_tile_prefix<<<1, 1, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, reinterpret_cast<long long *>(d_n_trig),
+                                  E0, state_out);
     k_unwrap<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tpre, toff, tp, tt, t_all, reinterpret_cast<long long *>(trig),
                                             trig_cap, &c->ctl->status);
     long long ntr_h = 0;
@@ -651,7 +659,7 @@ int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const t
     k_serial_prefix<<<1, 1, 0, s>>>(tkept, tkoff, tiles, reinterpret_cast<long long *>(d_n_hits));
     k_compact<<<(unsigned)tiles, GT, 0, s>>>(pk, n, base, t_all, reinterpret_cast<long long *>(trig), ntr_h,
                                              c->cfg.tof_max_ticks, c->cfg.d_timewalk_lut, tkoff, h, cap,
-                                             &c->ctl->status);
+                                             &c->ctl->status, E0);
     const unsigned long long np = (unsigned long long)n;
     if (cudaMemcpyAsync(&c->ctl->counters[C_PACKETS], &np, 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return TPX_ECUDA;
@@ -783,7 +791,8 @@ int redo_last(tpx_ctx *c) {
     long long *hl = a.take<long long>(n);
     unsigned char *hp = a.take<unsigned char>(n);
     long long *nh_d = a.take<long long>(1);
-    int rc = decode_impl(c, L.pk, n, L.base, h, n, reinterpret_cast<int64_t *>(nh_d), L.trig, L.trig_cap, L.n_trig, true);
+    int rc = decode_impl(c, L.pk, n, L.base, h, n, reinterpret_cast<int64_t *>(nh_d), L.trig, L.trig_cap, L.n_trig, true,
+                         L.E0, L.state_out);
     long long nh = 0;
     if (!rc) rc = ck(cudaMemcpyAsync(&nh, nh_d, 8, cudaMemcpyDeviceToHost, s));
     if (!rc) rc = ck(cudaStreamSynchronize(s));
@@ -826,7 +835,10 @@ extern "C" int tpx_decode(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t bas
         return TPX_EINVAL;
     if (trig_cap > 0 && !trig) return TPX_EINVAL;
     c->last.valid = false;
-    return tpxg::decode_impl(c, pk, n, base, *hits, cap, d_n_hits, trig, trig_cap, d_n_trig, true);
+    const tpxk::GAgg *E0 = nullptr;
+    tpxk::GAgg *out = nullptr;
+    take_state(c, &E0, &out);
+    return tpxg::decode_impl(c, pk, n, base, *hits, cap, d_n_hits, trig, trig_cap, d_n_trig, true, E0, out);
 }
 
 extern "C" int tpx_cluster(tpx_ctx *c, const tpx_hits *hits, int64_t n, int64_t *d_labels, uint8_t *d_is_peak) {

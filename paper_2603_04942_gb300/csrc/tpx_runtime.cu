@@ -12,6 +12,13 @@
 #include "tpx_fused.cuh"
 
 
+void take_state(tpx_ctx *c, const tpxk::GAgg **E0, tpxk::GAgg **out) {
+    *E0 = (c->cfg.chain || c->state_once) ? &c->d_state[c->cur] : nullptr;
+    *out = &c->d_state[c->cur ^ 1];
+    c->cur ^= 1;
+    c->state_once = false;
+}
+
 namespace {
 
 constexpr int64_t kMaxTofMax = (1LL << 24) - 65537;
@@ -115,6 +122,13 @@ int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *
     }
     std::memset(c->h_ctl, 0, sizeof(tpxk::Ctl));
     cudaMemset(c->ctl, 0, sizeof(tpxk::Ctl));
+    if (cudaMalloc(&c->d_state, 2 * sizeof(tpxk::GAgg)) != cudaSuccess) {
+        cudaFree(c->ctl);
+        cudaFreeHost(c->h_ctl);
+        delete c;
+        return TPX_ENOMEM;
+    }
+    cudaMemset(c->d_state, 0, 2 * sizeof(tpxk::GAgg));   // all zero = the start of a stream
     rc = alloc_scratch(c, max_packets);
     if (rc) {
         cudaFree(c->ctl);
@@ -147,6 +161,7 @@ int tpx_destroy(tpx_ctx *c) {
     if (c->st_trig) cudaFree(c->st_trig);
     if (c->st_counts) cudaFree(c->st_counts);
     if (c->g_mem) cudaFree(c->g_mem);
+    if (c->d_state) cudaFree(c->d_state);
     delete c;
     return TPX_OK;
 }
@@ -172,10 +187,19 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     c->last.trig = d_trig;
     c->last.trig_cap = trig_cap;
     c->last.n_trig = d_n_trig;
+    const tpxk::GAgg *E0 = nullptr;
+    tpxk::GAgg *state_out = nullptr;
+    take_state(c, &E0, &state_out);
+    c->last.E0 = E0;
+    c->last.state_out = state_out;
     if (cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), c->stream) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_clusters, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_trig, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
-    if (n == 0) return TPX_OK;
+    if (n == 0) {   // the state passes through unchanged
+        if (E0) return cudaMemcpyAsync(state_out, E0, sizeof(tpxk::GAgg), cudaMemcpyDeviceToDevice, c->stream)
+                       == cudaSuccess ? TPX_OK : TPX_ECUDA;
+        return cudaMemsetAsync(state_out, 0, sizeof(tpxk::GAgg), c->stream) == cudaSuccess ? TPX_OK : TPX_ECUDA;
+    }
     c->seq = (c->seq + 1) & 0x3FFFFFFFu;
     if (c->seq == 0) {   // sequence numbers wrapped: clear the flags once
         c->seq = 1;
@@ -208,6 +232,8 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.seq = c->seq;
     p.ts = c->ts;
     p.ctl = c->ctl;
+    p.E0 = E0;
+    p.state_out = state_out;
     int64_t grid = c->num_sms;   // persistent: one CTA per SM
     if (grid > p.n_tiles) grid = p.n_tiles;
     cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, (int)grid, c->stream);
@@ -291,6 +317,43 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     *h_n_clusters = counts[0];
     *h_n_trig = counts[1];
     return tpx_sync(c, nullptr);
+}
+
+int tpx_set_state(tpx_ctx *c, const tpx_stream_state *st) {
+    if (!c) return TPX_EINVAL;
+    tpxk::GAgg &g = c->h_state;
+    std::memset(&g, 0, sizeof g);
+    if (st) {
+        if (st->pixels < 0 || st->triggers < 0) return TPX_EINVAL;
+        g.pix.n = st->pixels;
+        g.pix.first = st->pix_last_raw;
+        g.pix.last = st->pix_last_raw;
+        g.pix.sum = st->pix_wraps;
+        g.tdc.n = st->triggers;
+        g.tdc.first = st->tdc_last_raw;
+        g.tdc.last = st->tdc_last_raw;
+        g.tdc.sum = st->tdc_wraps;
+    }
+    if (cudaMemcpyAsync(&c->d_state[c->cur], &g, sizeof g, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return TPX_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    c->state_once = true;
+    return TPX_OK;
+}
+
+int tpx_get_state(tpx_ctx *c, tpx_stream_state *st) {
+    if (!c || !st) return TPX_EINVAL;
+    tpxk::GAgg &g = c->h_state;
+    if (cudaMemcpyAsync(&g, &c->d_state[c->cur], sizeof g, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return TPX_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    st->pixels = g.pix.n;
+    st->pix_last_raw = g.pix.last;
+    st->pix_wraps = g.pix.sum;
+    st->triggers = g.tdc.n;
+    st->tdc_last_raw = g.tdc.last;
+    st->tdc_wraps = g.tdc.sum;
+    return TPX_OK;
 }
 
 const char *tpx_strerror(int code) {

@@ -1,0 +1,97 @@
+"""A stream fed as consecutive calls (cut at trigger packets) gives exactly the
+single-call result: the unwrap state and trigger count carry over on the
+device (chain mode) or through tpx_get_state / tpx_set_state."""
+import numpy as np
+import pytest
+
+import paper_2603_04942_gb300 as tpx
+import synth
+from gpu_common import assert_clusters_equal, gpu_run, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def run_calls(pk, cuts, chain=True, fused=True):
+    import torch
+    ctx = tpx.Context(tpx.Config(chain=chain), max_packets=pk.size)
+    labels, clusters, trig = [], [], []
+    try:
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            part = pk[a:b]
+            d = to_device(part)
+            out = ctx.alloc_outputs(part.size, True, True, max(16, part.size), max(16, part.size))
+            ctx.tpx_process(d, out, index_base=a)
+            rc, cnt = ctx.tpx_sync(check=False)
+            assert rc == 0
+            r = ctx.collect(out, rc, cnt)
+            labels.append(r["labels"])
+            clusters.append(r["clusters"])
+            trig.append(r["triggers"])
+        return np.concatenate(labels), np.concatenate(clusters), np.concatenate(trig), ctx.tpx_get_state()
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_chained_calls_equal_one_call(seed):
+    # shots 480..560 of the small configuration cross the first pixel wrap
+    pk = synth.generate(synth.small(shot_begin=0, n_shots=560, pair_frac=0.05, dark_per_shot=2.0))[0]
+    whole = gpu_run(pk)
+    tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
+    rng = np.random.default_rng(seed)
+    cuts = [0] + sorted(rng.choice(tdc[1:], size=7, replace=False).tolist()) + [pk.size]
+    labels, clusters, trig, state = run_calls(pk, cuts)
+    assert np.array_equal(labels, whole["labels"])
+    assert np.array_equal(trig, whole["triggers"])
+    assert_clusters_equal(clusters, whole["clusters"])
+    assert state["triggers"] == tdc.size
+    assert state["pix_wraps"] == 1
+
+
+def test_state_handed_to_another_context():
+    pk = synth.generate(synth.small(shot_begin=0, n_shots=540))[0]
+    whole = gpu_run(pk)
+    tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
+    cut = int(tdc[510])                       # after the first pixel wrap
+    import torch
+    a = tpx.Context(tpx.Config(), max_packets=pk.size)
+    out = a.alloc_outputs(cut, True, False, cut, cut)
+    a.tpx_process(to_device(pk[:cut]), out)
+    a.tpx_sync()
+    st = a.tpx_get_state()
+    a.close()
+    assert st["pix_wraps"] == 1 and st["triggers"] == 510
+    b = tpx.Context(tpx.Config(), max_packets=pk.size)
+    b.tpx_set_state(st)
+    rest = pk[cut:]
+    out = b.alloc_outputs(rest.size, True, False, rest.size, rest.size)
+    b.tpx_process(to_device(rest), out, index_base=cut)
+    rc, cnt = b.tpx_sync(check=False)
+    r = b.collect(out, rc, cnt)
+    b.close()
+    assert rc == 0
+    assert np.array_equal(r["labels"], whole["labels"][cut:])
+    sel = whole["clusters"]["label"] >= cut
+    assert_clusters_equal(r["clusters"], whole["clusters"][sel])
+    assert np.array_equal(r["triggers"], whole["triggers"][510:])
+
+
+def test_chained_general_path_redo():
+    """The exact redo through the general path also continues the state."""
+    rng = np.random.default_rng(5)
+    from streams import StreamBuilder
+    b = StreamBuilder()
+    t0 = 7_000_000
+    for s in range(3):
+        b.tdc(t0 + s * 640_000)
+        n = 9_000 if s == 1 else 300
+        for _ in range(n):
+            b.pix(rng.integers(0, 80), rng.integers(0, 80), rng.integers(1, 200), t0 + s * 640_000 + 900 + rng.integers(0, 3000))
+    pk = b.packets()
+    whole = gpu_run(pk)
+    assert whole["counters"]["redone"] == 1
+    tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
+    labels, clusters, trig, state = run_calls(pk, [0, int(tdc[1]), int(tdc[2]), pk.size])
+    assert np.array_equal(labels, whole["labels"])
+    assert_clusters_equal(clusters, whole["clusters"])
+    assert state["triggers"] == 3
