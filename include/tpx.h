@@ -259,6 +259,20 @@ int tpx_set_state(tpx_ctx *ctx, const tpx_stream_state *state);
 /* The state after the last tpx_process / tpx_decode (synchronises). */
 int tpx_get_state(tpx_ctx *ctx, tpx_stream_state *state);
 
+/* Associative summary of a stretch of the stream's two unwrap chains
+   (Sec. IV.A): counts, first and last raw times, and the wrap steps inside the
+   stretch.  Summaries of consecutive stretches combine in order; the
+   combination of all stretches before a shard is that shard's starting state
+   (tpx_set_state), which is how ranks that each hold a contiguous range of
+   shots agree on the unwrap state without exchanging packets. */
+typedef struct tpx_chain_summary {
+    int64_t pixels, pix_first_raw, pix_last_raw, pix_wraps;
+    int64_t triggers, tdc_first_raw, tdc_last_raw, tdc_wraps;
+} tpx_chain_summary;
+
+/* Summarise d_packets[0, n_packets) (one read of the packets; synchronises). */
+int tpx_summarize(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets, tpx_chain_summary *out);
+
 /* Static description of a status code. */
 const char *tpx_strerror(int code);
 

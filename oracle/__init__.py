@@ -42,7 +42,9 @@ class _Cfg(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("tof_max_ticks", ctypes.c_int64),
                 ("wrap_thr_pix_ticks", ctypes.c_int64), ("wrap_thr_tdc_ticks", ctypes.c_int64),
                 ("timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("epoch0_pix", ctypes.c_int64), ("epoch0_tdc", ctypes.c_int64)]
+                ("reserved", ctypes.c_int32), ("epoch0_pix", ctypes.c_int64), ("epoch0_tdc", ctypes.c_int64),
+                ("have_prev_pix", ctypes.c_int32), ("have_prev_tdc", ctypes.c_int32),
+                ("prev_pix_raw", ctypes.c_int64), ("prev_tdc_raw", ctypes.c_int64)]
 
 
 class _Counters(ctypes.Structure):
@@ -62,6 +64,8 @@ class Config:
     strict: bool = False
     epoch0_pix: int = 0      # wraps before the first pixel packet (slices of a longer stream)
     epoch0_tdc: int = 0
+    prev_pix_raw: int | None = None   # raw value of the pixel packet before the slice
+    prev_tdc_raw: int | None = None   # raw value of the TDC packet before the slice
 
 
 def _build() -> str:
@@ -103,7 +107,9 @@ def run(packets: np.ndarray, cfg: Config | None = None, idx_base: int = 0, want_
     pk = np.ascontiguousarray(packets, dtype=np.uint64)
     n = pk.size
     c = _Cfg(cfg.rx, cfg.ry, cfg.dt_ticks, cfg.mode, cfg.tof_max_ticks, cfg.wrap_thr_pix_ticks,
-             cfg.wrap_thr_tdc_ticks, None, int(cfg.strict), 0, int(cfg.epoch0_pix), int(cfg.epoch0_tdc))
+             cfg.wrap_thr_tdc_ticks, None, int(cfg.strict), 0, int(cfg.epoch0_pix), int(cfg.epoch0_tdc),
+             int(cfg.prev_pix_raw is not None), int(cfg.prev_tdc_raw is not None),
+             int(cfg.prev_pix_raw or 0), int(cfg.prev_tdc_raw or 0))
     lut = None
     if cfg.timewalk_lut is not None:
         lut = np.ascontiguousarray(cfg.timewalk_lut, dtype=np.int16)

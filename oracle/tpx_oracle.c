@@ -67,6 +67,9 @@ typedef struct orc_config {
     int32_t reserved;
     int64_t epoch0_pix, epoch0_tdc;      /* wraps before the first packet (a slice
                                             cut from the middle of a stream) */
+    int32_t have_prev_pix, have_prev_tdc;/* the slice continues a stream: the step
+                                            rule applies to its first packet too, */
+    int64_t prev_pix_raw, prev_tdc_raw;  /* against these previous raw values    */
 } orc_config;
 
 typedef struct orc_cluster {
@@ -140,8 +143,9 @@ int orc_run(const orc_config *cfg, const uint64_t *pk, int64_t n, int64_t idx_ba
     int32_t *py = (int32_t *)calloc((size_t)(n + 1), sizeof(int32_t));
     int32_t *ptot = (int32_t *)calloc((size_t)(n + 1), sizeof(int32_t));
     if (!type || !t || !px || !py || !ptot) return ORC_ENOMEM;
-    int have_pix = 0, have_tdc = 0;
-    int64_t prev_pix = 0, prev_tdc = 0, epoch_pix = cfg->epoch0_pix, epoch_tdc = cfg->epoch0_tdc;
+    int have_pix = cfg->have_prev_pix != 0, have_tdc = cfg->have_prev_tdc != 0;
+    int64_t prev_pix = cfg->prev_pix_raw, prev_tdc = cfg->prev_tdc_raw;
+    int64_t epoch_pix = cfg->epoch0_pix, epoch_tdc = cfg->epoch0_tdc;
     for (int64_t i = 0; i < n; i++) {
         uint64_t w = pk[i];
         unsigned hdr = (unsigned)(w >> 60);

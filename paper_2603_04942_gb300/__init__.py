@@ -38,7 +38,8 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_set_state", "tpx_get_state", "tpx_strerror", "tpx_version")
+                    "tpx_centroid", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_strerror",
+                    "tpx_version")
 
 
 class _CConfig(ctypes.Structure):
@@ -53,6 +54,14 @@ STATE_FIELDS = ("pixels", "pix_last_raw", "pix_wraps", "triggers", "tdc_last_raw
 
 class _CState(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in STATE_FIELDS]
+
+
+SUMMARY_FIELDS = ("pixels", "pix_first_raw", "pix_last_raw", "pix_wraps",
+                  "triggers", "tdc_first_raw", "tdc_last_raw", "tdc_wraps")
+
+
+class _CSummary(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in SUMMARY_FIELDS]
 
 
 class _CCounters(ctypes.Structure):
@@ -114,6 +123,8 @@ def load(path: str | None = None):
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_set_state.restype = i32
         L.tpx_get_state.restype = i32
+        L.tpx_summarize.argtypes = [vp, vp, i64, ctypes.POINTER(_CSummary)]
+        L.tpx_summarize.restype = i32
         L.tpx_decode.argtypes = [vp, vp, i64, i64, ctypes.POINTER(_CHits), i64, vp, vp, i64, vp]
         L.tpx_cluster.argtypes = [vp, ctypes.POINTER(_CHits), i64, vp, vp]
         L.tpx_centroid.argtypes = [vp, ctypes.POINTER(_CHits), vp, vp, i64, vp, i64, vp]
@@ -172,6 +183,15 @@ class Context:
         if rc:
             raise TpxError(rc, "tpx_get_state")
         return {f: int(getattr(st, f)) for f in STATE_FIELDS}
+
+    def tpx_summarize(self, packets, n_packets: int | None = None) -> dict:
+        """Associative unwrap summary of a packet range (see shard.py)."""
+        n = int(packets.numel() if n_packets is None else n_packets)
+        out = _CSummary()
+        rc = lib().tpx_summarize(self._h, _ptr(packets), n, ctypes.byref(out))
+        if rc:
+            raise TpxError(rc, "tpx_summarize")
+        return {f: int(getattr(out, f)) for f in SUMMARY_FIELDS}
 
     def close(self):
         if getattr(self, "_h", None):

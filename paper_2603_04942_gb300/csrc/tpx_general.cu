@@ -854,3 +854,36 @@ extern "C" int tpx_centroid(tpx_ctx *c, const tpx_hits *hits, const int64_t *d_l
     c->last.valid = false;
     return tpxg::centroid_impl(c, *hits, d_labels, d_is_peak, n, d_clusters, cap, d_n_clusters);
 }
+
+extern "C" int tpx_summarize(tpx_ctx *c, const uint64_t *pk, int64_t n, tpx_chain_summary *out) {
+    if (!c || !out || n < 0 || (n > 0 && !pk)) return TPX_EINVAL;
+    using namespace tpxg;
+    cudaStream_t s = c->stream;
+    const long long tiles = (n + GTILE - 1) / GTILE;
+    const size_t need = sz(tiles, sizeof(tpxk::GAgg)) * 2 + sz(tiles + 1, 8) * 2 + sz(1, sizeof(tpxk::GAgg)) + 4096;
+    int rc = reserve(c, need);
+    if (rc) return rc;
+    Arena a{static_cast<char *>(c->g_mem), 0, c->g_bytes};
+    tpxk::GAgg *tagg = a.take<tpxk::GAgg>(tiles), *tpre = a.take<tpxk::GAgg>(tiles);
+    long long *tcnt = a.take<long long>(tiles + 1), *toff = a.take<long long>(tiles + 1);
+    tpxk::GAgg *res = a.take<tpxk::GAgg>(1);
+    long long *ntr = toff + tiles;
+    tpxk::GAgg h;
+    std::memset(&h, 0, sizeof h);
+    if (n > 0) {
+        const long long tp = c->cfg.wrap_thr_pix_ticks, tt = c->cfg.wrap_thr_tdc_ticks;
+        k_tile_agg<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tp, tt, tagg, tcnt);
+        k_tile_prefix<<<1, 1, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, ntr, nullptr, res);
+        if (cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    out->pixels = h.pix.n;
+    out->pix_first_raw = h.pix.first;
+    out->pix_last_raw = h.pix.last;
+    out->pix_wraps = h.pix.sum;
+    out->triggers = h.tdc.n;
+    out->tdc_first_raw = h.tdc.first;
+    out->tdc_last_raw = h.tdc.last;
+    out->tdc_wraps = h.tdc.sum;
+    return TPX_OK;
+}

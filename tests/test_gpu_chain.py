@@ -95,3 +95,36 @@ def test_chained_general_path_redo():
     assert np.array_equal(labels, whole["labels"])
     assert_clusters_equal(clusters, whole["clusters"])
     assert state["triggers"] == 3
+
+
+def test_shards_on_one_gpu_equal_one_call():
+    """The multi-GPU shard pipeline, its ranks run one after another on one
+    GPU: per-range unwrap summaries on the device, the in-order combination,
+    and each range processed from its starting state."""
+    from paper_2603_04942_gb300 import shard
+    from test_shard_gloo import _summary
+    pk = synth.generate(synth.small(shot_begin=350, n_shots=350, pair_frac=0.05))[0]
+    whole = gpu_run(pk)
+    cuts = shard.plan_cuts((pk >> np.uint64(60)) == 6, 3)
+    summaries = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+        s = ctx.tpx_summarize(to_device(pk[a:b]))
+        ctx.close()
+        assert s == _summary(pk[a:b])
+        summaries.append(s)
+    states = shard.states_from_summaries(summaries)
+    labels, clusters = [], []
+    for (a, b), st in zip(zip(cuts[:-1], cuts[1:]), states):
+        ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+        part = pk[a:b]
+        out = ctx.alloc_outputs(part.size, True, False, part.size, part.size)
+        shard.process_shard(ctx, to_device(part), a, st, out)
+        rc, cnt = ctx.tpx_sync(check=False)
+        assert rc == 0
+        r = ctx.collect(out, rc, cnt)
+        ctx.close()
+        labels.append(r["labels"])
+        clusters.append(r["clusters"])
+    assert np.array_equal(np.concatenate(labels), whole["labels"])
+    assert_clusters_equal(np.concatenate(clusters), whole["clusters"])

@@ -371,3 +371,21 @@ def test_slice_with_initial_epochs_matches_full_stream():
     cs["shot"] += k
     assert np.array_equal(cf, cs)
     assert np.array_equal(rs["labels"], rf["labels"][tdc_pos[k]:tdc_pos[k + 1]])
+
+
+def test_slice_continuing_a_stream_across_a_wrap():
+    """A slice given the previous raw values and wrap counts applies the step
+    rule of Sec. IV.A to its first packet too, so a cut placed right after a
+    wrap still reproduces the full stream's times."""
+    P = 1 << 34
+    b = StreamBuilder()
+    b.tdc(P - 100_000)
+    true = [P - 9000, P - 5000, P + 300, P - 100, P + 900, P + 5000]
+    for t in true:
+        b.pix(3, 3, 10, t)
+    pk = b.packets()
+    full = oracle.run(pk, want_info=True)["info"]["t"]
+    # cut after the first post-wrap pixel: the slice starts with a straggler
+    cfg = oracle.Config(epoch0_pix=1, epoch0_tdc=0, prev_pix_raw=(P + 300) % P, prev_tdc_raw=P - 100_000)
+    part = oracle.run(pk[4:], cfg, want_info=True)["info"]["t"]
+    assert list(part) == list(full[4:]) == true[3:]
