@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-shots", type=int, default=50_000)
     ap.add_argument("--ref-shots", type=int, default=10_000)
+    ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--stream-only", action="store_true")
+    ap.add_argument("--stream-chunks", type=int, default=150)
+    ap.add_argument("--stream-rates", type=str, default="10,40,80")
     return ap.parse_args()
 
 
@@ -164,6 +168,72 @@ def cpu_baseline(args, sample_shots: int) -> dict:
                       f"in 25,000-shot calls, {tot_t:.1f} s single-threaded"}
 
 
+def stream_bench(args) -> dict:
+    """Streaming: a continuous ion-like stream (ToF over the whole 1 ms
+    period) at each rate, cut into chunks of U[1,100] ms of acquisition time
+    at arbitrary packets; each chunk is submitted from pinned host memory and
+    polled at once (service latency = submit entry to records on the host)."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    out = {"workload": "continuous ion-like stream, 1 kHz triggers, sigma 1.2 px, ToF uniform over the 1 ms "
+                       "period (cut at the full period), chunks of U[1,100] ms of acquisition time cut at "
+                       "arbitrary packets, hold 2 shots open, general path", "rates": {}}
+    rng = np.random.default_rng(3)
+    for rate_m in [float(r) for r in args.stream_rates.split(",") if r]:
+        durs = rng.uniform(1.0, 100.0, size=args.stream_chunks)
+        n_shots = int(np.ceil(durs.sum())) + 3
+        st = synth.Stream(synth.streaming(rate_m * 1e6, n_shots))
+        n = st.n_packets
+        h = torch.empty(n, dtype=torch.int64, pin_memory=True)
+        pk = st.packets_into(h.numpy().view(np.uint64))
+        st.close()
+        tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
+        # chunk ends at arbitrary packets: interpolate between trigger packets
+        ends_ms = np.cumsum(durs)
+        k = np.floor(ends_ms).astype(np.int64)
+        frac = ends_ms - k
+        cut = tdc[np.minimum(k, tdc.size - 2)] + (frac * (tdc[np.minimum(k + 1, tdc.size - 1)]
+                                                           - tdc[np.minimum(k, tdc.size - 2)])).astype(np.int64)
+        cut = np.minimum(np.maximum.accumulate(cut), n)
+        cut[-1] = n
+        sizes = np.diff(np.r_[0, cut])
+        cfg = tpx.Config(tof_max_ticks=synth.STREAM_TOF_MAX_TICKS)
+        s = tpx.Stream(cfg, max_chunk_packets=int(sizes.max()), max_hold_packets=int(4 * n / n_shots) + 65536,
+                       hold_triggers=2, slots=2)
+        # warm-up on a copy of the first chunks in a separate stream object
+        w = tpx.Stream(cfg, max_chunk_packets=int(sizes.max()), max_hold_packets=int(4 * n / n_shots) + 65536,
+                       hold_triggers=2, slots=2)
+        pos = 0
+        for c in sizes[:3]:
+            w.poll(w.submit(pk[pos:pos + c]))
+            pos += c
+        w.close()
+        lat, hits_done, clusters = [], 0, 0
+        pos = 0
+        t_all0 = time.perf_counter()
+        for c in sizes:
+            r = s.poll(s.submit(pk[pos:pos + c]))
+            lat.append(r["latency_us"])
+            clusters += r["clusters"].size
+            pos += c
+        r = s.poll(s.finish())
+        clusters += r["clusters"].size
+        wall = time.perf_counter() - t_all0
+        s.close()
+        hits = int(((pk >> np.uint64(60)) == 0xB).sum())
+        lat = np.array(lat)
+        acq_s = float(durs.sum()) / 1e3
+        out["rates"][f"{rate_m:g} Mhit/s"] = {
+            "chunks": int(sizes.size), "packets": int(n), "pixel_hits": hits, "clusters": int(clusters),
+            "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "p99.9": float(np.percentile(lat, 99.9)), "max": float(lat.max())},
+            "sustained_hits_per_s": hits / wall, "acquisition_s": acq_s, "processing_s": wall,
+            "realtime_factor": acq_s / wall}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, one bounded sample of
     the workload per step (a different shot range each step)."""
@@ -196,6 +266,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.stream_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2603_04942_gb300 import build as tbuild
+        tbuild.build()
+        print(json.dumps(stream_bench(args)), flush=True)
+        return 0
     import torch
     import torch.distributed as dist
 
@@ -304,6 +381,11 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args, args.cpu_shots)
+    stream = None
+    if rank == 0 and not args.no_stream:
+        del d_pk
+        torch.cuda.empty_cache()
+        stream = stream_bench(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -315,7 +397,7 @@ def main():
                            "l2": "inputs larger than L2 (10 GB packet stream per step)",
                            "parallelism": f"{world} independent shot ranges" if world > 1 else "1 GPU",
                            "generation_s": round(t_gen, 1)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "clocks": clk,
                 "gpu_launches": args.steps,
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "counters": counters}

@@ -273,6 +273,67 @@ typedef struct tpx_chain_summary {
 /* Summarise d_packets[0, n_packets) (one read of the packets; synchronises). */
 int tpx_summarize(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets, tpx_chain_summary *out);
 
+/* ---- streaming: acquisition chunks in, particle hits out ---------------
+   A stream takes the packet stream in consecutive chunks as they arrive
+   (any sizes; a chunk need not end at a trigger).  Each submit processes
+   everything held so far plus the new chunk through the general path and
+   emits the records of every shot that is closed: all shots except the
+   last `hold_triggers` ones, whose pixels may still arrive in a later chunk
+   (a pixel reports after its light curve ends, Sec. III, so with a long ToF
+   cut pixels of shot k follow trigger k+1 in the stream).  Clusters that
+   straddle chunk boundaries are therefore complete when emitted, and the
+   unwrap state of the held part stays on the device.  Results of a chunk are
+   exactly those of processing the whole stream at once, restricted to the
+   emitted shots, provided hold_triggers spans tof_max plus the readout
+   delay.  Each result lists its records in ascending label order; across
+   results the order is by shot (a late cluster of shot k, read out after
+   trigger k+1, can carry a larger label than an early cluster of shot k+1).
+   Per-packet labels are not produced by streams. */
+typedef struct tpx_stream tpx_stream;
+
+typedef struct tpx_stream_config {
+    tpx_config cfg;               /* processing configuration (chain ignored) */
+    int64_t max_chunk_packets;    /* largest chunk a submit accepts           */
+    int64_t max_hold_packets;     /* largest held (open) part; exceeding it is
+                                     TPX_EOVERFLOW                            */
+    int32_t hold_triggers;        /* shots held open after each chunk (>= 1)  */
+    int32_t slots;                /* chunks whose results may await poll      */
+    int64_t hbm_budget_bytes;     /* process-wide device memory for all
+                                     streams (0: no limit); create returns
+                                     TPX_EAGAIN when a new stream exceeds it  */
+} tpx_stream_config;
+
+typedef struct tpx_stream_result {
+    uint64_t ticket;
+    int32_t status;               /* status of processing this chunk          */
+    int32_t reserved;
+    int64_t first_shot;           /* emitted shots: [first_shot, first_shot +  */
+    int64_t n_shots;              /*                 n_shots), global indices  */
+    const int64_t *trig_t;        /* their trigger times (host)               */
+    int64_t n_clusters;
+    const tpx_record *clusters;   /* host; valid until the slot is reused     */
+    int64_t packets_processed;    /* packets the chunk's processing covered   */
+    double latency_us;            /* submit entry to results on the host      */
+} tpx_stream_result;
+
+/* Create a stream on the current device, working on `cuda_stream`.
+   Errors: TPX_EINVAL, TPX_ENOMEM, TPX_EAGAIN (budget). */
+int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda_stream);
+
+/* Submit a chunk (host memory; pinned for best latency).  Returns a ticket.
+   TPX_EAGAIN when every slot holds results not yet polled (admission);
+   TPX_EINVAL when n_packets exceeds max_chunk_packets. */
+int tpx_stream_submit(tpx_stream *st, const uint64_t *h_chunk, int64_t n_packets, uint64_t *ticket);
+
+/* End of the stream: emit every held shot (returns a ticket like submit). */
+int tpx_stream_finish(tpx_stream *st, uint64_t *ticket);
+
+/* Wait up to timeout_us (negative: forever) for a ticket's results.
+   TPX_ETIMEOUT if not ready in time, TPX_EINVAL for an unknown ticket. */
+int tpx_stream_poll(tpx_stream *st, uint64_t ticket, tpx_stream_result *out, int32_t timeout_us);
+
+int tpx_stream_destroy(tpx_stream *st);
+
 /* Static description of a status code. */
 const char *tpx_strerror(int code);
 

@@ -38,8 +38,9 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_strerror",
-                    "tpx_version")
+                    "tpx_centroid", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
+                    "tpx_strerror", "tpx_version")
 
 
 class _CConfig(ctypes.Structure):
@@ -70,6 +71,18 @@ class _CCounters(ctypes.Structure):
 
 class _CHits(ctypes.Structure):
     _fields_ = [(f, ctypes.c_void_p) for f in ("index", "shot", "t", "tof", "x", "y", "tot")]
+
+
+class _CStreamConfig(ctypes.Structure):
+    _fields_ = [("cfg", _CConfig), ("max_chunk_packets", ctypes.c_int64), ("max_hold_packets", ctypes.c_int64),
+                ("hold_triggers", ctypes.c_int32), ("slots", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64)]
+
+
+class _CStreamResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("first_shot", ctypes.c_int64), ("n_shots", ctypes.c_int64), ("trig_t", ctypes.c_void_p),
+                ("n_clusters", ctypes.c_int64), ("clusters", ctypes.c_void_p),
+                ("packets_processed", ctypes.c_int64), ("latency_us", ctypes.c_double)]
 
 
 class TpxError(RuntimeError):
@@ -125,6 +138,14 @@ def load(path: str | None = None):
         L.tpx_get_state.restype = i32
         L.tpx_summarize.argtypes = [vp, vp, i64, ctypes.POINTER(_CSummary)]
         L.tpx_summarize.restype = i32
+        L.tpx_stream_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_CStreamConfig), vp]
+        L.tpx_stream_submit.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+        L.tpx_stream_finish.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.tpx_stream_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(_CStreamResult), ctypes.c_int32]
+        L.tpx_stream_destroy.argtypes = [vp]
+        for f in ("tpx_stream_create", "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll",
+                  "tpx_stream_destroy"):
+            getattr(L, f).restype = i32
         L.tpx_decode.argtypes = [vp, vp, i64, i64, ctypes.POINTER(_CHits), i64, vp, vp, i64, vp]
         L.tpx_cluster.argtypes = [vp, ctypes.POINTER(_CHits), i64, vp, vp]
         L.tpx_centroid.argtypes = [vp, ctypes.POINTER(_CHits), vp, vp, i64, vp, i64, vp]
@@ -331,4 +352,67 @@ class Context:
         if rc:
             raise TpxError(rc, "tpx_centroid")
         return dict(clusters=cl, n_clusters=n_cl, cluster_capacity=cap)
+
+
+class Stream:
+    """tpx_stream: acquisition chunks in, records of closed shots out."""
+
+    def __init__(self, cfg: Config | None = None, max_chunk_packets: int = 1 << 20, max_hold_packets: int = 1 << 20,
+                 hold_triggers: int = 2, slots: int = 4, hbm_budget_bytes: int = 0, stream=None):
+        import torch
+        cfg = cfg or Config()
+        c = _CConfig(cfg.rx, cfg.ry, cfg.dt_ticks, cfg.mode, cfg.tof_max_ticks, cfg.wrap_thr_pix_ticks,
+                     cfg.wrap_thr_tdc_ticks, _ptr(cfg.timewalk_lut), int(cfg.strict), 0)
+        sc = _CStreamConfig(c, int(max_chunk_packets), int(max_hold_packets), int(hold_triggers), int(slots),
+                            int(hbm_budget_bytes))
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        rc = lib().tpx_stream_create(ctypes.byref(h), ctypes.byref(sc), ctypes.c_void_p(self.stream.cuda_stream))
+        if rc:
+            raise TpxError(rc, "tpx_stream_create")
+        self._h = h
+        self._keep = cfg
+
+    def submit(self, chunk: np.ndarray) -> int:
+        """Returns the ticket; raises TpxError (EAGAIN when all slots await poll)."""
+        chunk = np.ascontiguousarray(chunk, dtype=np.uint64)
+        t = ctypes.c_uint64()
+        rc = lib().tpx_stream_submit(self._h, chunk.ctypes.data if chunk.size else None, chunk.size, ctypes.byref(t))
+        if rc:
+            raise TpxError(rc, "tpx_stream_submit")
+        return t.value
+
+    def finish(self) -> int:
+        t = ctypes.c_uint64()
+        rc = lib().tpx_stream_finish(self._h, ctypes.byref(t))
+        if rc:
+            raise TpxError(rc, "tpx_stream_finish")
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1) -> dict:
+        r = _CStreamResult()
+        rc = lib().tpx_stream_poll(self._h, ticket, ctypes.byref(r), int(timeout_us))
+        if rc:
+            raise TpxError(rc, "tpx_stream_poll")
+        n = r.n_clusters
+        cl = np.zeros(0, CLUSTER_DTYPE)
+        if n:
+            buf = (ctypes.c_char * (n * CLUSTER_DTYPE.itemsize)).from_address(r.clusters)
+            cl = np.frombuffer(bytes(buf), CLUSTER_DTYPE).copy()
+        tr = np.zeros(0, np.int64)
+        if r.n_shots:
+            tr = np.array((ctypes.c_int64 * r.n_shots).from_address(r.trig_t), dtype=np.int64)
+        return dict(ticket=r.ticket, status=r.status, first_shot=r.first_shot, n_shots=r.n_shots, triggers=tr,
+                    clusters=cl, packets_processed=r.packets_processed, latency_us=r.latency_us)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tpx_stream_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

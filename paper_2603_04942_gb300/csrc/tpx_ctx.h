@@ -70,5 +70,8 @@ int reserve(tpx_ctx *c, size_t bytes);
 int redo_last(tpx_ctx *c);
 int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const tpx_hits &h, int64_t cap,
                 int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
-                const tpxk::GAgg *E0, tpxk::GAgg *state_out);
+                const tpxk::GAgg *E0, tpxk::GAgg *state_out, long long *trig_pos, long long **t_all_out);
+int cluster_impl(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8_t *is_peak);
+int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const uint8_t *is_peak, int64_t n,
+                  tpx_record *out, int64_t cap, int64_t *d_n_clusters);
 }  // namespace tpxg

@@ -129,7 +129,7 @@ __global__ void k_tile_prefix(const GAgg *tagg, GAgg *tpre, const long long *tcn
 
 __global__ void __launch_bounds__(GT) k_unwrap(const uint64_t *pk, long long n, const GAgg *tpre, const long long *toff,
                                                long long tp, long long tt, long long *t_all, long long *trig,
-                                               long long trig_cap, unsigned *status) {
+                                               long long trig_cap, unsigned *status, long long *trig_pos) {
     __shared__ GAgg s_w[GW];
     __shared__ GAgg s_tot;
     const long long tile = blockIdx.x, base = tile * GTILE;
@@ -166,7 +166,12 @@ __global__ void __launch_bounds__(GT) k_unwrap(const uint64_t *pk, long long n, 
             ht = true;
             lt = r;
             t = r + et * kTdcPeriod;
-            if (ti < trig_cap) trig[ti] = t; else atomicOr(status, ST_TRIG_CAP);
+            if (ti < trig_cap) {
+                trig[ti] = t;
+                if (trig_pos) trig_pos[ti] = q;
+            } else {
+                atomicOr(status, ST_TRIG_CAP);
+            }
             ++ti;
         }
         t_all[q] = t;
@@ -624,7 +629,7 @@ int sort_hits(tpx_ctx *c, Arena &a, const tpx_hits &h, long long n, unsigned **v
 
 int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const tpx_hits &h, int64_t cap,
                 int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
-                const GAgg *E0, GAgg *state_out) {
+                const GAgg *E0, GAgg *state_out, long long *trig_pos, long long **t_all_out) {
     cudaStream_t s = c->stream;
     const long long tiles = (n + GTILE - 1) / GTILE;
     const size_t need = sz(tiles, sizeof(GAgg)) * 2 + sz(tiles + 1, 8) * 4 + sz(n, 8) + 4096;
@@ -635,6 +640,7 @@ int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const t
     long long *tcnt = a.take<long long>(tiles + 1), *toff = a.take<long long>(tiles + 1);
     long long *tkept = a.take<long long>(tiles + 1), *tkoff = a.take<long long>(tiles + 1);
     long long *t_all = a.take<long long>(n);
+    if (t_all_out) *t_all_out = t_all;
     if (clear_ctl && cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), s) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_hits, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_n_trig, 0, 8, s) != cudaSuccess)
         return TPX_ECUDA;
@@ -648,7 +654,7 @@ int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const t
     k_tile_prefix<<<1, 1, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, reinterpret_cast<long long *>(d_n_trig),
                                   E0, state_out);
     k_unwrap<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tpre, toff, tp, tt, t_all, reinterpret_cast<long long *>(trig),
-                                            trig_cap, &c->ctl->status);
+                                            trig_cap, &c->ctl->status, trig_pos);
     long long ntr_h = 0;
     if (cudaMemcpyAsync(&ntr_h, d_n_trig, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
@@ -792,7 +798,7 @@ int redo_last(tpx_ctx *c) {
     unsigned char *hp = a.take<unsigned char>(n);
     long long *nh_d = a.take<long long>(1);
     int rc = decode_impl(c, L.pk, n, L.base, h, n, reinterpret_cast<int64_t *>(nh_d), L.trig, L.trig_cap, L.n_trig, true,
-                         L.E0, L.state_out);
+                         L.E0, L.state_out, nullptr, nullptr);
     long long nh = 0;
     if (!rc) rc = ck(cudaMemcpyAsync(&nh, nh_d, 8, cudaMemcpyDeviceToHost, s));
     if (!rc) rc = ck(cudaStreamSynchronize(s));
@@ -838,7 +844,8 @@ extern "C" int tpx_decode(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t bas
     const tpxk::GAgg *E0 = nullptr;
     tpxk::GAgg *out = nullptr;
     take_state(c, &E0, &out);
-    return tpxg::decode_impl(c, pk, n, base, *hits, cap, d_n_hits, trig, trig_cap, d_n_trig, true, E0, out);
+    return tpxg::decode_impl(c, pk, n, base, *hits, cap, d_n_hits, trig, trig_cap, d_n_trig, true, E0, out, nullptr,
+                             nullptr);
 }
 
 extern "C" int tpx_cluster(tpx_ctx *c, const tpx_hits *hits, int64_t n, int64_t *d_labels, uint8_t *d_is_peak) {

@@ -1,0 +1,439 @@
+// tpx_stream.cu -- streaming: acquisition chunks in, closed shots' records out.
+//
+// Per submit: the held (open) packets plus the new chunk are decoded by the
+// general path starting from the unwrap state at the held part's start
+// (device-resident); all shots but the last `hold_triggers` are closed and
+// emitted; the unwrap state at the first open shot's trigger packet is
+// computed on the device and the open part is moved to the front of the
+// other pending buffer for the next chunk.  Independent streams run on their
+// own CUDA streams, so chunks of different acquisitions overlap on the GPU.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "tpx.h"
+#include "tpx_common.cuh"
+#include "tpx_ctx.h"
+#include "tpx_fused.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+std::mutex g_budget_mu;
+int64_t g_budget_used = 0;
+
+struct Slot {
+    bool busy = false;
+    uint64_t ticket = 0;
+    cudaEvent_t done = nullptr;
+    tpx_record *h_cl = nullptr;
+    int64_t cap_cl = 0;
+    int64_t *h_trig = nullptr;
+    int64_t cap_trig = 0;
+    int64_t n_cl = 0, first_shot = 0, n_shots = 0, processed = 0;
+    int32_t status = 0;
+    Clock::time_point t_submit;
+};
+
+struct Probe {                      // k_state_at scratch
+    unsigned long long last_pix, last_tdc, n_pix, n_tdc;
+};
+
+}  // namespace
+
+struct tpx_stream {
+    tpx_stream_config cfg;
+    tpx_ctx *ctx = nullptr;
+    cudaStream_t s = nullptr;
+    uint64_t *pend[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t cap = 0;                // pending capacity (held + chunk)
+    int64_t held = 0;
+    int64_t index_base = 0;         // stream index of the first pending packet
+    int64_t trig_base = 0;          // global index of the first pending trigger
+    tpxk::GAgg *st[3] = {nullptr, nullptr, nullptr};   // state at pending start, scratch, next
+    tpx_hits h{}, he{};
+    void *dev_mem = nullptr;
+    int64_t *d_counts = nullptr;    // n_hits, n_trig, n_cl, n_emit
+    int64_t *d_trig = nullptr, *d_trig_pos = nullptr, *d_labels = nullptr;
+    uint8_t *d_peak = nullptr;
+    tpx_record *d_cl = nullptr;
+    unsigned *d_flags = nullptr, *d_offs = nullptr, *d_bsum = nullptr;
+    Probe *d_probe = nullptr;
+    std::vector<Slot> slots;
+    uint64_t next_ticket = 1;
+    int64_t bytes = 0;
+    bool finished = false;
+};
+
+namespace tpxs {
+
+using namespace tpxk;
+constexpr int BT = 256;
+
+__global__ void k_probe(const uint64_t *pk, long long p, Probe *pr) {
+    unsigned long long lp = 0, lt = 0, np = 0, nt = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < p; q += (long long)gridDim.x * blockDim.x) {
+        const unsigned h = (unsigned)(pk[q] >> 60);
+        if (h == 0xBu) { lp = max(lp, (unsigned long long)q + 1); ++np; }
+        else if (h == 0x6u) { lt = max(lt, (unsigned long long)q + 1); ++nt; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lp = max(lp, __shfl_down_sync(0xffffffffu, lp, o));
+        lt = max(lt, __shfl_down_sync(0xffffffffu, lt, o));
+        np += __shfl_down_sync(0xffffffffu, np, o);
+        nt += __shfl_down_sync(0xffffffffu, nt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lp) atomicMax(&pr->last_pix, lp);
+        if (lt) atomicMax(&pr->last_tdc, lt);
+        if (np) atomicAdd(&pr->n_pix, np);
+        if (nt) atomicAdd(&pr->n_tdc, nt);
+    }
+}
+
+// unwrap state before position p of the pending buffer (t_all from the decode)
+__global__ void k_state_at(const uint64_t *pk, const long long *t_all, const Probe *pr, const GAgg *E0, GAgg *out) {
+    GAgg g = *E0;
+    if (pr->last_pix) {
+        const long long q = (long long)pr->last_pix - 1;
+        const long long raw = pix_raw(pk[q]);
+        g.pix.n += (long long)pr->n_pix;
+        g.pix.last = raw;
+        g.pix.first = raw;
+        g.pix.sum = (t_all[q] - raw) / kPixPeriod;
+    }
+    if (pr->last_tdc) {
+        const long long q = (long long)pr->last_tdc - 1;
+        const long long raw = tdc_raw(pk[q]);
+        g.tdc.n += (long long)pr->n_tdc;
+        g.tdc.last = raw;
+        g.tdc.first = raw;
+        g.tdc.sum = (t_all[q] - raw) / kTdcPeriod;
+    }
+    *out = g;
+}
+
+__global__ void k_emit_flags(tpx_hits h, long long n, long long limit, unsigned *flags) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        flags[i] = h.shot[i] < limit;
+}
+__global__ void k_scan_blocks(const unsigned *in, unsigned *out, long long n, unsigned *bsum) {
+    // one block of 256 threads scans 4096 values (16 per thread)
+    __shared__ unsigned ws[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long base = blockIdx.x * 4096LL + threadIdx.x * 16;
+    unsigned mine = 0;
+    for (int j = 0; j < 16; ++j)
+        if (base + j < n) mine += in[base + j];
+    unsigned incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned x = lane < 8 ? ws[lane] : 0, xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += u;
+        }
+        if (lane < 8) ws[lane] = xi - x;
+        if (lane == 7) bsum[blockIdx.x] = xi;
+    }
+    __syncthreads();
+    unsigned o = ws[w] + incl - mine;
+    for (int j = 0; j < 16; ++j)
+        if (base + j < n) { out[base + j] = o; o += in[base + j]; }
+}
+__global__ void k_scan_bsum(unsigned *bsum, long long nb, long long *total) {
+    unsigned acc = 0;
+    for (long long b = 0; b < nb; ++b) { const unsigned v = bsum[b]; bsum[b] = acc; acc += v; }
+    *total = acc;
+}
+__global__ void k_emit_copy(tpx_hits h, long long n, const unsigned *flags, const unsigned *offs, const unsigned *bsum,
+                            tpx_hits e) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!flags[i]) continue;
+        const long long o = (long long)offs[i] + bsum[i / 4096];
+        e.index[o] = h.index[i];
+        e.shot[o] = h.shot[i];
+        e.t[o] = h.t[i];
+        e.tof[o] = h.tof[i];
+        e.x[o] = h.x[i];
+        e.y[o] = h.y[i];
+        e.tot[o] = h.tot[i];
+    }
+}
+
+inline unsigned gridn(long long n) {
+    long long g = (n + BT - 1) / BT;
+    if (g < 1) g = 1;
+    if (g > 152 * 8) g = 152 * 8;
+    return (unsigned)g;
+}
+inline size_t al(size_t b) { return (b + 255) & ~size_t(255); }
+
+int grow_pinned(Slot &sl, int64_t ncl, int64_t ntr) {
+    if (ncl > sl.cap_cl) {
+        if (sl.h_cl) cudaFreeHost(sl.h_cl);
+        sl.h_cl = nullptr;
+        sl.cap_cl = 0;
+        if (cudaMallocHost(&sl.h_cl, sizeof(tpx_record) * (size_t)ncl) != cudaSuccess) return TPX_ENOMEM;
+        sl.cap_cl = ncl;
+    }
+    if (ntr > sl.cap_trig) {
+        if (sl.h_trig) cudaFreeHost(sl.h_trig);
+        sl.h_trig = nullptr;
+        sl.cap_trig = 0;
+        if (cudaMallocHost(&sl.h_trig, sizeof(int64_t) * (size_t)ntr) != cudaSuccess) return TPX_ENOMEM;
+        sl.cap_trig = ntr;
+    }
+    return TPX_OK;
+}
+
+int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, uint64_t *ticket) {
+    Slot *sl = nullptr;
+    for (auto &x : S->slots)
+        if (!x.busy) { sl = &x; break; }
+    if (!sl) return TPX_EAGAIN;
+    const auto t0 = Clock::now();
+    cudaStream_t s = S->s;
+    tpx_ctx *c = S->ctx;
+    int rc = TPX_OK;
+    const int64_t P = S->held + n;
+    if (P > S->cap) return TPX_EOVERFLOW;
+    uint64_t *pk = S->pend[S->cur];
+    if (n > 0 && cudaMemcpyAsync(pk + S->held, h_chunk, sizeof(uint64_t) * (size_t)n, cudaMemcpyHostToDevice, s) !=
+                     cudaSuccess)
+        return TPX_ECUDA;
+    long long *t_all = nullptr;
+    rc = tpxg::decode_impl(c, pk, P, S->index_base, S->h, S->cap, S->d_counts, S->d_trig, S->cap, S->d_counts + 1,
+                           true, S->st[0], S->st[1], reinterpret_cast<long long *>(S->d_trig_pos), &t_all);
+    if (rc) return rc;
+    int64_t cnt[2] = {0, 0};
+    unsigned status = 0;
+    if (cudaMemcpyAsync(cnt, S->d_counts, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+    if (cudaMemcpyAsync(&status, &c->ctl->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    const int64_t n_hits = cnt[0], ntr = cnt[1];
+    if (status & ST_TRIG_ORDER) return TPX_ECORRUPT;
+    const int64_t hold = S->cfg.hold_triggers;
+    const int64_t emit = finishing ? ntr : (ntr > hold ? ntr - hold : 0);
+    // where the open part starts: the trigger packet of the first open shot
+    int64_t p = 0;
+    if (emit >= ntr && finishing) p = P;
+    else if (emit > 0) {
+        if (cudaMemcpyAsync(&p, S->d_trig_pos + emit, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    }
+    // unwrap state at p (before the decode scratch is reused)
+    if (p == P) {
+        if (cudaMemcpyAsync(S->st[2], S->st[1], sizeof(GAgg), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TPX_ECUDA;
+    } else if (p > 0) {
+        if (cudaMemsetAsync(S->d_probe, 0, sizeof(Probe), s) != cudaSuccess) return TPX_ECUDA;
+        k_probe<<<gridn(p), BT, 0, s>>>(pk, p, S->d_probe);
+        k_state_at<<<1, 1, 0, s>>>(pk, t_all, S->d_probe, S->st[0], S->st[2]);
+    } else {
+        if (cudaMemcpyAsync(S->st[2], S->st[0], sizeof(GAgg), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TPX_ECUDA;
+    }
+    // emitted shots: hits with shot < trig_base + emit, clustered and centroided
+    int64_t n_emit = 0, n_cl = 0;
+    if (emit > 0 && n_hits > 0) {
+        const long long limit = S->trig_base + emit;
+        k_emit_flags<<<gridn(n_hits), BT, 0, s>>>(S->h, n_hits, limit, S->d_flags);
+        const long long nb = (n_hits + 4095) / 4096;
+        k_scan_blocks<<<(unsigned)nb, 256, 0, s>>>(S->d_flags, S->d_offs, n_hits, S->d_bsum);
+        k_scan_bsum<<<1, 1, 0, s>>>(S->d_bsum, nb, reinterpret_cast<long long *>(S->d_counts + 3));
+        k_emit_copy<<<gridn(n_hits), BT, 0, s>>>(S->h, n_hits, S->d_flags, S->d_offs, S->d_bsum, S->he);
+        if (cudaMemcpyAsync(&n_emit, S->d_counts + 3, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        if (n_emit > 0) {
+            rc = tpxg::cluster_impl(c, S->he, n_emit, S->d_labels, S->d_peak);
+            if (rc) return rc;
+            rc = tpxg::centroid_impl(c, S->he, S->d_labels, S->d_peak, n_emit, S->d_cl, n_emit, S->d_counts + 2);
+            if (rc) return rc;
+            if (cudaMemcpyAsync(&n_cl, S->d_counts + 2, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        }
+    }
+    rc = grow_pinned(*sl, n_cl > 0 ? n_cl : 1, emit > 0 ? emit : 1);
+    if (rc) return rc;
+    if (n_cl > 0 && cudaMemcpyAsync(sl->h_cl, S->d_cl, sizeof(tpx_record) * (size_t)n_cl, cudaMemcpyDeviceToHost, s) !=
+                        cudaSuccess)
+        return TPX_ECUDA;
+    if (emit > 0 && cudaMemcpyAsync(sl->h_trig, S->d_trig, sizeof(int64_t) * (size_t)emit, cudaMemcpyDeviceToHost, s) !=
+                        cudaSuccess)
+        return TPX_ECUDA;
+    // move the open part to the front of the other pending buffer
+    const int64_t rest = P - p;
+    if (rest > S->cfg.max_hold_packets && !finishing) return TPX_EOVERFLOW;
+    if (rest > 0 && cudaMemcpyAsync(S->pend[S->cur ^ 1], pk + p, sizeof(uint64_t) * (size_t)rest,
+                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return TPX_ECUDA;
+    tpxk::GAgg *t = S->st[0];
+    S->st[0] = S->st[2];
+    S->st[2] = t;
+    S->cur ^= 1;
+    S->held = rest;
+    S->index_base += p;
+    sl->first_shot = S->trig_base;
+    sl->n_shots = emit;
+    S->trig_base += emit;
+    sl->n_cl = n_cl;
+    sl->processed = P;
+    sl->status = 0;
+    sl->t_submit = t0;
+    sl->ticket = S->next_ticket++;
+    sl->busy = true;
+    if (cudaEventRecord(sl->done, s) != cudaSuccess) return TPX_ECUDA;
+    *ticket = sl->ticket;
+    return TPX_OK;
+}
+
+}  // namespace tpxs
+
+extern "C" {
+
+using tpxs::al;
+
+int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda_stream) {
+    if (!out || !cfg) return TPX_EINVAL;
+    *out = nullptr;
+    if (cfg->max_chunk_packets <= 0 || cfg->max_hold_packets < 0 || cfg->hold_triggers < 1 || cfg->slots < 1)
+        return TPX_EINVAL;
+    tpx_stream *S = new (std::nothrow) tpx_stream;
+    if (!S) return TPX_ENOMEM;
+    S->cfg = *cfg;
+    S->cfg.cfg.chain = 0;
+    S->s = static_cast<cudaStream_t>(cuda_stream);
+    S->cap = cfg->max_chunk_packets + cfg->max_hold_packets;
+    const int64_t C = S->cap;
+    // device memory: pending x2, hits x2, per-hit outputs, records, triggers,
+    // scan scratch, states; plus the general path's scratch in the context
+    const size_t hit_b = al(8 * C) * 3 + al(4 * C) + al(2 * C) + 2 * al(C);
+    const size_t b = 2 * al(8 * (size_t)C) + 2 * hit_b + al(8 * C) + al(C) + al(sizeof(tpx_record) * C) +
+                     2 * al(8 * C) + 2 * al(4 * C) + al(4 * (C / 4096 + 2)) + 3 * al(sizeof(tpxk::GAgg)) +
+                     al(sizeof(Probe)) + al(64);
+    const size_t general = (size_t)C * 110;   // decode / sort / cluster / centroid scratch
+    S->bytes = (int64_t)(b + general);
+    {
+        std::lock_guard<std::mutex> lk(g_budget_mu);
+        if (cfg->hbm_budget_bytes > 0 && g_budget_used + S->bytes > cfg->hbm_budget_bytes) {
+            delete S;
+            return TPX_EAGAIN;
+        }
+        g_budget_used += S->bytes;
+    }
+    int rc = tpx_create(&S->ctx, &S->cfg.cfg, 0, cuda_stream);
+    if (!rc) rc = tpxg::reserve(S->ctx, general);
+    if (!rc && cudaMalloc(&S->dev_mem, b) != cudaSuccess) { cudaGetLastError(); rc = TPX_ENOMEM; }
+    if (rc) {
+        if (S->ctx) tpx_destroy(S->ctx);
+        std::lock_guard<std::mutex> lk(g_budget_mu);
+        g_budget_used -= S->bytes;
+        delete S;
+        return rc;
+    }
+    char *m = static_cast<char *>(S->dev_mem);
+    auto take = [&](size_t bytes) { char *r = m; m += al(bytes); return r; };
+    S->pend[0] = reinterpret_cast<uint64_t *>(take(8 * C));
+    S->pend[1] = reinterpret_cast<uint64_t *>(take(8 * C));
+    for (tpx_hits *hh : {&S->h, &S->he}) {
+        hh->index = reinterpret_cast<int64_t *>(take(8 * C));
+        hh->shot = reinterpret_cast<int64_t *>(take(8 * C));
+        hh->t = reinterpret_cast<int64_t *>(take(8 * C));
+        hh->tof = reinterpret_cast<int32_t *>(take(4 * C));
+        hh->tot = reinterpret_cast<uint16_t *>(take(2 * C));
+        hh->x = reinterpret_cast<uint8_t *>(take(C));
+        hh->y = reinterpret_cast<uint8_t *>(take(C));
+    }
+    S->d_labels = reinterpret_cast<int64_t *>(take(8 * C));
+    S->d_peak = reinterpret_cast<uint8_t *>(take(C));
+    S->d_cl = reinterpret_cast<tpx_record *>(take(sizeof(tpx_record) * C));
+    S->d_trig = reinterpret_cast<int64_t *>(take(8 * C));
+    S->d_trig_pos = reinterpret_cast<int64_t *>(take(8 * C));
+    S->d_flags = reinterpret_cast<unsigned *>(take(4 * C));
+    S->d_offs = reinterpret_cast<unsigned *>(take(4 * C));
+    S->d_bsum = reinterpret_cast<unsigned *>(take(4 * (C / 4096 + 2)));
+    for (int i = 0; i < 3; ++i) S->st[i] = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg)));
+    S->d_probe = reinterpret_cast<Probe *>(take(sizeof(Probe)));
+    S->d_counts = reinterpret_cast<int64_t *>(take(64));
+    cudaMemsetAsync(S->st[0], 0, sizeof(tpxk::GAgg), S->s);
+    S->slots.resize((size_t)cfg->slots);
+    for (auto &sl : S->slots)
+        if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            tpx_stream_destroy(S);
+            return TPX_ECUDA;
+        }
+    *out = S;
+    return TPX_OK;
+}
+
+int tpx_stream_submit(tpx_stream *S, const uint64_t *h_chunk, int64_t n, uint64_t *ticket) {
+    if (!S || !ticket || n < 0 || (n > 0 && !h_chunk) || n > S->cfg.max_chunk_packets || S->finished) return TPX_EINVAL;
+    return tpxs::process(S, h_chunk, n, false, ticket);
+}
+
+int tpx_stream_finish(tpx_stream *S, uint64_t *ticket) {
+    if (!S || !ticket || S->finished) return TPX_EINVAL;
+    const int rc = tpxs::process(S, nullptr, 0, true, ticket);
+    if (!rc) S->finished = true;
+    return rc;
+}
+
+int tpx_stream_poll(tpx_stream *S, uint64_t ticket, tpx_stream_result *out, int32_t timeout_us) {
+    if (!S || !out) return TPX_EINVAL;
+    Slot *sl = nullptr;
+    for (auto &x : S->slots)
+        if (x.busy && x.ticket == ticket) { sl = &x; break; }
+    if (!sl) return TPX_EINVAL;
+    const auto start = Clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(sl->done);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return TPX_ECUDA;
+        if (timeout_us >= 0 &&
+            std::chrono::duration_cast<std::chrono::microseconds>(Clock::now() - start).count() >= timeout_us)
+            return TPX_ETIMEOUT;
+    }
+    out->ticket = ticket;
+    out->status = sl->status;
+    out->reserved = 0;
+    out->first_shot = sl->first_shot;
+    out->n_shots = sl->n_shots;
+    out->trig_t = sl->h_trig;
+    out->n_clusters = sl->n_cl;
+    out->clusters = sl->h_cl;
+    out->packets_processed = sl->processed;
+    out->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - sl->t_submit).count();
+    sl->busy = false;
+    return TPX_OK;
+}
+
+int tpx_stream_destroy(tpx_stream *S) {
+    if (!S) return TPX_EINVAL;
+    if (S->s) cudaStreamSynchronize(S->s);
+    for (auto &sl : S->slots) {
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.h_cl) cudaFreeHost(sl.h_cl);
+        if (sl.h_trig) cudaFreeHost(sl.h_trig);
+    }
+    if (S->dev_mem) cudaFree(S->dev_mem);
+    if (S->ctx) tpx_destroy(S->ctx);
+    {
+        std::lock_guard<std::mutex> lk(g_budget_mu);
+        g_budget_used -= S->bytes;
+    }
+    delete S;
+    return TPX_OK;
+}
+
+}  // extern "C"

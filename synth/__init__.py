@@ -94,6 +94,18 @@ def large(**kw) -> Params:
                   pair_frac=0.05).replace(**kw)
 
 
+def streaming(rate_hits_per_s: float, n_shots: int, **kw) -> Params:
+    """Continuous ion-like stream: Poisson particles at `rate_hits_per_s`
+    pixel hits per second (sigma 1.2 px, ~36 px per particle), ToF uniform
+    over the whole 1 ms trigger period, seed 3. Pixels of a shot can be read
+    out after the next trigger."""
+    return Params(n_shots=n_shots, seed=3, poisson=True, particles_per_shot=rate_hits_per_s * 1e-3 / 36.0,
+                  sigma_px=1.2, tof_lo_ns=0.0, tof_hi_ns=999_999.0).replace(**kw)
+
+
+STREAM_TOF_MAX_TICKS = 639_999      # the ToF cut of the streaming workload: the whole period
+
+
 def stated_size(p: Params) -> Params:
     """Variant whose truncation (ToT >= 90) gives the 5-15 px per particle
     that the workload description quotes; the literal parameters give ~25."""

@@ -189,7 +189,7 @@ static int cmp_key(const void *a, const void *b) {
 }
 
 /* dark counts of trigger window k: uniform ToA over the period, random pixel */
-static void gen_dark(worker_t *w, const synth_params *p, int64_t k, int32_t tag, int64_t t_trig) {
+static void gen_dark(worker_t *w, const synth_params *p, int64_t k, int64_t t_trig) {
     if (p->dark_per_shot <= 0) return;
     rng_t r; rng_seed(&r, p->seed, (uint64_t)k, 7);
     int64_t nd = rng_poisson(&r, p->dark_per_shot);
@@ -202,26 +202,28 @@ static void gen_dark(worker_t *w, const synth_params *p, int64_t k, int32_t tag,
         hit_t *n = &w->h[w->n_h];
         n->q = q; n->amp = tot; n->tot = tot; n->toa = toa; n->readout = ro; n->order = -1;
         w->n_h++;
-        (void)tag;
     }
 }
 
-static void gen_shot(worker_t *w, const synth_params *p, int64_t k) {
+/* all hits of shot k (its particles, its dark counts), appended to w->h with
+   their readout times; the particles are recorded as truth if asked */
+static void gen_hits(worker_t *w, const synth_params *p, int64_t k, int truth, int particles) {
     const int64_t t_trig = p->t_start_ticks + k * p->trig_period_ticks;
-    const int64_t t_next = t_trig + p->trig_period_ticks;
-    const int32_t tag = (int32_t)(k & 0x7FFFFFFF) + 1;
+    const int32_t tag = (int32_t)(k & 0x3FFFFFFF) * 2 + 1 + (truth ? 0 : 1);
     rng_t r; rng_seed(&r, p->seed, (uint64_t)k, 0);
-    w->n_h = 0;
+    const int64_t h0 = w->n_h;
     int64_t np = p->poisson ? rng_poisson(&r, p->particles_per_shot) : (int64_t)p->particles_per_shot;
     const double tick = 1.5625;
-    for (int64_t i = 0; i < np; i++) {
+    for (int64_t i = 0; i < np && particles; i++) {
         double cx = rng_uniform(&r, 0.0, 256.0), cy = rng_uniform(&r, 0.0, 256.0);
         double peak = rng_uniform(&r, p->peak_lo, p->peak_hi);
         double tof = rng_uniform(&r, p->tof_lo_ns, p->tof_hi_ns);
         double t0 = (double)t_trig + tof / tick;
         int pair = p->pair_frac > 0 && rng_u01(&r) < p->pair_frac;
-        GROW(w->pt, w->n_pt, w->cap_pt, part_t);
-        w->pt[w->n_pt++] = (part_t){k, cx, cy, t0, peak, pair ? 1 : 0};
+        if (truth) {
+            GROW(w->pt, w->n_pt, w->cap_pt, part_t);
+            w->pt[w->n_pt++] = (part_t){k, cx, cy, t0, peak, pair ? 1 : 0};
+        }
         emit_cloud(w, p, &r, tag, cx, cy, peak, t0);
         if (pair) {
             double sep = rng_uniform(&r, p->pair_sep_lo, p->pair_sep_hi);
@@ -229,13 +231,15 @@ static void gen_shot(worker_t *w, const synth_params *p, int64_t k) {
             double dt = rng_uniform(&r, p->pair_dtoa_lo_ns, p->pair_dtoa_hi_ns) / tick;
             double ratio = rng_uniform(&r, p->pair_amp_lo, p->pair_amp_hi);
             double cx2 = cx + sep * cos(ang), cy2 = cy + sep * sin(ang);
-            GROW(w->pt, w->n_pt, w->cap_pt, part_t);
-            w->pt[w->n_pt++] = (part_t){k, cx2, cy2, t0 + dt, peak * ratio, 2};
+            if (truth) {
+                GROW(w->pt, w->n_pt, w->cap_pt, part_t);
+                w->pt[w->n_pt++] = (part_t){k, cx2, cy2, t0 + dt, peak * ratio, 2};
+            }
             emit_cloud(w, p, &r, tag, cx2, cy2, peak * ratio, t0 + dt);
         }
     }
     /* finalise particle hits: ToT, optional timewalk delay, readout time */
-    for (int64_t i = 0; i < w->n_h; i++) {
+    for (int64_t i = h0; i < w->n_h; i++) {
         hit_t *h = &w->h[i];
         int tot = (int)floor(h->amp);
         if (tot > 1023) tot = 1023;
@@ -244,21 +248,35 @@ static void gen_shot(worker_t *w, const synth_params *p, int64_t k) {
             h->toa += (int64_t)llround((p->timewalk_a / ((double)tot + p->timewalk_b) + p->timewalk_c) / tick);
         h->readout = h->toa + 16 * (int64_t)tot + (int64_t)(rng_next(&r) % (uint64_t)(p->readout_jitter_ticks + 1));
     }
-    /* dark counts: this window's that read out before the next trigger, plus
-       the previous window's that read out after this trigger */
-    int64_t keep_from = w->n_h;
-    gen_dark(w, p, k, tag, t_trig);
-    int64_t j = keep_from;
-    for (int64_t i = keep_from; i < w->n_h; i++)
-        if (w->h[i].readout < t_next || k + 1 == p->shot_end) w->h[j++] = w->h[i];
+    gen_dark(w, p, k, t_trig);
+}
+
+/* Trigger window k of the stream: its TDC packet, then -- in readout order --
+   the hits of shot k read out before trigger k+1 and the hits of shot k-1
+   read out after trigger k. */
+static void gen_shot(worker_t *w, const synth_params *p, int64_t k) {
+    const int64_t t_trig = p->t_start_ticks + k * p->trig_period_ticks;
+    const int64_t t_next = t_trig + p->trig_period_ticks;
+    const int last = k + 1 == p->shot_end;
+    w->n_h = 0;
+    gen_hits(w, p, k, 1, 1);
+    int64_t j = 0;
+    for (int64_t i = 0; i < w->n_h; i++)
+        if (w->h[i].readout < t_next || last) w->h[j++] = w->h[i];
     w->n_h = j;
     if (k > 0) {
-        keep_from = w->n_h;
-        gen_dark(w, p, k - 1, tag, t_trig - p->trig_period_ticks);
-        j = keep_from;
-        for (int64_t i = keep_from; i < w->n_h; i++)
-            if (w->h[i].readout >= t_trig) w->h[j++] = w->h[i];
-        w->n_h = j;
+        /* particles of shot k-1 can only be late when their ToF plus the
+           longest readout delay reaches the next trigger */
+        const double max_delay = 16.0 * 1023 + (double)p->readout_jitter_ticks + 8.0 * p->jitter_ns / 1.5625;
+        const int late_particles = p->tof_hi_ns / 1.5625 + max_delay >= (double)p->trig_period_ticks;
+        if (late_particles || p->dark_per_shot > 0) {
+            int64_t keep_from = w->n_h;
+            gen_hits(w, p, k - 1, 0, late_particles);
+            j = keep_from;
+            for (int64_t i = keep_from; i < w->n_h; i++)
+                if (w->h[i].readout >= t_trig) w->h[j++] = w->h[i];
+            w->n_h = j;
+        }
     }
     /* readout order: by readout time, ties by generation order */
     GROW(w->rank_key, w->n_h, w->cap_rk, int64_t);
