@@ -72,6 +72,13 @@ int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const t
                 int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
                 const tpxk::GAgg *E0, tpxk::GAgg *state_out, long long *trig_pos, long long **t_all_out);
 int cluster_impl(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8_t *is_peak);
+// sort + cluster + (when out != NULL) records of the hits with shot < shot_limit;
+// shot_span >= 0 bounds max - min shot of the hits (skips a host round trip)
+int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8_t *is_peak, long long shot_limit,
+                long long shot_span, tpx_record *out, int64_t cap, int64_t *d_n_clusters);
+// general-path scratch for n packets (decode) and n hits (cluster_all)
+size_t decode_bytes(long long n);
+size_t cluster_bytes(long long n);
 int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const uint8_t *is_peak, int64_t n,
                   tpx_record *out, int64_t cap, int64_t *d_n_clusters);
 }  // namespace tpxg

@@ -1,23 +1,26 @@
 // tpx_general.cu -- the general (global-memory) path: tpx_decode,
-// tpx_cluster, tpx_centroid, and the exact redo of a tpx_process call whose
-// input the fused kernel cannot hold on chip.
+// tpx_cluster, tpx_centroid, the exact redo of a tpx_process call whose
+// input the fused kernel cannot hold on chip, and the streaming calls.
 //
-// decode  : tile aggregates of the two unwrap chains (Sec. IV.A) -> serial
-//           prefix over tiles -> per-packet unwrapped times and the trigger
-//           list -> each pixel binned to the most recent trigger in time by
-//           binary search, cut at tof_max (Sec. IV.B), timewalk table
-//           subtracted (Sec. IV.C) -> kept pixels compacted in stream order.
+// decode  : tile aggregates of the two unwrap chains (Sec. IV.A) -> prefix
+//           over tiles -> per-packet unwrapped times and the trigger list ->
+//           each pixel binned to the most recent trigger in time by binary
+//           search, cut at tof_max (Sec. IV.B), timewalk table subtracted
+//           (Sec. IV.C) -> kept pixels compacted in stream order.
 // cluster : stable LSD radix sort of the hits on (shot, corrected ToF) --
-//           ties keep stream order -- then, for every hit, a forward scan of
-//           the hits within dt in that order; adjacent pairs (Sec. V.A box
-//           rule) set the local-maximum flags (Sec. V.B) and are joined by a
-//           lock-free union-find whose root is the smallest sorted position,
-//           i.e. the earliest hit of the cluster.
-// centroid: cluster ids in ascending label order, exact int64 moments by
-//           global atomics, f64 final division (Sec. V.C); PAPER mode sums the
+//           ties keep stream order. In that order a gap larger than dt ends
+//           every cluster, so the sorted hits split into independent
+//           segments; one warp clusters a segment in shared memory: each hit
+//           scans forward within dt, adjacent pairs (Sec. V.A box rule) set
+//           the local-maximum flags (Sec. V.B) and are joined by a lock-free
+//           union-find whose root is the smallest position, i.e. the
+//           earliest hit; the root's int64 moments are summed on the spot.
+//           Segments longer than a warp's buffer take the same steps in
+//           global memory.
+// centroid: cluster ids in ascending label order (a scan over root flags in
+//           stream order), f64 final division (Sec. V.C); PAPER mode sums the
 //           box neighbourhood of each local maximum.
-// Nothing here is on the benchmark path; it trades speed for having no
-// capacity limit besides 2^31 - 1 kept pixels per call.
+// No capacity limit besides 2^31 - 1 kept pixels per call.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -88,6 +91,58 @@ __device__ long long block_scan_ll(long long v, long long *s_w, long long *total
     return r;
 }
 
+// single-block scans (PT threads, each over a contiguous strip of items)
+constexpr int PT = 1024;
+__device__ long long block_excl_ll_pt(long long v, long long *s32, long long *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s32[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const long long x = s32[lane];
+        long long xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += u;
+        }
+        s32[lane] = xi - x;
+        if (lane == 31) *total = xi;
+    }
+    __syncthreads();
+    const long long r = s32[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+__device__ GAgg block_excl_agg_pt(const GAgg &v, GAgg *s32, long long tp, long long tt) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const GAgg incl = warp_incl_scan(v, lane, tp, tt);
+    GAgg lex = shfl_up_agg(incl, 1);
+    if (lane == 0) lex = agg_id();
+    if (lane == 31) s32[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const GAgg xi = warp_incl_scan(s32[lane], lane, tp, tt);
+        GAgg xe = shfl_up_agg(xi, 1);
+        if (lane == 0) xe = agg_id();
+        s32[lane] = xe;
+    }
+    __syncthreads();
+    const GAgg r = acomb(s32[w], lex, tp, tt);
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ void strip_of(long long items, long long *b, long long *e) {
+    const long long per = (items + PT - 1) / PT;
+    *b = min(items, (long long)threadIdx.x * per);
+    *e = min(items, *b + per);
+}
+
 // ------------------------------------------------------------ decode kernels
 __global__ void __launch_bounds__(GT) k_tile_agg(const uint64_t *pk, long long n, long long tp, long long tt,
                                                  GAgg *tagg, long long *tcnt) {
@@ -111,20 +166,36 @@ __global__ void __launch_bounds__(GT) k_tile_agg(const uint64_t *pk, long long n
     }
 }
 
-// exclusive prefix over tiles (one thread: this path is not on the benchmark)
-__global__ void k_tile_prefix(const GAgg *tagg, GAgg *tpre, const long long *tcnt, long long *toff, long long tiles,
-                              long long tp, long long tt, long long *n_trig_out, const GAgg *E0, GAgg *state_out) {
-    GAgg acc = E0 ? *E0 : agg_id();
-    long long off = 0;
-    for (long long t = 0; t < tiles; ++t) {
+// exclusive prefix over tiles, starting from the state before the call (one
+// block: strips of tiles, a block scan of the strip aggregates, then strips)
+__global__ void __launch_bounds__(PT) k_tile_prefix(const GAgg *tagg, GAgg *tpre, const long long *tcnt, long long *toff,
+                                                    long long tiles, long long tp, long long tt, long long *n_trig_out,
+                                                    const GAgg *E0, GAgg *state_out) {
+    __shared__ GAgg s_a[32];
+    __shared__ long long s_c[32];
+    __shared__ long long s_tot;
+    long long b, e;
+    strip_of(tiles, &b, &e);
+    GAgg a = agg_id();
+    long long cn = 0;
+    for (long long t = b; t < e; ++t) {
+        a = acomb(a, tagg[t], tp, tt);
+        cn += tcnt[t];
+    }
+    const GAgg ex = block_excl_agg_pt(a, s_a, tp, tt);
+    long long off = block_excl_ll_pt(cn, s_c, &s_tot);
+    GAgg acc = acomb(E0 ? *E0 : agg_id(), ex, tp, tt);
+    for (long long t = b; t < e; ++t) {
         tpre[t] = acc;
         toff[t] = off;
         acc = acomb(acc, tagg[t], tp, tt);
         off += tcnt[t];
     }
-    toff[tiles] = off;
-    *n_trig_out = off;
-    if (state_out) *state_out = acc;
+    if (threadIdx.x == PT - 1) {   // its strip is the last (possibly empty) one
+        toff[tiles] = off;
+        *n_trig_out = off;
+        if (state_out) *state_out = acc;
+    }
 }
 
 __global__ void __launch_bounds__(GT) k_unwrap(const uint64_t *pk, long long n, const GAgg *tpre, const long long *toff,
@@ -178,7 +249,15 @@ __global__ void __launch_bounds__(GT) k_unwrap(const uint64_t *pk, long long n, 
     }
 }
 
-__global__ void k_check_trig(const long long *trig, long long ntr, unsigned *status) {
+// the trigger count of the call, or -1 when it exceeded the trigger capacity
+// (the status is latched and nothing is binned)
+__device__ __forceinline__ long long usable_triggers(const long long *n_trig, long long trig_cap) {
+    const long long v = *n_trig;
+    return v > trig_cap ? -1 : v;
+}
+
+__global__ void k_check_trig(const long long *trig, const long long *n_trig, long long trig_cap, unsigned *status) {
+    const long long ntr = usable_triggers(n_trig, trig_cap);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i + 1 < ntr; i += (long long)gridDim.x * blockDim.x)
         if (trig[i + 1] < trig[i]) atomicOr(status, ST_TRIG_ORDER);
 }
@@ -206,15 +285,17 @@ __device__ __forceinline__ int bin_pixel(uint64_t w, long long t, const long lon
     return 0;
 }
 
+// per tile: kept pixels and the drop counters (packets read warp-strided)
 __global__ void __launch_bounds__(GT) k_bin(const uint64_t *pk, long long n, const long long *t_all, const long long *trig,
-                                            long long ntr, long long tof_max, long long *tile_kept,
-                                            unsigned long long *counters) {
+                                            const long long *n_trig, long long trig_cap, long long tof_max,
+                                            long long *tile_kept, unsigned long long *counters) {
     __shared__ long long s_w[GW];
     __shared__ long long s_tot;
-    const long long tile = blockIdx.x, q0 = tile * GTILE + threadIdx.x * GK;
+    const long long tile = blockIdx.x, base = tile * GTILE;
+    const long long ntr = usable_triggers(n_trig, trig_cap);
     long long keep = 0, bg = 0, pre = 0, pix = 0, tdc = 0, bad = 0;
-    for (int j = 0; j < GK; ++j) {
-        const long long q = q0 + j;
+    for (int j = 0; j < GK && ntr >= 0; ++j) {
+        const long long q = base + j * GT + threadIdx.x;
         if (q >= n) break;
         const uint64_t w = pk[q];
         const unsigned h = (unsigned)(w >> 60);
@@ -238,52 +319,77 @@ __global__ void __launch_bounds__(GT) k_bin(const uint64_t *pk, long long n, con
     if (threadIdx.x == 0) tile_kept[tile] = s_tot;
 }
 
-__global__ void k_serial_prefix(const long long *cnt, long long *off, long long tiles, long long *total_out) {
-    long long acc = 0;
-    for (long long t = 0; t < tiles; ++t) {
-        off[t] = acc;
-        acc += cnt[t];
+// exclusive prefix of per-tile counts (one block)
+__global__ void __launch_bounds__(PT) k_count_prefix(const long long *cnt, long long *off, long long tiles,
+                                                     long long *total_out) {
+    __shared__ long long s_c[32];
+    __shared__ long long s_tot;
+    long long b, e;
+    strip_of(tiles, &b, &e);
+    long long v = 0;
+    for (long long t = b; t < e; ++t) v += cnt[t];
+    long long o = block_excl_ll_pt(v, s_c, &s_tot);
+    for (long long t = b; t < e; ++t) {
+        off[t] = o;
+        o += cnt[t];
     }
-    off[tiles] = acc;
-    if (total_out) *total_out = acc;
+    if (threadIdx.x == PT - 1) {
+        off[tiles] = o;
+        if (total_out) *total_out = o;
+    }
 }
 
+// kept pixels in stream order: per round of GT consecutive packets, a ballot
+// and the warp counts give every kept pixel its slot (coalesced writes)
 __global__ void __launch_bounds__(GT) k_compact(const uint64_t *pk, long long n, long long idx_base, const long long *t_all,
-                                                const long long *trig, long long ntr, long long tof_max,
-                                                const int16_t *lut, const long long *tile_off, tpx_hits hits,
-                                                long long cap, unsigned *status, const GAgg *E0) {
+                                                const long long *trig, const long long *n_trig, long long trig_cap,
+                                                long long tof_max, const int16_t *lut, const long long *tile_off,
+                                                tpx_hits hits, long long cap, unsigned *status, const GAgg *E0) {
+    __shared__ unsigned s_wc[GW];
     const long long trig_base = E0 ? E0->tdc.n : 0;
-    __shared__ long long s_w[GW];
-    __shared__ long long s_tot;
-    const long long tile = blockIdx.x, q0 = tile * GTILE + threadIdx.x * GK;
-    long long mine = 0;
+    const long long ntr = usable_triggers(n_trig, trig_cap);
+    if (ntr < 0) return;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const long long tile = blockIdx.x, base = tile * GTILE;
+    long long o = tile_off[tile];
     for (int j = 0; j < GK; ++j) {
-        const long long q = q0 + j;
-        if (q >= n) break;
-        long long s, f;
-        mine += bin_pixel(pk[q], t_all[q], trig, ntr, tof_max, &s, &f) == 0;
-    }
-    long long o = tile_off[tile] + block_scan_ll(mine, s_w, &s_tot);
-    for (int j = 0; j < GK; ++j) {
-        const long long q = q0 + j;
-        if (q >= n) break;
-        const uint64_t w = pk[q];
-        long long s, f;
-        if (bin_pixel(w, t_all[q], trig, ntr, tof_max, &s, &f) != 0) continue;
-        if (o < cap) {
-            const int tot = pix_tot(w);
-            const long long corr = lut ? (long long)lut[tot] : 0LL;
-            hits.index[o] = idx_base + q;
-            hits.shot[o] = s + trig_base;
-            hits.t[o] = t_all[q] - corr;
-            hits.tof[o] = (int32_t)(f - corr);
-            hits.x[o] = (uint8_t)pix_x(w);
-            hits.y[o] = (uint8_t)pix_y(w);
-            hits.tot[o] = (uint16_t)tot;
-        } else {
-            atomicOr(status, ST_CLUSTER_CAP);
+        if (base + j * GT >= n) break;                  // uniform over the block
+        const long long q = base + j * GT + threadIdx.x;
+        uint64_t w = 0;
+        long long s = 0, f = 0;
+        bool keep = false;
+        if (q < n) {
+            w = pk[q];
+            keep = bin_pixel(w, t_all[q], trig, ntr, tof_max, &s, &f) == 0;
         }
-        ++o;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_wc[wi] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < GW; ++k) {
+            const unsigned c = s_wc[k];
+            before += k < wi ? c : 0u;
+            total += c;
+        }
+        if (keep) {
+            const long long slot = o + before + __popc(bal & ((1u << lane) - 1u));
+            if (slot < cap) {
+                const int tot = pix_tot(w);
+                const long long corr = lut ? (long long)lut[tot] : 0LL;
+                hits.index[slot] = idx_base + q;
+                hits.shot[slot] = s + trig_base;
+                hits.t[slot] = t_all[q] - corr;
+                hits.tof[slot] = (int32_t)(f - corr);
+                hits.x[slot] = (uint8_t)pix_x(w);
+                hits.y[slot] = (uint8_t)pix_y(w);
+                hits.tot[slot] = (uint16_t)tot;
+            } else {
+                atomicOr(status, ST_CLUSTER_CAP);
+            }
+        }
+        o += total;
+        __syncthreads();
     }
 }
 
@@ -352,9 +458,19 @@ __global__ void __launch_bounds__(GT) k_scan_blocks(const unsigned *in, unsigned
         if (base + j < n) { out[base + j] = (unsigned)o; o += in[base + j]; }
     if (threadIdx.x == 0) bsum[blockIdx.x] = (unsigned)s_tot;
 }
-__global__ void k_scan_bsum(unsigned *bsum, long long nb) {
-    unsigned acc = 0;
-    for (long long b = 0; b < nb; ++b) { const unsigned v = bsum[b]; bsum[b] = acc; acc += v; }
+__global__ void __launch_bounds__(PT) k_scan_bsum(unsigned *bsum, long long nb) {
+    __shared__ long long s_c[32];
+    __shared__ long long s_tot;
+    long long b, e;
+    strip_of(nb, &b, &e);
+    long long v = 0;
+    for (long long t = b; t < e; ++t) v += bsum[t];
+    long long o = block_excl_ll_pt(v, s_c, &s_tot);
+    for (long long t = b; t < e; ++t) {
+        const unsigned x = bsum[t];
+        bsum[t] = (unsigned)o;
+        o += x;
+    }
 }
 __global__ void k_scan_add(unsigned *out, long long n, const unsigned *bsum) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -362,17 +478,30 @@ __global__ void k_scan_add(unsigned *out, long long n, const unsigned *bsum) {
 }
 
 // ------------------------------------------------------------ cluster kernels
-__global__ void k_make_keys(tpx_hits h, long long n, unsigned long long *keys, unsigned *vals) {
+// sort key: (shot relative to the call's first shot) << 24 | corrected ToF + bias
+__global__ void k_make_keys(tpx_hits h, long long n, const unsigned long long *shot_min, unsigned long long *keys,
+                            unsigned *vals) {
+    const unsigned long long m = *shot_min;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        keys[i] = ((unsigned long long)h.shot[i] << 24) | (unsigned long long)(h.tof[i] + kBias);
+        keys[i] = (((unsigned long long)h.shot[i] - m) << 24) | (unsigned long long)(h.tof[i] + kBias);
         vals[i] = (unsigned)i;
     }
 }
-__global__ void k_max_shot(tpx_hits h, long long n, unsigned long long *mx) {
-    unsigned long long m = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        m = max(m, (unsigned long long)h.shot[i]);
-    atomicMax(mx, m);
+__global__ void k_shot_range(tpx_hits h, long long n, unsigned long long *mn, unsigned long long *mx) {
+    unsigned long long lo = ~0ull, hi = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long v = (unsigned long long)h.shot[i];
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mn, lo);
+        atomicMax(mx, hi);
+    }
 }
 
 struct Sorted {                     // hits in sorted order
@@ -397,6 +526,344 @@ __global__ void k_gather(tpx_hits h, const unsigned *vals, long long n, Sorted s
     }
 }
 
+// Segments: in sorted order a gap larger than dt (or a new shot) separates
+// everything before it from everything after it -- no adjacent pair spans
+// it -- so each run between such gaps clusters on its own.
+__global__ void k_seg_flags(Sorted s, long long n, int dt, unsigned *f) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        f[i] = (i == 0 || s.shot[i] != s.shot[i - 1] || s.tofb[i] - s.tofb[i - 1] > dt) ? 1u : 0u;
+}
+__global__ void k_seg_starts(const unsigned *f, const unsigned *off, long long n, long long *start, long long *nseg) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (f[i]) start[off[i]] = i;
+        if (i == n - 1) {
+            const long long m = (long long)off[i] + f[i];
+            start[m] = n;
+            *nseg = m;
+        }
+    }
+}
+
+// per-root moments, indexed by the hit position of the root
+struct AccH { long long s_tot, s_x, s_y, s_t; unsigned n, npk; };
+
+constexpr int WCAP = 256;           // hits of a segment held by one warp
+constexpr int ECAP = 1024;          // adjacent pairs of a segment kept for the hooking rounds
+constexpr int SEGW = 4;             // warps per block
+struct SegSm {
+    int tofb[WCAP];
+    int parent[WCAP];
+    unsigned edge[ECAP];            // (k << 16) | j, k < j
+    unsigned ecnt;
+    unsigned short tot[WCAP];
+    unsigned char x[WCAP], y[WCAP], np[WCAP];
+};
+
+__device__ __forceinline__ int s_find(volatile int *par, int x) {
+    for (;;) {
+        const int p = par[x];
+        if (p == x) return x;
+        const int g = par[p];
+        if (g == p) return p;
+        par[x] = g;
+        x = g;
+    }
+}
+// lock-free union in shared memory; the smaller position becomes the root
+__device__ __forceinline__ void s_unite(int *par, int a, int b) {
+    for (;;) {
+        a = s_find(par, a);
+        b = s_find(par, b);
+        if (a == b) return;
+        if (a > b) { const int t = a; a = b; b = t; }
+        const int old = atomicCAS(&par[b], b, a);
+        if (old == b) return;
+        b = old;
+    }
+}
+
+// Sec. V.B tie rule: equal ToT goes to the hit later in the stream
+__device__ __forceinline__ bool j_brighter(int tj, int ti, const long long *index, long long j, long long i) {
+    return tj > ti || (tj == ti && index[j] > index[i]);
+}
+
+// Segments of at most 64 hits, in registers: lane l holds hits l and l + 32.
+// For every hit k (warp-uniform loop) the ballots of "adjacent to k" give
+// its adjacency row as a 64-bit mask and "brighter than k" its local-maximum
+// flag; components are breadth-first closures over the rows, seeded at the
+// lowest unvisited position, so the seed is the component's earliest hit.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ void seg_small(const Sorted &s, long long s0, int L, int rx, int ry, int dt, int cc, bool emit,
+                          long long *labels, unsigned char *is_peak, unsigned *rflag, AccH *acc, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int a = lane, b = lane + 32;
+    const bool va = a < L, vb = b < L;
+    int ta = 0, tb = 0;
+    unsigned pa = 0, pb = 0, oa = 0, ob = 0, ha = 0, hb = 0;
+    long long ia = 0, ib = 0;
+    if (va) {
+        ta = s.tofb[s0 + a]; pa = s.x[s0 + a] | ((unsigned)s.y[s0 + a] << 8); oa = s.tot[s0 + a];
+        ia = s.index[s0 + a]; ha = s.hit[s0 + a];
+    }
+    if (vb) {
+        tb = s.tofb[s0 + b]; pb = s.x[s0 + b] | ((unsigned)s.y[s0 + b] << 8); ob = s.tot[s0 + b];
+        ib = s.index[s0 + b]; hb = s.hit[s0 + b];
+    }
+    const unsigned rxy = (unsigned)rx | ((unsigned)ry << 8);   // per-byte box radii
+    unsigned long long rowA = 0, rowB = 0;
+    bool npA = false, npB = false;
+    for (int k = 0; k < L; ++k) {
+        const bool kb = k >= 32;
+        const int src = k & 31;
+        const int kt = __shfl_sync(FULL, kb ? tb : ta, src);
+        const unsigned kp = __shfl_sync(FULL, kb ? pb : pa, src);
+        const unsigned ko = __shfl_sync(FULL, kb ? ob : oa, src);
+        const bool adjA = va && a != k && abs(ta - kt) <= dt && __vcmpleu4(__vabsdiffu4(pa, kp), rxy) == FULL;
+        const bool adjB = vb && b != k && abs(tb - kt) <= dt && __vcmpleu4(__vabsdiffu4(pb, kp), rxy) == FULL;
+        const unsigned lo = __ballot_sync(FULL, adjA), hi = __ballot_sync(FULL, adjB);
+        bool brA = adjA && oa > ko, brB = adjB && ob > ko;
+        const bool tA = adjA && oa == ko, tB = adjB && ob == ko;
+        if (__any_sync(FULL, tA || tB)) {   // Sec. V.B ties: the later hit in the stream wins
+            const long long ki = __shfl_sync(FULL, kb ? ib : ia, src);
+            brA = brA || (tA && ia > ki);
+            brB = brB || (tB && ib > ki);
+        }
+        const bool knp = __any_sync(FULL, brA || brB);
+        if (lane == src) {
+            const unsigned long long row = ((unsigned long long)hi << 32) | lo;
+            if (kb) { rowB = row; npB = knp; } else { rowA = row; npA = knp; }
+        }
+    }
+    const bool pkA = va && !npA, pkB = vb && !npB;
+    if (!cc) {   // PAPER mode: every hit is its own label; local maxima carry the records
+        if (va) {
+            if (labels) labels[ha] = ia;
+            if (is_peak) is_peak[ha] = pkA;
+            if (rflag) rflag[ha] = emit && pkA;
+        }
+        if (vb) {
+            if (labels) labels[hb] = ib;
+            if (is_peak) is_peak[hb] = pkB;
+            if (rflag) rflag[hb] = emit && pkB;
+        }
+        return;
+    }
+    const unsigned long long peaks = ((unsigned long long)__ballot_sync(FULL, pkB) << 32) | __ballot_sync(FULL, pkA);
+    unsigned long long todo = L == 64 ? ~0ull : ((1ull << L) - 1ull);
+    long long rootA = 0, rootB = 0;
+    int rposA = -1, rposB = -1;
+    while (todo) {
+        const int seed = __ffsll((long long)todo) - 1;
+        unsigned long long comp = 1ull << seed, front = comp;
+        while (front) {
+            unsigned long long c = 0;
+            if ((front >> a) & 1ull) c |= rowA;
+            if ((front >> b) & 1ull) c |= rowB;
+            const unsigned lo = __reduce_or_sync(FULL, (unsigned)c);
+            const unsigned hi = __reduce_or_sync(FULL, (unsigned)(c >> 32));
+            const unsigned long long nb = ((unsigned long long)hi << 32) | lo;
+            front = nb & ~comp;
+            comp |= nb;
+        }
+        const long long sidx = __shfl_sync(FULL, seed >= 32 ? ib : ia, seed & 31);
+        const bool inA = (comp >> a) & 1ull, inB = (comp >> b) & 1ull;
+        if (inA) { rootA = sidx; rposA = seed; }
+        if (inB) { rootB = sidx; rposB = seed; }
+        if (acc && emit) {
+            const int st = __shfl_sync(FULL, seed >= 32 ? tb : ta, seed & 31);
+            unsigned long long v_tot = 0, v_x = 0, v_y = 0, v_t = 0;
+            if (inA) { v_tot += oa; v_x += (unsigned long long)oa * (pa & 255u); v_y += (unsigned long long)oa * (pa >> 8);
+                       v_t += (unsigned long long)(ta - st) * oa; }
+            if (inB) { v_tot += ob; v_x += (unsigned long long)ob * (pb & 255u); v_y += (unsigned long long)ob * (pb >> 8);
+                       v_t += (unsigned long long)(tb - st) * ob; }
+            v_tot = warp_sum_u64(v_tot);
+            v_x = warp_sum_u64(v_x);
+            v_y = warp_sum_u64(v_y);
+            v_t = warp_sum_u64(v_t);
+            if (lane == (seed & 31)) {
+                AccH r;
+                r.s_tot = (long long)v_tot; r.s_x = (long long)v_x; r.s_y = (long long)v_y; r.s_t = (long long)v_t;
+                r.n = (unsigned)__popcll(comp); r.npk = (unsigned)__popcll(comp & peaks);
+                acc[seed >= 32 ? hb : ha] = r;
+            }
+        }
+        todo &= ~comp;
+    }
+    if (va) {
+        if (labels) labels[ha] = rootA;
+        if (is_peak) is_peak[ha] = pkA;
+        if (rflag) rflag[ha] = emit && rposA == a;
+    }
+    if (vb) {
+        if (labels) labels[hb] = rootB;
+        if (is_peak) is_peak[hb] = pkB;
+        if (rflag) rflag[hb] = emit && rposB == b;
+    }
+}
+
+// One warp per segment of at most WCAP hits, in shared memory: every hit
+// scans forward within dt (each adjacent pair met once, from its earlier
+// end), sets the local-maximum flags and joins the pair; then labels, peaks,
+// root flags (emitted shots only) and the root's int64 moments. Longer
+// segments are marked for the global-memory kernels below.
+__global__ void __launch_bounds__(SEGW * 32) k_segments(Sorted s, const long long *seg_start, const long long *nseg_p,
+                                                        int rx, int ry, int dt, int cc, long long shot_limit,
+                                                        long long *labels, unsigned char *is_peak, unsigned *rflag,
+                                                        AccH *acc, unsigned char *mark) {
+    __shared__ SegSm sm[SEGW];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    SegSm &W = sm[wi];
+    const long long nseg = *nseg_p;
+    for (long long seg = blockIdx.x * (long long)SEGW + wi; seg < nseg; seg += (long long)gridDim.x * SEGW) {
+        const long long s0 = seg_start[seg], len = seg_start[seg + 1] - s0;
+        if (len > WCAP) {
+            for (long long k = lane; k < len; k += 32) mark[s0 + k] = 1;
+            continue;
+        }
+        const int L = (int)len;
+        const bool emit = s.shot[s0] < shot_limit;
+        const bool sums = cc && acc && emit;
+        if (L > 1 && L <= 64) {
+            seg_small(s, s0, L, rx, ry, dt, cc, emit, labels, is_peak, rflag, sums ? acc : nullptr, lane);
+            continue;
+        }
+        if (L == 1) {
+            if (lane == 0) {
+                const unsigned hh = s.hit[s0];
+                if (labels) labels[hh] = s.index[s0];
+                if (is_peak) is_peak[hh] = 1;
+                if (rflag) rflag[hh] = emit;
+                if (sums) {
+                    const long long t = s.tot[s0];
+                    AccH a;
+                    a.s_tot = t; a.s_x = t * s.x[s0]; a.s_y = t * s.y[s0]; a.s_t = 0; a.n = 1; a.npk = 1;
+                    acc[hh] = a;
+                }
+            }
+            continue;
+        }
+        for (int k = lane; k < L; k += 32) {
+            W.tofb[k] = s.tofb[s0 + k];
+            W.x[k] = s.x[s0 + k];
+            W.y[k] = s.y[s0 + k];
+            W.tot[k] = s.tot[s0 + k];
+            W.parent[k] = k;
+            W.np[k] = 0;
+        }
+        if (lane == 0) W.ecnt = 0;
+        __syncwarp();
+        for (int k = lane; k < L; k += 32) {
+            const int tb = W.tofb[k], xk = W.x[k], yk = W.y[k], tk = W.tot[k];
+            for (int j = k + 1; j < L; ++j) {
+                if (W.tofb[j] - tb > dt) break;
+                const int dx = (int)W.x[j] - xk, dy = (int)W.y[j] - yk;
+                if (dx < -rx || dx > rx || dy < -ry || dy > ry) continue;
+                if (j_brighter(W.tot[j], tk, s.index, s0 + j, s0 + k)) W.np[k] = 1; else W.np[j] = 1;
+                if (cc) {   // record the pair (warp-aggregated slot); beyond the buffer, join it now
+                    const unsigned am = __activemask();
+                    const int leader = __ffs(am) - 1;
+                    unsigned slot = 0;
+                    if (lane == leader) slot = atomicAdd(&W.ecnt, (unsigned)__popc(am));
+                    slot = __shfl_sync(am, slot, leader) + __popc(am & ((1u << lane) - 1u));
+                    if (slot < (unsigned)ECAP) W.edge[slot] = ((unsigned)k << 16) | (unsigned)j;
+                    else s_unite(W.parent, k, j);
+                }
+            }
+        }
+        __syncwarp();
+        if (cc) {
+            // rounds of: pointer jumping until every hit points at its root,
+            // then every recorded pair whose roots differ hooks the larger
+            // root onto the smaller one (CAS on a root only, so no link is
+            // ever overwritten); until no pair has two roots. Pointers only
+            // go to smaller positions, so the root is the earliest hit.
+            const int m = min((int)W.ecnt, ECAP);
+            for (;;) {
+                for (;;) {
+                    bool moved = false;
+                    for (int k = lane; k < L; k += 32) {
+                        const int p = W.parent[k], pp = W.parent[p];
+                        if (pp != p) { W.parent[k] = pp; moved = true; }
+                    }
+                    __syncwarp();
+                    if (!__any_sync(0xffffffffu, moved)) break;
+                }
+                bool hooked = false;
+                for (int e = lane; e < m; e += 32) {
+                    const unsigned ed = W.edge[e];
+                    const int a = W.parent[ed >> 16], b = W.parent[ed & 0xFFFFu];
+                    if (a != b) {
+                        atomicCAS(&W.parent[max(a, b)], max(a, b), min(a, b));
+                        hooked = true;
+                    }
+                }
+                __syncwarp();
+                if (!__any_sync(0xffffffffu, hooked)) break;
+            }
+        }
+        __syncwarp();
+        // roots of every hit (full compression; only reads after the barrier)
+        int rk[WCAP / 32];
+#pragma unroll
+        for (int u = 0; u < WCAP / 32; ++u) {
+            const int k = u * 32 + lane;
+            rk[u] = (k < L && cc) ? s_find(W.parent, k) : k;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < WCAP / 32; ++u) {
+            const int k = u * 32 + lane;
+            if (k < L) W.parent[k] = rk[u];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < WCAP / 32; ++u) {
+            const int k = u * 32 + lane;
+            if (k >= L) break;
+            const int r = rk[u];
+            const unsigned hh = s.hit[s0 + k];
+            const bool peak = W.np[k] == 0;
+            if (labels) labels[hh] = s.index[s0 + r];
+            if (is_peak) is_peak[hh] = peak;
+            if (rflag) rflag[hh] = emit && (cc ? r == k : peak);
+        }
+        if (sums) {
+            // each root's lane sweeps the segment once (broadcast reads, no
+            // atomics): exact 64-bit moments in registers
+            for (int base = 0; base < L; base += 32) {
+                const int k = base + lane;
+                const bool own = k < L && W.parent[k] == k;
+                if (__ballot_sync(0xffffffffu, own) == 0) continue;
+                unsigned long long st = 0, sx = 0, sy = 0, stt = 0;
+                unsigned cnt = 0, npk = 0;
+                const int tk = own ? W.tofb[k] : 0;
+                for (int j = own ? k : L; j < L; ++j) {   // members sit at or after their root
+                    if (W.parent[j] != k) continue;
+                    const unsigned long long t = W.tot[j];
+                    st += t;
+                    sx += t * W.x[j];
+                    sy += t * W.y[j];
+                    stt += (unsigned long long)(W.tofb[j] - tk) * t;
+                    cnt += 1;
+                    npk += W.np[j] == 0;
+                }
+                if (own) {
+                    AccH a;
+                    a.s_tot = (long long)st; a.s_x = (long long)sx; a.s_y = (long long)sy; a.s_t = (long long)stt;
+                    a.n = cnt; a.npk = npk;
+                    acc[s.hit[s0 + k]] = a;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---- segments longer than WCAP: the same rules through global memory ----
 __device__ __forceinline__ int g_find(int *parent, int x) {
     for (;;) {
         const int p = ((volatile int *)parent)[x];
@@ -418,38 +885,56 @@ __device__ void g_unite(int *parent, int a, int b) {
         b = old;
     }
 }
-
-// every hit scans forward in sorted order while the shot is the same and the
-// time gap is within dt: each adjacent pair is met once (from its earlier end)
-__global__ void k_window(Sorted s, long long n, int rx, int ry, int dt, int cc, int *parent, unsigned char *notpeak) {
+__global__ void k_long_init(Sorted s, long long n, const unsigned char *mark, int *parent, unsigned char *notpeak,
+                            AccH *acc) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!mark[i]) continue;
+        parent[i] = (int)i;
+        notpeak[i] = 0;
+        if (acc) {
+            AccH z;
+            z.s_tot = 0; z.s_x = 0; z.s_y = 0; z.s_t = 0; z.n = 0; z.npk = 0;
+            acc[s.hit[i]] = z;
+        }
+    }
+}
+__global__ void k_long_window(Sorted s, long long n, const unsigned char *mark, int rx, int ry, int dt, int cc,
+                              int *parent, unsigned char *notpeak) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!mark[i]) continue;
         const long long sh = s.shot[i];
         const int tb = s.tofb[i], xi = s.x[i], yi = s.y[i], ti = s.tot[i];
-        const long long ii = s.index[i];
-        for (long long j = i + 1; j < n; ++j) {
+        for (long long j = i + 1; j < n; ++j) {       // stops at the segment's end
             if (s.shot[j] != sh || s.tofb[j] - tb > dt) break;
             const int dx = (int)s.x[j] - xi, dy = (int)s.y[j] - yi;
             if (dx < -rx || dx > rx || dy < -ry || dy > ry) continue;
-            const int tj = s.tot[j];
-            // local maxima: equal ToT goes to the later pixel in the stream (Sec. V.B)
-            if (tj > ti || (tj == ti && s.index[j] > ii)) notpeak[i] = 1; else notpeak[j] = 1;
+            if (j_brighter(s.tot[j], ti, s.index, j, i)) notpeak[i] = 1; else notpeak[j] = 1;
             if (cc) g_unite(parent, (int)i, (int)j);
         }
     }
 }
-
-__global__ void k_labels(Sorted s, long long n, int cc, int *parent, const unsigned char *notpeak, long long *labels,
-                         unsigned char *is_peak) {
+__global__ void k_long_finish(Sorted s, long long n, const unsigned char *mark, int cc, long long shot_limit,
+                              int *parent, const unsigned char *notpeak, long long *labels, unsigned char *is_peak,
+                              unsigned *rflag, AccH *acc) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const unsigned h = s.hit[i];
-        labels[h] = cc ? s.index[g_find(parent, (int)i)] : s.index[i];
-        if (is_peak) is_peak[h] = notpeak[i] ? 0 : 1;
+        if (!mark[i]) continue;
+        const long long r = cc ? g_find(parent, (int)i) : i;
+        const unsigned hh = s.hit[i];
+        const bool peak = notpeak[i] == 0, emit = s.shot[i] < shot_limit;
+        if (labels) labels[hh] = s.index[r];
+        if (is_peak) is_peak[hh] = peak;
+        if (rflag) rflag[hh] = emit && (cc ? r == i : peak);
+        if (cc && acc && emit) {
+            AccH &a = acc[s.hit[r]];
+            const unsigned long long t = s.tot[i];
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.s_tot), t);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.s_x), t * s.x[i]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.s_y), t * s.y[i]);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.s_t), (unsigned long long)(s.tofb[i] - s.tofb[r]) * t);
+            atomicAdd(&a.n, 1u);
+            if (peak) atomicAdd(&a.npk, 1u);
+        }
     }
-}
-
-__global__ void k_iota(int *p, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = (int)i;
 }
 
 // ------------------------------------------------------------ centroid kernels
@@ -507,11 +992,11 @@ __global__ void k_final(tpx_hits h, long long n, const unsigned *flags, const un
 
 // PAPER mode: each local maximum sums its box neighbourhood (both directions
 // in sorted order, within dt)
-__global__ void k_paper(Sorted s, long long n, int rx, int ry, int dt, const unsigned char *is_peak_hit,
+__global__ void k_paper(Sorted s, long long n, int rx, int ry, int dt, const unsigned *flag_hit,
                         const unsigned *cid_hit, tpx_hits h, tpx_record *out, long long cap) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const unsigned hi = s.hit[i];
-        if (!is_peak_hit[hi]) continue;
+        if (!flag_hit[hi]) continue;
         const long long c = cid_hit[hi];
         if (c >= cap) continue;
         const long long sh = s.shot[i];
@@ -544,8 +1029,34 @@ __global__ void k_paper(Sorted s, long long n, int rx, int ry, int dt, const uns
     }
 }
 
-__global__ void k_count_from_scan(const unsigned *flags, const unsigned *cid, long long n, long long *out) {
-    *out = n ? (long long)cid[n - 1] + flags[n - 1] : 0;
+// number of records; latches the capacity status and the clusters counter
+__global__ void k_count_from_scan(const unsigned *flags, const unsigned *cid, long long n, long long *out,
+                                  long long cap, unsigned *status, unsigned long long *counter) {
+    const long long m = n ? (long long)cid[n - 1] + flags[n - 1] : 0;
+    *out = m;
+    if (m > cap) atomicOr(status, ST_CLUSTER_CAP);
+    if (counter) *counter = (unsigned long long)m;
+}
+
+// CC records from the per-root moments (root hit positions carry the flag)
+__global__ void k_records(tpx_hits h, long long n, const unsigned *rflag, const unsigned *cid, const AccH *acc,
+                          tpx_record *out, long long cap) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!rflag[i]) continue;
+        const long long c = cid[i];
+        if (c >= cap) continue;
+        const AccH a = acc[i];
+        tpx_record o;
+        o.label = h.index[i];
+        o.shot = h.shot[i];
+        o.t0 = h.t[i];
+        o.s_tot = a.s_tot; o.s_x = a.s_x; o.s_y = a.s_y; o.s_t = a.s_t;
+        o.n = (int)a.n; o.n_peaks = (int)a.npk;
+        o.x = (double)o.s_x / (double)o.s_tot;
+        o.y = (double)o.s_y / (double)o.s_tot;
+        o.tof = (double)h.tof[i] + (double)o.s_t / (double)o.s_tot;
+        out[c] = o;
+    }
 }
 
 // ------------------------------------------------------------ host helpers
@@ -586,32 +1097,39 @@ int scan_u32(Arena &a, const unsigned *in, unsigned *out, long long n, cudaStrea
     const long long nb = (n + GTILE - 1) / GTILE;
     unsigned *bsum = a.take<unsigned>(nb);
     k_scan_blocks<<<(unsigned)(nb > 0 ? nb : 1), GT, 0, s>>>(in, out, n, bsum);
-    k_scan_bsum<<<1, 1, 0, s>>>(bsum, nb);
+    k_scan_bsum<<<1, PT, 0, s>>>(bsum, nb);
     k_scan_add<<<grid_for(n), GT, 0, s>>>(out, n, bsum);
     return ck(cudaGetLastError());
 }
 
 size_t sort_bytes(long long n) {
     const long long tiles = (n + GTILE - 1) / GTILE;
-    return 2 * sz(n, 8) + 2 * sz(n, 4) + 2 * sz(256 * tiles, 4) + sz((256 * tiles + GTILE - 1) / GTILE + 1, 4) + 4096;
+    return 2 * sz(n, 8) + 2 * sz(n, 4) + 2 * sz(256 * tiles, 4) + sz((256 * tiles + GTILE - 1) / GTILE + 1, 4) +
+           sz(2, 8) + 4096;
 }
 
-// sort the hits by (shot, corrected ToF); returns the sorted values buffer
-int sort_hits(tpx_ctx *c, Arena &a, const tpx_hits &h, long long n, unsigned **vals_out) {
+// sort the hits by (shot, corrected ToF); returns the sorted values buffer.
+// shot_span >= 0 bounds max shot - min shot (no host round trip); < 0 reads it.
+int sort_hits(tpx_ctx *c, Arena &a, const tpx_hits &h, long long n, long long shot_span, unsigned **vals_out) {
     cudaStream_t s = c->stream;
     const long long tiles = (n + GTILE - 1) / GTILE;
     unsigned long long *k0 = a.take<unsigned long long>(n), *k1 = a.take<unsigned long long>(n);
     unsigned *v0 = a.take<unsigned>(n), *v1 = a.take<unsigned>(n);
     unsigned *hist = a.take<unsigned>(256 * tiles), *offs = a.take<unsigned>(256 * tiles);
-    unsigned long long *mx = a.take<unsigned long long>(1);
-    if (cudaMemsetAsync(mx, 0, 8, s) != cudaSuccess) return TPX_ECUDA;
-    k_make_keys<<<grid_for(n), GT, 0, s>>>(h, n, k0, v0);
-    k_max_shot<<<grid_for(n), GT, 0, s>>>(h, n, mx);
-    unsigned long long hmx = 0;
-    if (cudaMemcpyAsync(&hmx, mx, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    unsigned long long *mm = a.take<unsigned long long>(2);   // min, max shot
+    const unsigned long long init[2] = {~0ull, 0ull};
+    if (cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, s) != cudaSuccess) return TPX_ECUDA;
+    k_shot_range<<<grid_for(n), GT, 0, s>>>(h, n, mm, mm + 1);
+    k_make_keys<<<grid_for(n), GT, 0, s>>>(h, n, mm, k0, v0);
+    unsigned long long span = (unsigned long long)shot_span;
+    if (shot_span < 0) {
+        unsigned long long hm[2] = {0, 0};
+        if (cudaMemcpyAsync(hm, mm, sizeof hm, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        span = hm[1] - hm[0];
+    }
     int bits = 24;
-    while (bits < 64 && (hmx >> (bits - 24)) != 0) ++bits;
+    while (bits < 64 && (span >> (bits - 24)) != 0) ++bits;
     const size_t mark = a.used;
     for (int shift = 0; shift < bits; shift += 8) {
         a.used = mark;
@@ -627,13 +1145,17 @@ int sort_hits(tpx_ctx *c, Arena &a, const tpx_hits &h, long long n, unsigned **v
     return ck(cudaGetLastError());
 }
 
+size_t decode_bytes(long long n) {
+    const long long tiles = (n + GTILE - 1) / GTILE;
+    return sz(tiles, sizeof(GAgg)) * 2 + sz(tiles + 1, 8) * 4 + sz(n, 8) + 4096;
+}
+
 int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const tpx_hits &h, int64_t cap,
                 int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
                 const GAgg *E0, GAgg *state_out, long long *trig_pos, long long **t_all_out) {
     cudaStream_t s = c->stream;
     const long long tiles = (n + GTILE - 1) / GTILE;
-    const size_t need = sz(tiles, sizeof(GAgg)) * 2 + sz(tiles + 1, 8) * 4 + sz(n, 8) + 4096;
-    int rc = reserve(c, need);
+    int rc = reserve(c, decode_bytes(n));
     if (rc) return rc;
     Arena a{static_cast<char *>(c->g_mem), 0, c->g_bytes};
     GAgg *tagg = a.take<GAgg>(tiles), *tpre = a.take<GAgg>(tiles);
@@ -650,33 +1172,42 @@ int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const t
         return ck(cudaMemsetAsync(state_out, 0, sizeof(GAgg), s));
     }
     const long long tp = c->cfg.wrap_thr_pix_ticks, tt = c->cfg.wrap_thr_tdc_ticks;
+    long long *ntr = reinterpret_cast<long long *>(d_n_trig);
+    long long *tr = reinterpret_cast<long long *>(trig);
     k_tile_agg<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tp, tt, tagg, tcnt);
-    k_tile_prefix<<<1, 1, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, reinterpret_cast<long long *>(d_n_trig),
-                                  E0, state_out);
-    k_unwrap<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tpre, toff, tp, tt, t_all, reinterpret_cast<long long *>(trig),
-                                            trig_cap, &c->ctl->status, trig_pos);
-    long long ntr_h = 0;
-    if (cudaMemcpyAsync(&ntr_h, d_n_trig, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-    if (ntr_h > trig_cap) return TPX_OK;   // status already latched; nothing to bin against
-    k_check_trig<<<grid_for(ntr_h), GT, 0, s>>>(reinterpret_cast<long long *>(trig), ntr_h, &c->ctl->status);
-    k_bin<<<(unsigned)tiles, GT, 0, s>>>(pk, n, t_all, reinterpret_cast<long long *>(trig), ntr_h,
-                                         c->cfg.tof_max_ticks, tkept, c->ctl->counters);
-    k_serial_prefix<<<1, 1, 0, s>>>(tkept, tkoff, tiles, reinterpret_cast<long long *>(d_n_hits));
-    k_compact<<<(unsigned)tiles, GT, 0, s>>>(pk, n, base, t_all, reinterpret_cast<long long *>(trig), ntr_h,
-                                             c->cfg.tof_max_ticks, c->cfg.d_timewalk_lut, tkoff, h, cap,
-                                             &c->ctl->status, E0);
+    k_tile_prefix<<<1, PT, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, ntr, E0, state_out);
+    k_unwrap<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tpre, toff, tp, tt, t_all, tr, trig_cap, &c->ctl->status, trig_pos);
+    k_check_trig<<<152, GT, 0, s>>>(tr, ntr, trig_cap, &c->ctl->status);
+    k_bin<<<(unsigned)tiles, GT, 0, s>>>(pk, n, t_all, tr, ntr, trig_cap, c->cfg.tof_max_ticks, tkept,
+                                         c->ctl->counters);
+    k_count_prefix<<<1, PT, 0, s>>>(tkept, tkoff, tiles, reinterpret_cast<long long *>(d_n_hits));
+    k_compact<<<(unsigned)tiles, GT, 0, s>>>(pk, n, base, t_all, tr, ntr, trig_cap, c->cfg.tof_max_ticks,
+                                             c->cfg.d_timewalk_lut, tkoff, h, cap, &c->ctl->status, E0);
     const unsigned long long np = (unsigned long long)n;
     if (cudaMemcpyAsync(&c->ctl->counters[C_PACKETS], &np, 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return TPX_ECUDA;
     return ck(cudaGetLastError());
 }
 
-int cluster_impl(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8_t *is_peak) {
+size_t cluster_bytes(long long n) {
+    return sort_bytes(n) + sz(n, 4) + sz(n, 8) * 2 + sz(n, 4) + sz(n, 2) + 2 * sz(n, 1)   // sorted hits
+           + 2 * sz(n, 4) + sz(n + 1, 8) + sz(1, 8)                                     // segments
+           + 2 * sz(n, 1) + sz(n, 4)                                                    // long segments
+           + 2 * sz(n, 4) + sz(n, sizeof(AccH)) + sz((n + GTILE - 1) / GTILE + 1, 4)    // records
+           + 8192;
+}
+
+// The whole clustering stage: sort, segments, labels, local maxima and, when
+// `out` is given, the records of the hits whose shot is below shot_limit.
+// labels / is_peak (per hit) may be NULL. No host round trip when
+// shot_span >= 0.
+int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8_t *is_peak, long long shot_limit,
+                long long shot_span, tpx_record *out, int64_t cap, int64_t *d_n_clusters) {
     cudaStream_t s = c->stream;
+    const int cc = c->cfg.mode == TPX_MODE_CC;
+    if (out && cudaMemsetAsync(d_n_clusters, 0, 8, s) != cudaSuccess) return TPX_ECUDA;
     if (n <= 0) return TPX_OK;
-    const size_t need = sort_bytes(n) + sz(n, 4) + sz(n, 8) * 2 + sz(n, 4) + sz(n, 2) + 3 * sz(n, 1) + sz(n, 4) + 4096;
-    int rc = reserve(c, need);
+    int rc = reserve(c, cluster_bytes(n));
     if (rc) return rc;
     Arena a{static_cast<char *>(c->g_mem), 0, c->g_bytes};
     Sorted so;
@@ -687,18 +1218,48 @@ int cluster_impl(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint
     so.tot = a.take<unsigned short>(n);
     so.x = a.take<unsigned char>(n);
     so.y = a.take<unsigned char>(n);
-    unsigned char *notpeak = a.take<unsigned char>(n);
+    unsigned *segf = a.take<unsigned>(n), *sego = a.take<unsigned>(n);
+    long long *seg_start = a.take<long long>(n + 1), *nseg = a.take<long long>(1);
+    unsigned char *mark = a.take<unsigned char>(n), *notpeak = a.take<unsigned char>(n);
     int *parent = a.take<int>(n);
+    unsigned *rflag = a.take<unsigned>(n), *cid = a.take<unsigned>(n);
+    AccH *acc = a.take<AccH>(n);
+    const size_t mark_used = a.used;
     unsigned *vals = nullptr;
-    rc = sort_hits(c, a, h, n, &vals);
+    rc = sort_hits(c, a, h, n, shot_span, &vals);
     if (rc) return rc;
     k_gather<<<grid_for(n), GT, 0, s>>>(h, vals, n, so);
-    if (cudaMemsetAsync(notpeak, 0, (size_t)n, s) != cudaSuccess) return TPX_ECUDA;
-    const int cc = c->cfg.mode == TPX_MODE_CC;
-    k_iota<<<grid_for(n), GT, 0, s>>>(parent, n);
-    k_window<<<grid_for(n), GT, 0, s>>>(so, n, c->cfg.rx, c->cfg.ry, c->cfg.dt_ticks, cc, parent, notpeak);
-    k_labels<<<grid_for(n), GT, 0, s>>>(so, n, cc, parent, notpeak, reinterpret_cast<long long *>(labels), is_peak);
+    a.used = mark_used;   // the sort's scratch is free again
+    const int dt = c->cfg.dt_ticks;
+    k_seg_flags<<<grid_for(n), GT, 0, s>>>(so, n, dt, segf);
+    rc = scan_u32(a, segf, sego, n, s);
+    if (rc) return rc;
+    k_seg_starts<<<grid_for(n), GT, 0, s>>>(segf, sego, n, seg_start, nseg);
+    if (cudaMemsetAsync(mark, 0, (size_t)n, s) != cudaSuccess) return TPX_ECUDA;
+    long long *lab = reinterpret_cast<long long *>(labels);
+    unsigned *rf = out ? rflag : nullptr;
+    AccH *ac = (out && cc) ? acc : nullptr;
+    int seg_blocks = c->num_sms * 8;
+    if ((long long)seg_blocks * SEGW > n) seg_blocks = (int)((n + SEGW - 1) / SEGW);
+    k_segments<<<seg_blocks, SEGW * 32, 0, s>>>(so, seg_start, nseg, c->cfg.rx, c->cfg.ry, dt, cc, shot_limit, lab,
+                                                is_peak, rf, ac, mark);
+    k_long_init<<<grid_for(n), GT, 0, s>>>(so, n, mark, parent, notpeak, ac);
+    k_long_window<<<grid_for(n), GT, 0, s>>>(so, n, mark, c->cfg.rx, c->cfg.ry, dt, cc, parent, notpeak);
+    k_long_finish<<<grid_for(n), GT, 0, s>>>(so, n, mark, cc, shot_limit, parent, notpeak, lab, is_peak, rf, ac);
+    if (!out) return ck(cudaGetLastError());
+    rc = scan_u32(a, rflag, cid, n, s);
+    if (rc) return rc;
+    k_count_from_scan<<<1, 1, 0, s>>>(rflag, cid, n, reinterpret_cast<long long *>(d_n_clusters), cap,
+                                      &c->ctl->status, &c->ctl->counters[C_CLUSTERS]);
+    if (cc)
+        k_records<<<grid_for(n), GT, 0, s>>>(h, n, rflag, cid, acc, out, cap);
+    else
+        k_paper<<<grid_for(n), GT, 0, s>>>(so, n, c->cfg.rx, c->cfg.ry, dt, rflag, cid, h, out, cap);
     return ck(cudaGetLastError());
+}
+
+int cluster_impl(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8_t *is_peak) {
+    return cluster_all(c, h, n, labels, is_peak, LLONG_MAX, -1, nullptr, 0, nullptr);
 }
 
 int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const uint8_t *is_peak, int64_t n,
@@ -719,18 +1280,10 @@ int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const ui
     k_root_flags<<<grid_for(n), GT, 0, s>>>(h, lab, is_peak, n, cc, flags);
     rc = scan_u32(a, flags, cid, n, s);
     if (rc) return rc;
-    k_count_from_scan<<<1, 1, 0, s>>>(flags, cid, n, reinterpret_cast<long long *>(d_n_clusters));
-    long long ncl = 0;
-    if (cudaMemcpyAsync(&ncl, d_n_clusters, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-    if (ncl > cap) {
-        unsigned st = ST_CLUSTER_CAP, cur = 0;
-        if (cudaMemcpy(&cur, &c->ctl->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return TPX_ECUDA;
-        cur |= st;
-        if (cudaMemcpy(&c->ctl->status, &cur, 4, cudaMemcpyHostToDevice) != cudaSuccess) return TPX_ECUDA;
-    }
+    k_count_from_scan<<<1, 1, 0, s>>>(flags, cid, n, reinterpret_cast<long long *>(d_n_clusters), cap,
+                                      &c->ctl->status, &c->ctl->counters[C_CLUSTERS]);
     if (cc) {
-        if (cudaMemsetAsync(acc, 0, sizeof(Acc) * (size_t)ncl, s) != cudaSuccess) return TPX_ECUDA;
+        if (cudaMemsetAsync(acc, 0, sizeof(Acc) * (size_t)n, s) != cudaSuccess) return TPX_ECUDA;
         k_accum<<<grid_for(n), GT, 0, s>>>(h, lab, is_peak, n, cid, acc);
         k_final<<<grid_for(n), GT, 0, s>>>(h, n, flags, cid, acc, out, cap);
     } else {
@@ -743,16 +1296,11 @@ int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const ui
         so.x = a.take<unsigned char>(n);
         so.y = a.take<unsigned char>(n);
         unsigned *vals = nullptr;
-        rc = sort_hits(c, a, h, n, &vals);
+        rc = sort_hits(c, a, h, n, -1, &vals);
         if (rc) return rc;
         k_gather<<<grid_for(n), GT, 0, s>>>(h, vals, n, so);
-        k_paper<<<grid_for(n), GT, 0, s>>>(so, n, c->cfg.rx, c->cfg.ry, c->cfg.dt_ticks, is_peak, cid, h, out, cap);
+        k_paper<<<grid_for(n), GT, 0, s>>>(so, n, c->cfg.rx, c->cfg.ry, c->cfg.dt_ticks, flags, cid, h, out, cap);
     }
-    // counters of the clustering stage
-    unsigned long long cl = (unsigned long long)ncl;
-    if (cudaMemcpyAsync(&c->ctl->counters[C_CLUSTERS], &cl, 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
     return ck(cudaGetLastError());
 }
 
@@ -805,8 +1353,7 @@ int redo_last(tpx_ctx *c) {
     unsigned status = 0;
     if (!rc) rc = ck(cudaMemcpy(&status, &c->ctl->status, 4, cudaMemcpyDeviceToHost));
     if (!rc && !(status & (ST_TRIG_ORDER | ST_TRIG_CAP))) {
-        rc = cluster_impl(c, h, nh, reinterpret_cast<int64_t *>(hl), hp);
-        if (!rc) rc = centroid_impl(c, h, reinterpret_cast<int64_t *>(hl), hp, nh, L.cl, L.cl_cap, L.n_cl);
+        rc = cluster_all(c, h, nh, reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, -1, L.cl, L.cl_cap, L.n_cl);
         if (!rc && (L.labels || L.is_peak)) {
             if (L.labels) k_fill_ll<<<grid_for(n), GT, 0, s>>>(reinterpret_cast<long long *>(L.labels), n, -1);
             if (L.is_peak && cudaMemsetAsync(L.is_peak, 0, (size_t)n, s) != cudaSuccess) rc = TPX_ECUDA;
@@ -880,7 +1427,7 @@ extern "C" int tpx_summarize(tpx_ctx *c, const uint64_t *pk, int64_t n, tpx_chai
     if (n > 0) {
         const long long tp = c->cfg.wrap_thr_pix_ticks, tt = c->cfg.wrap_thr_tdc_ticks;
         k_tile_agg<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tp, tt, tagg, tcnt);
-        k_tile_prefix<<<1, 1, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, ntr, nullptr, res);
+        k_tile_prefix<<<1, PT, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, ntr, nullptr, res);
         if (cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;

@@ -2,11 +2,14 @@
 //
 // Per submit: the held (open) packets plus the new chunk are decoded by the
 // general path starting from the unwrap state at the held part's start
-// (device-resident); all shots but the last `hold_triggers` are closed and
-// emitted; the unwrap state at the first open shot's trigger packet is
-// computed on the device and the open part is moved to the front of the
-// other pending buffer for the next chunk.  Independent streams run on their
-// own CUDA streams, so chunks of different acquisitions overlap on the GPU.
+// (device-resident); the hits are sorted and clustered, and records are
+// written for the shots that closed (all but the last `hold_triggers`); the
+// unwrap state at the first open shot's trigger packet is computed on the
+// device and the open part is moved to the front of the other pending buffer
+// for the next chunk.  Two host round trips per submit: one for the counts
+// after decoding, one for the record count.  Independent streams run on
+// their own CUDA streams, so chunks of different acquisitions overlap on the
+// GPU.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -58,14 +61,13 @@ struct tpx_stream {
     int64_t index_base = 0;         // stream index of the first pending packet
     int64_t trig_base = 0;          // global index of the first pending trigger
     tpxk::GAgg *st[3] = {nullptr, nullptr, nullptr};   // state at pending start, scratch, next
-    tpx_hits h{}, he{};
+    tpx_hits h{};
     void *dev_mem = nullptr;
-    int64_t *d_counts = nullptr;    // n_hits, n_trig, n_cl, n_emit
-    int64_t *d_trig = nullptr, *d_trig_pos = nullptr, *d_labels = nullptr;
-    uint8_t *d_peak = nullptr;
+    int64_t *d_counts = nullptr;    // n_hits, n_trig, n_cl, emit, p, status
+    int64_t *d_trig = nullptr, *d_trig_pos = nullptr;
     tpx_record *d_cl = nullptr;
-    unsigned *d_flags = nullptr, *d_offs = nullptr, *d_bsum = nullptr;
     Probe *d_probe = nullptr;
+    int64_t *h_counts = nullptr;    // pinned copy of d_counts
     std::vector<Slot> slots;
     uint64_t next_ticket = 1;
     int64_t bytes = 0;
@@ -120,57 +122,15 @@ __global__ void k_state_at(const uint64_t *pk, const long long *t_all, const Pro
     *out = g;
 }
 
-__global__ void k_emit_flags(tpx_hits h, long long n, long long limit, unsigned *flags) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        flags[i] = h.shot[i] < limit;
-}
-__global__ void k_scan_blocks(const unsigned *in, unsigned *out, long long n, unsigned *bsum) {
-    // one block of 256 threads scans 4096 values (16 per thread)
-    __shared__ unsigned ws[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long base = blockIdx.x * 4096LL + threadIdx.x * 16;
-    unsigned mine = 0;
-    for (int j = 0; j < 16; ++j)
-        if (base + j < n) mine += in[base + j];
-    unsigned incl = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) ws[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        unsigned x = lane < 8 ? ws[lane] : 0, xi = x;
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned u = __shfl_up_sync(0xffffffffu, xi, o);
-            if (lane >= o) xi += u;
-        }
-        if (lane < 8) ws[lane] = xi - x;
-        if (lane == 7) bsum[blockIdx.x] = xi;
-    }
-    __syncthreads();
-    unsigned o = ws[w] + incl - mine;
-    for (int j = 0; j < 16; ++j)
-        if (base + j < n) { out[base + j] = o; o += in[base + j]; }
-}
-__global__ void k_scan_bsum(unsigned *bsum, long long nb, long long *total) {
-    unsigned acc = 0;
-    for (long long b = 0; b < nb; ++b) { const unsigned v = bsum[b]; bsum[b] = acc; acc += v; }
-    *total = acc;
-}
-__global__ void k_emit_copy(tpx_hits h, long long n, const unsigned *flags, const unsigned *offs, const unsigned *bsum,
-                            tpx_hits e) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        if (!flags[i]) continue;
-        const long long o = (long long)offs[i] + bsum[i / 4096];
-        e.index[o] = h.index[i];
-        e.shot[o] = h.shot[i];
-        e.t[o] = h.t[i];
-        e.tof[o] = h.tof[i];
-        e.x[o] = h.x[i];
-        e.y[o] = h.y[i];
-        e.tot[o] = h.tot[i];
-    }
+// closed shots and where the open part starts: emit = shots to close,
+// p = position of the first open shot's trigger packet (P when none is open)
+__global__ void k_plan(long long *counts, const long long *trig_pos, long long hold, int finishing, long long P,
+                       const unsigned *status) {
+    const long long ntr = counts[1];
+    const long long emit = finishing ? ntr : (ntr > hold ? ntr - hold : 0);
+    counts[3] = emit;
+    counts[4] = emit < ntr ? trig_pos[emit] : (finishing ? P : 0);
+    counts[5] = (long long)*status;
 }
 
 inline unsigned gridn(long long n) {
@@ -215,26 +175,21 @@ int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, u
                      cudaSuccess)
         return TPX_ECUDA;
     long long *t_all = nullptr;
+    long long *cnt_d = reinterpret_cast<long long *>(S->d_counts);
     rc = tpxg::decode_impl(c, pk, P, S->index_base, S->h, S->cap, S->d_counts, S->d_trig, S->cap, S->d_counts + 1,
                            true, S->st[0], S->st[1], reinterpret_cast<long long *>(S->d_trig_pos), &t_all);
     if (rc) return rc;
-    int64_t cnt[2] = {0, 0};
-    unsigned status = 0;
-    if (cudaMemcpyAsync(cnt, S->d_counts, sizeof cnt, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-    if (cudaMemcpyAsync(&status, &c->ctl->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+    k_plan<<<1, 1, 0, s>>>(cnt_d, reinterpret_cast<long long *>(S->d_trig_pos), S->cfg.hold_triggers, finishing ? 1 : 0,
+                           P, &c->ctl->status);
+    int64_t *hc = S->h_counts;
+    if (cudaMemcpyAsync(hc, S->d_counts, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPX_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-    const int64_t n_hits = cnt[0], ntr = cnt[1];
+    const int64_t n_hits = hc[0], ntr = hc[1], emit = hc[3], p = hc[4];
+    const unsigned status = (unsigned)hc[5];
     if (status & ST_TRIG_ORDER) return TPX_ECORRUPT;
-    const int64_t hold = S->cfg.hold_triggers;
-    const int64_t emit = finishing ? ntr : (ntr > hold ? ntr - hold : 0);
-    // where the open part starts: the trigger packet of the first open shot
-    int64_t p = 0;
-    if (emit >= ntr && finishing) p = P;
-    else if (emit > 0) {
-        if (cudaMemcpyAsync(&p, S->d_trig_pos + emit, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-    }
-    // unwrap state at p (before the decode scratch is reused)
+    if (status & (ST_TRIG_CAP | ST_CLUSTER_CAP)) return TPX_EOVERFLOW;
+    // unwrap state at p, while the decode's per-packet times are still alive
     if (p == P) {
         if (cudaMemcpyAsync(S->st[2], S->st[1], sizeof(GAgg), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TPX_ECUDA;
     } else if (p > 0) {
@@ -244,25 +199,15 @@ int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, u
     } else {
         if (cudaMemcpyAsync(S->st[2], S->st[0], sizeof(GAgg), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TPX_ECUDA;
     }
-    // emitted shots: hits with shot < trig_base + emit, clustered and centroided
-    int64_t n_emit = 0, n_cl = 0;
+    // cluster every hit; records only for the closed shots (shot < limit)
+    int64_t n_cl = 0;
     if (emit > 0 && n_hits > 0) {
-        const long long limit = S->trig_base + emit;
-        k_emit_flags<<<gridn(n_hits), BT, 0, s>>>(S->h, n_hits, limit, S->d_flags);
-        const long long nb = (n_hits + 4095) / 4096;
-        k_scan_blocks<<<(unsigned)nb, 256, 0, s>>>(S->d_flags, S->d_offs, n_hits, S->d_bsum);
-        k_scan_bsum<<<1, 1, 0, s>>>(S->d_bsum, nb, reinterpret_cast<long long *>(S->d_counts + 3));
-        k_emit_copy<<<gridn(n_hits), BT, 0, s>>>(S->h, n_hits, S->d_flags, S->d_offs, S->d_bsum, S->he);
-        if (cudaMemcpyAsync(&n_emit, S->d_counts + 3, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+        rc = tpxg::cluster_all(c, S->h, n_hits, nullptr, nullptr, S->trig_base + emit, ntr, S->d_cl, S->cap,
+                               S->d_counts + 2);
+        if (rc) return rc;
+        if (cudaMemcpyAsync(&hc[2], S->d_counts + 2, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-        if (n_emit > 0) {
-            rc = tpxg::cluster_impl(c, S->he, n_emit, S->d_labels, S->d_peak);
-            if (rc) return rc;
-            rc = tpxg::centroid_impl(c, S->he, S->d_labels, S->d_peak, n_emit, S->d_cl, n_emit, S->d_counts + 2);
-            if (rc) return rc;
-            if (cudaMemcpyAsync(&n_cl, S->d_counts + 2, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-            if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-        }
+        n_cl = hc[2];
     }
     rc = grow_pinned(*sl, n_cl > 0 ? n_cl : 1, emit > 0 ? emit : 1);
     if (rc) return rc;
@@ -316,13 +261,13 @@ int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda
     S->s = static_cast<cudaStream_t>(cuda_stream);
     S->cap = cfg->max_chunk_packets + cfg->max_hold_packets;
     const int64_t C = S->cap;
-    // device memory: pending x2, hits x2, per-hit outputs, records, triggers,
-    // scan scratch, states; plus the general path's scratch in the context
+    // device memory: pending x2, hits, records, triggers, trigger positions,
+    // states, counts; plus the general path's scratch in the context
     const size_t hit_b = al(8 * C) * 3 + al(4 * C) + al(2 * C) + 2 * al(C);
-    const size_t b = 2 * al(8 * (size_t)C) + 2 * hit_b + al(8 * C) + al(C) + al(sizeof(tpx_record) * C) +
-                     2 * al(8 * C) + 2 * al(4 * C) + al(4 * (C / 4096 + 2)) + 3 * al(sizeof(tpxk::GAgg)) +
-                     al(sizeof(Probe)) + al(64);
-    const size_t general = (size_t)C * 110;   // decode / sort / cluster / centroid scratch
+    const size_t b = 2 * al(8 * (size_t)C) + hit_b + al(sizeof(tpx_record) * C) + 2 * al(8 * C) +
+                     3 * al(sizeof(tpxk::GAgg)) + al(sizeof(Probe)) + al(64);
+    size_t general = tpxg::decode_bytes(C);
+    if (tpxg::cluster_bytes(C) > general) general = tpxg::cluster_bytes(C);
     S->bytes = (int64_t)(b + general);
     {
         std::lock_guard<std::mutex> lk(g_budget_mu);
@@ -335,7 +280,9 @@ int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda
     int rc = tpx_create(&S->ctx, &S->cfg.cfg, 0, cuda_stream);
     if (!rc) rc = tpxg::reserve(S->ctx, general);
     if (!rc && cudaMalloc(&S->dev_mem, b) != cudaSuccess) { cudaGetLastError(); rc = TPX_ENOMEM; }
+    if (!rc && cudaMallocHost(&S->h_counts, 8 * sizeof(int64_t)) != cudaSuccess) { cudaGetLastError(); rc = TPX_ENOMEM; }
     if (rc) {
+        if (S->dev_mem) cudaFree(S->dev_mem);
         if (S->ctx) tpx_destroy(S->ctx);
         std::lock_guard<std::mutex> lk(g_budget_mu);
         g_budget_used -= S->bytes;
@@ -346,23 +293,16 @@ int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda
     auto take = [&](size_t bytes) { char *r = m; m += al(bytes); return r; };
     S->pend[0] = reinterpret_cast<uint64_t *>(take(8 * C));
     S->pend[1] = reinterpret_cast<uint64_t *>(take(8 * C));
-    for (tpx_hits *hh : {&S->h, &S->he}) {
-        hh->index = reinterpret_cast<int64_t *>(take(8 * C));
-        hh->shot = reinterpret_cast<int64_t *>(take(8 * C));
-        hh->t = reinterpret_cast<int64_t *>(take(8 * C));
-        hh->tof = reinterpret_cast<int32_t *>(take(4 * C));
-        hh->tot = reinterpret_cast<uint16_t *>(take(2 * C));
-        hh->x = reinterpret_cast<uint8_t *>(take(C));
-        hh->y = reinterpret_cast<uint8_t *>(take(C));
-    }
-    S->d_labels = reinterpret_cast<int64_t *>(take(8 * C));
-    S->d_peak = reinterpret_cast<uint8_t *>(take(C));
+    S->h.index = reinterpret_cast<int64_t *>(take(8 * C));
+    S->h.shot = reinterpret_cast<int64_t *>(take(8 * C));
+    S->h.t = reinterpret_cast<int64_t *>(take(8 * C));
+    S->h.tof = reinterpret_cast<int32_t *>(take(4 * C));
+    S->h.tot = reinterpret_cast<uint16_t *>(take(2 * C));
+    S->h.x = reinterpret_cast<uint8_t *>(take(C));
+    S->h.y = reinterpret_cast<uint8_t *>(take(C));
     S->d_cl = reinterpret_cast<tpx_record *>(take(sizeof(tpx_record) * C));
     S->d_trig = reinterpret_cast<int64_t *>(take(8 * C));
     S->d_trig_pos = reinterpret_cast<int64_t *>(take(8 * C));
-    S->d_flags = reinterpret_cast<unsigned *>(take(4 * C));
-    S->d_offs = reinterpret_cast<unsigned *>(take(4 * C));
-    S->d_bsum = reinterpret_cast<unsigned *>(take(4 * (C / 4096 + 2)));
     for (int i = 0; i < 3; ++i) S->st[i] = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg)));
     S->d_probe = reinterpret_cast<Probe *>(take(sizeof(Probe)));
     S->d_counts = reinterpret_cast<int64_t *>(take(64));
@@ -427,6 +367,7 @@ int tpx_stream_destroy(tpx_stream *S) {
         if (sl.h_trig) cudaFreeHost(sl.h_trig);
     }
     if (S->dev_mem) cudaFree(S->dev_mem);
+    if (S->h_counts) cudaFreeHost(S->h_counts);
     if (S->ctx) tpx_destroy(S->ctx);
     {
         std::lock_guard<std::mutex> lk(g_budget_mu);

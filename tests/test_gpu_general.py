@@ -76,6 +76,17 @@ def test_unfused_dense_random(mode, seed):
     check_unfused(pk, rx=rx, ry=ry, dt=dt, mode=mode, lut=lut)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_unfused_segments_longer_than_a_warp_buffer(mode):
+    """Hits closer than dt chain into time segments of several hundred hits:
+    beyond one warp's shared buffer, so the global-memory kernels take them,
+    next to short segments in the same call."""
+    rng = np.random.default_rng(31 + mode)
+    pk = random_dense_stream(rng, n_shots=12, per_shot=700, area=10, t_spread=80).packets()
+    check_unfused(pk, mode=mode, dt=4)
+    check_unfused(pk, mode=mode, dt=40)
+
+
 def test_unfused_large_slice():
     pk = synth.generate(synth.large(n_shots=150))[0]
     check_unfused(pk)
