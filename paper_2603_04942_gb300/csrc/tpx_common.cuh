@@ -78,5 +78,15 @@ __device__ __forceinline__ GAgg warp_incl_scan(GAgg v, int lane, long long tp, l
     return v;
 }
 
+// Sec. V.C centre of mass and ToT-weighted ToF from the exact integer
+// moments: one reciprocal of S_tot, then products (each within a few ulp of
+// the quotient; S_tot = 0 gives NaN, as 0/0 does)
+__device__ __forceinline__ void com_from_moments(long long s_x, long long s_y, long long s_t, long long s_tot,
+                                                 long long tof0, double *x, double *y, double *tof) {
+    const double r = 1.0 / (double)s_tot;
+    *x = (double)s_x * r;
+    *y = (double)s_y * r;
+    *tof = (double)tof0 + (double)s_t * r;
+}
 
 }  // namespace tpxk

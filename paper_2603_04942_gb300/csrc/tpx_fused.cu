@@ -785,9 +785,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 o.t0 = S.tdc_t[seg] + tofc0;
                 o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
                 o.n = n; o.n_peaks = npk;
-                o.x = (double)s_x / (double)s_tot;
-                o.y = (double)s_y / (double)s_tot;
-                o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
+                com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
                 p.clusters[O + i] = o;
             }
         } else {
@@ -842,9 +840,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 o.t0 = S.tdc_t[sg] + tofc0;
                 o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
                 o.n = (int)n; o.n_peaks = 1;
-                o.x = (double)s_x / (double)s_tot;
-                o.y = (double)s_y / (double)s_tot;
-                o.tof = (double)tofc0 + (double)s_t / (double)s_tot;
+                com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
                 p.clusters[O + i] = o;
             }
         }

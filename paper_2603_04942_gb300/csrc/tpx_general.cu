@@ -983,9 +983,7 @@ __global__ void k_final(tpx_hits h, long long n, const unsigned *flags, const un
         o.t0 = h.t[i];
         o.s_tot = (long long)a.s_tot; o.s_x = (long long)a.s_x; o.s_y = (long long)a.s_y; o.s_t = (long long)a.s_t;
         o.n = (int)a.n; o.n_peaks = (int)a.npk;
-        o.x = (double)o.s_x / (double)o.s_tot;
-        o.y = (double)o.s_y / (double)o.s_tot;
-        o.tof = (double)h.tof[i] + (double)o.s_t / (double)o.s_tot;
+        com_from_moments(o.s_x, o.s_y, o.s_t, o.s_tot, h.tof[i], &o.x, &o.y, &o.tof);
         out[c] = o;
     }
 }
@@ -1022,9 +1020,7 @@ __global__ void k_paper(Sorted s, long long n, int rx, int ry, int dt, const uns
         o.t0 = h.t[hi] - h.tof[hi] + tofc0;
         o.s_tot = st; o.s_x = sx; o.s_y = sy; o.s_t = a2 - (long long)tmin * st;
         o.n = (int)m; o.n_peaks = 1;
-        o.x = (double)sx / (double)st;
-        o.y = (double)sy / (double)st;
-        o.tof = (double)tofc0 + (double)o.s_t / (double)st;
+        com_from_moments(sx, sy, o.s_t, st, tofc0, &o.x, &o.y, &o.tof);
         out[c] = o;
     }
 }
@@ -1038,13 +1034,17 @@ __global__ void k_count_from_scan(const unsigned *flags, const unsigned *cid, lo
     if (counter) *counter = (unsigned long long)m;
 }
 
-// CC records from the per-root moments (root hit positions carry the flag)
-__global__ void k_records(tpx_hits h, long long n, const unsigned *rflag, const unsigned *cid, const AccH *acc,
-                          tpx_record *out, long long cap) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        if (!rflag[i]) continue;
-        const long long c = cid[i];
-        if (c >= cap) continue;
+// position of every record's root hit, in record (label) order
+__global__ void k_root_list(const unsigned *rflag, const unsigned *cid, long long n, long long cap, unsigned *rootpos) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (rflag[i] && cid[i] < cap) rootpos[cid[i]] = (unsigned)i;
+}
+// CC records from the per-root moments, one thread per record
+__global__ void k_records(tpx_hits h, const long long *n_rec, long long cap, const unsigned *rootpos, const AccH *acc,
+                          tpx_record *out) {
+    const long long m = min(*n_rec, cap);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < m; c += (long long)gridDim.x * blockDim.x) {
+        const long long i = rootpos[c];
         const AccH a = acc[i];
         tpx_record o;
         o.label = h.index[i];
@@ -1052,9 +1052,7 @@ __global__ void k_records(tpx_hits h, long long n, const unsigned *rflag, const 
         o.t0 = h.t[i];
         o.s_tot = a.s_tot; o.s_x = a.s_x; o.s_y = a.s_y; o.s_t = a.s_t;
         o.n = (int)a.n; o.n_peaks = (int)a.npk;
-        o.x = (double)o.s_x / (double)o.s_tot;
-        o.y = (double)o.s_y / (double)o.s_tot;
-        o.tof = (double)h.tof[i] + (double)o.s_t / (double)o.s_tot;
+        com_from_moments(o.s_x, o.s_y, o.s_t, o.s_tot, h.tof[i], &o.x, &o.y, &o.tof);
         out[c] = o;
     }
 }
@@ -1251,9 +1249,12 @@ int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8
     if (rc) return rc;
     k_count_from_scan<<<1, 1, 0, s>>>(rflag, cid, n, reinterpret_cast<long long *>(d_n_clusters), cap,
                                       &c->ctl->status, &c->ctl->counters[C_CLUSTERS]);
-    if (cc)
-        k_records<<<grid_for(n), GT, 0, s>>>(h, n, rflag, cid, acc, out, cap);
-    else
+    if (cc) {
+        unsigned *rootpos = segf;   // free again: the segments are done
+        k_root_list<<<grid_for(n), GT, 0, s>>>(rflag, cid, n, cap, rootpos);
+        k_records<<<grid_for(n / 16 + 1), GT, 0, s>>>(h, reinterpret_cast<const long long *>(d_n_clusters), cap, rootpos,
+                                                     acc, out);
+    } else
         k_paper<<<grid_for(n), GT, 0, s>>>(so, n, c->cfg.rx, c->cfg.ry, dt, rflag, cid, h, out, cap);
     return ck(cudaGetLastError());
 }
