@@ -18,6 +18,7 @@ struct tpx_ctx {
     unsigned seq;
     tpxk::TileScratch ts;
     void *scratch;            // one allocation for all tile records
+    tpx_record *stage;        // fused-kernel record staging (inside scratch)
     tpxk::Ctl *ctl;           // device control block
     tpxk::Ctl *h_ctl;         // pinned host copy
     // device staging for tpx_process_host

@@ -112,6 +112,9 @@ struct __align__(16) Smem {
     unsigned long long cnt[C_NUM];
     long long tile;
     long long clo;
+    long long pend_tile;          // staged records awaiting their offset (-1: none)
+    long long pend_ntr;
+    int pend_ncl;
     int first_tdc;
     int la_first;
     unsigned status;
@@ -190,24 +193,53 @@ __device__ __forceinline__ GChain shfl_down_chain(const GChain &v, int o) {
     return u;
 }
 
-// Bounded decoupled look-back over the unwrap chains, one warp: each trip
-// reads the flags of 32 predecessors at once, combines the aggregates in
-// stream order up to the nearest inclusive prefix, and stops there.
-// Called by all lanes of one warp; every lane returns the exclusive prefix.
-__device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
+// Bounded decoupled look-back, one warp. Each trip reads the flags of
+// 32 * LB predecessors at once (lane l holds tiles hi - LB*l - j, j = 0 the
+// latest), waits only for the tiles from hi down to the nearest inclusive
+// prefix, and combines them in stream order. Two dependent L2 round trips
+// per trip (flags, then values), so wide trips keep the chain short.
+// (LB = 1 for the 64-byte chain aggregates: the 64-register budget of a
+// 1024-thread CTA keeps only one in flight per lane; LB = 4 for counts.)
+constexpr int LBA = 1, LBC = 4;
+
+// per lane: which of its LB tiles are needed this trip, given the flags
+struct LbScan { unsigned need, inc; int stop; bool ok; };
+template <int LB>
+__device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, unsigned seq) {
+    const int lane = threadIdx.x & 31;
+    unsigned rdy = 0, inc = 0;
+#pragma unroll
+    for (int j = 0; j < LB; ++j) {
+        const long long q = hi - LB * lane - j;
+        if (q < 0) { rdy |= 1u << j; continue; }
+        const unsigned f = ld_acquire(&flags[q]);
+        if ((f >> 2) == seq && (f & 3u)) {
+            rdy |= 1u << j;
+            if ((f & 3u) == 2u) inc |= 1u << j;
+        }
+    }
+    const unsigned im = __ballot_sync(0xffffffffu, inc != 0);
+    LbScan r;
+    r.stop = im ? __ffs(im) - 1 : 31;
+    r.inc = inc;
+    const unsigned all = (1u << LB) - 1u;
+    r.need = lane < r.stop ? all : (lane == r.stop ? (inc ? ((inc & (0u - inc)) << 1) - 1u : all) : 0u);
+    r.ok = (rdy & r.need) == r.need;
+    return r;
+}
+
+// buf: 32 GAgg slots in shared memory, free while the look-back runs. The
+// combine is a tree over the slots (few live registers: the kernel runs at
+// the 64-register limit of a 1024-thread CTA). Lane 0 returns the prefix.
+__device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq, unsigned *status, GAgg *buf) {
     const int lane = threadIdx.x & 31;
     GAgg acc = agg_id();
-    for (long long hi = tile - 1; hi >= 0; hi -= 32) {
-        const long long q = hi - lane;
-        unsigned f = 0;
+    for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBA) {
+        LbScan sc;
         long long spins = 0;
         for (;;) {
-            bool ready = true;
-            if (q >= 0) {
-                f = ld_acquire(&p.ts.flags[q]);
-                ready = (f >> 2) == seq && (f & 3u);
-            }
-            if (__all_sync(0xffffffffu, ready)) break;
+            sc = lb_scan<LBA>(p.ts.flags, hi, seq);
+            if (__all_sync(0xffffffffu, sc.ok)) break;
             if (++spins > MAX_SPIN || timed_out(p)) {
                 if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
                 *status |= ST_DEVTIMEOUT;
@@ -215,31 +247,26 @@ __device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq,
             }
             __nanosleep(64);
         }
-        const unsigned pm = __ballot_sync(0xffffffffu, q >= 0 && (f & 3u) == 2u);
-        const int stop = pm ? __ffs(pm) - 1 : 31;
-        GAgg v = agg_id();
-        if (q >= 0 && lane <= stop) v = ld_agg((pm && lane == stop) ? &p.ts.pre[q] : &p.ts.agg[q]);
-        // lane L holds tile hi-L: combine earlier tiles (higher lanes) on the left
+        // lane l: its needed tile (an inclusive prefix, if present, is the
+        // earliest needed one), or the identity
+        {
+            const long long q = hi - lane;
+            const ulonglong2 *src = nullptr;
+            if (q >= 0 && (sc.need & 1u)) src = reinterpret_cast<const ulonglong2 *>((sc.inc & 1u) ? &p.ts.pre[q] : &p.ts.agg[q]);
+            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&buf[lane]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dst[k] = src ? __ldcg(src + k) : make_ulonglong2(0ull, 0ull);
+        }
+        __syncwarp();
+        // lane l + o holds earlier tiles than lane l: combine it on the left
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            GAgg u;
-            u.pix = shfl_down_chain(v.pix, o);
-            u.tdc = shfl_down_chain(v.tdc, o);
-            if (lane + o < 32) v = acomb(u, v, p.thr_pix, p.thr_tdc);
+            if ((lane & (2 * o - 1)) == 0) buf[lane] = acomb(buf[lane + o], buf[lane], p.thr_pix, p.thr_tdc);
+            __syncwarp();
         }
-        GAgg r;
-        r.pix = shfl_down_chain(v.pix, 0);
-        r.tdc = shfl_down_chain(v.tdc, 0);
-        r.pix.n = __shfl_sync(0xffffffffu, v.pix.n, 0);
-        r.pix.first = __shfl_sync(0xffffffffu, v.pix.first, 0);
-        r.pix.last = __shfl_sync(0xffffffffu, v.pix.last, 0);
-        r.pix.sum = __shfl_sync(0xffffffffu, v.pix.sum, 0);
-        r.tdc.n = __shfl_sync(0xffffffffu, v.tdc.n, 0);
-        r.tdc.first = __shfl_sync(0xffffffffu, v.tdc.first, 0);
-        r.tdc.last = __shfl_sync(0xffffffffu, v.tdc.last, 0);
-        r.tdc.sum = __shfl_sync(0xffffffffu, v.tdc.sum, 0);
-        acc = acomb(r, acc, p.thr_pix, p.thr_tdc);
-        if (pm) break;
+        if (lane == 0) acc = acomb(buf[0], acc, p.thr_pix, p.thr_tdc);
+        __syncwarp();
+        if (__any_sync(0xffffffffu, sc.inc != 0)) break;
     }
     return acc;
 }
@@ -248,17 +275,12 @@ __device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq,
 __device__ long long lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
     const int lane = threadIdx.x & 31;
     long long acc = 0;
-    for (long long hi = tile - 1; hi >= 0; hi -= 32) {
-        const long long q = hi - lane;
-        unsigned f = 0;
+    for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBC) {
+        LbScan sc;
         long long spins = 0;
         for (;;) {
-            bool ready = true;
-            if (q >= 0) {
-                f = ld_acquire(&p.ts.cflags[q]);
-                ready = (f >> 2) == seq && (f & 3u);
-            }
-            if (__all_sync(0xffffffffu, ready)) break;
+            sc = lb_scan<LBC>(p.ts.cflags, hi, seq);
+            if (__all_sync(0xffffffffu, sc.ok)) break;
             if (++spins > MAX_SPIN || timed_out(p)) {
                 if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
                 *status |= ST_DEVTIMEOUT;
@@ -266,14 +288,17 @@ __device__ long long lookback_count_warp(const Params &p, long long tile, unsign
             }
             __nanosleep(64);
         }
-        const unsigned pm = __ballot_sync(0xffffffffu, q >= 0 && (f & 3u) == 2u);
-        const int stop = pm ? __ffs(pm) - 1 : 31;
         long long v = 0;
-        if (q >= 0 && lane <= stop) v = __ldcg((pm && lane == stop) ? &p.ts.cpre[q] : &p.ts.cagg[q]);
+#pragma unroll
+        for (int j = 0; j < LBC; ++j) {
+            const long long q = hi - LBC * lane - j;
+            if (q < 0 || !((sc.need >> j) & 1u)) continue;
+            v += __ldcg(((sc.inc >> j) & 1u) ? &p.ts.cpre[q] : &p.ts.cagg[q]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         acc += v;
-        if (pm) break;
+        if (__any_sync(0xffffffffu, sc.inc != 0)) break;
     }
     return acc;
 }
@@ -294,8 +319,51 @@ __device__ void unite_one(const Smem &S, uint32_t pbase, uint32_t a, uint32_t b)
     }
 }
 
+// Warp 0 resolves the record offset of tile tl holding nc records (decoupled
+// look-back over the counts), publishes its inclusive count and, for the last
+// tile, the call's totals; the offset is left in S.clo.
+__device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr) {
+    if (threadIdx.x >= 32) return;
+    unsigned st2 = 0;
+    long long Ow = 0;
+    if (tl > 0) Ow = lookback_count_warp(p, tl, seq, &st2);
+    if (threadIdx.x == 0) {
+        if (tl > 0) {
+            __stcg(&p.ts.cpre[tl], Ow + (long long)nc);
+            st_release(&p.ts.cflags[tl], (seq << 2) | 2u);
+        }
+        S.clo = Ow;
+        if (st2) atomicOr(&S.status, st2);
+        if (tl == p.n_tiles - 1) {
+            *p.n_clusters = Ow + nc;
+            *p.n_trig = ntr;
+            if (Ow + nc > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
+            if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
+        }
+    }
+}
+
+// Staged output: a tile's records wait in the CTA's staging slot until the
+// next tile (or the end of the kernel) resolves their offset, when the
+// predecessors' counts are long published; then one coalesced copy.
+__device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
+    const long long pt = S.pend_tile;
+    if (pt < 0) return;
+    const int nc = S.pend_ncl;
+    resolve_offset(S, p, seq, pt, nc, S.pend_ntr);
+    __syncthreads();
+    const long long O = S.clo;
+    const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
+    constexpr int WPR = (int)(sizeof(tpx_record) / 8);
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
+    for (long long w = threadIdx.x; w < keep * WPR; w += NT) dst[w] = __ldcg(src + w);
+    __syncthreads();
+    if (threadIdx.x == 0) S.pend_tile = -1;
+}
+
 // ------------------------------------------------------------------- kernel
-template <int MODE>
+template <int MODE, bool STAGED>
 __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -303,6 +371,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
     const long long tp = p.thr_pix, tt = p.thr_tdc;
     const unsigned seq = p.seq & 0x3FFFFFFFu;
     const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(S.parent);
+    if (tid == 0) S.pend_tile = -1;
 
     for (;;) {
         __syncthreads();
@@ -314,7 +383,13 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         if (tid < C_NUM) S.cnt[tid] = 0;
         __syncthreads();
         const long long tile = S.tile;
-        if (tile >= p.n_tiles) break;
+        if (tile >= p.n_tiles) {
+            if (STAGED) {
+                flush_pending(S, p, seq);
+                if (tid == 0 && S.status) atomicOr(&p.ctl->status, S.status);
+            }
+            break;
+        }
         const long long base = tile * T;
         const int cnt = (int)min((long long)T, p.n - base);
 
@@ -420,7 +495,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
         if (tid < 32) {
             unsigned stl = 0;
             GAgg Ew = agg_id();
-            if (tile > 0) Ew = lookback_agg_warp(p, tile, seq, &stl);
+            if (tile > 0) Ew = lookback_agg_warp(p, tile, seq, &stl, S.warp_agg);
             else Ew = p.E0 ? *p.E0 : agg_id();
             if (tid == 0) {
                 if (tile > 0) {
@@ -707,28 +782,20 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 st_release(&p.ts.cflags[0], (seq << 2) | 2u);
             }
         }
-        // warp 0 resolves the record offset of this tile (decoupled look-back)
-        auto resolve_offset = [&]() {
-            if (tid < 32) {
-                unsigned st2 = 0;
-                long long Ow = 0;
-                if (tile > 0) Ow = lookback_count_warp(p, tile, seq, &st2);
-                if (tid == 0) {
-                    if (tile > 0) {
-                        __stcg(&p.ts.cpre[tile], Ow + (long long)ncl);
-                        st_release(&p.ts.cflags[tile], (seq << 2) | 2u);
-                    }
-                    S.clo = Ow;
-                    if (st2) atomicOr(&S.status, st2);
-                    if (tile == p.n_tiles - 1) {
-                        const long long ntr = E.tdc.n - trig_base + (long long)S.cnt[C_TDCS];
-                        *p.n_clusters = Ow + ncl;
-                        *p.n_trig = ntr;
-                        if (Ow + ncl > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
-                        if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
-                    }
-                }
+        const long long ntr_here = E.tdc.n - trig_base + (long long)S.cnt[C_TDCS];
+        // records go to the CTA's staging slot (STAGED) or straight to their
+        // offset after an inline look-back
+        auto record_target = [&](long long *lim) -> tpx_record * {
+            if (STAGED) {
+                flush_pending(S, p, seq);
+                __syncthreads();   // the member lists / peak list are complete
+                *lim = C;
+                return p.stage + (long long)blockIdx.x * C;
             }
+            resolve_offset(S, p, seq, tile, ncl, ntr_here);
+            __syncthreads();
+            *lim = p.cl_cap - S.clo;
+            return p.clusters + S.clo;
         };
 
         if (MODE == TPX_MODE_CC) {
@@ -755,13 +822,12 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             }
             c_pk = warp_sum(c_pk);
             if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
-            resolve_offset();
-            __syncthreads();
-            const long long O = S.clo;
+            long long lim = 0;
+            tpx_record *dst = record_target(&lim);
             // records: one thread per cluster walks its member list and forms
             // the exact integer moments in registers (Sec. V.C)
             for (int i = tid; i < ncl; i += NT) {
-                if (O + i >= p.cl_cap) break;
+                if (i >= lim) break;
                 const int q = rootpos[i];
                 const uint64_t r = S.buf[pad(q)];
                 const int tofb0 = r_tof(r);
@@ -786,7 +852,7 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
                 o.n = n; o.n_peaks = npk;
                 com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                p.clusters[O + i] = o;
+                dst[i] = o;
             }
         } else {
             unsigned long long c_pk = 0;
@@ -804,12 +870,11 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
             }
             c_pk = warp_sum(c_pk);
             if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
-            resolve_offset();
-            __syncthreads();
-            const long long O = S.clo;
+            long long lim = 0;
+            tpx_record *dst = record_target(&lim);
             // records: box neighbourhood sums of each local maximum (Sec. V.C)
             for (int i = tid; i < ncl; i += NT) {
-                if (O + i >= p.cl_cap) break;
+                if (i >= lim) break;
                 const int q = (int)S.parent[i];
                 const uint64_t r = S.buf[pad(q)];
                 const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
@@ -841,10 +906,17 @@ __global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
                 o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
                 o.n = (int)n; o.n_peaks = 1;
                 com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                p.clusters[O + i] = o;
+                dst[i] = o;
             }
         }
-        if (tid == 0) S.cnt[C_CLUSTERS] = (unsigned long long)ncl;
+        if (tid == 0) {
+            S.cnt[C_CLUSTERS] = (unsigned long long)ncl;
+            if (STAGED) {
+                S.pend_tile = tile;
+                S.pend_ncl = ncl;
+                S.pend_ntr = ntr_here;
+            }
+        }
         __syncthreads();
         if (tid < C_NUM && tid != C_PACKETS && S.cnt[tid]) atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
         if (tid == 0) {
@@ -858,25 +930,25 @@ int fused_tile_packets() { return T; }
 int fused_threads() { return NT; }
 int fused_smem_bytes() { return (int)sizeof(Smem); }
 
-cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s) {
-    static bool attr_done[2] = {false, false};
+template <int MODE, bool STAGED>
+cudaError_t launch_one(const Params &p, int grid, cudaStream_t s) {
+    static bool attr_done = false;
     const int smem = (int)sizeof(Smem);
-    if (mode == TPX_MODE_CC) {
-        if (!attr_done[0]) {
-            cudaError_t e = cudaFuncSetAttribute(fused_kernel<TPX_MODE_CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            attr_done[0] = true;
-        }
-        fused_kernel<TPX_MODE_CC><<<grid, NT, smem, s>>>(p);
-    } else {
-        if (!attr_done[1]) {
-            cudaError_t e = cudaFuncSetAttribute(fused_kernel<TPX_MODE_PAPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            attr_done[1] = true;
-        }
-        fused_kernel<TPX_MODE_PAPER><<<grid, NT, smem, s>>>(p);
+    if (!attr_done) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fused_kernel<MODE, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
     }
+    fused_kernel<MODE, STAGED><<<grid, NT, smem, s>>>(p);
     return cudaGetLastError();
 }
+
+cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s) {
+    if (mode == TPX_MODE_CC) return p.stage ? launch_one<TPX_MODE_CC, true>(p, grid, s) : launch_one<TPX_MODE_CC, false>(p, grid, s);
+    return p.stage ? launch_one<TPX_MODE_PAPER, true>(p, grid, s) : launch_one<TPX_MODE_PAPER, false>(p, grid, s);
+}
+
+int fused_range_capacity() { return C; }
 
 }  // namespace tpxk

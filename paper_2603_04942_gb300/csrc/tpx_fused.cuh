@@ -92,6 +92,8 @@ struct Params {
     unsigned int seq;
     TileScratch ts;
     Ctl *ctl;
+    tpx_record *stage;       // per-CTA record staging (range-capacity records per
+                             // CTA of the grid), or NULL: inline offset look-back
     const GAgg *E0;          // unwrap state before the call (NULL: stream start)
     GAgg *state_out;         // state after the call, written by the last tile (or NULL)
 };
@@ -103,5 +105,6 @@ namespace tpxk {
 int fused_tile_packets();
 int fused_smem_bytes();
 int fused_threads();
+int fused_range_capacity();
 cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s);
 }  // namespace tpxk

@@ -36,6 +36,7 @@ int check_cfg(const tpx_config *c) {
 void free_scratch(tpx_ctx *c) {
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
+    c->stage = nullptr;
     std::memset(&c->ts, 0, sizeof c->ts);
     c->max_tiles = 0;
 }
@@ -47,7 +48,10 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_flags = al(sizeof(unsigned) * tiles), b_agg = al(sizeof(tpxk::GAgg) * tiles),
                  b_cnt = al(sizeof(long long) * tiles);
-    const size_t total = 2 * b_flags + 2 * b_agg + 2 * b_cnt;
+    // record staging of the fused kernel: one range's records per CTA
+    const int64_t ctas = tiles < c->num_sms ? tiles : c->num_sms;   // the largest grid of a call
+    const size_t b_stage = al(sizeof(tpx_record) * (size_t)tpxk::fused_range_capacity() * (size_t)ctas);
+    const size_t total = 2 * b_flags + 2 * b_agg + 2 * b_cnt + b_stage;
     void *mem = nullptr;
     if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
     if (cudaMemset(mem, 0, total) != cudaSuccess) { cudaFree(mem); return TPX_ECUDA; }
@@ -57,7 +61,8 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
     c->ts.agg = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
     c->ts.pre = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
     c->ts.cagg = reinterpret_cast<long long *>(p); p += b_cnt;
-    c->ts.cpre = reinterpret_cast<long long *>(p);
+    c->ts.cpre = reinterpret_cast<long long *>(p); p += b_cnt;
+    c->stage = reinterpret_cast<tpx_record *>(p);
     c->scratch = mem;
     c->max_tiles = tiles;
     c->max_packets = tiles * T;
@@ -234,6 +239,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.ctl = c->ctl;
     p.E0 = E0;
     p.state_out = state_out;
+    p.stage = c->stage;
     int64_t grid = c->num_sms;   // persistent: one CTA per SM
     if (grid > p.n_tiles) grid = p.n_tiles;
     cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, (int)grid, c->stream);
