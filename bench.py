@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-shots", type=int, default=50_000)
     ap.add_argument("--ref-shots", type=int, default=10_000)
+    ap.add_argument("--tile", choices=["default", "4096", "2048"], default="default",
+                    help="fused-kernel tile geometry (speed only; results are identical)")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-only", action="store_true")
     ap.add_argument("--stream-chunks", type=int, default=150)
@@ -300,7 +302,8 @@ def main():
     hits = int(((h_pk.numpy().view(np.uint64) >> np.uint64(60)) == 0xB).sum())
     d_pk = h_pk.to("cuda", non_blocking=False)
 
-    ctx = tpx.Context(tpx.Config(), max_packets=n)
+    tile = {"default": tpx.TILE_DEFAULT, "4096": tpx.TILE_4096, "2048": tpx.TILE_2048}[args.tile]
+    ctx = tpx.Context(tpx.Config(tile_geometry=tile), max_packets=n)
     cl_cap = max(1024, n // 16)
     out = ctx.alloc_outputs(n, labels=True, is_peak=False, cluster_capacity=cl_cap,
                             trig_capacity=args.shots + 16)
@@ -312,6 +315,7 @@ def main():
         raise SystemExit(f"tpx_process failed in warm-up: {rc} {counters}")
     n_cl = int(out["n_clusters"].item())
     n_tr = int(out["n_trig"].item())
+    tuning = ctx.tpx_tuning()
 
     if world > 1:
         dist.barrier()
@@ -396,6 +400,10 @@ def main():
                            "clusters_per_gpu": n_cl, "shots_per_gpu": n_tr,
                            "l2": "inputs larger than L2 (10 GB packet stream per step)",
                            "parallelism": f"{world} independent shot ranges" if world > 1 else "1 GPU",
+                           "tile_geometry": {1: "4096-packet tiles, 1024-thread CTAs",
+                                             2: "2048-packet tiles, 2 x 512-thread CTAs per SM"}.get(
+                               tuning["tile_geometry"], "sampling"),
+                           "tile_choice": "autotuned in warm-up" if args.tile == "default" else "fixed by --tile",
                            "generation_s": round(t_gen, 1)},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "clocks": clk,
                 "gpu_launches": args.steps,

@@ -75,7 +75,20 @@ typedef struct tpx_config {
                                    fed in consecutive calls, each starting at
                                    a trigger packet); 0: each call starts a
                                    new stream unless tpx_set_state was used   */
+    int32_t tile_geometry;      /* fused kernel tiles: TPX_TILE_4096 (1024-
+                                   thread CTAs, one per SM, ranges of up to
+                                   8192 positions), TPX_TILE_2048 (512-thread
+                                   CTAs, two per SM, up to 4096 positions),
+                                   or TPX_TILE_DEFAULT (the library's choice,
+                                   TPX_TILE_4096).  Not a paper parameter:
+                                   results are identical, only speed and the
+                                   range limit differ.                        */
+    int32_t reserved;           /* zero                                       */
 } tpx_config;
+
+#define TPX_TILE_DEFAULT 0
+#define TPX_TILE_4096 1
+#define TPX_TILE_2048 2
 
 /* One particle hit.  CC mode: one record per connected component; PAPER
    mode: one record per local maximum, summed over its box neighbourhood
@@ -251,6 +264,21 @@ int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t
                         uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cluster_capacity,
                         int64_t *d_n_clusters, int64_t *d_trig_t, int64_t trig_capacity,
                         int64_t *d_n_trig, tpx_counters *h_counters);
+
+/* Tile-geometry autotuner (not in the paper).  With tile_geometry =
+   TPX_TILE_DEFAULT the first calls of at least 2^20 packets alternate the
+   two geometries, timed with CUDA events on the context stream; at the
+   tpx_sync after both have run, the faster one per packet is kept for the
+   context (a call that had to be redone by the general path counts as the
+   slowest).  Results do not depend on the geometry.
+     tile_geometry    out: TPX_TILE_4096 / TPX_TILE_2048 once chosen (or the
+                      geometry fixed by the configuration), TPX_TILE_DEFAULT
+                      while sampling
+     ms_per_mpacket   out, may be NULL: [2] the best times seen, ms per 10^6
+                      packets, for the 4096- and the 2048-packet tiles (0 if
+                      not sampled)
+   TPX_EINVAL for NULL ctx or tile_geometry. */
+int tpx_tuning(tpx_ctx *ctx, int32_t *tile_geometry, double *ms_per_mpacket);
 
 /* The next tpx_process / tpx_decode on the context starts from *state
    (NULL: the start of a stream).  Asynchronous on the context stream. */

@@ -22,6 +22,7 @@ __all__ = ["Config", "Context", "CLUSTER_DTYPE", "TpxError", "lib", "load", "MOD
 
 MODE_CC = 0
 MODE_PAPER = 1
+TILE_DEFAULT, TILE_4096, TILE_2048 = 0, 1, 2
 TICK_NS = 1.5625
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ECORRUPT, EAGAIN, ETIMEOUT, EDEVTIMEOUT, ECUDA, EUNSUPPORTED = \
@@ -38,7 +39,7 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_centroid", "tpx_tuning", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_strerror", "tpx_version")
 
@@ -47,7 +48,8 @@ class _CConfig(ctypes.Structure):
     _fields_ = [("rx", ctypes.c_int32), ("ry", ctypes.c_int32), ("dt_ticks", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("tof_max_ticks", ctypes.c_int64),
                 ("wrap_thr_pix_ticks", ctypes.c_int64), ("wrap_thr_tdc_ticks", ctypes.c_int64),
-                ("d_timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32), ("chain", ctypes.c_int32)]
+                ("d_timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32), ("chain", ctypes.c_int32),
+                ("tile_geometry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 STATE_FIELDS = ("pixels", "pix_last_raw", "pix_wraps", "triggers", "tdc_last_raw", "tdc_wraps")
@@ -104,6 +106,7 @@ class Config:
     timewalk_lut: object = None        # torch int16 tensor of 1024 on the device, or None
     strict: bool = False
     chain: bool = False                # each call continues where the previous one ended
+    tile_geometry: int = 0             # TILE_DEFAULT, TILE_4096 or TILE_2048 (speed only)
 
 
 _lock = threading.Lock()
@@ -132,6 +135,7 @@ def load(path: str | None = None):
         L.tpx_strerror.argtypes = [i32]
         L.tpx_strerror.restype = ctypes.c_char_p
         L.tpx_version.restype = ctypes.c_char_p
+        L.tpx_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_set_state.restype = i32
@@ -179,7 +183,7 @@ class Context:
             assert self._lut.dtype == torch.int16 and self._lut.numel() == 1024 and self._lut.is_cuda
         c = _CConfig(self.cfg.rx, self.cfg.ry, self.cfg.dt_ticks, self.cfg.mode, self.cfg.tof_max_ticks,
                      self.cfg.wrap_thr_pix_ticks, self.cfg.wrap_thr_tdc_ticks, _ptr(self._lut),
-                     int(self.cfg.strict), int(self.cfg.chain))
+                     int(self.cfg.strict), int(self.cfg.chain), int(self.cfg.tile_geometry), 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         rc = lib().tpx_create(ctypes.byref(h), ctypes.byref(c), int(max_packets), ctypes.c_void_p(self.stream.cuda_stream))
@@ -191,6 +195,16 @@ class Context:
         rc = lib().tpx_reserve(self._h, int(max_packets))
         if rc:
             raise TpxError(rc, "tpx_reserve")
+
+    def tpx_tuning(self) -> dict:
+        """The tile geometry in use (0 while the autotuner samples) and the
+        best measured ms per 10^6 packets of the 4096- and 2048-packet tiles."""
+        g = ctypes.c_int32(0)
+        ms = (ctypes.c_double * 2)()
+        rc = lib().tpx_tuning(self._h, ctypes.byref(g), ms)
+        if rc:
+            raise TpxError(rc, "tpx_tuning")
+        return {"tile_geometry": int(g.value), "ms_per_mpacket": {"4096": ms[0], "2048": ms[1]}}
 
     def tpx_set_state(self, state: dict | None):
         st = None if state is None else _CState(*(int(state[f]) for f in STATE_FIELDS))

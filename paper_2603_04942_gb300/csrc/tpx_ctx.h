@@ -13,6 +13,17 @@ struct tpx_ctx {
     cudaStream_t stream;
     int device;
     int num_sms;
+    int geo;                  // fused-kernel tile geometry (tpxk::GEO_*), when fixed by the config
+    // tile-geometry autotuner (TPX_TILE_DEFAULT): the first large calls
+    // alternate the geometries, timed with events; the faster one is kept
+    struct Tune {
+        int fixed;            // chosen tpxk::GEO_*, 0 while sampling
+        int issued[2];        // samples launched per geometry (index geo - 1)
+        int done[2];          // samples timed
+        double best[2];       // lowest ms per million packets seen
+        int head, tail;       // ring of launched, not yet timed samples
+        struct Sample { cudaEvent_t a, b; int geo; int64_t n; } ring[8];
+    } tune;
     int64_t max_packets;
     int64_t max_tiles;
     unsigned seq;

@@ -10,945 +10,26 @@
 
 namespace tpxk {
 
-constexpr int NT = 1024;           // threads per CTA
-constexpr int NW = NT / 32;
-constexpr int T = 4096;            // packets per tile
-constexpr int C = 8192;            // range capacity (tile + look-ahead), positions
-constexpr int KP = C / NT;         // positions per thread in contiguous walks
-constexpr int HB = 8192;           // hash buckets (power of two)
-constexpr int MAXSEG = T + 16;     // TDC packets per range: at most a tile's plus the terminator
-constexpr uint64_t INVALID = ~0ull;
-constexpr uint32_t EMPTY = 0xFFFFu;
-constexpr long long MAX_SPIN = 1LL << 22;   // bounded look-back waits (~0.5 s)
+// 1024-thread CTAs, one per SM, 4096-packet tiles, 8192-position ranges
+namespace geo_t4096 {
+constexpr int NT = 1024, T = 4096, C = 8192, HB = 8192, MINB = 1;
+#include "tpx_fused_body.cuh"
+}  // namespace geo_t4096
 
-static_assert(T % NT == 0 && C % NT == 0 && T <= C && C <= 16384, "tile geometry");
+// 512-thread CTAs, two per SM, 2048-packet tiles, 4096-position ranges
+namespace geo_t2048 {
+constexpr int NT = 512, T = 2048, C = 4096, HB = 4096, MINB = 2;
+#include "tpx_fused_body.cuh"
+}  // namespace geo_t2048
 
-// ------------------------------------------------------------------ helpers
-__device__ __forceinline__ int pad(int p) { return p + (p >> 3); }   // conflict-free 8-wide walks
+int fused_tile_packets(int geo) { return geo == GEO_T2048 ? geo_t2048::T : geo_t4096::T; }
+int fused_threads(int geo) { return geo == GEO_T2048 ? geo_t2048::NT : geo_t4096::NT; }
+int fused_range_capacity(int geo) { return geo == GEO_T2048 ? geo_t2048::C : geo_t4096::C; }
+int fused_ctas_per_sm(int geo) { return geo == GEO_T2048 ? geo_t2048::MINB : geo_t4096::MINB; }
+int fused_smem_bytes(int geo) { return geo == GEO_T2048 ? geo_t2048::smem_bytes() : geo_t4096::smem_bytes(); }
 
-// kept-pixel record: [63:40] tof+bias | [39:26] segment | [25:16] ToT | [15:8] y | [7:0] x
-__device__ __forceinline__ uint64_t mkrec(uint32_t tofb, uint32_t seg, uint32_t tot, uint32_t x, uint32_t y) {
-    return ((uint64_t)tofb << 40) | ((uint64_t)seg << 26) | ((uint64_t)tot << 16) | ((uint64_t)y << 8) | x;
+cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s) {
+    return geo == GEO_T2048 ? geo_t2048::launch(p, mode, grid, s) : geo_t4096::launch(p, mode, grid, s);
 }
-__device__ __forceinline__ int r_x(uint64_t r) { return (int)(r & 255); }
-__device__ __forceinline__ int r_y(uint64_t r) { return (int)((r >> 8) & 255); }
-__device__ __forceinline__ int r_tot(uint64_t r) { return (int)((r >> 16) & 1023); }
-__device__ __forceinline__ int r_seg(uint64_t r) { return (int)((r >> 26) & 0x3FFF); }
-__device__ __forceinline__ int r_tof(uint64_t r) { return (int)(r >> 40); }
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_agg(GAgg *dst, const GAgg &a) {
-    long long *d = reinterpret_cast<long long *>(dst);
-    const long long *s = reinterpret_cast<const long long *>(&a);
-#pragma unroll
-    for (int i = 0; i < 8; i++) __stcg(d + i, s[i]);
-}
-__device__ __forceinline__ GAgg ld_agg(const GAgg *src) {
-    GAgg a;
-    const long long *s = reinterpret_cast<const long long *>(src);
-    long long *d = reinterpret_cast<long long *>(&a);
-#pragma unroll
-    for (int i = 0; i < 8; i++) d[i] = __ldcg(s + i);
-    return a;
-}
-
-// hash of a (segment, x, y) cell
-__device__ __forceinline__ uint32_t hcell(int seg, int x, int y) {
-    return (uint32_t)(x + 67 * y + 1543 * seg) & (HB - 1);
-}
-
-// Union-find over a shared-memory parent array, addressed explicitly in the
-// shared window (32-bit addresses, ld/st.volatile.shared, atom.shared.cas).
-__device__ __forceinline__ uint32_t sh_ld(uint32_t a) {
-    uint32_t v;
-    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-    return v;
-}
-__device__ __forceinline__ void sh_st(uint32_t a, uint32_t v) {
-    asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t sh_cas(uint32_t a, uint32_t cmp, uint32_t v) {
-    uint32_t o;
-    asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(o) : "r"(a), "r"(cmp), "r"(v) : "memory");
-    return o;
-}
-__device__ __forceinline__ uint32_t find_root(uint32_t pbase, uint32_t x) {
-    for (;;) {
-        const uint32_t p = sh_ld(pbase + 4 * x);
-        if (p == x) return x;
-        const uint32_t g = sh_ld(pbase + 4 * p);
-        if (g == p) return p;
-        sh_st(pbase + 4 * x, g);   // path halving: g is an ancestor of x
-        x = g;
-    }
-}
-__device__ __forceinline__ uint32_t find_ro(uint32_t pbase, uint32_t x) {
-    uint32_t p;
-    while ((p = sh_ld(pbase + 4 * x)) != x) x = p;
-    return x;
-}
-
-// --------------------------------------------------------------- smem layout
-struct __align__(16) Smem {
-    uint64_t buf[C + C / 8];                          // packets, then kept-pixel records
-    uint32_t parent[C];                               // union-find; then member links and
-                                                      // root positions (CC) / peak list (PAPER)
-    union { uint32_t head[HB]; uint32_t mhead[C]; } u1; // hash heads, then member-list heads
-    union { uint16_t next[C]; uint16_t rootof[C]; } u2;
-    uint8_t notpeak[C];
-    long long tdc_t[MAXSEG];
-    GAgg warp_agg[NW];
-    GAgg tot_agg;
-    GAgg tile_agg;                // this tile's chain aggregate
-    GAgg E;                       // unwrap state before the tile
-    int warp_int[NW + 1];
-    unsigned long long cnt[C_NUM];
-    long long tile;
-    long long clo;
-    long long pend_tile;          // staged records awaiting their offset (-1: none)
-    long long pend_ntr;
-    int pend_ncl;
-    int first_tdc;
-    int la_first;
-    unsigned status;
-};
-
-// block exclusive scan of GAgg in thread order; returns this thread's
-// exclusive prefix and leaves the block total in S.tot_agg
-__device__ GAgg block_scan_agg(Smem &S, const GAgg &v, long long tp, long long tt) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    GAgg incl = warp_incl_scan(v, lane, tp, tt);
-    GAgg wex = shfl_up_agg(incl, 1);
-    if (lane == 0) wex = agg_id();
-    if (lane == 31) S.warp_agg[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        GAgg x = lane < NW ? S.warp_agg[lane] : agg_id();
-        GAgg xi = warp_incl_scan(x, lane, tp, tt);
-        GAgg xe = shfl_up_agg(xi, 1);
-        if (lane == 0) xe = agg_id();
-        if (lane < NW) S.warp_agg[lane] = xe;
-        if (lane == NW - 1) S.tot_agg = xi;
-    }
-    __syncthreads();
-    GAgg r = acomb(S.warp_agg[w], wex, tp, tt);
-    __syncthreads();
-    return r;
-}
-
-// block exclusive scan of int; total in *total
-__device__ int block_scan_int(Smem &S, int v, int *total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) S.warp_int[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        int x = lane < NW ? S.warp_int[lane] : 0;
-        int xi = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, xi, o);
-            if (lane >= o) xi += u;
-        }
-        if (lane < NW) S.warp_int[lane] = xi - x;
-        if (lane == NW - 1) S.warp_int[NW] = xi;
-    }
-    __syncthreads();
-    int r = S.warp_int[w] + incl - v;
-    *total = S.warp_int[NW];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// once any wait has run out, every later wait gives up at once, so a broken
-// chain costs one bounded wait, not one per tile
-__device__ __forceinline__ bool timed_out(const Params &p) {
-    return (*reinterpret_cast<volatile unsigned *>(&p.ctl->status) & ST_DEVTIMEOUT) != 0;
-}
-
-__device__ __forceinline__ GChain shfl_down_chain(const GChain &v, int o) {
-    GChain u;
-    u.n = __shfl_down_sync(0xffffffffu, v.n, o);
-    u.first = __shfl_down_sync(0xffffffffu, v.first, o);
-    u.last = __shfl_down_sync(0xffffffffu, v.last, o);
-    u.sum = __shfl_down_sync(0xffffffffu, v.sum, o);
-    return u;
-}
-
-// Bounded decoupled look-back, one warp. Each trip reads the flags of
-// 32 * LB predecessors at once (lane l holds tiles hi - LB*l - j, j = 0 the
-// latest), waits only for the tiles from hi down to the nearest inclusive
-// prefix, and combines them in stream order. Two dependent L2 round trips
-// per trip (flags, then values), so wide trips keep the chain short.
-// (LB = 1 for the 64-byte chain aggregates: the 64-register budget of a
-// 1024-thread CTA keeps only one in flight per lane; LB = 4 for counts.)
-constexpr int LBA = 1, LBC = 4;
-
-// per lane: which of its LB tiles are needed this trip, given the flags
-struct LbScan { unsigned need, inc; int stop; bool ok; };
-template <int LB>
-__device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, unsigned seq) {
-    const int lane = threadIdx.x & 31;
-    unsigned rdy = 0, inc = 0;
-#pragma unroll
-    for (int j = 0; j < LB; ++j) {
-        const long long q = hi - LB * lane - j;
-        if (q < 0) { rdy |= 1u << j; continue; }
-        const unsigned f = ld_acquire(&flags[q]);
-        if ((f >> 2) == seq && (f & 3u)) {
-            rdy |= 1u << j;
-            if ((f & 3u) == 2u) inc |= 1u << j;
-        }
-    }
-    const unsigned im = __ballot_sync(0xffffffffu, inc != 0);
-    LbScan r;
-    r.stop = im ? __ffs(im) - 1 : 31;
-    r.inc = inc;
-    const unsigned all = (1u << LB) - 1u;
-    r.need = lane < r.stop ? all : (lane == r.stop ? (inc ? ((inc & (0u - inc)) << 1) - 1u : all) : 0u);
-    r.ok = (rdy & r.need) == r.need;
-    return r;
-}
-
-// buf: 32 GAgg slots in shared memory, free while the look-back runs. The
-// combine is a tree over the slots (few live registers: the kernel runs at
-// the 64-register limit of a 1024-thread CTA). Lane 0 returns the prefix.
-__device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq, unsigned *status, GAgg *buf) {
-    const int lane = threadIdx.x & 31;
-    GAgg acc = agg_id();
-    for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBA) {
-        LbScan sc;
-        long long spins = 0;
-        for (;;) {
-            sc = lb_scan<LBA>(p.ts.flags, hi, seq);
-            if (__all_sync(0xffffffffu, sc.ok)) break;
-            if (++spins > MAX_SPIN || timed_out(p)) {
-                if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
-                *status |= ST_DEVTIMEOUT;
-                return acc;
-            }
-            __nanosleep(64);
-        }
-        // lane l: its needed tile (an inclusive prefix, if present, is the
-        // earliest needed one), or the identity
-        {
-            const long long q = hi - lane;
-            const ulonglong2 *src = nullptr;
-            if (q >= 0 && (sc.need & 1u)) src = reinterpret_cast<const ulonglong2 *>((sc.inc & 1u) ? &p.ts.pre[q] : &p.ts.agg[q]);
-            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&buf[lane]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) dst[k] = src ? __ldcg(src + k) : make_ulonglong2(0ull, 0ull);
-        }
-        __syncwarp();
-        // lane l + o holds earlier tiles than lane l: combine it on the left
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            if ((lane & (2 * o - 1)) == 0) buf[lane] = acomb(buf[lane + o], buf[lane], p.thr_pix, p.thr_tdc);
-            __syncwarp();
-        }
-        if (lane == 0) acc = acomb(buf[0], acc, p.thr_pix, p.thr_tdc);
-        __syncwarp();
-        if (__any_sync(0xffffffffu, sc.inc != 0)) break;
-    }
-    return acc;
-}
-
-// The same over the record counts of the tiles.
-__device__ long long lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
-    const int lane = threadIdx.x & 31;
-    long long acc = 0;
-    for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBC) {
-        LbScan sc;
-        long long spins = 0;
-        for (;;) {
-            sc = lb_scan<LBC>(p.ts.cflags, hi, seq);
-            if (__all_sync(0xffffffffu, sc.ok)) break;
-            if (++spins > MAX_SPIN || timed_out(p)) {
-                if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
-                *status |= ST_DEVTIMEOUT;
-                return acc;
-            }
-            __nanosleep(64);
-        }
-        long long v = 0;
-#pragma unroll
-        for (int j = 0; j < LBC; ++j) {
-            const long long q = hi - LBC * lane - j;
-            if (q < 0 || !((sc.need >> j) & 1u)) continue;
-            v += __ldcg(((sc.inc >> j) & 1u) ? &p.ts.cpre[q] : &p.ts.cagg[q]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc += v;
-        if (__any_sync(0xffffffffu, sc.inc != 0)) break;
-    }
-    return acc;
-}
-
-// lock-free union; the root is the member with the smallest (time, position)
-__device__ __forceinline__ uint64_t rkey(const Smem &S, uint32_t q) {
-    return ((uint64_t)r_tof(S.buf[pad((int)q)]) << 16) | q;
-}
-__device__ void unite_one(const Smem &S, uint32_t pbase, uint32_t a, uint32_t b) {
-    for (;;) {
-        a = find_root(pbase, a);
-        b = find_root(pbase, b);
-        if (a == b) return;
-        if (rkey(S, a) > rkey(S, b)) { uint32_t t = a; a = b; b = t; }
-        const uint32_t old = sh_cas(pbase + 4 * b, b, a);
-        if (old == b) return;
-        b = old;
-    }
-}
-
-// Warp 0 resolves the record offset of tile tl holding nc records (decoupled
-// look-back over the counts), publishes its inclusive count and, for the last
-// tile, the call's totals; the offset is left in S.clo.
-__device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr) {
-    if (threadIdx.x >= 32) return;
-    unsigned st2 = 0;
-    long long Ow = 0;
-    if (tl > 0) Ow = lookback_count_warp(p, tl, seq, &st2);
-    if (threadIdx.x == 0) {
-        if (tl > 0) {
-            __stcg(&p.ts.cpre[tl], Ow + (long long)nc);
-            st_release(&p.ts.cflags[tl], (seq << 2) | 2u);
-        }
-        S.clo = Ow;
-        if (st2) atomicOr(&S.status, st2);
-        if (tl == p.n_tiles - 1) {
-            *p.n_clusters = Ow + nc;
-            *p.n_trig = ntr;
-            if (Ow + nc > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
-            if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
-        }
-    }
-}
-
-// Staged output: a tile's records wait in the CTA's staging slot until the
-// next tile (or the end of the kernel) resolves their offset, when the
-// predecessors' counts are long published; then one coalesced copy.
-__device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
-    const long long pt = S.pend_tile;
-    if (pt < 0) return;
-    const int nc = S.pend_ncl;
-    resolve_offset(S, p, seq, pt, nc, S.pend_ntr);
-    __syncthreads();
-    const long long O = S.clo;
-    const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
-    constexpr int WPR = (int)(sizeof(tpx_record) / 8);
-    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
-    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
-    for (long long w = threadIdx.x; w < keep * WPR; w += NT) dst[w] = __ldcg(src + w);
-    __syncthreads();
-    if (threadIdx.x == 0) S.pend_tile = -1;
-}
-
-// ------------------------------------------------------------------- kernel
-template <int MODE, bool STAGED>
-__global__ void __launch_bounds__(NT, 1) fused_kernel(const Params p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31;
-    const long long tp = p.thr_pix, tt = p.thr_tdc;
-    const unsigned seq = p.seq & 0x3FFFFFFFu;
-    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(S.parent);
-    if (tid == 0) S.pend_tile = -1;
-
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) {
-            S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
-            S.first_tdc = INT_MAX;
-            S.status = 0;
-        }
-        if (tid < C_NUM) S.cnt[tid] = 0;
-        __syncthreads();
-        const long long tile = S.tile;
-        if (tile >= p.n_tiles) {
-            if (STAGED) {
-                flush_pending(S, p, seq);
-                if (tid == 0 && S.status) atomicOr(&p.ctl->status, S.status);
-            }
-            break;
-        }
-        const long long base = tile * T;
-        const int cnt = (int)min((long long)T, p.n - base);
-
-        // ---- load the tile: coalesced 16-byte loads into the padded buffer ----
-        {
-            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.pk + base);
-            const int npair = cnt >> 1;
-            for (int v = tid; v < npair; v += NT) {
-                ulonglong2 w = __ldcg(src + v);
-                S.buf[pad(2 * v)] = w.x;
-                S.buf[pad(2 * v + 1)] = w.y;
-            }
-            if ((cnt & 1) && tid == 0) S.buf[pad(cnt - 1)] = __ldcg(p.pk + base + cnt - 1);
-        }
-        for (int i = tid; i < HB; i += NT) S.u1.head[i] = EMPTY;
-        __syncthreads();
-
-        // ---- walk 1: unwrap-chain aggregate of the tile, packet counts ----
-        {
-            GAgg a = agg_id();
-            unsigned long long c_pix = 0, c_tdc = 0, c_bad = 0;
-            int my_first = INT_MAX;
-            const int p0 = tid * KP;
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= cnt) break;
-                const uint64_t w = S.buf[pad(q)];
-                const unsigned h = (unsigned)(w >> 60);
-                if (h == 0xBu) { chain_push(a.pix, pix_raw(w), tp); ++c_pix; }
-                else if (h == 0x6u) { chain_push(a.tdc, tdc_raw(w), tt); ++c_tdc; my_first = min(my_first, q); }
-                else ++c_bad;
-            }
-            (void)block_scan_agg(S, a, tp, tt);
-            c_pix = warp_sum(c_pix); c_tdc = warp_sum(c_tdc); c_bad = warp_sum(c_bad);
-            if (lane == 0) {
-                atomicAdd(&S.cnt[C_PIXELS], c_pix);
-                atomicAdd(&S.cnt[C_TDCS], c_tdc);
-                atomicAdd(&S.cnt[C_CORRUPT], c_bad);
-            }
-            if (my_first != INT_MAX) atomicMin(&S.first_tdc, my_first);
-        }
-        // publish the tile's aggregate now; the look-back waits until after the
-        // read-ahead and the block scan, which do not need it
-        if (tid == 0) {
-            S.tile_agg = S.tot_agg;
-            if (tile > 0) {
-                st_agg(&p.ts.agg[tile], S.tot_agg);
-                st_release(&p.ts.flags[tile], (seq << 2) | 1u);
-            } else {
-                const GAgg e0 = p.E0 ? *p.E0 : agg_id();
-                S.E = e0;
-                st_agg(&p.ts.pre[0], acomb(e0, S.tot_agg, tp, tt));
-                st_release(&p.ts.flags[0], (seq << 2) | 2u);
-            }
-        }
-        __syncthreads();
-        const int f = S.first_tdc;
-
-        // ---- look ahead past the tile up to the next TDC packet ----
-        int L = cnt;
-        bool term = false;
-        if (f != INT_MAX) {
-            while (base + L < p.n) {
-                const int room = C - L;
-                if (room <= 0) break;
-                const int chunk = (int)min((long long)min(NT, room), p.n - (base + L));
-                bool is_t = false;
-                if (tid < chunk) {
-                    const uint64_t w = __ldcg(p.pk + base + L + tid);
-                    S.buf[pad(L + tid)] = w;
-                    is_t = (w >> 60) == 0x6u;
-                }
-                if (tid == 0) S.la_first = INT_MAX;
-                __syncthreads();
-                if (is_t) atomicMin(&S.la_first, tid);
-                __syncthreads();
-                const int lf = S.la_first;
-                __syncthreads();
-                if (lf != INT_MAX) { L += lf + 1; term = true; break; }
-                L += chunk;
-            }
-            if (!term && base + L < p.n && tid == 0) atomicOr(&S.status, ST_CAPACITY);
-        }
-
-        // ---- walk 2: per-thread chain state over [0, L) ----
-        const int p0 = tid * KP;
-        GAgg ex;
-        int ntdc;
-        {
-            GAgg a = agg_id();
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= L) break;
-                const uint64_t w = S.buf[pad(q)];
-                const unsigned h = (unsigned)(w >> 60);
-                if (h == 0xBu) chain_push(a.pix, pix_raw(w), tp);
-                else if (h == 0x6u) chain_push(a.tdc, tdc_raw(w), tt);
-            }
-            ex = block_scan_agg(S, a, tp, tt);
-            ntdc = (int)S.tot_agg.tdc.n;
-        }
-        // ---- unwrap state before the tile: warp-parallel look-back ----
-        if (tid < 32) {
-            unsigned stl = 0;
-            GAgg Ew = agg_id();
-            if (tile > 0) Ew = lookback_agg_warp(p, tile, seq, &stl, S.warp_agg);
-            else Ew = p.E0 ? *p.E0 : agg_id();
-            if (tid == 0) {
-                if (tile > 0) {
-                    st_agg(&p.ts.pre[tile], acomb(Ew, S.tile_agg, tp, tt));
-                    st_release(&p.ts.flags[tile], (seq << 2) | 2u);
-                }
-                if (tile == p.n_tiles - 1 && p.state_out) *p.state_out = acomb(Ew, S.tile_agg, tp, tt);
-                S.E = Ew;
-                if (stl) atomicOr(&S.status, stl);
-            }
-        }
-        __syncthreads();
-        const GAgg E = S.E;
-        // a call sees only its own triggers: "earlier" means earlier in this call
-        const long long trig_base = p.E0 ? p.E0->tdc.n : 0;
-        const bool prev_global = E.tdc.n > trig_base;
-        const GAgg st = acomb(E, ex, tp, tt);   // global chain state before position p0
-
-        // ---- walk 3: unwrapped trigger times ----
-        {
-            bool has = st.tdc.n > 0;
-            long long last = st.tdc.last, ep = st.tdc.sum;
-            int li = (int)ex.tdc.n;
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= L) break;
-                const uint64_t w = S.buf[pad(q)];
-                if ((w >> 60) != 0x6u) continue;
-                const long long r = tdc_raw(w);
-                if (has) ep += jump(r - last, tt);
-                has = true;
-                last = r;
-                const long long t = r + ep * kTdcPeriod;
-                if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
-                if (q < cnt) {
-                    const long long g = E.tdc.n - trig_base + li;
-                    if (g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
-                }
-                ++li;
-            }
-        }
-        __syncthreads();
-        if (ntdc > MAXSEG && tid == 0) atomicOr(&S.status, ST_CAPACITY);
-        for (int i = tid; i + 1 < min(ntdc, MAXSEG); i += NT)
-            if (S.tdc_t[i + 1] < S.tdc_t[i]) atomicOr(&p.ctl->status, ST_TRIG_ORDER);
-
-        // ---- walk 4: pixels -> shot, cut, timewalk, packed record ----
-        {
-            bool has = st.pix.n > 0;
-            long long last = st.pix.last, ep = st.pix.sum;
-            int seg = (int)ex.tdc.n - 1;
-            const long long t_prev_global = E.tdc.last + E.tdc.sum * kTdcPeriod;
-            unsigned long long c_keep = 0, c_pre = 0, c_bg = 0;
-            bool exc = false;
-            const int nseg = min(ntdc, MAXSEG);
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= L) break;
-                const uint64_t w = S.buf[pad(q)];
-                const unsigned h = (unsigned)(w >> 60);
-                uint64_t rec = INVALID;
-                if (h == 0x6u) {
-                    ++seg;
-                } else if (h == 0xBu) {
-                    const long long r = pix_raw(w);
-                    if (has) ep += jump(r - last, tp);
-                    has = true;
-                    last = r;
-                    const long long t = r + ep * kPixPeriod;
-                    if (seg < 0) {
-                        if (!prev_global) ++c_pre;        // no trigger before it anywhere
-                    } else if (seg < nseg) {
-                        const long long t_lo = S.tdc_t[seg];
-                        const bool has_hi = seg + 1 < nseg;
-                        int verdict;                      // 0 keep, 1 bg, 2 pre, 3 undecidable here
-                        if (has_hi && t >= S.tdc_t[seg + 1]) verdict = 3;
-                        else if (t >= t_lo) verdict = (t - t_lo > p.tof_max) ? 1 : 0;
-                        else {
-                            const bool hp = seg > 0 || prev_global;
-                            const long long tprev = seg > 0 ? S.tdc_t[seg - 1] : t_prev_global;
-                            if (!hp) verdict = 2;
-                            else if (t >= tprev) verdict = (t - tprev > p.tof_max) ? 1 : 3;
-                            else verdict = 3;
-                        }
-                        if (verdict == 0) {
-                            const int tot = pix_tot(w);
-                            const long long tc = t - (p.lut ? (long long)p.lut[tot] : 0LL);
-                            const long long tofb = tc - t_lo + kTofBias;
-                            rec = mkrec((uint32_t)tofb, (uint32_t)seg, (uint32_t)tot, (uint32_t)pix_x(w), (uint32_t)pix_y(w));
-                            ++c_keep;
-                        } else if (verdict == 1) ++c_bg;
-                        else if (verdict == 2) ++c_pre;
-                        else exc = true;
-                    }
-                }
-                S.buf[pad(q)] = rec;
-            }
-            c_keep = warp_sum(c_keep); c_pre = warp_sum(c_pre); c_bg = warp_sum(c_bg);
-            if (lane == 0) {
-                atomicAdd(&S.cnt[C_KEPT], c_keep);
-                atomicAdd(&S.cnt[C_DROP_PRE], c_pre);
-                atomicAdd(&S.cnt[C_DROP_BG], c_bg);
-            }
-            if (exc) atomicOr(&S.status, ST_EXCEPTION);
-        }
-        __syncthreads();   // records written per contiguous chunk are read strided below
-
-        // the range this CTA owns: [R0, R1)
-        const int R0 = (f == INT_MAX) ? 0 : f;
-        const int R1 = (f == INT_MAX) ? 0 : (term ? L - 1 : L);
-        // label writes cover [W0, W1): the range, plus the packets before the
-        // tile's first trigger when no trigger precedes them anywhere
-        const int W0 = prev_global ? R0 : 0;
-        const int W1 = (f == INT_MAX) ? (prev_global ? 0 : cnt) : R1;
-
-        // ---- hash insert ----
-        for (int q = R0 + tid; q < R1; q += NT) {
-            const uint64_t r = S.buf[pad(q)];
-            S.parent[q] = (uint32_t)q;
-            S.notpeak[q] = 0;
-            if (r != INVALID) {
-                const uint32_t b = hcell(r_seg(r), r_x(r), r_y(r));
-                S.u2.next[q] = (uint16_t)atomicExch(&S.u1.head[b], (uint32_t)q);
-            }
-        }
-        __syncthreads();
-
-        // ---- neighbour pass: each adjacent pair once (Sec. V.A box rule) ----
-        // The warp walks 32 consecutive positions at a time. Each lane first
-        // gathers its pixel's partners in the forward half of the box (packed
-        // 16-bit positions in two registers); the unions then run
-        // warp-synchronously, one find hop or link attempt per loop trip, so
-        // the lanes stay converged (retry loops nested in the lookups would
-        // serialise them).
-        {
-            for (int qb = R0 + (tid & ~31); qb < R1; qb += NT) {
-                const int q = qb + lane;
-                const uint64_t r = q < R1 ? S.buf[pad(q)] : INVALID;
-                uint64_t eb0 = 0, eb1 = 0;
-                int ne = 0;
-                bool overflow = false;
-                if (r != INVALID) {
-                    const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
-                    bool dim = false;
-                    for (int dx = 0; dx <= p.rx; ++dx) {
-                        const int cx = x + dx;
-                        if (cx > 255) break;
-                        for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
-                            const int cy = y + dy;
-                            if (cy < 0 || cy > 255) continue;
-                            for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
-                                if (dx == 0 && dy == 0 && (int)j <= q) continue;
-                                const uint64_t rj = S.buf[pad((int)j)];
-                                if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
-                                const int d = r_tof(rj) - tb;
-                                if (d < -p.dt || d > p.dt) continue;
-                                const int tj = r_tot(rj);
-                                // local maxima: equal ToT goes to the later pixel (Sec. V.B)
-                                if (tj > tot || (tj == tot && (int)j > q)) dim = true;
-                                else S.notpeak[j] = 1;
-                                if (MODE == TPX_MODE_CC) {
-                                    if (ne < 4) eb0 |= (uint64_t)j << (16 * ne);
-                                    else if (ne < 8) eb1 |= (uint64_t)j << (16 * (ne - 4));
-                                    else overflow = true;
-                                    ++ne;
-                                }
-                            }
-                        }
-                    }
-                    if (dim) S.notpeak[q] = 1;
-                }
-                if (MODE == TPX_MODE_CC) {
-                    if (overflow) {
-                        // more than 8 partners (possible with larger radii): unite
-                        // this pixel's pairs one at a time
-                        const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
-                        for (int dx = 0; dx <= p.rx; ++dx)
-                            for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
-                                const int ux = x + dx, uy = y + dy;
-                                if (ux > 255 || uy < 0 || uy > 255) continue;
-                                for (uint32_t jj = S.u1.head[hcell(sg, ux, uy)]; jj != EMPTY; jj = S.u2.next[jj]) {
-                                    if (dx == 0 && dy == 0 && (int)jj <= q) continue;
-                                    const uint64_t rj = S.buf[pad((int)jj)];
-                                    if (r_x(rj) != ux || r_y(rj) != uy || r_seg(rj) != sg) continue;
-                                    const int d = r_tof(rj) - tb;
-                                    if (d < -p.dt || d > p.dt) continue;
-                                    unite_one(S, pbase, (uint32_t)q, jj);
-                                }
-                            }
-                        ne = 0;
-                    }
-                    // warp-synchronous unions: each trip advances every active lane by
-                    // one step (a find hop with path halving on either side, or one
-                    // link attempt); a lane moves to its next partner as soon as its
-                    // current union is done
-                    __syncwarp();
-                    int k = 0;
-                    uint32_t a = (uint32_t)(q < R1 ? q : 0), b = (uint32_t)(eb0 & 0xFFFF);
-                    bool active = ne > 0;
-                    while (__any_sync(0xffffffffu, active)) {
-                        if (active) {
-                            bool done = false;
-                            const uint32_t pa = sh_ld(pbase + 4 * a);
-                            const uint32_t pb = sh_ld(pbase + 4 * b);
-                            if (pa != a || pb != b) {
-                                if (pa != a) {
-                                    const uint32_t ga = sh_ld(pbase + 4 * pa);
-                                    if (ga != pa) sh_st(pbase + 4 * a, ga);
-                                    a = ga;
-                                }
-                                if (pb != b) {
-                                    const uint32_t gb = sh_ld(pbase + 4 * pb);
-                                    if (gb != pb) sh_st(pbase + 4 * b, gb);
-                                    b = gb;
-                                }
-                            } else if (a == b) {
-                                done = true;
-                            } else {
-                                uint32_t lo = a, hi = b;
-                                if (rkey(S, a) > rkey(S, b)) { lo = b; hi = a; }
-                                const uint32_t old = sh_cas(pbase + 4 * hi, hi, lo);
-                                if (old == hi) done = true;
-                                else b = old;      // hi was linked meanwhile: continue above it
-                                a = lo;
-                            }
-                            if (done) {
-                                if (++k < ne) {
-                                    const uint64_t w = k < 4 ? eb0 : eb1;
-                                    b = (uint32_t)((w >> (16 * (k & 3))) & 0xFFFF);
-                                } else {
-                                    active = false;
-                                }
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-
-        int ncl = 0;
-        if (MODE == TPX_MODE_CC) {
-            for (int q = R0 + tid; q < R1; q += NT)
-                if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(pbase, (uint32_t)q);
-            __syncthreads();
-            // cluster ids in ascending root position (= ascending label)
-            int c = 0;
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
-            }
-            int excl = block_scan_int(S, c, &ncl);
-            // the union-find array is free now: it holds the member links
-            // (first half) and the root position of each cluster id (second half)
-            uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
-                    rootpos[excl++] = (uint16_t)q;
-                    S.u1.mhead[q] = EMPTY;
-                }
-            }
-        } else {
-            // PAPER mode: one record per local maximum (list kept in parent[])
-            int c = 0;
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) ++c;
-            }
-            int excl = block_scan_int(S, c, &ncl);
-            for (int j = 0; j < KP; ++j) {
-                const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) S.parent[excl++] = (uint32_t)q;
-            }
-        }
-
-        // ---- record offsets: publish this tile's count now, look back later ----
-        if (tid == 0) {
-            if (tile > 0) {
-                __stcg(&p.ts.cagg[tile], (long long)ncl);
-                st_release(&p.ts.cflags[tile], (seq << 2) | 1u);
-            } else {
-                __stcg(&p.ts.cpre[0], (long long)ncl);
-                st_release(&p.ts.cflags[0], (seq << 2) | 2u);
-            }
-        }
-        const long long ntr_here = E.tdc.n - trig_base + (long long)S.cnt[C_TDCS];
-        // records go to the CTA's staging slot (STAGED) or straight to their
-        // offset after an inline look-back
-        auto record_target = [&](long long *lim) -> tpx_record * {
-            if (STAGED) {
-                flush_pending(S, p, seq);
-                __syncthreads();   // the member lists / peak list are complete
-                *lim = C;
-                return p.stage + (long long)blockIdx.x * C;
-            }
-            resolve_offset(S, p, seq, tile, ncl, ntr_here);
-            __syncthreads();
-            *lim = p.cl_cap - S.clo;
-            return p.clusters + S.clo;
-        };
-
-        if (MODE == TPX_MODE_CC) {
-            // Each kept pixel joins its cluster's member list (one exchange per
-            // pixel) and writes its label; then one thread per cluster walks the
-            // list and forms the exact integer moments in registers (Sec. V.C).
-            uint16_t *mnext = reinterpret_cast<uint16_t *>(S.parent);
-            const uint16_t *rootpos = mnext + C;
-            __syncthreads();
-            unsigned long long c_pk = 0;
-            for (int q = W0 + tid; q < W1; q += NT) {
-                const uint64_t r = S.buf[pad(q)];
-                const bool kept = q >= R0 && r != INVALID;
-                uint32_t root = 0;
-                uint8_t pk = 0;
-                if (kept) {
-                    root = S.u2.rootof[q];
-                    pk = S.notpeak[q] ? 0 : 1;
-                    c_pk += pk;
-                    mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[root], (uint32_t)q);
-                }
-                if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)root : -1LL;
-                if (p.is_peak) p.is_peak[base + q] = pk;
-            }
-            c_pk = warp_sum(c_pk);
-            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
-            long long lim = 0;
-            tpx_record *dst = record_target(&lim);
-            // records: one thread per cluster walks its member list and forms
-            // the exact integer moments in registers (Sec. V.C)
-            for (int i = tid; i < ncl; i += NT) {
-                if (i >= lim) break;
-                const int q = rootpos[i];
-                const uint64_t r = S.buf[pad(q)];
-                const int tofb0 = r_tof(r);
-                long long s_tot = 0, s_x = 0, s_y = 0, s_t = 0;
-                int n = 0, npk = 0;
-                for (uint32_t m = S.u1.mhead[q]; m != EMPTY; m = mnext[m]) {
-                    const uint64_t rm = S.buf[pad((int)m)];
-                    const long long tot = r_tot(rm);
-                    n += 1;
-                    npk += S.notpeak[m] ? 0 : 1;
-                    s_tot += tot;
-                    s_x += tot * r_x(rm);
-                    s_y += tot * r_y(rm);
-                    s_t += tot * (long long)(r_tof(rm) - tofb0);
-                }
-                const int seg = r_seg(r);
-                const long long tofc0 = (long long)tofb0 - kTofBias;
-                tpx_record o;
-                o.label = p.idx_base + base + q;
-                o.shot = E.tdc.n + seg;
-                o.t0 = S.tdc_t[seg] + tofc0;
-                o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
-                o.n = n; o.n_peaks = npk;
-                com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                dst[i] = o;
-            }
-        } else {
-            unsigned long long c_pk = 0;
-            for (int q = W0 + tid; q < W1; q += NT) {
-                const uint64_t r = S.buf[pad(q)];
-                long long lab = -1;
-                uint8_t pk = 0;
-                if (q >= R0 && r != INVALID) {
-                    lab = p.idx_base + base + q;
-                    pk = S.notpeak[q] ? 0 : 1;
-                    c_pk += pk;
-                }
-                if (p.labels) p.labels[base + q] = lab;
-                if (p.is_peak) p.is_peak[base + q] = pk;
-            }
-            c_pk = warp_sum(c_pk);
-            if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
-            long long lim = 0;
-            tpx_record *dst = record_target(&lim);
-            // records: box neighbourhood sums of each local maximum (Sec. V.C)
-            for (int i = tid; i < ncl; i += NT) {
-                if (i >= lim) break;
-                const int q = (int)S.parent[i];
-                const uint64_t r = S.buf[pad(q)];
-                const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
-                long long n = 0, s_tot = 0, s_x = 0, s_y = 0, a2 = 0;
-                int tmin = tb;
-                for (int dx = -p.rx; dx <= p.rx; ++dx) {
-                    const int cx = x + dx;
-                    if (cx < 0 || cx > 255) continue;
-                    for (int dy = -p.ry; dy <= p.ry; ++dy) {
-                        const int cy = y + dy;
-                        if (cy < 0 || cy > 255) continue;
-                        for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
-                            const uint64_t rj = S.buf[pad((int)j)];
-                            if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
-                            const int d = r_tof(rj) - tb;
-                            if (d < -p.dt || d > p.dt) continue;
-                            const long long tj = r_tot(rj);
-                            n += 1; s_tot += tj; s_x += tj * cx; s_y += tj * cy; a2 += tj * r_tof(rj);
-                            tmin = min(tmin, r_tof(rj));
-                        }
-                    }
-                }
-                const long long s_t = a2 - (long long)tmin * s_tot;
-                const long long tofc0 = (long long)tmin - kTofBias;
-                tpx_record o;
-                o.label = p.idx_base + base + q;
-                o.shot = E.tdc.n + sg;
-                o.t0 = S.tdc_t[sg] + tofc0;
-                o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
-                o.n = (int)n; o.n_peaks = 1;
-                com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                dst[i] = o;
-            }
-        }
-        if (tid == 0) {
-            S.cnt[C_CLUSTERS] = (unsigned long long)ncl;
-            if (STAGED) {
-                S.pend_tile = tile;
-                S.pend_ncl = ncl;
-                S.pend_ntr = ntr_here;
-            }
-        }
-        __syncthreads();
-        if (tid < C_NUM && tid != C_PACKETS && S.cnt[tid]) atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
-        if (tid == 0) {
-            atomicAdd(&p.ctl->counters[C_PACKETS], (unsigned long long)cnt);
-            if (S.status) atomicOr(&p.ctl->status, S.status);
-        }
-    }
-}
-
-int fused_tile_packets() { return T; }
-int fused_threads() { return NT; }
-int fused_smem_bytes() { return (int)sizeof(Smem); }
-
-template <int MODE, bool STAGED>
-cudaError_t launch_one(const Params &p, int grid, cudaStream_t s) {
-    static bool attr_done = false;
-    const int smem = (int)sizeof(Smem);
-    if (!attr_done) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(fused_kernel<MODE, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
-    fused_kernel<MODE, STAGED><<<grid, NT, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s) {
-    if (mode == TPX_MODE_CC) return p.stage ? launch_one<TPX_MODE_CC, true>(p, grid, s) : launch_one<TPX_MODE_CC, false>(p, grid, s);
-    return p.stage ? launch_one<TPX_MODE_PAPER, true>(p, grid, s) : launch_one<TPX_MODE_PAPER, false>(p, grid, s);
-}
-
-int fused_range_capacity() { return C; }
 
 }  // namespace tpxk

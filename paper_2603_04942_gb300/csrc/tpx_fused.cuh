@@ -102,9 +102,12 @@ struct Params {
 
 // launch entry points (defined in tpx_fused.cu)
 namespace tpxk {
-int fused_tile_packets();
-int fused_smem_bytes();
-int fused_threads();
-int fused_range_capacity();
-cudaError_t launch_fused(const Params &p, int mode, int grid, cudaStream_t s);
+// tile geometries of the fused kernel
+enum : int { GEO_T4096 = 1, GEO_T2048 = 2 };
+int fused_tile_packets(int geo);
+int fused_smem_bytes(int geo);
+int fused_threads(int geo);
+int fused_range_capacity(int geo);
+int fused_ctas_per_sm(int geo);
+cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s);
 }  // namespace tpxk

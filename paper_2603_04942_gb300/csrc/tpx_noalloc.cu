@@ -146,7 +146,7 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
         p.ts.cpre = scr->cpre;
         p.ctl = &scr->ctl;
         int64_t grid = num_sms < p.n_tiles ? num_sms : p.n_tiles;
-        if (tpxk::launch_fused(p, cfg->mode, (int)grid, s) != cudaSuccess) return TPX_ECUDA;
+        if (tpxk::launch_fused(p, cfg->mode, tpxk::GEO_T4096, (int)grid, s) != cudaSuccess) return TPX_ECUDA;
     }
 
     // wait for the call and report its device status (a copy to pageable host

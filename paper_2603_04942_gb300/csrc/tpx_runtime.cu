@@ -30,6 +30,8 @@ int check_cfg(const tpx_config *c) {
     if (c->mode != TPX_MODE_CC && c->mode != TPX_MODE_PAPER) return TPX_EINVAL;
     if (c->tof_max_ticks < 0 || c->tof_max_ticks > kMaxTofMax) return TPX_EINVAL;
     if (c->wrap_thr_pix_ticks <= 0 || c->wrap_thr_tdc_ticks <= 0) return TPX_EINVAL;
+    if (c->tile_geometry != TPX_TILE_DEFAULT && c->tile_geometry != TPX_TILE_4096 && c->tile_geometry != TPX_TILE_2048)
+        return TPX_EINVAL;
     return TPX_OK;
 }
 
@@ -42,15 +44,23 @@ void free_scratch(tpx_ctx *c) {
 }
 
 int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
-    const int64_t T = tpxk::fused_tile_packets();
+    // sized for either tile geometry: the smaller tiles need more tile records
+    const int64_t T = tpxk::fused_tile_packets(tpxk::GEO_T2048);
     int64_t tiles = (max_packets + T - 1) / T;
     if (tiles < 1) tiles = 1;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_flags = al(sizeof(unsigned) * tiles), b_agg = al(sizeof(tpxk::GAgg) * tiles),
                  b_cnt = al(sizeof(long long) * tiles);
     // record staging of the fused kernel: one range's records per CTA
-    const int64_t ctas = tiles < c->num_sms ? tiles : c->num_sms;   // the largest grid of a call
-    const size_t b_stage = al(sizeof(tpx_record) * (size_t)tpxk::fused_range_capacity() * (size_t)ctas);
+    size_t stage_records = 0;   // the largest grid of a call times its range capacity
+    for (int geo : {(int)tpxk::GEO_T4096, (int)tpxk::GEO_T2048}) {
+        const int64_t tg = (max_packets + tpxk::fused_tile_packets(geo) - 1) / tpxk::fused_tile_packets(geo);
+        int64_t ctas = (int64_t)c->num_sms * tpxk::fused_ctas_per_sm(geo);
+        if (tg < ctas) ctas = tg < 1 ? 1 : tg;
+        const size_t r = (size_t)ctas * (size_t)tpxk::fused_range_capacity(geo);
+        if (r > stage_records) stage_records = r;
+    }
+    const size_t b_stage = al(sizeof(tpx_record) * stage_records);
     const size_t total = 2 * b_flags + 2 * b_agg + 2 * b_cnt + b_stage;
     void *mem = nullptr;
     if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
@@ -88,6 +98,42 @@ int grow(Tp **ptr, int64_t *cap, int64_t want) {
 
 }  // namespace
 
+namespace {
+
+// ---- tile-geometry autotuner ----
+constexpr int64_t kTuneMinPackets = 1LL << 20;   // smaller calls run untimed on the 4096 tiles
+constexpr double kTunePenalty = 1e30;            // a sample whose call had to be redone
+
+int tune_pick(const tpx_ctx *c, int64_t n) {
+    if (c->cfg.tile_geometry != TPX_TILE_DEFAULT) return c->geo;
+    if (c->tune.fixed) return c->tune.fixed;
+    if (n < kTuneMinPackets) return tpxk::GEO_T4096;
+    // alternate, the smaller tiles first
+    return c->tune.issued[tpxk::GEO_T2048 - 1] <= c->tune.issued[tpxk::GEO_T4096 - 1] ? tpxk::GEO_T2048 : tpxk::GEO_T4096;
+}
+
+// time the samples whose calls have completed (all of them after a sync);
+// `redone_last` marks the newest one as redone by the general path
+void tune_collect(tpx_ctx *c, bool redone_last) {
+    auto &t = c->tune;
+    while (t.head != t.tail) {
+        auto &smp = t.ring[t.head];
+        if (cudaEventQuery(smp.b) != cudaSuccess) { cudaGetLastError(); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, smp.a, smp.b);
+        const bool newest = (t.head + 1) % 8 == t.tail;
+        const double v = (redone_last && newest) ? kTunePenalty : (double)ms * 1e6 / (double)smp.n;
+        const int k = smp.geo - 1;
+        if (t.done[k] == 0 || v < t.best[k]) t.best[k] = v;
+        t.done[k] += 1;
+        t.head = (t.head + 1) % 8;
+    }
+    if (!t.fixed && t.done[0] > 0 && t.done[1] > 0)
+        t.fixed = t.best[tpxk::GEO_T2048 - 1] < t.best[tpxk::GEO_T4096 - 1] ? tpxk::GEO_T2048 : tpxk::GEO_T4096;
+}
+
+}  // namespace
+
 extern "C" {
 
 void tpx_config_default(tpx_config *c) {
@@ -113,6 +159,7 @@ int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *
     if (!c) return TPX_ENOMEM;
     std::memset(c, 0, sizeof *c);
     c->cfg = *cfg;
+    c->geo = cfg->tile_geometry == TPX_TILE_2048 ? (int)tpxk::GEO_T2048 : (int)tpxk::GEO_T4096;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return TPX_ECUDA; }
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -134,6 +181,11 @@ int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *
         return TPX_ENOMEM;
     }
     cudaMemset(c->d_state, 0, 2 * sizeof(tpxk::GAgg));   // all zero = the start of a stream
+    for (auto &smp : c->tune.ring)
+        if (cudaEventCreate(&smp.a) != cudaSuccess || cudaEventCreate(&smp.b) != cudaSuccess) {
+            tpx_destroy(c);
+            return TPX_ECUDA;
+        }
     rc = alloc_scratch(c, max_packets);
     if (rc) {
         cudaFree(c->ctl);
@@ -167,6 +219,10 @@ int tpx_destroy(tpx_ctx *c) {
     if (c->st_counts) cudaFree(c->st_counts);
     if (c->g_mem) cudaFree(c->g_mem);
     if (c->d_state) cudaFree(c->d_state);
+    for (auto &smp : c->tune.ring) {
+        if (smp.a) cudaEventDestroy(smp.a);
+        if (smp.b) cudaEventDestroy(smp.b);
+    }
     delete c;
     return TPX_OK;
 }
@@ -232,7 +288,8 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.tof_max = c->cfg.tof_max_ticks;
     p.thr_pix = c->cfg.wrap_thr_pix_ticks;
     p.thr_tdc = c->cfg.wrap_thr_tdc_ticks;
-    const int64_t T = tpxk::fused_tile_packets();
+    const int geo = tune_pick(c, n);
+    const int64_t T = tpxk::fused_tile_packets(geo);
     p.n_tiles = (n + T - 1) / T;
     p.seq = c->seq;
     p.ts = c->ts;
@@ -240,10 +297,22 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.E0 = E0;
     p.state_out = state_out;
     p.stage = c->stage;
-    int64_t grid = c->num_sms;   // persistent: one CTA per SM
+    int64_t grid = (int64_t)c->num_sms * tpxk::fused_ctas_per_sm(geo);   // persistent, all resident
     if (grid > p.n_tiles) grid = p.n_tiles;
-    cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, (int)grid, c->stream);
-    return e == cudaSuccess ? TPX_OK : TPX_ECUDA;
+    auto &t = c->tune;
+    const bool timed = c->cfg.tile_geometry == TPX_TILE_DEFAULT && !t.fixed && n >= kTuneMinPackets &&
+                       (t.tail + 1) % 8 != t.head;
+    if (timed && cudaEventRecord(t.ring[t.tail].a, c->stream) != cudaSuccess) return TPX_ECUDA;
+    cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, c->stream);
+    if (e != cudaSuccess) return TPX_ECUDA;
+    if (timed) {
+        if (cudaEventRecord(t.ring[t.tail].b, c->stream) != cudaSuccess) return TPX_ECUDA;
+        t.ring[t.tail].geo = geo;
+        t.ring[t.tail].n = n;
+        t.tail = (t.tail + 1) % 8;
+        t.issued[geo - 1] += 1;
+    }
+    return TPX_OK;
 }
 
 int tpx_sync(tpx_ctx *c, tpx_counters *out) {
@@ -264,6 +333,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
             return TPX_ECUDA;
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
     }
+    tune_collect(c, redone != 0);
     const tpxk::Ctl &h = *c->h_ctl;
     if (out) {
         out->packets = (int64_t)h.counters[tpxk::C_PACKETS];
@@ -323,6 +393,17 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     *h_n_clusters = counts[0];
     *h_n_trig = counts[1];
     return tpx_sync(c, nullptr);
+}
+
+int tpx_tuning(tpx_ctx *c, int32_t *tile_geometry, double *ms_per_mpacket) {
+    if (!c || !tile_geometry) return TPX_EINVAL;
+    if (c->cfg.tile_geometry != TPX_TILE_DEFAULT) *tile_geometry = c->cfg.tile_geometry;
+    else *tile_geometry = c->tune.fixed == tpxk::GEO_T2048 ? TPX_TILE_2048 : (c->tune.fixed ? TPX_TILE_4096 : TPX_TILE_DEFAULT);
+    if (ms_per_mpacket) {
+        ms_per_mpacket[0] = c->tune.done[tpxk::GEO_T4096 - 1] ? c->tune.best[tpxk::GEO_T4096 - 1] : 0.0;
+        ms_per_mpacket[1] = c->tune.done[tpxk::GEO_T2048 - 1] ? c->tune.best[tpxk::GEO_T2048 - 1] : 0.0;
+    }
+    return TPX_OK;
 }
 
 int tpx_set_state(tpx_ctx *c, const tpx_stream_state *st) {

@@ -20,11 +20,11 @@ def to_device(pk: np.ndarray):
 
 
 def gpu_run(pk: np.ndarray, *, rx=1, ry=1, dt=32, mode=0, tof_max=64_000, lut=None, strict=False,
-            index_base=0, labels=True, is_peak=True, cluster_capacity=None, trig_capacity=None):
+            index_base=0, labels=True, is_peak=True, cluster_capacity=None, trig_capacity=None, tile=0):
     import torch
     dlut = None if lut is None else torch.from_numpy(np.asarray(lut, np.int16)).cuda()
     cfg = tpx.Config(rx=rx, ry=ry, dt_ticks=dt, mode=mode, tof_max_ticks=tof_max, timewalk_lut=dlut,
-                     strict=strict)
+                     strict=strict, tile_geometry=tile)
     ctx = tpx.Context(cfg, max_packets=max(1, pk.size))
     try:
         d = to_device(pk) if pk.size else torch.zeros(2, dtype=torch.int64, device="cuda")
