@@ -265,6 +265,35 @@ int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t
                         int64_t *d_n_clusters, int64_t *d_trig_t, int64_t trig_capacity,
                         int64_t *d_n_trig, tpx_counters *h_counters);
 
+/* Batched runs (Sec. VI batches shots by zero-padding them to a rectangle;
+   here nothing is padded): n_runs independent acquisitions concatenated in
+   one device buffer, run r being packets [h_run_offsets[r],
+   h_run_offsets[r+1]).  One persistent launch of the fused kernel works
+   through a device queue of tiles of all runs; every run is a stream of its
+   own (unwrap state and trigger count start from zero at its first packet),
+   the context's configuration applies to all.  Runs whose shots do not fit
+   the tiles' ranges are redone exactly by the general path at tpx_sync
+   (counters.redone = the number of such runs) and spliced into the outputs.
+     h_run_offsets   host [n_runs + 1], h_run_offsets[0] = 0, non-decreasing
+     d_labels, d_is_peak  per packet of the whole buffer, or NULL; labels are
+                     positions in the whole buffer
+     d_clusters, cluster_capacity, d_n_clusters   records of all runs, run
+                     after run, each run's in ascending label order; `shot`
+                     counts within the run
+     d_run_clusters  device [n_runs + 1]: first record of each run and the
+                     total (written by the call)
+     d_trig_t, trig_capacity, d_n_trig, d_run_trig   trigger times of all
+                     runs, run after run, with the same offsets layout
+   Asynchronous like tpx_process; tpx_sync returns the status.  The call
+   itself waits only until the previous batch's tables have been uploaded.
+   The first call for a larger batch grows the context's batch scratch.
+   Counters describe the tiles' pass (redone runs included as they ran).
+   TPX_EINVAL for bad offsets or pointers. */
+int tpx_process_batch(tpx_ctx *ctx, const uint64_t *d_packets, const int64_t *h_run_offsets, int64_t n_runs,
+                      int64_t *d_labels, uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cluster_capacity,
+                      int64_t *d_n_clusters, int64_t *d_run_clusters, int64_t *d_trig_t, int64_t trig_capacity,
+                      int64_t *d_n_trig, int64_t *d_run_trig);
+
 /* Tile-geometry autotuner (not in the paper).  With tile_geometry =
    TPX_TILE_DEFAULT the first calls of at least 2^20 packets alternate the
    two geometries, timed with CUDA events on the context stream; at the

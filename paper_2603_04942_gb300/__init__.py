@@ -39,7 +39,7 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_tuning", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_strerror", "tpx_version")
 
@@ -136,6 +136,7 @@ def load(path: str | None = None):
         L.tpx_strerror.restype = ctypes.c_char_p
         L.tpx_version.restype = ctypes.c_char_p
         L.tpx_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+        L.tpx_process_batch.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp]
         L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_set_state.restype = i32
@@ -263,6 +264,35 @@ class Context:
                                _ptr(out["n_trig"]))
         if rc:
             raise TpxError(rc, "tpx_process")
+
+    # -- batches of independent runs, one launch --
+    def alloc_batch_outputs(self, n_packets: int, n_runs: int, labels=False, is_peak=False, cluster_capacity=None,
+                            trig_capacity=None) -> dict:
+        import torch
+        out = self.alloc_outputs(n_packets, labels, is_peak, cluster_capacity, trig_capacity)
+        dev = out["n_clusters"].device
+        out["run_clusters"] = torch.zeros(n_runs + 1, dtype=torch.int64, device=dev)
+        out["run_trig"] = torch.zeros(n_runs + 1, dtype=torch.int64, device=dev)
+        return out
+
+    def tpx_process_batch(self, packets, run_offsets: np.ndarray, out: dict):
+        """Runs [run_offsets[r], run_offsets[r+1]) of the device packets, each
+        a stream of its own, in one launch (host int64 offsets)."""
+        offs = np.ascontiguousarray(run_offsets, dtype=np.int64)
+        self._batch_offs = offs   # the call reads them before it returns; kept for the caller's reference
+        rc = lib().tpx_process_batch(self._h, _ptr(packets), offs.ctypes.data, offs.size - 1, _ptr(out["labels"]),
+                                     _ptr(out["is_peak"]), _ptr(out["clusters"]), out["cluster_capacity"],
+                                     _ptr(out["n_clusters"]), _ptr(out["run_clusters"]), _ptr(out["trig"]),
+                                     out["trig_capacity"], _ptr(out["n_trig"]), _ptr(out["run_trig"]))
+        if rc:
+            raise TpxError(rc, "tpx_process_batch")
+
+    @staticmethod
+    def collect_batch(out: dict, rc: int, counters: dict) -> dict:
+        r = Context.collect(out, rc, counters)
+        r["run_clusters"] = out["run_clusters"].cpu().numpy()
+        r["run_trig"] = out["run_trig"].cpu().numpy()
+        return r
 
     def tpx_sync(self, check: bool = True) -> tuple[int, dict]:
         cnt = _CCounters()

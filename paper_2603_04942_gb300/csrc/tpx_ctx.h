@@ -30,6 +30,7 @@ struct tpx_ctx {
     tpxk::TileScratch ts;
     void *scratch;            // one allocation for all tile records
     tpx_record *stage;        // fused-kernel record staging (inside scratch)
+    int64_t stage_records;    // its capacity
     tpxk::Ctl *ctl;           // device control block
     tpxk::Ctl *h_ctl;         // pinned host copy
     // device staging for tpx_process_host
@@ -67,6 +68,29 @@ struct tpx_ctx {
         const tpxk::GAgg *E0;
         tpxk::GAgg *state_out;
     } last;
+    // batches of runs (tpx_process_batch): tile queue, run tables, their own
+    // tile records and trigger staging, grown on demand; the last batch call
+    struct Batch {
+        void *dev;
+        size_t dev_bytes;
+        int64_t *h_tab;           // pinned: run offsets, run first tiles, tile runs
+        size_t h_bytes;
+        cudaEvent_t tab_copied;   // the tables' upload has run: the host copy may change
+        tpxk::TileScratch ts;
+        tpxk::BatchTable bt;
+        bool last;                // the last call on the context was a batch
+        const uint64_t *pk;
+        int64_t n_runs;
+        int64_t *labels;
+        uint8_t *is_peak;
+        tpx_record *cl;
+        int64_t cl_cap;
+        int64_t *n_cl;
+        int64_t *trig;
+        int64_t trig_cap;
+        int64_t *n_trig;
+        int64_t redone;           // runs redone by the last tpx_sync
+    } batch;
 };
 
 // state for the next call and where it leaves its final state (advances the
@@ -80,6 +104,9 @@ int reserve(tpx_ctx *c, size_t bytes);
 // exact redo of the last tpx_process call with the general path; returns
 // the status of the redone call
 int redo_last(tpx_ctx *c);
+// exact redo of the runs of the last batch call that the tiles could not
+// hold, spliced into the call's outputs; *n_redone receives their number
+int redo_batch(tpx_ctx *c, int64_t *n_redone);
 int decode_impl(tpx_ctx *c, const uint64_t *pk, int64_t n, int64_t base, const tpx_hits &h, int64_t cap,
                 int64_t *d_n_hits, int64_t *trig, int64_t trig_cap, int64_t *d_n_trig, bool clear_ctl,
                 const tpxk::GAgg *E0, tpxk::GAgg *state_out, long long *trig_pos, long long **t_all_out);

@@ -45,6 +45,7 @@ enum : unsigned {
     ST_CLUSTER_CAP = 1u << 4,  // caller cluster buffer too small
     ST_TRIG_CAP = 1u << 5,     // caller trigger buffer too small
     ST_DEVTIMEOUT = 1u << 6,   // a look-back wait ran out
+    ST_RUN_REDO = 1u << 7,     // batch: a run needs the general path (see run_failed)
 };
 
 enum CounterIdx {
@@ -72,6 +73,20 @@ struct TileScratch {
     long long *cpre;         // [tiles]
 };
 
+// a batch of independent runs in one launch: the tile queue and per-run
+// outputs (all device memory)
+struct BatchTable {
+    const int *tile_run;          // [tiles] run of each tile
+    const long long *run_tile0;   // [runs] first tile of each run
+    const long long *run_off;     // [runs + 1] packet offsets of the runs
+    long long *run_rec_off;       // [runs + 1] out: record offsets
+    long long *run_trig_off;      // [runs + 1] out: trigger offsets
+    unsigned *run_failed;         // [runs] out: 1 = a range the tiles cannot hold
+    long long *tcagg, *tcpre;     // [tiles] trigger-count chain
+    long long *tstage;            // [grid * tile packets] trigger staging
+    long long n_runs;
+};
+
 struct Params {
     const uint64_t *pk;
     long long n;
@@ -94,6 +109,7 @@ struct Params {
     Ctl *ctl;
     tpx_record *stage;       // per-CTA record staging (range-capacity records per
                              // CTA of the grid), or NULL: inline offset look-back
+    BatchTable bt;           // batch of runs (tile_run == NULL: one stream)
     const GAgg *E0;          // unwrap state before the call (NULL: stream start)
     GAgg *state_out;         // state after the call, written by the last tile (or NULL)
 };

@@ -103,7 +103,11 @@ struct __align__(16) Smem {
     long long clo;
     long long pend_tile;          // staged records awaiting their offset (-1: none)
     long long pend_ntr;
+    long long tlo;                // trigger offset of a batch tile
     int pend_ncl;
+    int pend_ntdc;                // batch: the pending tile's triggers, its run,
+    int pend_run;                 // and whether it is the run's first tile
+    bool pend_first;
     int first_tdc;
     int la_first;
     unsigned status;
@@ -198,13 +202,13 @@ constexpr int LBA = 1, LBC = 4;
 // per lane: which of its LB tiles are needed this trip, given the flags
 struct LbScan { unsigned need, inc; int stop; bool ok; };
 template <int LB>
-__device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, unsigned seq) {
+__device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, long long lo, unsigned seq) {
     const int lane = threadIdx.x & 31;
     unsigned rdy = 0, inc = 0;
 #pragma unroll
     for (int j = 0; j < LB; ++j) {
         const long long q = hi - LB * lane - j;
-        if (q < 0) { rdy |= 1u << j; continue; }
+        if (q < lo) { rdy |= 1u << j; continue; }
         const unsigned f = ld_acquire(&flags[q]);
         if ((f >> 2) == seq && (f & 3u)) {
             rdy |= 1u << j;
@@ -224,14 +228,17 @@ __device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, u
 // buf: 32 GAgg slots in shared memory, owned by the look-back warp. The
 // combine is a tree over the slots (few live registers: the kernel runs at
 // the 64-register limit of a 1024-thread CTA). Lane 0 returns the prefix.
-__device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq, unsigned *status, GAgg *buf) {
+// Tiles before lo (the first tile of the stream: 0, or the run's first tile
+// in a batch) are not part of the chain.
+__device__ GAgg lookback_agg_warp(const Params &p, long long tile, long long lo, unsigned seq, unsigned *status,
+                                  GAgg *buf) {
     const int lane = threadIdx.x & 31;
     GAgg acc = agg_id();
-    for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBA) {
+    for (long long hi = tile - 1; hi >= lo; hi -= 32 * LBA) {
         LbScan sc;
         long long spins = 0;
         for (;;) {
-            sc = lb_scan<LBA>(p.ts.flags, hi, seq);
+            sc = lb_scan<LBA>(p.ts.flags, hi, lo, seq);
             if (__all_sync(0xffffffffu, sc.ok)) break;
             if (++spins > MAX_SPIN || timed_out(p)) {
                 if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
@@ -245,7 +252,7 @@ __device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq,
         {
             const long long q = hi - lane;
             const ulonglong2 *src = nullptr;
-            if (q >= 0 && (sc.need & 1u)) src = reinterpret_cast<const ulonglong2 *>((sc.inc & 1u) ? &p.ts.pre[q] : &p.ts.agg[q]);
+            if (q >= lo && (sc.need & 1u)) src = reinterpret_cast<const ulonglong2 *>((sc.inc & 1u) ? &p.ts.pre[q] : &p.ts.agg[q]);
             ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&buf[lane]);
 #pragma unroll
             for (int k = 0; k < 4; ++k) dst[k] = src ? __ldcg(src + k) : make_ulonglong2(0ull, 0ull);
@@ -264,15 +271,17 @@ __device__ GAgg lookback_agg_warp(const Params &p, long long tile, unsigned seq,
     return acc;
 }
 
-// The same over the record counts of the tiles.
-__device__ long long lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
+// The same over the record counts of the tiles (and, in a batch, their
+// trigger counts: .y), over all tiles of the call.
+template <bool BATCH>
+__device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
     const int lane = threadIdx.x & 31;
-    long long acc = 0;
+    longlong2 acc = make_longlong2(0, 0);
     for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBC) {
         LbScan sc;
         long long spins = 0;
         for (;;) {
-            sc = lb_scan<LBC>(p.ts.cflags, hi, seq);
+            sc = lb_scan<LBC>(p.ts.cflags, hi, 0, seq);
             if (__all_sync(0xffffffffu, sc.ok)) break;
             if (++spins > MAX_SPIN || timed_out(p)) {
                 if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
@@ -281,16 +290,22 @@ __device__ long long lookback_count_warp(const Params &p, long long tile, unsign
             }
             __nanosleep(64);
         }
-        long long v = 0;
+        long long v = 0, w = 0;
 #pragma unroll
         for (int j = 0; j < LBC; ++j) {
             const long long q = hi - LBC * lane - j;
             if (q < 0 || !((sc.need >> j) & 1u)) continue;
-            v += __ldcg(((sc.inc >> j) & 1u) ? &p.ts.cpre[q] : &p.ts.cagg[q]);
+            const bool inc = (sc.inc >> j) & 1u;
+            v += __ldcg(inc ? &p.ts.cpre[q] : &p.ts.cagg[q]);
+            if (BATCH) w += __ldcg(inc ? &p.bt.tcpre[q] : &p.bt.tcagg[q]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc += v;
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (BATCH) w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        acc.x += v;
+        acc.y += w;
         if (__any_sync(0xffffffffu, sc.inc != 0)) break;
     }
     return acc;
@@ -314,36 +329,53 @@ __device__ void unite_one(const Smem &S, uint32_t pbase, uint32_t a, uint32_t b)
 
 // Warp 0 resolves the record offset of tile tl holding nc records (decoupled
 // look-back over the counts), publishes its inclusive count and, for the last
-// tile, the call's totals; the offset is left in S.clo.
-__device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr) {
+// tile, the call's totals; the offset is left in S.clo. In a batch the chain
+// also carries the tile's nt triggers (offset in S.tlo), and a run's first
+// tile records the run's record and trigger offsets.
+template <bool BATCH>
+__device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr, int nt,
+                               int run, bool run_first) {
     if (threadIdx.x >= 32) return;
     unsigned st2 = 0;
-    long long Ow = 0;
-    if (tl > 0) Ow = lookback_count_warp(p, tl, seq, &st2);
+    longlong2 Ow = make_longlong2(0, 0);
+    if (tl > 0) Ow = lookback_count_warp<BATCH>(p, tl, seq, &st2);
     if (threadIdx.x == 0) {
         if (tl > 0) {
-            __stcg(&p.ts.cpre[tl], Ow + (long long)nc);
+            __stcg(&p.ts.cpre[tl], Ow.x + (long long)nc);
+            if (BATCH) __stcg(&p.bt.tcpre[tl], Ow.y + (long long)nt);
             st_release(&p.ts.cflags[tl], (seq << 2) | 2u);
         }
-        S.clo = Ow;
+        S.clo = Ow.x;
+        S.tlo = Ow.y;
         if (st2) atomicOr(&S.status, st2);
+        if (BATCH && run_first) {
+            p.bt.run_rec_off[run] = Ow.x;
+            p.bt.run_trig_off[run] = Ow.y;
+        }
         if (tl == p.n_tiles - 1) {
-            *p.n_clusters = Ow + nc;
-            *p.n_trig = ntr;
-            if (Ow + nc > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
-            if (ntr > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
+            const long long nt_all = BATCH ? Ow.y + nt : ntr;
+            *p.n_clusters = Ow.x + nc;
+            *p.n_trig = nt_all;
+            if (BATCH) {
+                p.bt.run_rec_off[p.bt.n_runs] = Ow.x + nc;
+                p.bt.run_trig_off[p.bt.n_runs] = nt_all;
+            }
+            if (Ow.x + nc > p.cl_cap) atomicOr(&p.ctl->status, ST_CLUSTER_CAP);
+            if (nt_all > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
         }
     }
 }
 
-// Staged output: a tile's records wait in the CTA's staging slot until the
-// next tile (or the end of the kernel) resolves their offset, when the
-// predecessors' counts are long published; then one coalesced copy.
+// Staged output: a tile's records (and, in a batch, its trigger times) wait
+// in the CTA's staging slot until the next tile (or the end of the kernel)
+// resolves their offset, when the predecessors' counts are long published;
+// then one coalesced copy.
+template <bool BATCH>
 __device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
     const long long pt = S.pend_tile;
     if (pt < 0) return;
-    const int nc = S.pend_ncl;
-    resolve_offset(S, p, seq, pt, nc, S.pend_ntr);
+    const int nc = S.pend_ncl, nt = S.pend_ntdc;
+    resolve_offset<BATCH>(S, p, seq, pt, nc, S.pend_ntr, nt, S.pend_run, S.pend_first);
     __syncthreads();
     const long long O = S.clo;
     const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
@@ -351,12 +383,18 @@ __device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
     const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
     for (long long w = threadIdx.x; w < keep * WPR; w += NT) dst[w] = __ldcg(src + w);
+    if (BATCH) {
+        const long long TO = S.tlo;
+        const long long tkeep = min((long long)nt, max(0LL, p.trig_cap - TO));
+        const long long *ts = p.bt.tstage + (long long)blockIdx.x * T;
+        for (long long i = threadIdx.x; i < tkeep; i += NT) p.trig[TO + i] = __ldcg(ts + i);
+    }
     __syncthreads();
     if (threadIdx.x == 0) S.pend_tile = -1;
 }
 
 // ------------------------------------------------------------------- kernel
-template <int MODE, bool STAGED>
+template <int MODE, bool STAGED, bool BATCH>
 __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -378,16 +416,29 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         const long long tile = S.tile;
         if (tile >= p.n_tiles) {
             if (STAGED) {
-                flush_pending(S, p, seq);
+                flush_pending<BATCH>(S, p, seq);
                 if (tid == 0 && S.status) atomicOr(&p.ctl->status, S.status);
             }
             break;
         }
-        const long long base = tile * T;
-        const int cnt = (int)min((long long)T, p.n - base);
+        // the tile: in a batch, the tile queue names the run (each run is a
+        // stream of its own: the chains start over at its first tile)
+        int run = 0;
+        long long tile0 = 0, rend = p.n, base;
+        if (BATCH) {
+            run = p.bt.tile_run[tile];
+            tile0 = p.bt.run_tile0[run];
+            base = p.bt.run_off[run] + (tile - tile0) * T;
+            rend = p.bt.run_off[run + 1];
+        } else {
+            base = tile * T;
+        }
+        const int cnt = (int)max(0LL, min((long long)T, rend - base));
 
         // ---- load the tile: coalesced 16-byte loads into the padded buffer ----
-        {
+        if (BATCH && (base & 1)) {   // a run starting at an odd packet: 8-byte loads
+            for (int v = tid; v < cnt; v += NT) S.buf[pad(v)] = __ldcg(p.pk + base + v);
+        } else {
             const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.pk + base);
             const int npair = cnt >> 1;
             for (int v = tid; v < npair; v += NT) {
@@ -428,14 +479,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // read-ahead and the block scan, which do not need it
         if (tid == 0) {
             S.tile_agg = S.tot_agg;
-            if (tile > 0) {
+            if (tile > tile0) {
                 st_agg(&p.ts.agg[tile], S.tot_agg);
                 st_release(&p.ts.flags[tile], (seq << 2) | 1u);
             } else {
-                const GAgg e0 = p.E0 ? *p.E0 : agg_id();
+                const GAgg e0 = (!BATCH && p.E0) ? *p.E0 : agg_id();
                 S.E = e0;
-                st_agg(&p.ts.pre[0], acomb(e0, S.tot_agg, tp, tt));
-                st_release(&p.ts.flags[0], (seq << 2) | 2u);
+                st_agg(&p.ts.pre[tile], acomb(e0, S.tot_agg, tp, tt));
+                st_release(&p.ts.flags[tile], (seq << 2) | 2u);
             }
         }
         __syncthreads();
@@ -445,10 +496,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         int L = cnt;
         bool term = false;
         if (f != INT_MAX) {
-            while (base + L < p.n) {
+            while (base + L < rend) {
                 const int room = C - L;
                 if (room <= 0) break;
-                const int chunk = (int)min((long long)min(NT, room), p.n - (base + L));
+                const int chunk = (int)min((long long)min(NT, room), rend - (base + L));
                 bool is_t = false;
                 if (tid < chunk) {
                     const uint64_t w = __ldcg(p.pk + base + L + tid);
@@ -464,7 +515,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (lf != INT_MAX) { L += lf + 1; term = true; break; }
                 L += chunk;
             }
-            if (!term && base + L < p.n && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+            if (!term && base + L < rend && tid == 0) atomicOr(&S.status, ST_CAPACITY);
         }
 
         // ---- walk 2: per-thread chain state over [0, L) ----
@@ -488,14 +539,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         if (tid < 32) {
             unsigned stl = 0;
             GAgg Ew = agg_id();
-            if (tile > 0) Ew = lookback_agg_warp(p, tile, seq, &stl, S.lb_buf);
-            else Ew = p.E0 ? *p.E0 : agg_id();
+            if (tile > tile0) Ew = lookback_agg_warp(p, tile, tile0, seq, &stl, S.lb_buf);
+            else Ew = (!BATCH && p.E0) ? *p.E0 : agg_id();
             if (tid == 0) {
-                if (tile > 0) {
+                if (tile > tile0) {
                     st_agg(&p.ts.pre[tile], acomb(Ew, S.tile_agg, tp, tt));
                     st_release(&p.ts.flags[tile], (seq << 2) | 2u);
                 }
-                if (tile == p.n_tiles - 1 && p.state_out) *p.state_out = acomb(Ew, S.tile_agg, tp, tt);
+                if (!BATCH && tile == p.n_tiles - 1 && p.state_out) *p.state_out = acomb(Ew, S.tile_agg, tp, tt);
                 S.E = Ew;
                 if (stl) atomicOr(&S.status, stl);
             }
@@ -503,7 +554,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         __syncthreads();
         const GAgg E = S.E;
         // a call sees only its own triggers: "earlier" means earlier in this call
-        const long long trig_base = p.E0 ? p.E0->tdc.n : 0;
+        const long long trig_base = (!BATCH && p.E0) ? p.E0->tdc.n : 0;
         const bool prev_global = E.tdc.n > trig_base;
         const GAgg st = acomb(E, ex, tp, tt);   // global chain state before position p0
 
@@ -523,7 +574,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 last = r;
                 const long long t = r + ep * kTdcPeriod;
                 if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
-                if (q < cnt) {
+                if (!BATCH && q < cnt) {   // a batch writes its triggers at the flush
                     const long long g = E.tdc.n - trig_base + li;
                     if (g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
                 }
@@ -769,9 +820,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         if (tid == 0) {
             if (tile > 0) {
                 __stcg(&p.ts.cagg[tile], (long long)ncl);
+                if (BATCH) __stcg(&p.bt.tcagg[tile], (long long)S.cnt[C_TDCS]);
                 st_release(&p.ts.cflags[tile], (seq << 2) | 1u);
             } else {
                 __stcg(&p.ts.cpre[0], (long long)ncl);
+                if (BATCH) __stcg(&p.bt.tcpre[0], (long long)S.cnt[C_TDCS]);
                 st_release(&p.ts.cflags[0], (seq << 2) | 2u);
             }
         }
@@ -780,12 +833,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // offset after an inline look-back
         auto record_target = [&](long long *lim) -> tpx_record * {
             if (STAGED) {
-                flush_pending(S, p, seq);
+                flush_pending<BATCH>(S, p, seq);
                 __syncthreads();   // the member lists / peak list are complete
                 *lim = C;
                 return p.stage + (long long)blockIdx.x * C;
             }
-            resolve_offset(S, p, seq, tile, ncl, ntr_here);
+            resolve_offset<false>(S, p, seq, tile, ncl, ntr_here, 0, 0, false);
             __syncthreads();
             *lim = p.cl_cap - S.clo;
             return p.clusters + S.clo;
@@ -902,40 +955,57 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 dst[i] = o;
             }
         }
+        if (BATCH) {   // this tile's trigger times wait with its records
+            const int nt = min((int)S.cnt[C_TDCS], MAXSEG);
+            long long *ts = p.bt.tstage + (long long)blockIdx.x * T;
+            for (int i = tid; i < nt; i += NT) ts[i] = S.tdc_t[i];
+        }
         if (tid == 0) {
             S.cnt[C_CLUSTERS] = (unsigned long long)ncl;
             if (STAGED) {
                 S.pend_tile = tile;
                 S.pend_ncl = ncl;
                 S.pend_ntr = ntr_here;
+                S.pend_ntdc = (int)S.cnt[C_TDCS];
+                S.pend_run = run;
+                S.pend_first = tile == tile0;
             }
         }
         __syncthreads();
         if (tid < C_NUM && tid != C_PACKETS && S.cnt[tid]) atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
         if (tid == 0) {
             atomicAdd(&p.ctl->counters[C_PACKETS], (unsigned long long)cnt);
-            if (S.status) atomicOr(&p.ctl->status, S.status);
+            unsigned st = S.status;
+            if (BATCH && (st & (ST_CAPACITY | ST_EXCEPTION))) {   // only this run is redone
+                p.bt.run_failed[run] = 1u;
+                st = (st & ~(ST_CAPACITY | ST_EXCEPTION)) | ST_RUN_REDO;
+            }
+            if (st) atomicOr(&p.ctl->status, st);
         }
     }
 }
 
 int smem_bytes() { return (int)sizeof(Smem); }
 
-template <int MODE, bool STAGED>
+template <int MODE, bool STAGED, bool BATCH>
 cudaError_t launch_one(const Params &p, int grid, cudaStream_t s) {
     static bool attr_done = false;
     const int smem = (int)sizeof(Smem);
     if (!attr_done) {
         const cudaError_t e =
-            cudaFuncSetAttribute(fused_kernel<MODE, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaFuncSetAttribute(fused_kernel<MODE, STAGED, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    fused_kernel<MODE, STAGED><<<grid, NT, smem, s>>>(p);
+    fused_kernel<MODE, STAGED, BATCH><<<grid, NT, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch(const Params &p, int mode, int grid, cudaStream_t s) {
-    if (mode == TPX_MODE_CC) return p.stage ? launch_one<TPX_MODE_CC, true>(p, grid, s) : launch_one<TPX_MODE_CC, false>(p, grid, s);
-    return p.stage ? launch_one<TPX_MODE_PAPER, true>(p, grid, s) : launch_one<TPX_MODE_PAPER, false>(p, grid, s);
+    const bool cc = mode == TPX_MODE_CC;
+    if (p.bt.tile_run)   // a batch always stages its output
+        return cc ? launch_one<TPX_MODE_CC, true, true>(p, grid, s) : launch_one<TPX_MODE_PAPER, true, true>(p, grid, s);
+    if (p.stage)
+        return cc ? launch_one<TPX_MODE_CC, true, false>(p, grid, s) : launch_one<TPX_MODE_PAPER, true, false>(p, grid, s);
+    return cc ? launch_one<TPX_MODE_CC, false, false>(p, grid, s) : launch_one<TPX_MODE_PAPER, false, false>(p, grid, s);
 }

@@ -26,6 +26,8 @@
 #include <climits>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
+#include <vector>
 
 #include "tpx.h"
 #include "tpx_common.cuh"
@@ -1373,6 +1375,136 @@ int redo_last(tpx_ctx *c) {
         rc = ck(cudaMemcpyAsync(&c->ctl->counters[C_PACKETS], &np, 8, cudaMemcpyHostToDevice, s));
     }
     if (!rc) rc = ck(cudaStreamSynchronize(s));
+    cudaFree(hm);
+    return rc;
+}
+
+int redo_batch(tpx_ctx *c, int64_t *n_redone) {
+    auto &B = c->batch;
+    cudaStream_t s = c->stream;
+    const int64_t R = B.n_runs;
+    const int64_t *off = B.h_tab;   // the run offsets of the call (host)
+    *n_redone = 0;
+    std::vector<unsigned> failed((size_t)R);
+    std::vector<int64_t> roff((size_t)R + 1), toff((size_t)R + 1);
+    Ctl snap;
+    if (cudaMemcpyAsync(failed.data(), B.bt.run_failed, 4 * (size_t)R, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(roff.data(), B.bt.run_rec_off, 8 * (size_t)(R + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(toff.data(), B.bt.run_trig_off, 8 * (size_t)(R + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&snap, c->ctl, sizeof snap, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPX_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    int64_t first = -1, max_len = 0, sum_len = 0;
+    for (int64_t r = 0; r < R; ++r)
+        if (failed[(size_t)r]) {
+            if (first < 0) first = r;
+            const int64_t len = off[r + 1] - off[r];
+            if (len > max_len) max_len = len;
+            sum_len += len;
+            *n_redone += 1;
+        }
+    if (first < 0) return TPX_OK;
+    if (max_len >= (1LL << 31)) return TPX_EUNSUPPORTED;
+    // per-run temporaries (hits, per-hit outputs, triggers) and the redone
+    // runs' records and triggers, back to back
+    const int64_t old_rec = roff[(size_t)R] - roff[(size_t)first], old_trig = toff[(size_t)R] - toff[(size_t)first];
+    const size_t hb = sz(max_len, 8) * 5 + sz(max_len, 4) + sz(max_len, 2) + 3 * sz(max_len, 1) + sz(4, 8) +
+                      sz(sum_len, sizeof(tpx_record)) + sz(sum_len, 8) + sz(old_rec, sizeof(tpx_record)) +
+                      sz(old_trig, 8) + 4096;
+    void *hm = nullptr;
+    if (cudaMalloc(&hm, hb) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
+    Arena a{static_cast<char *>(hm), 0, hb};
+    tpx_hits h;
+    h.index = reinterpret_cast<int64_t *>(a.take<long long>(max_len));
+    h.shot = reinterpret_cast<int64_t *>(a.take<long long>(max_len));
+    h.t = reinterpret_cast<int64_t *>(a.take<long long>(max_len));
+    h.tof = a.take<int32_t>(max_len);
+    h.x = a.take<uint8_t>(max_len);
+    h.y = a.take<uint8_t>(max_len);
+    h.tot = a.take<uint16_t>(max_len);
+    long long *hl = a.take<long long>(max_len);
+    unsigned char *hp = a.take<unsigned char>(max_len);
+    long long *tr = a.take<long long>(max_len);
+    long long *cnt = a.take<long long>(4);   // n_hits, n_trig, n_clusters
+    tpx_record *acc_rec = a.take<tpx_record>(sum_len);
+    long long *acc_trig = a.take<long long>(sum_len);
+    tpx_record *old_rec_copy = a.take<tpx_record>(old_rec);
+    long long *old_trig_copy = a.take<long long>(old_trig);
+    std::vector<int64_t> nrec((size_t)R), ntrg((size_t)R), rstart((size_t)R), tstart((size_t)R);
+    int64_t rec_used = 0, trig_used = 0;
+    int rc = TPX_OK;
+    for (int64_t r = first; r < R && !rc; ++r) {
+        if (!failed[(size_t)r]) continue;
+        const int64_t len = off[r + 1] - off[r];
+        rc = decode_impl(c, B.pk + off[r], len, off[r], h, len, reinterpret_cast<int64_t *>(cnt),
+                         reinterpret_cast<int64_t *>(tr), len, reinterpret_cast<int64_t *>(cnt + 1), false, nullptr,
+                         nullptr, nullptr, nullptr);
+        long long hc[3] = {0, 0, 0};
+        if (!rc) rc = ck(cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, s));
+        if (!rc) rc = ck(cudaStreamSynchronize(s));
+        if (!rc) rc = cluster_all(c, h, hc[0], reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, -1, acc_rec + rec_used,
+                                  hc[0], reinterpret_cast<int64_t *>(cnt + 2));
+        if (!rc && (B.labels || B.is_peak)) {
+            if (B.labels) k_fill_ll<<<grid_for(len), GT, 0, s>>>(reinterpret_cast<long long *>(B.labels) + off[r], len, -1);
+            if (B.is_peak && cudaMemsetAsync(B.is_peak + off[r], 0, (size_t)len, s) != cudaSuccess) rc = TPX_ECUDA;
+            if (hc[0] > 0)
+                k_packet_outputs<<<grid_for(hc[0]), GT, 0, s>>>(h, hl, hp, hc[0], 0, reinterpret_cast<long long *>(B.labels),
+                                                               B.is_peak);
+        }
+        if (!rc && hc[0] > 0) rc = ck(cudaMemcpyAsync(&hc[2], cnt + 2, 8, cudaMemcpyDeviceToHost, s));
+        if (!rc && hc[1] > 0)
+            rc = ck(cudaMemcpyAsync(acc_trig + trig_used, tr, 8 * (size_t)hc[1], cudaMemcpyDeviceToDevice, s));
+        if (!rc) rc = ck(cudaStreamSynchronize(s));
+        if (rc) break;
+        if (hc[0] == 0) hc[2] = 0;
+        nrec[(size_t)r] = hc[2];
+        ntrg[(size_t)r] = hc[1];
+        rstart[(size_t)r] = rec_used;
+        tstart[(size_t)r] = trig_used;
+        rec_used += hc[2];
+        trig_used += hc[1];
+    }
+    // the runs' final offsets, and the outputs from the first redone run on
+    std::vector<long long> NO((size_t)R + 1), NTo((size_t)R + 1);
+    NO[0] = 0;
+    NTo[0] = 0;
+    for (int64_t r = 0; r < R && !rc; ++r) {
+        const int64_t nr = failed[(size_t)r] ? nrec[(size_t)r] : roff[(size_t)r + 1] - roff[(size_t)r];
+        const int64_t nt = failed[(size_t)r] ? ntrg[(size_t)r] : toff[(size_t)r + 1] - toff[(size_t)r];
+        NO[(size_t)r + 1] = NO[(size_t)r] + nr;
+        NTo[(size_t)r + 1] = NTo[(size_t)r] + nt;
+    }
+    if (!rc && old_rec > 0)
+        rc = ck(cudaMemcpyAsync(old_rec_copy, B.cl + roff[(size_t)first], sizeof(tpx_record) * (size_t)old_rec,
+                                cudaMemcpyDeviceToDevice, s));
+    if (!rc && old_trig > 0)
+        rc = ck(cudaMemcpyAsync(old_trig_copy, B.trig + toff[(size_t)first], 8 * (size_t)old_trig, cudaMemcpyDeviceToDevice, s));
+    for (int64_t r = first; r < R && !rc; ++r) {
+        const int64_t nr = NO[(size_t)r + 1] - NO[(size_t)r], nt = NTo[(size_t)r + 1] - NTo[(size_t)r];
+        const int64_t kr = std::max<int64_t>(0, std::min<int64_t>(nr, B.cl_cap - NO[(size_t)r]));
+        const int64_t kt = std::max<int64_t>(0, std::min<int64_t>(nt, B.trig_cap - NTo[(size_t)r]));
+        const tpx_record *sr = failed[(size_t)r] ? acc_rec + rstart[(size_t)r] : old_rec_copy + (roff[(size_t)r] - roff[(size_t)first]);
+        const long long *st = failed[(size_t)r] ? acc_trig + tstart[(size_t)r] : old_trig_copy + (toff[(size_t)r] - toff[(size_t)first]);
+        if (kr > 0) rc = ck(cudaMemcpyAsync(B.cl + NO[(size_t)r], sr, sizeof(tpx_record) * (size_t)kr, cudaMemcpyDeviceToDevice, s));
+        if (!rc && kt > 0) rc = ck(cudaMemcpyAsync(B.trig + NTo[(size_t)r], st, 8 * (size_t)kt, cudaMemcpyDeviceToDevice, s));
+    }
+    if (!rc) {
+        // offsets, totals; the counters keep describing the tiles' pass
+        snap.counters[C_CLUSTERS] = (unsigned long long)NO[(size_t)R];
+        if (NO[(size_t)R] > B.cl_cap) snap.status |= ST_CLUSTER_CAP;
+        if (NTo[(size_t)R] > B.trig_cap) snap.status |= ST_TRIG_CAP;
+        Ctl cur;
+        rc = ck(cudaMemcpyAsync(&cur, c->ctl, sizeof cur, cudaMemcpyDeviceToHost, s));
+        if (!rc) rc = ck(cudaStreamSynchronize(s));
+        snap.status |= cur.status & ST_TRIG_ORDER;   // a redone run may have decreasing triggers
+        if (!rc) rc = ck(cudaMemcpyAsync(B.bt.run_rec_off, NO.data(), 8 * (size_t)(R + 1), cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(B.bt.run_trig_off, NTo.data(), 8 * (size_t)(R + 1), cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(B.n_cl, &NO[(size_t)R], 8, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(B.n_trig, &NTo[(size_t)R], 8, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(c->ctl, &snap, sizeof snap, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaStreamSynchronize(s));
+    }
+    cudaStreamSynchronize(s);
     cudaFree(hm);
     return rc;
 }

@@ -60,6 +60,7 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
         const size_t r = (size_t)ctas * (size_t)tpxk::fused_range_capacity(geo);
         if (r > stage_records) stage_records = r;
     }
+    c->stage_records = (int64_t)stage_records;
     const size_t b_stage = al(sizeof(tpx_record) * stage_records);
     const size_t total = 2 * b_flags + 2 * b_agg + 2 * b_cnt + b_stage;
     void *mem = nullptr;
@@ -186,6 +187,10 @@ int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *
             tpx_destroy(c);
             return TPX_ECUDA;
         }
+    if (cudaEventCreateWithFlags(&c->batch.tab_copied, cudaEventDisableTiming) != cudaSuccess) {
+        tpx_destroy(c);
+        return TPX_ECUDA;
+    }
     rc = alloc_scratch(c, max_packets);
     if (rc) {
         cudaFree(c->ctl);
@@ -223,6 +228,9 @@ int tpx_destroy(tpx_ctx *c) {
         if (smp.a) cudaEventDestroy(smp.a);
         if (smp.b) cudaEventDestroy(smp.b);
     }
+    if (c->batch.tab_copied) cudaEventDestroy(c->batch.tab_copied);
+    if (c->batch.dev) cudaFree(c->batch.dev);
+    if (c->batch.h_tab) cudaFreeHost(c->batch.h_tab);
     delete c;
     return TPX_OK;
 }
@@ -237,6 +245,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
     c->last.valid = true;
+    c->batch.last = false;
     c->last.pk = d_packets;
     c->last.n = n;
     c->last.base = idx_base;
@@ -315,6 +324,169 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     return TPX_OK;
 }
 
+int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_run_offsets, int64_t n_runs,
+                      int64_t *d_labels, uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cl_cap,
+                      int64_t *d_n_clusters, int64_t *d_run_clusters, int64_t *d_trig, int64_t trig_cap,
+                      int64_t *d_n_trig, int64_t *d_run_trig) {
+    if (!c || !h_run_offsets || n_runs < 1 || cl_cap < 0 || trig_cap < 0 || !d_n_clusters || !d_n_trig ||
+        !d_run_clusters || !d_run_trig)
+        return TPX_EINVAL;
+    if (h_run_offsets[0] != 0) return TPX_EINVAL;
+    for (int64_t r = 0; r < n_runs; ++r)
+        if (h_run_offsets[r + 1] < h_run_offsets[r]) return TPX_EINVAL;
+    const int64_t n = h_run_offsets[n_runs];
+    if (n > (1LL << 40) || n_runs > (1LL << 30)) return TPX_EINVAL;
+    if (n > 0 && !d_packets) return TPX_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_packets) & 15) != 0) return TPX_EINVAL;
+    if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
+    if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
+    cudaStream_t s = c->stream;
+    const int geo = tune_pick(c, n);
+    const int64_t T = tpxk::fused_tile_packets(geo), C = tpxk::fused_range_capacity(geo);
+    // the tile queue: every run gets at least one tile (an empty run's tile
+    // still records the run's offsets)
+    int64_t n_tiles = 0;
+    for (int64_t r = 0; r < n_runs; ++r) {
+        const int64_t len = h_run_offsets[r + 1] - h_run_offsets[r];
+        n_tiles += len > 0 ? (len + T - 1) / T : 1;
+    }
+    if (n_tiles >= (1LL << 31)) return TPX_EINVAL;
+    int64_t grid = (int64_t)c->num_sms * tpxk::fused_ctas_per_sm(geo);
+    if (grid > c->stage_records / C) grid = c->stage_records / C;
+    if (grid > n_tiles) grid = n_tiles;
+    if (grid < 1) return TPX_EINVAL;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    // device scratch of the batch
+    auto &B = c->batch;
+    const size_t need_dev = al(4 * (size_t)n_tiles) + al(8 * (size_t)n_runs) + al(8 * (size_t)(n_runs + 1)) +
+                            al(4 * (size_t)n_runs) + 4 * al(8 * (size_t)n_tiles) + al(8 * (size_t)(grid * T)) +
+                            2 * al(4 * (size_t)n_tiles) + 2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles);
+    if (need_dev > B.dev_bytes) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        if (B.dev) cudaFree(B.dev);
+        B.dev = nullptr;
+        B.dev_bytes = 0;
+        if (cudaMalloc(&B.dev, need_dev) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
+        if (cudaMemset(B.dev, 0, need_dev) != cudaSuccess) return TPX_ECUDA;   // fresh flags
+        B.dev_bytes = need_dev;
+    }
+    const size_t need_host = 8 * (size_t)(n_runs + 1) + 8 * (size_t)n_runs + 4 * (size_t)n_tiles + 64;
+    if (B.h_tab) {   // the previous batch's tables may still be uploading
+        if (cudaEventSynchronize(B.tab_copied) != cudaSuccess) return TPX_ECUDA;
+    }
+    if (need_host > B.h_bytes) {
+        if (B.h_tab) cudaFreeHost(B.h_tab);
+        B.h_tab = nullptr;
+        B.h_bytes = 0;
+        if (cudaMallocHost(&B.h_tab, need_host) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
+        B.h_bytes = need_host;
+    }
+    char *m = static_cast<char *>(B.dev);
+    auto take = [&](size_t bytes) { char *r = m; m += al(bytes); return r; };
+    tpxk::BatchTable &bt = B.bt;
+    bt.tile_run = reinterpret_cast<int *>(take(4 * (size_t)n_tiles));
+    bt.run_tile0 = reinterpret_cast<long long *>(take(8 * (size_t)n_runs));
+    bt.run_off = reinterpret_cast<long long *>(take(8 * (size_t)(n_runs + 1)));
+    bt.run_failed = reinterpret_cast<unsigned *>(take(4 * (size_t)n_runs));
+    bt.tcagg = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
+    bt.tcpre = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
+    B.ts.cagg = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
+    B.ts.cpre = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
+    bt.tstage = reinterpret_cast<long long *>(take(8 * (size_t)(grid * T)));
+    B.ts.flags = reinterpret_cast<unsigned *>(take(4 * (size_t)n_tiles));
+    B.ts.cflags = reinterpret_cast<unsigned *>(take(4 * (size_t)n_tiles));
+    B.ts.agg = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg) * (size_t)n_tiles));
+    B.ts.pre = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg) * (size_t)n_tiles));
+    bt.run_rec_off = reinterpret_cast<long long *>(d_run_clusters);
+    bt.run_trig_off = reinterpret_cast<long long *>(d_run_trig);
+    bt.n_runs = n_runs;
+    // the tables, built on the host and uploaded from pinned memory
+    int64_t *h_off = B.h_tab, *h_t0 = B.h_tab + (n_runs + 1);
+    int *h_tr = reinterpret_cast<int *>(B.h_tab + (n_runs + 1) + n_runs);
+    std::memcpy(h_off, h_run_offsets, 8 * (size_t)(n_runs + 1));
+    int64_t g = 0;
+    for (int64_t r = 0; r < n_runs; ++r) {
+        const int64_t len = h_off[r + 1] - h_off[r];
+        const int64_t k = len > 0 ? (len + T - 1) / T : 1;
+        h_t0[r] = g;
+        for (int64_t i = 0; i < k; ++i) h_tr[g + i] = (int)r;
+        g += k;
+    }
+    if (cudaMemcpyAsync(const_cast<long long *>(bt.run_off), h_off, 8 * (size_t)(n_runs + 1), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(const_cast<long long *>(bt.run_tile0), h_t0, 8 * (size_t)n_runs, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(const_cast<int *>(bt.tile_run), h_tr, 4 * (size_t)n_tiles, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return TPX_ECUDA;
+    if (cudaEventRecord(B.tab_copied, s) != cudaSuccess) return TPX_ECUDA;
+    if (cudaMemsetAsync(bt.run_failed, 0, 4 * (size_t)n_runs, s) != cudaSuccess) return TPX_ECUDA;
+    if (cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), s) != cudaSuccess) return TPX_ECUDA;
+    if (cudaMemsetAsync(d_n_clusters, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_n_trig, 0, 8, s) != cudaSuccess)
+        return TPX_ECUDA;
+    c->seq = (c->seq + 1) & 0x3FFFFFFFu;
+    if (c->seq == 0) {   // sequence numbers wrapped: clear every flag once
+        c->seq = 1;
+        cudaMemsetAsync(c->ts.flags, 0, sizeof(unsigned) * c->max_tiles, s);
+        cudaMemsetAsync(c->ts.cflags, 0, sizeof(unsigned) * c->max_tiles, s);
+        cudaMemsetAsync(B.ts.flags, 0, 4 * (size_t)n_tiles, s);
+        cudaMemsetAsync(B.ts.cflags, 0, 4 * (size_t)n_tiles, s);
+    }
+    tpxk::Params p;
+    std::memset(&p, 0, sizeof p);
+    p.pk = d_packets;
+    p.n = n;
+    p.idx_base = 0;
+    p.labels = reinterpret_cast<long long *>(d_labels);
+    p.is_peak = d_is_peak;
+    p.clusters = d_clusters;
+    p.cl_cap = cl_cap;
+    p.n_clusters = reinterpret_cast<long long *>(d_n_clusters);
+    p.trig = reinterpret_cast<long long *>(d_trig);
+    p.trig_cap = trig_cap;
+    p.n_trig = reinterpret_cast<long long *>(d_n_trig);
+    p.lut = c->cfg.d_timewalk_lut;
+    p.rx = c->cfg.rx;
+    p.ry = c->cfg.ry;
+    p.dt = c->cfg.dt_ticks;
+    p.strict = c->cfg.strict;
+    p.tof_max = c->cfg.tof_max_ticks;
+    p.thr_pix = c->cfg.wrap_thr_pix_ticks;
+    p.thr_tdc = c->cfg.wrap_thr_tdc_ticks;
+    p.n_tiles = n_tiles;
+    p.seq = c->seq;
+    p.ts = B.ts;
+    p.ctl = c->ctl;
+    p.stage = c->stage;
+    p.bt = bt;
+    auto &t = c->tune;
+    const bool timed = c->cfg.tile_geometry == TPX_TILE_DEFAULT && !t.fixed && n >= kTuneMinPackets &&
+                       (t.tail + 1) % 8 != t.head;
+    if (timed && cudaEventRecord(t.ring[t.tail].a, s) != cudaSuccess) return TPX_ECUDA;
+    if (tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s) != cudaSuccess) return TPX_ECUDA;
+    if (timed) {
+        if (cudaEventRecord(t.ring[t.tail].b, s) != cudaSuccess) return TPX_ECUDA;
+        t.ring[t.tail].geo = geo;
+        t.ring[t.tail].n = n;
+        t.tail = (t.tail + 1) % 8;
+        t.issued[geo - 1] += 1;
+    }
+    // what a redo of failed runs needs
+    c->last.valid = false;
+    B.last = true;
+    B.pk = d_packets;
+    B.n_runs = n_runs;
+    B.labels = d_labels;
+    B.is_peak = d_is_peak;
+    B.cl = d_clusters;
+    B.cl_cap = cl_cap;
+    B.n_cl = d_n_clusters;
+    B.trig = d_trig;
+    B.trig_cap = trig_cap;
+    B.n_trig = d_n_trig;
+    return TPX_OK;
+}
+
 int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     if (!c) return TPX_EINVAL;
     int64_t redone = 0;
@@ -328,6 +500,16 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
         const int rc = tpxg::redo_last(c);
         c->last.valid = false;
         redone = 1;
+        if (rc) return rc;
+        if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return TPX_ECUDA;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    }
+    if ((c->h_ctl->status & tpxk::ST_RUN_REDO) && !(c->h_ctl->status & tpxk::ST_DEVTIMEOUT) && c->batch.last) {
+        // runs of the last batch that the tiles could not hold: redo them
+        // exactly with the general path and splice their outputs in
+        const int rc = tpxg::redo_batch(c, &redone);
+        c->batch.last = false;
         if (rc) return rc;
         if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             return TPX_ECUDA;

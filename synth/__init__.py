@@ -106,6 +106,29 @@ def streaming(rate_hits_per_s: float, n_shots: int, **kw) -> Params:
 STREAM_TOF_MAX_TICKS = 639_999      # the ToF cut of the streaming workload: the whole period
 
 
+ELECTRON = dict(sigma_px=0.6, tof_lo_ns=0.0, tof_hi_ns=50.0)
+ION = dict(sigma_px=1.2, tof_lo_ns=1000.0, tof_hi_ns=20000.0)
+
+
+def batched(n_runs: int = 4096, seed: int = 2, shots_lo: int = 10, shots_hi: int = 10_000,
+            particles_lo: float = 1.0, particles_hi: float = 500.0) -> list[Params]:
+    """Uneven batch of independent runs: per run, shots log-uniform in
+    [shots_lo, shots_hi], Poisson particles per shot with a mean log-uniform
+    in [particles_lo, particles_hi], electron-like (sigma 0.6 px, ToF 0-50 ns)
+    or ion-like (sigma 1.2 px, ToF 1-20 us) with equal odds, its own seed and
+    start time anywhere in the pixel time range (seed 2 for the batch)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for r in range(n_runs):
+        shots = int(round(np.exp(rng.uniform(np.log(shots_lo), np.log(shots_hi)))))
+        mean = float(np.exp(rng.uniform(np.log(particles_lo), np.log(particles_hi))))
+        kind = ELECTRON if rng.random() < 0.5 else ION
+        t0 = int(rng.integers(0, PIX_PERIOD_TICKS))
+        runs.append(Params(n_shots=shots, seed=seed * 1_000_003 + r, poisson=True, particles_per_shot=mean,
+                           t_start_ticks=t0, **kind))
+    return runs
+
+
 def stated_size(p: Params) -> Params:
     """Variant whose truncation (ToT >= 90) gives the 5-15 px per particle
     that the workload description quotes; the literal parameters give ~25."""

@@ -1,0 +1,120 @@
+"""Batched runs in one launch (tpx_process_batch) against the oracle run on
+each run alone: every run is a stream of its own; records and triggers come
+run after run with per-run offsets; runs the tiles cannot hold (one shot
+longer than a range) are redone exactly; empty runs, one-packet runs, runs
+starting at odd packets and runs crossing the pixel wrap are covered."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2603_04942_gb300 as tpx
+import synth
+from gpu_common import assert_clusters_equal, oracle_run, to_device
+from streams import StreamBuilder
+
+pytestmark = pytest.mark.gpu
+
+
+def _long_shot_run(rng, pixels=9000):
+    b = StreamBuilder()
+    t = 50_000_000
+    for s in range(3):
+        b.tdc(t + s * 640_000)
+        for _ in range(pixels if s == 1 else 300):
+            b.pix(rng.integers(0, 256), rng.integers(0, 256), rng.integers(1, 400),
+                  t + s * 640_000 + 800 + rng.integers(0, 50_000))
+    return b.packets()
+
+
+def make_batch(n_runs=20, seed=5, long_shot=True):
+    runs = [synth.generate(p)[0] for p in synth.batched(n_runs=n_runs, seed=seed, shots_hi=150, particles_hi=40)]
+    rng = np.random.default_rng(seed)
+    runs.insert(3, np.zeros(0, np.uint64))                 # an empty run
+    runs.insert(5, runs[4][:1].copy())                     # a one-packet run (odd offsets after it)
+    runs.insert(8, runs[7][: 2 * 4096 + 3].copy())         # a run cut mid-shot
+    if long_shot:
+        runs.insert(11, _long_shot_run(rng))               # needs the general path
+    offs = np.zeros(len(runs) + 1, np.int64)
+    offs[1:] = np.cumsum([r.size for r in runs])
+    pk = np.concatenate(runs) if offs[-1] else np.zeros(0, np.uint64)
+    return pk, offs
+
+
+def run_batch(pk, offs, mode=0, tile=0, labels=True):
+    ctx = tpx.Context(tpx.Config(mode=mode, tile_geometry=tile), max_packets=max(1, pk.size))
+    try:
+        out = ctx.alloc_batch_outputs(pk.size, offs.size - 1, labels=labels, is_peak=labels,
+                                      cluster_capacity=max(16, pk.size), trig_capacity=max(16, pk.size))
+        ctx.tpx_process_batch(to_device(pk), offs, out)
+        rc, cnt = ctx.tpx_sync(check=False)
+        return ctx.collect_batch(out, rc, cnt)
+    finally:
+        ctx.close()
+
+
+def check_against_oracle(g, pk, offs, mode=0):
+    assert g["status"] == 0
+    assert g["run_clusters"][-1] == g["n_clusters"] and g["run_trig"][-1] == g["n_trig"]
+    labels = []
+    for r in range(offs.size - 1):
+        a, b = int(offs[r]), int(offs[r + 1])
+        o = oracle_run(pk[a:b], mode=mode, index_base=a)
+        gc = g["clusters"][g["run_clusters"][r]: g["run_clusters"][r + 1]]
+        assert_clusters_equal(gc, o["clusters"])
+        assert np.array_equal(g["triggers"][g["run_trig"][r]: g["run_trig"][r + 1]], o["triggers"]), r
+        labels.append(o["labels"])
+        if g["is_peak"] is not None:
+            assert np.array_equal(g["is_peak"][a:b], o["is_peak"]), r
+    if g["labels"] is not None:
+        assert np.array_equal(g["labels"], np.concatenate(labels))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_matches_each_run_alone(mode):
+    pk, offs = make_batch()
+    g = run_batch(pk, offs, mode=mode)
+    assert g["counters"]["redone"] == 1          # the long-shot run
+    check_against_oracle(g, pk, offs, mode)
+
+
+def test_batch_on_the_smaller_tiles():
+    pk, offs = make_batch(seed=6)
+    g = run_batch(pk, offs, tile=tpx.TILE_2048)
+    check_against_oracle(g, pk, offs)
+
+
+def test_batch_without_redo_and_without_labels():
+    pk, offs = make_batch(seed=7, long_shot=False)
+    g = run_batch(pk, offs, labels=False)
+    assert g["counters"]["redone"] == 0
+    check_against_oracle(g, pk, offs)
+
+
+def test_single_run_batch_equals_tpx_process():
+    pk = synth.generate(synth.small(n_shots=300))[0]
+    offs = np.array([0, pk.size], np.int64)
+    g = run_batch(pk, offs)
+    o = oracle.run(pk)
+    assert_clusters_equal(g["clusters"], o["clusters"])
+    assert np.array_equal(g["labels"], o["labels"])
+
+
+def test_all_runs_empty():
+    pk = np.zeros(0, np.uint64)
+    offs = np.zeros(4, np.int64)
+    g = run_batch(pk, offs)
+    assert g["status"] == 0 and g["n_clusters"] == 0 and g["n_trig"] == 0
+    assert np.array_equal(g["run_clusters"], np.zeros(4)) and np.array_equal(g["run_trig"], np.zeros(4))
+
+
+def test_bad_offsets_rejected():
+    import torch
+    ctx = tpx.Context(tpx.Config(), max_packets=16)
+    try:
+        out = ctx.alloc_batch_outputs(16, 2)
+        d = torch.zeros(16, dtype=torch.int64, device="cuda")
+        for offs in (np.array([1, 5, 16]), np.array([0, 9, 5])):
+            with pytest.raises(tpx.TpxError):
+                ctx.tpx_process_batch(d, offs, out)
+    finally:
+        ctx.close()
