@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--tile", choices=["default", "4096", "2048"], default="default",
                     help="fused-kernel tile geometry (speed only; results are identical)")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=4096)
+    ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--stream-only", action="store_true")
     ap.add_argument("--stream-chunks", type=int, default=150)
     ap.add_argument("--stream-rates", type=str, default="10,40,80")
@@ -236,6 +239,86 @@ def stream_bench(args) -> dict:
     return out
 
 
+def batch_bench(args) -> dict:
+    """Uneven batch: independent runs (log-uniform shots and particles per
+    shot, electron- or ion-like) concatenated on the device and processed by
+    one tpx_process_batch launch per step; device-resident, CUDA events."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    runs = synth.batched(n_runs=args.batch_runs)
+    t0 = time.perf_counter()
+    parts, sizes, staging = [], [], None
+    for p in runs:
+        st = synth.Stream(p)
+        n = st.n_packets
+        if staging is None or staging.numel() < n:
+            staging = torch.empty(max(n, 1 << 24), dtype=torch.int64, pin_memory=True)
+        st.packets_into(staging.numpy().view(np.uint64))
+        st.close()
+        parts.append(staging[:n].to("cuda", non_blocking=False))
+        sizes.append(n)
+    del staging
+    d_pk = torch.cat(parts) if parts else torch.zeros(2, dtype=torch.int64, device="cuda")
+    del parts
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    offs = np.zeros(len(runs) + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    n = int(offs[-1])
+    shots = sum(p.n_shots for p in runs)
+    expect = sum(p.n_shots * p.particles_per_shot for p in runs)
+    ctx = tpx.Context(tpx.Config(), max_packets=max(1, n))
+    out = ctx.alloc_batch_outputs(n, len(runs), labels=False, is_peak=False,
+                                  cluster_capacity=int(1.3 * expect) + (1 << 20), trig_capacity=shots + 16)
+    s = ctx.stream
+    for _ in range(args.warmup):
+        ctx.tpx_process_batch(d_pk, offs, out)
+    rc, counters = ctx.tpx_sync(check=False)
+    if rc != 0:
+        raise SystemExit(f"tpx_process_batch failed in warm-up: {rc} {counters}")
+    # a step is the whole call: the launch and the tpx_sync that redoes the
+    # runs the tiles could not hold (host wall clock, device synchronised)
+    steps = args.steps
+    step_ms = []
+    torch.cuda.synchronize()
+    for k in range(steps):
+        t0 = time.perf_counter()
+        ctx.tpx_process_batch(d_pk, offs, out)
+        rc, counters = ctx.tpx_sync(check=False)
+        torch.cuda.synchronize()
+        step_ms.append(1e3 * (time.perf_counter() - t0))
+        assert rc == 0, rc
+    total_ms = sum(step_ms)
+    # the tiles' pass alone (one launch, CUDA events), for the split
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(s)
+    ctx.tpx_process_batch(d_pk, offs, out)
+    ev1.record(s)
+    torch.cuda.synchronize()
+    tiles_ms = ev0.elapsed_time(ev1)
+    rc2, _ = ctx.tpx_sync(check=False)
+    assert rc2 == 0, rc2
+    tune = ctx.tpx_tuning()
+    n_cl = int(out["n_clusters"].item())
+    res = {"workload": f"{len(runs)} independent runs, one launch per step: shots log-uniform 10-10^4, Poisson "
+                       "particles per shot with a mean log-uniform 1-500, electron-like (sigma 0.6 px, ToF 0-50 ns) "
+                       "or ion-like (sigma 1.2 px, ToF 1-20 us), seed 2",
+           "metric": "pixel hits/s clustered+centroided", "unit": "hits/s",
+           "value": counters["pixels"] * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+           "timing": "wall clock per whole call (launch + tpx_sync, redone runs included), device synchronised",
+           "tiles_pass_ms": tiles_ms,
+           "runs": len(runs), "shots": shots, "packets": n, "pixel_hits": counters["pixels"], "clusters": n_cl,
+           "redone_runs": counters["redone"], "steps": steps, "warmup": args.warmup,
+           "tile_geometry": {1: "4096-packet tiles", 2: "2048-packet tiles"}.get(tune["tile_geometry"], "sampling"),
+           "generation_s": round(gen_s, 1)}
+    ctx.close()
+    del d_pk, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, one bounded sample of
     the workload per step (a different shot range each step)."""
@@ -268,12 +351,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.stream_only:
+    if args.stream_only or args.batch_only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2603_04942_gb300 import build as tbuild
         tbuild.build()
-        print(json.dumps(stream_bench(args)), flush=True)
+        print(json.dumps(stream_bench(args) if args.stream_only else batch_bench(args)), flush=True)
         return 0
     import torch
     import torch.distributed as dist
@@ -385,11 +468,15 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args, args.cpu_shots)
+    del d_pk
+    ctx.close()
+    torch.cuda.empty_cache()
     stream = None
     if rank == 0 and not args.no_stream:
-        del d_pk
-        torch.cuda.empty_cache()
         stream = stream_bench(args)
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_bench(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -405,12 +492,11 @@ def main():
                                tuning["tile_geometry"], "sampling"),
                            "tile_choice": "autotuned in warm-up" if args.tile == "default" else "fixed by --tile",
                            "generation_s": round(t_gen, 1)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "clocks": clk,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "batch": batch, "clocks": clk,
                 "gpu_launches": args.steps,
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "counters": counters}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

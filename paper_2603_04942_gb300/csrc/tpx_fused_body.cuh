@@ -647,13 +647,16 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         __syncthreads();   // records written per contiguous chunk are read strided below
 
+        // a batch tile whose range the tiles cannot hold: its run is redone by
+        // the general path, so it clusters nothing (its counts still flow)
+        const bool skip = BATCH && (S.status & (ST_CAPACITY | ST_EXCEPTION)) != 0;
         // the range this CTA owns: [R0, R1)
-        const int R0 = (f == INT_MAX) ? 0 : f;
-        const int R1 = (f == INT_MAX) ? 0 : (term ? L - 1 : L);
+        const int R0 = (f == INT_MAX || skip) ? 0 : f;
+        const int R1 = (f == INT_MAX || skip) ? 0 : (term ? L - 1 : L);
         // label writes cover [W0, W1): the range, plus the packets before the
         // tile's first trigger when no trigger precedes them anywhere
         const int W0 = prev_global ? R0 : 0;
-        const int W1 = (f == INT_MAX) ? (prev_global ? 0 : cnt) : R1;
+        const int W1 = skip ? 0 : ((f == INT_MAX) ? (prev_global ? 0 : cnt) : R1);
 
         // ---- hash insert ----
         for (int q = R0 + tid; q < R1; q += NT) {

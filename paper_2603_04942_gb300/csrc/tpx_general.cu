@@ -10,13 +10,14 @@
 // cluster : stable LSD radix sort of the hits on (shot, corrected ToF) --
 //           ties keep stream order. In that order a gap larger than dt ends
 //           every cluster, so the sorted hits split into independent
-//           segments; one warp clusters a segment in shared memory: each hit
-//           scans forward within dt, adjacent pairs (Sec. V.A box rule) set
-//           the local-maximum flags (Sec. V.B) and are joined by a lock-free
-//           union-find whose root is the smallest position, i.e. the
-//           earliest hit; the root's int64 moments are summed on the spot.
-//           Segments longer than a warp's buffer take the same steps in
-//           global memory.
+//           segments. One warp clusters a segment of up to 64 hits in
+//           registers: ballots give each hit's adjacency row (Sec. V.A box
+//           rule) and local-maximum flag (Sec. V.B); components are closures
+//           over the rows seeded at the earliest hit; the root's int64
+//           moments are warp sums. Longer segments (shots whose particles
+//           arrive within dt of each other) find their pairs through a hash
+//           of (shot, x, y) cells and join them in a global lock-free
+//           union-find whose root is the smallest position.
 // centroid: cluster ids in ascending label order (a scan over root flags in
 //           stream order), f64 final division (Sec. V.C); PAPER mode sums the
 //           box neighbourhood of each local maximum.
@@ -25,6 +26,8 @@
 
 #include <climits>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <vector>
@@ -549,17 +552,22 @@ __global__ void k_seg_starts(const unsigned *f, const unsigned *off, long long n
 // per-root moments, indexed by the hit position of the root
 struct AccH { long long s_tot, s_x, s_y, s_t; unsigned n, npk; };
 
-constexpr int WCAP = 256;           // hits of a segment held by one warp
+constexpr int WREG = 64;            // hits of a segment held in registers (two per lane)
+constexpr int WCAP = 256;           // hits of a segment held by one warp in shared memory
 constexpr int ECAP = 1024;          // adjacent pairs of a segment kept for the hooking rounds
+constexpr int HBW = 512;            // cell-hash buckets of a warp's segment
 constexpr int SEGW = 4;             // warps per block
 struct SegSm {
     int tofb[WCAP];
     int parent[WCAP];
     unsigned edge[ECAP];            // (k << 16) | j, k < j
+    unsigned hhead[HBW];            // cell hash: first position, 0xFFFF = none
     unsigned ecnt;
+    unsigned short hnext[WCAP];
     unsigned short tot[WCAP];
     unsigned char x[WCAP], y[WCAP], np[WCAP];
 };
+__device__ __forceinline__ unsigned wcell(int x, int y) { return (unsigned)(x * 67 + y * 131) & (HBW - 1); }
 
 __device__ __forceinline__ int s_find(volatile int *par, int x) {
     for (;;) {
@@ -707,11 +715,14 @@ __device__ void seg_small(const Sorted &s, long long s0, int L, int rx, int ry, 
     }
 }
 
-// One warp per segment of at most WCAP hits, in shared memory: every hit
-// scans forward within dt (each adjacent pair met once, from its earlier
-// end), sets the local-maximum flags and joins the pair; then labels, peaks,
-// root flags (emitted shots only) and the root's int64 moments. Longer
-// segments are marked for the global-memory kernels below.
+// One warp per segment. Up to 64 hits: in registers (seg_small). Up to
+// WCAP: in shared memory, where a cell hash of the segment gives every hit
+// the candidates of the forward half of its box (same cell: later positions
+// only), so that each adjacent pair is met once even when the whole segment
+// lies within dt; pairs set the local-maximum flags and are joined by
+// hooking rounds; then labels, peaks, root flags (emitted shots only) and
+// the root's int64 moments. Longer segments are marked for the cell-hash
+// kernels in global memory below.
 __global__ void __launch_bounds__(SEGW * 32) k_segments(Sorted s, const long long *seg_start, const long long *nseg_p,
                                                         int rx, int ry, int dt, int cc, long long shot_limit,
                                                         long long *labels, unsigned char *is_peak, unsigned *rflag,
@@ -729,7 +740,7 @@ __global__ void __launch_bounds__(SEGW * 32) k_segments(Sorted s, const long lon
         const int L = (int)len;
         const bool emit = s.shot[s0] < shot_limit;
         const bool sums = cc && acc && emit;
-        if (L > 1 && L <= 64) {
+        if (L > 1 && L <= WREG) {
             seg_small(s, s0, L, rx, ry, dt, cc, emit, labels, is_peak, rflag, sums ? acc : nullptr, lane);
             continue;
         }
@@ -756,23 +767,37 @@ __global__ void __launch_bounds__(SEGW * 32) k_segments(Sorted s, const long lon
             W.parent[k] = k;
             W.np[k] = 0;
         }
+        for (int b = lane; b < HBW; b += 32) W.hhead[b] = 0xFFFFu;
         if (lane == 0) W.ecnt = 0;
+        __syncwarp();
+        for (int k = lane; k < L; k += 32) W.hnext[k] = (unsigned short)atomicExch(&W.hhead[wcell(W.x[k], W.y[k])], (unsigned)k);
         __syncwarp();
         for (int k = lane; k < L; k += 32) {
             const int tb = W.tofb[k], xk = W.x[k], yk = W.y[k], tk = W.tot[k];
-            for (int j = k + 1; j < L; ++j) {
-                if (W.tofb[j] - tb > dt) break;
-                const int dx = (int)W.x[j] - xk, dy = (int)W.y[j] - yk;
-                if (dx < -rx || dx > rx || dy < -ry || dy > ry) continue;
-                if (j_brighter(W.tot[j], tk, s.index, s0 + j, s0 + k)) W.np[k] = 1; else W.np[j] = 1;
-                if (cc) {   // record the pair (warp-aggregated slot); beyond the buffer, join it now
-                    const unsigned am = __activemask();
-                    const int leader = __ffs(am) - 1;
-                    unsigned slot = 0;
-                    if (lane == leader) slot = atomicAdd(&W.ecnt, (unsigned)__popc(am));
-                    slot = __shfl_sync(am, slot, leader) + __popc(am & ((1u << lane) - 1u));
-                    if (slot < (unsigned)ECAP) W.edge[slot] = ((unsigned)k << 16) | (unsigned)j;
-                    else s_unite(W.parent, k, j);
+            for (int dx = 0; dx <= rx; ++dx) {
+                const int cx = xk + dx;
+                if (cx > 255) break;
+                for (int dy = (dx == 0 ? 0 : -ry); dy <= ry; ++dy) {
+                    const int cy = yk + dy;
+                    if (cy < 0 || cy > 255) continue;
+                    for (unsigned j = W.hhead[wcell(cx, cy)]; j != 0xFFFFu; j = W.hnext[j]) {
+                        if (dx == 0 && dy == 0 && (int)j <= k) continue;
+                        if (W.x[j] != cx || W.y[j] != cy) continue;
+                        const int d = W.tofb[j] - tb;
+                        if (d < -dt || d > dt) continue;
+                        // the pair (lo, hi) in position order
+                        const int lo = min(k, (int)j), hi = max(k, (int)j);
+                        if (j_brighter(W.tot[j], tk, s.index, s0 + j, s0 + k)) W.np[k] = 1; else W.np[j] = 1;
+                        if (cc) {   // record the pair (warp-aggregated slot); beyond the buffer, join it now
+                            const unsigned am = __activemask();
+                            const int leader = __ffs(am) - 1;
+                            unsigned slot = 0;
+                            if (lane == leader) slot = atomicAdd(&W.ecnt, (unsigned)__popc(am));
+                            slot = __shfl_sync(am, slot, leader) + __popc(am & ((1u << lane) - 1u));
+                            if (slot < (unsigned)ECAP) W.edge[slot] = ((unsigned)lo << 16) | (unsigned)hi;
+                            else s_unite(W.parent, lo, hi);
+                        }
+                    }
                 }
             }
         }
@@ -900,18 +925,44 @@ __global__ void k_long_init(Sorted s, long long n, const unsigned char *mark, in
         }
     }
 }
-__global__ void k_long_window(Sorted s, long long n, const unsigned char *mark, int rx, int ry, int dt, int cc,
-                              int *parent, unsigned char *notpeak) {
+// Long segments can hold thousands of hits within dt of each other (a shot
+// of many particles arriving together), so their pairs come from a hash of
+// (shot, x, y) cells: every hit looks up the cells of the forward half of its
+// box (same cell: later positions only), which meets each adjacent pair once.
+__device__ __forceinline__ unsigned long long cell_hash(long long shot, int x, int y, unsigned long long mask) {
+    unsigned long long k = ((unsigned long long)shot << 16) ^ ((unsigned long long)x << 8) ^ (unsigned long long)y;
+    k *= 0x9E3779B97F4A7C15ull;   // Fibonacci hashing
+    return (k >> 20) & mask;
+}
+__global__ void k_long_insert(Sorted s, long long n, const unsigned char *mark, unsigned *head, unsigned *next,
+                              unsigned long long mask) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!mark[i]) continue;
+        next[i] = atomicExch(&head[cell_hash(s.shot[i], s.x[i], s.y[i], mask)], (unsigned)i);
+    }
+}
+__global__ void k_long_pairs(Sorted s, long long n, const unsigned char *mark, const unsigned *head,
+                             const unsigned *next, unsigned long long mask, int rx, int ry, int dt, int cc,
+                             int *parent, unsigned char *notpeak) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         if (!mark[i]) continue;
         const long long sh = s.shot[i];
         const int tb = s.tofb[i], xi = s.x[i], yi = s.y[i], ti = s.tot[i];
-        for (long long j = i + 1; j < n; ++j) {       // stops at the segment's end
-            if (s.shot[j] != sh || s.tofb[j] - tb > dt) break;
-            const int dx = (int)s.x[j] - xi, dy = (int)s.y[j] - yi;
-            if (dx < -rx || dx > rx || dy < -ry || dy > ry) continue;
-            if (j_brighter(s.tot[j], ti, s.index, j, i)) notpeak[i] = 1; else notpeak[j] = 1;
-            if (cc) g_unite(parent, (int)i, (int)j);
+        for (int dx = 0; dx <= rx; ++dx) {
+            const int cx = xi + dx;
+            if (cx > 255) break;
+            for (int dy = (dx == 0 ? 0 : -ry); dy <= ry; ++dy) {
+                const int cy = yi + dy;
+                if (cy < 0 || cy > 255) continue;
+                for (unsigned j = head[cell_hash(sh, cx, cy, mask)]; j != 0xFFFFFFFFu; j = next[j]) {
+                    if (dx == 0 && dy == 0 && (long long)j <= i) continue;
+                    if (s.x[j] != cx || s.y[j] != cy || s.shot[j] != sh) continue;
+                    const int d = s.tofb[j] - tb;
+                    if (d < -dt || d > dt) continue;
+                    if (j_brighter(s.tot[j], ti, s.index, j, i)) notpeak[i] = 1; else notpeak[j] = 1;
+                    if (cc) g_unite(parent, (int)i, (int)j);
+                }
+            }
         }
     }
 }
@@ -1060,7 +1111,13 @@ __global__ void k_records(tpx_hits h, const long long *n_rec, long long cap, con
 }
 
 // ------------------------------------------------------------ host helpers
-inline int ck(cudaError_t e) { return e == cudaSuccess ? TPX_OK : TPX_ECUDA; }
+// a failed CUDA call becomes TPX_ECUDA; with TPX_DEBUG set in the
+// environment its error is also printed to stderr
+inline int ck(cudaError_t e, int line = __builtin_LINE()) {
+    if (e == cudaSuccess) return TPX_OK;
+    if (std::getenv("TPX_DEBUG")) std::fprintf(stderr, "tpx_general.cu:%d: %s\n", line, cudaGetErrorString(e));
+    return TPX_ECUDA;
+}
 inline unsigned grid_for(long long n) {
     long long g = (n + GT - 1) / GT;
     if (g < 1) g = 1;
@@ -1083,7 +1140,7 @@ inline size_t sz(long long count, size_t elem) { return ((size_t)(count > 0 ? co
 
 int reserve(tpx_ctx *c, size_t bytes) {
     if (c->g_mem && c->g_bytes >= bytes) return TPX_OK;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (ck(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     if (c->g_mem) cudaFree(c->g_mem);
     c->g_mem = nullptr;
     c->g_bytes = 0;
@@ -1118,14 +1175,14 @@ int sort_hits(tpx_ctx *c, Arena &a, const tpx_hits &h, long long n, long long sh
     unsigned *hist = a.take<unsigned>(256 * tiles), *offs = a.take<unsigned>(256 * tiles);
     unsigned long long *mm = a.take<unsigned long long>(2);   // min, max shot
     const unsigned long long init[2] = {~0ull, 0ull};
-    if (cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, s) != cudaSuccess) return TPX_ECUDA;
+    if (ck(cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, s))) return TPX_ECUDA;
     k_shot_range<<<grid_for(n), GT, 0, s>>>(h, n, mm, mm + 1);
     k_make_keys<<<grid_for(n), GT, 0, s>>>(h, n, mm, k0, v0);
     unsigned long long span = (unsigned long long)shot_span;
     if (shot_span < 0) {
         unsigned long long hm[2] = {0, 0};
-        if (cudaMemcpyAsync(hm, mm, sizeof hm, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        if (ck(cudaMemcpyAsync(hm, mm, sizeof hm, cudaMemcpyDeviceToHost, s))) return TPX_ECUDA;
+        if (ck(cudaStreamSynchronize(s))) return TPX_ECUDA;
         span = hm[1] - hm[0];
     }
     int bits = 24;
@@ -1194,6 +1251,7 @@ size_t cluster_bytes(long long n) {
            + 2 * sz(n, 4) + sz(n + 1, 8) + sz(1, 8)                                     // segments
            + 2 * sz(n, 1) + sz(n, 4)                                                    // long segments
            + 2 * sz(n, 4) + sz(n, sizeof(AccH)) + sz((n + GTILE - 1) / GTILE + 1, 4)    // records
+           + sz(4 * n + 2, 4) + sz(n, 4)                                               // long-segment hash
            + 8192;
 }
 
@@ -1224,6 +1282,9 @@ int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8
     int *parent = a.take<int>(n);
     unsigned *rflag = a.take<unsigned>(n), *cid = a.take<unsigned>(n);
     AccH *acc = a.take<AccH>(n);
+    unsigned long long lmask = 1;   // the long segments' cell hash: >= 2n buckets
+    while (lmask + 1 < 2ull * (unsigned long long)n) lmask = 2 * lmask + 1;
+    unsigned *lhead = a.take<unsigned>((long long)lmask + 1), *lnext = a.take<unsigned>(n);
     const size_t mark_used = a.used;
     unsigned *vals = nullptr;
     rc = sort_hits(c, a, h, n, shot_span, &vals);
@@ -1235,7 +1296,7 @@ int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8
     rc = scan_u32(a, segf, sego, n, s);
     if (rc) return rc;
     k_seg_starts<<<grid_for(n), GT, 0, s>>>(segf, sego, n, seg_start, nseg);
-    if (cudaMemsetAsync(mark, 0, (size_t)n, s) != cudaSuccess) return TPX_ECUDA;
+    if (ck(cudaMemsetAsync(mark, 0, (size_t)n, s))) return TPX_ECUDA;
     long long *lab = reinterpret_cast<long long *>(labels);
     unsigned *rf = out ? rflag : nullptr;
     AccH *ac = (out && cc) ? acc : nullptr;
@@ -1244,7 +1305,10 @@ int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8
     k_segments<<<seg_blocks, SEGW * 32, 0, s>>>(so, seg_start, nseg, c->cfg.rx, c->cfg.ry, dt, cc, shot_limit, lab,
                                                 is_peak, rf, ac, mark);
     k_long_init<<<grid_for(n), GT, 0, s>>>(so, n, mark, parent, notpeak, ac);
-    k_long_window<<<grid_for(n), GT, 0, s>>>(so, n, mark, c->cfg.rx, c->cfg.ry, dt, cc, parent, notpeak);
+    if (ck(cudaMemsetAsync(lhead, 0xFF, sizeof(unsigned) * (size_t)(lmask + 1), s))) return TPX_ECUDA;
+    k_long_insert<<<grid_for(n), GT, 0, s>>>(so, n, mark, lhead, lnext, lmask);
+    k_long_pairs<<<grid_for(n), GT, 0, s>>>(so, n, mark, lhead, lnext, lmask, c->cfg.rx, c->cfg.ry, dt, cc, parent,
+                                            notpeak);
     k_long_finish<<<grid_for(n), GT, 0, s>>>(so, n, mark, cc, shot_limit, parent, notpeak, lab, is_peak, rf, ac);
     if (!out) return ck(cudaGetLastError());
     rc = scan_u32(a, rflag, cid, n, s);
@@ -1268,7 +1332,7 @@ int cluster_impl(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint
 int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const uint8_t *is_peak, int64_t n,
                   tpx_record *out, int64_t cap, int64_t *d_n_clusters) {
     cudaStream_t s = c->stream;
-    if (cudaMemsetAsync(d_n_clusters, 0, 8, s) != cudaSuccess) return TPX_ECUDA;
+    if (ck(cudaMemsetAsync(d_n_clusters, 0, 8, s))) return TPX_ECUDA;
     if (n <= 0) return TPX_OK;
     const int cc = c->cfg.mode == TPX_MODE_CC;
     if (!cc && !is_peak) return TPX_EINVAL;
@@ -1286,7 +1350,7 @@ int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const ui
     k_count_from_scan<<<1, 1, 0, s>>>(flags, cid, n, reinterpret_cast<long long *>(d_n_clusters), cap,
                                       &c->ctl->status, &c->ctl->counters[C_CLUSTERS]);
     if (cc) {
-        if (cudaMemsetAsync(acc, 0, sizeof(Acc) * (size_t)n, s) != cudaSuccess) return TPX_ECUDA;
+        if (ck(cudaMemsetAsync(acc, 0, sizeof(Acc) * (size_t)n, s))) return TPX_ECUDA;
         k_accum<<<grid_for(n), GT, 0, s>>>(h, lab, is_peak, n, cid, acc);
         k_final<<<grid_for(n), GT, 0, s>>>(h, n, flags, cid, acc, out, cap);
     } else {
@@ -1379,6 +1443,69 @@ int redo_last(tpx_ctx *c) {
     return rc;
 }
 
+// ---- redo of a batch's failed runs ----
+__global__ void k_add_ll(long long *v, long long n, long long d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] += d;
+}
+// first record of each run of a group: records are in label order and the
+// runs' labels are the runs' packet ranges
+__global__ void k_rec_bounds(const tpx_record *rec, long long ncl, const long long *run_start, long long nr,
+                             long long *bound) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k <= nr; k += (long long)gridDim.x * blockDim.x) {
+        if (k == nr) { bound[k] = ncl; continue; }
+        long long lo = 0, hi = ncl;
+        while (lo < hi) {
+            const long long mid = lo + ((hi - lo) >> 1);
+            if (rec[mid].label < run_start[k]) lo = mid + 1; else hi = mid;
+        }
+        bound[k] = lo;
+    }
+}
+// records of group run k count their shots from the run's first trigger
+__global__ void k_rec_shots(tpx_record *rec, long long ncl, const long long *bound, const long long *shot_base,
+                            long long nr) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncl; i += (long long)gridDim.x * blockDim.x) {
+        long long lo = 0, hi = nr;   // the run k with bound[k] <= i < bound[k + 1]
+        while (hi - lo > 1) {
+            const long long mid = (lo + hi) >> 1;
+            if (bound[mid] <= i) lo = mid; else hi = mid;
+        }
+        rec[i].shot -= shot_base[lo];
+    }
+}
+// segmented copy of 8-byte words: segment i moves len[i] words src[i] -> dst[i]
+__global__ void k_seg_copy(const unsigned long long *const *src, unsigned long long *const *dst, const long long *len,
+                           long long nseg) {
+    for (long long i = blockIdx.x; i < nseg; i += gridDim.x) {
+        const unsigned long long *a = src[i];
+        unsigned long long *b = dst[i];
+        for (long long w = threadIdx.x; w < len[i]; w += blockDim.x) b[w] = a[w];
+    }
+}
+
+namespace {
+// a device buffer that keeps its contents when it grows
+struct Grow {
+    char *p = nullptr;
+    size_t used = 0, cap = 0;
+    int ensure(size_t want, cudaStream_t s) {
+        if (want <= cap) return TPX_OK;
+        size_t nc = cap ? cap : (size_t)1 << 24;
+        while (nc < want) nc *= 2;
+        char *q = nullptr;
+        if (cudaMalloc(&q, nc) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
+        if (used && ck(cudaMemcpyAsync(q, p, used, cudaMemcpyDeviceToDevice, s))) { cudaFree(q); return TPX_ECUDA; }
+        if (ck(cudaStreamSynchronize(s))) { cudaFree(q); return TPX_ECUDA; }
+        if (p) cudaFree(p);
+        p = q;
+        cap = nc;
+        return TPX_OK;
+    }
+    ~Grow() { if (p) cudaFree(p); }
+};
+}  // namespace
+
 int redo_batch(tpx_ctx *c, int64_t *n_redone) {
     auto &B = c->batch;
     cudaStream_t s = c->stream;
@@ -1388,105 +1515,203 @@ int redo_batch(tpx_ctx *c, int64_t *n_redone) {
     std::vector<unsigned> failed((size_t)R);
     std::vector<int64_t> roff((size_t)R + 1), toff((size_t)R + 1);
     Ctl snap;
-    if (cudaMemcpyAsync(failed.data(), B.bt.run_failed, 4 * (size_t)R, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(roff.data(), B.bt.run_rec_off, 8 * (size_t)(R + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(toff.data(), B.bt.run_trig_off, 8 * (size_t)(R + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaMemcpyAsync(&snap, c->ctl, sizeof snap, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (ck(cudaMemcpyAsync(failed.data(), B.bt.run_failed, 4 * (size_t)R, cudaMemcpyDeviceToHost, s)) ||
+        ck(cudaMemcpyAsync(roff.data(), B.bt.run_rec_off, 8 * (size_t)(R + 1), cudaMemcpyDeviceToHost, s)) ||
+        ck(cudaMemcpyAsync(toff.data(), B.bt.run_trig_off, 8 * (size_t)(R + 1), cudaMemcpyDeviceToHost, s)) ||
+        ck(cudaMemcpyAsync(&snap, c->ctl, sizeof snap, cudaMemcpyDeviceToHost, s)))
         return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
-    int64_t first = -1, max_len = 0, sum_len = 0;
+    if (ck(cudaStreamSynchronize(s))) return TPX_ECUDA;
+    // the tiles' pass wrote records and triggers only below the capacities
+    for (int64_t r = 0; r <= R; ++r) {
+        roff[(size_t)r] = std::min<int64_t>(roff[(size_t)r], B.cl_cap);
+        toff[(size_t)r] = std::min<int64_t>(toff[(size_t)r], B.trig_cap);
+    }
+    std::vector<int64_t> F;
+    int64_t max_len = 0;
     for (int64_t r = 0; r < R; ++r)
         if (failed[(size_t)r]) {
-            if (first < 0) first = r;
-            const int64_t len = off[r + 1] - off[r];
-            if (len > max_len) max_len = len;
-            sum_len += len;
-            *n_redone += 1;
+            F.push_back(r);
+            max_len = std::max<int64_t>(max_len, off[r + 1] - off[r]);
         }
-    if (first < 0) return TPX_OK;
-    if (max_len >= (1LL << 31)) return TPX_EUNSUPPORTED;
-    // per-run temporaries (hits, per-hit outputs, triggers) and the redone
-    // runs' records and triggers, back to back
-    const int64_t old_rec = roff[(size_t)R] - roff[(size_t)first], old_trig = toff[(size_t)R] - toff[(size_t)first];
-    const size_t hb = sz(max_len, 8) * 5 + sz(max_len, 4) + sz(max_len, 2) + 3 * sz(max_len, 1) + sz(4, 8) +
-                      sz(sum_len, sizeof(tpx_record)) + sz(sum_len, 8) + sz(old_rec, sizeof(tpx_record)) +
-                      sz(old_trig, 8) + 4096;
+    *n_redone = (int64_t)F.size();
+    if (F.empty()) return TPX_OK;
+    // failed runs are redone in groups of consecutive failed runs holding at
+    // most G packets (or one larger run): each run decodes on its own (a
+    // stream of its own), its shots offset to keep the group's shots apart,
+    // and one clustering pass serves the whole group
+    const int64_t G = std::max<int64_t>(max_len, 1LL << 26);
+    if (G >= (1LL << 31)) return TPX_EUNSUPPORTED;
+    const bool per_packet = B.labels || B.is_peak;
+    const size_t hb = sz(G, 8) * 3 + sz(G, 4) + sz(G, 2) + 2 * sz(G, 1) + (per_packet ? sz(G, 8) + sz(G, 1) : 0) +
+                      sz(G, 8) + sz(G, sizeof(tpx_record)) + 3 * sz((int64_t)F.size() + 1, 8) + sz(4, 8) + 4096;
     void *hm = nullptr;
     if (cudaMalloc(&hm, hb) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
     Arena a{static_cast<char *>(hm), 0, hb};
     tpx_hits h;
-    h.index = reinterpret_cast<int64_t *>(a.take<long long>(max_len));
-    h.shot = reinterpret_cast<int64_t *>(a.take<long long>(max_len));
-    h.t = reinterpret_cast<int64_t *>(a.take<long long>(max_len));
-    h.tof = a.take<int32_t>(max_len);
-    h.x = a.take<uint8_t>(max_len);
-    h.y = a.take<uint8_t>(max_len);
-    h.tot = a.take<uint16_t>(max_len);
-    long long *hl = a.take<long long>(max_len);
-    unsigned char *hp = a.take<unsigned char>(max_len);
-    long long *tr = a.take<long long>(max_len);
-    long long *cnt = a.take<long long>(4);   // n_hits, n_trig, n_clusters
-    tpx_record *acc_rec = a.take<tpx_record>(sum_len);
-    long long *acc_trig = a.take<long long>(sum_len);
-    tpx_record *old_rec_copy = a.take<tpx_record>(old_rec);
-    long long *old_trig_copy = a.take<long long>(old_trig);
+    h.index = reinterpret_cast<int64_t *>(a.take<long long>(G));
+    h.shot = reinterpret_cast<int64_t *>(a.take<long long>(G));
+    h.t = reinterpret_cast<int64_t *>(a.take<long long>(G));
+    h.tof = a.take<int32_t>(G);
+    h.tot = a.take<uint16_t>(G);
+    h.x = a.take<uint8_t>(G);
+    h.y = a.take<uint8_t>(G);
+    long long *hl = per_packet ? a.take<long long>(G) : nullptr;
+    unsigned char *hp = per_packet ? a.take<unsigned char>(G) : nullptr;
+    long long *tr = a.take<long long>(G);
+    tpx_record *grec = a.take<tpx_record>(G);
+    long long *d_start = a.take<long long>((int64_t)F.size() + 1), *d_base = a.take<long long>((int64_t)F.size() + 1);
+    long long *d_bound = a.take<long long>((int64_t)F.size() + 1);
+    long long *cnt = a.take<long long>(4);
+    Grow acc_rec, acc_trig;   // the redone runs' records and triggers, run after run
     std::vector<int64_t> nrec((size_t)R), ntrg((size_t)R), rstart((size_t)R), tstart((size_t)R);
-    int64_t rec_used = 0, trig_used = 0;
     int rc = TPX_OK;
-    for (int64_t r = first; r < R && !rc; ++r) {
-        if (!failed[(size_t)r]) continue;
-        const int64_t len = off[r + 1] - off[r];
-        rc = decode_impl(c, B.pk + off[r], len, off[r], h, len, reinterpret_cast<int64_t *>(cnt),
-                         reinterpret_cast<int64_t *>(tr), len, reinterpret_cast<int64_t *>(cnt + 1), false, nullptr,
-                         nullptr, nullptr, nullptr);
-        long long hc[3] = {0, 0, 0};
-        if (!rc) rc = ck(cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, s));
-        if (!rc) rc = ck(cudaStreamSynchronize(s));
-        if (!rc) rc = cluster_all(c, h, hc[0], reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, -1, acc_rec + rec_used,
-                                  hc[0], reinterpret_cast<int64_t *>(cnt + 2));
-        if (!rc && (B.labels || B.is_peak)) {
-            if (B.labels) k_fill_ll<<<grid_for(len), GT, 0, s>>>(reinterpret_cast<long long *>(B.labels) + off[r], len, -1);
-            if (B.is_peak && cudaMemsetAsync(B.is_peak + off[r], 0, (size_t)len, s) != cudaSuccess) rc = TPX_ECUDA;
-            if (hc[0] > 0)
-                k_packet_outputs<<<grid_for(hc[0]), GT, 0, s>>>(h, hl, hp, hc[0], 0, reinterpret_cast<long long *>(B.labels),
-                                                               B.is_peak);
+    for (size_t i = 0; i < F.size() && !rc;) {
+        size_t j = i;
+        int64_t pk_sum = 0;
+        while (j < F.size() && (j == i || pk_sum + (off[F[j] + 1] - off[F[j]]) <= G)) {
+            pk_sum += off[F[j] + 1] - off[F[j]];
+            ++j;
         }
-        if (!rc && hc[0] > 0) rc = ck(cudaMemcpyAsync(&hc[2], cnt + 2, 8, cudaMemcpyDeviceToHost, s));
-        if (!rc && hc[1] > 0)
-            rc = ck(cudaMemcpyAsync(acc_trig + trig_used, tr, 8 * (size_t)hc[1], cudaMemcpyDeviceToDevice, s));
+        const int64_t nr = (int64_t)(j - i);
+        std::vector<long long> start((size_t)nr), base((size_t)nr);
+        int64_t hoff = 0, tcount = 0;
+        for (int64_t k = 0; k < nr && !rc; ++k) {
+            const int64_t r = F[i + (size_t)k], len = off[r + 1] - off[r];
+            tpx_hits hk = h;
+            hk.index += hoff; hk.shot += hoff; hk.t += hoff; hk.tof += hoff; hk.tot += hoff; hk.x += hoff; hk.y += hoff;
+            rc = decode_impl(c, B.pk + off[r], len, off[r], hk, len, reinterpret_cast<int64_t *>(cnt),
+                             reinterpret_cast<int64_t *>(tr + tcount), len, reinterpret_cast<int64_t *>(cnt + 1), false,
+                             nullptr, nullptr, nullptr, nullptr);
+            long long hc[2] = {0, 0};
+            if (!rc) rc = ck(cudaMemcpyAsync(hc, cnt, 16, cudaMemcpyDeviceToHost, s));
+            if (!rc) rc = ck(cudaStreamSynchronize(s));
+            if (rc) break;
+            if (hc[0] > 0 && tcount > 0) k_add_ll<<<grid_for(hc[0]), GT, 0, s>>>(reinterpret_cast<long long *>(hk.shot), hc[0], tcount);
+            start[(size_t)k] = off[r];
+            base[(size_t)k] = tcount;
+            ntrg[(size_t)r] = hc[1];
+            hoff += hc[0];
+            tcount += hc[1];
+        }
+        if (rc) break;
+        // one clustering pass for the group; records in label order = run order
+        rc = cluster_all(c, h, hoff, reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, tcount, grec, hoff,
+                         reinterpret_cast<int64_t *>(cnt + 2));
+        if (!rc && per_packet && hoff > 0) {
+            for (int64_t k = 0; k < nr; ++k) {
+                const int64_t r = F[i + (size_t)k], len = off[r + 1] - off[r];
+                if (B.labels) k_fill_ll<<<grid_for(len), GT, 0, s>>>(reinterpret_cast<long long *>(B.labels) + off[r], len, -1);
+                if (B.is_peak && ck(cudaMemsetAsync(B.is_peak + off[r], 0, (size_t)len, s))) rc = TPX_ECUDA;
+            }
+            k_packet_outputs<<<grid_for(hoff), GT, 0, s>>>(h, hl, hp, hoff, 0, reinterpret_cast<long long *>(B.labels),
+                                                           B.is_peak);
+        }
+        long long ncl = 0;
+        if (!rc) rc = ck(cudaMemcpyAsync(&ncl, cnt + 2, 8, cudaMemcpyDeviceToHost, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(d_start, start.data(), 8 * (size_t)nr, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(d_base, base.data(), 8 * (size_t)nr, cudaMemcpyHostToDevice, s));
         if (!rc) rc = ck(cudaStreamSynchronize(s));
         if (rc) break;
-        if (hc[0] == 0) hc[2] = 0;
-        nrec[(size_t)r] = hc[2];
-        ntrg[(size_t)r] = hc[1];
-        rstart[(size_t)r] = rec_used;
-        tstart[(size_t)r] = trig_used;
-        rec_used += hc[2];
-        trig_used += hc[1];
+        if (hoff == 0) ncl = 0;
+        std::vector<long long> bound((size_t)nr + 1, 0);
+        if (ncl > 0) {
+            k_rec_bounds<<<grid_for(nr + 1), GT, 0, s>>>(grec, ncl, d_start, nr, d_bound);
+            k_rec_shots<<<grid_for(ncl), GT, 0, s>>>(grec, ncl, d_bound, d_base, nr);
+            rc = ck(cudaMemcpyAsync(bound.data(), d_bound, 8 * (size_t)(nr + 1), cudaMemcpyDeviceToHost, s));
+        }
+        // append the group's records and triggers
+        if (!rc) rc = acc_rec.ensure(acc_rec.used + sizeof(tpx_record) * (size_t)ncl, s);
+        if (!rc) rc = acc_trig.ensure(acc_trig.used + 8 * (size_t)tcount, s);
+        if (!rc && ncl > 0)
+            rc = ck(cudaMemcpyAsync(acc_rec.p + acc_rec.used, grec, sizeof(tpx_record) * (size_t)ncl,
+                                    cudaMemcpyDeviceToDevice, s));
+        if (!rc && tcount > 0)
+            rc = ck(cudaMemcpyAsync(acc_trig.p + acc_trig.used, tr, 8 * (size_t)tcount, cudaMemcpyDeviceToDevice, s));
+        if (!rc) rc = ck(cudaStreamSynchronize(s));
+        if (rc) break;
+        for (int64_t k = 0; k < nr; ++k) {
+            const int64_t r = F[i + (size_t)k];
+            nrec[(size_t)r] = bound[(size_t)k + 1] - bound[(size_t)k];
+            rstart[(size_t)r] = (int64_t)(acc_rec.used / sizeof(tpx_record)) + bound[(size_t)k];
+            tstart[(size_t)r] = (int64_t)(acc_trig.used / 8) + base[(size_t)k];
+        }
+        acc_rec.used += sizeof(tpx_record) * (size_t)ncl;
+        acc_trig.used += 8 * (size_t)tcount;
+        i = j;
     }
-    // the runs' final offsets, and the outputs from the first redone run on
+    // the runs' final offsets; every run from the first redone one on moves
+    // (the tiles' outputs of the others are kept aside first)
+    const int64_t first = F.front();
     std::vector<long long> NO((size_t)R + 1), NTo((size_t)R + 1);
     NO[0] = 0;
     NTo[0] = 0;
-    for (int64_t r = 0; r < R && !rc; ++r) {
-        const int64_t nr = failed[(size_t)r] ? nrec[(size_t)r] : roff[(size_t)r + 1] - roff[(size_t)r];
-        const int64_t nt = failed[(size_t)r] ? ntrg[(size_t)r] : toff[(size_t)r + 1] - toff[(size_t)r];
-        NO[(size_t)r + 1] = NO[(size_t)r] + nr;
-        NTo[(size_t)r + 1] = NTo[(size_t)r] + nt;
+    for (int64_t r = 0; r < R; ++r) {
+        NO[(size_t)r + 1] = NO[(size_t)r] + (failed[(size_t)r] ? nrec[(size_t)r] : roff[(size_t)r + 1] - roff[(size_t)r]);
+        NTo[(size_t)r + 1] = NTo[(size_t)r] + (failed[(size_t)r] ? ntrg[(size_t)r] : toff[(size_t)r + 1] - toff[(size_t)r]);
     }
+    const int64_t old_rec = roff[(size_t)R] - roff[(size_t)first], old_trig = toff[(size_t)R] - toff[(size_t)first];
+    Grow keep;
+    if (!rc) rc = keep.ensure(sizeof(tpx_record) * (size_t)old_rec + 8 * (size_t)old_trig + 512, s);
+    tpx_record *old_rec_copy = reinterpret_cast<tpx_record *>(keep.p);
+    long long *old_trig_copy = reinterpret_cast<long long *>(keep.p + ((sizeof(tpx_record) * (size_t)old_rec + 255) & ~size_t(255)));
     if (!rc && old_rec > 0)
         rc = ck(cudaMemcpyAsync(old_rec_copy, B.cl + roff[(size_t)first], sizeof(tpx_record) * (size_t)old_rec,
                                 cudaMemcpyDeviceToDevice, s));
     if (!rc && old_trig > 0)
         rc = ck(cudaMemcpyAsync(old_trig_copy, B.trig + toff[(size_t)first], 8 * (size_t)old_trig, cudaMemcpyDeviceToDevice, s));
+    // one segmented copy for all moved runs (records, then triggers)
+    std::vector<const unsigned long long *> src;
+    std::vector<unsigned long long *> dst;
+    std::vector<long long> len;
+    constexpr int WPR = (int)(sizeof(tpx_record) / 8);
     for (int64_t r = first; r < R && !rc; ++r) {
         const int64_t nr = NO[(size_t)r + 1] - NO[(size_t)r], nt = NTo[(size_t)r + 1] - NTo[(size_t)r];
         const int64_t kr = std::max<int64_t>(0, std::min<int64_t>(nr, B.cl_cap - NO[(size_t)r]));
         const int64_t kt = std::max<int64_t>(0, std::min<int64_t>(nt, B.trig_cap - NTo[(size_t)r]));
-        const tpx_record *sr = failed[(size_t)r] ? acc_rec + rstart[(size_t)r] : old_rec_copy + (roff[(size_t)r] - roff[(size_t)first]);
-        const long long *st = failed[(size_t)r] ? acc_trig + tstart[(size_t)r] : old_trig_copy + (toff[(size_t)r] - toff[(size_t)first]);
-        if (kr > 0) rc = ck(cudaMemcpyAsync(B.cl + NO[(size_t)r], sr, sizeof(tpx_record) * (size_t)kr, cudaMemcpyDeviceToDevice, s));
-        if (!rc && kt > 0) rc = ck(cudaMemcpyAsync(B.trig + NTo[(size_t)r], st, 8 * (size_t)kt, cudaMemcpyDeviceToDevice, s));
+        const tpx_record *sr = failed[(size_t)r] ? reinterpret_cast<const tpx_record *>(acc_rec.p) + rstart[(size_t)r]
+                                                 : old_rec_copy + (roff[(size_t)r] - roff[(size_t)first]);
+        const long long *st = failed[(size_t)r] ? reinterpret_cast<const long long *>(acc_trig.p) + tstart[(size_t)r]
+                                                : old_trig_copy + (toff[(size_t)r] - toff[(size_t)first]);
+        if (kr > 0) {
+            src.push_back(reinterpret_cast<const unsigned long long *>(sr));
+            dst.push_back(reinterpret_cast<unsigned long long *>(B.cl + NO[(size_t)r]));
+            len.push_back(kr * WPR);
+        }
+        if (kt > 0) {
+            src.push_back(reinterpret_cast<const unsigned long long *>(st));
+            dst.push_back(reinterpret_cast<unsigned long long *>(B.trig + NTo[(size_t)r]));
+            len.push_back(kt);
+        }
+    }
+    if (!rc && !len.empty()) {
+        {   // pieces of at most 2^16 words, so that large runs spread over blocks
+            std::vector<const unsigned long long *> s2;
+            std::vector<unsigned long long *> d2;
+            std::vector<long long> l2;
+            for (size_t k = 0; k < len.size(); ++k)
+                for (long long o = 0; o < len[k]; o += 1 << 16) {
+                    s2.push_back(src[k] + o);
+                    d2.push_back(dst[k] + o);
+                    l2.push_back(std::min<long long>(1 << 16, len[k] - o));
+                }
+            src.swap(s2);
+            dst.swap(d2);
+            len.swap(l2);
+        }
+        const size_t ns = len.size();
+        Grow desc;
+        rc = desc.ensure(3 * 8 * ns + 512, s);
+        void **d_src = reinterpret_cast<void **>(desc.p);
+        void **d_dst = d_src + ns;
+        long long *d_len = reinterpret_cast<long long *>(d_dst + ns);
+        if (!rc) rc = ck(cudaMemcpyAsync(d_src, src.data(), 8 * ns, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(d_dst, dst.data(), 8 * ns, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = ck(cudaMemcpyAsync(d_len, len.data(), 8 * ns, cudaMemcpyHostToDevice, s));
+        if (!rc)
+            k_seg_copy<<<(unsigned)std::min<size_t>(ns, 152 * 8), 256, 0, s>>>(
+                reinterpret_cast<const unsigned long long *const *>(d_src), reinterpret_cast<unsigned long long *const *>(d_dst),
+                d_len, (long long)ns);
+        if (!rc) rc = ck(cudaStreamSynchronize(s));   // the descriptors are freed on return
     }
     if (!rc) {
         // offsets, totals; the counters keep describing the tiles' pass
@@ -1561,9 +1786,9 @@ extern "C" int tpx_summarize(tpx_ctx *c, const uint64_t *pk, int64_t n, tpx_chai
         const long long tp = c->cfg.wrap_thr_pix_ticks, tt = c->cfg.wrap_thr_tdc_ticks;
         k_tile_agg<<<(unsigned)tiles, GT, 0, s>>>(pk, n, tp, tt, tagg, tcnt);
         k_tile_prefix<<<1, PT, 0, s>>>(tagg, tpre, tcnt, toff, tiles, tp, tt, ntr, nullptr, res);
-        if (cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+        if (ck(cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s))) return TPX_ECUDA;
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    if (ck(cudaStreamSynchronize(s))) return TPX_ECUDA;
     out->pixels = h.pix.n;
     out->pix_first_raw = h.pix.first;
     out->pix_last_raw = h.pix.last;

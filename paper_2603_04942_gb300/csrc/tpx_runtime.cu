@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -17,6 +19,15 @@ void take_state(tpx_ctx *c, const tpxk::GAgg **E0, tpxk::GAgg **out) {
     *out = &c->d_state[c->cur ^ 1];
     c->cur ^= 1;
     c->state_once = false;
+}
+
+
+// a failed CUDA call: true; with TPX_DEBUG set in the environment its error
+// is printed to stderr
+static inline bool ckr(cudaError_t e, int line = __builtin_LINE()) {
+    if (e == cudaSuccess) return false;
+    if (std::getenv("TPX_DEBUG")) std::fprintf(stderr, "tpx_runtime.cu:%d: %s\n", line, cudaGetErrorString(e));
+    return true;
 }
 
 namespace {
@@ -205,7 +216,7 @@ int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *
 int tpx_reserve(tpx_ctx *c, int64_t max_packets) {
     if (!c || max_packets < 0) return TPX_EINVAL;
     if (max_packets <= c->max_packets) return TPX_OK;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     free_scratch(c);
     return alloc_scratch(c, max_packets);
 }
@@ -262,9 +273,9 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     take_state(c, &E0, &state_out);
     c->last.E0 = E0;
     c->last.state_out = state_out;
-    if (cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), c->stream) != cudaSuccess) return TPX_ECUDA;
-    if (cudaMemsetAsync(d_n_clusters, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
-    if (cudaMemsetAsync(d_n_trig, 0, sizeof(int64_t), c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), c->stream))) return TPX_ECUDA;
+    if (ckr(cudaMemsetAsync(d_n_clusters, 0, sizeof(int64_t), c->stream))) return TPX_ECUDA;
+    if (ckr(cudaMemsetAsync(d_n_trig, 0, sizeof(int64_t), c->stream))) return TPX_ECUDA;
     if (n == 0) {   // the state passes through unchanged
         if (E0) return cudaMemcpyAsync(state_out, E0, sizeof(tpxk::GAgg), cudaMemcpyDeviceToDevice, c->stream)
                        == cudaSuccess ? TPX_OK : TPX_ECUDA;
@@ -315,7 +326,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, c->stream);
     if (e != cudaSuccess) return TPX_ECUDA;
     if (timed) {
-        if (cudaEventRecord(t.ring[t.tail].b, c->stream) != cudaSuccess) return TPX_ECUDA;
+        if (ckr(cudaEventRecord(t.ring[t.tail].b, c->stream))) return TPX_ECUDA;
         t.ring[t.tail].geo = geo;
         t.ring[t.tail].n = n;
         t.tail = (t.tail + 1) % 8;
@@ -341,7 +352,9 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
     cudaStream_t s = c->stream;
-    const int geo = tune_pick(c, n);
+    // batches run on the larger ranges unless the configuration says
+    // otherwise: a run whose shots overflow a range costs a general-path redo
+    const int geo = c->cfg.tile_geometry == TPX_TILE_DEFAULT ? (int)tpxk::GEO_T4096 : c->geo;
     const int64_t T = tpxk::fused_tile_packets(geo), C = tpxk::fused_range_capacity(geo);
     // the tile queue: every run gets at least one tile (an empty run's tile
     // still records the run's offsets)
@@ -362,17 +375,17 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
                             al(4 * (size_t)n_runs) + 4 * al(8 * (size_t)n_tiles) + al(8 * (size_t)(grid * T)) +
                             2 * al(4 * (size_t)n_tiles) + 2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles);
     if (need_dev > B.dev_bytes) {
-        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        if (ckr(cudaStreamSynchronize(s))) return TPX_ECUDA;
         if (B.dev) cudaFree(B.dev);
         B.dev = nullptr;
         B.dev_bytes = 0;
         if (cudaMalloc(&B.dev, need_dev) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
-        if (cudaMemset(B.dev, 0, need_dev) != cudaSuccess) return TPX_ECUDA;   // fresh flags
+        if (ckr(cudaMemset(B.dev, 0, need_dev))) return TPX_ECUDA;   // fresh flags
         B.dev_bytes = need_dev;
     }
     const size_t need_host = 8 * (size_t)(n_runs + 1) + 8 * (size_t)n_runs + 4 * (size_t)n_tiles + 64;
     if (B.h_tab) {   // the previous batch's tables may still be uploading
-        if (cudaEventSynchronize(B.tab_copied) != cudaSuccess) return TPX_ECUDA;
+        if (ckr(cudaEventSynchronize(B.tab_copied))) return TPX_ECUDA;
     }
     if (need_host > B.h_bytes) {
         if (B.h_tab) cudaFreeHost(B.h_tab);
@@ -419,9 +432,13 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
         cudaMemcpyAsync(const_cast<int *>(bt.tile_run), h_tr, 4 * (size_t)n_tiles, cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
         return TPX_ECUDA;
-    if (cudaEventRecord(B.tab_copied, s) != cudaSuccess) return TPX_ECUDA;
-    if (cudaMemsetAsync(bt.run_failed, 0, 4 * (size_t)n_runs, s) != cudaSuccess) return TPX_ECUDA;
-    if (cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), s) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaEventRecord(B.tab_copied, s))) return TPX_ECUDA;
+    // the scratch layout follows the tile count: start every call's flags at zero
+    if (ckr(cudaMemsetAsync(B.ts.flags, 0, 4 * (size_t)n_tiles, s)) ||
+        ckr(cudaMemsetAsync(B.ts.cflags, 0, 4 * (size_t)n_tiles, s)))
+        return TPX_ECUDA;
+    if (ckr(cudaMemsetAsync(bt.run_failed, 0, 4 * (size_t)n_runs, s))) return TPX_ECUDA;
+    if (ckr(cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), s))) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_clusters, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_n_trig, 0, 8, s) != cudaSuccess)
         return TPX_ECUDA;
     c->seq = (c->seq + 1) & 0x3FFFFFFFu;
@@ -459,18 +476,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     p.ctl = c->ctl;
     p.stage = c->stage;
     p.bt = bt;
-    auto &t = c->tune;
-    const bool timed = c->cfg.tile_geometry == TPX_TILE_DEFAULT && !t.fixed && n >= kTuneMinPackets &&
-                       (t.tail + 1) % 8 != t.head;
-    if (timed && cudaEventRecord(t.ring[t.tail].a, s) != cudaSuccess) return TPX_ECUDA;
-    if (tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s) != cudaSuccess) return TPX_ECUDA;
-    if (timed) {
-        if (cudaEventRecord(t.ring[t.tail].b, s) != cudaSuccess) return TPX_ECUDA;
-        t.ring[t.tail].geo = geo;
-        t.ring[t.tail].n = n;
-        t.tail = (t.tail + 1) % 8;
-        t.issued[geo - 1] += 1;
-    }
+    if (ckr(tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s))) return TPX_ECUDA;
     // what a redo of failed runs needs
     c->last.valid = false;
     B.last = true;
@@ -492,7 +498,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     int64_t redone = 0;
     if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return TPX_ECUDA;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     if ((c->h_ctl->status & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) && !(c->h_ctl->status & tpxk::ST_DEVTIMEOUT) &&
         c->last.valid) {
         // the fused kernel met an input it cannot hold on chip: redo the call
@@ -503,7 +509,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
         if (rc) return rc;
         if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             return TPX_ECUDA;
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+        if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     }
     if ((c->h_ctl->status & tpxk::ST_RUN_REDO) && !(c->h_ctl->status & tpxk::ST_DEVTIMEOUT) && c->batch.last) {
         // runs of the last batch that the tiles could not hold: redo them
@@ -513,7 +519,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
         if (rc) return rc;
         if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             return TPX_ECUDA;
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+        if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     }
     tune_collect(c, redone != 0);
     const tpxk::Ctl &h = *c->h_ctl;
@@ -559,13 +565,13 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
                      c->st_cl, cl_cap, c->st_counts, c->st_trig, trig_cap, c->st_counts + 1);
     if (rc) return rc;
     int64_t counts[2] = {0, 0};
-    if (cudaMemcpyAsync(counts, c->st_counts, sizeof counts, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaMemcpyAsync(counts, c->st_counts, sizeof counts, cudaMemcpyDeviceToHost, s))) return TPX_ECUDA;
     if (h_labels && n &&
         cudaMemcpyAsync(h_labels, c->st_labels, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;
     if (h_is_peak && n && cudaMemcpyAsync(h_is_peak, c->st_peak, n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaStreamSynchronize(s))) return TPX_ECUDA;
     const int64_t ncl = counts[0] < cl_cap ? counts[0] : cl_cap;
     const int64_t ntr = counts[1] < trig_cap ? counts[1] : trig_cap;
     if (ncl > 0 && cudaMemcpyAsync(h_clusters, c->st_cl, sizeof(tpx_record) * ncl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -605,7 +611,7 @@ int tpx_set_state(tpx_ctx *c, const tpx_stream_state *st) {
     }
     if (cudaMemcpyAsync(&c->d_state[c->cur], &g, sizeof g, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return TPX_ECUDA;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     c->state_once = true;
     return TPX_OK;
 }
@@ -615,7 +621,7 @@ int tpx_get_state(tpx_ctx *c, tpx_stream_state *st) {
     tpxk::GAgg &g = c->h_state;
     if (cudaMemcpyAsync(&g, &c->d_state[c->cur], sizeof g, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return TPX_ECUDA;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TPX_ECUDA;
+    if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     st->pixels = g.pix.n;
     st->pix_last_raw = g.pix.last;
     st->pix_wraps = g.pix.sum;

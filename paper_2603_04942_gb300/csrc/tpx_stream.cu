@@ -14,6 +14,8 @@
 
 #include <chrono>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -23,6 +25,15 @@
 #include "tpx_common.cuh"
 #include "tpx_ctx.h"
 #include "tpx_fused.cuh"
+
+
+// a failed CUDA call: true; with TPX_DEBUG set in the environment its error
+// is printed to stderr
+static inline bool cks(cudaError_t e, int line = __builtin_LINE()) {
+    if (e == cudaSuccess) return false;
+    if (std::getenv("TPX_DEBUG")) std::fprintf(stderr, "tpx_stream.cu:%d: %s\n", line, cudaGetErrorString(e));
+    return true;
+}
 
 namespace {
 
@@ -184,20 +195,20 @@ int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, u
     int64_t *hc = S->h_counts;
     if (cudaMemcpyAsync(hc, S->d_counts, 6 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+    if (cks(cudaStreamSynchronize(s))) return TPX_ECUDA;
     const int64_t n_hits = hc[0], ntr = hc[1], emit = hc[3], p = hc[4];
     const unsigned status = (unsigned)hc[5];
     if (status & ST_TRIG_ORDER) return TPX_ECORRUPT;
     if (status & (ST_TRIG_CAP | ST_CLUSTER_CAP)) return TPX_EOVERFLOW;
     // unwrap state at p, while the decode's per-packet times are still alive
     if (p == P) {
-        if (cudaMemcpyAsync(S->st[2], S->st[1], sizeof(GAgg), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TPX_ECUDA;
+        if (cks(cudaMemcpyAsync(S->st[2], S->st[1], sizeof(GAgg), cudaMemcpyDeviceToDevice, s))) return TPX_ECUDA;
     } else if (p > 0) {
-        if (cudaMemsetAsync(S->d_probe, 0, sizeof(Probe), s) != cudaSuccess) return TPX_ECUDA;
+        if (cks(cudaMemsetAsync(S->d_probe, 0, sizeof(Probe), s))) return TPX_ECUDA;
         k_probe<<<gridn(p), BT, 0, s>>>(pk, p, S->d_probe);
         k_state_at<<<1, 1, 0, s>>>(pk, t_all, S->d_probe, S->st[0], S->st[2]);
     } else {
-        if (cudaMemcpyAsync(S->st[2], S->st[0], sizeof(GAgg), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return TPX_ECUDA;
+        if (cks(cudaMemcpyAsync(S->st[2], S->st[0], sizeof(GAgg), cudaMemcpyDeviceToDevice, s))) return TPX_ECUDA;
     }
     // cluster every hit; records only for the closed shots (shot < limit)
     int64_t n_cl = 0;
@@ -205,8 +216,8 @@ int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, u
         rc = tpxg::cluster_all(c, S->h, n_hits, nullptr, nullptr, S->trig_base + emit, ntr, S->d_cl, S->cap,
                                S->d_counts + 2);
         if (rc) return rc;
-        if (cudaMemcpyAsync(&hc[2], S->d_counts + 2, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPX_ECUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return TPX_ECUDA;
+        if (cks(cudaMemcpyAsync(&hc[2], S->d_counts + 2, 8, cudaMemcpyDeviceToHost, s))) return TPX_ECUDA;
+        if (cks(cudaStreamSynchronize(s))) return TPX_ECUDA;
         n_cl = hc[2];
     }
     rc = grow_pinned(*sl, n_cl > 0 ? n_cl : 1, emit > 0 ? emit : 1);
@@ -238,7 +249,7 @@ int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, u
     sl->t_submit = t0;
     sl->ticket = S->next_ticket++;
     sl->busy = true;
-    if (cudaEventRecord(sl->done, s) != cudaSuccess) return TPX_ECUDA;
+    if (cks(cudaEventRecord(sl->done, s))) return TPX_ECUDA;
     *ticket = sl->ticket;
     return TPX_OK;
 }

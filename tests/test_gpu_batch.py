@@ -77,6 +77,23 @@ def test_batch_matches_each_run_alone(mode):
     check_against_oracle(g, pk, offs, mode)
 
 
+def test_several_redone_runs_share_one_clustering_pass():
+    """Three runs with shots longer than a range, between ordinary runs: they
+    are redone together (shots kept apart per run) and spliced back in run
+    order, with per-packet labels."""
+    rng = np.random.default_rng(21)
+    pk, offs = make_batch(n_runs=12, seed=8, long_shot=False)
+    runs = [pk[offs[r]:offs[r + 1]] for r in range(offs.size - 1)]
+    for k, at in enumerate((2, 6, 9)):
+        runs.insert(at, _long_shot_run(rng, pixels=8500 + 700 * k))
+    offs = np.zeros(len(runs) + 1, np.int64)
+    offs[1:] = np.cumsum([r.size for r in runs])
+    pk = np.concatenate(runs)
+    g = run_batch(pk, offs)
+    assert g["counters"]["redone"] == 3
+    check_against_oracle(g, pk, offs)
+
+
 def test_batch_on_the_smaller_tiles():
     pk, offs = make_batch(seed=6)
     g = run_batch(pk, offs, tile=tpx.TILE_2048)
