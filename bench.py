@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "pixel hits/s clustered+centroided"
 UNIT = "hits/s"
 CLUSTER_BYTES = 88
-KERNEL_SRC = os.path.join(ROOT, "paper_2603_04942_gb300", "csrc", "tpx_fused.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2603_04942_gb300", "csrc", f) for f in ("tpx_fused.cu", "tpx_fused_body.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_large_batch.md")
 
 
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=4096)
     ap.add_argument("--batch-only", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=3, help="timed whole calls of the batch (each ~5 s)")
     ap.add_argument("--stream-only", action="store_true")
     ap.add_argument("--stream-chunks", type=int, default=150)
     ap.add_argument("--stream-rates", type=str, default="10,40,80")
@@ -127,7 +128,7 @@ def traffic_per_packet():
     summary, if it was taken on the current kernel source."""
     try:
         txt = open(TRAFFIC_FILE).read()
-        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()[:16]
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         m_b = re.search(r"dram_bytes_per_packet:\s*([0-9.]+)", txt)
         if m_sha and m_b and m_sha.group(1) == sha:
@@ -273,14 +274,14 @@ def batch_bench(args) -> dict:
     out = ctx.alloc_batch_outputs(n, len(runs), labels=False, is_peak=False,
                                   cluster_capacity=int(1.3 * expect) + (1 << 20), trig_capacity=shots + 16)
     s = ctx.stream
-    for _ in range(args.warmup):
+    for _ in range(max(3, min(args.warmup, 3))):
         ctx.tpx_process_batch(d_pk, offs, out)
-    rc, counters = ctx.tpx_sync(check=False)
-    if rc != 0:
-        raise SystemExit(f"tpx_process_batch failed in warm-up: {rc} {counters}")
+        rc, counters = ctx.tpx_sync(check=False)
+        if rc != 0:
+            raise SystemExit(f"tpx_process_batch failed in warm-up: {rc} {counters}")
     # a step is the whole call: the launch and the tpx_sync that redoes the
     # runs the tiles could not hold (host wall clock, device synchronised)
-    steps = args.steps
+    steps = args.batch_steps
     step_ms = []
     torch.cuda.synchronize()
     for k in range(steps):
@@ -310,7 +311,7 @@ def batch_bench(args) -> dict:
            "timing": "wall clock per whole call (launch + tpx_sync, redone runs included), device synchronised",
            "tiles_pass_ms": tiles_ms,
            "runs": len(runs), "shots": shots, "packets": n, "pixel_hits": counters["pixels"], "clusters": n_cl,
-           "redone_runs": counters["redone"], "steps": steps, "warmup": args.warmup,
+           "redone_runs": counters["redone"], "steps": steps, "warmup": 3,
            "tile_geometry": {1: "4096-packet tiles", 2: "2048-packet tiles"}.get(tune["tile_geometry"], "sampling"),
            "generation_s": round(gen_s, 1)}
     ctx.close()
@@ -434,7 +435,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None if tpp is None else tpp * n,
             "algorithmic_bytes": alg_bytes, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-            "kernel": "tpxk::fused_kernel<0>", "avg_launch_ms": avg_ms}
+            "kernel": {1: "geo_t4096::fused_kernel<CC, staged>", 2: "geo_t2048::fused_kernel<CC, staged>"}.get(
+                tuning["tile_geometry"], "fused_kernel"), "avg_launch_ms": avg_ms}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
