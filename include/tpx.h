@@ -233,9 +233,13 @@ int tpx_centroid(tpx_ctx *ctx, const tpx_hits *hits, const int64_t *d_labels, co
 /* Wait for the context's queued work and translate the device status word
    of the last call into a status code.  If counters != NULL, fill it.
    When the last call was tpx_process and the fused kernel met an input it
-   cannot hold on chip (a range longer than 8192 packets, or a pixel whose
+   cannot hold on chip (a range longer than the tiles' range capacity -- 8192
+   positions for TPX_TILE_4096, 5120 for TPX_TILE_2048 -- or a pixel whose
    trigger lies outside its range), tpx_sync redoes that call exactly with the
-   general path before returning (this may allocate general scratch). */
+   general path before returning (this may allocate general scratch); for a
+   batch, the runs concerned.  Only the last call since the previous tpx_sync
+   is redone: if an earlier one needed it, tpx_sync returns TPX_EUNSUPPORTED
+   (call tpx_sync after each call whose input may be unusual). */
 int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
 
 /* Upper bound on n_packets for tpx_process_noalloc (2^26 packets, 512 MB of

@@ -22,7 +22,7 @@ struct tpx_ctx {
         int done[2];          // samples timed
         double best[2];       // lowest ms per million packets seen
         int head, tail;       // ring of launched, not yet timed samples
-        struct Sample { cudaEvent_t a, b; int geo; int64_t n; } ring[8];
+        struct Sample { cudaEvent_t a, b; int geo; int64_t n; bool failed; } ring[8];
     } tune;
     int64_t max_packets;
     int64_t max_tiles;
@@ -33,6 +33,9 @@ struct tpx_ctx {
     int64_t stage_records;    // its capacity
     tpxk::Ctl *ctl;           // device control block
     tpxk::Ctl *h_ctl;         // pinned host copy
+    unsigned *d_sticky;       // failure bits of calls that were not synchronised
+    bool synced;              // tpx_sync ran after the last call
+    int64_t redone_early;     // the last call was already redone (autotuner sample)
     // device staging for tpx_process_host
     uint64_t *st_pk;
     int64_t *st_labels;

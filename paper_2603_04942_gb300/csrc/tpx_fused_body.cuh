@@ -1,10 +1,11 @@
 // tpx_fused_body.cuh -- the fused kernel, included once per tile geometry
 // by tpx_fused.cu inside a namespace that defines NT (threads per CTA),
-// T (packets per tile), C (range capacity), HB (hash buckets) and MINB
-// (CTAs per SM). No include guard: it is meant to be included repeatedly.
+// T (packets per tile), C (range capacity), HB (hash buckets), MS (trigger
+// packets a range may hold) and MINB (CTAs per SM). No include guard: it
+// is meant to be included repeatedly.
 constexpr int NW = NT / 32;
 constexpr int KP = C / NT;         // positions per thread in contiguous walks
-constexpr int MAXSEG = T + 16;     // TDC packets per range: at most a tile's plus the terminator
+constexpr int MAXSEG = MS;         // TDC packets a range may hold (more: the call is redone)
 constexpr uint64_t INVALID = ~0ull;
 constexpr uint32_t EMPTY = 0xFFFFu;
 constexpr long long MAX_SPIN = 1LL << 22;   // bounded look-back waits (~0.5 s)

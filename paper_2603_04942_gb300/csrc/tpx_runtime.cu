@@ -112,6 +112,24 @@ int grow(Tp **ptr, int64_t *cap, int64_t want) {
 
 namespace {
 
+// A call's failure bits (a range the tiles could not hold, a batch run to
+// redo) are resolved by the tpx_sync after it. When a new call starts before
+// that sync, the previous call's bits move to the sticky word, and tpx_sync
+// reports them instead of leaving that call's outputs silently incomplete.
+__global__ void k_keep_status(const tpxk::Ctl *ctl, unsigned *sticky) {
+    const unsigned f = ctl->status & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION | tpxk::ST_RUN_REDO);
+    if (f) *sticky |= f;
+}
+int begin_call(tpx_ctx *c) {
+    if (!c->synced) {
+        k_keep_status<<<1, 1, 0, c->stream>>>(c->ctl, c->d_sticky);
+        if (ckr(cudaGetLastError())) return TPX_ECUDA;
+    }
+    c->synced = false;
+    c->redone_early = 0;
+    return TPX_OK;
+}
+
 // ---- tile-geometry autotuner ----
 constexpr int64_t kTuneMinPackets = 1LL << 20;   // smaller calls run untimed on the 4096 tiles
 constexpr double kTunePenalty = 1e30;            // a sample whose call had to be redone
@@ -134,7 +152,7 @@ void tune_collect(tpx_ctx *c, bool redone_last) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, smp.a, smp.b);
         const bool newest = (t.head + 1) % 8 == t.tail;
-        const double v = (redone_last && newest) ? kTunePenalty : (double)ms * 1e6 / (double)smp.n;
+        const double v = (smp.failed || (redone_last && newest)) ? kTunePenalty : (double)ms * 1e6 / (double)smp.n;
         const int k = smp.geo - 1;
         if (t.done[k] == 0 || v < t.best[k]) t.best[k] = v;
         t.done[k] += 1;
@@ -193,6 +211,12 @@ int tpx_create(tpx_ctx **out, const tpx_config *cfg, int64_t max_packets, void *
         return TPX_ENOMEM;
     }
     cudaMemset(c->d_state, 0, 2 * sizeof(tpxk::GAgg));   // all zero = the start of a stream
+    if (cudaMalloc(&c->d_sticky, sizeof(unsigned)) != cudaSuccess || cudaMemset(c->d_sticky, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        tpx_destroy(c);
+        return TPX_ENOMEM;
+    }
+    c->synced = true;
     for (auto &smp : c->tune.ring)
         if (cudaEventCreate(&smp.a) != cudaSuccess || cudaEventCreate(&smp.b) != cudaSuccess) {
             tpx_destroy(c);
@@ -235,6 +259,7 @@ int tpx_destroy(tpx_ctx *c) {
     if (c->st_counts) cudaFree(c->st_counts);
     if (c->g_mem) cudaFree(c->g_mem);
     if (c->d_state) cudaFree(c->d_state);
+    if (c->d_sticky) cudaFree(c->d_sticky);
     for (auto &smp : c->tune.ring) {
         if (smp.a) cudaEventDestroy(smp.a);
         if (smp.b) cudaEventDestroy(smp.b);
@@ -255,6 +280,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     if ((reinterpret_cast<uintptr_t>(d_packets) & 15) != 0) return TPX_EINVAL;
     if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
+    if (begin_call(c)) return TPX_ECUDA;
     c->last.valid = true;
     c->batch.last = false;
     c->last.pk = d_packets;
@@ -326,11 +352,27 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, c->stream);
     if (e != cudaSuccess) return TPX_ECUDA;
     if (timed) {
-        if (ckr(cudaEventRecord(t.ring[t.tail].b, c->stream))) return TPX_ECUDA;
-        t.ring[t.tail].geo = geo;
-        t.ring[t.tail].n = n;
+        // a sample runs synchronously: a geometry whose ranges could not hold
+        // the input loses, and that call is redone at once, so that a later
+        // call cannot leave it unresolved
+        auto &smp = t.ring[t.tail];
+        if (ckr(cudaEventRecord(smp.b, c->stream))) return TPX_ECUDA;
+        smp.geo = geo;
+        smp.n = n;
+        smp.failed = false;
         t.tail = (t.tail + 1) % 8;
         t.issued[geo - 1] += 1;
+        unsigned st = 0;
+        if (ckr(cudaMemcpyAsync(&st, &c->ctl->status, 4, cudaMemcpyDeviceToHost, c->stream)) ||
+            ckr(cudaStreamSynchronize(c->stream)))
+            return TPX_ECUDA;
+        if ((st & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) && !(st & tpxk::ST_DEVTIMEOUT)) {
+            smp.failed = true;
+            const int rc = tpxg::redo_last(c);
+            c->last.valid = false;
+            c->redone_early = 1;
+            if (rc) return rc;
+        }
     }
     return TPX_OK;
 }
@@ -351,6 +393,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     if ((reinterpret_cast<uintptr_t>(d_packets) & 15) != 0) return TPX_EINVAL;
     if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
+    if (begin_call(c)) return TPX_ECUDA;
     cudaStream_t s = c->stream;
     // batches run on the larger ranges unless the configuration says
     // otherwise: a run whose shots overflow a range costs a general-path redo
@@ -495,7 +538,13 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
 
 int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     if (!c) return TPX_EINVAL;
-    int64_t redone = 0;
+    int64_t redone = c->redone_early;
+    c->redone_early = 0;
+    c->synced = true;
+    unsigned sticky = 0;
+    if (ckr(cudaMemcpyAsync(&sticky, c->d_sticky, 4, cudaMemcpyDeviceToHost, c->stream)) ||
+        ckr(cudaMemsetAsync(c->d_sticky, 0, 4, c->stream)))
+        return TPX_ECUDA;
     if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return TPX_ECUDA;
     if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
@@ -538,6 +587,9 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     }
     const unsigned s = h.status;
     if (s & tpxk::ST_DEVTIMEOUT) return TPX_EDEVTIMEOUT;
+    // an earlier call since the previous sync needed the general path, which
+    // only the last call gets: its outputs are incomplete
+    if (sticky) return TPX_EUNSUPPORTED;
     if (s & tpxk::ST_TRIG_ORDER) return TPX_ECORRUPT;
     if (s & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) return TPX_EUNSUPPORTED;
     if (c->cfg.strict && h.counters[tpxk::C_CORRUPT]) return TPX_ECORRUPT;

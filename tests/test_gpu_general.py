@@ -135,3 +135,34 @@ def test_fallback_for_pixels_whose_trigger_is_outside_the_range():
 def test_normal_input_is_not_redone():
     pk = synth.generate(synth.small(n_shots=50))[0]
     assert gpu_run(pk)["counters"]["redone"] == 0
+
+
+def test_an_unsynchronised_call_that_needed_the_general_path_is_reported():
+    """Only the last call before tpx_sync is redone; when an earlier call
+    needed it, tpx_sync reports TPX_EUNSUPPORTED instead of returning that
+    call's incomplete outputs as if they were fine."""
+    rng = np.random.default_rng(41)
+    b = StreamBuilder()
+    t0 = 5_000_000
+    b.tdc(t0)
+    for _ in range(10_000):   # longer than any range
+        b.pix(rng.integers(0, 64), rng.integers(0, 64), rng.integers(1, 300), t0 + 700 + rng.integers(0, 3000))
+    b.tdc(t0 + 640_000)
+    long_pk = b.packets()
+    ok_pk = synth.generate(synth.small(n_shots=40))[0]
+    ctx = tpx.Context(tpx.Config(tile_geometry=tpx.TILE_4096), max_packets=max(long_pk.size, ok_pk.size))
+    try:
+        d_long, d_ok = to_device(long_pk), to_device(ok_pk)
+        out1 = ctx.alloc_outputs(long_pk.size, True, False, long_pk.size, 16)
+        out2 = ctx.alloc_outputs(ok_pk.size, True, False, ok_pk.size, 64)
+        ctx.tpx_process(d_long, out1)
+        ctx.tpx_process(d_ok, out2)
+        rc, _ = ctx.tpx_sync(check=False)
+        assert rc == -9   # TPX_EUNSUPPORTED
+        # synchronised calls are exact again
+        ctx.tpx_process(d_long, out1)
+        rc, cnt = ctx.tpx_sync(check=False)
+        assert rc == 0 and cnt["redone"] == 1
+        assert_parity(ctx.collect(out1, rc, cnt), oracle_run(long_pk), check_counters=False)
+    finally:
+        ctx.close()

@@ -57,8 +57,9 @@ def test_dense_random_streams(seed, mode):
 
 
 def test_shot_longer_than_the_smaller_range_is_redone():
-    """A 5000-pixel shot fits the 8192-position ranges but not 4096-position
-    ones: the smaller geometry hands the call to the general path, exactly."""
+    """A 5000-pixel shot fits the 8192-position ranges but not the 5120-position
+    ones once its trigger's tile adds its own packets: the smaller geometry
+    hands the call to the general path, exactly."""
     rng = np.random.default_rng(9)
     b = StreamBuilder()
     t = 20_000_000
@@ -123,15 +124,15 @@ def test_autotuner_times_both_geometries_and_keeps_one():
 
 
 def test_autotuner_avoids_the_geometry_that_needed_a_redo():
-    """3000-pixel shots fit every 8192-position range (at most 4095 + 3001
-    positions) but overflow many 4096-position ones: the sample on the
+    """3500-pixel shots fit every 8192-position range (at most 4095 + 3501
+    positions) but overflow many 5120-position ones: the sample on the
     2048-packet tiles is redone by the general path and loses."""
     rng = np.random.default_rng(13)
     b = StreamBuilder()
     t = 30_000_000
-    for s in range(360):
+    for s in range(310):
         b.tdc(t + s * 640_000)
-        for _ in range(3000):
+        for _ in range(3500):
             b.pix(rng.integers(0, 256), rng.integers(0, 256), rng.integers(1, 300),
                   t + s * 640_000 + 900 + rng.integers(0, 60_000))
     pk = b.packets()
