@@ -12,6 +12,7 @@
 // GPU.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdint>
 #include <cstdio>
@@ -152,7 +153,11 @@ inline unsigned gridn(long long n) {
 }
 inline size_t al(size_t b) { return (b + 255) & ~size_t(255); }
 
+// grows a slot's pinned result buffers geometrically (freeing pinned memory
+// synchronises the device, so growth must stay rare)
 int grow_pinned(Slot &sl, int64_t ncl, int64_t ntr) {
+    if (ncl > sl.cap_cl) ncl = std::max<int64_t>(ncl, 2 * sl.cap_cl);
+    if (ntr > sl.cap_trig) ntr = std::max<int64_t>(ntr, 2 * sl.cap_trig);
     if (ncl > sl.cap_cl) {
         if (sl.h_cl) cudaFreeHost(sl.h_cl);
         sl.h_cl = nullptr;
@@ -320,7 +325,8 @@ int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda
     cudaMemsetAsync(S->st[0], 0, sizeof(tpxk::GAgg), S->s);
     S->slots.resize((size_t)cfg->slots);
     for (auto &sl : S->slots)
-        if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            tpxs::grow_pinned(sl, std::max<int64_t>(1024, C / 16), std::max<int64_t>(64, C / 4096))) {
             tpx_stream_destroy(S);
             return TPX_ECUDA;
         }
