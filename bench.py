@@ -51,6 +51,7 @@ def parse():
                     help="fused-kernel tile geometry (speed only; results are identical)")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-timewalk", action="store_true")
     ap.add_argument("--batch-runs", type=int, default=4096)
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed whole calls of the batch (each ~5 s)")
@@ -320,6 +321,44 @@ def batch_bench(args) -> dict:
     return res
 
 
+def timewalk_bench(args) -> dict:
+    """Timewalk calibration (Sec. IV.C): the GPU ToT-ToF histogram of a
+    calibration run (one ion peak, a known delay model) timed with CUDA
+    events, then the host fits of Eq. 1."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    from paper_2603_04942_gb300 import timewalk as tw
+    p = synth.calibration(n_shots=20_000)
+    pk = synth.generate(p)[0]
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+    dec = ctx.tpx_decode(d)
+    ctx.tpx_sync()
+    nh = int(dec["n_hits"].item())
+    lo, nb = synth.CALIBRATION_TOF_TICKS - 10, 128
+    hist = ctx.tpx_tot_tof_histogram(dec["hits"], nh, lo, 1, nb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(ctx.stream)
+    for _ in range(reps):
+        ctx.tpx_tot_tof_histogram(dec["hits"], nh, lo, 1, nb, hist=hist)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    fit, _ = tw.calibrate(ctx, dec["hits"], nh, lo, 1, nb, fix_d=True)
+    fit_s = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "calibration run: 20,000 shots x 20 particles at one ToF (5 us), ToA delay "
+                        "1500 / (ToT + 5) + 10 ns per pixel, seed 4",
+            "hits": nh, "histogram_ms": ms, "histogram_hits_per_s": nh / (ms / 1e3), "calibration_s": fit_s,
+            "fit_ticks": {"a": fit.a, "b": fit.b, "c": fit.c, "d": fit.d, "rms": fit.rms},
+            "truth_ticks": {"a": p.timewalk_a / 1.5625, "b": p.timewalk_b,
+                            "c": synth.CALIBRATION_TOF_TICKS + p.timewalk_c / 1.5625, "d": 1.0}}
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, one bounded sample of
     the workload per step (a different shot range each step)."""
@@ -479,6 +518,9 @@ def main():
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_bench(args)
+    timewalk = None
+    if rank == 0 and not args.no_timewalk:
+        timewalk = timewalk_bench(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -494,7 +536,7 @@ def main():
                                tuning["tile_geometry"], "sampling"),
                            "tile_choice": "autotuned in warm-up" if args.tile == "default" else "fixed by --tile",
                            "generation_s": round(t_gen, 1)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "batch": batch, "clocks": clk,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk, "clocks": clk,
                 "gpu_launches": 2 * args.steps - 1,   # fused kernels + status carries between unsynchronised calls
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "counters": counters}

@@ -269,6 +269,19 @@ int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t
                         int64_t *d_n_clusters, int64_t *d_trig_t, int64_t trig_capacity,
                         int64_t *d_n_trig, tpx_counters *h_counters);
 
+/* ToT-ToF joint histogram for the timewalk calibration (Sec. IV.C: a
+   narrow ToF slice around an ion peak, the ToF distribution of every ToT
+   value; the fit of Eq. 1 to the per-ToT centres is host work).  Adds, for
+   every hit whose tof lies in [tof_lo_ticks, tof_lo_ticks + n_tof_bins *
+   tof_bin_ticks), one count to d_hist[tot * n_tof_bins + (tof - tof_lo_ticks)
+   / tof_bin_ticks]; the caller zeroes d_hist (1024 * n_tof_bins uint32,
+   device) and may accumulate several calls.  Hits as produced by tpx_decode
+   on a context without a timewalk table (tof is then the measured ToF).
+   Asynchronous on the context stream.  TPX_EINVAL for n_tof_bins < 1,
+   tof_bin_ticks < 1 or NULL pointers with n_hits > 0. */
+int tpx_tot_tof_histogram(tpx_ctx *ctx, const tpx_hits *hits, int64_t n_hits, int32_t tof_lo_ticks,
+                          int32_t tof_bin_ticks, int32_t n_tof_bins, uint32_t *d_hist);
+
 /* Batched runs (Sec. VI batches shots by zero-padding them to a rectangle;
    here nothing is padded): n_runs independent acquisitions concatenated in
    one device buffer, run r being packets [h_run_offsets[r],

@@ -39,7 +39,7 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_strerror", "tpx_version")
 
@@ -137,6 +137,7 @@ def load(path: str | None = None):
         L.tpx_version.restype = ctypes.c_char_p
         L.tpx_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.tpx_process_batch.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp]
+        L.tpx_tot_tof_histogram.argtypes = [vp, ctypes.POINTER(_CHits), i64, i32, i32, i32, vp]
         L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_set_state.restype = i32
@@ -372,6 +373,20 @@ class Context:
     @staticmethod
     def _chits(h: dict) -> _CHits:
         return _CHits(*(_ptr(h[f]) for f in ("index", "shot", "t", "tof", "x", "y", "tot")))
+
+    def tpx_tot_tof_histogram(self, hits: dict, n_hits: int, tof_lo_ticks: int, tof_bin_ticks: int,
+                              n_tof_bins: int, hist=None):
+        """Adds the ToT-ToF histogram of the hits' ToF window to `hist` (a zeroed
+        device uint32 tensor of 1024 x n_tof_bins if None); returns it."""
+        import torch
+        if hist is None:
+            hist = torch.zeros(1024 * n_tof_bins, dtype=torch.int32, device=hits["tof"].device)
+        ch = self._chits(hits)
+        rc = lib().tpx_tot_tof_histogram(self._h, ctypes.byref(ch), int(n_hits), int(tof_lo_ticks), int(tof_bin_ticks),
+                                         int(n_tof_bins), _ptr(hist))
+        if rc:
+            raise TpxError(rc, "tpx_tot_tof_histogram")
+        return hist
 
     def tpx_cluster(self, hits: dict, n_hits: int, is_peak: bool = True) -> dict:
         import torch

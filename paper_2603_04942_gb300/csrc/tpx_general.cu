@@ -1767,6 +1767,29 @@ extern "C" int tpx_centroid(tpx_ctx *c, const tpx_hits *hits, const int64_t *d_l
     return tpxg::centroid_impl(c, *hits, d_labels, d_is_peak, n, d_clusters, cap, d_n_clusters);
 }
 
+namespace tpxg {
+// one count per hit inside the ToF window (Sec. IV.C calibration histogram)
+__global__ void k_tot_tof_hist(const int32_t *tof, const uint16_t *tot, long long n, int lo, int bin, int nb,
+                               unsigned *hist) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long d = (long long)tof[i] - lo;
+        if (d < 0) continue;
+        const long long b = d / bin;
+        if (b >= nb) continue;
+        atomicAdd(&hist[(long long)tot[i] * nb + b], 1u);
+    }
+}
+}  // namespace tpxg
+
+extern "C" int tpx_tot_tof_histogram(tpx_ctx *c, const tpx_hits *hits, int64_t n, int32_t lo, int32_t bin, int32_t nb,
+                                     uint32_t *d_hist) {
+    if (!c || !hits || n < 0 || bin < 1 || nb < 1 || !d_hist) return TPX_EINVAL;
+    if (n > 0 && (!hits->tof || !hits->tot)) return TPX_EINVAL;
+    if (n == 0) return TPX_OK;
+    tpxg::k_tot_tof_hist<<<tpxg::grid_for(n), tpxg::GT, 0, c->stream>>>(hits->tof, hits->tot, n, lo, bin, nb, d_hist);
+    return tpxg::ck(cudaGetLastError());
+}
+
 extern "C" int tpx_summarize(tpx_ctx *c, const uint64_t *pk, int64_t n, tpx_chain_summary *out) {
     if (!c || !out || n < 0 || (n > 0 && !pk)) return TPX_EINVAL;
     using namespace tpxg;

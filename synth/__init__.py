@@ -129,6 +129,17 @@ def batched(n_runs: int = 4096, seed: int = 2, shots_lo: int = 10, shots_hi: int
     return runs
 
 
+def calibration(n_shots: int = 2000, a_ns: float = 1500.0, b: float = 5.0, c_ns: float = 10.0, **kw) -> Params:
+    """Timewalk calibration run: one narrow ion peak (every particle at a ToF
+    of 5 us), 20 particles per shot, and a ToA delay of a / (ToT + b) + c ns
+    per pixel (the form of Eq. 1 with d = 1), seed 4."""
+    return Params(n_shots=n_shots, seed=4, particles_per_shot=20.0, tof_lo_ns=5000.0, tof_hi_ns=5000.0,
+                  timewalk_a=a_ns, timewalk_b=b, timewalk_c=c_ns).replace(**kw)
+
+
+CALIBRATION_TOF_TICKS = 3200       # 5 us of the calibration recipe, in ticks
+
+
 def stated_size(p: Params) -> Params:
     """Variant whose truncation (ToT >= 90) gives the 5-15 px per particle
     that the workload description quotes; the literal parameters give ~25."""

@@ -121,6 +121,18 @@ def test_dense_random_streams(seed, mode):
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_large_box_radius(small, mode):
+    """A 5-pixel box radius (the size of the paper's toy neighbourhood,
+    Sec. V.A) on a slice of the small configuration: many more cells per
+    hit, partners beyond eight per pixel (the serial union fallback)."""
+    pk = small[0][: 25 * TILE + 11]
+    g = gpu_run(pk, rx=5, ry=5, dt=100, mode=mode)
+    o = oracle_run(pk, rx=5, ry=5, dt=100, mode=mode)
+    assert g["status"] == 0
+    assert_parity(g, o)
+
+
 def test_pixel_wrap_straddle_and_stragglers(small):
     """Shot 500 of the small configuration straddles the 2^34-tick pixel wrap
     with pre-wrap pixels reported after post-wrap ones (Sec. IV.A)."""
