@@ -282,6 +282,54 @@ int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t
 int tpx_tot_tof_histogram(tpx_ctx *ctx, const tpx_hits *hits, int64_t n_hits, int32_t tof_lo_ticks,
                           int32_t tof_bin_ticks, int32_t n_tof_bins, uint32_t *d_hist);
 
+/* ---- learned overlap refiner (not in the paper; its multi-hit discussion,
+   Sec. VII.B, and the local-maximum count of Sec. V.B motivate it) ----
+   A cluster may hold two particles. Its 9 x 9 patch (channel 0: ToT / 1023
+   rounded to bf16; channel 1: ToA relative to the cluster's earliest pixel in
+   units of 32 ticks, clamped to [-8, 8], rounded to fp16; empty cells 0;
+   stored as fp32), centred on the centroid rounded half up, goes through a multilayer perceptron 162 -> H -> H -> 6 (ReLU):
+   two logits (one or two particles) and (dx, dy) of each particle in pixels
+   from the patch centre.  Parameters are one fp32 array (W1[162 x H], b1,
+   W2[H x H], b2, W3[H x 6], b3; row-major). */
+
+/* Patches of the CC-mode clusters with more than min_pixels pixels, from a
+   tpx_process call's packets, per-packet labels and records (device, as
+   that call wrote them).  d_patches [capacity x 162] floats, d_sel
+   [capacity] record index of each patch, d_centre [capacity x 2] patch
+   centre (x, y); *d_n_patches the number of such clusters (TPX_EOVERFLOW
+   if above capacity: only `capacity` are written).  Synchronises. */
+int tpx_refine_patches(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets, int64_t packet_index_base,
+                       const int64_t *d_labels, const tpx_record *d_clusters, int64_t n_clusters, int32_t min_pixels,
+                       float *d_patches, int64_t *d_sel, int32_t *d_centre, int64_t capacity, int64_t *d_n_patches);
+
+/* Number of floats of the parameter array for H hidden units. */
+int64_t tpx_refiner_params(int32_t hidden);
+
+/* Forward pass of n patches: d_out [n x 6]; d_work [n x 2H] floats.
+   Asynchronous (fp32 tiled GEMMs on the context stream). */
+int tpx_refiner_forward(tpx_ctx *ctx, const float *d_params, int32_t hidden, const float *d_x, int64_t n,
+                        float *d_work, float *d_out);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, step >= 1) on a minibatch of
+   n <= 2^21 patches with targets d_y [n x 5] = (count 1 or 2, dx1, dy1, dx2,
+   dy2): loss = mean softmax cross-entropy of the count + offset_weight x
+   mean half squared error of the true particles' offsets.  d_grad,
+   d_adam_m, d_adam_v: parameter-sized; d_work [n x (4H + 12)] floats;
+   *d_loss the minibatch loss before the step.  Asynchronous. */
+int tpx_refiner_train_step(tpx_ctx *ctx, float *d_params, float *d_adam_m, float *d_adam_v, float *d_grad,
+                           int32_t hidden, int64_t step, const float *d_x, const float *d_y, int64_t n, float lr,
+                           float offset_weight, float *d_work, float *d_loss);
+
+/* Refined hits from the forward outputs: per patch d_hits[5] = (k, x1, y1,
+   x2, y2): k = 2 when the probability of two particles reaches `threshold`
+   (positions from the offsets); else (x1, y1) is the cluster's plain
+   centroid (Sec. V.C) with k = 1 when the probability of one particle
+   reaches `threshold`, k = 0 otherwise (x2 = y2 = 0).  The count is decided on the fp32 logit margin
+   o1 - o0 against log(threshold / (1 - threshold)).  TPX_EINVAL unless
+   0 < threshold < 1.  Asynchronous. */
+int tpx_refine_decide(tpx_ctx *ctx, const float *d_out, const tpx_record *d_clusters, const int64_t *d_sel,
+                      const int32_t *d_centre, int64_t n, float threshold, float *d_hits);
+
 /* Batched runs (Sec. VI batches shots by zero-padding them to a rectangle;
    here nothing is padded): n_runs independent acquisitions concatenated in
    one device buffer, run r being packets [h_run_offsets[r],

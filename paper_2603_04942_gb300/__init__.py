@@ -39,7 +39,8 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
-                    "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_refine_patches", "tpx_refiner_params",
+                    "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_strerror", "tpx_version")
 
@@ -138,6 +139,15 @@ def load(path: str | None = None):
         L.tpx_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.tpx_process_batch.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp]
         L.tpx_tot_tof_histogram.argtypes = [vp, ctypes.POINTER(_CHits), i64, i32, i32, i32, vp]
+        L.tpx_refine_patches.argtypes = [vp, vp, i64, i64, vp, vp, i64, i32, vp, vp, vp, i64, vp]
+        L.tpx_refiner_params.argtypes = [i32]
+        L.tpx_refiner_params.restype = i64
+        L.tpx_refiner_forward.argtypes = [vp, vp, i32, vp, i64, vp, vp]
+        L.tpx_refiner_train_step.argtypes = [vp, vp, vp, vp, vp, i32, i64, vp, vp, i64, ctypes.c_float,
+                                             ctypes.c_float, vp, vp]
+        L.tpx_refine_decide.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.c_float, vp]
+        for f in ("tpx_refine_patches", "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide"):
+            getattr(L, f).restype = i32
         L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_set_state.restype = i32
@@ -387,6 +397,62 @@ class Context:
         if rc:
             raise TpxError(rc, "tpx_tot_tof_histogram")
         return hist
+
+    # -- the learned overlap refiner --
+    def tpx_refine_patches(self, packets, labels, clusters, n_clusters: int, min_pixels: int = 12,
+                           capacity: int | None = None, index_base: int = 0) -> dict:
+        """Patches of the clusters with more than `min_pixels` pixels (device
+        tensors: patches [n x 162] f32, sel [n] record index, centre [n x 2];
+        n the number of such clusters, status 0 or TPX_EOVERFLOW)."""
+        import torch
+        dev = packets.device
+        cap = int(capacity if capacity is not None else max(1, n_clusters))
+        out = dict(patches=torch.empty((cap, 162), dtype=torch.float32, device=dev),
+                   sel=torch.empty(cap, dtype=torch.int64, device=dev),
+                   centre=torch.empty((cap, 2), dtype=torch.int32, device=dev),
+                   n=torch.zeros(1, dtype=torch.int64, device=dev), capacity=cap)
+        rc = lib().tpx_refine_patches(self._h, _ptr(packets), int(packets.numel()), int(index_base), _ptr(labels),
+                                      _ptr(clusters), int(n_clusters), int(min_pixels), _ptr(out["patches"]),
+                                      _ptr(out["sel"]), _ptr(out["centre"]), cap, _ptr(out["n"]))
+        if rc and rc != EOVERFLOW:
+            raise TpxError(rc, "tpx_refine_patches")
+        out["status"] = rc   # TPX_EOVERFLOW: only the first `capacity` patches were written
+        return out
+
+    @staticmethod
+    def tpx_refiner_params(hidden: int) -> int:
+        return int(lib().tpx_refiner_params(int(hidden)))
+
+    def tpx_refiner_forward(self, params, hidden: int, x, n: int | None = None, work=None, out=None):
+        import torch
+        n = int(x.shape[0] if n is None else n)
+        if work is None:
+            work = torch.empty(max(1, 2 * n * hidden), dtype=torch.float32, device=x.device)
+        if out is None:
+            out = torch.empty((max(1, n), 6), dtype=torch.float32, device=x.device)
+        rc = lib().tpx_refiner_forward(self._h, _ptr(params), int(hidden), _ptr(x), n, _ptr(work), _ptr(out))
+        if rc:
+            raise TpxError(rc, "tpx_refiner_forward")
+        return out
+
+    def tpx_refiner_train_step(self, params, adam_m, adam_v, grad, hidden: int, step: int, x, y, lr: float,
+                               offset_weight: float, work, loss, n: int | None = None):
+        n = int(x.shape[0] if n is None else n)
+        rc = lib().tpx_refiner_train_step(self._h, _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(grad), int(hidden),
+                                          int(step), _ptr(x), _ptr(y), n, float(lr), float(offset_weight),
+                                          _ptr(work), _ptr(loss))
+        if rc:
+            raise TpxError(rc, "tpx_refiner_train_step")
+
+    def tpx_refine_decide(self, out, clusters, sel, centre, n: int, threshold: float, hits=None):
+        import torch
+        if hits is None:
+            hits = torch.empty((max(1, n), 5), dtype=torch.float32, device=out.device)
+        rc = lib().tpx_refine_decide(self._h, _ptr(out), _ptr(clusters), _ptr(sel), _ptr(centre), int(n),
+                                     float(threshold), _ptr(hits))
+        if rc:
+            raise TpxError(rc, "tpx_refine_decide")
+        return hits
 
     def tpx_cluster(self, hits: dict, n_hits: int, is_peak: bool = True) -> dict:
         import torch

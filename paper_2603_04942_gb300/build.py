@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtpx.so")
-SOURCES = ["tpx_fused.cu", "tpx_runtime.cu", "tpx_noalloc.cu", "tpx_general.cu", "tpx_stream.cu"]
+SOURCES = ["tpx_fused.cu", "tpx_runtime.cu", "tpx_noalloc.cu", "tpx_general.cu", "tpx_stream.cu", "tpx_refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -140,6 +140,16 @@ def calibration(n_shots: int = 2000, a_ns: float = 1500.0, b: float = 5.0, c_ns:
 CALIBRATION_TOF_TICKS = 3200       # 5 us of the calibration recipe, in ticks
 
 
+def refiner(n_shots: int = 20_000, seed: int = 6, **kw) -> Params:
+    """Learned-refiner data: the small recipe's ion-like clouds (sigma 1 px,
+    peak ToT 200-1023, ToF 1-10 us, 20 particles per shot, Poisson), 30% of
+    particles with a planted partner (separation 0-4 px, ToA gap 0-20 ns,
+    amplitude ratio 0.3-1). Training and held-out sets differ by seed."""
+    return Params(n_shots=n_shots, seed=seed, poisson=True, particles_per_shot=20.0, pair_frac=0.3,
+                  pair_sep_lo=0.0, pair_sep_hi=4.0, pair_dtoa_lo_ns=0.0, pair_dtoa_hi_ns=20.0,
+                  pair_amp_lo=0.3, pair_amp_hi=1.0).replace(**kw)
+
+
 def stated_size(p: Params) -> Params:
     """Variant whose truncation (ToT >= 90) gives the 5-15 px per particle
     that the workload description quotes; the literal parameters give ~25."""
