@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-timewalk", action="store_true")
+    ap.add_argument("--no-refiner", action="store_true")
+    ap.add_argument("--refiner-only", action="store_true")
+    ap.add_argument("--refiner-shots", type=int, default=500_000, help="training shots (about 20 clusters each)")
+    ap.add_argument("--refiner-epochs", type=int, default=1)
     ap.add_argument("--batch-runs", type=int, default=4096)
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed whole calls of the batch (each ~5 s)")
@@ -359,6 +363,94 @@ def timewalk_bench(args) -> dict:
                             "c": synth.CALIBRATION_TOF_TICKS + p.timewalk_c / 1.5625, "d": 1.0}}
 
 
+def refiner_bench(args) -> dict:
+    """The learned overlap refiner: a training set of generator clusters
+    with planted pairs (seed 6), one pass of minibatch Adam, then the errors
+    on a held-out set (seed 7) against the generator's truth next to the
+    plain centroid's, and the inference throughput (patch extraction,
+    network, decision) timed with CUDA events."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    from paper_2603_04942_gb300 import refiner as R
+    ctx = tpx.Context(tpx.Config(), max_packets=1 << 20)
+    t0 = time.perf_counter()
+    train = R.make_dataset(ctx, synth.refiner(n_shots=args.refiner_shots, seed=6))
+    test = R.make_dataset(ctx, synth.refiner(n_shots=max(2000, args.refiner_shots // 25), seed=7), shuffle_seed=None)
+    data_s = time.perf_counter() - t0
+    net = R.Refiner(ctx, hidden=R.HIDDEN, seed=0)
+    t0 = time.perf_counter()
+    losses = net.train(train, epochs=args.refiner_epochs, batch=4096, lr=2e-3, lr_final=1e-4)
+    train_s = time.perf_counter() - t0
+    thr = 0.8
+    ev = R.evaluate(test, net.refine_rows(test, thr))
+    ev32 = R.evaluate(test, net.refine_rows(test, thr, fp32=True))
+    # inference on every selected cluster of the training stream: patches from
+    # the fused path's outputs, the network, the decision
+    pk = synth.Stream(synth.refiner(n_shots=args.refiner_shots, seed=6))
+    host = pk.packets()
+    pk.close()
+    d = torch.from_numpy(host.view(np.int64)).cuda()
+    del host
+    n = d.numel()
+    out = ctx.alloc_outputs(n, labels=True)
+    ctx.tpx_process(d, out)
+    ctx.tpx_sync()
+    n_cl = int(out["n_clusters"].item())
+    pt = ctx.tpx_refine_patches(d, out["labels"], out["clusters"], n_cl, R.MIN_PIXELS)
+    ns = int(pt["n"].item())
+    o6 = torch.empty((ns, 6), dtype=torch.float32, device="cuda")
+    hits = torch.empty((ns, 5), dtype=torch.float32, device="cuda")
+    net.infer(pt["patches"], ns, o6)          # packs the bf16 weights
+    for _ in range(2):
+        ctx.tpx_refiner_infer(net.packed, net.h, pt["patches"], ns, o6)
+        ctx.tpx_refine_decide(o6, out["clusters"], pt["sel"], pt["centre"], ns, thr, hits)
+    torch.cuda.synchronize()
+    reps = 5
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    tot = [0.0, 0.0, 0.0]
+    for _ in range(reps):
+        e[0].record(ctx.stream)
+        pt2 = ctx.tpx_refine_patches(d, out["labels"], out["clusters"], n_cl, R.MIN_PIXELS)   # synchronises (count)
+        e[1].record(ctx.stream)
+        ctx.tpx_refiner_infer(net.packed, net.h, pt2["patches"], ns, o6)
+        e[2].record(ctx.stream)
+        ctx.tpx_refine_decide(o6, out["clusters"], pt2["sel"], pt2["centre"], ns, thr, hits)
+        e[3].record(ctx.stream)
+        torch.cuda.synchronize()
+        for k in range(3):
+            tot[k] += e[k].elapsed_time(e[k + 1]) / reps
+        del pt2
+    # the fp32 network on the same patches, for comparison
+    work = torch.empty(2 * ns * R.HIDDEN, dtype=torch.float32, device="cuda")
+    ctx.tpx_refiner_forward(net.params, net.h, pt["patches"], ns, work, o6)
+    e[0].record(ctx.stream)
+    for _ in range(reps):
+        ctx.tpx_refiner_forward(net.params, net.h, pt["patches"], ns, work, o6)
+    e[1].record(ctx.stream)
+    torch.cuda.synchronize()
+    fp32_ms = e[0].elapsed_time(e[1]) / reps
+    del work
+    ctx.close()
+    ms = sum(tot)
+    flops = 2 * ns * (162 * net.h + net.h * net.h + net.h * 6)
+    return {"workload": f"{args.refiner_shots:,} shots x Poisson(20) ion-like particles, 30% with a planted "
+                        "partner (separation 0-4 px, ToA gap 0-20 ns, amplitude ratio 0.3-1), seed 6; "
+                        "held-out set seed 7",
+            "network": f"162-{net.h}-{net.h}-6 perceptron, {net.n_params:,} parameters; trained in fp32, "
+                       "inferred with bf16 operands",
+            "train_clusters": int(train.x.shape[0]), "epochs": args.refiner_epochs, "data_s": round(data_s, 1),
+            "train_s": round(train_s, 2), "train_clusters_per_s": args.refiner_epochs * train.x.shape[0] / train_s,
+            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
+            "threshold": thr, "eval": ev,
+            "eval_fp32": {k: ev32[k] for k in ("pair_recall", "single_split", "pair_err_refined", "fallback")},
+            "infer": {"clusters": ns, "patches_ms": tot[0], "network_ms": tot[1], "decide_ms": tot[2],
+                      "clusters_per_s": ns / (ms / 1e3), "network": "bf16 tensor cores (mma.sync), fp32 sums",
+                      "network_tflops": flops / (tot[1] / 1e3) / 1e12,
+                      "fp32_network_ms": fp32_ms, "fp32_network_tflops": flops / (fp32_ms / 1e3) / 1e12}}
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, one bounded sample of
     the workload per step (a different shot range each step)."""
@@ -391,12 +483,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.stream_only or args.batch_only:
+    if args.stream_only or args.batch_only or args.refiner_only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2603_04942_gb300 import build as tbuild
         tbuild.build()
-        print(json.dumps(stream_bench(args) if args.stream_only else batch_bench(args)), flush=True)
+        f = stream_bench if args.stream_only else batch_bench if args.batch_only else refiner_bench
+        print(json.dumps(f(args)), flush=True)
         return 0
     import torch
     import torch.distributed as dist
@@ -521,6 +614,13 @@ def main():
     timewalk = None
     if rank == 0 and not args.no_timewalk:
         timewalk = timewalk_bench(args)
+    refiner = None
+    if rank == 0 and not args.no_refiner:
+        torch.cuda.empty_cache()
+        refiner = refiner_bench(args)
+        # the main path's cluster rate: the budget the refiner's inference is held to
+        refiner["main_path_clusters_per_s"] = value * n_cl / max(1, hits) / world
+        refiner["infer"]["vs_main_path"] = refiner["infer"]["clusters_per_s"] / refiner["main_path_clusters_per_s"]
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -536,7 +636,8 @@ def main():
                                tuning["tile_geometry"], "sampling"),
                            "tile_choice": "autotuned in warm-up" if args.tile == "default" else "fixed by --tile",
                            "generation_s": round(t_gen, 1)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk, "clocks": clk,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk,
+                "refiner": refiner, "clocks": clk,
                 "gpu_launches": 2 * args.steps - 1,   # fused kernels + status carries between unsynchronised calls
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "counters": counters}

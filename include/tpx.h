@@ -320,6 +320,19 @@ int tpx_refiner_train_step(tpx_ctx *ctx, float *d_params, float *d_adam_m, float
                            int32_t hidden, int64_t step, const float *d_x, const float *d_y, int64_t n, float lr,
                            float offset_weight, float *d_work, float *d_loss);
 
+/* Inference on the tensor cores (hidden = 64, 128 or 160, else
+   TPX_EUNSUPPORTED): tpx_refiner_pack rounds the fp32 parameters to a bf16
+   copy (d_packed, tpx_refiner_packed_bytes(hidden) bytes, 16-byte aligned;
+   0 bytes for an unsupported width); tpx_refiner_infer runs all three
+   layers in one kernel: inputs and weights in bf16 (the patch values are
+   exact in bf16), fp32 accumulation and biases, each hidden activation
+   rounded to bf16 after its ReLU.  d_x 8-byte aligned [n x 162], d_out
+   [n x 6].  Asynchronous. */
+int64_t tpx_refiner_packed_bytes(int32_t hidden);
+int tpx_refiner_pack(tpx_ctx *ctx, const float *d_params, int32_t hidden, void *d_packed);
+int tpx_refiner_infer(tpx_ctx *ctx, const void *d_packed, int32_t hidden, const float *d_x, int64_t n,
+                      float *d_out);
+
 /* Refined hits from the forward outputs: per patch d_hits[5] = (k, x1, y1,
    x2, y2): k = 2 when the probability of two particles reaches `threshold`
    (positions from the offsets); else (x1, y1) is the cluster's plain

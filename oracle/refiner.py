@@ -23,6 +23,9 @@ path feeds the network):
             plus w * 1/2 * sum of squared errors of the offsets of the
             particles that exist (the first always, the second in pairs).
   Adam    : Kingma and Ba (2015), beta1 0.9, beta2 0.999, eps 1e-8.
+  infer   : the same network at the inference precision: inputs and
+            weights rounded to bfloat16, each hidden activation rounded to
+            bfloat16 after its ReLU, sums and biases wider.
   decide  : two particles at the network's positions when that count's
             probability reaches the threshold; else the plain centroid
             (Sec. V.C), flagged 1 when the probability of one particle
@@ -30,8 +33,10 @@ path feeds the network):
 
 Parity pins (tests/test_refiner_pins.py): a hand-built patch, the closed
 forms of the cross-entropy and of Adam's first step, a hand-evaluated
-one-unit network, positive homogeneity of the bias-free ReLU network, and
-the backward pass against central finite differences of the loss.
+one-unit network, positive homogeneity of the bias-free ReLU network, the
+backward pass against central finite differences of the loss, and the
+inference precision equal to the plain network on bf16-exact values and
+rounding a hand-made activation tie to even.
 """
 from __future__ import annotations
 
@@ -118,6 +123,25 @@ def forward(p: np.ndarray, h: int, x: np.ndarray, keep: bool = False):
     a2 = np.maximum(a1 @ w2 + b2, 0.0)
     out = a2 @ w3 + b3
     return (out, a1, a2) if keep else out
+
+
+def bf16_array(a) -> np.ndarray:
+    """Elementwise bf16 rounding (as `bf16`) of a float32 array."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def forward_bf16(p: np.ndarray, h: int, x: np.ndarray) -> np.ndarray:
+    """The inference precision: inputs and weights rounded to bf16, sums
+    exact (float64 here), biases in float32, each hidden activation rounded
+    to bf16 after its ReLU."""
+    w1, b1, w2, b2, w3, b3 = unpack(np.asarray(p, np.float32), h)
+    r = lambda a: bf16_array(a).astype(np.float64)              # noqa: E731
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)  # noqa: E731
+    a1 = r(np.maximum(r(x) @ r(w1) + f(b1), 0.0).astype(np.float32))
+    a2 = r(np.maximum(a1 @ r(w2) + f(b2), 0.0).astype(np.float32))
+    return a2 @ r(w3) + f(b3)
 
 
 def loss(p: np.ndarray, h: int, x: np.ndarray, y: np.ndarray, w_off: float) -> float:

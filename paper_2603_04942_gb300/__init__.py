@@ -40,7 +40,8 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
                     "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_refine_patches", "tpx_refiner_params",
-                    "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
+                    "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_strerror", "tpx_version")
 
@@ -146,7 +147,12 @@ def load(path: str | None = None):
         L.tpx_refiner_train_step.argtypes = [vp, vp, vp, vp, vp, i32, i64, vp, vp, i64, ctypes.c_float,
                                              ctypes.c_float, vp, vp]
         L.tpx_refine_decide.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.c_float, vp]
-        for f in ("tpx_refine_patches", "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide"):
+        L.tpx_refiner_packed_bytes.argtypes = [i32]
+        L.tpx_refiner_packed_bytes.restype = i64
+        L.tpx_refiner_pack.argtypes = [vp, vp, i32, vp]
+        L.tpx_refiner_infer.argtypes = [vp, vp, i32, vp, i64, vp]
+        for f in ("tpx_refine_patches", "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
+                  "tpx_refiner_pack", "tpx_refiner_infer"):
             getattr(L, f).restype = i32
         L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
@@ -443,6 +449,29 @@ class Context:
                                           _ptr(work), _ptr(loss))
         if rc:
             raise TpxError(rc, "tpx_refiner_train_step")
+
+    def tpx_refiner_pack(self, params, hidden: int, packed=None):
+        """The bf16 inference copy of fp32 parameters (device uint8 tensor)."""
+        import torch
+        nb = int(lib().tpx_refiner_packed_bytes(int(hidden)))
+        if nb <= 0:
+            raise TpxError(EUNSUPPORTED, "tpx_refiner_packed_bytes")
+        if packed is None:
+            packed = torch.empty(nb, dtype=torch.uint8, device=params.device)
+        rc = lib().tpx_refiner_pack(self._h, _ptr(params), int(hidden), _ptr(packed))
+        if rc:
+            raise TpxError(rc, "tpx_refiner_pack")
+        return packed
+
+    def tpx_refiner_infer(self, packed, hidden: int, x, n: int | None = None, out=None):
+        import torch
+        n = int(x.shape[0] if n is None else n)
+        if out is None:
+            out = torch.empty((max(1, n), 6), dtype=torch.float32, device=x.device)
+        rc = lib().tpx_refiner_infer(self._h, _ptr(packed), int(hidden), _ptr(x), n, _ptr(out))
+        if rc:
+            raise TpxError(rc, "tpx_refiner_infer")
+        return out
 
     def tpx_refine_decide(self, out, clusters, sel, centre, n: int, threshold: float, hits=None):
         import torch

@@ -209,7 +209,7 @@ void gemm(cudaStream_t s, const float *A, long long sam, long long sak, const fl
 struct Layout {
     int h;
     long long w1, b1, w2, b2, w3, b3, total;
-    explicit Layout(int hidden) : h(hidden) {
+    __host__ __device__ explicit Layout(int hidden) : h(hidden) {
         w1 = 0; b1 = w1 + (long long)NIN * h; w2 = b1 + h; b2 = w2 + (long long)h * h; w3 = b2 + h;
         b3 = w3 + (long long)h * NOUT; total = b3 + NOUT;
     }
@@ -288,6 +288,207 @@ __global__ void k_decide(const float *out, const tpx_record *cl, const long long
             h[0] = -margin >= lt ? 1.f : 0.f; h[1] = (float)r.x; h[2] = (float)r.y; h[3] = 0.f; h[4] = 0.f;
         }
     }
+}
+
+// ---------------------------------------------------------------- bf16 inference
+// The whole network in one persistent kernel on the tensor cores
+// (mma.sync m16n8k16, bf16 operands, fp32 accumulation). Each warp owns 16
+// patches and carries them through the three layers: the fp32 accumulator
+// fragment of one layer, after bias and ReLU, is exactly the bf16 A-operand
+// fragment of the next (row g = lane / 4 and column pair 2 (lane % 4) of
+// n-tile j are row g, k pair of k-step j / 2), so activations never leave
+// registers. The weights, transposed to [n][k] bf16 by tpx_refiner_pack, sit
+// in shared memory for the kernel's lifetime; patches stream from global
+// memory as fp32 pairs (8-byte loads; a row's 4 lanes read one 32-byte
+// sector) and are rounded to bf16 (exact for the patch precisions).
+constexpr int K1P = 176;                       // 162 inputs padded to 11 k-steps
+constexpr int S1 = K1P + 8;                    // smem row stride of W1t (92 words: conflict-free)
+template <int H> struct MlpGeo {
+    static constexpr int S2 = H + 8;           // smem row stride of W2t / W3t
+    static constexpr int NT = H / 8;           // n-tiles of a hidden layer
+    static constexpr int KS = H / 16;          // k-steps over a hidden layer
+    static constexpr size_t w1 = 0, w2 = w1 + (size_t)H * K1P, w3 = w2 + (size_t)H * H, wend = w3 + (size_t)8 * H;
+    static constexpr size_t packed_bytes = ((wend * 2 + 15) / 16) * 16 + (size_t)(2 * H + 8) * 4;
+    static constexpr size_t smem = (size_t)H * S1 * 2 + (size_t)H * S2 * 2 + (size_t)8 * S2 * 2 + (size_t)(2 * H + 8) * 4;
+};
+inline size_t packed_bias_off(size_t wend) { return ((wend * 2 + 15) / 16) * 16; }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (lower k) in the low half
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// fp32 parameters -> W1t [H][176], W2t [H][H], W3t [8][H] bf16 (zero padded),
+// then b1, b2, b3 (padded to 8) fp32
+template <int H>
+__global__ void k_pack(const float *P, uint16_t *wt, float *bias) {
+    using G = MlpGeo<H>;
+    const Layout L(H);
+    const long long total = (long long)G::wend + 2 * H + 8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        if (i >= (long long)G::wend) {
+            const int b = (int)(i - G::wend);
+            bias[b] = b < H ? P[L.b1 + b] : b < 2 * H ? P[L.b2 + b - H] : (b - 2 * H < NOUT ? P[L.b3 + b - 2 * H] : 0.f);
+            continue;
+        }
+        float v = 0.f;
+        if (i < (long long)G::w2) {
+            const int j = (int)(i / K1P), k = (int)(i % K1P);
+            if (k < NIN) v = P[L.w1 + (long long)k * H + j];
+        } else if (i < (long long)G::w3) {
+            const long long r = i - G::w2;
+            const int j = (int)(r / H), k = (int)(r % H);
+            v = P[L.w2 + (long long)k * H + j];
+        } else {
+            const long long r = i - G::w3;
+            const int j = (int)(r / H), k = (int)(r % H);
+            if (j < NOUT) v = P[L.w3 + (long long)k * NOUT + j];
+        }
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        wt[i] = *reinterpret_cast<uint16_t *>(&b);
+    }
+}
+
+// hidden layer epilogue: bias was the accumulator's start; ReLU, round to
+// bf16 and regroup n-tile pairs into next-layer A fragments
+template <int NT>
+__device__ __forceinline__ void to_frags(const float (&acc)[NT][4], uint32_t (&a)[NT / 2][4]) {
+#pragma unroll
+    for (int s = 0; s < NT / 2; ++s) {
+        a[s][0] = pack_bf16(fmaxf(acc[2 * s][0], 0.f), fmaxf(acc[2 * s][1], 0.f));
+        a[s][1] = pack_bf16(fmaxf(acc[2 * s][2], 0.f), fmaxf(acc[2 * s][3], 0.f));
+        a[s][2] = pack_bf16(fmaxf(acc[2 * s + 1][0], 0.f), fmaxf(acc[2 * s + 1][1], 0.f));
+        a[s][3] = pack_bf16(fmaxf(acc[2 * s + 1][2], 0.f), fmaxf(acc[2 * s + 1][3], 0.f));
+    }
+}
+
+template <int H>
+__global__ void __launch_bounds__(256, 1) k_mlp_bf16(const float *__restrict__ x, long long n,
+                                                      const uint16_t *__restrict__ wt, const float *__restrict__ bias,
+                                                      float *__restrict__ out) {
+    using G = MlpGeo<H>;
+    constexpr int NT = G::NT, S2 = G::S2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t *W1s = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *W2s = W1s + H * S1;
+    uint16_t *W3s = W2s + H * S2;
+    float *Bs = reinterpret_cast<float *>(W3s + 8 * S2);
+    // weights into shared memory, 16 bytes at a time (rows are 16-byte multiples)
+    for (int i = threadIdx.x; i < H * (K1P / 8); i += blockDim.x) {
+        const int r = i / (K1P / 8), c = i % (K1P / 8);
+        *reinterpret_cast<uint4 *>(W1s + r * S1 + c * 8) = *reinterpret_cast<const uint4 *>(wt + G::w1 + (size_t)r * K1P + c * 8);
+    }
+    for (int i = threadIdx.x; i < H * (H / 8); i += blockDim.x) {
+        const int r = i / (H / 8), c = i % (H / 8);
+        *reinterpret_cast<uint4 *>(W2s + r * S2 + c * 8) = *reinterpret_cast<const uint4 *>(wt + G::w2 + (size_t)r * H + c * 8);
+    }
+    for (int i = threadIdx.x; i < 8 * (H / 8); i += blockDim.x) {
+        const int r = i / (H / 8), c = i % (H / 8);
+        *reinterpret_cast<uint4 *>(W3s + r * S2 + c * 8) = *reinterpret_cast<const uint4 *>(wt + G::w3 + (size_t)r * H + c * 8);
+    }
+    for (int i = threadIdx.x; i < 2 * H + 8; i += blockDim.x) Bs[i] = bias[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const long long n_tiles = (n + 127) / 128;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const long long r0 = tile * 128 + warp * 16 + g, r1 = r0 + 8;
+        const float *x0 = x + r0 * NIN, *x1 = x + r1 * NIN;
+        const bool v0 = r0 < n, v1 = r1 < n;
+        // layer 1: acc = b1 + x W1
+        float acc[NT][4];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            acc[j][0] = acc[j][2] = Bs[8 * j + 2 * t];
+            acc[j][1] = acc[j][3] = Bs[8 * j + 2 * t + 1];
+        }
+        float2 p[4], q[4];
+        auto load = [&](int s, float2 (&f)[4]) {
+            const int k0 = 16 * s + 2 * t, k1 = k0 + 8;
+            const float2 z = make_float2(0.f, 0.f);
+            f[0] = v0 && k0 < NIN ? *reinterpret_cast<const float2 *>(x0 + k0) : z;
+            f[1] = v1 && k0 < NIN ? *reinterpret_cast<const float2 *>(x1 + k0) : z;
+            f[2] = v0 && k1 < NIN ? *reinterpret_cast<const float2 *>(x0 + k1) : z;
+            f[3] = v1 && k1 < NIN ? *reinterpret_cast<const float2 *>(x1 + k1) : z;
+        };
+        load(0, p);
+#pragma unroll
+        for (int s = 0; s < K1P / 16; ++s) {
+            if (s + 1 < K1P / 16) load(s + 1, q);
+            const uint32_t a[4] = {pack_bf16(p[0].x, p[0].y), pack_bf16(p[1].x, p[1].y), pack_bf16(p[2].x, p[2].y),
+                                   pack_bf16(p[3].x, p[3].y)};
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const uint16_t *w = W1s + (8 * j + g) * S1 + 16 * s + 2 * t;
+                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] = q[u];
+        }
+        uint32_t af[NT / 2][4];
+        to_frags<NT>(acc, af);
+        // layer 2
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            acc[j][0] = acc[j][2] = Bs[H + 8 * j + 2 * t];
+            acc[j][1] = acc[j][3] = Bs[H + 8 * j + 2 * t + 1];
+        }
+#pragma unroll
+        for (int s = 0; s < G::KS; ++s)
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const uint16_t *w = W2s + (8 * j + g) * S2 + 16 * s + 2 * t;
+                mma_bf16(acc[j], af[s], *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
+            }
+        to_frags<NT>(acc, af);
+        // layer 3 (6 outputs in one n-tile of 8)
+        float o[4];
+        o[0] = o[2] = Bs[2 * H + 2 * t];
+        o[1] = o[3] = Bs[2 * H + 2 * t + 1];
+#pragma unroll
+        for (int s = 0; s < G::KS; ++s) {
+            const uint16_t *w = W3s + g * S2 + 16 * s + 2 * t;
+            mma_bf16(o, af[s], *reinterpret_cast<const uint32_t *>(w), *reinterpret_cast<const uint32_t *>(w + 8));
+        }
+        if (t < 3) {
+            if (v0) *reinterpret_cast<float2 *>(out + r0 * NOUT + 2 * t) = make_float2(o[0], o[1]);
+            if (v1) *reinterpret_cast<float2 *>(out + r1 * NOUT + 2 * t) = make_float2(o[2], o[3]);
+        }
+    }
+}
+
+template <int H>
+int infer_h(tpx_ctx *c, const void *packed, const float *x, long long n, float *out) {
+    using G = MlpGeo<H>;
+    static bool attr = false;
+    if (!attr) {
+        if (ck(cudaFuncSetAttribute(k_mlp_bf16<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem)))
+            return TPX_ECUDA;
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    if (ck(cudaGetDevice(&dev)) || ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return TPX_ECUDA;
+    const long long tiles = (n + 127) / 128;
+    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+    const uint16_t *wt = static_cast<const uint16_t *>(packed);
+    const float *bias = reinterpret_cast<const float *>(static_cast<const char *>(packed) + packed_bias_off(G::wend));
+    k_mlp_bf16<H><<<grid, 256, G::smem, c->stream>>>(x, n, wt, bias, out);
+    return ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
+}
+template <int H>
+int pack_h(tpx_ctx *c, const float *P, void *packed) {
+    using G = MlpGeo<H>;
+    uint16_t *wt = static_cast<uint16_t *>(packed);
+    float *bias = reinterpret_cast<float *>(static_cast<char *>(packed) + packed_bias_off(G::wend));
+    k_pack<H><<<grid_for((long long)G::wend + 2 * H + 8), 256, 0, c->stream>>>(P, wt, bias);
+    return ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
 }
 
 }  // namespace tpxr
@@ -397,6 +598,39 @@ int tpx_refiner_train_step(tpx_ctx *c, float *d_params, float *d_adam_m, float *
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_adam<<<grid_for(L.total), 256, 0, s>>>(d_params, d_grad, d_adam_m, d_adam_v, L.total, lr, b1, b2, c1, c2, 1e-8f);
     return ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
+}
+
+int64_t tpx_refiner_packed_bytes(int32_t hidden) {
+    switch (hidden) {
+        case 64: return (int64_t)MlpGeo<64>::packed_bytes;
+        case 128: return (int64_t)MlpGeo<128>::packed_bytes;
+        case 160: return (int64_t)MlpGeo<160>::packed_bytes;
+        default: return 0;
+    }
+}
+
+int tpx_refiner_pack(tpx_ctx *c, const float *d_params, int32_t hidden, void *d_packed) {
+    if (!c || !d_params || !d_packed || (reinterpret_cast<uintptr_t>(d_packed) & 15)) return TPX_EINVAL;
+    switch (hidden) {
+        case 64: return pack_h<64>(c, d_params, d_packed);
+        case 128: return pack_h<128>(c, d_params, d_packed);
+        case 160: return pack_h<160>(c, d_params, d_packed);
+        default: return TPX_EUNSUPPORTED;
+    }
+}
+
+int tpx_refiner_infer(tpx_ctx *c, const void *d_packed, int32_t hidden, const float *d_x, int64_t n, float *d_out) {
+    if (!c || n < 0 || (n > 0 && (!d_packed || !d_x || !d_out))) return TPX_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_packed) & 15) || (reinterpret_cast<uintptr_t>(d_x) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_out) & 7))
+        return TPX_EINVAL;
+    if (hidden != 64 && hidden != 128 && hidden != 160) return TPX_EUNSUPPORTED;
+    if (n == 0) return TPX_OK;
+    switch (hidden) {
+        case 64: return infer_h<64>(c, d_packed, d_x, n, d_out);
+        case 128: return infer_h<128>(c, d_packed, d_x, n, d_out);
+        default: return infer_h<160>(c, d_packed, d_x, n, d_out);
+    }
 }
 
 int tpx_refine_decide(tpx_ctx *c, const float *d_out, const tpx_record *d_clusters, const int64_t *d_sel,

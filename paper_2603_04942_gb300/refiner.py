@@ -16,7 +16,9 @@ centroid stands.
              rows (count, offsets of the brighter particle, then of the
              other, in pixels from the patch centre).
   training : tpx_refiner_train_step per minibatch (fp32 GEMMs, Adam).
-  inference: tpx_refiner_forward, then tpx_refine_decide.
+  inference: tpx_refiner_infer (all layers in one tensor-core kernel, bf16
+             operands) or tpx_refiner_forward (fp32), then
+             tpx_refine_decide.
 
 Every arithmetic step runs in the library's kernels; this module only
 prepares targets on the host and moves buffers.
@@ -181,21 +183,30 @@ class Refiner:
         return losses.cpu().numpy()
 
     def forward(self, x, n: int | None = None):
+        """The fp32 network (the training precision)."""
         return self.ctx.tpx_refiner_forward(self.params, self.h, x, n)
 
-    def refine(self, patches: dict, clusters_dev, n: int, threshold: float = 0.8):
+    def infer(self, x, n: int | None = None, out=None):
+        """The network on the tensor cores (bf16 operands, fp32 sums); the
+        bf16 copy of the parameters is refreshed after training steps."""
+        if getattr(self, "_packed_step", None) != self.step:
+            self.packed = self.ctx.tpx_refiner_pack(self.params, self.h, getattr(self, "packed", None))
+            self._packed_step = self.step
+        return self.ctx.tpx_refiner_infer(self.packed, self.h, x, n, out)
+
+    def refine(self, patches: dict, clusters_dev, n: int, threshold: float = 0.8, fp32: bool = False):
         """Refined hits (device [n x 5]) of the first n patches of a
         tpx_refine_patches call."""
-        out = self.forward(patches["patches"], n)
+        out = self.forward(patches["patches"], n) if fp32 else self.infer(patches["patches"], n)
         return self.ctx.tpx_refine_decide(out, clusters_dev, patches["sel"], patches["centre"], n, threshold)
 
-    def refine_rows(self, ds: Dataset, threshold: float = 0.8) -> np.ndarray:
+    def refine_rows(self, ds: Dataset, threshold: float = 0.8, fp32: bool = False) -> np.ndarray:
         """Refined hits (host [n x 5]) of the dataset's rows."""
         import torch
         rows = torch.from_numpy(ds.rows).cuda()
         sel = ds.patches["sel"][: ds.n_selected].index_select(0, rows).contiguous()
         centre = ds.patches["centre"][: ds.n_selected].index_select(0, rows).contiguous()
-        out = self.forward(ds.x)
+        out = self.forward(ds.x) if fp32 else self.infer(ds.x)
         n = ds.x.shape[0]
         return self.ctx.tpx_refine_decide(out, ds.clusters_dev, sel, centre, n, threshold)[:n].cpu().numpy()
 

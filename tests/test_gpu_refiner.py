@@ -115,6 +115,31 @@ def test_forward_matches_oracle(data, h, n):
     assert np.abs(g - o).max() <= 1e-4 * max(1.0, np.abs(o).max())
 
 
+@pytest.mark.parametrize("h,n", [(160, 4099), (128, 129), (64, 1), (160, 20_000)])
+def test_bf16_inference_matches_oracle(data, h, n):
+    """The tensor-core kernel against the oracle's inference precision.
+    Sums are fp32 on the GPU and exact in the oracle, so a hidden activation
+    can round to the neighbouring bf16 value (2^-8 relative) in a few rows:
+    nearly all rows agree to 1e-4 of the output scale, every row to 3e-2."""
+    import torch
+    op = data[1][0]
+    x = np.concatenate([op, np.random.default_rng(h).random((max(0, n - op.shape[0]), 162), np.float32)])[:n]
+    p = _params(h, n + 1)
+    ctx = tpx.Context(tpx.Config(), max_packets=16)
+    try:
+        packed = ctx.tpx_refiner_pack(torch.from_numpy(p).cuda(), h)
+        g = ctx.tpx_refiner_infer(packed, h, torch.from_numpy(x).cuda())[:n].cpu().numpy().astype(np.float64)
+        with pytest.raises(tpx.TpxError):
+            ctx.tpx_refiner_pack(torch.from_numpy(p).cuda(), 100)
+    finally:
+        ctx.close()
+    o = orf.forward_bf16(p, h, x)
+    scale = max(1.0, np.abs(o).max())
+    row_err = np.abs(g - o).max(axis=1)
+    assert np.mean(row_err <= 1e-4 * scale) >= 0.95
+    assert row_err.max() <= 3e-2 * scale
+
+
 def _targets(n, seed):
     rng = np.random.default_rng(seed)
     y = np.zeros((n, 5), np.float32)
@@ -198,6 +223,9 @@ def test_training_splits_merged_pairs():
         losses = net.train(train, epochs=4, batch=1024, lr=2e-3, lr_final=2e-4)
         assert losses[-20:].mean() < 0.5 * losses[:5].mean()
         hits = net.refine_rows(test, 0.8)
+        # the fp32 network decides nearly every cluster the same way
+        h32 = net.refine_rows(test, 0.8, fp32=True)
+        assert np.mean(h32[:, 0] == hits[:, 0]) > 0.99
         ev = R.evaluate(test, hits)
         assert ev["pairs"] > 2000 and ev["singles"] > 4000
         assert ev["pair_recall"] > 0.6 and ev["single_split"] < 0.05

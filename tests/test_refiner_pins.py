@@ -160,3 +160,40 @@ def test_oracle_training_reduces_the_loss():
     for step in range(1, 301):
         p, m, v = orf.adam(p, m, v, orf.grad(p, h, x, y, 1.0), step, 0.01)
     assert orf.loss(p, h, x, y, 1.0) < 0.3 * l0
+
+
+def test_bf16_inference_precision():
+    """On inputs, weights and activations that bf16 holds exactly, the
+    inference precision is the plain network; a hidden activation of
+    1 + 2^-8 (a bf16 tie) becomes 1, and 1 + 3 * 2^-8 becomes 1 + 2^-6."""
+    rng = np.random.default_rng(4)
+    h = 4
+    L = orf.layout(h)
+    p = np.zeros(L["total"])
+    # W1, b1, W3, b3: multiples of 1/8 in [-1/2, 1/2]; W2: half a cyclic shift
+    for k in ("w1", "b1", "w3", "b3"):
+        o, n = L[k]
+        p[o: o + n] = rng.integers(-4, 5, n) / 8.0
+    w2 = np.zeros((h, h))
+    w2[np.arange(h), (np.arange(h) + 1) % h] = 0.5
+    p[L["w2"][0]: L["w2"][0] + h * h] = w2.ravel()
+    p[L["b2"][0]: L["b2"][0] + h] = rng.integers(0, 5, h) / 8.0
+    # two inputs of 1/8 .. 1 per row: a1 < 2 in steps of 1/64, a2 < 1.5 in
+    # steps of 1/128 -- at most 8 significant bits, exact in bf16
+    x = np.zeros((6, 162))
+    for r in range(6):
+        x[r, rng.choice(162, 2, replace=False)] = rng.integers(1, 9, 2) / 8.0
+    assert np.array_equal(orf.forward_bf16(p, h, x), orf.forward(p, h, x))
+    assert np.array_equal(orf.bf16_array(np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8], np.float32)),
+                          np.array([1.0, 1 + 2 ** -6], np.float32))
+    h = 1
+    L = orf.layout(h)
+    p = np.zeros(L["total"])
+    p[L["w1"][0]] = 1.0
+    p[L["b1"][0]] = 2.0 ** -8                # a1 = 1 + 2^-8 -> 1 in bf16
+    p[L["w2"][0]] = 1.0
+    p[L["w3"][0]: L["w3"][0] + 6] = [1, 0, 0, 0, 0, 0]
+    x = np.zeros((1, 162))
+    x[0, 0] = 1.0
+    assert orf.forward_bf16(p, h, x)[0, 0] == 1.0
+    assert orf.forward(p, h, x)[0, 0] == 1.0 + 2.0 ** -8
