@@ -386,6 +386,17 @@ def refiner_bench(args) -> dict:
     thr = 0.8
     ev = R.evaluate(test, net.refine_rows(test, thr))
     ev32 = R.evaluate(test, net.refine_rows(test, thr, fp32=True))
+    # resolving power as the paper's Fig. 6 measures it: pairwise distances of
+    # the hits of each shot, for the generator's particles, the plain
+    # centroids and the refined hits
+    h_all = net.refine(test.patches, test.clusters_dev, test.n_selected, thr)[: test.n_selected].cpu().numpy()
+    tr = test.truth
+    bins = 0.25
+    hist = {"bin_px": bins,
+            "truth": R.pair_distance_histogram(tr["cx"], tr["cy"], tr["shot"], 4.0, bins).tolist(),
+            "centroid": R.pair_distance_histogram(test.clusters["x"], test.clusters["y"], test.clusters["shot"],
+                                                  4.0, bins).tolist(),
+            "refined": R.pair_distance_histogram(*R.hit_list(test, h_all), 4.0, bins).tolist()}
     # inference on every selected cluster of the training stream: patches from
     # the fused path's outputs, the network, the decision
     pk = synth.Stream(synth.refiner(n_shots=args.refiner_shots, seed=6))
@@ -444,6 +455,7 @@ def refiner_bench(args) -> dict:
             "train_s": round(train_s, 2), "train_clusters_per_s": args.refiner_epochs * train.x.shape[0] / train_s,
             "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-10:].mean()),
             "threshold": thr, "eval": ev,
+            "pair_distance_histogram": hist,
             "eval_fp32": {k: ev32[k] for k in ("pair_recall", "single_split", "pair_err_refined", "fallback")},
             "infer": {"clusters": ns, "patches_ms": tot[0], "network_ms": tot[1], "decide_ms": tot[2],
                       "clusters_per_s": ns / (ms / 1e3), "network": "bf16 tensor cores (mma.sync), fp32 sums",

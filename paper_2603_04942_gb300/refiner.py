@@ -54,6 +54,8 @@ class Dataset:
     clusters: np.ndarray   # host copy of all records of the call
     clusters_dev: object   # the records on the device (uint8 tensor)
     n_selected: int        # clusters with more than MIN_PIXELS pixels
+    sel: np.ndarray        # [n_selected] record index of each patch (host)
+    truth: dict            # the generator's particles (shot relative to the stream, cx, cy)
 
 
 def _truth_match(cl: np.ndarray, truth: dict, sel: np.ndarray, centre: np.ndarray, t_start: int,
@@ -133,7 +135,8 @@ def make_dataset(ctx: Context, p, min_pixels: int = MIN_PIXELS, shuffle_seed: in
     c = cl[sel[rows]]
     return Dataset(x=x, y=torch.from_numpy(y).cuda(), count=count[rows], pos=pos[rows],
                    centroid=np.stack([c["x"], c["y"]], axis=1), sep=sep[rows], rows=rows, patches=pt,
-                   clusters=cl, clusters_dev=out["clusters"], n_selected=n_sel)
+                   clusters=cl, clusters_dev=out["clusters"], n_selected=n_sel, sel=sel,
+                   truth=dict(shot=truth["shot"] - p.shot_begin, cx=truth["cx"], cy=truth["cy"]))
 
 
 class Refiner:
@@ -259,3 +262,29 @@ def evaluate(ds: Dataset, hits: np.ndarray) -> dict:
         rp.append(dict(sep=[lo, min(hi, 4)], pairs=int(m.sum()), resolved_refined=float(np.mean(own))))
     res["resolving"] = rp
     return res
+
+
+def hit_list(ds: Dataset, hits_selected: np.ndarray):
+    """All hits of the dataset's stream (x, y, shot): every cluster's plain
+    centroid, except that a selected cluster reported as two particles
+    (rows of a refine() call over all selected patches) gives its two
+    positions."""
+    cl = ds.clusters
+    two = np.zeros(cl.size, bool)
+    k = hits_selected[:, 0].astype(int)
+    two[ds.sel[k == 2]] = True
+    h2 = hits_selected[k == 2]
+    x = np.concatenate([cl["x"][~two], h2[:, 1], h2[:, 3]])
+    y = np.concatenate([cl["y"][~two], h2[:, 2], h2[:, 4]])
+    shot = np.concatenate([cl["shot"][~two], np.repeat(cl["shot"][ds.sel[k == 2]], 2)])
+    return x, y, shot
+
+
+def pair_distance_histogram(x, y, shot, r_max: float = 4.0, bin_px: float = 0.25) -> np.ndarray:
+    """Counts of hit pairs of the same shot by distance, in bins of `bin_px`
+    up to `r_max` (the multi-hit measure of the paper's Fig. 6)."""
+    from scipy.spatial import cKDTree
+    pts = np.stack([np.asarray(x, float), np.asarray(y, float), np.asarray(shot, float) * 1e4], axis=1)
+    pairs = cKDTree(pts).query_pairs(r_max, output_type="ndarray")
+    d = np.hypot(pts[pairs[:, 0], 0] - pts[pairs[:, 1], 0], pts[pairs[:, 0], 1] - pts[pairs[:, 1], 1])
+    return np.histogram(d, bins=np.arange(0.0, r_max + 1e-9, bin_px))[0]

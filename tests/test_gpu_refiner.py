@@ -235,5 +235,12 @@ def test_training_splits_merged_pairs():
         n = test.n_selected
         h = net.refine(test.patches, test.clusters_dev, n, 0.8)[:n].cpu().numpy()
         assert np.array_equal(h[test.rows], hits)
+        # Fig. 6 measure: below 2 px the refined hits recover pairs the
+        # centroids merge (the truth has them)
+        tr = test.truth
+        ht = R.pair_distance_histogram(tr["cx"], tr["cy"], tr["shot"], 2.0, 0.5)
+        hc = R.pair_distance_histogram(test.clusters["x"], test.clusters["y"], test.clusters["shot"], 2.0, 0.5)
+        hr = R.pair_distance_histogram(*R.hit_list(test, h), 2.0, 0.5)
+        assert hc[1:].sum() < 0.2 * ht[1:].sum() and hr[1:].sum() > 0.6 * ht[1:].sum()
     finally:
         ctx.close()
