@@ -46,6 +46,22 @@ struct tpx_ctx {
     int64_t *st_trig;
     int64_t st_trig_cap;
     int64_t *st_counts;       // [2]: n_clusters, n_trig
+    // tpx_process_host on large inputs: pieces cut at trigger packets, their
+    // copies in and out overlapping the fused kernel of the neighbouring pieces
+    struct Pipe {
+        static constexpr int kMax = 16;
+        cudaStream_t s_in, s_out;
+        cudaEvent_t ev_in[kMax], ev_done[kMax], ev_out[kMax];
+        struct Slot { int64_t counts[2]; tpxk::Ctl ctl; } *h_slot;   // pinned, [kMax]
+        int64_t *d_counts;        // [kMax][2]
+        uint64_t *pk[2];
+        int64_t pk_cap;
+        tpx_record *cl[2];
+        int64_t cl_cap;
+        int64_t *trig[2];
+        int64_t trig_cap;
+        bool ready;
+    } pipe;
     // unwrap state before / after a call, on the device (ping-pong)
     tpxk::GAgg *d_state;      // [2]
     int cur;                  // d_state[cur]: state for the next call

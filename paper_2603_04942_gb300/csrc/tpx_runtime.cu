@@ -2,9 +2,9 @@
 // context and scratch management, argument checks, launches, status words.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
-#include <cstdlib>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -263,6 +263,24 @@ int tpx_destroy(tpx_ctx *c) {
     for (auto &smp : c->tune.ring) {
         if (smp.a) cudaEventDestroy(smp.a);
         if (smp.b) cudaEventDestroy(smp.b);
+    }
+    if (c->pipe.ready) {
+        cudaStreamSynchronize(c->pipe.s_in);
+        cudaStreamSynchronize(c->pipe.s_out);
+        for (int k = 0; k < tpx_ctx::Pipe::kMax; ++k) {
+            cudaEventDestroy(c->pipe.ev_in[k]);
+            cudaEventDestroy(c->pipe.ev_done[k]);
+            cudaEventDestroy(c->pipe.ev_out[k]);
+        }
+        cudaStreamDestroy(c->pipe.s_in);
+        cudaStreamDestroy(c->pipe.s_out);
+        cudaFreeHost(c->pipe.h_slot);
+        cudaFree(c->pipe.d_counts);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->pipe.pk[b]) cudaFree(c->pipe.pk[b]);
+        if (c->pipe.cl[b]) cudaFree(c->pipe.cl[b]);
+        if (c->pipe.trig[b]) cudaFree(c->pipe.trig[b]);
     }
     if (c->batch.tab_copied) cudaEventDestroy(c->batch.tab_copied);
     if (c->batch.dev) cudaFree(c->batch.dev);
@@ -597,13 +615,180 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     return TPX_OK;
 }
 
+namespace {
+
+constexpr int64_t kPipeMinPackets = 1LL << 24;     // below this one call does it
+constexpr int64_t kPipePiecePackets = 1LL << 23;   // smallest piece
+
+int pipe_init(tpx_ctx *c) {
+    auto &P = c->pipe;
+    if (P.ready) return TPX_OK;
+    if (ckr(cudaStreamCreateWithFlags(&P.s_in, cudaStreamNonBlocking)) ||
+        ckr(cudaStreamCreateWithFlags(&P.s_out, cudaStreamNonBlocking)))
+        return TPX_ECUDA;
+    for (int k = 0; k < tpx_ctx::Pipe::kMax; ++k)
+        if (ckr(cudaEventCreateWithFlags(&P.ev_in[k], cudaEventDisableTiming)) ||
+            ckr(cudaEventCreateWithFlags(&P.ev_done[k], cudaEventDisableTiming)) ||
+            ckr(cudaEventCreateWithFlags(&P.ev_out[k], cudaEventDisableTiming)))
+            return TPX_ECUDA;
+    if (ckr(cudaMallocHost(reinterpret_cast<void **>(&P.h_slot), sizeof(tpx_ctx::Pipe::Slot) * tpx_ctx::Pipe::kMax)))
+        return TPX_ENOMEM;
+    if (ckr(cudaMalloc(reinterpret_cast<void **>(&P.d_counts), sizeof(int64_t) * 2 * tpx_ctx::Pipe::kMax)))
+        return TPX_ENOMEM;
+    P.ready = true;
+    return TPX_OK;
+}
+
+// piece boundaries: near k n / K, moved forward to the next trigger packet,
+// so that each piece starts with its own shot; returns the number of pieces
+int pipe_cuts(const uint64_t *h, int64_t n, int64_t *cut) {
+    int K = (int)std::min<int64_t>(tpx_ctx::Pipe::kMax, n / kPipePiecePackets);
+    int m = 0;
+    cut[m++] = 0;
+    for (int k = 1; k < K; ++k) {
+        int64_t q = std::max(k * (n / K), cut[m - 1] + kPipePiecePackets / 2);
+        while (q < n && (h[q] >> 60) != 0x6u) ++q;
+        if (q >= n) break;
+        cut[m++] = q;
+    }
+    cut[m] = n;
+    return m;
+}
+
+}  // namespace
+
+// The host call on a large input, pipelined: piece k's packets go up while
+// piece k-1 runs and piece k-2's labels and records come down. The pieces are
+// chained through the unwrap state exactly as consecutive calls; a cut is
+// exact when no pixel after it belongs to the shot before it in time, and a
+// piece whose fused kernel reports anything it cannot hold (such a pixel is
+// one) sends the whole call back to the one-piece path. Returns 1 when it
+// declined (the caller then runs the plain path), else a status.
+static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base,
+                                  int64_t *h_labels, uint8_t *h_is_peak, tpx_record *h_clusters, int64_t cl_cap,
+                                  int64_t *h_n_clusters, int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
+    if (n < kPipeMinPackets || c->cfg.chain || c->state_once) return 1;
+    int64_t cut[tpx_ctx::Pipe::kMax + 1];
+    const int K = pipe_cuts(h_packets, n, cut);
+    if (K < 2) return 1;
+    int rc = pipe_init(c);
+    if (rc) return rc;
+    auto &P = c->pipe;
+    int64_t maxp = 0;
+    for (int k = 0; k < K; ++k) maxp = std::max(maxp, cut[k + 1] - cut[k]);
+    for (int b = 0; b < 2; ++b) {
+        int64_t cap = P.pk_cap;
+        if ((rc = grow(&P.pk[b], &cap, maxp))) return rc;
+        cap = P.cl_cap;
+        if ((rc = grow(&P.cl[b], &cap, cl_cap))) return rc;
+        cap = P.trig_cap;
+        if ((rc = grow(&P.trig[b], &cap, trig_cap))) return rc;
+    }
+    P.pk_cap = std::max(P.pk_cap, maxp);
+    P.cl_cap = std::max(P.cl_cap, cl_cap);
+    P.trig_cap = std::max(P.trig_cap, trig_cap);
+    if (h_labels && (rc = grow(&c->st_labels, &c->st_labels_cap, n))) return rc;
+    if (h_is_peak && (rc = grow(&c->st_peak, &c->st_peak_cap, n))) return rc;
+    cudaStream_t sc = c->stream;
+    // all earlier work on the context stream is done before the copies start
+    if (ckr(cudaEventRecord(P.ev_done[0], sc)) || ckr(cudaStreamWaitEvent(P.s_in, P.ev_done[0], 0)) ||
+        ckr(cudaStreamWaitEvent(P.s_out, P.ev_done[0], 0)))
+        return TPX_ECUDA;
+    auto h2d = [&](int k) -> int {
+        const int64_t m = cut[k + 1] - cut[k];
+        if (k >= 2 && ckr(cudaStreamWaitEvent(P.s_in, P.ev_done[k - 2], 0))) return TPX_ECUDA;
+        if (ckr(cudaMemcpyAsync(P.pk[k & 1], h_packets + cut[k], sizeof(uint64_t) * m, cudaMemcpyHostToDevice, P.s_in)) ||
+            ckr(cudaEventRecord(P.ev_in[k], P.s_in)))
+            return TPX_ECUDA;
+        return TPX_OK;
+    };
+    int64_t rec_off = 0, trig_off = 0;
+    bool failed = false;
+    tpxk::Ctl total;
+    std::memset(&total, 0, sizeof total);
+    // records and triggers of piece k come down once its counts are known
+    auto d2h_records = [&](int k) -> int {
+        if (ckr(cudaEventSynchronize(P.ev_done[k]))) return TPX_ECUDA;
+        const auto &sl = P.h_slot[k];
+        total.status |= sl.ctl.status;
+        for (int i = 0; i < tpxk::C_NUM; ++i) total.counters[i] += sl.ctl.counters[i];
+        if (sl.ctl.status & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION | tpxk::ST_DEVTIMEOUT)) failed = true;
+        const int64_t ncl = sl.counts[0], ntr = sl.counts[1];
+        const int64_t ccl = std::max<int64_t>(0, std::min(ncl, cl_cap - rec_off));
+        const int64_t ctr = std::max<int64_t>(0, std::min(ntr, trig_cap - trig_off));
+        if (!failed && ccl > 0 &&
+            ckr(cudaMemcpyAsync(h_clusters + rec_off, P.cl[k & 1], sizeof(tpx_record) * ccl, cudaMemcpyDeviceToHost,
+                                P.s_out)))
+            return TPX_ECUDA;
+        if (!failed && ctr > 0 &&
+            ckr(cudaMemcpyAsync(h_trig + trig_off, P.trig[k & 1], sizeof(int64_t) * ctr, cudaMemcpyDeviceToHost, P.s_out)))
+            return TPX_ECUDA;
+        rec_off += ncl;
+        trig_off += ntr;
+        return ckr(cudaEventRecord(P.ev_out[k], P.s_out)) ? TPX_ECUDA : TPX_OK;
+    };
+    if ((rc = h2d(0))) return rc;
+    for (int k = 0; k < K; ++k) {
+        if (k + 1 < K && (rc = h2d(k + 1))) return rc;
+        const int64_t m = cut[k + 1] - cut[k];
+        if (ckr(cudaStreamWaitEvent(sc, P.ev_in[k], 0))) return TPX_ECUDA;
+        if (k >= 2 && ckr(cudaStreamWaitEvent(sc, P.ev_out[k - 2], 0))) return TPX_ECUDA;
+        c->state_once = k > 0;   // continue from the previous piece's state
+        rc = tpx_process(c, P.pk[k & 1], m, idx_base + cut[k], h_labels ? c->st_labels + cut[k] : nullptr,
+                         h_is_peak ? c->st_peak + cut[k] : nullptr, P.cl[k & 1], cl_cap, P.d_counts + 2 * k,
+                         P.trig[k & 1], trig_cap, P.d_counts + 2 * k + 1);
+        if (rc) return rc;
+        // a piece the autotuner's sample already redid on the general path
+        // cannot show whether its cut was exact
+        if (c->redone_early) failed = true;
+        if (ckr(cudaMemcpyAsync(P.h_slot[k].counts, P.d_counts + 2 * k, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, sc)) ||
+            ckr(cudaMemcpyAsync(&P.h_slot[k].ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, sc)) ||
+            ckr(cudaEventRecord(P.ev_done[k], sc)))
+            return TPX_ECUDA;
+        // piece k-1's records go down before piece k's labels: the kernel of
+        // piece k+1 waits for them (it reuses their buffer), not for k's labels
+        if (k >= 1 && (rc = d2h_records(k - 1))) return rc;
+        if (ckr(cudaStreamWaitEvent(P.s_out, P.ev_done[k], 0))) return TPX_ECUDA;
+        if (h_labels && ckr(cudaMemcpyAsync(h_labels + cut[k], c->st_labels + cut[k], sizeof(int64_t) * m,
+                                            cudaMemcpyDeviceToHost, P.s_out)))
+            return TPX_ECUDA;
+        if (h_is_peak && ckr(cudaMemcpyAsync(h_is_peak + cut[k], c->st_peak + cut[k], (size_t)m, cudaMemcpyDeviceToHost,
+                                             P.s_out)))
+            return TPX_ECUDA;
+    }
+    if ((rc = d2h_records(K - 1))) return rc;
+    if (ckr(cudaStreamSynchronize(P.s_out)) || ckr(cudaStreamSynchronize(sc))) return TPX_ECUDA;
+    if (failed) {
+        // forget the pieces: no failure of theirs may reach the next sync
+        if (ckr(cudaMemsetAsync(c->d_sticky, 0, 4, sc)) || ckr(cudaStreamSynchronize(sc))) return TPX_ECUDA;
+        c->synced = true;
+        c->last.valid = false;
+        c->state_once = false;
+        return 1;
+    }
+    // the call's counters and status, as one call would leave them
+    total.tile_counter = 0;
+    if (ckr(cudaMemcpyAsync(c->ctl, &total, sizeof total, cudaMemcpyHostToDevice, sc)) ||
+        ckr(cudaStreamSynchronize(sc)))
+        return TPX_ECUDA;
+    *h_n_clusters = rec_off;
+    *h_n_trig = trig_off;
+    rc = tpx_sync(c, nullptr);
+    if (rc == TPX_OK && (rec_off > cl_cap || trig_off > trig_cap)) rc = TPX_EOVERFLOW;
+    return rc;
+}
+
 int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base, int64_t *h_labels,
                      uint8_t *h_is_peak, tpx_record *h_clusters, int64_t cl_cap, int64_t *h_n_clusters,
                      int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
     if (!c || n < 0 || cl_cap < 0 || trig_cap < 0 || !h_n_clusters || !h_n_trig) return TPX_EINVAL;
     if (n > 0 && !h_packets) return TPX_EINVAL;
     if (n > c->max_packets) return TPX_EINVAL;
-    int rc;
+    if (cl_cap > 0 && !h_clusters) return TPX_EINVAL;
+    if (trig_cap > 0 && !h_trig) return TPX_EINVAL;
+    int rc = process_host_pipelined(c, h_packets, n, idx_base, h_labels, h_is_peak, h_clusters, cl_cap, h_n_clusters,
+                                    h_trig, trig_cap, h_n_trig);
+    if (rc != 1) return rc;
     if ((rc = grow(&c->st_pk, &c->st_n, n))) return rc;
     if (h_labels && (rc = grow(&c->st_labels, &c->st_labels_cap, n))) return rc;
     if (h_is_peak && (rc = grow(&c->st_peak, &c->st_peak_cap, n))) return rc;

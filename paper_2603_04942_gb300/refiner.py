@@ -276,7 +276,8 @@ def hit_list(ds: Dataset, hits_selected: np.ndarray):
     h2 = hits_selected[k == 2]
     x = np.concatenate([cl["x"][~two], h2[:, 1], h2[:, 3]])
     y = np.concatenate([cl["y"][~two], h2[:, 2], h2[:, 4]])
-    shot = np.concatenate([cl["shot"][~two], np.repeat(cl["shot"][ds.sel[k == 2]], 2)])
+    s2 = cl["shot"][ds.sel[k == 2]]
+    shot = np.concatenate([cl["shot"][~two], s2, s2])
     return x, y, shot
 
 
