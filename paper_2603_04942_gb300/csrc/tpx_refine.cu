@@ -71,11 +71,29 @@ __global__ void k_scan_local(const unsigned *in, unsigned *out, long long n, uns
     if (i < n) out[i] = s[threadIdx.x] - v;
     if (threadIdx.x == SB - 1) bsum[blockIdx.x] = s[SB - 1];
 }
+// exclusive scan of the block sums by one block, SB at a time
 __global__ void k_scan_sums(unsigned *bsum, long long nb, long long *total) {
-    // one thread: the number of blocks is n / 1024 (small next to n)
-    unsigned acc = 0;
-    for (long long b = 0; b < nb; ++b) { const unsigned v = bsum[b]; bsum[b] = acc; acc += v; }
-    *total = acc;
+    __shared__ unsigned s[SB];
+    __shared__ unsigned carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b0 = 0; b0 < nb; b0 += SB) {
+        const long long b = b0 + threadIdx.x;
+        const unsigned v = b < nb ? bsum[b] : 0u;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < SB; o <<= 1) {
+            const unsigned u = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+            __syncthreads();
+            s[threadIdx.x] += u;
+            __syncthreads();
+        }
+        if (b < nb) bsum[b] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == SB - 1) carry += s[SB - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
 }
 __global__ void k_scan_add(unsigned *out, long long n, const unsigned *bsum) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -521,7 +539,7 @@ int tpx_refine_patches(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t
     unsigned long long *key = reinterpret_cast<unsigned long long *>(m);
     k_sel_flags<<<grid_for(n_clusters), 256, 0, s>>>(d_clusters, n_clusters, min_pixels, f);
     k_scan_local<<<(unsigned)nb, SB, 0, s>>>(f, off, n_clusters, bsum);
-    k_scan_sums<<<1, 1, 0, s>>>(bsum, nb, reinterpret_cast<long long *>(d_n_patches));
+    k_scan_sums<<<1, SB, 0, s>>>(bsum, nb, reinterpret_cast<long long *>(d_n_patches));
     k_scan_add<<<grid_for(n_clusters), 256, 0, s>>>(off, n_clusters, bsum);
     k_fill_i32<<<grid_for(n), 256, 0, s>>>(slot, n, -1);
     long long np = 0;
