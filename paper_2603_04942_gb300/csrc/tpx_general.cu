@@ -934,30 +934,41 @@ __device__ __forceinline__ unsigned long long cell_hash(long long shot, int x, i
     k *= 0x9E3779B97F4A7C15ull;   // Fibonacci hashing
     return (k >> 20) & mask;
 }
-__global__ void k_long_insert(Sorted s, long long n, const unsigned char *mark, unsigned *head, unsigned *next,
-                              unsigned long long mask) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        if (!mark[i]) continue;
-        next[i] = atomicExch(&head[cell_hash(s.shot[i], s.x[i], s.y[i], mask)], (unsigned)i);
-    }
+// a marked hit's cell and time in one word for the pair search: x, y, the
+// shot's low 16 bits, ToF + bias (the full shot is compared on a match)
+__device__ __forceinline__ unsigned cell_key(long long shot, int x, int y) {
+    return (unsigned)x | ((unsigned)y << 8) | ((unsigned)(shot & 0xFFFF) << 16);
 }
-__global__ void k_long_pairs(Sorted s, long long n, const unsigned char *mark, const unsigned *head,
-                             const unsigned *next, unsigned long long mask, int rx, int ry, int dt, int cc,
-                             int *parent, unsigned char *notpeak) {
+__global__ void k_long_insert(Sorted s, long long n, const unsigned char *mark, unsigned *head, unsigned *next,
+                              unsigned long long *word, unsigned long long mask) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         if (!mark[i]) continue;
         const long long sh = s.shot[i];
-        const int tb = s.tofb[i], xi = s.x[i], yi = s.y[i], ti = s.tot[i];
+        const int x = s.x[i], y = s.y[i];
+        word[i] = (unsigned long long)cell_key(sh, x, y) | ((unsigned long long)(unsigned)s.tofb[i] << 32);
+        next[i] = atomicExch(&head[cell_hash(sh, x, y, mask)], (unsigned)i);
+    }
+}
+__global__ void k_long_pairs(Sorted s, long long n, const unsigned char *mark, const unsigned *head,
+                             const unsigned *next, const unsigned long long *word, unsigned long long mask, int rx,
+                             int ry, int dt, int cc, int *parent, unsigned char *notpeak) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (!mark[i]) continue;
+        const unsigned long long wi = word[i];
+        const long long sh = s.shot[i];
+        const int tb = (int)(unsigned)(wi >> 32), xi = (int)(wi & 255), yi = (int)((wi >> 8) & 255), ti = s.tot[i];
         for (int dx = 0; dx <= rx; ++dx) {
             const int cx = xi + dx;
             if (cx > 255) break;
             for (int dy = (dx == 0 ? 0 : -ry); dy <= ry; ++dy) {
                 const int cy = yi + dy;
                 if (cy < 0 || cy > 255) continue;
+                const unsigned key = cell_key(sh, cx, cy);
                 for (unsigned j = head[cell_hash(sh, cx, cy, mask)]; j != 0xFFFFFFFFu; j = next[j]) {
                     if (dx == 0 && dy == 0 && (long long)j <= i) continue;
-                    if (s.x[j] != cx || s.y[j] != cy || s.shot[j] != sh) continue;
-                    const int d = s.tofb[j] - tb;
+                    const unsigned long long wj = word[j];
+                    if ((unsigned)wj != key || s.shot[j] != sh) continue;
+                    const int d = (int)(unsigned)(wj >> 32) - tb;
                     if (d < -dt || d > dt) continue;
                     if (j_brighter(s.tot[j], ti, s.index, j, i)) notpeak[i] = 1; else notpeak[j] = 1;
                     if (cc) g_unite(parent, (int)i, (int)j);
@@ -1251,7 +1262,7 @@ size_t cluster_bytes(long long n) {
            + 2 * sz(n, 4) + sz(n + 1, 8) + sz(1, 8)                                     // segments
            + 2 * sz(n, 1) + sz(n, 4)                                                    // long segments
            + 2 * sz(n, 4) + sz(n, sizeof(AccH)) + sz((n + GTILE - 1) / GTILE + 1, 4)    // records
-           + sz(4 * n + 2, 4) + sz(n, 4)                                               // long-segment hash
+           + sz(4 * n + 2, 4) + sz(n, 4) + sz(n, 8)                                    // long-segment hash
            + 8192;
 }
 
@@ -1285,6 +1296,7 @@ int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8
     unsigned long long lmask = 1;   // the long segments' cell hash: >= 2n buckets
     while (lmask + 1 < 2ull * (unsigned long long)n) lmask = 2 * lmask + 1;
     unsigned *lhead = a.take<unsigned>((long long)lmask + 1), *lnext = a.take<unsigned>(n);
+    unsigned long long *lword = a.take<unsigned long long>(n);
     const size_t mark_used = a.used;
     unsigned *vals = nullptr;
     rc = sort_hits(c, a, h, n, shot_span, &vals);
@@ -1306,9 +1318,9 @@ int cluster_all(tpx_ctx *c, const tpx_hits &h, int64_t n, int64_t *labels, uint8
                                                 is_peak, rf, ac, mark);
     k_long_init<<<grid_for(n), GT, 0, s>>>(so, n, mark, parent, notpeak, ac);
     if (ck(cudaMemsetAsync(lhead, 0xFF, sizeof(unsigned) * (size_t)(lmask + 1), s))) return TPX_ECUDA;
-    k_long_insert<<<grid_for(n), GT, 0, s>>>(so, n, mark, lhead, lnext, lmask);
-    k_long_pairs<<<grid_for(n), GT, 0, s>>>(so, n, mark, lhead, lnext, lmask, c->cfg.rx, c->cfg.ry, dt, cc, parent,
-                                            notpeak);
+    k_long_insert<<<grid_for(n), GT, 0, s>>>(so, n, mark, lhead, lnext, lword, lmask);
+    k_long_pairs<<<grid_for(n), GT, 0, s>>>(so, n, mark, lhead, lnext, lword, lmask, c->cfg.rx, c->cfg.ry, dt, cc,
+                                            parent, notpeak);
     k_long_finish<<<grid_for(n), GT, 0, s>>>(so, n, mark, cc, shot_limit, parent, notpeak, lab, is_peak, rf, ac);
     if (!out) return ck(cudaGetLastError());
     rc = scan_u32(a, rflag, cid, n, s);
