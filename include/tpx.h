@@ -282,6 +282,15 @@ int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t
 int tpx_tot_tof_histogram(tpx_ctx *ctx, const tpx_hits *hits, int64_t n_hits, int32_t tof_lo_ticks,
                           int32_t tof_bin_ticks, int32_t n_tof_bins, uint32_t *d_hist);
 
+/* Failure detection without a GPU fault (no counterpart in the paper): the
+   next tpx_process call leaves tile `tile`'s look-back flags unpublished
+   (a negative tile clears the request), so the bounded waits of the tiles
+   after it run out (about 0.5 s once; every later wait then gives up at
+   once); the call completes, its outputs are not valid, and tpx_sync returns
+   TPX_EDEVTIMEOUT.  The context stays usable.  For tests of the timeout
+   path only. */
+int tpx_debug_hold_tile(tpx_ctx *ctx, int64_t tile);
+
 /* ---- learned overlap refiner (not in the paper; its multi-hit discussion,
    Sec. VII.B, and the local-maximum count of Sec. V.B motivate it) ----
    A cluster may hold two particles. Its 9 x 9 patch (channel 0: ToT / 1023

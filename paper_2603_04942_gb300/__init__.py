@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_dest
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
                     "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_refine_patches", "tpx_refiner_params",
                     "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
-                    "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_strerror", "tpx_version")
 
@@ -147,6 +147,8 @@ def load(path: str | None = None):
         L.tpx_refiner_train_step.argtypes = [vp, vp, vp, vp, vp, i32, i64, vp, vp, i64, ctypes.c_float,
                                              ctypes.c_float, vp, vp]
         L.tpx_refine_decide.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.c_float, vp]
+        L.tpx_debug_hold_tile.argtypes = [vp, i64]
+        L.tpx_debug_hold_tile.restype = i32
         L.tpx_refiner_packed_bytes.argtypes = [i32]
         L.tpx_refiner_packed_bytes.restype = i64
         L.tpx_refiner_pack.argtypes = [vp, vp, i32, vp]
@@ -403,6 +405,13 @@ class Context:
         if rc:
             raise TpxError(rc, "tpx_tot_tof_histogram")
         return hist
+
+    def tpx_debug_hold_tile(self, tile: int):
+        """The next tpx_process call holds tile `tile`'s look-back flags back
+        (tests of the bounded device waits: tpx_sync then returns EDEVTIMEOUT)."""
+        rc = lib().tpx_debug_hold_tile(self._h, int(tile))
+        if rc:
+            raise TpxError(rc, "tpx_debug_hold_tile")
 
     # -- the learned overlap refiner --
     def tpx_refine_patches(self, packets, labels, clusters, n_clusters: int, min_pixels: int = 12,

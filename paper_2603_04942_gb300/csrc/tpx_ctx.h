@@ -36,6 +36,7 @@ struct tpx_ctx {
     unsigned *d_sticky;       // failure bits of calls that were not synchronised
     bool synced;              // tpx_sync ran after the last call
     int64_t redone_early;     // the last call was already redone (autotuner sample)
+    int64_t hold_next;        // tile + 1 the next tpx_process call holds back (tpx_debug_hold_tile)
     // device staging for tpx_process_host
     uint64_t *st_pk;
     int64_t *st_labels;

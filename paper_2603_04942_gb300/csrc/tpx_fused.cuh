@@ -110,6 +110,8 @@ struct Params {
     tpx_record *stage;       // per-CTA record staging (range-capacity records per
                              // CTA of the grid), or NULL: inline offset look-back
     BatchTable bt;           // batch of runs (tile_run == NULL: one stream)
+    long long hold;          // tile + 1 whose look-back flags stay unpublished (0: none): lets a
+                             // test run its successors' bounded waits out (TPX_EDEVTIMEOUT)
     const GAgg *E0;          // unwrap state before the call (NULL: stream start)
     GAgg *state_out;         // state after the call, written by the last tile (or NULL)
 };

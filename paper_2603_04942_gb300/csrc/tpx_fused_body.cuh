@@ -341,7 +341,7 @@ __device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long
     longlong2 Ow = make_longlong2(0, 0);
     if (tl > 0) Ow = lookback_count_warp<BATCH>(p, tl, seq, &st2);
     if (threadIdx.x == 0) {
-        if (tl > 0) {
+        if (tl > 0 && tl + 1 != p.hold) {
             __stcg(&p.ts.cpre[tl], Ow.x + (long long)nc);
             if (BATCH) __stcg(&p.bt.tcpre[tl], Ow.y + (long long)nt);
             st_release(&p.ts.cflags[tl], (seq << 2) | 2u);
@@ -480,7 +480,9 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // read-ahead and the block scan, which do not need it
         if (tid == 0) {
             S.tile_agg = S.tot_agg;
-            if (tile > tile0) {
+            if (tile + 1 == p.hold) {
+                // a test holds this tile's flags back: its successors' waits run out
+            } else if (tile > tile0) {
                 st_agg(&p.ts.agg[tile], S.tot_agg);
                 st_release(&p.ts.flags[tile], (seq << 2) | 1u);
             } else {
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             if (tile > tile0) Ew = lookback_agg_warp(p, tile, tile0, seq, &stl, S.lb_buf);
             else Ew = (!BATCH && p.E0) ? *p.E0 : agg_id();
             if (tid == 0) {
-                if (tile > tile0) {
+                if (tile > tile0 && tile + 1 != p.hold) {
                     st_agg(&p.ts.pre[tile], acomb(Ew, S.tile_agg, tp, tt));
                     st_release(&p.ts.flags[tile], (seq << 2) | 2u);
                 }
@@ -577,7 +579,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
                 if (!BATCH && q < cnt) {   // a batch writes its triggers at the flush
                     const long long g = E.tdc.n - trig_base + li;
-                    if (g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
+                    // (g < 0 only after a look-back ran out: the state is partial)
+                    if (g >= 0 && g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
                 }
                 ++li;
             }
@@ -821,7 +824,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
 
         // ---- record offsets: publish this tile's count now, look back later ----
-        if (tid == 0) {
+        if (tid == 0 && tile + 1 != p.hold) {
             if (tile > 0) {
                 __stcg(&p.ts.cagg[tile], (long long)ncl);
                 if (BATCH) __stcg(&p.bt.tcagg[tile], (long long)S.cnt[C_TDCS]);

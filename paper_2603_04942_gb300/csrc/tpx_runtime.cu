@@ -361,6 +361,8 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.E0 = E0;
     p.state_out = state_out;
     p.stage = c->stage;
+    p.hold = c->hold_next;
+    c->hold_next = 0;
     int64_t grid = (int64_t)c->num_sms * tpxk::fused_ctas_per_sm(geo);   // persistent, all resident
     if (grid > p.n_tiles) grid = p.n_tiles;
     auto &t = c->tune;
@@ -818,6 +820,12 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     *h_n_clusters = counts[0];
     *h_n_trig = counts[1];
     return tpx_sync(c, nullptr);
+}
+
+int tpx_debug_hold_tile(tpx_ctx *c, int64_t tile) {
+    if (!c) return TPX_EINVAL;
+    c->hold_next = tile >= 0 ? tile + 1 : 0;
+    return TPX_OK;
 }
 
 int tpx_tuning(tpx_ctx *c, int32_t *tile_geometry, double *ms_per_mpacket) {

@@ -115,3 +115,35 @@ def test_combine_is_associative_and_matches_whole():
     for p in reversed(parts):
         right = shard.combine(p, right)
     assert left == right == _summary(pk)
+
+
+def _rank_dies(rank, world, port, outdir):
+    """Rank 1 leaves between steps (after joining, before the exchange); rank
+    0's exchange must end with an error within the group's timeout, not hang."""
+    import datetime
+
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", world_size=world, rank=rank,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(0)
+    pk = synth.generate(synth.small(n_shots=40))[0]
+    try:
+        shard.exchange_states(_summary(pk))
+        outcome = "completed"
+    except Exception as e:   # the backend's error type differs between versions
+        outcome = "error: " + type(e).__name__
+    with open(os.path.join(outdir, "outcome.txt"), "w") as f:
+        f.write(outcome)
+    os._exit(0)   # the group is broken: leave without a collective teardown
+
+
+def test_a_rank_that_dies_is_reported_by_the_exchange(tmp_path):
+    import time
+
+    import torch.multiprocessing as mp
+    t0 = time.perf_counter()
+    mp.spawn(_rank_dies, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    outcome = (tmp_path / "outcome.txt").read_text()
+    assert outcome.startswith("error"), outcome
+    assert time.perf_counter() - t0 < 120
