@@ -478,6 +478,25 @@ int tpx_stream_poll(tpx_stream *st, uint64_t ticket, tpx_stream_result *out, int
 
 int tpx_stream_destroy(tpx_stream *st);
 
+/* Checkpoint and resume (no counterpart in the paper, which processes whole
+   files): all that a stream carries from one submit to the next -- the
+   packets of its open shots, the unwrap state and trigger count where they
+   start, the stream index of the first -- as one host byte block of
+   tpx_stream_snapshot_bytes() bytes (header + 8 bytes per held packet).
+   tpx_stream_snapshot waits for the stream's queued work; results not yet
+   polled are not part of the checkpoint (poll them first; they stay
+   pollable).  TPX_EOVERFLOW (and *written = the size needed) if capacity is
+   short; TPX_EINVAL after tpx_stream_finish.  tpx_stream_restore loads one
+   into a stream created with the same configuration that has not been
+   submitted to; its later submits continue the old stream exactly (the same
+   shots, trigger times and records as if it had not stopped).  TPX_EINVAL for
+   a damaged block, another configuration (radii, dt, mode, ToF cut, wrap
+   thresholds, hold_triggers) or a stream already in use,
+   TPX_EOVERFLOW if the held packets exceed max_hold_packets. */
+int64_t tpx_stream_snapshot_bytes(tpx_stream *st);
+int tpx_stream_snapshot(tpx_stream *st, void *h_buf, int64_t capacity, int64_t *written);
+int tpx_stream_restore(tpx_stream *st, const void *h_buf, int64_t n_bytes);
+
 /* Static description of a status code. */
 const char *tpx_strerror(int code);
 

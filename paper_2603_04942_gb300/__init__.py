@@ -43,6 +43,7 @@ EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_dest
                     "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
                     "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
+                    "tpx_stream_snapshot_bytes", "tpx_stream_snapshot", "tpx_stream_restore",
                     "tpx_strerror", "tpx_version")
 
 
@@ -167,6 +168,12 @@ def load(path: str | None = None):
         L.tpx_stream_finish.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
         L.tpx_stream_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(_CStreamResult), ctypes.c_int32]
         L.tpx_stream_destroy.argtypes = [vp]
+        L.tpx_stream_snapshot_bytes.argtypes = [vp]
+        L.tpx_stream_snapshot_bytes.restype = i64
+        L.tpx_stream_snapshot.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)]
+        L.tpx_stream_snapshot.restype = i32
+        L.tpx_stream_restore.argtypes = [vp, vp, i64]
+        L.tpx_stream_restore.restype = i32
         for f in ("tpx_stream_create", "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll",
                   "tpx_stream_destroy"):
             getattr(L, f).restype = i32
@@ -567,6 +574,22 @@ class Stream:
             tr = np.array((ctypes.c_int64 * r.n_shots).from_address(r.trig_t), dtype=np.int64)
         return dict(ticket=r.ticket, status=r.status, first_shot=r.first_shot, n_shots=r.n_shots, triggers=tr,
                     clusters=cl, packets_processed=r.packets_processed, latency_us=r.latency_us)
+
+    def snapshot(self) -> bytes:
+        """The stream's carry as a host byte block (poll pending results first)."""
+        n = int(lib().tpx_stream_snapshot_bytes(self._h))
+        buf = ctypes.create_string_buffer(n)
+        w = ctypes.c_int64()
+        rc = lib().tpx_stream_snapshot(self._h, buf, n, ctypes.byref(w))
+        if rc:
+            raise TpxError(rc, "tpx_stream_snapshot")
+        return buf.raw[: w.value]
+
+    def restore(self, block: bytes):
+        """Continue a checkpointed stream (this stream must not have started)."""
+        rc = lib().tpx_stream_restore(self._h, block, len(block))
+        if rc:
+            raise TpxError(rc, "tpx_stream_restore")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -375,6 +375,80 @@ int tpx_stream_poll(tpx_stream *S, uint64_t ticket, tpx_stream_result *out, int3
     return TPX_OK;
 }
 
+// checkpoint: a fixed header, then the held packets
+namespace {
+constexpr uint64_t kSnapMagic = 0x31504E5358505454ull;   // "TTPXSNP1", little-endian
+struct SnapHeader {
+    uint64_t magic;
+    int64_t held, index_base, trig_base, hold_triggers, max_hold_packets;
+    int64_t rx, ry, dt, mode, tof_max, wrap_pix, wrap_tdc;   // the processing configuration
+    tpxk::GAgg state;          // unwrap state and trigger count where the held packets start
+};
+void snap_cfg(const tpx_stream *S, SnapHeader &h) {
+    const tpx_config &c = S->cfg.cfg;
+    h.rx = c.rx; h.ry = c.ry; h.dt = c.dt_ticks; h.mode = c.mode; h.tof_max = c.tof_max_ticks;
+    h.wrap_pix = c.wrap_thr_pix_ticks; h.wrap_tdc = c.wrap_thr_tdc_ticks;
+}
+}  // namespace
+
+int64_t tpx_stream_snapshot_bytes(tpx_stream *S) {
+    if (!S) return 0;
+    return (int64_t)sizeof(SnapHeader) + 8 * S->held;
+}
+
+int tpx_stream_snapshot(tpx_stream *S, void *h_buf, int64_t capacity, int64_t *written) {
+    if (!S || !h_buf || !written) return TPX_EINVAL;
+    const int64_t need = tpx_stream_snapshot_bytes(S);
+    *written = need;
+    if (capacity < need) return TPX_EOVERFLOW;
+    if (S->finished) return TPX_EINVAL;
+    SnapHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    hd.magic = kSnapMagic;
+    hd.held = S->held;
+    hd.index_base = S->index_base;
+    hd.trig_base = S->trig_base;
+    hd.hold_triggers = S->cfg.hold_triggers;
+    hd.max_hold_packets = S->cfg.max_hold_packets;
+    snap_cfg(S, hd);
+    char *dst = static_cast<char *>(h_buf);
+    // the carry is written by the stream's own kernels and copies: read it behind them
+    if (cks(cudaMemcpyAsync(&hd.state, S->st[0], sizeof(tpxk::GAgg), cudaMemcpyDeviceToHost, S->s))) return TPX_ECUDA;
+    if (S->held > 0 && cks(cudaMemcpyAsync(dst + sizeof hd, S->pend[S->cur], 8 * (size_t)S->held,
+                                           cudaMemcpyDeviceToHost, S->s)))
+        return TPX_ECUDA;
+    if (cks(cudaStreamSynchronize(S->s))) return TPX_ECUDA;
+    std::memcpy(dst, &hd, sizeof hd);
+    return TPX_OK;
+}
+
+int tpx_stream_restore(tpx_stream *S, const void *h_buf, int64_t n) {
+    if (!S || !h_buf || n < (int64_t)sizeof(SnapHeader)) return TPX_EINVAL;
+    SnapHeader hd;
+    std::memcpy(&hd, h_buf, sizeof hd);
+    if (hd.magic != kSnapMagic || hd.held < 0 || n != (int64_t)sizeof hd + 8 * hd.held) return TPX_EINVAL;
+    SnapHeader mine;
+    std::memset(&mine, 0, sizeof mine);
+    snap_cfg(S, mine);
+    if (hd.hold_triggers != S->cfg.hold_triggers || hd.rx != mine.rx || hd.ry != mine.ry || hd.dt != mine.dt ||
+        hd.mode != mine.mode || hd.tof_max != mine.tof_max || hd.wrap_pix != mine.wrap_pix ||
+        hd.wrap_tdc != mine.wrap_tdc)
+        return TPX_EINVAL;
+    // only into a stream that has not started
+    if (S->next_ticket != 1 || S->held != 0 || S->finished) return TPX_EINVAL;
+    if (hd.held > S->cfg.max_hold_packets) return TPX_EOVERFLOW;
+    const char *src = static_cast<const char *>(h_buf);
+    if (cks(cudaMemcpyAsync(S->st[0], &hd.state, sizeof(tpxk::GAgg), cudaMemcpyHostToDevice, S->s))) return TPX_ECUDA;
+    if (hd.held > 0 && cks(cudaMemcpyAsync(S->pend[S->cur], src + sizeof hd, 8 * (size_t)hd.held,
+                                           cudaMemcpyHostToDevice, S->s)))
+        return TPX_ECUDA;
+    if (cks(cudaStreamSynchronize(S->s))) return TPX_ECUDA;
+    S->held = hd.held;
+    S->index_base = hd.index_base;
+    S->trig_base = hd.trig_base;
+    return TPX_OK;
+}
+
 int tpx_stream_destroy(tpx_stream *S) {
     if (!S) return TPX_EINVAL;
     if (S->s) cudaStreamSynchronize(S->s);

@@ -2,7 +2,8 @@
 of all chunks' records equals the single-stream result (oracle), including a
 high-rate stream whose ToF cut spans the whole trigger period (pixels of a
 shot are read out after the next trigger); streams give the same results alone
-and run concurrently; admission answers EAGAIN."""
+and run concurrently; admission answers EAGAIN; a stream checkpointed to a
+host block and restored into a new stream continues exactly."""
 import threading
 
 import numpy as np
@@ -109,3 +110,56 @@ def test_admission():
     with pytest.raises(tpx.TpxError) as e:   # its buffers alone exceed a 1 MB budget
         tpx.Stream(tpx.Config(), max_chunk_packets=1 << 16, max_hold_packets=1 << 16, hbm_budget_bytes=1 << 20)
     assert e.value.code == tpx.EAGAIN
+
+
+@pytest.mark.parametrize("kind", ["small", "high_rate"])
+def test_checkpoint_and_resume_continue_the_stream_exactly(kind):
+    """Halfway through, the stream's carry goes to a host block, the stream
+    is destroyed, and a new stream restored from the block takes the rest:
+    the records and triggers equal one uninterrupted run."""
+    if kind == "small":
+        pk = synth.generate(synth.small(n_shots=400, pair_frac=0.05))[0]
+        cfg = tpx.Config()
+        whole = gpu_run(pk)
+    else:
+        pk = synth.generate(synth.streaming(10e6, n_shots=60))[0]
+        cfg = tpx.Config(tof_max_ticks=synth.STREAM_TOF_MAX_TICKS)
+        whole = oracle_run(pk, tof_max=synth.STREAM_TOF_MAX_TICKS)
+    sizes = chunks_for(pk.size, np.random.default_rng(5), 1000, 40_000)
+    half = len(sizes) // 2
+    kw = dict(max_chunk_packets=max(sizes), max_hold_packets=1 << 20, hold_triggers=2, slots=2)
+    recs, trig, pos = [], [], 0
+    st = tpx.Stream(cfg, **kw)
+    for c in sizes[:half]:
+        r = st.poll(st.submit(pk[pos:pos + c]))
+        recs.append(r["clusters"])
+        trig.append(r["triggers"])
+        pos += c
+    block = st.snapshot()
+    with pytest.raises(tpx.TpxError) as e:
+        st.restore(block)                  # a stream already in use
+    assert e.value.code == tpx.EINVAL
+    st.close()
+    other = tpx.Stream(tpx.Config(dt_ticks=cfg.dt_ticks + 1, tof_max_ticks=cfg.tof_max_ticks), **kw)
+    with pytest.raises(tpx.TpxError):
+        other.restore(block)               # another configuration
+    other.close()
+    st = tpx.Stream(cfg, **kw)
+    try:
+        with pytest.raises(tpx.TpxError):
+            st.restore(block[:-8] if len(block) > 8 else b"")   # a damaged block
+        st.restore(block)
+        for c in sizes[half:]:
+            r = st.poll(st.submit(pk[pos:pos + c]))
+            recs.append(r["clusters"])
+            trig.append(r["triggers"])
+            pos += c
+        r = st.poll(st.finish())
+        recs.append(r["clusters"])
+        trig.append(r["triggers"])
+    finally:
+        st.close()
+    assert np.array_equal(np.concatenate(trig), whole["triggers"])
+    # results come in shot order; a late cluster of shot k can carry a larger
+    # label than an early one of shot k+1: compare in label order
+    assert_clusters_equal(np.sort(np.concatenate(recs), order="label"), whole["clusters"])
