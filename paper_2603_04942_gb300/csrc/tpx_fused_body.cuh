@@ -4,7 +4,6 @@
 // packets a range may hold) and MINB (CTAs per SM). No include guard: it
 // is meant to be included repeatedly.
 constexpr int NW = NT / 32;
-constexpr int KP = C / NT;         // positions per thread in contiguous walks
 constexpr int MAXSEG = MS;         // TDC packets a range may hold (more: the call is redone)
 constexpr uint64_t INVALID = ~0ull;
 constexpr uint32_t EMPTY = 0xFFFFu;
@@ -457,8 +456,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             GAgg a = agg_id();
             unsigned long long c_pix = 0, c_tdc = 0, c_bad = 0;
             int my_first = INT_MAX;
-            const int p0 = tid * KP;
-            for (int j = 0; j < KP; ++j) {
+            // the tile's own packets split evenly over all threads
+            const int kp1 = (cnt + NT - 1) / NT;
+            const int p0 = tid * kp1;
+            for (int j = 0; j < kp1; ++j) {
                 const int q = p0 + j;
                 if (q >= cnt) break;
                 const uint64_t w = S.buf[pad(q)];
@@ -522,12 +523,15 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
 
         // ---- walk 2: per-thread chain state over [0, L) ----
-        const int p0 = tid * KP;
+        // [0, L) split evenly over all threads, in thread order (every later
+        // per-thread walk and scan uses the same contiguous chunks)
+        const int kpd = (L + NT - 1) / NT;
+        const int p0 = tid * kpd;
         GAgg ex;
         int ntdc;
         {
             GAgg a = agg_id();
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= L) break;
                 const uint64_t w = S.buf[pad(q)];
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             bool has = st.tdc.n > 0;
             long long last = st.tdc.last, ep = st.tdc.sum;
             int li = (int)ex.tdc.n;
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= L) break;
                 const uint64_t w = S.buf[pad(q)];
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             unsigned long long c_keep = 0, c_pre = 0, c_bg = 0;
             bool exc = false;
             const int nseg = min(ntdc, MAXSEG);
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= L) break;
                 const uint64_t w = S.buf[pad(q)];
@@ -794,7 +798,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             __syncthreads();
             // cluster ids in ascending root position (= ascending label)
             int c = 0;
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
             }
@@ -802,7 +806,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             // the union-find array is free now: it holds the member links
             // (first half) and the root position of each cluster id (second half)
             uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
                     rootpos[excl++] = (uint16_t)q;
@@ -812,12 +816,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         } else {
             // PAPER mode: one record per local maximum (list kept in parent[])
             int c = 0;
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) ++c;
             }
             int excl = block_scan_int(S, c, &ncl);
-            for (int j = 0; j < KP; ++j) {
+            for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) S.parent[excl++] = (uint32_t)q;
             }
