@@ -12,14 +12,14 @@ namespace tpxk {
 
 // 1024-thread CTAs, one per SM, 4096-packet tiles, 8192-position ranges
 namespace geo_t4096 {
-constexpr int NT = 1024, T = 4096, C = 8192, HB = 8192, MS = T + 16, MINB = 1;
+constexpr int NT = 1024, T = 4096, C = 8192, HB = 16384, MS = T + 16, MINB = 1;
 #include "tpx_fused_body.cuh"
 }  // namespace geo_t4096
 
 // 512-thread CTAs, two per SM, 2048-packet tiles, 5120-position ranges (any
 // shot of up to 3072 packets fits, wherever its trigger falls in the tile)
 namespace geo_t2048 {
-constexpr int NT = 512, T = 2048, C = 5120, HB = 4096, MS = T / 4 + 16, MINB = 2;
+constexpr int NT = 512, T = 2048, C = 5120, HB = 8192, MS = T / 4 + 16, MINB = 2;
 #include "tpx_fused_body.cuh"
 }  // namespace geo_t2048
 

@@ -10,6 +10,7 @@ constexpr uint32_t EMPTY = 0xFFFFu;
 constexpr long long MAX_SPIN = 1LL << 22;   // bounded look-back waits (~0.5 s)
 
 static_assert(T % NT == 0 && C % NT == 0 && T <= C && C <= 16384, "tile geometry");
+static_assert(C < 0xFFFF && HB % 2 == 0 && (HB & (HB - 1)) == 0 && HB * 2 <= C * 4, "16-bit hash heads");
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ int pad(int p) { return p + (p >> 3); }   // conflict-free 8-wide walks
@@ -88,7 +89,8 @@ struct __align__(16) Smem {
     uint64_t buf[C + C / 8];                          // packets, then kept-pixel records
     uint32_t parent[C];                               // union-find; then member links and
                                                       // root positions (CC) / peak list (PAPER)
-    union { uint32_t head[HB]; uint32_t mhead[C]; } u1; // hash heads, then member-list heads
+    union { uint16_t head[HB]; uint32_t mhead[C]; } u1; // hash heads (16-bit positions), then
+                                                      // member-list heads
     union { uint16_t next[C]; uint16_t rootof[C]; } u2;
     uint8_t notpeak[C];
     long long tdc_t[MAXSEG];
@@ -448,7 +450,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             }
             if ((cnt & 1) && tid == 0) S.buf[pad(cnt - 1)] = __ldcg(p.pk + base + cnt - 1);
         }
-        for (int i = tid; i < HB; i += NT) S.u1.head[i] = EMPTY;
+        for (int i = tid; i < HB / 2; i += NT) reinterpret_cast<uint32_t *>(S.u1.head)[i] = 0xFFFFFFFFu;
         __syncthreads();
 
         // ---- walk 1: unwrap-chain aggregate of the tile, packet counts ----
@@ -673,7 +675,13 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             S.notpeak[q] = 0;
             if (r != INVALID) {
                 const uint32_t b = hcell(r_seg(r), r_x(r), r_y(r));
-                S.u2.next[q] = (uint16_t)atomicExch(&S.u1.head[b], (uint32_t)q);
+                // push q on the bucket's list (16-bit exchange as a CAS loop)
+                unsigned short old = S.u1.head[b], seen;
+                do {
+                    seen = old;
+                    old = atomicCAS(&S.u1.head[b], seen, (unsigned short)q);
+                } while (old != seen);
+                S.u2.next[q] = old;
             }
         }
         __syncthreads();
