@@ -608,7 +608,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 __device__ void seg_small(const Sorted &s, long long s0, int L, int rx, int ry, int dt, int cc, bool emit,
-                          long long *labels, unsigned char *is_peak, unsigned *rflag, AccH *acc, int lane) {
+                          long long *labels, unsigned char *is_peak, unsigned *rflag, AccH *acc, int lane,
+                          SegSm &W) {
     constexpr unsigned FULL = 0xffffffffu;
     const int a = lane, b = lane + 32;
     const bool va = a < L, vb = b < L;
@@ -623,10 +624,62 @@ __device__ void seg_small(const Sorted &s, long long s0, int L, int rx, int ry, 
         tb = s.tofb[s0 + b]; pb = s.x[s0 + b] | ((unsigned)s.y[s0 + b] << 8); ob = s.tot[s0 + b];
         ib = s.index[s0 + b]; hb = s.hit[s0 + b];
     }
-    const unsigned rxy = (unsigned)rx | ((unsigned)ry << 8);   // per-byte box radii
     unsigned long long rowA = 0, rowB = 0;
     bool npA = false, npB = false;
-    for (int k = 0; k < L; ++k) {
+    // A compact segment (one particle, or a few close ones) with the 8-neighbour
+    // box: its hits go into a 16 x 16 occupancy grid of their bounding box and
+    // every lane reads its hits' 8 neighbour cells -- a few dozen instructions
+    // per hit instead of one warp-wide step per hit of the segment. Two hits on
+    // one pixel, a larger box or other radii take the all-pairs steps below.
+    bool grid = false;
+    if (rx == 1 && ry == 1) {
+        const unsigned xa = pa & 255u, ya = pa >> 8, xb = pb & 255u, yb = pb >> 8;
+        const unsigned x0 = __reduce_min_sync(FULL, min(va ? xa : 255u, vb ? xb : 255u));
+        const unsigned x1 = __reduce_max_sync(FULL, max(va ? xa : 0u, vb ? xb : 0u));
+        const unsigned y0 = __reduce_min_sync(FULL, min(va ? ya : 255u, vb ? yb : 255u));
+        const unsigned y1 = __reduce_max_sync(FULL, max(va ? ya : 0u, vb ? yb : 0u));
+        if (x1 - x0 <= 13u && y1 - y0 <= 13u) {
+            unsigned *cell = W.edge;   // 256 cells: hit + 1, 0 = empty (the edge list is not in use)
+            __syncwarp();              // the warp's previous segment is done with W
+            for (int i = lane; i < 256; i += 32) cell[i] = 0u;
+            if (va) { W.tofb[a] = ta; W.tot[a] = (unsigned short)oa; }
+            if (vb) { W.tofb[b] = tb; W.tot[b] = (unsigned short)ob; }
+            __syncwarp();
+            const int ca = (int)(xa - x0 + 1) + 16 * (int)(ya - y0 + 1), cb = (int)(xb - x0 + 1) + 16 * (int)(yb - y0 + 1);
+            bool twice = false;
+            if (va && atomicCAS(&cell[ca], 0u, (unsigned)a + 1u) != 0u) twice = true;
+            if (vb && atomicCAS(&cell[cb], 0u, (unsigned)b + 1u) != 0u) twice = true;
+            __syncwarp();
+            grid = !__any_sync(FULL, twice);
+            if (grid) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const bool v = h ? vb : va;
+                    if (!v) continue;
+                    const int c = h ? cb : ca, t = h ? tb : ta;
+                    const unsigned o = h ? ob : oa;
+                    const long long ix = h ? ib : ia;
+                    unsigned long long row = 0;
+                    bool np = false;
+#pragma unroll
+                    for (int d = 0; d < 9; ++d) {
+                        if (d == 4) continue;
+                        const unsigned j1 = cell[c + (d % 3 - 1) + 16 * (d / 3 - 1)];
+                        if (!j1) continue;
+                        const int j = (int)j1 - 1;
+                        if (abs(W.tofb[j] - t) > dt) continue;
+                        row |= 1ull << j;
+                        const unsigned oj = W.tot[j];
+                        if (oj > o || (oj == o && s.index[s0 + j] > ix)) np = true;
+                    }
+                    if (h) { rowB = row; npB = np; } else { rowA = row; npA = np; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    const unsigned rxy = (unsigned)rx | ((unsigned)ry << 8);   // per-byte box radii
+    for (int k = 0; k < (grid ? 0 : L); ++k) {
         const bool kb = k >= 32;
         const int src = k & 31;
         const int kt = __shfl_sync(FULL, kb ? tb : ta, src);
@@ -741,7 +794,7 @@ __global__ void __launch_bounds__(SEGW * 32) k_segments(Sorted s, const long lon
         const bool emit = s.shot[s0] < shot_limit;
         const bool sums = cc && acc && emit;
         if (L > 1 && L <= WREG) {
-            seg_small(s, s0, L, rx, ry, dt, cc, emit, labels, is_peak, rflag, sums ? acc : nullptr, lane);
+            seg_small(s, s0, L, rx, ry, dt, cc, emit, labels, is_peak, rflag, sums ? acc : nullptr, lane, W);
             continue;
         }
         if (L == 1) {
