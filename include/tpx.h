@@ -113,7 +113,11 @@ typedef struct tpx_record {
 typedef struct tpx_counters {
     int64_t packets, pixels, tdcs, corrupt, dropped_pre_trigger, dropped_background,
             kept, clusters, peaks;
-    int64_t status_bits;        /* raw device status word of the last call    */
+    int64_t status_bits;        /* raw device status word of the last call;
+                                   bit 8: the checked build (libtpx_checked.so,
+                                   -DTPX_CHECKED) met an index outside its array
+                                   and skipped the access (tpx_sync then returns
+                                   TPX_EUNSUPPORTED)                          */
     int64_t redone;             /* 1 if tpx_sync redid the last tpx_process
                                    call with the general path                 */
 } tpx_counters;

@@ -46,6 +46,7 @@ enum : unsigned {
     ST_TRIG_CAP = 1u << 5,     // caller trigger buffer too small
     ST_DEVTIMEOUT = 1u << 6,   // a look-back wait ran out
     ST_RUN_REDO = 1u << 7,     // batch: a run needs the general path (see run_failed)
+    ST_BOUNDS = 1u << 8,       // checked build: an index outside its array (the access was skipped)
 };
 
 enum CounterIdx {

@@ -13,6 +13,21 @@ static_assert(T % NT == 0 && C % NT == 0 && T <= C && C <= 16384, "tile geometry
 static_assert(C < 0xFFFF && HB % 2 == 0 && (HB & (HB - 1)) == 0 && HB * 2 <= C * 4, "16-bit hash heads");
 
 // ------------------------------------------------------------------ helpers
+// Checked build (-DTPX_CHECKED): every data-dependent shared-memory or global
+// index (hash chains, member lists, roots, cluster ids, output positions) is
+// tested against its array before use; a violation sets ST_BOUNDS in the
+// status word and skips the access. The normal build compiles the tests away.
+#ifdef TPX_CHECKED
+__device__ __forceinline__ bool in_bounds(long long i, long long n, const Params &p) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&p.ctl->status, ST_BOUNDS);
+    return false;
+}
+#define TPX_IN(i, n) in_bounds((long long)(i), (long long)(n), p)
+#else
+#define TPX_IN(i, n) true
+#endif
+
 __device__ __forceinline__ int pad(int p) { return p + (p >> 3); }   // conflict-free 8-wide walks
 
 // kept-pixel record: [63:40] tof+bias | [39:26] segment | [25:16] ToT | [15:8] y | [7:0] x
@@ -509,7 +524,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 bool is_t = false;
                 if (tid < chunk) {
                     const uint64_t w = __ldcg(p.pk + base + L + tid);
-                    S.buf[pad(L + tid)] = w;
+                    if (TPX_IN(L + tid, C)) S.buf[pad(L + tid)] = w;
                     is_t = (w >> 60) == 0x6u;
                 }
                 if (tid == 0) S.la_first = INT_MAX;
@@ -710,6 +725,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                             const int cy = y + dy;
                             if (cy < 0 || cy > 255) continue;
                             for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                                if (!TPX_IN(j, C)) break;
                                 if (dx == 0 && dy == 0 && (int)j <= q) continue;
                                 const uint64_t rj = S.buf[pad((int)j)];
                                 if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
@@ -740,6 +756,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                                 const int ux = x + dx, uy = y + dy;
                                 if (ux > 255 || uy < 0 || uy > 255) continue;
                                 for (uint32_t jj = S.u1.head[hcell(sg, ux, uy)]; jj != EMPTY; jj = S.u2.next[jj]) {
+                                    if (!TPX_IN(jj, C)) break;
                                     if (dx == 0 && dy == 0 && (int)jj <= q) continue;
                                     const uint64_t rj = S.buf[pad((int)jj)];
                                     if (r_x(rj) != ux || r_y(rj) != uy || r_seg(rj) != sg) continue;
@@ -817,7 +834,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
-                    rootpos[excl++] = (uint16_t)q;
+                    if (TPX_IN(excl, C)) rootpos[excl] = (uint16_t)q;
+                    ++excl;
                     S.u1.mhead[q] = EMPTY;
                 }
             }
@@ -831,7 +849,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             int excl = block_scan_int(S, c, &ncl);
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) S.parent[excl++] = (uint32_t)q;
+                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && !S.notpeak[q]) {
+                    if (TPX_IN(excl, C)) S.parent[excl] = (uint32_t)q;
+                    ++excl;
+                }
             }
         }
 
@@ -873,15 +894,17 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             unsigned long long c_pk = 0;
             for (int q = W0 + tid; q < W1; q += NT) {
                 const uint64_t r = S.buf[pad(q)];
-                const bool kept = q >= R0 && r != INVALID;
+                bool kept = q >= R0 && r != INVALID;
                 uint32_t root = 0;
                 uint8_t pk = 0;
+                if (kept && !TPX_IN(S.u2.rootof[q], C)) kept = false;
                 if (kept) {
                     root = S.u2.rootof[q];
                     pk = S.notpeak[q] ? 0 : 1;
                     c_pk += pk;
                     mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[root], (uint32_t)q);
                 }
+                if (!TPX_IN(base + q, rend)) continue;
                 if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)root : -1LL;
                 if (p.is_peak) p.is_peak[base + q] = pk;
             }
@@ -894,11 +917,13 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             for (int i = tid; i < ncl; i += NT) {
                 if (i >= lim) break;
                 const int q = rootpos[i];
+                if (!TPX_IN(q, C)) continue;
                 const uint64_t r = S.buf[pad(q)];
                 const int tofb0 = r_tof(r);
                 long long s_tot = 0, s_x = 0, s_y = 0, s_t = 0;
                 int n = 0, npk = 0;
                 for (uint32_t m = S.u1.mhead[q]; m != EMPTY; m = mnext[m]) {
+                    if (!TPX_IN(m, C)) break;
                     const uint64_t rm = S.buf[pad((int)m)];
                     const long long tot = r_tot(rm);
                     n += 1;
@@ -930,6 +955,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     pk = S.notpeak[q] ? 0 : 1;
                     c_pk += pk;
                 }
+                if (!TPX_IN(base + q, rend)) continue;
                 if (p.labels) p.labels[base + q] = lab;
                 if (p.is_peak) p.is_peak[base + q] = pk;
             }
@@ -941,6 +967,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             for (int i = tid; i < ncl; i += NT) {
                 if (i >= lim) break;
                 const int q = (int)S.parent[i];
+                if (!TPX_IN(q, C)) continue;
                 const uint64_t r = S.buf[pad(q)];
                 const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
                 long long n = 0, s_tot = 0, s_x = 0, s_y = 0, a2 = 0;
@@ -952,6 +979,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                         const int cy = y + dy;
                         if (cy < 0 || cy > 255) continue;
                         for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                            if (!TPX_IN(j, C)) break;
                             const uint64_t rj = S.buf[pad((int)j)];
                             if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
                             const int d = r_tof(rj) - tb;

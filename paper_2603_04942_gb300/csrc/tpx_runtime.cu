@@ -568,6 +568,8 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return TPX_ECUDA;
     if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
+    // a checked build's index violation stays reported even when the call is redone
+    const unsigned bounds = c->h_ctl->status & tpxk::ST_BOUNDS;
     if ((c->h_ctl->status & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) && !(c->h_ctl->status & tpxk::ST_DEVTIMEOUT) &&
         c->last.valid) {
         // the fused kernel met an input it cannot hold on chip: redo the call
@@ -591,6 +593,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
         if (ckr(cudaStreamSynchronize(c->stream))) return TPX_ECUDA;
     }
     tune_collect(c, redone != 0);
+    c->h_ctl->status |= bounds;
     const tpxk::Ctl &h = *c->h_ctl;
     if (out) {
         out->packets = (int64_t)h.counters[tpxk::C_PACKETS];
@@ -607,6 +610,7 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     }
     const unsigned s = h.status;
     if (s & tpxk::ST_DEVTIMEOUT) return TPX_EDEVTIMEOUT;
+    if (s & tpxk::ST_BOUNDS) return TPX_EUNSUPPORTED;   // checked build: an access was skipped
     // an earlier call since the previous sync needed the general path, which
     // only the last call gets: its outputs are incomplete
     if (sticky) return TPX_EUNSUPPORTED;

@@ -1,0 +1,52 @@
+"""The checked build (-DTPX_CHECKED, libtpx_checked.so): the fused kernel
+tests every data-dependent index (hash chains, member lists, roots, cluster
+ids, output positions) against its array and reports a violation in the
+status word instead of touching memory -- the stand-in for a sanitizer. On
+the parity workloads it reports none, and its results equal the oracle's.
+Runs in a subprocess: a process loads one build of the library."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+SCRIPT = r"""
+import sys
+sys.path[:0] = [ROOT, HERE]
+import paper_2603_04942_gb300 as tpx
+from paper_2603_04942_gb300 import build
+tpx.load(build.build(checked=True))
+import synth
+from gpu_common import assert_parity, gpu_run, oracle_run
+ST_BOUNDS = 1 << 8
+small = synth.generate(synth.small(n_shots=300, pair_frac=0.3, dark_per_shot=2.0))[0]
+dense = synth.generate(synth.small(n_shots=100, particles_per_shot=200.0, pair_frac=0.5))[0]
+high = synth.generate(synth.streaming(10e6, 12))[0]
+cases = [
+    ("cc 4096 tiles", small, dict(tile=tpx.TILE_4096), {}),
+    ("cc 2048 tiles", small, dict(tile=tpx.TILE_2048), {}),
+    ("paper mode", small, dict(mode=tpx.MODE_PAPER), dict(mode=tpx.MODE_PAPER)),
+    ("radius 3", small, dict(rx=3, ry=3), dict(rx=3, ry=3)),
+    ("dense shots", dense, {}, {}),
+    ("shots beyond a range (redo)", high, dict(tof_max=synth.STREAM_TOF_MAX_TICKS),
+     dict(tof_max=synth.STREAM_TOF_MAX_TICKS)),
+]
+for name, pk, gkw, okw in cases:
+    g = gpu_run(pk, **gkw)
+    assert g["status"] == 0, (name, g["status"])
+    assert not (g["counters"]["status_bits"] & ST_BOUNDS), name
+    assert_parity(g, oracle_run(pk, **okw))
+    print("ok", name, flush=True)
+"""
+
+
+def test_checked_build_reports_no_violation_and_matches_the_oracle():
+    code = f"ROOT = {ROOT!r}\nHERE = {HERE!r}\n" + SCRIPT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1500)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+    assert r.stdout.count("ok ") == 6
