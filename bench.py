@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-shots", type=int, default=50_000)
+    ap.add_argument("--cpu-shots-per-core", type=int, default=10_000)
     ap.add_argument("--ref-shots", type=int, default=10_000)
     ap.add_argument("--tile", choices=["default", "4096", "2048"], default="default",
                     help="fused-kernel tile geometry (speed only; results are identical)")
@@ -177,6 +178,52 @@ def cpu_baseline(args, sample_shots: int) -> dict:
     return {"value": tot_h / tot_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {sample_shots:,} shots of the workload ({tot_h:,} pixel hits, {tot_p:,} packets) "
                       f"in 25,000-shot calls, {tot_t:.1f} s single-threaded"}
+
+
+def _oracle_worker(p, shot_begin, n_shots, barrier, out_q):
+    """One process of the parallel CPU baseline: generate its shot range
+    (untimed), wait for the others, time the oracle on it."""
+    import oracle
+    import synth
+    st = synth.Stream(p.replace(shot_begin=shot_begin, n_shots=n_shots, n_threads=1))
+    pk = st.packets()
+    e_pix, e_tdc = st.wrap_counts()
+    st.close()
+    hits = int(((pk >> np.uint64(60)) == 0xB).sum())
+    cfg = oracle.Config(epoch0_pix=e_pix, epoch0_tdc=e_tdc)
+    barrier.wait()
+    t0 = time.perf_counter()
+    r = oracle.run(pk, cfg)
+    out_q.put((time.perf_counter() - t0, hits, int(r["status"])))
+
+
+def cpu_baseline_parallel(args, shots_per_core: int) -> dict:
+    """The same oracle on every host core at once: one process per core,
+    each on its own range of shots (shots are independent; each range gets
+    its wrap counts), started together; throughput = all hits / the slowest
+    process's time."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    p, _ = workload(args)
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n)
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(p, k * shots_per_core, shots_per_core, barrier, q))
+             for k in range(n)]
+    for pr in procs:
+        pr.start()
+    res = [q.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    assert all(r[2] == 0 for r in res)
+    wall = max(r[0] for r in res)
+    hits = sum(r[1] for r in res)
+    return {"value": hits / wall, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} processes x {shots_per_core:,} shots of the workload ({hits:,} pixel hits), one "
+                      f"single-threaded oracle per core started together, slowest {wall:.1f} s"}
 
 
 def stream_bench(args) -> dict:
@@ -611,9 +658,10 @@ def main():
                "d2h_bytes_per_step": 8 * n + CLUSTER_BYTES * ncl_h + 8 * ntr_h + 16,
                "ms_per_step": 1e3 * statistics.mean(tim)}
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args, args.cpu_shots)
+        cpu_par = cpu_baseline_parallel(args, args.cpu_shots_per_core)
     del d_pk
     ctx.close()
     torch.cuda.empty_cache()
@@ -648,7 +696,7 @@ def main():
                                tuning["tile_geometry"], "sampling"),
                            "tile_choice": "autotuned in warm-up" if args.tile == "default" else "fixed by --tile",
                            "generation_s": round(t_gen, 1)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk,
+                "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_par, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk,
                 "refiner": refiner, "clocks": clk,
                 "gpu_launches": 2 * args.steps - 1,   # fused kernels + status carries between unsynchronised calls
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
