@@ -322,10 +322,11 @@ def batch_bench(args) -> dict:
     n = int(offs[-1])
     shots = sum(p.n_shots for p in runs)
     expect = sum(p.n_shots * p.particles_per_shot for p in runs)
-    ctx = tpx.Context(tpx.Config(), max_packets=max(1, n))
+    s = torch.cuda.Stream()   # a stream of its own: the call is also captured into a CUDA graph below
+    ctx = tpx.Context(tpx.Config(), max_packets=max(1, n), stream=s)
     out = ctx.alloc_batch_outputs(n, len(runs), labels=False, is_peak=False,
                                   cluster_capacity=int(1.3 * expect) + (1 << 20), trig_capacity=shots + 16)
-    s = ctx.stream
+    torch.cuda.synchronize()
     for _ in range(max(3, min(args.warmup, 3))):
         ctx.tpx_process_batch(d_pk, offs, out)
         rc, counters = ctx.tpx_sync(check=False)
@@ -353,6 +354,22 @@ def batch_bench(args) -> dict:
     tiles_ms = ev0.elapsed_time(ev1)
     rc2, _ = ctx.tpx_sync(check=False)
     assert rc2 == 0, rc2
+    # the same call captured once into a CUDA graph, then replayed (the run
+    # tables' upload and the persistent kernel), each replay with its tpx_sync
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        ctx.tpx_process_batch(d_pk, offs, out)
+    graph_ms = []
+    for k in range(steps):
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            g.replay()
+        rc3, c3 = ctx.tpx_sync(check=False)
+        torch.cuda.synchronize()
+        graph_ms.append(1e3 * (time.perf_counter() - t0))
+        assert rc3 == 0 and c3["redone"] == counters["redone"], (rc3, c3)
+    assert int(out["n_clusters"].item()) > 0
+    del g
     tune = ctx.tpx_tuning()
     n_cl = int(out["n_clusters"].item())
     res = {"workload": f"{len(runs)} independent runs, one launch per step: shots log-uniform 10-10^4, Poisson "
@@ -362,6 +379,9 @@ def batch_bench(args) -> dict:
            "value": counters["pixels"] * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
            "timing": "wall clock per whole call (launch + tpx_sync, redone runs included), device synchronised",
            "tiles_pass_ms": tiles_ms,
+           "graph": {"ms_per_step": sum(graph_ms) / steps,
+                     "value": counters["pixels"] * steps / (sum(graph_ms) / 1e3),
+                     "timing": "the call captured once into a CUDA graph; per step one replay + tpx_sync"},
            "runs": len(runs), "shots": shots, "packets": n, "pixel_hits": counters["pixels"], "clusters": n_cl,
            "redone_runs": counters["redone"], "steps": steps, "warmup": 3,
            "tile_geometry": {1: "4096-packet tiles", 2: "2048-packet tiles"}.get(tune["tile_geometry"], "sampling"),

@@ -379,6 +379,14 @@ int tpx_refine_decide(tpx_ctx *ctx, const float *d_out, const tpx_record *d_clus
    itself waits only until the previous batch's tables have been uploaded.
    The first call for a larger batch grows the context's batch scratch.
    Counters describe the tiles' pass (redone runs included as they ran).
+   CUDA graphs: the call may be captured on the context's stream (relaxed
+   capture mode, after one ordinary batch call on the context so that its
+   kernels are set up); a captured call keeps device and pinned host tables
+   of its own for the graph (freed with the context), and each replay
+   re-uploads its run tables and launches the one persistent kernel.  Call
+   tpx_sync after each replay (runs that need the general path are redone
+   there, outside the graph), replay on the same context, and do not call
+   tpx_reserve between capture and replay.
    TPX_EINVAL for bad offsets or pointers. */
 int tpx_process_batch(tpx_ctx *ctx, const uint64_t *d_packets, const int64_t *h_run_offsets, int64_t n_runs,
                       int64_t *d_labels, uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cluster_capacity,

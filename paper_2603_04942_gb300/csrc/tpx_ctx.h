@@ -110,6 +110,10 @@ struct tpx_ctx {
         int64_t trig_cap;
         int64_t *n_trig;
         int64_t redone;           // runs redone by the last tpx_sync
+        const int64_t *h_off;     // run offsets of the last batch call (its host table)
+        // calls captured into a CUDA graph get tables of their own (the graph
+        // reads them at every replay); freed with the context
+        struct Owned { void *dev; void *host; Owned *next; } *graph_owned;
     } batch;
 };
 

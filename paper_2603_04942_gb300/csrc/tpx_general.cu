@@ -1575,7 +1575,7 @@ int redo_batch(tpx_ctx *c, int64_t *n_redone) {
     auto &B = c->batch;
     cudaStream_t s = c->stream;
     const int64_t R = B.n_runs;
-    const int64_t *off = B.h_tab;   // the run offsets of the call (host)
+    const int64_t *off = B.h_off;   // the run offsets of the call (host)
     *n_redone = 0;
     std::vector<unsigned> failed((size_t)R);
     std::vector<int64_t> roff((size_t)R + 1), toff((size_t)R + 1);
@@ -1787,6 +1787,7 @@ int redo_batch(tpx_ctx *c, int64_t *n_redone) {
         rc = ck(cudaMemcpyAsync(&cur, c->ctl, sizeof cur, cudaMemcpyDeviceToHost, s));
         if (!rc) rc = ck(cudaStreamSynchronize(s));
         snap.status |= cur.status & ST_TRIG_ORDER;   // a redone run may have decreasing triggers
+        snap.status &= ~ST_RUN_REDO;                 // done: a later sync has nothing to redo
         if (!rc) rc = ck(cudaMemcpyAsync(B.bt.run_rec_off, NO.data(), 8 * (size_t)(R + 1), cudaMemcpyHostToDevice, s));
         if (!rc) rc = ck(cudaMemcpyAsync(B.bt.run_trig_off, NTo.data(), 8 * (size_t)(R + 1), cudaMemcpyHostToDevice, s));
         if (!rc) rc = ck(cudaMemcpyAsync(B.n_cl, &NO[(size_t)R], 8, cudaMemcpyHostToDevice, s));

@@ -283,6 +283,13 @@ int tpx_destroy(tpx_ctx *c) {
         if (c->pipe.trig[b]) cudaFree(c->pipe.trig[b]);
     }
     if (c->batch.tab_copied) cudaEventDestroy(c->batch.tab_copied);
+    for (auto *o = c->batch.graph_owned; o;) {
+        auto *nx = o->next;
+        cudaFree(o->dev);
+        cudaFreeHost(o->host);
+        delete o;
+        o = nx;
+    }
     if (c->batch.dev) cudaFree(c->batch.dev);
     if (c->batch.h_tab) cudaFreeHost(c->batch.h_tab);
     delete c;
@@ -437,7 +444,28 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     const size_t need_dev = al(4 * (size_t)n_tiles) + al(8 * (size_t)n_runs) + al(8 * (size_t)(n_runs + 1)) +
                             al(4 * (size_t)n_runs) + 4 * al(8 * (size_t)n_tiles) + al(8 * (size_t)(grid * T)) +
                             2 * al(4 * (size_t)n_tiles) + 2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles);
-    if (need_dev > B.dev_bytes) {
+    const size_t need_host = 8 * (size_t)(n_runs + 1) + 8 * (size_t)n_runs + 4 * (size_t)n_tiles + 64;
+    // a call captured into a CUDA graph (relaxed capture mode) gets its own
+    // device tables and pinned host tables, kept for the graph's replays
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (ckr(cudaStreamIsCapturing(s, &cap))) return TPX_ECUDA;
+    const bool capturing = cap == cudaStreamCaptureStatusActive;
+    void *dev = nullptr;
+    int64_t *h_tab = nullptr;
+    if (capturing) {
+        auto *o = new (std::nothrow) tpx_ctx::Batch::Owned{nullptr, nullptr, B.graph_owned};
+        if (!o) return TPX_ENOMEM;
+        if (cudaMalloc(&o->dev, need_dev) != cudaSuccess || cudaMallocHost(&o->host, need_host) != cudaSuccess) {
+            cudaGetLastError();
+            if (o->dev) cudaFree(o->dev);
+            delete o;
+            return TPX_ENOMEM;
+        }
+        B.graph_owned = o;
+        dev = o->dev;
+        h_tab = static_cast<int64_t *>(o->host);
+    }
+    if (!capturing && need_dev > B.dev_bytes) {
         if (ckr(cudaStreamSynchronize(s))) return TPX_ECUDA;
         if (B.dev) cudaFree(B.dev);
         B.dev = nullptr;
@@ -446,18 +474,21 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
         if (ckr(cudaMemset(B.dev, 0, need_dev))) return TPX_ECUDA;   // fresh flags
         B.dev_bytes = need_dev;
     }
-    const size_t need_host = 8 * (size_t)(n_runs + 1) + 8 * (size_t)n_runs + 4 * (size_t)n_tiles + 64;
-    if (B.h_tab) {   // the previous batch's tables may still be uploading
+    if (!capturing && B.h_tab) {   // the previous batch's tables may still be uploading
         if (ckr(cudaEventSynchronize(B.tab_copied))) return TPX_ECUDA;
     }
-    if (need_host > B.h_bytes) {
+    if (!capturing && need_host > B.h_bytes) {
         if (B.h_tab) cudaFreeHost(B.h_tab);
         B.h_tab = nullptr;
         B.h_bytes = 0;
         if (cudaMallocHost(&B.h_tab, need_host) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
         B.h_bytes = need_host;
     }
-    char *m = static_cast<char *>(B.dev);
+    if (!capturing) {
+        dev = B.dev;
+        h_tab = B.h_tab;
+    }
+    char *m = static_cast<char *>(dev);
     auto take = [&](size_t bytes) { char *r = m; m += al(bytes); return r; };
     tpxk::BatchTable &bt = B.bt;
     bt.tile_run = reinterpret_cast<int *>(take(4 * (size_t)n_tiles));
@@ -477,8 +508,8 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     bt.run_trig_off = reinterpret_cast<long long *>(d_run_trig);
     bt.n_runs = n_runs;
     // the tables, built on the host and uploaded from pinned memory
-    int64_t *h_off = B.h_tab, *h_t0 = B.h_tab + (n_runs + 1);
-    int *h_tr = reinterpret_cast<int *>(B.h_tab + (n_runs + 1) + n_runs);
+    int64_t *h_off = h_tab, *h_t0 = h_tab + (n_runs + 1);
+    int *h_tr = reinterpret_cast<int *>(h_tab + (n_runs + 1) + n_runs);
     std::memcpy(h_off, h_run_offsets, 8 * (size_t)(n_runs + 1));
     int64_t g = 0;
     for (int64_t r = 0; r < n_runs; ++r) {
@@ -495,7 +526,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
         cudaMemcpyAsync(const_cast<int *>(bt.tile_run), h_tr, 4 * (size_t)n_tiles, cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
         return TPX_ECUDA;
-    if (ckr(cudaEventRecord(B.tab_copied, s))) return TPX_ECUDA;
+    if (!capturing && ckr(cudaEventRecord(B.tab_copied, s))) return TPX_ECUDA;
     // the scratch layout follows the tile count: start every call's flags at zero
     if (ckr(cudaMemsetAsync(B.ts.flags, 0, 4 * (size_t)n_tiles, s)) ||
         ckr(cudaMemsetAsync(B.ts.cflags, 0, 4 * (size_t)n_tiles, s)))
@@ -553,6 +584,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     B.trig = d_trig;
     B.trig_cap = trig_cap;
     B.n_trig = d_n_trig;
+    B.h_off = h_off;
     return TPX_OK;
 }
 
@@ -585,8 +617,9 @@ int tpx_sync(tpx_ctx *c, tpx_counters *out) {
     if ((c->h_ctl->status & tpxk::ST_RUN_REDO) && !(c->h_ctl->status & tpxk::ST_DEVTIMEOUT) && c->batch.last) {
         // runs of the last batch that the tiles could not hold: redo them
         // exactly with the general path and splice their outputs in
+        // (the batch stays the last call: a CUDA-graph replay of it sets the
+        // redo bit again; the redo clears it, so a second sync does not redo)
         const int rc = tpxg::redo_batch(c, &redone);
-        c->batch.last = false;
         if (rc) return rc;
         if (cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(tpxk::Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             return TPX_ECUDA;

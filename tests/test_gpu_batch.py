@@ -135,3 +135,43 @@ def test_bad_offsets_rejected():
                 ctx.tpx_process_batch(d, offs, out)
     finally:
         ctx.close()
+
+
+def test_batch_captured_in_a_cuda_graph_replays_exactly():
+    """The batched launch captured into a CUDA graph: every replay (run
+    tables uploaded, one persistent kernel; the long-shot run redone at
+    tpx_sync) gives the eager call's outputs, and eager calls still work
+    after the capture."""
+    import torch
+    pk, offs = make_batch(n_runs=24, seed=9)
+    s = torch.cuda.Stream()
+    ctx = tpx.Context(tpx.Config(tile_geometry=tpx.TILE_4096), max_packets=pk.size, stream=s)
+    try:
+        d = to_device(pk)
+        kw = dict(labels=True, is_peak=True, cluster_capacity=max(16, pk.size), trig_capacity=max(16, pk.size))
+        with torch.cuda.stream(s):
+            ref_out = ctx.alloc_batch_outputs(pk.size, offs.size - 1, **kw)
+            out = ctx.alloc_batch_outputs(pk.size, offs.size - 1, **kw)
+        ctx.tpx_process_batch(d, offs, ref_out)
+        rc, cnt = ctx.tpx_sync(check=False)
+        ref = ctx.collect_batch(ref_out, rc, cnt)
+        assert rc == 0 and cnt["redone"] >= 1
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+            ctx.tpx_process_batch(d, offs, out)
+        for _ in range(3):
+            with torch.cuda.stream(s):             # the context's stream: tpx_sync waits on it
+                out["labels"].fill_(-7)
+                g.replay()
+            rc, cnt = ctx.tpx_sync(check=False)
+            r = ctx.collect_batch(out, rc, cnt)
+            assert rc == 0 and cnt["redone"] == ref["counters"]["redone"]
+            assert np.array_equal(r["labels"], ref["labels"]) and np.array_equal(r["is_peak"], ref["is_peak"])
+            assert np.array_equal(r["run_clusters"], ref["run_clusters"])
+            assert np.array_equal(r["run_trig"], ref["run_trig"]) and np.array_equal(r["triggers"], ref["triggers"])
+            assert_clusters_equal(r["clusters"], ref["clusters"])
+        ctx.tpx_process_batch(d, offs, ref_out)            # an ordinary call after the capture
+        rc, cnt = ctx.tpx_sync(check=False)
+        assert rc == 0 and np.array_equal(ctx.collect_batch(ref_out, rc, cnt)["labels"], ref["labels"])
+    finally:
+        ctx.close()
