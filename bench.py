@@ -676,7 +676,8 @@ def main():
         e2e = {"value": float(h_all.item()) / float(e_t.item()), "unit": UNIT,
                "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": 8 * n + CLUSTER_BYTES * ncl_h + 8 * ntr_h + 16,
-               "ms_per_step": 1e3 * statistics.mean(tim)}
+               "ms_per_step": 1e3 * statistics.mean(tim),
+               "step_ms": {"min": 1e3 * min(tim), "median": 1e3 * statistics.median(tim), "max": 1e3 * max(tim)}}
 
     cpu = cpu_par = None
     if rank == 0 and not args.no_cpu:
