@@ -718,6 +718,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (r != INVALID) {
                     const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
                     bool dim = false;
+                    // 8-neighbour box: a diagonal partner (dx = 1, dy = -1 or +1) is
+                    // held back and needs no union when the pixel's partner to the
+                    // side (dx = 1, dy = 0), or above it (dx = 0, dy = +1) for
+                    // dy = +1, is adjacent to it as well: that path of two
+                    // axis-aligned pairs, which are never held back, joins them
+                    const bool box1 = MODE == TPX_MODE_CC && p.rx == 1 && p.ry == 1;
+                    uint32_t hold = 0xFFFFFFFFu;   // held partners: dy = -1 low half, dy = +1 high half
+                    int tA = 0, tB = 0, tE = INT_MIN, tN = INT_MIN;
                     for (int dx = 0; dx <= p.rx; ++dx) {
                         const int cx = x + dx;
                         if (cx > 255) break;
@@ -735,6 +743,19 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                                 // local maxima: equal ToT goes to the later pixel (Sec. V.B)
                                 if (tj > tot || (tj == tot && (int)j > q)) dim = true;
                                 else S.notpeak[j] = 1;
+                                if (box1) {
+                                    const int tjt = r_tof(rj);
+                                    if (dx == 1 && dy == 0 && tE == INT_MIN) tE = tjt;
+                                    if (dx == 0 && dy == 1 && tN == INT_MIN) tN = tjt;
+                                    if (dx == 1 && dy != 0) {
+                                        const int sh = dy > 0 ? 16 : 0;
+                                        if (((hold >> sh) & 0xFFFFu) == 0xFFFFu) {
+                                            hold = (hold & ~(0xFFFFu << sh)) | ((uint32_t)j << sh);
+                                            if (dy > 0) tB = tjt; else tA = tjt;
+                                            continue;
+                                        }
+                                    }
+                                }
                                 if (MODE == TPX_MODE_CC) {
                                     if (ne < 4) eb0 |= (uint64_t)j << (16 * ne);
                                     else if (ne < 8) eb1 |= (uint64_t)j << (16 * (ne - 4));
@@ -742,6 +763,19 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                                     ++ne;
                                 }
                             }
+                        }
+                    }
+                    if (box1) {
+                        const uint32_t jA = hold & 0xFFFFu, jB = hold >> 16;
+                        const bool skipA = tE != INT_MIN && abs(tE - tA) <= p.dt;
+                        const bool skipB = (tE != INT_MIN && abs(tE - tB) <= p.dt) || (tN != INT_MIN && abs(tN - tB) <= p.dt);
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t jh = h ? jB : jA;
+                            if (jh == 0xFFFFu || (h ? skipB : skipA)) continue;
+                            if (ne < 4) eb0 |= (uint64_t)jh << (16 * ne);
+                            else if (ne < 8) eb1 |= (uint64_t)jh << (16 * (ne - 4));
+                            else overflow = true;
+                            ++ne;
                         }
                     }
                     if (dim) S.notpeak[q] = 1;
