@@ -558,6 +558,17 @@ def run_reference(args):
     return 0
 
 
+def _section(fn, *a):
+    """A secondary part of the line: a failure there is reported in the line
+    (and on stderr) instead of losing the main measurement."""
+    try:
+        return fn(*a)
+    except (Exception, SystemExit) as e:   # noqa: BLE001
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"[:500]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -681,27 +692,28 @@ def main():
 
     cpu = cpu_par = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(args, args.cpu_shots)
-        cpu_par = cpu_baseline_parallel(args, args.cpu_shots_per_core)
+        cpu = _section(cpu_baseline, args, args.cpu_shots)
+        cpu_par = _section(cpu_baseline_parallel, args, args.cpu_shots_per_core)
     del d_pk
     ctx.close()
     torch.cuda.empty_cache()
     stream = None
     if rank == 0 and not args.no_stream:
-        stream = stream_bench(args)
+        stream = _section(stream_bench, args)
     batch = None
     if rank == 0 and not args.no_batch:
-        batch = batch_bench(args)
+        batch = _section(batch_bench, args)
     timewalk = None
     if rank == 0 and not args.no_timewalk:
-        timewalk = timewalk_bench(args)
+        timewalk = _section(timewalk_bench, args)
     refiner = None
     if rank == 0 and not args.no_refiner:
         torch.cuda.empty_cache()
-        refiner = refiner_bench(args)
-        # the main path's cluster rate: the budget the refiner's inference is held to
-        refiner["main_path_clusters_per_s"] = value * n_cl / max(1, hits) / world
-        refiner["infer"]["vs_main_path"] = refiner["infer"]["clusters_per_s"] / refiner["main_path_clusters_per_s"]
+        refiner = _section(refiner_bench, args)
+        if "error" not in refiner:
+            # the main path's cluster rate: the budget the refiner's inference is held to
+            refiner["main_path_clusters_per_s"] = value * n_cl / max(1, hits) / world
+            refiner["infer"]["vs_main_path"] = refiner["infer"]["clusters_per_s"] / refiner["main_path_clusters_per_s"]
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
