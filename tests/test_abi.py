@@ -75,3 +75,21 @@ def test_product_path_has_no_oracle_import():
                 txt = open(os.path.join(root, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "tpx_oracle" not in txt, f
+
+
+def test_refiner_and_stream_host_calls(libpath):
+    """Host-only entry points of the later additions: sizes and argument checks."""
+    L = tpx.load(libpath)
+    # 162 -> 160 -> 160 -> 6 with biases: 52,806 parameters; bf16 packing for 64/128/160 only
+    assert L.tpx_refiner_params(160) == 162 * 160 + 160 + 160 * 160 + 160 + 160 * 6 + 6 == 52806
+    assert L.tpx_refiner_params(0) == 0
+    assert L.tpx_refiner_packed_bytes(160) > 0 and L.tpx_refiner_packed_bytes(128) > 0
+    assert L.tpx_refiner_packed_bytes(100) == 0
+    assert L.tpx_refiner_pack(None, None, 160, None) == tpx.EINVAL
+    assert L.tpx_refiner_infer(None, None, 160, None, 0, None) == tpx.EINVAL
+    assert L.tpx_refine_decide(None, None, None, None, None, 0, ctypes.c_float(0.5), None) == tpx.EINVAL
+    assert L.tpx_debug_hold_tile(None, 3) == tpx.EINVAL
+    assert L.tpx_stream_snapshot_bytes(None) == 0
+    w = ctypes.c_int64()
+    assert L.tpx_stream_snapshot(None, None, 0, ctypes.byref(w)) == tpx.EINVAL
+    assert L.tpx_stream_restore(None, None, 0) == tpx.EINVAL
