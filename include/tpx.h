@@ -177,11 +177,20 @@ int tpx_process(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets,
                 tpx_record *d_clusters, int64_t cluster_capacity, int64_t *d_n_clusters,
                 int64_t *d_trig_t, int64_t trig_capacity, int64_t *d_n_trig);
 
-/* The same with host buffers: copies h_packets to the device, processes and
-   copies results back, all on the context stream, and synchronises.
-   h_labels / h_is_peak may be NULL.  *h_n_clusters and *h_n_trig receive the
-   counts.  Device staging comes from the context's scratch (tpx_reserve),
-   so it allocates nothing either.  Returns the tpx_sync status. */
+/* The same with host buffers: copies h_packets to the device, processes
+   them, copies the results back and synchronises.  h_labels / h_is_peak may
+   be NULL.  *h_n_clusters and *h_n_trig receive the counts (the required
+   ones when a buffer is short: TPX_EOVERFLOW).  Device staging is allocated
+   on first use and kept by the context, grown for a larger call.  A call of
+   at least 2^24 packets on a context without a carried state (chain = 0, no
+   tpx_set_state) is pipelined: cut into up to 16 pieces at trigger packets,
+   chained through the unwrap state on the device, each piece's copy in
+   overlapping the previous piece's kernel and its labels and records going
+   out behind it (two more CUDA streams); a piece whose kernel meets anything
+   it cannot hold -- a pixel after a cut that belongs in time to the shot
+   before it is one -- sends the whole call back to the one-piece path, so
+   the result always equals one call's.  Pinned host buffers let the copies
+   overlap.  Returns the tpx_sync status. */
 int tpx_process_host(tpx_ctx *ctx, const uint64_t *h_packets, int64_t n_packets,
                      int64_t packet_index_base, int64_t *h_labels, uint8_t *h_is_peak,
                      tpx_record *h_clusters, int64_t cluster_capacity, int64_t *h_n_clusters,
