@@ -12,9 +12,11 @@
  *
  * Conventions
  *   - Pointers named d_* are device pointers; h_* are host pointers.  The
- *     caller owns every buffer it passes in; the context owns its scratch,
- *     which is sized once by tpx_create / tpx_reserve.  No call on the
- *     processing path allocates device memory.
+ *     caller owns every buffer it passes in; the context owns its scratch.
+ *     The fused path's scratch is sized by tpx_create / tpx_reserve, and
+ *     tpx_process allocates nothing (tpx_process_noalloc not even scratch);
+ *     the host-buffer, batch, general-path, streaming and refiner calls grow
+ *     the context's scratch on demand and keep it for later calls.
  *   - Calls are asynchronous on the context's CUDA stream.  Device-side
  *     conditions (capacity, corrupt input, timeouts) are latched into a
  *     status word that tpx_sync() reads; the kernels never trap.
