@@ -389,3 +389,29 @@ def test_slice_continuing_a_stream_across_a_wrap():
     cfg = oracle.Config(epoch0_pix=1, epoch0_tdc=0, prev_pix_raw=(P + 300) % P, prev_tdc_raw=P - 100_000)
     part = oracle.run(pk[4:], cfg, want_info=True)["info"]["t"]
     assert list(part) == list(full[4:]) == true[3:]
+
+
+def test_literal_tie_break_diverges_only_past_position_1000():
+    """Sec. V.B's +0.001 * position tie-break, literally, against the exact
+    (ToT, position) reading: equal on ties and below position 1000; past it
+    the literal key lets a dimmer, later pixel beat a brighter neighbour."""
+    import oracle.tiebreak as tb
+    adj = np.array([[0, 1], [1, 0]], bool)
+    # a tie: the later pixel wins under both readings
+    assert list(tb.maxima_literal([50, 50], [3, 7], adj)) == list(tb.maxima_exact([50, 50], [3, 7], adj)) == [False, True]
+    # brighter earlier pixel, positions below 1000: the readings agree
+    assert list(tb.maxima_literal([101, 100], [0, 999], adj)) == list(tb.maxima_exact([101, 100], [0, 999], adj)) == [True, False]
+    # past position 1000 the literal key flips the order of two ToT values
+    assert list(tb.maxima_exact([101, 100], [0, 1500], adj)) == [True, False]
+    assert list(tb.maxima_literal([101, 100], [0, 1500], adj)) == [False, True]
+    # the oracle follows the exact reading on such a pair (a shot of 1,501 pixels)
+    b = StreamBuilder()
+    b.tdc(1000)
+    for k in range(1499):                     # far-away filler pixels, one per position
+        b.pix(200 + (k % 40), 200 + (k // 40) % 40, 20, 2000 + 40 * k)
+    b.pix(10, 10, 101, 3000)                  # the brighter pixel, stream position 1500
+    b.pix(10, 11, 100, 3001)                  # its dimmer neighbour, stream position 1501
+    pk = b.packets()
+    r = oracle.run(pk)
+    assert r["labels"][1500] >= 0 and r["labels"][1501] == r["labels"][1500]
+    assert r["is_peak"][1500] == 1 and r["is_peak"][1501] == 0
