@@ -207,7 +207,7 @@ def cpu_baseline_parallel(args, shots_per_core: int) -> dict:
     import oracle
     oracle.build()
     p, _ = workload(args)
-    n = os.cpu_count() or 1
+    n = min(64, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(n)
     q = ctx.Queue()
