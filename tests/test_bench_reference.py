@@ -23,3 +23,16 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_cpu_baselines_on_small_samples():
+    """Both CPU-baseline legs of the line (single-threaded, and one process
+    per core started together) run on small samples of the workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sys.argv = ["bench.py", "--shots", "4000"]
+    args = bench.parse()
+    one = bench.cpu_baseline(args, 300)
+    allc = bench.cpu_baseline_parallel(args, 200)
+    assert one["cores"] == 1 and one["value"] > 0 and one["kind"] == "oracle"
+    assert allc["cores"] >= 1 and allc["value"] > 0 and "processes" in allc["sample"]
