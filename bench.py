@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--shots", type=int, default=1_000_000)
     ap.add_argument("--variant", choices=["literal", "stated"], default="literal")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--parity-shots", type=int, default=10_000,
+                    help="shots per range of the sampled oracle check of the timed call")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-shots", type=int, default=50_000)
     ap.add_argument("--cpu-shots-per-core", type=int, default=10_000)
@@ -161,6 +164,90 @@ def oracle_timed(p, shot_begin: int, n_shots: int) -> tuple[float, int, int]:
     dt = time.perf_counter() - t0
     assert r["status"] == 0, r["status"]
     return dt, hits, pk.size
+
+
+FIRST_TDC_WRAP_SHOT = 81_031   # first trigger at or after 2^36 ticks on the recipe's time line
+
+
+def sample_ranges(n_shots: int, k: int) -> list[tuple[int, int]]:
+    """Shot ranges of k shots checked against the oracle: the start of the
+    stream (the first pixel wrap, shot 500), the first TDC wrap (also a pixel
+    wrap), and the end of the stream (the last tiles)."""
+    k = min(k, n_shots)
+    want = [0, FIRST_TDC_WRAP_SHOT - k // 2, n_shots - k]
+    out = []
+    for s0 in want:
+        s0 = max(0, min(s0, n_shots - k))
+        if (s0, s0 + k) not in out:
+            out.append((s0, s0 + k))
+    return out
+
+
+def parity_sampled(p, h_pk, d_pk, out, n_cl: int, n_shots: int, k: int) -> dict:
+    """The timed call's outputs against the oracle on sampled shot ranges.
+    A range [s0, s1) is the packets from trigger s0's TDC packet to trigger
+    s1's; it is regenerated independently (and must equal that part of the
+    stream), and the oracle runs on it from the wrap counts at its start. The
+    triggers of the range, the records of its shots (all but the last, whose
+    late pixels may follow the range) and the labels of their pixels must
+    equal the oracle's: integers bit for bit, centroids within 1e-6."""
+    import torch
+
+    import oracle
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    oracle.build()
+    tdc_pos = torch.nonzero((d_pk >> 60) == 6).flatten().cpu().numpy()
+    assert tdc_pos.size == n_shots, (tdc_pos.size, n_shots)
+    rec_i64 = out["clusters"][: n_cl * CLUSTER_BYTES].view(torch.int64).view(n_cl, CLUSTER_BYTES // 8)
+    rec_label = rec_i64[:, 0].contiguous()
+    a_pk = h_pk.numpy().view(np.uint64)
+    n = a_pk.size
+    res = {"ranges": [], "ok": True, "records": 0, "labels": 0, "triggers": 0}
+    for s0, s1 in sample_ranges(n_shots, k):
+        a = 0 if s0 == 0 else int(tdc_pos[s0])
+        b = n if s1 >= n_shots else int(tdc_pos[s1])
+        st = synth.Stream(p.replace(shot_begin=s0, n_shots=s1 - s0))
+        pk = st.packets()
+        e_pix, e_tdc = st.wrap_counts()
+        st.close()
+        ok = pk.size == b - a and np.array_equal(pk, a_pk[a:b])
+        o = oracle.run(pk, oracle.Config(epoch0_pix=e_pix, epoch0_tdc=e_tdc), idx_base=a)
+        ok = ok and o["status"] == 0
+        last = s1 - 1 if s1 >= n_shots else s1 - 2      # the last shot compared
+        # triggers
+        g_tr = out["trig"][s0:s1].cpu().numpy()
+        ok = ok and np.array_equal(g_tr, o["triggers"])
+        # records of shots [s0, last]: their labels lie in [a, b)
+        i0, i1 = (int(v) for v in torch.searchsorted(rec_label, torch.tensor([a, b], device=rec_label.device)))
+        g_cl = np.frombuffer(out["clusters"][i0 * CLUSTER_BYTES: i1 * CLUSTER_BYTES].cpu().numpy().tobytes(),
+                             tpx.CLUSTER_DTYPE)
+        g_cl = g_cl[(g_cl["shot"] >= s0) & (g_cl["shot"] <= last)]
+        o_cl = o["clusters"].copy()
+        o_cl["shot"] += s0
+        o_cl = o_cl[o_cl["shot"] <= last]
+        ok = ok and g_cl.size == o_cl.size and g_cl.size > 0
+        if ok:
+            for f in ("label", "shot", "t0", "s_tot", "s_x", "s_y", "s_t", "n", "n_peaks"):
+                ok = ok and np.array_equal(g_cl[f], o_cl[f])
+            for f in ("x", "y", "tof"):
+                ok = ok and bool(np.all(np.abs(g_cl[f] - o_cl[f]) <= 1e-6))
+        # labels of the pixels of those records
+        g_lab = out["labels"][a:b].cpu().numpy()
+        o_lab = o["labels"]
+        sel = o_lab >= 0
+        pos = np.searchsorted(o_cl["label"], o_lab[sel])
+        inside = (pos < o_cl.size) & (o_cl["label"][np.minimum(pos, max(o_cl.size - 1, 0))] == o_lab[sel])
+        m = np.zeros(o_lab.size, bool)
+        m[np.flatnonzero(sel)[inside]] = True
+        ok = ok and bool(np.array_equal(g_lab[m], o_lab[m])) and int(m.sum()) > 0
+        res["ranges"].append({"shots": [s0, s1], "packets": [a, b], "records": int(o_cl.size),
+                              "labels": int(m.sum()), "wraps_at_start": [int(e_pix), int(e_tdc)], "ok": bool(ok)})
+        res["records"] += int(o_cl.size)
+        res["labels"] += int(m.sum())
+        res["triggers"] += int(g_tr.size)
+        res["ok"] = res["ok"] and bool(ok)
+    return res
 
 
 def cpu_baseline(args, sample_shots: int) -> dict:
@@ -647,6 +734,11 @@ def main():
         dist.all_reduce(h_all, op=dist.ReduceOp.SUM)
     value = float(h_all.item()) / (float(t_max.item()) / 1e3)
 
+    # sampled oracle parity of the timed call's outputs
+    parity = None
+    if not args.no_parity:
+        parity = _section(parity_sampled, p, h_pk, d_pk, out, n_cl, n_tr, args.parity_shots)
+
     # roofline of the fused kernel (the only kernel of a step)
     pk_info, peak_kind = peaks()
     alg_bytes = 8 * n + 8 * n + CLUSTER_BYTES * n_cl + 8 * n_tr
@@ -729,6 +821,8 @@ def main():
                                tuning["tile_geometry"], "sampling"),
                            "tile_choice": "autotuned in warm-up" if args.tile == "default" else "fixed by --tile",
                            "generation_s": round(t_gen, 1)},
+                "parity_sampled": None if parity is None else (parity.get("ok") is True),
+                "parity": parity,
                 "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_par, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk,
                 "refiner": refiner, "clocks": clk,
                 "gpu_launches": 2 * args.steps - 1,   # fused kernels + status carries between unsynchronised calls
@@ -737,6 +831,9 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    if parity is not None and parity.get("ok") is not True:
+        print(f"sampled oracle parity failed: {json.dumps(parity)[:2000]}", file=sys.stderr)
+        return 1
     return 0
 
 

@@ -263,21 +263,27 @@ int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
 
 /* The fused path without any device allocation (no counterpart in the paper;
    it serves callers that cannot call cudaMalloc where they process data --
-   code running while a CUDA graph is captured, real-time acquisition loops that
-   must not block in the allocator, hosts that fix the library's memory up
-   front).  Same inputs, outputs and results as tpx_process, but no context:
-   the configuration and the CUDA stream are passed directly, and the
-   look-back scratch is one fixed array in device memory that is part of the
-   library (about 2.4 MB per device that loads it, held until exit).
-   The first call on each device, with that device current, looks up the
-   array's device address (cudaGetSymbolAddress); make that first call before
-   any stream capture.  All calls on a device share the array and it keeps the
-   last call's contents (the per-call control block is cleared first): calls
-   that overlap on the GPU race and must not be made.  The call synchronises
-   the stream and returns the status that tpx_sync would; if h_counters is not
-   NULL it receives the counters.
+   real-time acquisition loops that must not block in the allocator, hosts
+   that fix the library's memory up front).  Same inputs and outputs as
+   tpx_process, but no context: the configuration and the CUDA stream are
+   passed directly, and the look-back scratch is one fixed array in device
+   memory that is part of the library (about 2.4 MB per device that loads it,
+   held until exit).  The first call on each device, with that device current,
+   looks up the array's device address (cudaGetSymbolAddress).  All calls on a
+   device share the array and it keeps the last call's contents (the per-call
+   control block is cleared first): calls that overlap on the GPU race and
+   must not be made.  The call reads the device status back and synchronises
+   the stream before it returns, so it must not be made on a stream that is
+   being captured into a CUDA graph.  If h_counters is not NULL it receives
+   the counters.
+   Results equal tpx_process's when the fused kernel can hold the input.  The
+   call has no redo: where tpx_sync would redo a call with the general path (a
+   shot longer than the 8192-position range of the 4096-packet tiles, or a
+   pixel whose trigger lies outside its range), this call returns
+   TPX_EUNSUPPORTED and its outputs are incomplete.
    Errors: TPX_EINVAL for a bad configuration or argument, or n_packets above
-   TPX_NOALLOC_MAX_PACKETS; then the status codes of tpx_sync. */
+   TPX_NOALLOC_MAX_PACKETS; TPX_EUNSUPPORTED as above; TPX_EDEVTIMEOUT,
+   TPX_ECORRUPT, TPX_EOVERFLOW as for tpx_sync; TPX_ECUDA. */
 int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, const uint64_t *d_packets,
                         int64_t n_packets, int64_t packet_index_base, int64_t *d_labels,
                         uint8_t *d_is_peak, tpx_record *d_clusters, int64_t cluster_capacity,
@@ -305,6 +311,14 @@ int tpx_tot_tof_histogram(tpx_ctx *ctx, const tpx_hits *hits, int64_t n_hits, in
    TPX_EDEVTIMEOUT.  The context stays usable.  For tests of the timeout
    path only. */
 int tpx_debug_hold_tile(tpx_ctx *ctx, int64_t tile);
+
+/* Test hook for tpx_process_noalloc (no counterpart in the paper): sets the
+   look-back sequence number that the current device's last call used, so
+   that a test can make the next calls cross the wrap of the 30-bit sequence
+   (where the fixed array's flags are cleared) without 2^30 calls.  The next
+   call uses last_seq + 1 (mod 2^30; 0 is skipped).  TPX_EINVAL if last_seq
+   >= 2^30; TPX_ECUDA if the current device cannot be read. */
+int tpx_debug_noalloc_seq(uint32_t last_seq);
 
 /* ---- learned overlap refiner (not in the paper; its multi-hit discussion,
    Sec. VII.B, and the local-maximum count of Sec. V.B motivate it) ----

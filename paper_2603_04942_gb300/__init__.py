@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_dest
                     "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
                     "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_refine_patches", "tpx_refiner_params",
                     "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
-                    "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
+                    "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_debug_noalloc_seq", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_stream_snapshot_bytes", "tpx_stream_snapshot", "tpx_stream_restore",
                     "tpx_strerror", "tpx_version")

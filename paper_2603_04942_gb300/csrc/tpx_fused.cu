@@ -2,6 +2,7 @@
 // centroid kernel for sm_103a.  See tpx_fused.cuh for the structure.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <climits>
 #include <cstdint>
 
@@ -9,6 +10,8 @@
 #include "tpx_fused.cuh"
 
 namespace tpxk {
+
+constexpr int kAttrDevices = 64;   // devices whose kernel attributes are remembered
 
 // 1024-thread CTAs, one per SM, 4096-packet tiles, 8192-position ranges
 namespace geo_t4096 {

@@ -1068,15 +1068,20 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
 
 int smem_bytes() { return (int)sizeof(Smem); }
 
+// The shared-memory attribute belongs to each device's context: it is set
+// once per device (and again on any device beyond the table).
 template <int MODE, bool STAGED, bool BATCH>
 cudaError_t launch_one(const Params &p, int grid, cudaStream_t s) {
-    static bool attr_done = false;
+    static std::atomic<bool> attr_done[kAttrDevices];
     const int smem = (int)sizeof(Smem);
-    if (!attr_done) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(fused_kernel<MODE, STAGED, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool known = dev >= 0 && dev < kAttrDevices;
+    if (!known || !attr_done[dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(fused_kernel<MODE, STAGED, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        attr_done = true;
+        if (known) attr_done[dev].store(true, std::memory_order_release);
     }
     fused_kernel<MODE, STAGED, BATCH><<<grid, NT, smem, s>>>(p);
     return cudaGetLastError();

@@ -2,13 +2,20 @@
 // cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they process data:
-// code running while a CUDA graph is being captured, real-time acquisition
-// loops that must not block in the allocator, and hosts that hand the
-// library a fixed memory budget up front. tpx_create allocates the look-back
-// scratch of a context, so those callers cannot use tpx_process. This entry
-// point runs the same fused kernel with its scratch taken from one fixed
-// array in device memory that is part of the library image, so it allocates
-// nothing.
+// real-time acquisition loops that must not block in the allocator (a
+// cudaMalloc can wait for the device or trigger an implicit synchronisation),
+// and hosts that hand the library a fixed memory budget up front and account
+// for every byte. tpx_create allocates the look-back scratch of a context, so
+// those callers cannot use tpx_process. This entry point runs the same fused
+// kernel with its scratch taken from one fixed array in device memory that is
+// part of the library image, so it allocates nothing.
+//
+// The call reads the device status back and synchronises its stream before
+// it returns, so it must not be made on a stream that is being captured into
+// a CUDA graph. It has no redo: where tpx_sync would hand an input the fused
+// kernel cannot hold (a shot longer than a tile's range, a pixel whose trigger
+// lies outside its range) to the general path, this call returns
+// TPX_EUNSUPPORTED and its outputs are incomplete.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (about 2.4 MB) until the process exits, and all calls on a
@@ -173,5 +180,14 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
     if (st & (tpxk::ST_CAPACITY | tpxk::ST_EXCEPTION)) return TPX_EUNSUPPORTED;
     if (cfg->strict && h.counters[tpxk::C_CORRUPT]) return TPX_ECORRUPT;
     if (st & (tpxk::ST_CLUSTER_CAP | tpxk::ST_TRIG_CAP)) return TPX_EOVERFLOW;
+    return TPX_OK;
+}
+
+extern "C" int tpx_debug_noalloc_seq(uint32_t last_seq) {
+    if (last_seq > 0x3FFFFFFFu) return TPX_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TPX_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_dev_seq[dev] = last_seq;
     return TPX_OK;
 }

@@ -18,6 +18,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -485,14 +487,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const float *__restrict__ x
 template <int H>
 int infer_h(tpx_ctx *c, const void *packed, const float *x, long long n, float *out) {
     using G = MlpGeo<H>;
-    static bool attr = false;
-    if (!attr) {
-        if (ck(cudaFuncSetAttribute(k_mlp_bf16<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem)))
-            return TPX_ECUDA;
-        attr = true;
-    }
+    // the shared-memory attribute belongs to each device's context
+    static std::atomic<bool> attr[64];
     int dev = 0, sms = 0;
     if (ck(cudaGetDevice(&dev)) || ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return TPX_ECUDA;
+    const bool known = dev >= 0 && dev < 64;
+    if (!known || !attr[dev].load(std::memory_order_acquire)) {
+        if (ck(cudaFuncSetAttribute(k_mlp_bf16<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem)))
+            return TPX_ECUDA;
+        if (known) attr[dev].store(true, std::memory_order_release);
+    }
     const long long tiles = (n + 127) / 128;
     const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
     const uint16_t *wt = static_cast<const uint16_t *>(packed);

@@ -6,7 +6,7 @@ import pytest
 
 import paper_2603_04942_gb300 as tpx
 import synth
-from gpu_common import assert_clusters_equal, gpu_run, to_device
+from gpu_common import assert_clusters_equal, gpu_run, oracle_run, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +36,7 @@ def run_calls(pk, cuts, chain=True, fused=True):
 def test_chained_calls_equal_one_call(seed):
     # shots 480..560 of the small configuration cross the first pixel wrap
     pk = synth.generate(synth.small(shot_begin=0, n_shots=560, pair_frac=0.05, dark_per_shot=2.0))[0]
-    whole = gpu_run(pk)
+    whole = oracle_run(pk)
     tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
     rng = np.random.default_rng(seed)
     cuts = [0] + sorted(rng.choice(tdc[1:], size=7, replace=False).tolist()) + [pk.size]
@@ -50,7 +50,7 @@ def test_chained_calls_equal_one_call(seed):
 
 def test_state_handed_to_another_context():
     pk = synth.generate(synth.small(shot_begin=0, n_shots=540))[0]
-    whole = gpu_run(pk)
+    whole = oracle_run(pk)
     tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
     cut = int(tdc[510])                       # after the first pixel wrap
     import torch
@@ -88,8 +88,8 @@ def test_chained_general_path_redo():
         for _ in range(n):
             b.pix(rng.integers(0, 80), rng.integers(0, 80), rng.integers(1, 200), t0 + s * 640_000 + 900 + rng.integers(0, 3000))
     pk = b.packets()
-    whole = gpu_run(pk)
-    assert whole["counters"]["redone"] == 1
+    assert gpu_run(pk)["counters"]["redone"] == 1
+    whole = oracle_run(pk)
     tdc = np.flatnonzero((pk >> np.uint64(60)) == 6)
     labels, clusters, trig, state = run_calls(pk, [0, int(tdc[1]), int(tdc[2]), pk.size])
     assert np.array_equal(labels, whole["labels"])
@@ -104,7 +104,7 @@ def test_shards_on_one_gpu_equal_one_call():
     from paper_2603_04942_gb300 import shard
     from test_shard_gloo import _summary
     pk = synth.generate(synth.small(shot_begin=350, n_shots=350, pair_frac=0.05))[0]
-    whole = gpu_run(pk)
+    whole = oracle_run(pk)
     cuts = shard.plan_cuts((pk >> np.uint64(60)) == 6, 3)
     summaries = []
     for a, b in zip(cuts[:-1], cuts[1:]):

@@ -48,7 +48,7 @@ def chunks_for(n, rng, lo, hi):
 
 def test_stream_small_config_in_random_chunks():
     pk = synth.generate(synth.small(n_shots=400, pair_frac=0.05))[0]
-    whole = gpu_run(pk)
+    whole = oracle_run(pk)
     rng = np.random.default_rng(1)
     recs, trig, first = run_stream(pk, chunks_for(pk.size, rng, 1, 30_000))
     assert np.array_equal(trig, whole["triggers"])
@@ -120,7 +120,7 @@ def test_checkpoint_and_resume_continue_the_stream_exactly(kind):
     if kind == "small":
         pk = synth.generate(synth.small(n_shots=400, pair_frac=0.05))[0]
         cfg = tpx.Config()
-        whole = gpu_run(pk)
+        whole = oracle_run(pk)
     else:
         pk = synth.generate(synth.streaming(10e6, n_shots=60))[0]
         cfg = tpx.Config(tof_max_ticks=synth.STREAM_TOF_MAX_TICKS)
