@@ -2,11 +2,11 @@
 //
 // One persistent kernel reads the packet stream once.  Each CTA repeatedly
 // claims the next tile of T packets (dynamic, in stream order), and:
-//   1. loads the tile into shared memory and reduces the two ToA unwrap
-//      chains (pixels, TDCs) over it (Sec. IV.A: a step down by more than the
-//      threshold adds a wrap, a step up by more removes one).  The chains are
-//      associative, so tiles publish their aggregate and a decoupled look-back
-//      over predecessors yields the exact state at the tile start;
+//   1. loads the tile into shared memory; the exact state of the two ToA
+//      unwrap chains (pixels, TDCs; Sec. IV.A: a step down by more than the
+//      threshold adds a wrap, a step up by more removes one) at the tile start
+//      comes from the unwrap pre-pass, which scans the tiles' chain
+//      aggregates before the kernel starts (the chains are associative);
 //   2. owns the laser shots whose TDC packet lies in the tile, reading past
 //      the tile end up to the next TDC packet (its "range");
 //   3. unwraps every packet of the range, bins each pixel to the most recent
@@ -64,12 +64,13 @@ struct Ctl {                     // per-launch control block, cleared before eac
 struct GChain { long long n, first, last, sum; };
 struct GAgg { GChain pix, tdc; };            // 64 bytes
 
-// per-tile look-back records
+// per-tile records: the unwrap pre-pass's tile aggregates and states, and
+// the record-count look-back chain
 struct TileScratch {
-    unsigned int *flags;     // [tiles] (seq<<2)|1 aggregate, |2 inclusive prefix
-    GAgg *agg;               // [tiles]
-    GAgg *pre;               // [tiles]
-    unsigned int *cflags;    // [tiles] cluster-count chain
+    GAgg *agg;               // [tiles] unwrap-chain aggregate of each tile
+    GAgg *pre;               // [tiles] unwrap state before each tile
+    GAgg *blk;               // unwrap_prepass_scratch_bytes(tiles): block totals of the scan
+    unsigned int *cflags;    // [tiles] cluster-count chain: (seq<<2)|1 count, |2 inclusive prefix
     long long *cagg;         // [tiles]
     long long *cpre;         // [tiles]
 };
@@ -114,7 +115,7 @@ struct Params {
     long long hold;          // tile + 1 whose look-back flags stay unpublished (0: none): lets a
                              // test run its successors' bounded waits out (TPX_EDEVTIMEOUT)
     const GAgg *E0;          // unwrap state before the call (NULL: stream start)
-    GAgg *state_out;         // state after the call, written by the last tile (or NULL)
+    GAgg *state_out;         // state after the call, written by the pre-pass (or NULL)
 };
 
 }  // namespace tpxk
@@ -128,5 +129,10 @@ int fused_smem_bytes(int geo);
 int fused_threads(int geo);
 int fused_range_capacity(int geo);
 int fused_ctas_per_sm(int geo);
+// the unwrap pre-pass (tpx_prepass.cu): ts.pre[tile] = the state before each
+// tile, *state_out = the state after the call; adds the pixel, TDC and
+// corrupt-packet counters. launch_fused runs it before the fused kernel.
+size_t unwrap_prepass_scratch_bytes(long long n_tiles);
+cudaError_t launch_unwrap_prepass(const Params &p, int T, int grid, cudaStream_t s);
 cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s);
 }  // namespace tpxk

@@ -83,19 +83,9 @@ __device__ __forceinline__ uint32_t sh_cas(uint32_t a, uint32_t cmp, uint32_t v)
     asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(o) : "r"(a), "r"(cmp), "r"(v) : "memory");
     return o;
 }
-__device__ __forceinline__ uint32_t find_root(uint32_t pbase, uint32_t x) {
-    for (;;) {
-        const uint32_t p = sh_ld(pbase + 4 * x);
-        if (p == x) return x;
-        const uint32_t g = sh_ld(pbase + 4 * p);
-        if (g == p) return p;
-        sh_st(pbase + 4 * x, g);   // path halving: g is an ancestor of x
-        x = g;
-    }
-}
 __device__ __forceinline__ uint32_t find_ro(uint32_t pbase, uint32_t x) {
     uint32_t p;
-    while ((p = sh_ld(pbase + 4 * x)) != x) x = p;
+    while ((p = sh_ld(pbase + 4 * x) & 0xFFFFu) != x) x = p;
     return x;
 }
 
@@ -110,10 +100,8 @@ struct __align__(16) Smem {
     uint8_t notpeak[C];
     long long tdc_t[MAXSEG];
     GAgg warp_agg[NW];
-    GAgg lb_buf[32];              // one slot per lane of the look-back warp
     GAgg tot_agg;
-    GAgg tile_agg;                // this tile's chain aggregate
-    GAgg E;                       // unwrap state before the tile
+    GAgg E;                       // unwrap state before the tile (from the pre-pass)
     int warp_int[NW + 1];
     unsigned long long cnt[C_NUM];
     long long tile;
@@ -212,9 +200,7 @@ __device__ __forceinline__ GChain shfl_down_chain(const GChain &v, int o) {
 // latest), waits only for the tiles from hi down to the nearest inclusive
 // prefix, and combines them in stream order. Two dependent L2 round trips
 // per trip (flags, then values), so wide trips keep the chain short.
-// (LB = 1 for the 64-byte chain aggregates: the 64-register budget of a
-// 1024-thread CTA keeps only one in flight per lane; LB = 4 for counts.)
-constexpr int LBA = 1, LBC = 4;
+constexpr int LBC = 4;
 
 // per lane: which of its LB tiles are needed this trip, given the flags
 struct LbScan { unsigned need, inc; int stop; bool ok; };
@@ -242,54 +228,8 @@ __device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, l
     return r;
 }
 
-// buf: 32 GAgg slots in shared memory, owned by the look-back warp. The
-// combine is a tree over the slots (few live registers: the kernel runs at
-// the 64-register limit of a 1024-thread CTA). Lane 0 returns the prefix.
-// Tiles before lo (the first tile of the stream: 0, or the run's first tile
-// in a batch) are not part of the chain.
-__device__ GAgg lookback_agg_warp(const Params &p, long long tile, long long lo, unsigned seq, unsigned *status,
-                                  GAgg *buf) {
-    const int lane = threadIdx.x & 31;
-    GAgg acc = agg_id();
-    for (long long hi = tile - 1; hi >= lo; hi -= 32 * LBA) {
-        LbScan sc;
-        long long spins = 0;
-        for (;;) {
-            sc = lb_scan<LBA>(p.ts.flags, hi, lo, seq);
-            if (__all_sync(0xffffffffu, sc.ok)) break;
-            if (++spins > MAX_SPIN || timed_out(p)) {
-                if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
-                *status |= ST_DEVTIMEOUT;
-                return acc;
-            }
-            __nanosleep(64);
-        }
-        // lane l: its needed tile (an inclusive prefix, if present, is the
-        // earliest needed one), or the identity
-        {
-            const long long q = hi - lane;
-            const ulonglong2 *src = nullptr;
-            if (q >= lo && (sc.need & 1u)) src = reinterpret_cast<const ulonglong2 *>((sc.inc & 1u) ? &p.ts.pre[q] : &p.ts.agg[q]);
-            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&buf[lane]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) dst[k] = src ? __ldcg(src + k) : make_ulonglong2(0ull, 0ull);
-        }
-        __syncwarp();
-        // lane l + o holds earlier tiles than lane l: combine it on the left
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            if ((lane & (2 * o - 1)) == 0) buf[lane] = acomb(buf[lane + o], buf[lane], p.thr_pix, p.thr_tdc);
-            __syncwarp();
-        }
-        if (lane == 0) acc = acomb(buf[0], acc, p.thr_pix, p.thr_tdc);
-        __syncwarp();
-        if (__any_sync(0xffffffffu, sc.inc != 0)) break;
-    }
-    return acc;
-}
-
-// The same over the record counts of the tiles (and, in a batch, their
-// trigger counts: .y), over all tiles of the call.
+// Decoupled look-back over the record counts of the tiles (and, in a batch,
+// their trigger counts: .y), over all tiles of the call.
 template <bool BATCH>
 __device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
     const int lane = threadIdx.x & 31;
@@ -328,19 +268,61 @@ __device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsign
     return acc;
 }
 
-// lock-free union; the root is the member with the smallest (time, position)
-__device__ __forceinline__ uint64_t rkey(const Smem &S, uint32_t q) {
-    return ((uint64_t)r_tof(S.buf[pad((int)q)]) << 16) | q;
-}
-__device__ void unite_one(const Smem &S, uint32_t pbase, uint32_t a, uint32_t b) {
+// The CC union-find array holds one 32-bit word per position: the parent in
+// the lower half, in the upper half the pixel's second partner (NO_EXT: none;
+// REWALK: more than two, re-walked at the unions). Finds look at the lower
+// halves; writes keep the upper halves.
+constexpr uint32_t NO_EXT = 0xFFFFu, REWALK = 0xFFFEu;
+static_assert(C < (int)REWALK, "positions fit below the markers");
+
+__device__ __forceinline__ uint32_t find_hw(uint32_t pbase, uint32_t x) {
     for (;;) {
-        a = find_root(pbase, a);
-        b = find_root(pbase, b);
+        const uint32_t w = sh_ld(pbase + 4 * x);
+        const uint32_t px = w & 0xFFFFu;
+        if (px == x) return x;
+        const uint32_t g = sh_ld(pbase + 4 * px) & 0xFFFFu;
+        if (g == px) return px;
+        sh_st(pbase + 4 * x, (w & 0xFFFF0000u) | g);   // path halving: g is an ancestor of x
+        x = g;
+    }
+}
+
+// lock-free union: the larger root position is linked under the smaller
+__device__ void unite_hw(uint32_t pbase, uint32_t a, uint32_t b) {
+    for (;;) {
+        a = find_hw(pbase, a);
+        b = find_hw(pbase, b);
         if (a == b) return;
-        if (rkey(S, a) > rkey(S, b)) { uint32_t t = a; a = b; b = t; }
-        const uint32_t old = sh_cas(pbase + 4 * b, b, a);
-        if (old == b) return;
-        b = old;
+        const uint32_t lo = min(a, b), hi = max(a, b);
+        const uint32_t w = sh_ld(pbase + 4 * hi);
+        if ((w & 0xFFFFu) == hi && sh_cas(pbase + 4 * hi, w, (w & 0xFFFF0000u) | lo) == w) return;
+        a = lo;
+        b = hi;   // hi was linked meanwhile: find again
+    }
+}
+
+// a pixel with more than two partners: unite it with each partner in the
+// forward half of its box (Sec. V.A), found again in the cell hash
+template <int MODE>
+__device__ void rewalk_unite(const Smem &S, const Params &p, uint32_t pbase, int q) {
+    const uint64_t r = S.buf[pad(q)];
+    const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
+    for (int dx = 0; dx <= p.rx; ++dx) {
+        const int cx = x + dx;
+        if (cx > 255) break;
+        for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
+            const int cy = y + dy;
+            if (cy < 0 || cy > 255) continue;
+            for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                if (!TPX_IN(j, C)) break;
+                if (dx == 0 && dy == 0 && (int)j <= q) continue;
+                const uint64_t rj = S.buf[pad((int)j)];
+                if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
+                const int d = r_tof(rj) - tb;
+                if (d < -p.dt || d > p.dt) continue;
+                unite_hw(pbase, (uint32_t)q, j);
+            }
+        }
     }
 }
 
@@ -431,6 +413,9 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         if (tid < C_NUM) S.cnt[tid] = 0;
         __syncthreads();
         const long long tile = S.tile;
+        // the unwrap state before the tile, from the pre-pass
+        if (tid < 8 && tile < p.n_tiles)
+            reinterpret_cast<long long *>(&S.E)[tid] = __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[tile]) + tid);
         if (tile >= p.n_tiles) {
             if (STAGED) {
                 flush_pending<BATCH>(S, p, seq);
@@ -452,65 +437,44 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         const int cnt = (int)max(0LL, min((long long)T, rend - base));
 
-        // ---- load the tile: coalesced 16-byte loads into the padded buffer ----
-        if (BATCH && (base & 1)) {   // a run starting at an odd packet: 8-byte loads
-            for (int v = tid; v < cnt; v += NT) S.buf[pad(v)] = __ldcg(p.pk + base + v);
-        } else {
-            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.pk + base);
-            const int npair = cnt >> 1;
-            for (int v = tid; v < npair; v += NT) {
-                ulonglong2 w = __ldcg(src + v);
-                S.buf[pad(2 * v)] = w.x;
-                S.buf[pad(2 * v + 1)] = w.y;
+        // ---- load the tile: coalesced 16-byte loads into the padded buffer;
+        // its TDC packets are counted and the first one found on the way ----
+        {
+            int my_first = INT_MAX, c_tdc = 0;
+            if (BATCH && (base & 1)) {   // a run starting at an odd packet: 8-byte loads
+                for (int v = tid; v < cnt; v += NT) {
+                    const uint64_t w = __ldcg(p.pk + base + v);
+                    S.buf[pad(v)] = w;
+                    if ((w >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, v); }
+                }
+            } else {
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.pk + base);
+                const int npair = cnt >> 1;
+                for (int v = tid; v < npair; v += NT) {
+                    ulonglong2 w = __ldcg(src + v);
+                    S.buf[pad(2 * v)] = w.x;
+                    S.buf[pad(2 * v + 1)] = w.y;
+                    if ((w.x >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, 2 * v); }
+                    if ((w.y >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, 2 * v + 1); }
+                }
+                if ((cnt & 1) && tid == 0) {
+                    const uint64_t w = __ldcg(p.pk + base + cnt - 1);
+                    S.buf[pad(cnt - 1)] = w;
+                    if ((w >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, cnt - 1); }
+                }
             }
-            if ((cnt & 1) && tid == 0) S.buf[pad(cnt - 1)] = __ldcg(p.pk + base + cnt - 1);
+            for (int i = tid; i < HB / 2; i += NT) reinterpret_cast<uint32_t *>(S.u1.head)[i] = 0xFFFFFFFFu;
+            if (__any_sync(0xffffffffu, c_tdc != 0)) {
+                c_tdc = (int)warp_sum((unsigned long long)c_tdc);
+                my_first = __reduce_min_sync(0xffffffffu, (unsigned)my_first);
+                if (lane == 0) {
+                    atomicAdd(&S.cnt[C_TDCS], (unsigned long long)c_tdc);
+                    atomicMin(&S.first_tdc, my_first);
+                }
+            }
         }
-        for (int i = tid; i < HB / 2; i += NT) reinterpret_cast<uint32_t *>(S.u1.head)[i] = 0xFFFFFFFFu;
         __syncthreads();
 
-        // ---- walk 1: unwrap-chain aggregate of the tile, packet counts ----
-        {
-            GAgg a = agg_id();
-            unsigned long long c_pix = 0, c_tdc = 0, c_bad = 0;
-            int my_first = INT_MAX;
-            // the tile's own packets split evenly over all threads
-            const int kp1 = (cnt + NT - 1) / NT;
-            const int p0 = tid * kp1;
-            for (int j = 0; j < kp1; ++j) {
-                const int q = p0 + j;
-                if (q >= cnt) break;
-                const uint64_t w = S.buf[pad(q)];
-                const unsigned h = (unsigned)(w >> 60);
-                if (h == 0xBu) { chain_push(a.pix, pix_raw(w), tp); ++c_pix; }
-                else if (h == 0x6u) { chain_push(a.tdc, tdc_raw(w), tt); ++c_tdc; my_first = min(my_first, q); }
-                else ++c_bad;
-            }
-            (void)block_scan_agg(S, a, tp, tt);
-            c_pix = warp_sum(c_pix); c_tdc = warp_sum(c_tdc); c_bad = warp_sum(c_bad);
-            if (lane == 0) {
-                atomicAdd(&S.cnt[C_PIXELS], c_pix);
-                atomicAdd(&S.cnt[C_TDCS], c_tdc);
-                atomicAdd(&S.cnt[C_CORRUPT], c_bad);
-            }
-            if (my_first != INT_MAX) atomicMin(&S.first_tdc, my_first);
-        }
-        // publish the tile's aggregate now; the look-back waits until after the
-        // read-ahead and the block scan, which do not need it
-        if (tid == 0) {
-            S.tile_agg = S.tot_agg;
-            if (tile + 1 == p.hold) {
-                // a test holds this tile's flags back: its successors' waits run out
-            } else if (tile > tile0) {
-                st_agg(&p.ts.agg[tile], S.tot_agg);
-                st_release(&p.ts.flags[tile], (seq << 2) | 1u);
-            } else {
-                const GAgg e0 = (!BATCH && p.E0) ? *p.E0 : agg_id();
-                S.E = e0;
-                st_agg(&p.ts.pre[tile], acomb(e0, S.tot_agg, tp, tt));
-                st_release(&p.ts.flags[tile], (seq << 2) | 2u);
-            }
-        }
-        __syncthreads();
         const int f = S.first_tdc;
 
         // ---- look ahead past the tile up to the next TDC packet ----
@@ -559,23 +523,6 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             ex = block_scan_agg(S, a, tp, tt);
             ntdc = (int)S.tot_agg.tdc.n;
         }
-        // ---- unwrap state before the tile: warp-parallel look-back ----
-        if (tid < 32) {
-            unsigned stl = 0;
-            GAgg Ew = agg_id();
-            if (tile > tile0) Ew = lookback_agg_warp(p, tile, tile0, seq, &stl, S.lb_buf);
-            else Ew = (!BATCH && p.E0) ? *p.E0 : agg_id();
-            if (tid == 0) {
-                if (tile > tile0 && tile + 1 != p.hold) {
-                    st_agg(&p.ts.pre[tile], acomb(Ew, S.tile_agg, tp, tt));
-                    st_release(&p.ts.flags[tile], (seq << 2) | 2u);
-                }
-                if (!BATCH && tile == p.n_tiles - 1 && p.state_out) *p.state_out = acomb(Ew, S.tile_agg, tp, tt);
-                S.E = Ew;
-                if (stl) atomicOr(&S.status, stl);
-            }
-        }
-        __syncthreads();
         const GAgg E = S.E;
         // a call sees only its own triggers: "earlier" means earlier in this call
         const long long trig_base = (!BATCH && p.E0) ? p.E0->tdc.n : 0;
@@ -600,7 +547,6 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
                 if (!BATCH && q < cnt) {   // a batch writes its triggers at the flush
                     const long long g = E.tdc.n - trig_base + li;
-                    // (g < 0 only after a look-back ran out: the state is partial)
                     if (g >= 0 && g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
                 }
                 ++li;
@@ -686,7 +632,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // ---- hash insert ----
         for (int q = R0 + tid; q < R1; q += NT) {
             const uint64_t r = S.buf[pad(q)];
-            S.parent[q] = (uint32_t)q;
+            S.parent[q] = (NO_EXT << 16) | (uint32_t)q;
             S.notpeak[q] = 0;
             if (r != INVALID) {
                 const uint32_t b = hcell(r_seg(r), r_x(r), r_y(r));
@@ -702,20 +648,22 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         __syncthreads();
 
         // ---- neighbour pass: each adjacent pair once (Sec. V.A box rule) ----
-        // The warp walks 32 consecutive positions at a time. Each lane first
-        // gathers its pixel's partners in the forward half of the box (packed
-        // 16-bit positions in two registers); the unions then run
-        // warp-synchronously, one find hop or link attempt per loop trip, so
-        // the lanes stay converged (retry loops nested in the lookups would
-        // serialise them).
+        // The warp walks 32 consecutive positions at a time; each lane gathers
+        // its pixel's partners in the forward half of the box -- a strict order
+        // of the pairs: a larger x, or the same x and a larger y, or the same
+        // cell and a later position -- and updates the local-maximum flags
+        // (Sec. V.B). CC mode: the pixel points to its first partner (a plain
+        // store: pointers only go forward, so they form a forest) and keeps its
+        // second partner in the upper half of its pointer word; a pixel with
+        // more partners marks its word for a re-walk.
         {
             for (int qb = R0 + (tid & ~31); qb < R1; qb += NT) {
                 const int q = qb + lane;
                 const uint64_t r = q < R1 ? S.buf[pad(q)] : INVALID;
-                uint64_t eb0 = 0, eb1 = 0;
+                if (r == INVALID) continue;
+                uint32_t e0 = (uint32_t)q, e1 = NO_EXT;
                 int ne = 0;
-                bool overflow = false;
-                if (r != INVALID) {
+                {
                     const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
                     bool dim = false;
                     // 8-neighbour box: a diagonal partner (dx = 1, dy = -1 or +1) is
@@ -757,9 +705,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                                     }
                                 }
                                 if (MODE == TPX_MODE_CC) {
-                                    if (ne < 4) eb0 |= (uint64_t)j << (16 * ne);
-                                    else if (ne < 8) eb1 |= (uint64_t)j << (16 * (ne - 4));
-                                    else overflow = true;
+                                    if (ne == 0) e0 = j; else if (ne == 1) e1 = j;
                                     ++ne;
                                 }
                             }
@@ -769,108 +715,113 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                         const uint32_t jA = hold & 0xFFFFu, jB = hold >> 16;
                         const bool skipA = tE != INT_MIN && abs(tE - tA) <= p.dt;
                         const bool skipB = (tE != INT_MIN && abs(tE - tB) <= p.dt) || (tN != INT_MIN && abs(tN - tB) <= p.dt);
-                        for (int h = 0; h < 2; ++h) {
-                            const uint32_t jh = h ? jB : jA;
-                            if (jh == 0xFFFFu || (h ? skipB : skipA)) continue;
-                            if (ne < 4) eb0 |= (uint64_t)jh << (16 * ne);
-                            else if (ne < 8) eb1 |= (uint64_t)jh << (16 * (ne - 4));
-                            else overflow = true;
-                            ++ne;
-                        }
+                        if (jA != 0xFFFFu && !skipA) { if (ne == 0) e0 = jA; else if (ne == 1) e1 = jA; ++ne; }
+                        if (jB != 0xFFFFu && !skipB) { if (ne == 0) e0 = jB; else if (ne == 1) e1 = jB; ++ne; }
                     }
                     if (dim) S.notpeak[q] = 1;
                 }
-                if (MODE == TPX_MODE_CC) {
-                    if (overflow) {
-                        // more than 8 partners (possible with larger radii): unite
-                        // this pixel's pairs one at a time
-                        const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r);
-                        for (int dx = 0; dx <= p.rx; ++dx)
-                            for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
-                                const int ux = x + dx, uy = y + dy;
-                                if (ux > 255 || uy < 0 || uy > 255) continue;
-                                for (uint32_t jj = S.u1.head[hcell(sg, ux, uy)]; jj != EMPTY; jj = S.u2.next[jj]) {
-                                    if (!TPX_IN(jj, C)) break;
-                                    if (dx == 0 && dy == 0 && (int)jj <= q) continue;
-                                    const uint64_t rj = S.buf[pad((int)jj)];
-                                    if (r_x(rj) != ux || r_y(rj) != uy || r_seg(rj) != sg) continue;
-                                    const int d = r_tof(rj) - tb;
-                                    if (d < -p.dt || d > p.dt) continue;
-                                    unite_one(S, pbase, (uint32_t)q, jj);
-                                }
-                            }
-                        ne = 0;
-                    }
-                    // warp-synchronous unions: each trip advances every active lane by
-                    // one step (a find hop with path halving on either side, or one
-                    // link attempt); a lane moves to its next partner as soon as its
-                    // current union is done
-                    __syncwarp();
-                    int k = 0;
-                    uint32_t a = (uint32_t)(q < R1 ? q : 0), b = (uint32_t)(eb0 & 0xFFFF);
-                    bool active = ne > 0;
-                    while (__any_sync(0xffffffffu, active)) {
-                        if (active) {
-                            bool done = false;
-                            const uint32_t pa = sh_ld(pbase + 4 * a);
-                            const uint32_t pb = sh_ld(pbase + 4 * b);
-                            if (pa != a || pb != b) {
-                                if (pa != a) {
-                                    const uint32_t ga = sh_ld(pbase + 4 * pa);
-                                    if (ga != pa) sh_st(pbase + 4 * a, ga);
-                                    a = ga;
-                                }
-                                if (pb != b) {
-                                    const uint32_t gb = sh_ld(pbase + 4 * pb);
-                                    if (gb != pb) sh_st(pbase + 4 * b, gb);
-                                    b = gb;
-                                }
-                            } else if (a == b) {
-                                done = true;
-                            } else {
-                                uint32_t lo = a, hi = b;
-                                if (rkey(S, a) > rkey(S, b)) { lo = b; hi = a; }
-                                const uint32_t old = sh_cas(pbase + 4 * hi, hi, lo);
-                                if (old == hi) done = true;
-                                else b = old;      // hi was linked meanwhile: continue above it
-                                a = lo;
-                            }
-                            if (done) {
-                                if (++k < ne) {
-                                    const uint64_t w = k < 4 ? eb0 : eb1;
-                                    b = (uint32_t)((w >> (16 * (k & 3))) & 0xFFFF);
-                                } else {
-                                    active = false;
-                                }
-                            }
-                        }
-                    }
-                }
+                if (MODE == TPX_MODE_CC) S.parent[q] = ((ne > 2 ? REWALK : e1) << 16) | e0;
             }
         }
         __syncthreads();
 
         int ncl = 0;
         if (MODE == TPX_MODE_CC) {
-            for (int q = R0 + tid; q < R1; q += NT)
-                if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(pbase, (uint32_t)q);
+            // compress: every pixel points to the root of its tree
+            for (int q = R0 + tid; q < R1; q += NT) {
+                const uint32_t w = sh_ld(pbase + 4 * q);
+                if ((w & 0xFFFFu) == (uint32_t)q) continue;
+                sh_st(pbase + 4 * q, (w & 0xFFFF0000u) | find_hw(pbase, w & 0xFFFFu));
+            }
             __syncthreads();
-            // cluster ids in ascending root position (= ascending label)
+            // unions of the second partners, warp-synchronous: each trip
+            // advances every active lane by one find hop (path halving) or one
+            // link attempt, the larger root position linked under the smaller.
+            // A pixel marked for a re-walk unites each of its partners in turn.
+            for (int qb = R0 + (tid & ~31); qb < R1; qb += NT) {
+                const int q = qb + lane;
+                uint32_t b = q < R1 ? sh_ld(pbase + 4 * q) >> 16 : NO_EXT;
+                if (b == REWALK) {
+                    rewalk_unite<MODE>(S, p, pbase, q);
+                    b = NO_EXT;
+                }
+                __syncwarp();
+                uint32_t a = (uint32_t)q;
+                bool active = b != NO_EXT && TPX_IN(b, C);
+                while (__any_sync(0xffffffffu, active)) {
+                    if (active) {
+                        const uint32_t wa = sh_ld(pbase + 4 * a), wb = sh_ld(pbase + 4 * b);
+                        const uint32_t pa = wa & 0xFFFFu, pb = wb & 0xFFFFu;
+                        if (pa != a || pb != b) {
+                            if (pa != a) {
+                                const uint32_t ga = sh_ld(pbase + 4 * pa) & 0xFFFFu;
+                                if (ga != pa) sh_st(pbase + 4 * a, (wa & 0xFFFF0000u) | ga);
+                                a = ga;
+                            }
+                            if (pb != b) {
+                                const uint32_t gb = sh_ld(pbase + 4 * pb) & 0xFFFFu;
+                                if (gb != pb) sh_st(pbase + 4 * b, (wb & 0xFFFF0000u) | gb);
+                                b = gb;
+                            }
+                        } else if (a == b) {
+                            active = false;
+                        } else {
+                            const uint32_t lo = min(a, b), hi = max(a, b);
+                            const uint32_t wh = hi == a ? wa : wb;
+                            const uint32_t old = sh_cas(pbase + 4 * hi, wh, (wh & 0xFFFF0000u) | lo);
+                            if (old == wh) active = false;
+                            else { a = lo; b = old & 0xFFFFu; }   // hi was linked meanwhile: go on above it
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // roots; the hash is free now: member-list heads, cleared
+            for (int q = R0 + tid; q < R1; q += NT) {
+                S.u1.mhead[q] = EMPTY;
+                if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(pbase, (uint32_t)q);
+            }
+            __syncthreads();
+            // member lists: each kept pixel joins its root's list (the links
+            // take the first half of the union-find array)
+            uint16_t *mnext = reinterpret_cast<uint16_t *>(S.parent);
+            for (int q = R0 + tid; q < R1; q += NT)
+                if (S.buf[pad(q)] != INVALID) {
+                    const uint32_t rt = S.u2.rootof[q];
+                    if (TPX_IN(rt, C)) mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[rt], (uint32_t)q);
+                }
+            __syncthreads();
+            // each root walks its list for the cluster's earliest pixel in
+            // (time, position) order -- its canonical label -- keeps it in the
+            // upper half of the list head and flags it (bit 1 of notpeak)
+            for (int q = R0 + tid; q < R1; q += NT) {
+                if (S.buf[pad(q)] == INVALID || S.u2.rootof[q] != q) continue;
+                const uint32_t head = S.u1.mhead[q] & 0xFFFFu;
+                uint64_t best = ~0ull;
+                for (uint32_t m = head; m != EMPTY; m = mnext[m]) {
+                    if (!TPX_IN(m, C)) break;
+                    best = min(best, ((uint64_t)r_tof(S.buf[pad((int)m)]) << 16) | m);
+                }
+                const uint32_t lp = (uint32_t)(best & 0xFFFFu);
+                S.u1.mhead[q] = (lp << 16) | head;
+                if (TPX_IN(lp, C)) S.notpeak[lp] |= 2;
+            }
+            __syncthreads();
+            // cluster ids in ascending label position
             int c = 0;
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
+                if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) ++c;
             }
             int excl = block_scan_int(S, c, &ncl);
-            // the union-find array is free now: it holds the member links
-            // (first half) and the root position of each cluster id (second half)
+            // the label position of each cluster id: the second half of the
+            // union-find array
             uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
-                if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
+                if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) {
                     if (TPX_IN(excl, C)) rootpos[excl] = (uint16_t)q;
                     ++excl;
-                    S.u1.mhead[q] = EMPTY;
                 }
             }
         } else {
@@ -919,27 +870,27 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         };
 
         if (MODE == TPX_MODE_CC) {
-            // Each kept pixel joins its cluster's member list (one exchange per
-            // pixel) and writes its label; then one thread per cluster walks the
-            // list and forms the exact integer moments in registers (Sec. V.C).
-            uint16_t *mnext = reinterpret_cast<uint16_t *>(S.parent);
+            // Each kept pixel writes its label (the stream index of its
+            // cluster's earliest pixel); then one thread per cluster walks the
+            // member list and forms the exact integer moments in registers
+            // (Sec. V.C).
+            const uint16_t *mnext = reinterpret_cast<const uint16_t *>(S.parent);
             const uint16_t *rootpos = mnext + C;
             __syncthreads();
             unsigned long long c_pk = 0;
             for (int q = W0 + tid; q < W1; q += NT) {
                 const uint64_t r = S.buf[pad(q)];
                 bool kept = q >= R0 && r != INVALID;
-                uint32_t root = 0;
+                uint32_t lp = 0;
                 uint8_t pk = 0;
                 if (kept && !TPX_IN(S.u2.rootof[q], C)) kept = false;
                 if (kept) {
-                    root = S.u2.rootof[q];
-                    pk = S.notpeak[q] ? 0 : 1;
+                    lp = S.u1.mhead[S.u2.rootof[q]] >> 16;
+                    pk = (S.notpeak[q] & 1) ? 0 : 1;
                     c_pk += pk;
-                    mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[root], (uint32_t)q);
                 }
                 if (!TPX_IN(base + q, rend)) continue;
-                if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)root : -1LL;
+                if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)lp : -1LL;
                 if (p.is_peak) p.is_peak[base + q] = pk;
             }
             c_pk = warp_sum(c_pk);
@@ -951,17 +902,17 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             for (int i = tid; i < ncl; i += NT) {
                 if (i >= lim) break;
                 const int q = rootpos[i];
-                if (!TPX_IN(q, C)) continue;
+                if (!TPX_IN(q, C) || !TPX_IN(S.u2.rootof[q], C)) continue;
                 const uint64_t r = S.buf[pad(q)];
                 const int tofb0 = r_tof(r);
                 long long s_tot = 0, s_x = 0, s_y = 0, s_t = 0;
                 int n = 0, npk = 0;
-                for (uint32_t m = S.u1.mhead[q]; m != EMPTY; m = mnext[m]) {
+                for (uint32_t m = S.u1.mhead[S.u2.rootof[q]] & 0xFFFFu; m != EMPTY; m = mnext[m]) {
                     if (!TPX_IN(m, C)) break;
                     const uint64_t rm = S.buf[pad((int)m)];
                     const long long tot = r_tot(rm);
                     n += 1;
-                    npk += S.notpeak[m] ? 0 : 1;
+                    npk += (S.notpeak[m] & 1) ? 0 : 1;
                     s_tot += tot;
                     s_x += tot * r_x(rm);
                     s_y += tot * r_y(rm);
@@ -1053,7 +1004,9 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             }
         }
         __syncthreads();
-        if (tid < C_NUM && tid != C_PACKETS && S.cnt[tid]) atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
+        // (packets of each class are counted by the unwrap pre-pass)
+        if (tid < C_NUM && tid != C_PACKETS && tid != C_PIXELS && tid != C_TDCS && tid != C_CORRUPT && S.cnt[tid])
+            atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
         if (tid == 0) {
             atomicAdd(&p.ctl->counters[C_PACKETS], (unsigned long long)cnt);
             unsigned st = S.status;

@@ -39,10 +39,15 @@ constexpr int64_t kTile = 4096;                            // packets per tile o
 constexpr int64_t kMaxTiles = TPX_NOALLOC_MAX_PACKETS / kTile;
 constexpr int kMaxDevices = 64;
 
-// layout of the fixed scratch (all members naturally aligned)
+// layout of the fixed scratch (all members naturally aligned); blk holds what
+// unwrap_prepass_scratch_bytes(kMaxTiles) asks for: (tiles / 1024 + 1) block
+// totals and flags, plus 256 bytes
+static_assert(sizeof(tpxk::GAgg) * (kMaxTiles / 1024 + 8) >=
+                  (kMaxTiles / 1024 + 1) * (sizeof(tpxk::GAgg) + sizeof(int)) + 256,
+              "pre-pass block totals");
 struct NoAllocScratch {
     tpxk::Ctl ctl;
-    unsigned flags[kMaxTiles];
+    tpxk::GAgg blk[kMaxTiles / 1024 + 8];   // the unwrap pre-pass's block totals and flags
     unsigned cflags[kMaxTiles];
     tpxk::GAgg agg[kMaxTiles];
     tpxk::GAgg pre[kMaxTiles];
@@ -115,7 +120,6 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
     if (cudaMemsetAsync(d_n_clusters, 0, sizeof(int64_t), s) != cudaSuccess) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_trig, 0, sizeof(int64_t), s) != cudaSuccess) return TPX_ECUDA;
     if (wrapped) {
-        if (cudaMemsetAsync(scr->flags, 0, sizeof scr->flags, s) != cudaSuccess) return TPX_ECUDA;
         if (cudaMemsetAsync(scr->cflags, 0, sizeof scr->cflags, s) != cudaSuccess) return TPX_ECUDA;
     }
 
@@ -145,7 +149,7 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
         p.thr_tdc = cfg->wrap_thr_tdc_ticks;
         p.n_tiles = (n + kTile - 1) / kTile;
         p.seq = seq;
-        p.ts.flags = scr->flags;
+        p.ts.blk = scr->blk;
         p.ts.cflags = scr->cflags;
         p.ts.agg = scr->agg;
         p.ts.pre = scr->pre;

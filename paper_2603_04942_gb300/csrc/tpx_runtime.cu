@@ -61,7 +61,7 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
     if (tiles < 1) tiles = 1;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_flags = al(sizeof(unsigned) * tiles), b_agg = al(sizeof(tpxk::GAgg) * tiles),
-                 b_cnt = al(sizeof(long long) * tiles);
+                 b_cnt = al(sizeof(long long) * tiles), b_blk = al(tpxk::unwrap_prepass_scratch_bytes(tiles));
     // record staging of the fused kernel: one range's records per CTA
     size_t stage_records = 0;   // the largest grid of a call times its range capacity
     for (int geo : {(int)tpxk::GEO_T4096, (int)tpxk::GEO_T2048}) {
@@ -73,12 +73,12 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
     }
     c->stage_records = (int64_t)stage_records;
     const size_t b_stage = al(sizeof(tpx_record) * stage_records);
-    const size_t total = 2 * b_flags + 2 * b_agg + 2 * b_cnt + b_stage;
+    const size_t total = b_flags + b_blk + 2 * b_agg + 2 * b_cnt + b_stage;
     void *mem = nullptr;
     if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
     if (cudaMemset(mem, 0, total) != cudaSuccess) { cudaFree(mem); return TPX_ECUDA; }
     char *p = static_cast<char *>(mem);
-    c->ts.flags = reinterpret_cast<unsigned *>(p); p += b_flags;
+    c->ts.blk = reinterpret_cast<tpxk::GAgg *>(p); p += b_blk;
     c->ts.cflags = reinterpret_cast<unsigned *>(p); p += b_flags;
     c->ts.agg = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
     c->ts.pre = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
@@ -335,7 +335,6 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     c->seq = (c->seq + 1) & 0x3FFFFFFFu;
     if (c->seq == 0) {   // sequence numbers wrapped: clear the flags once
         c->seq = 1;
-        cudaMemsetAsync(c->ts.flags, 0, sizeof(unsigned) * c->max_tiles, c->stream);
         cudaMemsetAsync(c->ts.cflags, 0, sizeof(unsigned) * c->max_tiles, c->stream);
     }
     tpxk::Params p;
@@ -443,7 +442,8 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     auto &B = c->batch;
     const size_t need_dev = al(4 * (size_t)n_tiles) + al(8 * (size_t)n_runs) + al(8 * (size_t)(n_runs + 1)) +
                             al(4 * (size_t)n_runs) + 4 * al(8 * (size_t)n_tiles) + al(8 * (size_t)(grid * T)) +
-                            2 * al(4 * (size_t)n_tiles) + 2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles);
+                            al(tpxk::unwrap_prepass_scratch_bytes(n_tiles)) + al(4 * (size_t)n_tiles) +
+                            2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles);
     const size_t need_host = 8 * (size_t)(n_runs + 1) + 8 * (size_t)n_runs + 4 * (size_t)n_tiles + 64;
     // a call captured into a CUDA graph (relaxed capture mode) gets its own
     // device tables and pinned host tables, kept for the graph's replays
@@ -500,7 +500,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     B.ts.cagg = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
     B.ts.cpre = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
     bt.tstage = reinterpret_cast<long long *>(take(8 * (size_t)(grid * T)));
-    B.ts.flags = reinterpret_cast<unsigned *>(take(4 * (size_t)n_tiles));
+    B.ts.blk = reinterpret_cast<tpxk::GAgg *>(take(tpxk::unwrap_prepass_scratch_bytes(n_tiles)));
     B.ts.cflags = reinterpret_cast<unsigned *>(take(4 * (size_t)n_tiles));
     B.ts.agg = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg) * (size_t)n_tiles));
     B.ts.pre = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg) * (size_t)n_tiles));
@@ -528,9 +528,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
         return TPX_ECUDA;
     if (!capturing && ckr(cudaEventRecord(B.tab_copied, s))) return TPX_ECUDA;
     // the scratch layout follows the tile count: start every call's flags at zero
-    if (ckr(cudaMemsetAsync(B.ts.flags, 0, 4 * (size_t)n_tiles, s)) ||
-        ckr(cudaMemsetAsync(B.ts.cflags, 0, 4 * (size_t)n_tiles, s)))
-        return TPX_ECUDA;
+    if (ckr(cudaMemsetAsync(B.ts.cflags, 0, 4 * (size_t)n_tiles, s))) return TPX_ECUDA;
     if (ckr(cudaMemsetAsync(bt.run_failed, 0, 4 * (size_t)n_runs, s))) return TPX_ECUDA;
     if (ckr(cudaMemsetAsync(c->ctl, 0, sizeof(tpxk::Ctl), s))) return TPX_ECUDA;
     if (cudaMemsetAsync(d_n_clusters, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_n_trig, 0, 8, s) != cudaSuccess)
@@ -538,9 +536,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     c->seq = (c->seq + 1) & 0x3FFFFFFFu;
     if (c->seq == 0) {   // sequence numbers wrapped: clear every flag once
         c->seq = 1;
-        cudaMemsetAsync(c->ts.flags, 0, sizeof(unsigned) * c->max_tiles, s);
         cudaMemsetAsync(c->ts.cflags, 0, sizeof(unsigned) * c->max_tiles, s);
-        cudaMemsetAsync(B.ts.flags, 0, 4 * (size_t)n_tiles, s);
         cudaMemsetAsync(B.ts.cflags, 0, 4 * (size_t)n_tiles, s);
     }
     tpxk::Params p;
