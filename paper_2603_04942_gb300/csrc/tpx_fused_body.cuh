@@ -30,15 +30,19 @@ __device__ __forceinline__ bool in_bounds(long long i, long long n, const Params
 
 __device__ __forceinline__ int pad(int p) { return p + (p >> 3); }   // conflict-free 8-wide walks
 
-// kept-pixel record: [63:40] tof+bias | [39:26] segment | [25:16] ToT | [15:8] y | [7:0] x
+// kept-pixel record: [63:40] tof+bias | [39:30] ToT | [29:16] segment | [15:8] y | [7:0] x;
+// the low 30 bits are the pixel's cell (segment, y, x)
 __device__ __forceinline__ uint64_t mkrec(uint32_t tofb, uint32_t seg, uint32_t tot, uint32_t x, uint32_t y) {
-    return ((uint64_t)tofb << 40) | ((uint64_t)seg << 26) | ((uint64_t)tot << 16) | ((uint64_t)y << 8) | x;
+    return ((uint64_t)tofb << 40) | ((uint64_t)tot << 30) | ((uint64_t)seg << 16) | ((uint64_t)y << 8) | x;
 }
 __device__ __forceinline__ int r_x(uint64_t r) { return (int)(r & 255); }
 __device__ __forceinline__ int r_y(uint64_t r) { return (int)((r >> 8) & 255); }
-__device__ __forceinline__ int r_tot(uint64_t r) { return (int)((r >> 16) & 1023); }
-__device__ __forceinline__ int r_seg(uint64_t r) { return (int)((r >> 26) & 0x3FFF); }
+__device__ __forceinline__ int r_seg(uint64_t r) { return (int)((r >> 16) & 0x3FFF); }
+__device__ __forceinline__ int r_tot(uint64_t r) { return (int)((r >> 30) & 1023); }
 __device__ __forceinline__ int r_tof(uint64_t r) { return (int)(r >> 40); }
+__device__ __forceinline__ uint32_t r_cell(uint64_t r) { return (uint32_t)r & 0x3FFFFFFFu; }
+// |d| <= dt, for 0 <= dt < 2^31
+__device__ __forceinline__ bool within(int d, int dt) { return (uint32_t)d + (uint32_t)dt <= 2u * (uint32_t)dt; }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -98,9 +102,8 @@ struct __align__(16) Smem {
                                                       // member-list heads
     union { uint16_t next[C]; uint16_t rootof[C]; } u2;
     uint8_t notpeak[C];
-    long long tdc_t[MAXSEG];
-    GAgg warp_agg[NW];
-    GAgg tot_agg;
+    long long tdc_t[MAXSEG];      // unwrapped trigger times of the range
+    uint16_t tdc_pos[MAXSEG];     // their positions
     GAgg E;                       // unwrap state before the tile (from the pre-pass)
     int warp_int[NW + 1];
     unsigned long long cnt[C_NUM];
@@ -114,6 +117,7 @@ struct __align__(16) Smem {
     int pend_run;                 // and whether it is the run's first tile
     bool pend_first;
     int first_tdc;
+    int first_pix;                // first pixel of the range
     int la_first;
     unsigned status;
 };
@@ -122,25 +126,32 @@ struct __align__(16) Smem {
 // reserved per CTA)
 static_assert(MINB * (sizeof(Smem) + 1024) <= 228 * 1024, "shared memory of the tile geometry");
 
-// block exclusive scan of GAgg in thread order; returns this thread's
-// exclusive prefix and leaves the block total in S.tot_agg
-__device__ GAgg block_scan_agg(Smem &S, const GAgg &v, long long tp, long long tt) {
+// block exclusive scan in thread order of two 16-bit halves added
+// separately (__vadd2); each half's sums must fit it. Total in *total.
+__device__ unsigned block_scan_vadd2(Smem &S, unsigned v, unsigned *total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    GAgg incl = warp_incl_scan(v, lane, tp, tt);
-    GAgg wex = shfl_up_agg(incl, 1);
-    if (lane == 0) wex = agg_id();
-    if (lane == 31) S.warp_agg[w] = incl;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = __vadd2(incl, u);
+    }
+    if (lane == 31) S.warp_int[w] = (int)incl;
     __syncthreads();
     if (w == 0) {
-        GAgg x = lane < NW ? S.warp_agg[lane] : agg_id();
-        GAgg xi = warp_incl_scan(x, lane, tp, tt);
-        GAgg xe = shfl_up_agg(xi, 1);
-        if (lane == 0) xe = agg_id();
-        if (lane < NW) S.warp_agg[lane] = xe;
-        if (lane == NW - 1) S.tot_agg = xi;
+        const unsigned x = lane < NW ? (unsigned)S.warp_int[lane] : 0u;
+        unsigned xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi = __vadd2(xi, u);
+        }
+        if (lane < NW) S.warp_int[lane] = (int)__vsub2(xi, x);
+        if (lane == NW - 1) S.warp_int[NW] = (int)xi;
     }
     __syncthreads();
-    GAgg r = acomb(S.warp_agg[w], wex, tp, tt);
+    const unsigned r = __vadd2((unsigned)S.warp_int[w], __vsub2(incl, v));
+    *total = (unsigned)S.warp_int[NW];
     __syncthreads();
     return r;
 }
@@ -408,6 +419,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         if (tid == 0) {
             S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
             S.first_tdc = INT_MAX;
+            S.first_pix = INT_MAX;
             S.status = 0;
         }
         if (tid < C_NUM) S.cnt[tid] = 0;
@@ -503,69 +515,116 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             if (!term && base + L < rend && tid == 0) atomicOr(&S.status, ST_CAPACITY);
         }
 
-        // ---- walk 2: per-thread chain state over [0, L) ----
-        // [0, L) split evenly over all threads, in thread order (every later
-        // per-thread walk and scan uses the same contiguous chunks)
+        // ---- walk 2: wrap steps and TDC counts over [0, L) ----
+        // [0, L) is split evenly over all threads, in thread order (every
+        // later per-thread walk and scan uses the same contiguous chunks). A
+        // thread counts its TDC packets and the pixel wrap steps (Sec. IV.A)
+        // between consecutive pixels from its first pixel up to the first
+        // pixel after its chunk, so that one scan gives every chunk the wraps
+        // before its first pixel.
         const int kpd = (L + NT - 1) / NT;
         const int p0 = tid * kpd;
-        GAgg ex;
-        int ntdc;
+        int ntd = 0, fpx = INT_MAX, jp = 0;
         {
-            GAgg a = agg_id();
+            int lpx = -1;
+            long long lr = 0;
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= L) break;
                 const uint64_t w = S.buf[pad(q)];
                 const unsigned h = (unsigned)(w >> 60);
-                if (h == 0xBu) chain_push(a.pix, pix_raw(w), tp);
-                else if (h == 0x6u) chain_push(a.tdc, tdc_raw(w), tt);
+                if (h == 0xBu) {
+                    const long long r = pix_raw(w);
+                    if (lpx >= 0) jp += (int)jump(r - lr, tp); else fpx = q;
+                    lpx = q;
+                    lr = r;
+                } else if (h == 0x6u) {
+                    ++ntd;
+                }
             }
-            ex = block_scan_agg(S, a, tp, tt);
-            ntdc = (int)S.tot_agg.tdc.n;
+            if (lpx >= 0) {   // the step to the next pixel after the chunk
+                for (int q = p0 + kpd; q < L; ++q) {
+                    const uint64_t w = S.buf[pad(q)];
+                    if ((w >> 60) == 0xBu) { jp += (int)jump(pix_raw(w) - lr, tp); break; }
+                }
+            }
+            const int fw = (int)__reduce_min_sync(0xffffffffu, (unsigned)fpx);
+            if (lane == 0 && fw != INT_MAX) atomicMin(&S.first_pix, fw);
         }
+        // one scan of (TDC count, wrap steps) packed as two 16-bit halves
+        unsigned pk_tot;
+        const unsigned pk_ex = block_scan_vadd2(S, ((unsigned)ntd << 16) | ((unsigned)jp & 0xFFFFu), &pk_tot);
+        const int li0 = (int)(pk_ex >> 16);              // TDC packets before the chunk
+        const int ntdc = (int)(pk_tot >> 16);            // in [0, L)
+        const int jp_ex = (int)(short)(pk_ex & 0xFFFFu); // pixel wraps between the range's first pixel and the chunk
         const GAgg E = S.E;
         // a call sees only its own triggers: "earlier" means earlier in this call
         const long long trig_base = (!BATCH && p.E0) ? p.E0->tdc.n : 0;
         const bool prev_global = E.tdc.n > trig_base;
-        const GAgg st = acomb(E, ex, tp, tt);   // global chain state before position p0
-
-        // ---- walk 3: unwrapped trigger times ----
-        {
-            bool has = st.tdc.n > 0;
-            long long last = st.tdc.last, ep = st.tdc.sum;
-            int li = (int)ex.tdc.n;
+        const int nseg = min(ntdc, MAXSEG);
+        if (ntdc > MAXSEG && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+        // ---- TDC packets of the range in stream order, then their unwrapped
+        // times (one warp, a scan of the wrap steps) ----
+        if (ntd) {
+            int li = li0;
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= L) break;
-                const uint64_t w = S.buf[pad(q)];
-                if ((w >> 60) != 0x6u) continue;
-                const long long r = tdc_raw(w);
-                if (has) ep += jump(r - last, tt);
-                has = true;
-                last = r;
-                const long long t = r + ep * kTdcPeriod;
-                if (li < MAXSEG) S.tdc_t[li] = t; else atomicOr(&S.status, ST_CAPACITY);
-                if (!BATCH && q < cnt) {   // a batch writes its triggers at the flush
-                    const long long g = E.tdc.n - trig_base + li;
-                    if (g >= 0 && g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
-                }
+                if ((S.buf[pad(q)] >> 60) != 0x6u) continue;
+                if (li < MAXSEG) S.tdc_pos[li] = (uint16_t)q;
                 ++li;
             }
         }
         __syncthreads();
-        if (ntdc > MAXSEG && tid == 0) atomicOr(&S.status, ST_CAPACITY);
-        for (int i = tid; i + 1 < min(ntdc, MAXSEG); i += NT)
-            if (S.tdc_t[i + 1] < S.tdc_t[i]) atomicOr(&p.ctl->status, ST_TRIG_ORDER);
+        if (tid < 32) {
+            bool has = E.tdc.n > 0;
+            long long last = E.tdc.last, ep = E.tdc.sum, t_last = 0;
+            for (int i0 = 0; i0 < nseg; i0 += 32) {
+                const int i = i0 + lane;
+                long long r = 0;
+                if (i < nseg) r = tdc_raw(S.buf[pad((int)S.tdc_pos[i])]);
+                const long long rp = __shfl_up_sync(0xffffffffu, r, 1);
+                int st = 0;
+                if (i < nseg && (lane > 0 || has)) st = (int)jump(r - (lane > 0 ? rp : last), tt);
+                int inc = st;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += u;
+                }
+                const long long t = r + (ep + inc) * kTdcPeriod;
+                const long long tp_ = __shfl_up_sync(0xffffffffu, t, 1);
+                if (i < nseg) {
+                    S.tdc_t[i] = t;
+                    if ((lane > 0 || i0 > 0) && t < (lane > 0 ? tp_ : t_last)) atomicOr(&p.ctl->status, ST_TRIG_ORDER);
+                    if (!BATCH && S.tdc_pos[i] < cnt) {   // a batch writes its triggers at the flush
+                        const long long g = E.tdc.n - trig_base + i;
+                        if (g >= 0 && g < p.trig_cap) p.trig[g] = t; else atomicOr(&p.ctl->status, ST_TRIG_CAP);
+                    }
+                }
+                const int lastl = min(31, nseg - 1 - i0);
+                ep += __shfl_sync(0xffffffffu, inc, lastl);
+                last = __shfl_sync(0xffffffffu, r, lastl);
+                t_last = __shfl_sync(0xffffffffu, t, lastl);
+                has = true;
+            }
+        }
+        __syncthreads();
 
         // ---- walk 4: pixels -> shot, cut, timewalk, packed record ----
         {
-            bool has = st.pix.n > 0;
-            long long last = st.pix.last, ep = st.pix.sum;
-            int seg = (int)ex.tdc.n - 1;
+            // wraps at the chunk's first pixel: before the range, the step from
+            // the last pixel before it to the range's first pixel, the steps
+            // inside the range before the chunk
+            const int fp = S.first_pix;
+            const long long j0 = (fp != INT_MAX && E.pix.n > 0) ? jump(pix_raw(S.buf[pad(fp)]) - E.pix.last, tp) : 0;
+            long long ep = E.pix.sum + j0 + jp_ex;
+            bool has = false;
+            long long last = 0;
+            int seg = li0 - 1;
             const long long t_prev_global = E.tdc.last + E.tdc.sum * kTdcPeriod;
             unsigned long long c_keep = 0, c_pre = 0, c_bg = 0;
             bool exc = false;
-            const int nseg = min(ntdc, MAXSEG);
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= L) break;
@@ -663,47 +722,72 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (r == INVALID) continue;
                 uint32_t e0 = (uint32_t)q, e1 = NO_EXT;
                 int ne = 0;
-                {
-                    const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
-                    bool dim = false;
-                    // 8-neighbour box: a diagonal partner (dx = 1, dy = -1 or +1) is
-                    // held back and needs no union when the pixel's partner to the
-                    // side (dx = 1, dy = 0), or above it (dx = 0, dy = +1) for
-                    // dy = +1, is adjacent to it as well: that path of two
-                    // axis-aligned pairs, which are never held back, joins them
-                    const bool box1 = MODE == TPX_MODE_CC && p.rx == 1 && p.ry == 1;
+                const int x = r_x(r), y = r_y(r), sg = r_seg(r), tb = r_tof(r), tot = r_tot(r);
+                const uint32_t hb = (uint32_t)(x + 67 * y + 1543 * sg);   // hcell of (x, y), unmasked
+                bool dim = false;
+                if (MODE == TPX_MODE_CC && p.rx == 1 && p.ry == 1) {
+                    // 8-neighbour box, its five forward cells unrolled. A diagonal
+                    // partner (dx = 1, dy = -1 or +1) is held back and needs no
+                    // union when the pixel's partner to the side (dx = 1, dy = 0),
+                    // or above it (dx = 0, dy = +1) for dy = +1, is adjacent to it
+                    // as well: that path of two axis-aligned pairs, which are never
+                    // held back, joins them
                     uint32_t hold = 0xFFFFFFFFu;   // held partners: dy = -1 low half, dy = +1 high half
                     int tA = 0, tB = 0, tE = INT_MIN, tN = INT_MIN;
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) {
+                        const int dx = c < 2 ? 0 : 1;
+                        const int dy = c == 0 ? 0 : (c == 1 ? 1 : c - 3);
+                        if (x + dx > 255 || y + dy < 0 || y + dy > 255) continue;
+                        const uint32_t ck = r_cell(r) + (uint32_t)(256 * dy + dx);
+                        for (uint32_t j = S.u1.head[(hb + 67 * dy + dx) & (HB - 1)]; j != EMPTY; j = S.u2.next[j]) {
+                            if (!TPX_IN(j, C)) break;
+                            if (c == 0 && (int)j <= q) continue;
+                            const uint64_t rj = S.buf[pad((int)j)];
+                            if (r_cell(rj) != ck) continue;
+                            const int tjt = r_tof(rj);
+                            if (!within(tjt - tb, p.dt)) continue;
+                            const int tj = r_tot(rj);
+                            // local maxima: equal ToT goes to the later pixel (Sec. V.B)
+                            if (tj > tot || (tj == tot && (int)j > q)) dim = true;
+                            else S.notpeak[j] = 1;
+                            if (c == 3 && tE == INT_MIN) tE = tjt;
+                            if (c == 1 && tN == INT_MIN) tN = tjt;
+                            if (c == 2 || c == 4) {
+                                const int sh = c == 4 ? 16 : 0;
+                                if (((hold >> sh) & 0xFFFFu) == 0xFFFFu) {
+                                    hold = (hold & ~(0xFFFFu << sh)) | (j << sh);
+                                    if (c == 4) tB = tjt; else tA = tjt;
+                                    continue;
+                                }
+                            }
+                            if (ne == 0) e0 = j; else if (ne == 1) e1 = j;
+                            ++ne;
+                        }
+                    }
+                    const uint32_t jA = hold & 0xFFFFu, jB = hold >> 16;
+                    const bool skipA = tE != INT_MIN && within(tE - tA, p.dt);
+                    const bool skipB = (tE != INT_MIN && within(tE - tB, p.dt)) || (tN != INT_MIN && within(tN - tB, p.dt));
+                    if (jA != 0xFFFFu && !skipA) { if (ne == 0) e0 = jA; else if (ne == 1) e1 = jA; ++ne; }
+                    if (jB != 0xFFFFu && !skipB) { if (ne == 0) e0 = jB; else if (ne == 1) e1 = jB; ++ne; }
+                } else {
                     for (int dx = 0; dx <= p.rx; ++dx) {
                         const int cx = x + dx;
                         if (cx > 255) break;
                         for (int dy = (dx == 0 ? 0 : -p.ry); dy <= p.ry; ++dy) {
                             const int cy = y + dy;
                             if (cy < 0 || cy > 255) continue;
-                            for (uint32_t j = S.u1.head[hcell(sg, cx, cy)]; j != EMPTY; j = S.u2.next[j]) {
+                            const uint32_t ck = r_cell(r) + (uint32_t)(256 * dy + dx);
+                            for (uint32_t j = S.u1.head[(hb + 67 * dy + dx) & (HB - 1)]; j != EMPTY; j = S.u2.next[j]) {
                                 if (!TPX_IN(j, C)) break;
                                 if (dx == 0 && dy == 0 && (int)j <= q) continue;
                                 const uint64_t rj = S.buf[pad((int)j)];
-                                if (r_x(rj) != cx || r_y(rj) != cy || r_seg(rj) != sg) continue;
-                                const int d = r_tof(rj) - tb;
-                                if (d < -p.dt || d > p.dt) continue;
+                                if (r_cell(rj) != ck) continue;
+                                if (!within(r_tof(rj) - tb, p.dt)) continue;
                                 const int tj = r_tot(rj);
                                 // local maxima: equal ToT goes to the later pixel (Sec. V.B)
                                 if (tj > tot || (tj == tot && (int)j > q)) dim = true;
                                 else S.notpeak[j] = 1;
-                                if (box1) {
-                                    const int tjt = r_tof(rj);
-                                    if (dx == 1 && dy == 0 && tE == INT_MIN) tE = tjt;
-                                    if (dx == 0 && dy == 1 && tN == INT_MIN) tN = tjt;
-                                    if (dx == 1 && dy != 0) {
-                                        const int sh = dy > 0 ? 16 : 0;
-                                        if (((hold >> sh) & 0xFFFFu) == 0xFFFFu) {
-                                            hold = (hold & ~(0xFFFFu << sh)) | ((uint32_t)j << sh);
-                                            if (dy > 0) tB = tjt; else tA = tjt;
-                                            continue;
-                                        }
-                                    }
-                                }
                                 if (MODE == TPX_MODE_CC) {
                                     if (ne == 0) e0 = j; else if (ne == 1) e1 = j;
                                     ++ne;
@@ -711,15 +795,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                             }
                         }
                     }
-                    if (box1) {
-                        const uint32_t jA = hold & 0xFFFFu, jB = hold >> 16;
-                        const bool skipA = tE != INT_MIN && abs(tE - tA) <= p.dt;
-                        const bool skipB = (tE != INT_MIN && abs(tE - tB) <= p.dt) || (tN != INT_MIN && abs(tN - tB) <= p.dt);
-                        if (jA != 0xFFFFu && !skipA) { if (ne == 0) e0 = jA; else if (ne == 1) e1 = jA; ++ne; }
-                        if (jB != 0xFFFFu && !skipB) { if (ne == 0) e0 = jB; else if (ne == 1) e1 = jB; ++ne; }
-                    }
-                    if (dim) S.notpeak[q] = 1;
                 }
+                if (dim) S.notpeak[q] = 1;
                 if (MODE == TPX_MODE_CC) S.parent[q] = ((ne > 2 ? REWALK : e1) << 16) | e0;
             }
         }
@@ -791,11 +868,33 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     if (TPX_IN(rt, C)) mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[rt], (uint32_t)q);
                 }
             __syncthreads();
-            // each root walks its list for the cluster's earliest pixel in
-            // (time, position) order -- its canonical label -- keeps it in the
-            // upper half of the list head and flags it (bit 1 of notpeak)
-            for (int q = R0 + tid; q < R1; q += NT) {
-                if (S.buf[pad(q)] == INVALID || S.u2.rootof[q] != q) continue;
+            // the roots in position order (the label positions of the cluster
+            // ids take the second half of the union-find array later)
+            uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
+            {
+                int c = 0;
+                for (int j = 0; j < kpd; ++j) {
+                    const int q = p0 + j;
+                    if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
+                }
+                int excl = block_scan_int(S, c, &ncl);
+                for (int j = 0; j < kpd; ++j) {
+                    const int q = p0 + j;
+                    if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
+                        if (TPX_IN(excl, C)) rootpos[excl] = (uint16_t)q;
+                        ++excl;
+                    }
+                }
+            }
+            __syncthreads();
+            // one thread per root walks its list for the cluster's earliest
+            // pixel in (time, position) order -- its canonical label -- keeps
+            // it in the upper half of the list head and flags it (bit 1 of
+            // notpeak)
+            for (int i = tid; i < ncl; i += NT) {
+                if (!TPX_IN(i, C)) break;
+                const uint32_t q = rootpos[i];
+                if (!TPX_IN(q, C)) continue;
                 const uint32_t head = S.u1.mhead[q] & 0xFFFFu;
                 uint64_t best = ~0ull;
                 for (uint32_t m = head; m != EMPTY; m = mnext[m]) {
@@ -814,9 +913,6 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) ++c;
             }
             int excl = block_scan_int(S, c, &ncl);
-            // the label position of each cluster id: the second half of the
-            // union-find array
-            uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
             for (int j = 0; j < kpd; ++j) {
                 const int q = p0 + j;
                 if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) {
