@@ -597,7 +597,48 @@ def refiner_bench(args) -> dict:
     torch.cuda.synchronize()
     fp32_ms = e[0].elapsed_time(e[1]) / reps
     del work
+    # the convolutional refiner: trained on the same rows, inferred with
+    # tcgen05 implicit GEMMs on bf16 patches
+    cnn = R.CnnRefiner(ctx, seed=0)
+    t0 = time.perf_counter()
+    closses = cnn.train(train, epochs=args.refiner_epochs, batch=4096, lr=2e-3, lr_final=1e-4)
+    ctrain_s = time.perf_counter() - t0
+    cev = R.evaluate(test, cnn.refine_rows(test, thr))
+    cev32 = R.evaluate(test, cnn.refine_rows(test, thr, fp32=True))
+    ch_all = cnn.refine(test.patches16, test.clusters_dev, test.n_selected, thr)[: test.n_selected].cpu().numpy()
+    hist["refined_cnn"] = R.pair_distance_histogram(*R.hit_list(test, ch_all), 4.0, bins).tolist()
+    pt16 = ctx.tpx_refine_patches_bf16(d, out["labels"], out["clusters"], n_cl, R.MIN_PIXELS)
+    cnn.infer(pt16["patches"], ns, o6)
+    cwork = torch.empty(int(tpx.lib().tpx_cnn_infer_work_bytes(ns)), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        ctx.tpx_cnn_infer(cnn.packed, pt16["patches"], ns, work=cwork, out=o6)
+    torch.cuda.synchronize()
+    ctot = [0.0, 0.0, 0.0]
+    for _ in range(reps):
+        e[0].record(ctx.stream)
+        p16 = ctx.tpx_refine_patches_bf16(d, out["labels"], out["clusters"], n_cl, R.MIN_PIXELS)   # synchronises (count)
+        e[1].record(ctx.stream)
+        ctx.tpx_cnn_infer(cnn.packed, p16["patches"], ns, work=cwork, out=o6)
+        e[2].record(ctx.stream)
+        ctx.tpx_refine_decide(o6, out["clusters"], p16["sel"], p16["centre"], ns, thr, hits)
+        e[3].record(ctx.stream)
+        torch.cuda.synchronize()
+        for k in range(3):
+            ctot[k] += e[k].elapsed_time(e[k + 1]) / reps
+        del p16
+    rc_c, _ = ctx.tpx_sync(check=False)
     ctx.close()
+    cflops = 2 * ns * (49 * 18 * 16 + 25 * 144 * 16 + 9 * 144 * 32 + 288 * 144 + 144 * 6)
+    cms = sum(ctot)
+    cnn_res = {"network": f"CNN: conv 3x3 2->16->16->32 channels (9x9 -> 3x3), fc 288->144->6, {cnn.n_params:,} "
+                          "parameters; trained in fp32, inferred with tcgen05 (bf16 operands, fp32 accumulators in "
+                          "tensor memory)",
+               "train_s": round(ctrain_s, 2), "train_clusters_per_s": args.refiner_epochs * train.x.shape[0] / ctrain_s,
+               "loss_first": float(closses[:10].mean()), "loss_last": float(closses[-10:].mean()), "eval": cev,
+               "eval_fp32": {k: cev32[k] for k in ("pair_recall", "single_split", "pair_err_refined", "fallback")},
+               "infer": {"clusters": ns, "patches_ms": ctot[0], "network_ms": ctot[1], "decide_ms": ctot[2],
+                         "clusters_per_s": ns / (cms / 1e3), "network_tflops": cflops / (ctot[1] / 1e3) / 1e12,
+                         "status": rc_c}}
     ms = sum(tot)
     flops = 2 * ns * (162 * net.h + net.h * net.h + net.h * 6)
     return {"workload": f"{args.refiner_shots:,} shots x Poisson(20) ion-like particles, 30% with a planted "
@@ -614,7 +655,8 @@ def refiner_bench(args) -> dict:
             "infer": {"clusters": ns, "patches_ms": tot[0], "network_ms": tot[1], "decide_ms": tot[2],
                       "clusters_per_s": ns / (ms / 1e3), "network": "bf16 tensor cores (mma.sync), fp32 sums",
                       "network_tflops": flops / (tot[1] / 1e3) / 1e12,
-                      "fp32_network_ms": fp32_ms, "fp32_network_tflops": flops / (fp32_ms / 1e3) / 1e12}}
+                      "fp32_network_ms": fp32_ms, "fp32_network_tflops": flops / (fp32_ms / 1e3) / 1e12},
+            "cnn": cnn_res}
 
 
 def run_reference(args):
@@ -806,6 +848,8 @@ def main():
             # the main path's cluster rate: the budget the refiner's inference is held to
             refiner["main_path_clusters_per_s"] = value * n_cl / max(1, hits) / world
             refiner["infer"]["vs_main_path"] = refiner["infer"]["clusters_per_s"] / refiner["main_path_clusters_per_s"]
+            refiner["cnn"]["infer"]["vs_main_path"] = (refiner["cnn"]["infer"]["clusters_per_s"] /
+                                                       refiner["main_path_clusters_per_s"])
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

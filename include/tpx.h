@@ -381,6 +381,57 @@ int tpx_refiner_infer(tpx_ctx *ctx, const void *d_packed, int32_t hidden, const 
 int tpx_refine_decide(tpx_ctx *ctx, const float *d_out, const tpx_record *d_clusters, const int64_t *d_sel,
                       const int32_t *d_centre, int64_t n, float threshold, float *d_hits);
 
+/* ---- the convolutional refiner (the same patch, count and offsets) ----
+   The 2 x 9 x 9 patch through three 3 x 3 convolutions without padding and
+   two dense layers: conv1 2 -> 16 channels (7 x 7), conv2 16 -> 16 (5 x 5),
+   conv3 16 -> 32 (3 x 3), fc1 288 -> 144 (conv3's map flattened in channel,
+   row, column order), fc2 144 -> 6; ReLU after every layer but the last.
+   A convolution is out[co][y][x] = b[co] + sum W[co][ci][ky][kx]
+   in[ci][y + ky][x + kx].  Parameters: one fp32 array of tpx_cnn_params()
+   floats: W1 [16][2][3][3], b1, W2 [16][16][3][3], b2, W3 [32][16][3][3], b3,
+   W4 [144][288], b4, W5 [6][144], b5. */
+
+/* Number of parameters (49,750). */
+int64_t tpx_cnn_params(void);
+
+/* Floats of workspace tpx_cnn_forward and tpx_cnn_train_step need for n
+   patches. */
+int64_t tpx_cnn_work_floats(int64_t n);
+
+/* fp32 forward pass of n <= 2^22 patches: d_x [n x 162] floats (channel 0,
+   then channel 1, rows of 9), d_out [n x 6].  Asynchronous. */
+int tpx_cnn_forward(tpx_ctx *ctx, const float *d_params, const float *d_x, int64_t n, float *d_work, float *d_out);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, step >= 1) on a minibatch of
+   1 <= n <= 2^20 patches, targets d_y [n x 5] and loss as in
+   tpx_refiner_train_step; d_grad receives the gradient, *d_loss the loss
+   before the step.  fp32 GEMMs over the layers' im2col matrices.
+   Asynchronous. */
+int tpx_cnn_train_step(tpx_ctx *ctx, float *d_params, float *d_adam_m, float *d_adam_v, float *d_grad, int64_t step,
+                       const float *d_x, const float *d_y, int64_t n, float lr, float offset_weight, float *d_work,
+                       float *d_loss);
+
+/* Inference on the tensor cores (tcgen05, fp32 accumulation in tensor
+   memory): tpx_cnn_pack writes a bf16 copy of the weights (and fp32 biases)
+   to d_packed (tpx_cnn_packed_bytes() bytes, 256-byte aligned);
+   tpx_cnn_infer runs the five layers as implicit GEMMs over n <= 2^30
+   patches d_x [n x 162] bf16 (16-byte aligned; tpx_refine_patches_bf16),
+   each hidden activation rounded to bf16 after its ReLU, into d_out [n x 6]
+   floats.  d_work: tpx_cnn_infer_work_bytes(n) bytes, 16-byte aligned (the
+   bf16 activations between layers).  Asynchronous; a tensor-core wait that
+   runs out sets the context's status (TPX_EDEVTIMEOUT at tpx_sync). */
+int64_t tpx_cnn_packed_bytes(void);
+int tpx_cnn_pack(tpx_ctx *ctx, const float *d_params, void *d_packed);
+int64_t tpx_cnn_infer_work_bytes(int64_t n);
+int tpx_cnn_infer(tpx_ctx *ctx, const void *d_packed, const uint16_t *d_x, int64_t n, void *d_work, float *d_out);
+
+/* tpx_refine_patches writing the patches as bf16 [capacity x 162] (the patch
+   values are exact in bf16: 324 bytes a patch instead of 648). */
+int tpx_refine_patches_bf16(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets, int64_t packet_index_base,
+                            const int64_t *d_labels, const tpx_record *d_clusters, int64_t n_clusters,
+                            int32_t min_pixels, uint16_t *d_patches, int64_t *d_sel, int32_t *d_centre,
+                            int64_t capacity, int64_t *d_n_patches);
+
 /* Batched runs (Sec. VI batches shots by zero-padding them to a rectangle;
    here nothing is padded): n_runs independent acquisitions concatenated in
    one device buffer, run r being packets [h_run_offsets[r],

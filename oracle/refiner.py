@@ -205,3 +205,131 @@ def decide(out: np.ndarray, centre: np.ndarray, centroid_xy: np.ndarray, thresho
         else:
             res[s] = (1 if -margin[s] >= lt else 0, np.float32(centroid_xy[s][0]), np.float32(centroid_xy[s][1]), 0, 0)
     return res
+
+
+# ---------------------------------------------------------------- CNN
+# The convolutional refiner: the same patch, count and offsets, through three
+# 3 x 3 convolutions without padding and two dense layers:
+#   input  2 x 9 x 9 (ToT, ToA)
+#   conv1  2 -> 16 channels, 7 x 7, ReLU
+#   conv2 16 -> 16 channels, 5 x 5, ReLU
+#   conv3 16 -> 32 channels, 3 x 3, ReLU
+#   fc1   288 (conv3 flattened channel, row, column) -> 144, ReLU
+#   fc2   144 -> 6
+# A convolution here is the plain cross-correlation
+#   out[co, y, x] = b[co] + sum_{ci, ky, kx} W[co, ci, ky, kx] in[ci, y + ky, x + kx].
+# Parameters, flat: W1 [16, 2, 3, 3], b1, W2 [16, 16, 3, 3], b2, W3 [32, 16, 3, 3],
+# b3, W4 [144, 288], b4, W5 [6, 144], b5 (49,750 floats).
+CNN_SHAPES = (("w1", (16, 2, 3, 3)), ("b1", (16,)), ("w2", (16, 16, 3, 3)), ("b2", (16,)),
+              ("w3", (32, 16, 3, 3)), ("b3", (32,)), ("w4", (144, 288)), ("b4", (144,)),
+              ("w5", (NOUT, 144)), ("b5", (NOUT,)))
+
+
+def cnn_layout() -> dict:
+    o, d = 0, {}
+    for name, shape in CNN_SHAPES:
+        size = int(np.prod(shape))
+        d[name] = (o, size, shape)
+        o += size
+    d["total"] = o
+    return d
+
+
+def cnn_unpack(p: np.ndarray) -> dict:
+    L = cnn_layout()
+    return {k: p[L[k][0]: L[k][0] + L[k][1]].reshape(L[k][2]) for k, _ in CNN_SHAPES}
+
+
+def conv2d(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """x [n, ci, h, w], w [co, ci, 3, 3] -> [n, co, h - 2, w - 2], the sum
+    written out over the nine kernel taps."""
+    n, ci, h, wd = x.shape
+    co = w.shape[0]
+    out = np.zeros((n, co, h - 2, wd - 2), np.float64) + b.reshape(1, co, 1, 1)
+    for ky in range(3):
+        for kx in range(3):
+            patch = x[:, :, ky: ky + h - 2, kx: kx + wd - 2]          # [n, ci, h-2, w-2]
+            out += np.einsum("nchw,oc->nohw", patch, w[:, :, ky, kx])
+    return out
+
+
+def conv2d_back(x: np.ndarray, w: np.ndarray, d: np.ndarray):
+    """Gradients of conv2d given d = d loss / d out: (d x, d w, d b)."""
+    n, ci, h, wd = x.shape
+    dx = np.zeros_like(x, dtype=np.float64)
+    dw = np.zeros_like(w, dtype=np.float64)
+    for ky in range(3):
+        for kx in range(3):
+            patch = x[:, :, ky: ky + h - 2, kx: kx + wd - 2]
+            dw[:, :, ky, kx] = np.einsum("nohw,nchw->oc", d, patch)
+            dx[:, :, ky: ky + h - 2, kx: kx + wd - 2] += np.einsum("nohw,oc->nchw", d, w[:, :, ky, kx])
+    return dx, dw, d.sum(axis=(0, 2, 3))
+
+
+def cnn_forward(p: np.ndarray, x: np.ndarray, keep: bool = False, act=None):
+    """The CNN in float64; `act` (optional) maps every hidden activation after
+    its ReLU (the inference precision passes bf16 rounding)."""
+    P = cnn_unpack(np.asarray(p, np.float64))
+    a0 = np.asarray(x, np.float64).reshape(-1, 2, PS, PS)
+    f = act or (lambda a: a)
+    a1 = f(np.maximum(conv2d(a0, P["w1"], P["b1"]), 0.0))
+    a2 = f(np.maximum(conv2d(a1, P["w2"], P["b2"]), 0.0))
+    a3 = f(np.maximum(conv2d(a2, P["w3"], P["b3"]), 0.0))
+    h3 = a3.reshape(a3.shape[0], -1)                                  # (channel, row, column)
+    a4 = f(np.maximum(h3 @ P["w4"].T + P["b4"], 0.0))
+    out = a4 @ P["w5"].T + P["b5"]
+    return (out, (a0, a1, a2, a3, a4)) if keep else out
+
+
+def cnn_forward_bf16(p: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """The inference precision: inputs and weights rounded to bf16 (biases
+    float32), sums exact, every hidden activation rounded to bf16 after its
+    ReLU; the outputs unrounded."""
+    p32 = np.asarray(p, np.float32)
+    L = cnn_layout()
+    q = p32.copy()
+    for k, _ in CNN_SHAPES:
+        if k.startswith("w"):
+            o, size, _ = L[k]
+            q[o: o + size] = bf16_array(p32[o: o + size])
+    r = lambda a: bf16_array(np.asarray(a, np.float32)).astype(np.float64)   # noqa: E731
+    return cnn_forward(q.astype(np.float64), r(x), act=r)
+
+
+def cnn_loss(p: np.ndarray, x: np.ndarray, y: np.ndarray, w_off: float) -> float:
+    out = cnn_forward(p, x)
+    y = np.asarray(y, np.float64)
+    two = y[:, 0] > 1.5
+    z = np.logaddexp(out[:, 0], out[:, 1])
+    ce = z - np.where(two, out[:, 1], out[:, 0])
+    used = np.stack([np.ones_like(two), np.ones_like(two), two, two], axis=1)
+    se = (((out[:, 2:] - y[:, 1:]) ** 2) * used).sum(axis=1)
+    return float(np.mean(ce + 0.5 * w_off * se))
+
+
+def cnn_grad(p: np.ndarray, x: np.ndarray, y: np.ndarray, w_off: float) -> np.ndarray:
+    """d loss / d p by the chain rule through the five layers."""
+    y = np.asarray(y, np.float64)
+    P = cnn_unpack(np.asarray(p, np.float64))
+    out, (a0, a1, a2, a3, a4) = cnn_forward(p, x, keep=True)
+    n = out.shape[0]
+    two = y[:, 0] > 1.5
+    p2 = 1.0 / (1.0 + np.exp(out[:, 0] - out[:, 1]))
+    dout = np.zeros_like(out)
+    dout[:, 0] = (1.0 - p2) - (~two)
+    dout[:, 1] = p2 - two
+    used = np.stack([np.ones_like(two), np.ones_like(two), two, two], axis=1)
+    dout[:, 2:] = w_off * (out[:, 2:] - y[:, 1:]) * used
+    dout /= n
+    g = {}
+    g["w5"], g["b5"] = dout.T @ a4, dout.sum(0)
+    d4 = (dout @ P["w5"]) * (a4 > 0)
+    h3 = a3.reshape(n, -1)
+    g["w4"], g["b4"] = d4.T @ h3, d4.sum(0)
+    d3 = ((d4 @ P["w4"]).reshape(a3.shape)) * (a3 > 0)
+    dx2, g["w3"], g["b3"] = conv2d_back(a2, P["w3"], d3)
+    d2 = dx2 * (a2 > 0)
+    dx1, g["w2"], g["b2"] = conv2d_back(a1, P["w2"], d2)
+    d1 = dx1 * (a1 > 0)
+    _, g["w1"], g["b1"] = conv2d_back(a0, P["w1"], d1)
+    return np.concatenate([g[k].ravel() for k, _ in CNN_SHAPES])

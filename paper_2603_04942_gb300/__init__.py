@@ -44,7 +44,9 @@ EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_dest
                     "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_debug_noalloc_seq", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_stream_snapshot_bytes", "tpx_stream_snapshot", "tpx_stream_restore",
-                    "tpx_strerror", "tpx_version")
+                    "tpx_cnn_params", "tpx_cnn_work_floats", "tpx_cnn_forward", "tpx_cnn_train_step",
+                    "tpx_cnn_packed_bytes", "tpx_cnn_pack", "tpx_cnn_infer_work_bytes", "tpx_cnn_infer",
+                    "tpx_refine_patches_bf16", "tpx_strerror", "tpx_version")
 
 
 class _CConfig(ctypes.Structure):
@@ -156,6 +158,20 @@ def load(path: str | None = None):
         L.tpx_refiner_infer.argtypes = [vp, vp, i32, vp, i64, vp]
         for f in ("tpx_refine_patches", "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
                   "tpx_refiner_pack", "tpx_refiner_infer"):
+            getattr(L, f).restype = i32
+        L.tpx_refine_patches_bf16.argtypes = [vp, vp, i64, i64, vp, vp, i64, i32, vp, vp, vp, i64, vp]
+        L.tpx_refine_patches_bf16.restype = i32
+        for f in ("tpx_cnn_params", "tpx_cnn_packed_bytes"):
+            getattr(L, f).argtypes = []
+            getattr(L, f).restype = i64
+        for f in ("tpx_cnn_work_floats", "tpx_cnn_infer_work_bytes"):
+            getattr(L, f).argtypes = [i64]
+            getattr(L, f).restype = i64
+        L.tpx_cnn_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.tpx_cnn_train_step.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp]
+        L.tpx_cnn_pack.argtypes = [vp, vp, vp]
+        L.tpx_cnn_infer.argtypes = [vp, vp, vp, i64, vp, vp]
+        for f in ("tpx_cnn_forward", "tpx_cnn_train_step", "tpx_cnn_pack", "tpx_cnn_infer"):
             getattr(L, f).restype = i32
         L.tpx_set_state.argtypes = [vp, ctypes.POINTER(_CState)]
         L.tpx_get_state.argtypes = [vp, ctypes.POINTER(_CState)]
@@ -439,6 +455,74 @@ class Context:
         if rc and rc != EOVERFLOW:
             raise TpxError(rc, "tpx_refine_patches")
         out["status"] = rc   # TPX_EOVERFLOW: only the first `capacity` patches were written
+        return out
+
+    def tpx_refine_patches_bf16(self, packets, labels, clusters, n_clusters: int, min_pixels: int = 12,
+                                capacity: int | None = None, index_base: int = 0) -> dict:
+        """tpx_refine_patches with the patches as bf16 (device int16 tensor
+        [n x 162] holding the bf16 bits)."""
+        import torch
+        dev = packets.device
+        cap = int(capacity if capacity is not None else max(1, n_clusters))
+        out = dict(patches=torch.empty((cap, 162), dtype=torch.int16, device=dev),
+                   sel=torch.empty(cap, dtype=torch.int64, device=dev),
+                   centre=torch.empty((cap, 2), dtype=torch.int32, device=dev),
+                   n=torch.zeros(1, dtype=torch.int64, device=dev), capacity=cap)
+        rc = lib().tpx_refine_patches_bf16(self._h, _ptr(packets), int(packets.numel()), int(index_base), _ptr(labels),
+                                           _ptr(clusters), int(n_clusters), int(min_pixels), _ptr(out["patches"]),
+                                           _ptr(out["sel"]), _ptr(out["centre"]), cap, _ptr(out["n"]))
+        if rc and rc != EOVERFLOW:
+            raise TpxError(rc, "tpx_refine_patches_bf16")
+        out["status"] = rc
+        return out
+
+    # -- the convolutional refiner --
+    @staticmethod
+    def tpx_cnn_params() -> int:
+        return int(lib().tpx_cnn_params())
+
+    def tpx_cnn_forward(self, params, x, n: int | None = None, work=None, out=None):
+        import torch
+        n = int(x.shape[0] if n is None else n)
+        if work is None:
+            work = torch.empty(max(1, int(lib().tpx_cnn_work_floats(n))), dtype=torch.float32, device=x.device)
+        if out is None:
+            out = torch.empty((max(1, n), 6), dtype=torch.float32, device=x.device)
+        rc = lib().tpx_cnn_forward(self._h, _ptr(params), _ptr(x), n, _ptr(work), _ptr(out))
+        if rc:
+            raise TpxError(rc, "tpx_cnn_forward")
+        return out
+
+    def tpx_cnn_train_step(self, params, adam_m, adam_v, grad, step: int, x, y, lr: float, offset_weight: float,
+                           work, loss, n: int | None = None):
+        n = int(x.shape[0] if n is None else n)
+        rc = lib().tpx_cnn_train_step(self._h, _ptr(params), _ptr(adam_m), _ptr(adam_v), _ptr(grad), int(step),
+                                      _ptr(x), _ptr(y), n, float(lr), float(offset_weight), _ptr(work), _ptr(loss))
+        if rc:
+            raise TpxError(rc, "tpx_cnn_train_step")
+
+    def tpx_cnn_pack(self, params, packed=None):
+        import torch
+        nb = int(lib().tpx_cnn_packed_bytes())
+        if packed is None:
+            packed = torch.empty(nb + 256, dtype=torch.uint8, device=params.device)
+        rc = lib().tpx_cnn_pack(self._h, _ptr(params), _ptr(packed))
+        if rc:
+            raise TpxError(rc, "tpx_cnn_pack")
+        return packed
+
+    def tpx_cnn_infer(self, packed, x, n: int | None = None, work=None, out=None):
+        """The CNN on the tensor cores; x: bf16 patches (int16 tensor of the
+        bits, [n x 162])."""
+        import torch
+        n = int(x.shape[0] if n is None else n)
+        if work is None:
+            work = torch.empty(max(16, int(lib().tpx_cnn_infer_work_bytes(n))), dtype=torch.uint8, device=x.device)
+        if out is None:
+            out = torch.empty((max(1, n), 6), dtype=torch.float32, device=x.device)
+        rc = lib().tpx_cnn_infer(self._h, _ptr(packed), _ptr(x), n, _ptr(work), _ptr(out))
+        if rc:
+            raise TpxError(rc, "tpx_cnn_infer")
         return out
 
     @staticmethod

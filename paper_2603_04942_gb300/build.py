@@ -15,7 +15,7 @@ LIB = os.path.join(OUT_DIR, "libtpx.so")
 # index and reports a violation in the status word instead of touching memory)
 CHECKED_LIB = os.path.join(OUT_DIR, "libtpx_checked.so")
 SOURCES = ["tpx_fused.cu", "tpx_prepass.cu", "tpx_runtime.cu", "tpx_noalloc.cu", "tpx_general.cu", "tpx_stream.cu",
-           "tpx_refine.cu"]
+           "tpx_refine.cu", "tpx_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -30,6 +30,7 @@ struct tpx_ctx {
     tpxk::TileScratch ts;
     void *scratch;            // one allocation for all tile records
     tpx_record *stage;        // fused-kernel record staging (inside scratch)
+    uint16_t *stage_perm;     // the staged records' label order (inside scratch)
     int64_t stage_records;    // its capacity
     tpxk::Ctl *ctl;           // device control block
     tpxk::Ctl *h_ctl;         // pinned host copy
@@ -145,3 +146,7 @@ size_t cluster_bytes(long long n);
 int centroid_impl(tpx_ctx *c, const tpx_hits &h, const int64_t *labels, const uint8_t *is_peak, int64_t n,
                   tpx_record *out, int64_t cap, int64_t *d_n_clusters);
 }  // namespace tpxg
+
+// the refiners' shared loss and Adam step (tpx_refine.cu)
+int tpxr_loss(cudaStream_t s, const float *out, const float *y, int n, float w_off, float *dout, float *loss);
+int tpxr_adam(cudaStream_t s, float *p, const float *g, float *m, float *v, long long n, float lr, long long step);

@@ -111,6 +111,8 @@ struct Params {
     Ctl *ctl;
     tpx_record *stage;       // per-CTA record staging (range-capacity records per
                              // CTA of the grid), or NULL: inline offset look-back
+    uint16_t *stage_perm;    // per CTA of the grid, range-capacity entries: the staged
+                             // record of each cluster id in label order (CC mode)
     BatchTable bt;           // batch of runs (tile_run == NULL: one stream)
     long long hold;          // tile + 1 whose look-back flags stay unpublished (0: none): lets a
                              // test run its successors' bounded waits out (TPX_EDEVTIMEOUT)

@@ -106,7 +106,9 @@ struct __align__(16) Smem {
     uint16_t tdc_pos[MAXSEG];     // their positions
     GAgg E;                       // unwrap state before the tile (from the pre-pass)
     int warp_int[NW + 1];
-    unsigned long long cnt[C_NUM];
+    unsigned long long cnt[C_NUM];   // this tile's counters
+    unsigned long long acc[C_NUM];   // this CTA's counters, added to the call's at its end
+    long long next_tile;          // claimed while the current tile runs
     long long tile;
     long long clo;
     long long pend_tile;          // staged records awaiting their offset (-1: none)
@@ -380,7 +382,7 @@ __device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long
 // in the CTA's staging slot until the next tile (or the end of the kernel)
 // resolves their offset, when the predecessors' counts are long published;
 // then one coalesced copy.
-template <bool BATCH>
+template <int MODE, bool BATCH>
 __device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
     const long long pt = S.pend_tile;
     if (pt < 0) return;
@@ -392,7 +394,15 @@ __device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
     constexpr int WPR = (int)(sizeof(tpx_record) / 8);
     const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
-    for (long long w = threadIdx.x; w < keep * WPR; w += NT) dst[w] = __ldcg(src + w);
+    if (MODE == TPX_MODE_CC) {   // staged in root order: copied out in label order
+        const uint16_t *perm = p.stage_perm + (long long)blockIdx.x * C;
+        for (long long w = threadIdx.x; w < keep * WPR; w += NT) {
+            const long long k = w / WPR;
+            dst[w] = __ldcg(src + (long long)__ldcg(perm + k) * WPR + (w - k * WPR));
+        }
+    } else {
+        for (long long w = threadIdx.x; w < keep * WPR; w += NT) dst[w] = __ldcg(src + w);
+    }
     if (BATCH) {
         const long long TO = S.tlo;
         const long long tkeep = min((long long)nt, max(0LL, p.trig_cap - TO));
@@ -412,27 +422,38 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
     const long long tp = p.thr_pix, tt = p.thr_tdc;
     const unsigned seq = p.seq & 0x3FFFFFFFu;
     const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(S.parent);
-    if (tid == 0) S.pend_tile = -1;
+    if (tid == 0) {
+        S.pend_tile = -1;
+        S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
+    }
+    if (tid < C_NUM) S.acc[tid] = 0;
+    __syncthreads();
+    // the unwrap state before the first tile, from the pre-pass
+    if (tid < 8 && S.tile < p.n_tiles)
+        reinterpret_cast<long long *>(&S.E)[tid] = __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[S.tile]) + tid);
 
     for (;;) {
         __syncthreads();
+        const long long tile = S.tile;
+        // the next tile is claimed now; its number is needed only at the end
+        unsigned long long claim = 0;
         if (tid == 0) {
-            S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
+            if (tile < p.n_tiles) claim = atomicAdd(&p.ctl->tile_counter, 1u);
             S.first_tdc = INT_MAX;
             S.first_pix = INT_MAX;
             S.status = 0;
         }
         if (tid < C_NUM) S.cnt[tid] = 0;
         __syncthreads();
-        const long long tile = S.tile;
-        // the unwrap state before the tile, from the pre-pass
-        if (tid < 8 && tile < p.n_tiles)
-            reinterpret_cast<long long *>(&S.E)[tid] = __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[tile]) + tid);
         if (tile >= p.n_tiles) {
             if (STAGED) {
-                flush_pending<BATCH>(S, p, seq);
+                flush_pending<MODE, BATCH>(S, p, seq);
                 if (tid == 0 && S.status) atomicOr(&p.ctl->status, S.status);
             }
+            // this CTA's counters (packets of each class are counted by the
+            // unwrap pre-pass)
+            if (tid < C_NUM && tid != C_PIXELS && tid != C_TDCS && tid != C_CORRUPT && S.acc[tid])
+                atomicAdd(&p.ctl->counters[tid], S.acc[tid]);
             break;
         }
         // the tile: in a batch, the tile queue names the run (each run is a
@@ -797,7 +818,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     }
                 }
                 if (dim) S.notpeak[q] = 1;
-                if (MODE == TPX_MODE_CC) S.parent[q] = ((ne > 2 ? REWALK : e1) << 16) | e0;
+                // with two partners the pointer takes the later-found one (the
+                // larger x when the two differ): pointers run along x first,
+                // which keeps the trees of a compact cloud shallow
+                if (MODE == TPX_MODE_CC)
+                    S.parent[q] = ne > 2 ? ((REWALK << 16) | e0) : ne == 2 ? ((e0 << 16) | e1) : ((NO_EXT << 16) | e0);
             }
         }
         __syncthreads();
@@ -887,6 +912,70 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 }
             }
             __syncthreads();
+            if (STAGED) {
+                // the CTA's staging slot: the previous tile's records go out first
+                flush_pending<MODE, BATCH>(S, p, seq);
+                __syncthreads();
+                // one thread per root walks its list: the cluster's earliest
+                // pixel in (time, position) order -- its canonical label -- and
+                // the exact integer moments (Sec. V.C); the record is staged in
+                // root order, the list head keeps (label, record index), and
+                // the label pixel is flagged (bit 1 of notpeak)
+                tpx_record *dst = p.stage + (long long)blockIdx.x * C;
+                for (int i = tid; i < ncl; i += NT) {
+                    if (!TPX_IN(i, C)) break;
+                    const uint32_t rt = rootpos[i];
+                    if (!TPX_IN(rt, C)) continue;
+                    const uint32_t head = S.u1.mhead[rt] & 0xFFFFu;
+                    uint64_t best = ~0ull;
+                    long long s_tot = 0, s_x = 0, s_y = 0, s_tt = 0;
+                    int n = 0, npk = 0;
+                    for (uint32_t m = head; m != EMPTY; m = mnext[m]) {
+                        if (!TPX_IN(m, C)) break;
+                        const uint64_t rm = S.buf[pad((int)m)];
+                        const long long tot = r_tot(rm);
+                        const int tf = r_tof(rm);
+                        best = min(best, ((uint64_t)tf << 16) | m);
+                        n += 1;
+                        npk += (S.notpeak[m] & 1) ? 0 : 1;
+                        s_tot += tot;
+                        s_x += tot * r_x(rm);
+                        s_y += tot * r_y(rm);
+                        s_tt += tot * (long long)tf;
+                    }
+                    const uint32_t lp = (uint32_t)(best & 0xFFFFu);
+                    const int tofb0 = (int)(best >> 16);
+                    const int seg = r_seg(S.buf[pad((int)rt)]);
+                    const long long tofc0 = (long long)tofb0 - kTofBias;
+                    const long long s_t = s_tt - (long long)tofb0 * s_tot;
+                    tpx_record o;
+                    o.label = p.idx_base + base + lp;
+                    o.shot = E.tdc.n + seg;
+                    o.t0 = S.tdc_t[seg] + tofc0;
+                    o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
+                    o.n = n; o.n_peaks = npk;
+                    com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
+                    dst[i] = o;
+                    S.u1.mhead[rt] = (lp << 16) | (uint32_t)i;
+                    if (TPX_IN(lp, C)) S.notpeak[lp] |= 2;
+                }
+                __syncthreads();
+                // the staged record of each cluster id in ascending label order
+                int c = 0;
+                for (int j = 0; j < kpd; ++j) {
+                    const int q = p0 + j;
+                    if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) ++c;
+                }
+                int excl = block_scan_int(S, c, &ncl);
+                uint16_t *perm = p.stage_perm + (long long)blockIdx.x * C;
+                for (int j = 0; j < kpd; ++j) {
+                    const int q = p0 + j;
+                    if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) {
+                        if (TPX_IN(excl, C)) perm[excl] = (uint16_t)(S.u1.mhead[S.u2.rootof[q]] & 0xFFFFu);
+                        ++excl;
+                    }
+                }
+            } else {
             // one thread per root walks its list for the cluster's earliest
             // pixel in (time, position) order -- its canonical label -- keeps
             // it in the upper half of the list head and flags it (bit 1 of
@@ -919,6 +1008,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     if (TPX_IN(excl, C)) rootpos[excl] = (uint16_t)q;
                     ++excl;
                 }
+            }
             }
         } else {
             // PAPER mode: one record per local maximum (list kept in parent[])
@@ -954,7 +1044,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // offset after an inline look-back
         auto record_target = [&](long long *lim) -> tpx_record * {
             if (STAGED) {
-                flush_pending<BATCH>(S, p, seq);
+                flush_pending<MODE, BATCH>(S, p, seq);
                 __syncthreads();   // the member lists / peak list are complete
                 *lim = C;
                 return p.stage + (long long)blockIdx.x * C;
@@ -992,10 +1082,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             c_pk = warp_sum(c_pk);
             if (lane == 0) atomicAdd(&S.cnt[C_PEAKS], c_pk);
             long long lim = 0;
-            tpx_record *dst = record_target(&lim);
-            // records: one thread per cluster walks its member list and forms
-            // the exact integer moments in registers (Sec. V.C)
-            for (int i = tid; i < ncl; i += NT) {
+            tpx_record *dst = STAGED ? nullptr : record_target(&lim);
+            // records (unstaged: after the inline look-back, in label order):
+            // one thread per cluster walks its member list and forms the
+            // exact integer moments in registers (Sec. V.C)
+            for (int i = tid; !STAGED && i < ncl; i += NT) {
                 if (i >= lim) break;
                 const int q = rootpos[i];
                 if (!TPX_IN(q, C) || !TPX_IN(S.u2.rootof[q], C)) continue;
@@ -1100,11 +1191,15 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             }
         }
         __syncthreads();
-        // (packets of each class are counted by the unwrap pre-pass)
-        if (tid < C_NUM && tid != C_PACKETS && tid != C_PIXELS && tid != C_TDCS && tid != C_CORRUPT && S.cnt[tid])
-            atomicAdd(&p.ctl->counters[tid], S.cnt[tid]);
+        if (tid < C_NUM) S.acc[tid] += tid == C_PACKETS ? (unsigned long long)cnt : S.cnt[tid];
+        // the next tile and its unwrap state
+        if (tid == 0) S.next_tile = (long long)claim;
+        __syncthreads();
+        if (tid < 8 && S.next_tile < p.n_tiles)
+            reinterpret_cast<long long *>(&S.E)[tid] =
+                __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[S.next_tile]) + tid);
         if (tid == 0) {
-            atomicAdd(&p.ctl->counters[C_PACKETS], (unsigned long long)cnt);
+            S.tile = S.next_tile;
             unsigned st = S.status;
             if (BATCH && (st & (ST_CAPACITY | ST_EXCEPTION))) {   // only this run is redone
                 p.bt.run_failed[run] = 1u;

@@ -144,8 +144,9 @@ __global__ void k_patch_keys(const uint64_t *pk, long long n, long long base, co
 // channel 0: ToT / 1023 rounded to bf16; channel 1: ToA relative to the
 // cluster's earliest pixel, in units of 32 ticks (50 ns), clamped to [-8, 8],
 // rounded to fp16 (exact: multiples of 1/32 below 8); empty cells 0
+template <typename OutT>
 __global__ void k_patch_fill(const uint64_t *pk, long long base, const tpx_record *cl, const long long *sel,
-                             const unsigned long long *key, long long ns, float *patch) {
+                             const unsigned long long *key, long long ns, OutT *patch) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ns * PC; c += (long long)gridDim.x * blockDim.x) {
         const long long s = c / PC;
         const int cell = (int)(c % PC);
@@ -161,8 +162,13 @@ __global__ void k_patch_fill(const uint64_t *pk, long long base, const tpx_recor
             tot = __bfloat162float(__float2bfloat16_rn((float)pix_tot(w) / 1023.f));
             rel = __half2float(__float2half_rn(fminf(8.f, fmaxf(-8.f, (float)d / 32.f))));
         }
-        patch[s * NIN + cell] = tot;
-        patch[s * NIN + PC + cell] = rel;
+        if (sizeof(OutT) == 4) {
+            patch[s * NIN + cell] = tot;
+            patch[s * NIN + PC + cell] = rel;
+        } else {   // exact in bf16 as well
+            reinterpret_cast<__nv_bfloat16 *>(patch)[s * NIN + cell] = __float2bfloat16_rn(tot);
+            reinterpret_cast<__nv_bfloat16 *>(patch)[s * NIN + PC + cell] = __float2bfloat16_rn(rel);
+        }
     }
 }
 
@@ -515,13 +521,25 @@ int pack_h(tpx_ctx *c, const float *P, void *packed) {
 
 }  // namespace tpxr
 
+// the minibatch loss and its output gradient, and one Adam step, for the
+// convolutional refiner (tpx_cnn.cu), which shares the loss and optimiser
+int tpxr_loss(cudaStream_t s, const float *out, const float *y, int n, float w_off, float *dout, float *loss) {
+    tpxr::k_loss<<<tpxr::grid_for(n), 256, 0, s>>>(out, y, n, w_off, dout, loss);
+    return tpxr::ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
+}
+int tpxr_adam(cudaStream_t s, float *p, const float *g, float *m, float *v, long long n, float lr, long long step) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    tpxr::k_adam<<<tpxr::grid_for(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, c1, c2, 1e-8f);
+    return tpxr::ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
+}
+
 using namespace tpxr;
 
-extern "C" {
-
-int tpx_refine_patches(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t base, const int64_t *d_labels,
-                       const tpx_record *d_clusters, int64_t n_clusters, int32_t min_pixels, float *d_patches,
-                       int64_t *d_sel, int32_t *d_centre, int64_t capacity, int64_t *d_n_patches) {
+template <typename OutT>
+static int refine_patches(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t base, const int64_t *d_labels,
+                          const tpx_record *d_clusters, int64_t n_clusters, int32_t min_pixels, OutT *d_patches,
+                          int64_t *d_sel, int32_t *d_centre, int64_t capacity, int64_t *d_n_patches) {
     if (!c || n < 0 || n_clusters < 0 || capacity < 0 || !d_n_patches || min_pixels < 0) return TPX_EINVAL;
     if ((n > 0 && (!d_packets || !d_labels)) || (n_clusters > 0 && !d_clusters)) return TPX_EINVAL;
     if (capacity > 0 && (!d_patches || !d_sel || !d_centre)) return TPX_EINVAL;
@@ -556,10 +574,26 @@ int tpx_refine_patches(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t
     if (ck(cudaMemsetAsync(key, 0, 8 * (size_t)ns * PC, s))) return TPX_ECUDA;
     k_patch_keys<<<grid_for(n), 256, 0, s>>>(d_packets, n, base, reinterpret_cast<const long long *>(d_labels), slot,
                                              d_centre, key);
-    k_patch_fill<<<grid_for(ns * PC), 256, 0, s>>>(d_packets, base, d_clusters, reinterpret_cast<const long long *>(d_sel),
-                                                   key, ns, d_patches);
+    k_patch_fill<OutT><<<grid_for(ns * PC), 256, 0, s>>>(d_packets, base, d_clusters,
+                                                         reinterpret_cast<const long long *>(d_sel), key, ns, d_patches);
     if (ck(cudaGetLastError())) return TPX_ECUDA;
     return np > capacity ? TPX_EOVERFLOW : TPX_OK;
+}
+
+extern "C" {
+
+int tpx_refine_patches(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t base, const int64_t *d_labels,
+                       const tpx_record *d_clusters, int64_t n_clusters, int32_t min_pixels, float *d_patches,
+                       int64_t *d_sel, int32_t *d_centre, int64_t capacity, int64_t *d_n_patches) {
+    return refine_patches<float>(c, d_packets, n, base, d_labels, d_clusters, n_clusters, min_pixels, d_patches, d_sel,
+                                 d_centre, capacity, d_n_patches);
+}
+
+int tpx_refine_patches_bf16(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t base, const int64_t *d_labels,
+                            const tpx_record *d_clusters, int64_t n_clusters, int32_t min_pixels, uint16_t *d_patches,
+                            int64_t *d_sel, int32_t *d_centre, int64_t capacity, int64_t *d_n_patches) {
+    return refine_patches<uint16_t>(c, d_packets, n, base, d_labels, d_clusters, n_clusters, min_pixels, d_patches,
+                                    d_sel, d_centre, capacity, d_n_patches);
 }
 
 int64_t tpx_refiner_params(int32_t hidden) { return hidden > 0 ? Layout(hidden).total : 0; }

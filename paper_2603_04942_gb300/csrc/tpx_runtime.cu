@@ -50,6 +50,7 @@ void free_scratch(tpx_ctx *c) {
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
     c->stage = nullptr;
+    c->stage_perm = nullptr;
     std::memset(&c->ts, 0, sizeof c->ts);
     c->max_tiles = 0;
 }
@@ -72,8 +73,8 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
         if (r > stage_records) stage_records = r;
     }
     c->stage_records = (int64_t)stage_records;
-    const size_t b_stage = al(sizeof(tpx_record) * stage_records);
-    const size_t total = b_flags + b_blk + 2 * b_agg + 2 * b_cnt + b_stage;
+    const size_t b_stage = al(sizeof(tpx_record) * stage_records), b_perm = al(sizeof(uint16_t) * stage_records);
+    const size_t total = b_flags + b_blk + 2 * b_agg + 2 * b_cnt + b_stage + b_perm;
     void *mem = nullptr;
     if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
     if (cudaMemset(mem, 0, total) != cudaSuccess) { cudaFree(mem); return TPX_ECUDA; }
@@ -84,7 +85,8 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
     c->ts.pre = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
     c->ts.cagg = reinterpret_cast<long long *>(p); p += b_cnt;
     c->ts.cpre = reinterpret_cast<long long *>(p); p += b_cnt;
-    c->stage = reinterpret_cast<tpx_record *>(p);
+    c->stage = reinterpret_cast<tpx_record *>(p); p += b_stage;
+    c->stage_perm = reinterpret_cast<uint16_t *>(p);
     c->scratch = mem;
     c->max_tiles = tiles;
     c->max_packets = tiles * T;
@@ -367,6 +369,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.E0 = E0;
     p.state_out = state_out;
     p.stage = c->stage;
+    p.stage_perm = c->stage_perm;
     p.hold = c->hold_next;
     c->hold_next = 0;
     int64_t grid = (int64_t)c->num_sms * tpxk::fused_ctas_per_sm(geo);   // persistent, all resident
@@ -565,6 +568,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     p.ts = B.ts;
     p.ctl = c->ctl;
     p.stage = c->stage;
+    p.stage_perm = c->stage_perm;
     p.bt = bt;
     if (ckr(tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s))) return TPX_ECUDA;
     // what a redo of failed runs needs

@@ -44,6 +44,7 @@ class Dataset:
     """Patches (device) and targets for the clusters whose truth is one or
     two particles inside the patch."""
     x: object              # torch float32 [n x 162] (device)
+    xb: object             # the same rows as bf16 bits (torch int16 [n x 162], device)
     y: object              # torch float32 [n x 5] (device): count, dx1, dy1, dx2, dy2
     count: np.ndarray      # [n] truth count (1 or 2)
     pos: np.ndarray        # [n x 4] truth positions (x1, y1, x2, y2), pixels
@@ -51,6 +52,7 @@ class Dataset:
     sep: np.ndarray        # [n] pair separation (0 for singles), pixels
     rows: np.ndarray       # [n] row in the patch arrays of the call
     patches: dict          # the tpx_refine_patches outputs (device)
+    patches16: dict        # the tpx_refine_patches_bf16 outputs (device)
     clusters: np.ndarray   # host copy of all records of the call
     clusters_dev: object   # the records on the device (uint8 tensor)
     n_selected: int        # clusters with more than MIN_PIXELS pixels
@@ -117,6 +119,7 @@ def make_dataset(ctx: Context, p, min_pixels: int = MIN_PIXELS, shuffle_seed: in
     ctx.tpx_sync()
     n_cl = int(out["n_clusters"].item())
     pt = ctx.tpx_refine_patches(d_pk, out["labels"], out["clusters"], n_cl, min_pixels)
+    pt16 = ctx.tpx_refine_patches_bf16(d_pk, out["labels"], out["clusters"], n_cl, min_pixels)
     torch.cuda.synchronize()
     n_sel = int(pt["n"].item())
     cl = np.frombuffer(out["clusters"][: n_cl * CLUSTER_DTYPE.itemsize].cpu().numpy().tobytes(), CLUSTER_DTYPE)
@@ -132,9 +135,10 @@ def make_dataset(ctx: Context, p, min_pixels: int = MIN_PIXELS, shuffle_seed: in
     y[:, 1:] = (pos[rows] - c2) * (np.repeat(count[rows], 4).reshape(-1, 4) >= np.array([1, 1, 2, 2]))
     d_rows = torch.from_numpy(rows).cuda()
     x = pt["patches"][:n_sel].index_select(0, d_rows).contiguous()
+    xb = pt16["patches"][:n_sel].index_select(0, d_rows).contiguous()
     c = cl[sel[rows]]
-    return Dataset(x=x, y=torch.from_numpy(y).cuda(), count=count[rows], pos=pos[rows],
-                   centroid=np.stack([c["x"], c["y"]], axis=1), sep=sep[rows], rows=rows, patches=pt,
+    return Dataset(x=x, xb=xb, y=torch.from_numpy(y).cuda(), count=count[rows], pos=pos[rows],
+                   centroid=np.stack([c["x"], c["y"]], axis=1), sep=sep[rows], rows=rows, patches=pt, patches16=pt16,
                    clusters=cl, clusters_dev=out["clusters"], n_selected=n_sel, sel=sel,
                    truth=dict(shot=truth["shot"] - p.shot_begin, cx=truth["cx"], cy=truth["cy"]))
 
@@ -215,6 +219,79 @@ class Refiner:
 
     def state(self) -> dict:
         return dict(hidden=self.h, params=self.params.cpu().numpy(), step=self.step)
+
+
+class CnnRefiner:
+    """The convolutional refiner (conv 2->16->16->32 channels of 3 x 3, fc
+    288->144->6; 49,750 parameters) and its Adam state, on the device;
+    trained in fp32, inferred on the tensor cores with bf16 operands."""
+
+    def __init__(self, ctx: Context, seed: int = 0):
+        import torch
+        self.ctx = ctx
+        self.n_params = Context.tpx_cnn_params()
+        rng = np.random.default_rng(seed)
+        p = np.zeros(self.n_params, np.float32)
+        o = 0
+        for fan_in, size, bias in ((2 * 9, 16 * 2 * 9, 16), (16 * 9, 16 * 16 * 9, 16), (16 * 9, 32 * 16 * 9, 32),
+                                   (288, 144 * 288, 144), (144, 6 * 144, 6)):
+            lim = math.sqrt(6.0 / fan_in)                        # He-uniform for ReLU layers
+            p[o: o + size] = rng.uniform(-lim, lim, size)
+            o += size + bias                                     # biases start at 0
+        assert o == self.n_params
+        self.params = torch.from_numpy(p).cuda()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.step = 0
+
+    def train(self, ds: Dataset, epochs: int = 1, batch: int = 4096, lr: float = 2e-3, offset_weight: float = 1.0,
+              seed: int = 0, lr_final: float | None = None) -> np.ndarray:
+        import torch
+        from . import lib
+        n = ds.x.shape[0]
+        nb = max(1, n // batch)
+        work = torch.empty(int(lib().tpx_cnn_work_floats(batch)), dtype=torch.float32, device=ds.x.device)
+        losses = torch.zeros(epochs * nb, dtype=torch.float32, device=ds.x.device)
+        rng = np.random.default_rng(seed)
+        total = epochs * nb
+        k = 0
+        for _ in range(epochs):
+            for b in rng.permutation(nb):
+                self.step += 1
+                rate = lr if lr_final is None else lr * (lr_final / lr) ** (k / max(1, total - 1))
+                r0 = int(b) * batch
+                self.ctx.tpx_cnn_train_step(self.params, self.m, self.v, self.grad, self.step, ds.x[r0: r0 + batch],
+                                            ds.y[r0: r0 + batch], rate, offset_weight, work, losses[k:], n=batch)
+                k += 1
+        torch.cuda.synchronize()
+        return losses.cpu().numpy()
+
+    def forward(self, x, n: int | None = None):
+        """The fp32 network (the training precision)."""
+        return self.ctx.tpx_cnn_forward(self.params, x, n)
+
+    def infer(self, xb, n: int | None = None, out=None):
+        """The network on the tensor cores; xb: bf16 patches."""
+        if getattr(self, "_packed_step", None) != self.step:
+            self.packed = self.ctx.tpx_cnn_pack(self.params, getattr(self, "packed", None))
+            self._packed_step = self.step
+        return self.ctx.tpx_cnn_infer(self.packed, xb, n, out=out)
+
+    def refine(self, patches16: dict, clusters_dev, n: int, threshold: float = 0.8):
+        """Refined hits (device [n x 5]) of the first n patches of a
+        tpx_refine_patches_bf16 call."""
+        out = self.infer(patches16["patches"], n)
+        return self.ctx.tpx_refine_decide(out, clusters_dev, patches16["sel"], patches16["centre"], n, threshold)
+
+    def refine_rows(self, ds: Dataset, threshold: float = 0.8, fp32: bool = False) -> np.ndarray:
+        import torch
+        rows = torch.from_numpy(ds.rows).cuda()
+        sel = ds.patches["sel"][: ds.n_selected].index_select(0, rows).contiguous()
+        centre = ds.patches["centre"][: ds.n_selected].index_select(0, rows).contiguous()
+        out = self.forward(ds.x) if fp32 else self.infer(ds.xb)
+        n = ds.x.shape[0]
+        return self.ctx.tpx_refine_decide(out, ds.clusters_dev, sel, centre, n, threshold)[:n].cpu().numpy()
 
 
 def evaluate(ds: Dataset, hits: np.ndarray) -> dict:
