@@ -85,8 +85,17 @@ typedef struct tpx_config {
                                    TPX_TILE_4096).  Not a paper parameter:
                                    results are identical, only speed and the
                                    range limit differ.                        */
-    int32_t reserved;           /* zero                                       */
+    int32_t flags;              /* TPX_FLAG_* bits, 0 by default              */
 } tpx_config;
+
+/* tpx_config.flags: TPX_FLAG_HOST_DIRECT -- tpx_process_host runs the fused
+   kernel on the caller's host buffers in place (no device staging, no
+   copies) when every one of them is pinned host memory mapped into the
+   device at the same address (cudaHostAlloc / cudaHostRegister on a unified
+   address space; checked with cudaPointerGetAttributes); the kernel then
+   reads the packets and writes labels, records and triggers over the host
+   link.  Otherwise the call stages through device memory as usual. */
+#define TPX_FLAG_HOST_DIRECT 4
 
 #define TPX_TILE_DEFAULT 0
 #define TPX_TILE_4096 1
@@ -184,9 +193,10 @@ int tpx_process(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_packets,
    be NULL.  *h_n_clusters and *h_n_trig receive the counts (the required
    ones when a buffer is short: TPX_EOVERFLOW).  Device staging is allocated
    on first use and kept by the context, grown for a larger call.  A call of
-   at least 2^24 packets on a context without a carried state (chain = 0, no
-   tpx_set_state) is pipelined: cut into up to 16 pieces at trigger packets,
-   chained through the unwrap state on the device, each piece's copy in
+   at least 2^24 packets on a context with chain = 0 is pipelined (from the
+   state of tpx_set_state, when one was set): cut into up to 16 pieces at
+   trigger packets, chained through the unwrap state on the device, each
+   piece's copy in
    overlapping the previous piece's kernel and its labels and records going
    out behind it (two more CUDA streams); a piece whose kernel meets anything
    it cannot hold -- a pixel after a cut that belongs in time to the shot

@@ -23,6 +23,7 @@ __all__ = ["Config", "Context", "CLUSTER_DTYPE", "TpxError", "lib", "load", "MOD
 MODE_CC = 0
 MODE_PAPER = 1
 TILE_DEFAULT, TILE_4096, TILE_2048 = 0, 1, 2
+FLAG_HOST_DIRECT = 4
 TICK_NS = 1.5625
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ECORRUPT, EAGAIN, ETIMEOUT, EDEVTIMEOUT, ECUDA, EUNSUPPORTED = \
@@ -54,7 +55,7 @@ class _CConfig(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("tof_max_ticks", ctypes.c_int64),
                 ("wrap_thr_pix_ticks", ctypes.c_int64), ("wrap_thr_tdc_ticks", ctypes.c_int64),
                 ("d_timewalk_lut", ctypes.c_void_p), ("strict", ctypes.c_int32), ("chain", ctypes.c_int32),
-                ("tile_geometry", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_geometry", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 STATE_FIELDS = ("pixels", "pix_last_raw", "pix_wraps", "triggers", "tdc_last_raw", "tdc_wraps")
@@ -112,6 +113,7 @@ class Config:
     strict: bool = False
     chain: bool = False                # each call continues where the previous one ended
     tile_geometry: int = 0             # TILE_DEFAULT, TILE_4096 or TILE_2048 (speed only)
+    host_direct: bool = False          # tpx_process_host on mapped pinned host buffers in place
 
 
 _lock = threading.Lock()
@@ -226,7 +228,8 @@ class Context:
             assert self._lut.dtype == torch.int16 and self._lut.numel() == 1024 and self._lut.is_cuda
         c = _CConfig(self.cfg.rx, self.cfg.ry, self.cfg.dt_ticks, self.cfg.mode, self.cfg.tof_max_ticks,
                      self.cfg.wrap_thr_pix_ticks, self.cfg.wrap_thr_tdc_ticks, _ptr(self._lut),
-                     int(self.cfg.strict), int(self.cfg.chain), int(self.cfg.tile_geometry), 0)
+                     int(self.cfg.strict), int(self.cfg.chain), int(self.cfg.tile_geometry),
+                     FLAG_HOST_DIRECT if self.cfg.host_direct else 0)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         rc = lib().tpx_create(ctypes.byref(h), ctypes.byref(c), int(max_packets), ctypes.c_void_p(self.stream.cuda_stream))

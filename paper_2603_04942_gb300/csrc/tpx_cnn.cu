@@ -271,8 +271,14 @@ struct TcLayer {
     static constexpr int K = CIN * KK * KK;   // real reduction length
     static constexpr int ROWS = HO * HO;      // output positions per patch
     static constexpr int TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));   // TMEM columns
+    // layers with several output positions per patch stage the inputs of the
+    // tile's patches in shared memory first (coalesced), then gather from there
+    static constexpr bool STAGE = HO > 1;
+    static constexpr int PIN = CIN * HIN * HIN;                      // input elements per patch
+    static constexpr int PPT = STAGE ? (127 + ROWS - 1) / ROWS + 1 : 0;   // patches a tile can span
     static constexpr size_t A_BYTES = (size_t)128 * KP * 2, B_BYTES = (size_t)N * KP * 2;
-    static constexpr size_t SMEM = A_BYTES + B_BYTES + 64 + 1024;   // + barrier, TMEM address, alignment
+    static constexpr size_t IN_BYTES = (((size_t)PPT * PIN * 2 + 15) / 16) * 16;
+    static constexpr size_t SMEM = A_BYTES + B_BYTES + IN_BYTES + 64 + 1024;   // + barrier, TMEM address, alignment
     static_assert(KP % 16 == 0 && KP >= K && N % 16 == 0 && N >= 16 && N <= 256 && COUT <= N, "tcgen05 shape");
 };
 
@@ -283,6 +289,18 @@ __device__ __forceinline__ uint32_t core_off(int r, int k, int kp) {
 
 constexpr long long kSpin = 1LL << 24;   // bounded mbarrier wait (then an error flag)
 
+// asynchronous global -> shared copies (16 or 4 bytes; 0 source bytes fill zeros)
+__device__ __forceinline__ void cp16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 template <int CIN, int HIN, int N, int HO, int KK, int KP, bool IN_CHW, bool OUT_F32, int COUT>
 __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16 *__restrict__ in, long long n_rows,
                                                  const __nv_bfloat16 *__restrict__ w, const float *__restrict__ bias,
@@ -292,7 +310,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16 *__restrict
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *As = base;
     unsigned char *Bs = base + G::A_BYTES;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + G::B_BYTES);
+    __nv_bfloat16 *Sin = reinterpret_cast<__nv_bfloat16 *>(Bs + G::B_BYTES);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + G::B_BYTES + G::IN_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -322,33 +341,58 @@ __global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16 *__restrict
         bool failed = false;
         // ---- the im2col tile: 128 output positions x KP reduction columns ----
         const long long r0 = tile * 128;
-        if (IN_CHW) {   // conv1: channel-major patch rows of 162, one value at a time
-            for (int i = tid; i < 128 * KP; i += 128) {
-                const int r = i / KP, k = i % KP;
-                const long long row = r0 + r;
-                float v = 0.f;
-                if (row < n_rows && k < G::K) {
-                    const long long p = row / G::ROWS;
-                    const int pos = (int)(row % G::ROWS), oy = pos / HO, ox = pos % HO;
-                    const int ci = k / (KK * KK), t = k % (KK * KK), ky = t / KK, kx = t % KK;
-                    v = __bfloat162float(in[p * (CIN * HIN * HIN) + ci * HIN * HIN + (oy + ky) * HIN + (ox + kx)]);
-                }
-                *reinterpret_cast<__nv_bfloat16 *>(As + core_off(r, k, KP)) = __float2bfloat16_rn(v);
+        const long long n_pat = (n_rows + G::ROWS - 1) / G::ROWS;
+        const long long pf = r0 / G::ROWS;   // the tile's first patch
+        if (G::STAGE) {   // the inputs of the tile's patches, coalesced, into shared memory
+            const long long pl = min(n_pat, (r0 + 127) / G::ROWS + 1);
+            const int elems = (int)((pl - pf) * G::PIN);
+            const __nv_bfloat16 *src = in + pf * G::PIN;
+            if (G::PIN % 8 == 0) {
+                for (int i = tid; i < elems / 8; i += 128) cp16(Sin + 8 * i, src + 8 * i, true);
+            } else {      // PIN is even: 4-byte words
+                for (int i = tid; i < elems / 2; i += 128) cp4(Sin + 2 * i, src + 2 * i);
             }
-        } else {        // channel-minor activations: 8 channels of one tap per 16-byte chunk
-            static_assert(IN_CHW || CIN % 8 == 0, "16-byte gathers");
+            cp_wait_all();
+            __syncthreads();
+        }
+        if (G::STAGE) {   // one thread per row: the taps' offsets are compile-time constants
+            const int r = tid;
+            const long long row = r0 + r;
+            const bool valid = row < n_rows;
+            const int p = valid ? (int)(row / G::ROWS - pf) : 0;
+            const int pos = valid ? (int)(row % G::ROWS) : 0, oy = pos / HO, ox = pos % HO;
+            unsigned char *arow = As + core_off(r, 0, KP);
+            if (IN_CHW) {   // conv1: channel-major patch rows of 162, two k at a time
+                const __nv_bfloat16 *src = Sin + p * G::PIN + oy * HIN + ox;
+#pragma unroll
+                for (int k = 0; k < KP; k += 2) {
+                    __nv_bfloat16 v[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int kk = k + u, ci = kk / (KK * KK), t = kk % (KK * KK);
+                        v[u] = (valid && kk < G::K) ? src[ci * HIN * HIN + (t / KK) * HIN + (t % KK)] : __float2bfloat16_rn(0.f);
+                    }
+                    *reinterpret_cast<__nv_bfloat162 *>(arow + (((k >> 3) << 7) + ((k & 7) << 1))) = __halves2bfloat162(v[0], v[1]);
+                }
+            } else {        // channel-minor activations: 8 channels of a tap per 16-byte chunk
+                static_assert(IN_CHW || CIN % 8 == 0, "16-byte gathers");
+                const __nv_bfloat16 *src = Sin + p * G::PIN + (oy * HIN + ox) * CIN;
+#pragma unroll
+                for (int c8 = 0; c8 < KP; c8 += 8) {
+                    const int t = c8 / CIN, ci = c8 % CIN;
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (valid && c8 < G::K) v = *reinterpret_cast<const uint4 *>(src + ((t / KK) * HIN + (t % KK)) * CIN + ci);
+                    *reinterpret_cast<uint4 *>(arow + ((c8 >> 3) << 7)) = v;
+                }
+            }
+        } else {        // one output position per patch: the row is the patch's activations, copied
             for (int i = tid; i < 128 * (KP / 8); i += 128) {
                 const int r = i / (KP / 8), c8 = (i % (KP / 8)) * 8;
                 const long long row = r0 + r;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (row < n_rows && c8 < G::K) {
-                    const long long p = row / G::ROWS;
-                    const int pos = (int)(row % G::ROWS), oy = pos / HO, ox = pos % HO;
-                    const int t = c8 / CIN, ci = c8 % CIN, ky = t / KK, kx = t % KK;
-                    v = *reinterpret_cast<const uint4 *>(in + (p * HIN * HIN + (oy + ky) * HIN + (ox + kx)) * CIN + ci);
-                }
-                *reinterpret_cast<uint4 *>(As + core_off(r, c8, KP)) = v;
+                const bool ok = row < n_rows && c8 < G::K;
+                cp16(As + core_off(r, c8, KP), ok ? in + row * G::K + c8 : in, ok);
             }
+            cp_wait_all();
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -476,9 +520,10 @@ int launch_tc(tpx_ctx *c, const __nv_bfloat16 *in, long long n_rows, const __nv_
     using G = TcLayer<CIN, HIN, N, HO, KK, KP, IN_CHW, OUT_F32, COUT>;
     auto kern = k_conv_tc<CIN, HIN, N, HO, KK, KP, IN_CHW, OUT_F32, COUT>;
     if (ck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM))) return TPX_ECUDA;
-    int per_sm = 0;
-    if (ck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, G::SMEM))) return TPX_ECUDA;
-    // every resident CTA holds TCOLS of the SM's 512 tensor-memory columns
+    // CTAs per SM: by shared memory (227 KB, 1 KB reserved per CTA), by
+    // threads (16 of 128), and by tensor memory (each holds TCOLS of 512 columns)
+    int per_sm = (int)((227 * 1024) / (G::SMEM + 1024));
+    if (per_sm > 16) per_sm = 16;
     if (per_sm > 512 / G::TCOLS) per_sm = 512 / G::TCOLS;
     if (per_sm < 1) per_sm = 1;
     const long long tiles = (n_rows + 127) / 128;

@@ -43,6 +43,7 @@ int check_cfg(const tpx_config *c) {
     if (c->wrap_thr_pix_ticks <= 0 || c->wrap_thr_tdc_ticks <= 0) return TPX_EINVAL;
     if (c->tile_geometry != TPX_TILE_DEFAULT && c->tile_geometry != TPX_TILE_4096 && c->tile_geometry != TPX_TILE_2048)
         return TPX_EINVAL;
+    if (c->flags & ~TPX_FLAG_HOST_DIRECT) return TPX_EINVAL;
     return TPX_OK;
 }
 
@@ -701,12 +702,15 @@ int pipe_cuts(const uint64_t *h, int64_t n, int64_t *cut) {
 // chained through the unwrap state exactly as consecutive calls; a cut is
 // exact when no pixel after it belongs to the shot before it in time, and a
 // piece whose fused kernel reports anything it cannot hold (such a pixel is
-// one) sends the whole call back to the one-piece path. Returns 1 when it
-// declined (the caller then runs the plain path), else a status.
+// one) sends the whole call back to the one-piece path. A state set by
+// tpx_set_state starts the first piece (and is put back for the one-piece
+// path). Returns 1 when it declined (the caller then runs the plain path),
+// else a status.
 static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base,
                                   int64_t *h_labels, uint8_t *h_is_peak, tpx_record *h_clusters, int64_t cl_cap,
                                   int64_t *h_n_clusters, int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
-    if (n < kPipeMinPackets || c->cfg.chain || c->state_once) return 1;
+    if (n < kPipeMinPackets || c->cfg.chain) return 1;
+    const bool user_state = c->state_once;   // tpx_set_state before the call: the first piece starts there
     int64_t cut[tpx_ctx::Pipe::kMax + 1];
     const int K = pipe_cuts(h_packets, n, cut);
     if (K < 2) return 1;
@@ -772,7 +776,7 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
         const int64_t m = cut[k + 1] - cut[k];
         if (ckr(cudaStreamWaitEvent(sc, P.ev_in[k], 0))) return TPX_ECUDA;
         if (k >= 2 && ckr(cudaStreamWaitEvent(sc, P.ev_out[k - 2], 0))) return TPX_ECUDA;
-        c->state_once = k > 0;   // continue from the previous piece's state
+        c->state_once = k > 0 || user_state;   // continue from the previous piece's state
         rc = tpx_process(c, P.pk[k & 1], m, idx_base + cut[k], h_labels ? c->st_labels + cut[k] : nullptr,
                          h_is_peak ? c->st_peak + cut[k] : nullptr, P.cl[k & 1], cl_cap, P.d_counts + 2 * k,
                          P.trig[k & 1], trig_cap, P.d_counts + 2 * k + 1);
@@ -803,6 +807,12 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
         c->synced = true;
         c->last.valid = false;
         c->state_once = false;
+        if (user_state) {   // the one-piece path starts from the same state
+            if (ckr(cudaMemcpyAsync(&c->d_state[c->cur], &c->h_state, sizeof c->h_state, cudaMemcpyHostToDevice, sc)) ||
+                ckr(cudaStreamSynchronize(sc)))
+                return TPX_ECUDA;
+            c->state_once = true;
+        }
         return 1;
     }
     // the call's counters and status, as one call would leave them
@@ -817,6 +827,39 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
     return rc;
 }
 
+// a host buffer the device reaches at the same address (pinned and mapped)
+static bool host_mapped(const void *p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
+// TPX_FLAG_HOST_DIRECT: the fused kernel on the mapped host buffers in place
+// (counts in device memory); returns 1 when it declined
+static int process_host_direct(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base, int64_t *h_labels,
+                               uint8_t *h_is_peak, tpx_record *h_clusters, int64_t cl_cap, int64_t *h_n_clusters,
+                               int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
+    if (!(c->cfg.flags & TPX_FLAG_HOST_DIRECT) || n == 0) return 1;
+    if (!host_mapped(h_packets) || !host_mapped(h_labels) || !host_mapped(h_is_peak) || !host_mapped(h_clusters) ||
+        !host_mapped(h_trig) || (reinterpret_cast<uintptr_t>(h_packets) & 15))
+        return 1;
+    int rc = grow(&c->st_counts, &c->st_counts_cap, 2);
+    if (rc) return rc;
+    rc = tpx_process(c, h_packets, n, idx_base, h_labels, h_is_peak, h_clusters, cl_cap, c->st_counts, h_trig, trig_cap,
+                     c->st_counts + 1);
+    if (rc) return rc;
+    rc = tpx_sync(c, nullptr);
+    int64_t cnt[2] = {0, 0};
+    if (ckr(cudaMemcpy(cnt, c->st_counts, sizeof cnt, cudaMemcpyDeviceToHost))) return TPX_ECUDA;
+    *h_n_clusters = cnt[0];
+    *h_n_trig = cnt[1];
+    return rc;
+}
+
 int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t idx_base, int64_t *h_labels,
                      uint8_t *h_is_peak, tpx_record *h_clusters, int64_t cl_cap, int64_t *h_n_clusters,
                      int64_t *h_trig, int64_t trig_cap, int64_t *h_n_trig) {
@@ -825,7 +868,10 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     if (n > c->max_packets) return TPX_EINVAL;
     if (cl_cap > 0 && !h_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !h_trig) return TPX_EINVAL;
-    int rc = process_host_pipelined(c, h_packets, n, idx_base, h_labels, h_is_peak, h_clusters, cl_cap, h_n_clusters,
+    int rc = process_host_direct(c, h_packets, n, idx_base, h_labels, h_is_peak, h_clusters, cl_cap, h_n_clusters,
+                                 h_trig, trig_cap, h_n_trig);
+    if (rc != 1) return rc;
+    rc = process_host_pipelined(c, h_packets, n, idx_base, h_labels, h_is_peak, h_clusters, cl_cap, h_n_clusters,
                                     h_trig, trig_cap, h_n_trig);
     if (rc != 1) return rc;
     if ((rc = grow(&c->st_pk, &c->st_n, n))) return rc;

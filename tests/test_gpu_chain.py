@@ -128,3 +128,43 @@ def test_shards_on_one_gpu_equal_one_call():
         clusters.append(r["clusters"])
     assert np.array_equal(np.concatenate(labels), whole["labels"])
     assert_clusters_equal(np.concatenate(clusters), whole["clusters"])
+
+
+def test_shards_generated_apart_equal_one_call():
+    """As the benchmark's ranks run: each shot range of one acquisition
+    generated on its own (shots [r S, (r + 1) S)), its unwrap summary formed
+    on the device, the summaries combined in rank order, each range processed
+    from its starting state with its stream index base. Together they equal
+    one oracle run over the whole acquisition (the pixel wrap at shot 500
+    falls in the second range)."""
+    from paper_2603_04942_gb300 import shard
+    S, R = 400, 3
+    whole = synth.generate(synth.large(n_shots=S * R))[0]
+    parts = [synth.generate(synth.large(n_shots=S, shot_begin=r * S))[0] for r in range(R)]
+    assert np.array_equal(np.concatenate(parts), whole)
+    o = oracle_run(whole)
+    summaries = []
+    for pk in parts:
+        ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+        summaries.append(ctx.tpx_summarize(to_device(pk)))
+        ctx.close()
+    states = shard.states_from_summaries(summaries)
+    labels, clusters, trig = [], [], []
+    base = 0
+    for r, (pk, st) in enumerate(zip(parts, states)):
+        ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+        if r > 0:
+            ctx.tpx_set_state(st)
+        out = ctx.alloc_outputs(pk.size, True, False, pk.size, pk.size)
+        ctx.tpx_process(to_device(pk), out, index_base=base)
+        rc, cnt = ctx.tpx_sync(check=False)
+        assert rc == 0
+        g = ctx.collect(out, rc, cnt)
+        ctx.close()
+        labels.append(g["labels"])
+        clusters.append(g["clusters"])
+        trig.append(g["triggers"])
+        base += pk.size
+    assert np.array_equal(np.concatenate(labels), o["labels"])
+    assert np.array_equal(np.concatenate(trig), o["triggers"])
+    assert_clusters_equal(np.concatenate(clusters), o["clusters"])

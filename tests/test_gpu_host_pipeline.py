@@ -8,7 +8,7 @@ import pytest
 
 import paper_2603_04942_gb300 as tpx
 import synth
-from gpu_common import COUNTERS, assert_clusters_equal, to_device
+from gpu_common import COUNTERS, assert_clusters_equal, oracle_run, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -84,3 +84,31 @@ def test_pipelined_host_call_with_a_short_record_buffer(large_stream):
     assert rc == tpx.EOVERFLOW and ncl == g["n_clusters"]
     assert_clusters_equal(cl[:cap], g["clusters"][:cap])
     assert np.array_equal(lab, g["labels"])
+
+
+def test_host_direct_mode_equals_the_device_call():
+    """TPX_FLAG_HOST_DIRECT: with every host buffer pinned (mapped into the
+    device), the fused kernel works on them in place; the result equals the
+    oracle's. A pageable buffer makes the call stage through the device as
+    usual, with the same result."""
+    import torch
+    pk = synth.generate(synth.large(n_shots=600))[0]
+    o = oracle_run(pk)
+    n = pk.size
+    h_pk = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    h_pk.numpy()[:] = pk.view(np.int64)
+    lab = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    cl = torch.empty(n // 8 * tpx.CLUSTER_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+    tr = torch.empty(1000, dtype=torch.int64, pin_memory=True)
+    ctx = tpx.Context(tpx.Config(host_direct=True), max_packets=n)
+    try:
+        for labels in (lab.numpy(), np.empty(n, np.int64)):       # pinned, then pageable labels
+            a_cl = cl.numpy().view(tpx.CLUSTER_DTYPE)
+            rc, ncl, ntr = ctx.tpx_process_host(h_pk.numpy().view(np.uint64), labels, None, a_cl, tr.numpy())
+            assert rc == 0
+            assert np.array_equal(labels, o["labels"])
+            assert np.array_equal(tr.numpy()[:ntr], o["triggers"])
+            assert ncl == o["clusters"].size
+            assert_clusters_equal(a_cl[:ncl].copy(), o["clusters"])
+    finally:
+        ctx.close()
