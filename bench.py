@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pixel hits/s clustered+centroided"
 UNIT = "hits/s"
-CLUSTER_BYTES = 88
+CLUSTER_BYTES = 88        # tpx_record as written
+ALG_CLUSTER_BYTES = 56    # the per-cluster sums the method must write: label, t0, shot, n, 4 sums, n_peaks
 KERNEL_SRC = [os.path.join(ROOT, "paper_2603_04942_gb300", "csrc", f) for f in ("tpx_fused.cu", "tpx_fused_body.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_kernel_large_batch.md")
 
@@ -60,6 +61,8 @@ def parse():
     ap.add_argument("--refiner-only", action="store_true")
     ap.add_argument("--refiner-shots", type=int, default=500_000, help="training shots (about 20 clusters each)")
     ap.add_argument("--refiner-epochs", type=int, default=1)
+    ap.add_argument("--cnn-infer-only", type=int, default=0, metavar="N",
+                    help="time only the CNN refiner's tcgen05 inference on N random bf16 patches (random weights)")
     ap.add_argument("--batch-runs", type=int, default=4096)
     ap.add_argument("--batch-only", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed whole calls of the batch (each ~5 s)")
@@ -153,14 +156,15 @@ def peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def traffic_per_packet():
-    """DRAM bytes per packet of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def profile_per_packet(key: str = "dram_bytes_per_packet"):
+    """A per-packet figure of the fused kernel (DRAM bytes, warp
+    instructions) from the committed ncu summary, if it was taken on the
+    current kernel source."""
     try:
         txt = open(TRAFFIC_FILE).read()
         sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRC)).hexdigest()[:16]
         m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-        m_b = re.search(r"dram_bytes_per_packet:\s*([0-9.]+)", txt)
+        m_b = re.search(key + r":\s*([0-9.]+)", txt)
         if m_sha and m_b and m_sha.group(1) == sha:
             return float(m_b.group(1))
     except Exception:
@@ -538,6 +542,40 @@ def timewalk_bench(args) -> dict:
                             "c": synth.CALIBRATION_TOF_TICKS + p.timewalk_c / 1.5625, "d": 1.0}}
 
 
+CNN_FLOPS_PER_PATCH = 2 * (49 * 18 * 16 + 25 * 144 * 16 + 9 * 144 * 32 + 288 * 144 + 144 * 6)
+
+
+def cnn_infer_bench(n: int, steps: int, warmup: int) -> dict:
+    """The CNN refiner's inference alone: n patches of bf16 values in [0, 2),
+    weights N(0, 0.1), both seeded; `steps` timed calls after `warmup`."""
+    import numpy as np
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    ctx = tpx.Context(tpx.Config(), max_packets=16)
+    w = np.random.default_rng(0).normal(scale=0.1, size=tpx.Context.tpx_cnn_params()).astype(np.float32)
+    x32 = np.random.default_rng(1).random((n, 162), np.float32) * 2
+    x16 = (x32.view(np.uint32) >> np.uint32(16)).astype(np.uint16).view(np.int16)
+    packed = ctx.tpx_cnn_pack(torch.from_numpy(w).cuda())
+    x = torch.from_numpy(x16).cuda()
+    out = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    work = torch.empty(int(tpx.lib().tpx_cnn_infer_work_bytes(n)), dtype=torch.uint8, device="cuda")
+    for _ in range(max(1, warmup)):
+        ctx.tpx_cnn_infer(packed, x, n, work=work, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(steps):
+        ctx.tpx_cnn_infer(packed, x, n, work=work, out=out)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rc, _ = ctx.tpx_sync(check=False)
+    ctx.close()
+    return {"metric": "CNN refiner inference", "patches": n, "ms_per_call": ms, "patches_per_s": n / (ms / 1e3),
+            "tflops": CNN_FLOPS_PER_PATCH * n / (ms / 1e3) / 1e12, "status": rc, "steps": steps, "warmup": warmup}
+
+
 def refiner_bench(args) -> dict:
     """The learned overlap refiner: a training set of generator clusters
     with planted pairs (seed 6), one pass of minibatch Adam, then the errors
@@ -649,7 +687,7 @@ def refiner_bench(args) -> dict:
         del p16
     rc_c, _ = ctx.tpx_sync(check=False)
     ctx.close()
-    cflops = 2 * ns * (49 * 18 * 16 + 25 * 144 * 16 + 9 * 144 * 32 + 288 * 144 + 144 * 6)
+    cflops = CNN_FLOPS_PER_PATCH * ns
     cms = sum(ctot)
     cnn_res = {"network": f"CNN: conv 3x3 2->16->16->32 channels (9x9 -> 3x3), fc 288->144->6, {cnn.n_params:,} "
                           "parameters; trained in fp32, inferred with tcgen05 (bf16 operands, fp32 accumulators in "
@@ -723,6 +761,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cnn_infer_only:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2603_04942_gb300 import build as tbuild
+        tbuild.build()
+        print(json.dumps(cnn_infer_bench(args.cnn_infer_only, args.steps, args.warmup)), flush=True)
+        return 0
     if args.stream_only or args.batch_only or args.refiner_only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -785,11 +830,14 @@ def main():
     torch.cuda.synchronize()
     clocks = Clocks(local)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ctx.tpx_kernel_timing(True)   # events on the launching stream around the pre-pass and the fused kernel
     ev[0].record(s)
     for k in range(args.steps):
         step()
         ev[k + 1].record(s)
     torch.cuda.synchronize()
+    ktimes = ctx.tpx_kernel_times()
+    ctx.tpx_kernel_timing(False)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -809,18 +857,29 @@ def main():
     if not args.no_parity and rank == 0:
         parity = _section(parity_sampled, p, h_pk, d_pk, out, n_cl, n_tr, args.parity_shots)
 
-    # roofline of the fused kernel (the only kernel of a step)
+    # roofline of the fused kernel (95% of a step's kernel time; the unwrap pre-pass is the rest)
     pk_info, peak_kind = peaks()
-    alg_bytes = 8 * n + 8 * n + CLUSTER_BYTES * n_cl + 8 * n_tr
-    avg_ms = statistics.mean(step_ms)
+    alg_bytes = 8 * n + 8 * n + ALG_CLUSTER_BYTES * n_cl + 8 * n_tr
+    avg_ms = ktimes["fused_ms"] / max(1, ktimes["launches"])
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     peak = float(pk_info.get("hbm_gbs", 6800.0))
-    tpp = traffic_per_packet()
+    tpp = profile_per_packet("dram_bytes_per_packet")
+    wpp = profile_per_packet("warp_instructions_per_packet")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None if tpp is None else tpp * n,
             "algorithmic_bytes": alg_bytes, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
             "kernel": {1: "geo_t4096::fused_kernel<CC, staged>", 2: "geo_t2048::fused_kernel<CC, staged>"}.get(
-                tuning["tile_geometry"], "fused_kernel"), "avg_launch_ms": avg_ms}
+                tuning["tile_geometry"], "fused_kernel"), "avg_launch_ms": avg_ms,
+            "prepass_avg_ms": ktimes["prepass_ms"] / max(1, ktimes["launches"]),
+            "launches_timed": ktimes["launches"],
+            "bytes_per_unit": {"packet": 16, "cluster": ALG_CLUSTER_BYTES, "trigger": 8}}
+    if wpp is not None:
+        # the bound that holds: warp-instruction issue, 4 schedulers per SM at the sampled clock
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        ipk = wpp * n / (avg_ms / 1e3)
+        ipeak = 4.0 * torch.cuda.get_device_properties(local).multi_processor_count * mhz * 1e6
+        roof["issue"] = {"warp_instructions_per_packet": wpp, "achieved_per_s": ipk, "peak_per_s": ipeak,
+                         "frac": ipk / ipeak, "clock_mhz": mhz}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -939,7 +998,7 @@ def main():
                 "parity": parity,
                 "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_par, "e2e": e2e, "stream": stream, "batch": batch, "timewalk": timewalk,
                 "refiner": refiner, "clocks": clk,
-                "gpu_launches": 2 * args.steps - 1,   # fused kernels + status carries between unsynchronised calls
+                "gpu_launches": 6 * args.steps - 1,   # 4 pre-pass kernels + the fused kernel per call, and the status carries between unsynchronised calls
                 "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
                 "counters": counters}
         print(json.dumps(line), flush=True)

@@ -267,6 +267,19 @@ int tpx_centroid(tpx_ctx *ctx, const tpx_hits *hits, const int64_t *d_labels, co
    (call tpx_sync after each call whose input may be unusual). */
 int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
 
+/* Kernel timing (the measurement of the fused path, Sec. V).
+   tpx_kernel_timing(ctx, 1) turns it on and resets the sums: every later
+   fused launch of tpx_process / tpx_process_batch on the context records CUDA
+   events on its stream before the unwrap pre-pass, between the pre-pass and
+   the fused kernel, and after the fused kernel (not while the stream is being
+   captured into a graph).  0 turns it off.  The events are created on the
+   first enable; TPX_ECUDA if that fails.
+   tpx_kernel_times waits for the recorded launches and writes the summed
+   pre-pass and fused-kernel milliseconds and the number of launches timed
+   (any pointer may be NULL).  TPX_EINVAL for a NULL context. */
+int tpx_kernel_timing(tpx_ctx *ctx, int enable);
+int tpx_kernel_times(tpx_ctx *ctx, double *prepass_ms, double *fused_ms, int64_t *launches);
+
 /* Upper bound on n_packets for tpx_process_noalloc (2^26 packets, 512 MB of
    input): the size of its fixed scratch array. */
 #define TPX_NOALLOC_MAX_PACKETS (1LL << 26)

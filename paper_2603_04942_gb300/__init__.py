@@ -39,7 +39,7 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
                   "kept", "clusters", "peaks", "status_bits", "redone")
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
-                    "tpx_process_host", "tpx_sync", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
+                    "tpx_process_host", "tpx_sync", "tpx_kernel_timing", "tpx_kernel_times", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
                     "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_refine_patches", "tpx_refiner_params",
                     "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
                     "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_debug_noalloc_seq", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
@@ -139,6 +139,9 @@ def load(path: str | None = None):
         L.tpx_process.argtypes = [vp, vp, i64, i64, vp, vp, vp, i64, vp, vp, i64, vp]
         L.tpx_process_host.argtypes = [vp, vp, i64, i64, vp, vp, vp, i64, vp, vp, i64, vp]
         L.tpx_sync.argtypes = [vp, ctypes.POINTER(_CCounters)]
+        L.tpx_kernel_timing.argtypes = [vp, i32]
+        L.tpx_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]
         L.tpx_strerror.argtypes = [i32]
         L.tpx_strerror.restype = ctypes.c_char_p
         L.tpx_version.restype = ctypes.c_char_p
@@ -199,7 +202,7 @@ def load(path: str | None = None):
         L.tpx_cluster.argtypes = [vp, ctypes.POINTER(_CHits), i64, vp, vp]
         L.tpx_centroid.argtypes = [vp, ctypes.POINTER(_CHits), vp, vp, i64, vp, i64, vp]
         for f in ("tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process", "tpx_process_host", "tpx_sync",
-                  "tpx_decode", "tpx_cluster", "tpx_centroid"):
+                  "tpx_kernel_timing", "tpx_kernel_times", "tpx_decode", "tpx_cluster", "tpx_centroid"):
             getattr(L, f).restype = i32
         _lib = L
         return L
@@ -346,6 +349,20 @@ class Context:
         if check and rc:
             raise TpxError(rc, "tpx_sync")
         return rc, counters
+
+    def tpx_kernel_timing(self, enable: bool = True) -> None:
+        rc = lib().tpx_kernel_timing(self._h, 1 if enable else 0)
+        if rc:
+            raise TpxError(rc, "tpx_kernel_timing")
+
+    def tpx_kernel_times(self) -> dict:
+        """Summed CUDA-event times of the fused launches since timing was
+        enabled: {"prepass_ms", "fused_ms", "launches"}."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        rc = lib().tpx_kernel_times(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n))
+        if rc:
+            raise TpxError(rc, "tpx_kernel_times")
+        return {"prepass_ms": a.value, "fused_ms": b.value, "launches": n.value}
 
     def process(self, packets, labels=True, is_peak=False, cluster_capacity=None, trig_capacity=None,
                 index_base: int = 0, check: bool = True) -> dict:

@@ -24,6 +24,16 @@ struct tpx_ctx {
         int head, tail;       // ring of launched, not yet timed samples
         struct Sample { cudaEvent_t a, b; int geo; int64_t n; bool failed; } ring[8];
     } tune;
+    // kernel timing (tpx_kernel_timing): events before the pre-pass, between
+    // it and the fused kernel, and after, for each fused launch
+    struct KTime {
+        static constexpr int kRing = 32;
+        bool on;
+        int head, tail;           // recorded, not yet collected
+        cudaEvent_t ev[kRing][3];
+        double pre_ms, fused_ms;
+        int64_t launches;
+    } kt;
     int64_t max_packets;
     int64_t max_tiles;
     unsigned seq;

@@ -32,8 +32,9 @@ int fused_range_capacity(int geo) { return geo == GEO_T2048 ? geo_t2048::C : geo
 int fused_ctas_per_sm(int geo) { return geo == GEO_T2048 ? geo_t2048::MINB : geo_t4096::MINB; }
 int fused_smem_bytes(int geo) { return geo == GEO_T2048 ? geo_t2048::smem_bytes() : geo_t4096::smem_bytes(); }
 
-cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s) {
-    const cudaError_t e = launch_unwrap_prepass(p, fused_tile_packets(geo), grid, s);
+cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s, cudaEvent_t mid) {
+    cudaError_t e = launch_unwrap_prepass(p, fused_tile_packets(geo), grid, s);
+    if (e == cudaSuccess && mid) e = cudaEventRecord(mid, s);
     if (e != cudaSuccess) return e;
     return geo == GEO_T2048 ? geo_t2048::launch(p, mode, grid, s) : geo_t4096::launch(p, mode, grid, s);
 }

@@ -136,5 +136,6 @@ int fused_ctas_per_sm(int geo);
 // corrupt-packet counters. launch_fused runs it before the fused kernel.
 size_t unwrap_prepass_scratch_bytes(long long n_tiles);
 cudaError_t launch_unwrap_prepass(const Params &p, int T, int grid, cudaStream_t s);
-cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s);
+// `mid`, if given, is recorded on `s` between the pre-pass and the fused kernel
+cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s, cudaEvent_t mid = nullptr);
 }  // namespace tpxk

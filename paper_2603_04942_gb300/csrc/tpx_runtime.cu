@@ -145,6 +145,43 @@ int tune_pick(const tpx_ctx *c, int64_t n) {
     return c->tune.issued[tpxk::GEO_T2048 - 1] <= c->tune.issued[tpxk::GEO_T4096 - 1] ? tpxk::GEO_T2048 : tpxk::GEO_T4096;
 }
 
+// kernel timing: add the oldest recorded launch's pre-pass and fused-kernel
+// times to the sums (waits for it)
+int ktime_collect_one(tpx_ctx *c) {
+    auto &k = c->kt;
+    cudaEvent_t *e = k.ev[k.head];
+    if (ckr(cudaEventSynchronize(e[2]))) return TPX_ECUDA;
+    float a = 0.f, b = 0.f;
+    if (ckr(cudaEventElapsedTime(&a, e[0], e[1])) || ckr(cudaEventElapsedTime(&b, e[1], e[2]))) return TPX_ECUDA;
+    k.pre_ms += a;
+    k.fused_ms += b;
+    k.launches += 1;
+    k.head = (k.head + 1) % tpx_ctx::KTime::kRing;
+    return TPX_OK;
+}
+
+// the events of the next fused launch on `s`, or null when timing is off or
+// the stream is being captured; the first one is recorded here
+cudaEvent_t *ktime_begin(tpx_ctx *c, cudaStream_t s) {
+    auto &k = c->kt;
+    if (!k.on) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if ((k.tail + 1) % tpx_ctx::KTime::kRing == k.head && ktime_collect_one(c)) return nullptr;
+    cudaEvent_t *e = k.ev[k.tail];
+    if (cudaEventRecord(e[0], s) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+void ktime_end(tpx_ctx *c, cudaEvent_t *e, cudaStream_t s) {
+    if (!e) return;
+    if (cudaEventRecord(e[2], s) != cudaSuccess) { cudaGetLastError(); return; }
+    c->kt.tail = (c->kt.tail + 1) % tpx_ctx::KTime::kRing;
+}
+
 // time the samples whose calls have completed (all of them after a sync);
 // `redone_last` marks the newest one as redone by the general path
 void tune_collect(tpx_ctx *c, bool redone_last) {
@@ -267,6 +304,9 @@ int tpx_destroy(tpx_ctx *c) {
         if (smp.a) cudaEventDestroy(smp.a);
         if (smp.b) cudaEventDestroy(smp.b);
     }
+    for (auto &tri : c->kt.ev)
+        for (cudaEvent_t ev : tri)
+            if (ev) cudaEventDestroy(ev);
     if (c->pipe.ready) {
         cudaStreamSynchronize(c->pipe.s_in);
         cudaStreamSynchronize(c->pipe.s_out);
@@ -379,8 +419,10 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     const bool timed = c->cfg.tile_geometry == TPX_TILE_DEFAULT && !t.fixed && n >= kTuneMinPackets &&
                        (t.tail + 1) % 8 != t.head;
     if (timed && cudaEventRecord(t.ring[t.tail].a, c->stream) != cudaSuccess) return TPX_ECUDA;
-    cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, c->stream);
+    cudaEvent_t *kte = ktime_begin(c, c->stream);
+    cudaError_t e = tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, c->stream, kte ? kte[1] : nullptr);
     if (e != cudaSuccess) return TPX_ECUDA;
+    ktime_end(c, kte, c->stream);
     if (timed) {
         // a sample runs synchronously: a geometry whose ranges could not hold
         // the input loses, and that call is redone at once, so that a later
@@ -571,7 +613,9 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     p.stage = c->stage;
     p.stage_perm = c->stage_perm;
     p.bt = bt;
-    if (ckr(tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s))) return TPX_ECUDA;
+    cudaEvent_t *kte = ktime_begin(c, s);
+    if (ckr(tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s, kte ? kte[1] : nullptr))) return TPX_ECUDA;
+    ktime_end(c, kte, s);
     // what a redo of failed runs needs
     c->last.valid = false;
     B.last = true;
@@ -586,6 +630,31 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     B.trig_cap = trig_cap;
     B.n_trig = d_n_trig;
     B.h_off = h_off;
+    return TPX_OK;
+}
+
+int tpx_kernel_timing(tpx_ctx *c, int enable) {
+    if (!c) return TPX_EINVAL;
+    auto &k = c->kt;
+    if (enable && !k.ev[0][0])
+        for (auto &tri : k.ev)
+            for (cudaEvent_t &ev : tri)
+                if (ckr(cudaEventCreate(&ev))) return TPX_ECUDA;
+    k.on = enable != 0;
+    k.head = k.tail = 0;
+    k.pre_ms = k.fused_ms = 0.0;
+    k.launches = 0;
+    return TPX_OK;
+}
+
+int tpx_kernel_times(tpx_ctx *c, double *prepass_ms, double *fused_ms, int64_t *launches) {
+    if (!c) return TPX_EINVAL;
+    auto &k = c->kt;
+    while (k.head != k.tail)
+        if (int rc = ktime_collect_one(c)) return rc;
+    if (prepass_ms) *prepass_ms = k.pre_ms;
+    if (fused_ms) *fused_ms = k.fused_ms;
+    if (launches) *launches = k.launches;
     return TPX_OK;
 }
 

@@ -168,3 +168,34 @@ def test_shards_generated_apart_equal_one_call():
     assert np.array_equal(np.concatenate(labels), o["labels"])
     assert np.array_equal(np.concatenate(trig), o["triggers"])
     assert_clusters_equal(np.concatenate(clusters), o["clusters"])
+
+
+def test_kernel_timing_counts_each_fused_launch_and_leaves_results_unchanged():
+    import torch
+    pk = synth.generate(synth.small(shot_begin=0, n_shots=300, pair_frac=0.05))[0]
+    ref = oracle_run(pk)
+    ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+    try:
+        d = to_device(pk)
+        ctx.tpx_kernel_timing(True)
+        for _ in range(3):
+            out = ctx.alloc_outputs(pk.size, True, False, pk.size, pk.size)
+            ctx.tpx_process(d, out)
+            rc, cnt = ctx.tpx_sync(check=False)
+            assert rc == 0
+        t = ctx.tpx_kernel_times()
+        assert t["launches"] == 3
+        assert t["fused_ms"] > 0 and t["prepass_ms"] > 0
+        r = ctx.collect(out, rc, cnt)
+        assert np.array_equal(r["labels"], ref["labels"])
+        assert_clusters_equal(r["clusters"], ref["clusters"])
+        # off: nothing more is recorded; on again: the sums restart
+        ctx.tpx_kernel_timing(False)
+        ctx.tpx_process(d, out)
+        ctx.tpx_sync()
+        assert ctx.tpx_kernel_times()["launches"] == 3
+        ctx.tpx_kernel_timing(True)
+        assert ctx.tpx_kernel_times()["launches"] == 0
+        torch.cuda.synchronize()
+    finally:
+        ctx.close()
