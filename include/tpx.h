@@ -96,6 +96,15 @@ typedef struct tpx_config {
    reads the packets and writes labels, records and triggers over the host
    link.  Otherwise the call stages through device memory as usual. */
 #define TPX_FLAG_HOST_DIRECT 4
+/* TPX_FLAG_LABELS32 -- the per-packet labels of tpx_process,
+   tpx_process_host and tpx_process_noalloc are int32, not int64: the label
+   minus the call's packet_index_base (for tpx_process_host, the base of the
+   whole call), -1 where the packet is not a kept pixel.  The d_labels /
+   h_labels argument then points to n_packets int32 values (the pointer type
+   stays int64_t *).  Half the label bytes, the same information; a call whose
+   labels would not fit 31 bits is rejected (TPX_EINVAL), as is a batch call
+   with labels. */
+#define TPX_FLAG_LABELS32 8
 
 #define TPX_TILE_DEFAULT 0
 #define TPX_TILE_4096 1
@@ -272,8 +281,8 @@ int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
    fused launch of tpx_process / tpx_process_batch on the context records CUDA
    events on its stream before the unwrap pre-pass, between the pre-pass and
    the fused kernel, and after the fused kernel (not while the stream is being
-   captured into a graph).  0 turns it off.  The events are created on the
-   first enable; TPX_ECUDA if that fails.
+   captured into a graph).  0 turns it off and keeps the sums.  The events
+   are created on the first enable; TPX_ECUDA if that fails.
    tpx_kernel_times waits for the recorded launches and writes the summed
    pre-pass and fused-kernel milliseconds and the number of launches timed
    (any pointer may be NULL).  TPX_EINVAL for a NULL context. */

@@ -24,6 +24,7 @@ MODE_CC = 0
 MODE_PAPER = 1
 TILE_DEFAULT, TILE_4096, TILE_2048 = 0, 1, 2
 FLAG_HOST_DIRECT = 4
+FLAG_LABELS32 = 8
 TICK_NS = 1.5625
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ECORRUPT, EAGAIN, ETIMEOUT, EDEVTIMEOUT, ECUDA, EUNSUPPORTED = \
@@ -114,6 +115,10 @@ class Config:
     chain: bool = False                # each call continues where the previous one ended
     tile_geometry: int = 0             # TILE_DEFAULT, TILE_4096 or TILE_2048 (speed only)
     host_direct: bool = False          # tpx_process_host on mapped pinned host buffers in place
+    labels32: bool = False             # per-packet labels as int32, relative to the call's index base
+
+    def flags(self) -> int:
+        return (FLAG_HOST_DIRECT if self.host_direct else 0) | (FLAG_LABELS32 if self.labels32 else 0)
 
 
 _lock = threading.Lock()
@@ -232,7 +237,7 @@ class Context:
         c = _CConfig(self.cfg.rx, self.cfg.ry, self.cfg.dt_ticks, self.cfg.mode, self.cfg.tof_max_ticks,
                      self.cfg.wrap_thr_pix_ticks, self.cfg.wrap_thr_tdc_ticks, _ptr(self._lut),
                      int(self.cfg.strict), int(self.cfg.chain), int(self.cfg.tile_geometry),
-                     FLAG_HOST_DIRECT if self.cfg.host_direct else 0)
+                     self.cfg.flags())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         rc = lib().tpx_create(ctypes.byref(h), ctypes.byref(c), int(max_packets), ctypes.c_void_p(self.stream.cuda_stream))
@@ -296,7 +301,8 @@ class Context:
         cl_cap = int(cluster_capacity if cluster_capacity is not None else max(16, n_packets // 4))
         tr_cap = int(trig_capacity if trig_capacity is not None else max(16, n_packets // 8))
         return dict(
-            labels=torch.empty(n_packets, dtype=torch.int64, device=dev) if labels else None,
+            labels=torch.empty(n_packets, dtype=torch.int32 if self.cfg.labels32 else torch.int64,
+                               device=dev) if labels else None,
             is_peak=torch.empty(n_packets, dtype=torch.uint8, device=dev) if is_peak else None,
             clusters=torch.empty(cl_cap * CLUSTER_DTYPE.itemsize, dtype=torch.uint8, device=dev),
             n_clusters=torch.zeros(1, dtype=torch.int64, device=dev),
@@ -396,6 +402,7 @@ class Context:
     def tpx_process_host(self, packets: np.ndarray, labels: np.ndarray | None, is_peak: np.ndarray | None,
                          clusters: np.ndarray, triggers: np.ndarray, index_base: int = 0) -> tuple[int, int, int]:
         assert packets.dtype == np.uint64 and packets.flags.c_contiguous
+        assert labels is None or labels.dtype == (np.int32 if self.cfg.labels32 else np.int64)
         n_cl = ctypes.c_int64()
         n_tr = ctypes.c_int64()
         rc = lib().tpx_process_host(self._h, packets.ctypes.data, packets.size, int(index_base),

@@ -40,7 +40,6 @@ struct tpx_ctx {
     tpxk::TileScratch ts;
     void *scratch;            // one allocation for all tile records
     tpx_record *stage;        // fused-kernel record staging (inside scratch)
-    uint16_t *stage_perm;     // the staged records' label order (inside scratch)
     int64_t stage_records;    // its capacity
     tpxk::Ctl *ctl;           // device control block
     tpxk::Ctl *h_ctl;         // pinned host copy
@@ -78,6 +77,8 @@ struct tpx_ctx {
     tpxk::GAgg *d_state;      // [2]
     int cur;                  // d_state[cur]: state for the next call
     bool state_once;          // tpx_set_state was called for the next call
+    bool lab32_outer;         // int32 labels of the next calls are relative to lab32_base
+    int64_t lab32_base;       // (the pieces of one pipelined host call), not to their own base
     tpxk::GAgg h_state;       // host staging for tpx_set_state / tpx_get_state
     // scratch of the general (global-memory) path, grown on demand
     void *g_mem;
@@ -89,6 +90,8 @@ struct tpx_ctx {
         const uint64_t *pk;
         int64_t n, base;
         int64_t *labels;
+        bool lab32;               // labels are int32, minus lab32_base (TPX_FLAG_LABELS32)
+        int64_t lab32_base;
         uint8_t *is_peak;
         tpx_record *cl;
         int64_t cl_cap;

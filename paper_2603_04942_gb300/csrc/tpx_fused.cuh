@@ -94,6 +94,8 @@ struct Params {
     long long n;
     long long idx_base;
     long long *labels;
+    int *labels32;            // TPX_FLAG_LABELS32: labels minus lab32_base, as int32 (labels NULL)
+    long long lab32_base;
     uint8_t *is_peak;
     tpx_record *clusters;
     long long cl_cap;
@@ -110,9 +112,8 @@ struct Params {
     TileScratch ts;
     Ctl *ctl;
     tpx_record *stage;       // per-CTA record staging (range-capacity records per
-                             // CTA of the grid), or NULL: inline offset look-back
-    uint16_t *stage_perm;    // per CTA of the grid, range-capacity entries: the staged
-                             // record of each cluster id in label order (CC mode)
+                             // CTA of the grid, in label order), or NULL: inline
+                             // offset look-back
     BatchTable bt;           // batch of runs (tile_run == NULL: one stream)
     long long hold;          // tile + 1 whose look-back flags stay unpublished (0: none): lets a
                              // test run its successors' bounded waits out (TPX_EDEVTIMEOUT)

@@ -102,6 +102,8 @@ struct __align__(16) Smem {
                                                       // member-list heads
     union { uint16_t next[C]; uint16_t rootof[C]; } u2;
     uint8_t notpeak[C];
+    uint32_t lbits[C / 32];       // CC: the tile's label positions, one bit each
+    uint16_t lpre[C / 32];        // labels before each bitmap word
     long long tdc_t[MAXSEG];      // unwrapped trigger times of the range
     uint16_t tdc_pos[MAXSEG];     // their positions
     GAgg E;                       // unwrap state before the tile (from the pre-pass)
@@ -121,6 +123,7 @@ struct __align__(16) Smem {
     int first_tdc;
     int first_pix;                // first pixel of the range
     int la_first;
+    int nroot;                    // CC: clusters of the tile (roots appended to the root list)
     unsigned status;
 };
 
@@ -287,6 +290,7 @@ __device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsign
 // halves; writes keep the upper halves.
 constexpr uint32_t NO_EXT = 0xFFFFu, REWALK = 0xFFFEu;
 static_assert(C < (int)REWALK, "positions fit below the markers");
+static_assert((C / 32) % 32 == 0, "the label bitmap splits evenly over a warp");
 
 __device__ __forceinline__ uint32_t find_hw(uint32_t pbase, uint32_t x) {
     for (;;) {
@@ -339,19 +343,18 @@ __device__ void rewalk_unite(const Smem &S, const Params &p, uint32_t pbase, int
     }
 }
 
-// Warp 0 resolves the record offset of tile tl holding nc records (decoupled
-// look-back over the counts), publishes its inclusive count and, for the last
-// tile, the call's totals; the offset is left in S.clo. In a batch the chain
-// also carries the tile's nt triggers (offset in S.tlo), and a run's first
-// tile records the run's record and trigger offsets.
+// One warp resolves the record offset of tile tl holding nc records
+// (decoupled look-back over the counts), publishes its inclusive count and,
+// for the last tile, the call's totals; the offset is left in S.clo. In a
+// batch the chain also carries the tile's nt triggers (offset in S.tlo), and a
+// run's first tile records the run's record and trigger offsets.
 template <bool BATCH>
 __device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr, int nt,
                                int run, bool run_first) {
-    if (threadIdx.x >= 32) return;
     unsigned st2 = 0;
     longlong2 Ow = make_longlong2(0, 0);
     if (tl > 0) Ow = lookback_count_warp<BATCH>(p, tl, seq, &st2);
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & 31) == 0) {
         if (tl > 0 && tl + 1 != p.hold) {
             __stcg(&p.ts.cpre[tl], Ow.x + (long long)nc);
             if (BATCH) __stcg(&p.bt.tcpre[tl], Ow.y + (long long)nt);
@@ -378,39 +381,94 @@ __device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long
     }
 }
 
-// Staged output: a tile's records (and, in a batch, its trigger times) wait
-// in the CTA's staging slot until the next tile (or the end of the kernel)
-// resolves their offset, when the predecessors' counts are long published;
-// then one coalesced copy.
-template <int MODE, bool BATCH>
-__device__ void flush_pending(Smem &S, const Params &p, unsigned seq) {
+// Staged output: a tile's records (in label order) and, in a batch, its
+// trigger times wait in the CTA's staging slot until the CTA's next tile (or
+// the end of the kernel) resolves their offset, when the predecessors' counts
+// are long published; then one warp copies them out, coalesced, eight loads
+// in flight per lane. Called by one whole warp.
+template <bool BATCH>
+__device__ void flush_pending_warp(Smem &S, const Params &p, unsigned seq) {
     const long long pt = S.pend_tile;
     if (pt < 0) return;
+    const int lane = threadIdx.x & 31;
     const int nc = S.pend_ncl, nt = S.pend_ntdc;
     resolve_offset<BATCH>(S, p, seq, pt, nc, S.pend_ntr, nt, S.pend_run, S.pend_first);
-    __syncthreads();
+    __syncwarp();
     const long long O = S.clo;
     const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
     constexpr int WPR = (int)(sizeof(tpx_record) / 8);
     const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
-    if (MODE == TPX_MODE_CC) {   // staged in root order: copied out in label order
-        const uint16_t *perm = p.stage_perm + (long long)blockIdx.x * C;
-        for (long long w = threadIdx.x; w < keep * WPR; w += NT) {
-            const long long k = w / WPR;
-            dst[w] = __ldcg(src + (long long)__ldcg(perm + k) * WPR + (w - k * WPR));
-        }
-    } else {
-        for (long long w = threadIdx.x; w < keep * WPR; w += NT) dst[w] = __ldcg(src + w);
+    const long long nw = keep * WPR;
+    for (long long w0 = lane; w0 < nw; w0 += 32 * 8) {
+        unsigned long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = w0 + 32 * u < nw ? __ldcg(src + w0 + 32 * u) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (w0 + 32 * u < nw) dst[w0 + 32 * u] = v[u];
     }
     if (BATCH) {
         const long long TO = S.tlo;
         const long long tkeep = min((long long)nt, max(0LL, p.trig_cap - TO));
         const long long *ts = p.bt.tstage + (long long)blockIdx.x * T;
-        for (long long i = threadIdx.x; i < tkeep; i += NT) p.trig[TO + i] = __ldcg(ts + i);
+        for (long long i = lane; i < tkeep; i += 32) p.trig[TO + i] = __ldcg(ts + i);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) S.pend_tile = -1;
+    __syncwarp();
+    if (lane == 0) S.pend_tile = -1;
+}
+
+// the exact integer moments of one cluster from its member list (Sec. V.C)
+// and its canonical label: the earliest member in (time, position) order
+struct Moments {
+    long long s_tot, s_x, s_y, s_tt;   // s_tt: sum of ToT x biased ToF
+    int n, npk;
+    uint32_t best_lo;                  // label position
+    int tofb0;                         // its biased ToF
+};
+
+__device__ __forceinline__ Moments walk_members(const Smem &S, const Params &p, uint32_t head) {
+    const uint16_t *mnext = reinterpret_cast<const uint16_t *>(S.parent);
+    uint64_t best = ~0ull;
+    Moments m{0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t k = head; k != EMPTY; k = mnext[k]) {
+        if (!TPX_IN(k, C)) break;
+        const uint64_t rm = S.buf[pad((int)k)];
+        const long long tot = r_tot(rm);
+        const int tf = r_tof(rm);
+        best = min(best, ((uint64_t)tf << 16) | k);
+        m.n += 1;
+        m.npk += (S.notpeak[k] & 1) ? 0 : 1;
+        m.s_tot += tot;
+        m.s_x += tot * r_x(rm);
+        m.s_y += tot * r_y(rm);
+        m.s_tt += tot * (long long)tf;
+    }
+    m.best_lo = (uint32_t)(best & 0xFFFFu);
+    m.tofb0 = (int)(best >> 16);
+    return m;
+}
+
+// the record of a cluster whose label pixel lies at position best_lo of the
+// tile at stream position base
+__device__ __forceinline__ void put_record(tpx_record *dst, const Moments &m, const Smem &S, const Params &p,
+                                           long long base, long long shot0) {
+    const int seg = r_seg(S.buf[pad((int)m.best_lo)]);
+    const long long tofc0 = (long long)m.tofb0 - kTofBias;
+    const long long s_t = m.s_tt - (long long)m.tofb0 * m.s_tot;
+    tpx_record o;
+    o.label = p.idx_base + base + m.best_lo;
+    o.shot = shot0 + seg;
+    o.t0 = S.tdc_t[seg] + tofc0;
+    o.s_tot = m.s_tot; o.s_x = m.s_x; o.s_y = m.s_y; o.s_t = s_t;
+    o.n = m.n; o.n_peaks = m.npk;
+    com_from_moments(m.s_x, m.s_y, s_t, m.s_tot, tofc0, &o.x, &o.y, &o.tof);
+    *dst = o;
+}
+
+// rank of label position lp among the tile's labels (after the bitmap scan)
+__device__ __forceinline__ int label_rank(const Smem &S, uint32_t lp) {
+    return (int)S.lpre[lp >> 5] + __popc(S.lbits[lp >> 5] & ((1u << (lp & 31)) - 1u));
 }
 
 // ------------------------------------------------------------------- kernel
@@ -441,13 +499,15 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             if (tile < p.n_tiles) claim = atomicAdd(&p.ctl->tile_counter, 1u);
             S.first_tdc = INT_MAX;
             S.first_pix = INT_MAX;
+            S.nroot = 0;
             S.status = 0;
         }
         if (tid < C_NUM) S.cnt[tid] = 0;
         __syncthreads();
         if (tile >= p.n_tiles) {
             if (STAGED) {
-                flush_pending<MODE, BATCH>(S, p, seq);
+                if (tid < 32) flush_pending_warp<BATCH>(S, p, seq);
+                __syncthreads();
                 if (tid == 0 && S.status) atomicOr(&p.ctl->status, S.status);
             }
             // this CTA's counters (packets of each class are counted by the
@@ -885,95 +945,88 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             }
             __syncthreads();
             // member lists: each kept pixel joins its root's list (the links
-            // take the first half of the union-find array)
+            // take the first half of the union-find array); the roots are
+            // appended to the root list (its second half) in any order, and
+            // the label bitmap is cleared
             uint16_t *mnext = reinterpret_cast<uint16_t *>(S.parent);
-            for (int q = R0 + tid; q < R1; q += NT)
-                if (S.buf[pad(q)] != INVALID) {
+            uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
+            for (int w = tid; w < C / 32; w += NT) S.lbits[w] = 0u;
+            for (int qb = R0 + (tid & ~31); qb < R1; qb += NT) {
+                const int q = qb + lane;
+                bool is_root = false;
+                if (q < R1 && S.buf[pad(q)] != INVALID) {
                     const uint32_t rt = S.u2.rootof[q];
                     if (TPX_IN(rt, C)) mnext[q] = (uint16_t)atomicExch(&S.u1.mhead[rt], (uint32_t)q);
+                    is_root = rt == (uint32_t)q;
                 }
-            __syncthreads();
-            // the roots in position order (the label positions of the cluster
-            // ids take the second half of the union-find array later)
-            uint16_t *rootpos = reinterpret_cast<uint16_t *>(S.parent) + C;
-            {
-                int c = 0;
-                for (int j = 0; j < kpd; ++j) {
-                    const int q = p0 + j;
-                    if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) ++c;
-                }
-                int excl = block_scan_int(S, c, &ncl);
-                for (int j = 0; j < kpd; ++j) {
-                    const int q = p0 + j;
-                    if (q >= R0 && q < R1 && S.buf[pad(q)] != INVALID && S.u2.rootof[q] == q) {
-                        if (TPX_IN(excl, C)) rootpos[excl] = (uint16_t)q;
-                        ++excl;
-                    }
-                }
+                const unsigned m = __ballot_sync(0xffffffffu, is_root);
+                int at = 0;
+                if (lane == 0 && m) at = atomicAdd(&S.nroot, __popc(m));
+                at = __shfl_sync(0xffffffffu, at, 0) + __popc(m & ((1u << lane) - 1u));
+                if (is_root && TPX_IN(at, C)) rootpos[at] = (uint16_t)q;
             }
             __syncthreads();
+            ncl = S.nroot;
             if (STAGED) {
-                // the CTA's staging slot: the previous tile's records go out first
-                flush_pending<MODE, BATCH>(S, p, seq);
+                // The last warp copies the previous tile's staged records out
+                // while the others walk this tile's member lists: one thread
+                // per cluster forms the exact integer moments (Sec. V.C) and
+                // finds the cluster's earliest pixel in (time, position) order
+                // -- its canonical label -- which is kept in the upper half of
+                // the list head and marked in the label bitmap. A thread keeps
+                // its first cluster's moments in registers until the labels'
+                // ranks are known; the records are staged in label order.
+                constexpr int NWALK = NT - 32;
+                Moments held{0, 0, 0, 0, 0, 0, 0, 0};
+                if (tid >= NWALK) {
+                    flush_pending_warp<BATCH>(S, p, seq);
+                } else {
+                    for (int i = tid; i < ncl; i += NWALK) {
+                        if (!TPX_IN(i, C)) break;
+                        const uint32_t rt = rootpos[i];
+                        if (!TPX_IN(rt, C)) continue;
+                        const uint32_t head = S.u1.mhead[rt] & 0xFFFFu;
+                        const Moments m = walk_members(S, p, head);
+                        if (!TPX_IN(m.best_lo, C)) continue;
+                        S.u1.mhead[rt] = (m.best_lo << 16) | head;
+                        atomicOr(&S.lbits[m.best_lo >> 5], 1u << (m.best_lo & 31));
+                        if (i == tid) held = m;
+                    }
+                }
                 __syncthreads();
-                // one thread per root walks its list: the cluster's earliest
-                // pixel in (time, position) order -- its canonical label -- and
-                // the exact integer moments (Sec. V.C); the record is staged in
-                // root order, the list head keeps (label, record index), and
-                // the label pixel is flagged (bit 1 of notpeak)
+                // the labels' ranks: one warp scans the bitmap's counts
+                if (tid < 32) {
+                    constexpr int WPL = C / 32 / 32;   // bitmap words per lane
+                    int c = 0;
+#pragma unroll
+                    for (int k = 0; k < WPL; ++k) c += __popc(S.lbits[lane * WPL + k]);
+                    int incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += u;
+                    }
+                    int run = incl - c;
+#pragma unroll
+                    for (int k = 0; k < WPL; ++k) {
+                        S.lpre[lane * WPL + k] = (uint16_t)run;
+                        run += __popc(S.lbits[lane * WPL + k]);
+                    }
+                }
+                __syncthreads();
                 tpx_record *dst = p.stage + (long long)blockIdx.x * C;
-                for (int i = tid; i < ncl; i += NT) {
+                if (tid < NWALK && tid < ncl && held.n > 0) {
+                    const int k = label_rank(S, held.best_lo);
+                    if (TPX_IN(k, C)) put_record(dst + k, held, S, p, base, E.tdc.n);
+                }
+                // clusters beyond one per walking thread: walked again
+                for (int i = tid + NWALK; tid < NWALK && i < ncl; i += NWALK) {
                     if (!TPX_IN(i, C)) break;
                     const uint32_t rt = rootpos[i];
                     if (!TPX_IN(rt, C)) continue;
-                    const uint32_t head = S.u1.mhead[rt] & 0xFFFFu;
-                    uint64_t best = ~0ull;
-                    long long s_tot = 0, s_x = 0, s_y = 0, s_tt = 0;
-                    int n = 0, npk = 0;
-                    for (uint32_t m = head; m != EMPTY; m = mnext[m]) {
-                        if (!TPX_IN(m, C)) break;
-                        const uint64_t rm = S.buf[pad((int)m)];
-                        const long long tot = r_tot(rm);
-                        const int tf = r_tof(rm);
-                        best = min(best, ((uint64_t)tf << 16) | m);
-                        n += 1;
-                        npk += (S.notpeak[m] & 1) ? 0 : 1;
-                        s_tot += tot;
-                        s_x += tot * r_x(rm);
-                        s_y += tot * r_y(rm);
-                        s_tt += tot * (long long)tf;
-                    }
-                    const uint32_t lp = (uint32_t)(best & 0xFFFFu);
-                    const int tofb0 = (int)(best >> 16);
-                    const int seg = r_seg(S.buf[pad((int)rt)]);
-                    const long long tofc0 = (long long)tofb0 - kTofBias;
-                    const long long s_t = s_tt - (long long)tofb0 * s_tot;
-                    tpx_record o;
-                    o.label = p.idx_base + base + lp;
-                    o.shot = E.tdc.n + seg;
-                    o.t0 = S.tdc_t[seg] + tofc0;
-                    o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
-                    o.n = n; o.n_peaks = npk;
-                    com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                    dst[i] = o;
-                    S.u1.mhead[rt] = (lp << 16) | (uint32_t)i;
-                    if (TPX_IN(lp, C)) S.notpeak[lp] |= 2;
-                }
-                __syncthreads();
-                // the staged record of each cluster id in ascending label order
-                int c = 0;
-                for (int j = 0; j < kpd; ++j) {
-                    const int q = p0 + j;
-                    if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) ++c;
-                }
-                int excl = block_scan_int(S, c, &ncl);
-                uint16_t *perm = p.stage_perm + (long long)blockIdx.x * C;
-                for (int j = 0; j < kpd; ++j) {
-                    const int q = p0 + j;
-                    if (q >= R0 && q < R1 && (S.notpeak[q] & 2)) {
-                        if (TPX_IN(excl, C)) perm[excl] = (uint16_t)(S.u1.mhead[S.u2.rootof[q]] & 0xFFFFu);
-                        ++excl;
-                    }
+                    const Moments m = walk_members(S, p, S.u1.mhead[rt] & 0xFFFFu);
+                    const int k = label_rank(S, m.best_lo);
+                    if (TPX_IN(k, C) && TPX_IN(m.best_lo, C)) put_record(dst + k, m, S, p, base, E.tdc.n);
                 }
             } else {
             // one thread per root walks its list for the cluster's earliest
@@ -1044,12 +1097,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // offset after an inline look-back
         auto record_target = [&](long long *lim) -> tpx_record * {
             if (STAGED) {
-                flush_pending<MODE, BATCH>(S, p, seq);
-                __syncthreads();   // the member lists / peak list are complete
+                if (tid < 32) flush_pending_warp<BATCH>(S, p, seq);
+                __syncthreads();   // the peak list is complete
                 *lim = C;
                 return p.stage + (long long)blockIdx.x * C;
             }
-            resolve_offset<false>(S, p, seq, tile, ncl, ntr_here, 0, 0, false);
+            if (tid < 32) resolve_offset<false>(S, p, seq, tile, ncl, ntr_here, 0, 0, false);
             __syncthreads();
             *lim = p.cl_cap - S.clo;
             return p.clusters + S.clo;
@@ -1077,6 +1130,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 }
                 if (!TPX_IN(base + q, rend)) continue;
                 if (p.labels) p.labels[base + q] = kept ? p.idx_base + base + (long long)lp : -1LL;
+                else if (p.labels32) p.labels32[base + q] = kept ? (int)(p.idx_base - p.lab32_base + base + lp) : -1;
                 if (p.is_peak) p.is_peak[base + q] = pk;
             }
             c_pk = warp_sum(c_pk);
@@ -1129,6 +1183,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 }
                 if (!TPX_IN(base + q, rend)) continue;
                 if (p.labels) p.labels[base + q] = lab;
+                else if (p.labels32) p.labels32[base + q] = lab < 0 ? -1 : (int)(lab - p.lab32_base);
                 if (p.is_peak) p.is_peak[base + q] = pk;
             }
             c_pk = warp_sum(c_pk);

@@ -1444,6 +1444,14 @@ __global__ void k_packet_outputs(tpx_hits h, const long long *hl, const unsigned
         if (is_peak) is_peak[q] = hp[i];
     }
 }
+__global__ void k_packet_labels32(tpx_hits h, const long long *hl, long long nh, long long base, long long lbase,
+                                  int *labels) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nh; i += (long long)gridDim.x * blockDim.x)
+        labels[h.index[i] - base] = (int)(hl[i] - lbase);
+}
+__global__ void k_fill_i32(int *p, long long n, int v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
+}
 __global__ void k_fill_ll(long long *p, long long n, long long v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -1487,10 +1495,13 @@ int redo_last(tpx_ctx *c) {
     if (!rc && !(status & (ST_TRIG_ORDER | ST_TRIG_CAP))) {
         rc = cluster_all(c, h, nh, reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, -1, L.cl, L.cl_cap, L.n_cl);
         if (!rc && (L.labels || L.is_peak)) {
-            if (L.labels) k_fill_ll<<<grid_for(n), GT, 0, s>>>(reinterpret_cast<long long *>(L.labels), n, -1);
+            long long *l64 = L.lab32 ? nullptr : reinterpret_cast<long long *>(L.labels);
+            int *l32 = L.lab32 ? reinterpret_cast<int *>(L.labels) : nullptr;
+            if (l64) k_fill_ll<<<grid_for(n), GT, 0, s>>>(l64, n, -1);
+            if (l32) k_fill_i32<<<grid_for(n), GT, 0, s>>>(l32, n, -1);
             if (L.is_peak && cudaMemsetAsync(L.is_peak, 0, (size_t)n, s) != cudaSuccess) rc = TPX_ECUDA;
-            k_packet_outputs<<<grid_for(nh), GT, 0, s>>>(h, hl, hp, nh, L.base, reinterpret_cast<long long *>(L.labels),
-                                                        L.is_peak);
+            k_packet_outputs<<<grid_for(nh), GT, 0, s>>>(h, hl, hp, nh, L.base, l64, L.is_peak);
+            if (l32) k_packet_labels32<<<grid_for(nh), GT, 0, s>>>(h, hl, nh, L.base, L.lab32_base, l32);
         }
         if (!rc && nh > 0) {
             unsigned long long z = 0;

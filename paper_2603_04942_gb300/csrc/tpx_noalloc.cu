@@ -131,7 +131,10 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
         p.pk = d_packets;
         p.n = n;
         p.idx_base = idx_base;
-        p.labels = reinterpret_cast<long long *>(d_labels);
+        const bool l32 = (cfg->flags & TPX_FLAG_LABELS32) != 0;
+        p.labels = l32 ? nullptr : reinterpret_cast<long long *>(d_labels);
+        p.labels32 = l32 ? reinterpret_cast<int *>(d_labels) : nullptr;
+        p.lab32_base = idx_base;
         p.is_peak = d_is_peak;
         p.clusters = d_clusters;
         p.cl_cap = cl_cap;

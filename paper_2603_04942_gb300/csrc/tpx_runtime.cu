@@ -43,7 +43,7 @@ int check_cfg(const tpx_config *c) {
     if (c->wrap_thr_pix_ticks <= 0 || c->wrap_thr_tdc_ticks <= 0) return TPX_EINVAL;
     if (c->tile_geometry != TPX_TILE_DEFAULT && c->tile_geometry != TPX_TILE_4096 && c->tile_geometry != TPX_TILE_2048)
         return TPX_EINVAL;
-    if (c->flags & ~TPX_FLAG_HOST_DIRECT) return TPX_EINVAL;
+    if (c->flags & ~(TPX_FLAG_HOST_DIRECT | TPX_FLAG_LABELS32)) return TPX_EINVAL;
     return TPX_OK;
 }
 
@@ -51,7 +51,6 @@ void free_scratch(tpx_ctx *c) {
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
     c->stage = nullptr;
-    c->stage_perm = nullptr;
     std::memset(&c->ts, 0, sizeof c->ts);
     c->max_tiles = 0;
 }
@@ -74,8 +73,8 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
         if (r > stage_records) stage_records = r;
     }
     c->stage_records = (int64_t)stage_records;
-    const size_t b_stage = al(sizeof(tpx_record) * stage_records), b_perm = al(sizeof(uint16_t) * stage_records);
-    const size_t total = b_flags + b_blk + 2 * b_agg + 2 * b_cnt + b_stage + b_perm;
+    const size_t b_stage = al(sizeof(tpx_record) * stage_records);
+    const size_t total = b_flags + b_blk + 2 * b_agg + 2 * b_cnt + b_stage;
     void *mem = nullptr;
     if (cudaMalloc(&mem, total) != cudaSuccess) { cudaGetLastError(); return TPX_ENOMEM; }
     if (cudaMemset(mem, 0, total) != cudaSuccess) { cudaFree(mem); return TPX_ECUDA; }
@@ -86,8 +85,7 @@ int alloc_scratch(tpx_ctx *c, int64_t max_packets) {
     c->ts.pre = reinterpret_cast<tpxk::GAgg *>(p); p += b_agg;
     c->ts.cagg = reinterpret_cast<long long *>(p); p += b_cnt;
     c->ts.cpre = reinterpret_cast<long long *>(p); p += b_cnt;
-    c->stage = reinterpret_cast<tpx_record *>(p); p += b_stage;
-    c->stage_perm = reinterpret_cast<uint16_t *>(p);
+    c->stage = reinterpret_cast<tpx_record *>(p);
     c->scratch = mem;
     c->max_tiles = tiles;
     c->max_packets = tiles * T;
@@ -348,6 +346,9 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     if ((reinterpret_cast<uintptr_t>(d_packets) & 15) != 0) return TPX_EINVAL;
     if (cl_cap > 0 && !d_clusters) return TPX_EINVAL;
     if (trig_cap > 0 && !d_trig) return TPX_EINVAL;
+    const bool l32 = (c->cfg.flags & TPX_FLAG_LABELS32) != 0;
+    const int64_t l32_base = c->lab32_outer ? c->lab32_base : idx_base;
+    if (l32 && d_labels && idx_base - l32_base + n > (1LL << 31) - 1) return TPX_EINVAL;
     if (begin_call(c)) return TPX_ECUDA;
     c->last.valid = true;
     c->batch.last = false;
@@ -355,6 +356,8 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     c->last.n = n;
     c->last.base = idx_base;
     c->last.labels = d_labels;
+    c->last.lab32 = l32;
+    c->last.lab32_base = l32_base;
     c->last.is_peak = d_is_peak;
     c->last.cl = d_clusters;
     c->last.cl_cap = cl_cap;
@@ -385,7 +388,9 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.pk = d_packets;
     p.n = n;
     p.idx_base = idx_base;
-    p.labels = reinterpret_cast<long long *>(d_labels);
+    p.labels = l32 ? nullptr : reinterpret_cast<long long *>(d_labels);
+    p.labels32 = l32 ? reinterpret_cast<int *>(d_labels) : nullptr;
+    p.lab32_base = l32_base;
     p.is_peak = d_is_peak;
     p.clusters = d_clusters;
     p.cl_cap = cl_cap;
@@ -410,7 +415,6 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.E0 = E0;
     p.state_out = state_out;
     p.stage = c->stage;
-    p.stage_perm = c->stage_perm;
     p.hold = c->hold_next;
     c->hold_next = 0;
     int64_t grid = (int64_t)c->num_sms * tpxk::fused_ctas_per_sm(geo);   // persistent, all resident
@@ -457,6 +461,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
         !d_run_clusters || !d_run_trig)
         return TPX_EINVAL;
     if (h_run_offsets[0] != 0) return TPX_EINVAL;
+    if ((c->cfg.flags & TPX_FLAG_LABELS32) && d_labels) return TPX_EINVAL;   // batch labels are int64
     for (int64_t r = 0; r < n_runs; ++r)
         if (h_run_offsets[r + 1] < h_run_offsets[r]) return TPX_EINVAL;
     const int64_t n = h_run_offsets[n_runs];
@@ -611,7 +616,6 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     p.ts = B.ts;
     p.ctl = c->ctl;
     p.stage = c->stage;
-    p.stage_perm = c->stage_perm;
     p.bt = bt;
     cudaEvent_t *kte = ktime_begin(c, s);
     if (ckr(tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s, kte ? kte[1] : nullptr))) return TPX_ECUDA;
@@ -640,10 +644,12 @@ int tpx_kernel_timing(tpx_ctx *c, int enable) {
         for (auto &tri : k.ev)
             for (cudaEvent_t &ev : tri)
                 if (ckr(cudaEventCreate(&ev))) return TPX_ECUDA;
+    if (enable) {
+        if (int rc = tpx_kernel_times(c, nullptr, nullptr, nullptr)) return rc;   // nothing left in flight
+        k.pre_ms = k.fused_ms = 0.0;
+        k.launches = 0;
+    }
     k.on = enable != 0;
-    k.head = k.tail = 0;
-    k.pre_ms = k.fused_ms = 0.0;
-    k.launches = 0;
     return TPX_OK;
 }
 
@@ -801,6 +807,10 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
     P.trig_cap = std::max(P.trig_cap, trig_cap);
     if (h_labels && (rc = grow(&c->st_labels, &c->st_labels_cap, n))) return rc;
     if (h_is_peak && (rc = grow(&c->st_peak, &c->st_peak_cap, n))) return rc;
+    // int32 labels (TPX_FLAG_LABELS32) stay relative to the whole call
+    const size_t les = (c->cfg.flags & TPX_FLAG_LABELS32) ? 4 : 8;
+    char *st_lab = reinterpret_cast<char *>(c->st_labels);
+    char *h_lab = reinterpret_cast<char *>(h_labels);
     cudaStream_t sc = c->stream;
     // all earlier work on the context stream is done before the copies start
     if (ckr(cudaEventRecord(P.ev_done[0], sc)) || ckr(cudaStreamWaitEvent(P.s_in, P.ev_done[0], 0)) ||
@@ -846,9 +856,13 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
         if (ckr(cudaStreamWaitEvent(sc, P.ev_in[k], 0))) return TPX_ECUDA;
         if (k >= 2 && ckr(cudaStreamWaitEvent(sc, P.ev_out[k - 2], 0))) return TPX_ECUDA;
         c->state_once = k > 0 || user_state;   // continue from the previous piece's state
-        rc = tpx_process(c, P.pk[k & 1], m, idx_base + cut[k], h_labels ? c->st_labels + cut[k] : nullptr,
+        c->lab32_outer = true;
+        c->lab32_base = idx_base;
+        rc = tpx_process(c, P.pk[k & 1], m, idx_base + cut[k],
+                         h_labels ? reinterpret_cast<int64_t *>(st_lab + les * cut[k]) : nullptr,
                          h_is_peak ? c->st_peak + cut[k] : nullptr, P.cl[k & 1], cl_cap, P.d_counts + 2 * k,
                          P.trig[k & 1], trig_cap, P.d_counts + 2 * k + 1);
+        c->lab32_outer = false;
         if (rc) return rc;
         // a piece the autotuner's sample already redid on the general path
         // cannot show whether its cut was exact
@@ -861,7 +875,7 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
         // piece k+1 waits for them (it reuses their buffer), not for k's labels
         if (k >= 1 && (rc = d2h_records(k - 1))) return rc;
         if (ckr(cudaStreamWaitEvent(P.s_out, P.ev_done[k], 0))) return TPX_ECUDA;
-        if (h_labels && ckr(cudaMemcpyAsync(h_labels + cut[k], c->st_labels + cut[k], sizeof(int64_t) * m,
+        if (h_labels && ckr(cudaMemcpyAsync(h_lab + les * cut[k], st_lab + les * cut[k], les * m,
                                             cudaMemcpyDeviceToHost, P.s_out)))
             return TPX_ECUDA;
         if (h_is_peak && ckr(cudaMemcpyAsync(h_is_peak + cut[k], c->st_peak + cut[k], (size_t)m, cudaMemcpyDeviceToHost,
@@ -958,7 +972,8 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     int64_t counts[2] = {0, 0};
     if (ckr(cudaMemcpyAsync(counts, c->st_counts, sizeof counts, cudaMemcpyDeviceToHost, s))) return TPX_ECUDA;
     if (h_labels && n &&
-        cudaMemcpyAsync(h_labels, c->st_labels, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        cudaMemcpyAsync(h_labels, c->st_labels, ((c->cfg.flags & TPX_FLAG_LABELS32) ? 4 : 8) * (size_t)n,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;
     if (h_is_peak && n && cudaMemcpyAsync(h_is_peak, c->st_peak, n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;

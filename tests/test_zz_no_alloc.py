@@ -147,3 +147,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc = L.tpx_process_noalloc(ctypes.byref(cfg), None, None, NOALLOC_MAX_PACKETS + 1, 0, None, None, None, 0,
                                ctypes.addressof(dummy), None, 0, ctypes.addressof(dummy), None)
     assert rc == tpx.EINVAL
+
+
+def test_labels32_equal_the_oracle():
+    import torch
+    tpx, L = _lib()
+    pk = synth.generate(synth.small(shot_begin=0, n_shots=300))[0]
+    base = 1000
+    ref = oracle_run(pk, index_base=base)
+    cfg = tpx._CConfig()
+    L.tpx_config_default(ctypes.byref(cfg))
+    cfg.flags = tpx.FLAG_LABELS32
+    n = pk.size
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    labels = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    clusters = torch.zeros(n * tpx.CLUSTER_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    trig = torch.zeros(n, dtype=torch.int64, device="cuda")
+    n_cl = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n_tr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = tpx._CCounters()
+    torch.cuda.synchronize()
+    rc = L.tpx_process_noalloc(ctypes.byref(cfg), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                               d.data_ptr(), n, base, labels.data_ptr(), None, clusters.data_ptr(), n,
+                               n_cl.data_ptr(), trig.data_ptr(), n, n_tr.data_ptr(), ctypes.byref(cnt))
+    assert rc == 0
+    want = np.where(ref["labels"] < 0, -1, ref["labels"] - base).astype(np.int32)
+    assert np.array_equal(labels.cpu().numpy(), want)
+    ncl = int(n_cl.item())
+    g = np.frombuffer(clusters[: ncl * tpx.CLUSTER_DTYPE.itemsize].cpu().numpy().tobytes(), tpx.CLUSTER_DTYPE)
+    assert_clusters_equal(g, ref["clusters"])
