@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--refiner-only", action="store_true")
     ap.add_argument("--refiner-shots", type=int, default=500_000, help="training shots (about 20 clusters each)")
     ap.add_argument("--refiner-epochs", type=int, default=1)
+    ap.add_argument("--phase-shares", type=int, default=0, metavar="SHOTS",
+                    help="per-phase cycle shares of the fused kernel (instrumented build) on SHOTS shots of the "
+                         "large recipe, --tile geometry (2048 when default)")
     ap.add_argument("--cnn-infer-only", type=int, default=0, metavar="N",
                     help="time only the CNN refiner's tcgen05 inference on N random bf16 patches (random weights)")
     ap.add_argument("--batch-runs", type=int, default=4096)
@@ -542,6 +545,32 @@ def timewalk_bench(args) -> dict:
                             "c": synth.CALIBRATION_TOF_TICKS + p.timewalk_c / 1.5625, "d": 1.0}}
 
 
+def phase_bench(shots: int, tile: str) -> dict:
+    """Per-phase cycle shares of the fused kernel on `shots` shots of the
+    large recipe (the instrumented library must be loaded): two untimed calls,
+    then one call whose counters are read."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    geo = tpx.TILE_4096 if tile == "4096" else tpx.TILE_2048
+    pk = synth.generate(synth.large(n_shots=shots))[0]
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    ctx = tpx.Context(tpx.Config(tile_geometry=geo), max_packets=pk.size)
+    out = ctx.alloc_outputs(pk.size, True, False, pk.size // 8, shots + 16)
+    for _ in range(2):
+        ctx.tpx_process(d, out)
+    ctx.tpx_sync()
+    tpx.phase_times(geo, clear=True)
+    ctx.tpx_process(d, out)
+    ctx.tpx_sync()
+    cyc = tpx.phase_times(geo, clear=True).astype(np.float64)
+    ctx.close()
+    return {"metric": "fused-kernel phase shares (warp cycles, barrier waits included)", "packets": int(pk.size),
+            "tile_geometry": tile if tile != "default" else "2048",
+            "shares": {nm: round(float(c / cyc.sum()), 4) for nm, c in zip(tpx.PHASE_NAMES, cyc)}}
+
+
 CNN_FLOPS_PER_PATCH = 2 * (49 * 18 * 16 + 25 * 144 * 16 + 9 * 144 * 32 + 288 * 144 + 144 * 6)
 
 
@@ -761,6 +790,14 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.phase_shares:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2603_04942_gb300 import build as tbuild
+        import paper_2603_04942_gb300 as tpx
+        tpx.load(tbuild.build(phases=True))
+        print(json.dumps(phase_bench(args.phase_shares, args.tile)), flush=True)
+        return 0
     if args.cnn_infer_only:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -897,6 +934,7 @@ def main():
         # pinned packets and write the pinned outputs in place over the host
         # link); labels as int64 stream indices or int32 (TPX_FLAG_LABELS32)
         modes = [("staged through device memory, pipelined copies", False, False),
+                 ("staged through device memory, pipelined copies, int32 labels (TPX_FLAG_LABELS32)", False, True),
                  ("TPX_FLAG_HOST_DIRECT: kernels on the pinned host buffers in place, no copies", True, False),
                  ("TPX_FLAG_HOST_DIRECT + TPX_FLAG_LABELS32: in place, int32 labels", True, True)]
         results = []

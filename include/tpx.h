@@ -289,6 +289,21 @@ int tpx_sync(tpx_ctx *ctx, tpx_counters *counters);
 int tpx_kernel_timing(tpx_ctx *ctx, int enable);
 int tpx_kernel_times(tpx_ctx *ctx, double *prepass_ms, double *fused_ms, int64_t *launches);
 
+/* Per-phase cycle counters of the fused kernel (a measurement aid).  In the
+   instrumented build (libtpx_phases.so, compiled with -DTPX_PHASE_TIMING)
+   lane 0 of every warp adds the clock64 cycles of each phase of each tile to
+   the phase's counter (a phase's time includes the barrier wait that ends
+   it).  This call synchronises the device and copies the 32 counters of one
+   tile geometry (TPX_TILE_4096 or TPX_TILE_2048) to h_cycles[32], zeroing
+   them when `clear` is nonzero.  Phases: 0 tile start, 1 tile load,
+   2 look-ahead, 3 walk 2 and its scan, 4 trigger times, 5 walk 4 (records),
+   6 hash insert, 7 neighbour pass, 8 compression, 9 unions, 10 roots,
+   11 member lists, 12 member-list walks (and the previous tile's copy-out),
+   13 label ranks and staged stores, 14 labels and offsets, 15 tail,
+   16 the CTA's end.  The normal build returns TPX_EUNSUPPORTED (zeros);
+   TPX_EINVAL for another geometry or a NULL pointer. */
+int tpx_debug_phase_times(int tile_geometry, uint64_t *h_cycles, int clear);
+
 /* Upper bound on n_packets for tpx_process_noalloc (2^26 packets, 512 MB of
    input): the size of its fixed scratch array. */
 #define TPX_NOALLOC_MAX_PACKETS (1LL << 26)

@@ -40,7 +40,7 @@ COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger",
                   "kept", "clusters", "peaks", "status_bits", "redone")
 
 EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_destroy", "tpx_process",
-                    "tpx_process_host", "tpx_sync", "tpx_kernel_timing", "tpx_kernel_times", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
+                    "tpx_process_host", "tpx_sync", "tpx_kernel_timing", "tpx_kernel_times", "tpx_debug_phase_times", "tpx_process_noalloc", "tpx_decode", "tpx_cluster",
                     "tpx_centroid", "tpx_tuning", "tpx_process_batch", "tpx_tot_tof_histogram", "tpx_refine_patches", "tpx_refiner_params",
                     "tpx_refiner_forward", "tpx_refiner_train_step", "tpx_refine_decide",
                     "tpx_refiner_packed_bytes", "tpx_refiner_pack", "tpx_refiner_infer", "tpx_debug_hold_tile", "tpx_debug_noalloc_seq", "tpx_set_state", "tpx_get_state", "tpx_summarize", "tpx_stream_create",
@@ -145,6 +145,8 @@ def load(path: str | None = None):
         L.tpx_process_host.argtypes = [vp, vp, i64, i64, vp, vp, vp, i64, vp, vp, i64, vp]
         L.tpx_sync.argtypes = [vp, ctypes.POINTER(_CCounters)]
         L.tpx_kernel_timing.argtypes = [vp, i32]
+        L.tpx_debug_phase_times.argtypes = [i32, ctypes.POINTER(ctypes.c_uint64), i32]
+        L.tpx_debug_phase_times.restype = i32
         L.tpx_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]
         L.tpx_strerror.argtypes = [i32]
@@ -215,6 +217,21 @@ def load(path: str | None = None):
 
 def lib():
     return load()
+
+
+PHASE_NAMES = ("tile start", "tile load", "look-ahead", "walk 2 and its scan", "trigger times",
+               "walk 4 (records)", "hash insert", "neighbour pass", "compression", "unions", "roots",
+               "member lists", "member-list walks (and the previous tile's copy-out)",
+               "label ranks and staged stores", "labels and offsets", "tail", "CTA end")
+
+
+def phase_times(tile_geometry: int, clear: bool = True) -> np.ndarray:
+    """The fused kernel's per-phase cycle counters (instrumented build only)."""
+    arr = (ctypes.c_uint64 * 32)()
+    rc = lib().tpx_debug_phase_times(int(tile_geometry), arr, 1 if clear else 0)
+    if rc:
+        raise TpxError(rc, "tpx_debug_phase_times")
+    return np.array(arr[:len(PHASE_NAMES)], dtype=np.uint64)
 
 
 def _ptr(t) -> int | None:

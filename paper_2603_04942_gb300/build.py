@@ -14,6 +14,9 @@ LIB = os.path.join(OUT_DIR, "libtpx.so")
 # the checked build (-DTPX_CHECKED: the fused kernel tests every data-dependent
 # index and reports a violation in the status word instead of touching memory)
 CHECKED_LIB = os.path.join(OUT_DIR, "libtpx_checked.so")
+# the phase-timing build (-DTPX_PHASE_TIMING: per-phase clock64 counters in
+# the fused kernel, read with tpx_debug_phase_times)
+PHASES_LIB = os.path.join(OUT_DIR, "libtpx_phases.so")
 SOURCES = ["tpx_fused.cu", "tpx_prepass.cu", "tpx_runtime.cu", "tpx_noalloc.cu", "tpx_general.cu", "tpx_stream.cu",
            "tpx_refine.cu", "tpx_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,17 +39,18 @@ def _stale(lib: str = LIB) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
-    lib = CHECKED_LIB if checked else LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False, phases: bool = False) -> str:
+    lib = CHECKED_LIB if checked else PHASES_LIB if phases else LIB
     if not force and not _stale(lib):
         return lib
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     objs = []
-    extra = ["-DTPX_CHECKED"] if checked else []
+    extra = ["-DTPX_CHECKED"] if checked else ["-DTPX_PHASE_TIMING"] if phases else []
+    tag = "chk." if checked else "ph." if phases else ""
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{'chk.' if checked else ''}{os.getpid()}.o"))
+        obj = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}{os.getpid()}.o"))
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")

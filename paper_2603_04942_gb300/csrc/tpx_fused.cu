@@ -40,3 +40,24 @@ cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStrea
 }
 
 }  // namespace tpxk
+
+// Per-phase cycle counters of the instrumented build (-DTPX_PHASE_TIMING).
+extern "C" int tpx_debug_phase_times(int tile_geometry, uint64_t *h_cycles, int clear) {
+    if (!h_cycles || (tile_geometry != TPX_TILE_4096 && tile_geometry != TPX_TILE_2048)) return TPX_EINVAL;
+#ifdef TPX_PHASE_TIMING
+    const bool g2 = tile_geometry == TPX_TILE_2048;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TPX_ECUDA;
+    cudaError_t e = g2 ? cudaMemcpyFromSymbol(h_cycles, tpxk::geo_t2048::g_phase, 32 * 8)
+                       : cudaMemcpyFromSymbol(h_cycles, tpxk::geo_t4096::g_phase, 32 * 8);
+    if (e == cudaSuccess && clear) {
+        static const unsigned long long zero[32] = {0};
+        e = g2 ? cudaMemcpyToSymbol(tpxk::geo_t2048::g_phase, zero, 32 * 8)
+               : cudaMemcpyToSymbol(tpxk::geo_t4096::g_phase, zero, 32 * 8);
+    }
+    return e == cudaSuccess ? TPX_OK : TPX_ECUDA;
+#else
+    (void)clear;
+    for (int i = 0; i < 32; ++i) h_cycles[i] = 0;
+    return TPX_EUNSUPPORTED;
+#endif
+}

@@ -8,6 +8,8 @@ constexpr int MAXSEG = MS;         // TDC packets a range may hold (more: the ca
 constexpr uint64_t INVALID = ~0ull;
 constexpr uint32_t EMPTY = 0xFFFFu;
 constexpr long long MAX_SPIN = 1LL << 22;   // bounded look-back waits (~0.5 s)
+constexpr int LA0 = T / 2;         // look-ahead window loaded with the tile
+static_assert(T + LA0 <= C, "the look-ahead window fits the range");
 
 static_assert(T % NT == 0 && C % NT == 0 && T <= C && C <= 16384, "tile geometry");
 static_assert(C < 0xFFFF && HB % 2 == 0 && (HB & (HB - 1)) == 0 && HB * 2 <= C * 4, "16-bit hash heads");
@@ -26,6 +28,23 @@ __device__ __forceinline__ bool in_bounds(long long i, long long n, const Params
 #define TPX_IN(i, n) in_bounds((long long)(i), (long long)(n), p)
 #else
 #define TPX_IN(i, n) true
+#endif
+
+// Phase timing (-DTPX_PHASE_TIMING, the libtpx_phases.so build): lane 0 of
+// every warp adds the clock64 cycles since the previous mark to the phase's
+// counter; the kernel's end adds the CTA's counters to g_phase. A phase's
+// time includes the barrier wait that ends it. The normal build compiles the
+// marks away.
+#ifdef TPX_PHASE_TIMING
+__device__ unsigned long long g_phase[32];
+#define TPX_PH(k)                                                                         \
+    do {                                                                                  \
+        const long long ph_now = clock64();                                               \
+        if ((threadIdx.x & 31) == 0) atomicAdd(&S.ph[k], (unsigned long long)(ph_now - ph_t)); \
+        ph_t = ph_now;                                                                    \
+    } while (0)
+#else
+#define TPX_PH(k) do {} while (0)
 #endif
 
 __device__ __forceinline__ int pad(int p) { return p + (p >> 3); }   // conflict-free 8-wide walks
@@ -107,6 +126,7 @@ struct __align__(16) Smem {
     long long tdc_t[MAXSEG];      // unwrapped trigger times of the range
     uint16_t tdc_pos[MAXSEG];     // their positions
     GAgg E;                       // unwrap state before the tile (from the pre-pass)
+    long long j0;                 // pixel wrap step from the last pixel before the range to its first
     int warp_int[NW + 1];
     unsigned long long cnt[C_NUM];   // this tile's counters
     unsigned long long acc[C_NUM];   // this CTA's counters, added to the call's at its end
@@ -122,9 +142,12 @@ struct __align__(16) Smem {
     bool pend_first;
     int first_tdc;
     int first_pix;                // first pixel of the range
-    int la_first;
+    int la_first[3];              // first TDC packet past the tile (window, then rotating chunk slots)
     int nroot;                    // CC: clusters of the tile (roots appended to the root list)
     unsigned status;
+#ifdef TPX_PHASE_TIMING
+    unsigned long long ph[32];
+#endif
 };
 
 // MINB CTAs per SM within the SM's 228 KB of shared memory (1 KB of it is
@@ -483,27 +506,32 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
     if (tid == 0) {
         S.pend_tile = -1;
         S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
+        S.first_tdc = INT_MAX;
+        S.first_pix = INT_MAX;
+        S.nroot = 0;
+        S.status = 0;
+        S.la_first[0] = S.la_first[1] = S.la_first[2] = INT_MAX;
     }
+    if (tid < C_NUM) S.cnt[tid] = 0;
     if (tid < C_NUM) S.acc[tid] = 0;
+#ifdef TPX_PHASE_TIMING
+    if (tid < 32) S.ph[tid] = 0;
+    long long ph_t = clock64();
+#endif
     __syncthreads();
     // the unwrap state before the first tile, from the pre-pass
     if (tid < 8 && S.tile < p.n_tiles)
         reinterpret_cast<long long *>(&S.E)[tid] = __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[S.tile]) + tid);
 
     for (;;) {
+        // the tile's number, its unwrap state and the reset per-tile fields
+        // were written before this barrier (at the kernel's start or at the
+        // previous tile's tail)
         __syncthreads();
         const long long tile = S.tile;
         // the next tile is claimed now; its number is needed only at the end
         unsigned long long claim = 0;
-        if (tid == 0) {
-            if (tile < p.n_tiles) claim = atomicAdd(&p.ctl->tile_counter, 1u);
-            S.first_tdc = INT_MAX;
-            S.first_pix = INT_MAX;
-            S.nroot = 0;
-            S.status = 0;
-        }
-        if (tid < C_NUM) S.cnt[tid] = 0;
-        __syncthreads();
+        if (tid == 0 && tile < p.n_tiles) claim = atomicAdd(&p.ctl->tile_counter, 1u);
         if (tile >= p.n_tiles) {
             if (STAGED) {
                 if (tid < 32) flush_pending_warp<BATCH>(S, p, seq);
@@ -514,6 +542,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             // unwrap pre-pass)
             if (tid < C_NUM && tid != C_PIXELS && tid != C_TDCS && tid != C_CORRUPT && S.acc[tid])
                 atomicAdd(&p.ctl->counters[tid], S.acc[tid]);
+#ifdef TPX_PHASE_TIMING
+            TPX_PH(16);
+            __syncthreads();
+            if (tid < 32 && S.ph[tid]) atomicAdd(&g_phase[tid], S.ph[tid]);
+#endif
             break;
         }
         // the tile: in a batch, the tile queue names the run (each run is a
@@ -529,73 +562,97 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             base = tile * T;
         }
         const int cnt = (int)max(0LL, min((long long)T, rend - base));
+        TPX_PH(0);
 
-        // ---- load the tile: coalesced 16-byte loads into the padded buffer;
-        // its TDC packets are counted and the first one found on the way ----
+        // ---- load the tile and a first look-ahead window past it:
+        // coalesced 16-byte loads into the padded buffer; the tile's TDC
+        // packets are counted and its first one found on the way, and the
+        // first TDC packet of the window ----
+        const int lw = (int)max(0LL, min((long long)min(LA0, C - cnt), rend - base - cnt));   // window length
         {
-            int my_first = INT_MAX, c_tdc = 0;
+            int my_first = INT_MAX, my_la = INT_MAX, c_tdc = 0;
+            const int ltot = cnt + lw;
             if (BATCH && (base & 1)) {   // a run starting at an odd packet: 8-byte loads
-                for (int v = tid; v < cnt; v += NT) {
+                for (int v = tid; v < ltot; v += NT) {
                     const uint64_t w = __ldcg(p.pk + base + v);
                     S.buf[pad(v)] = w;
-                    if ((w >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, v); }
+                    if ((w >> 60) == 0x6u) {
+                        if (v < cnt) { ++c_tdc; my_first = min(my_first, v); } else my_la = min(my_la, v);
+                    }
                 }
             } else {
                 const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(p.pk + base);
-                const int npair = cnt >> 1;
+                const int npair = ltot >> 1;
                 for (int v = tid; v < npair; v += NT) {
                     ulonglong2 w = __ldcg(src + v);
                     S.buf[pad(2 * v)] = w.x;
                     S.buf[pad(2 * v + 1)] = w.y;
-                    if ((w.x >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, 2 * v); }
-                    if ((w.y >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, 2 * v + 1); }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int q = 2 * v + u;
+                        if (((u ? w.y : w.x) >> 60) == 0x6u) {
+                            if (q < cnt) { ++c_tdc; my_first = min(my_first, q); } else my_la = min(my_la, q);
+                        }
+                    }
                 }
-                if ((cnt & 1) && tid == 0) {
-                    const uint64_t w = __ldcg(p.pk + base + cnt - 1);
-                    S.buf[pad(cnt - 1)] = w;
-                    if ((w >> 60) == 0x6u) { ++c_tdc; my_first = min(my_first, cnt - 1); }
+                if ((ltot & 1) && tid == 0) {
+                    const uint64_t w = __ldcg(p.pk + base + ltot - 1);
+                    S.buf[pad(ltot - 1)] = w;
+                    if ((w >> 60) == 0x6u) {
+                        if (ltot - 1 < cnt) { ++c_tdc; my_first = min(my_first, ltot - 1); }
+                        else my_la = min(my_la, ltot - 1);
+                    }
                 }
             }
             for (int i = tid; i < HB / 2; i += NT) reinterpret_cast<uint32_t *>(S.u1.head)[i] = 0xFFFFFFFFu;
-            if (__any_sync(0xffffffffu, c_tdc != 0)) {
+            if (__any_sync(0xffffffffu, c_tdc != 0 || my_la != INT_MAX)) {
                 c_tdc = (int)warp_sum((unsigned long long)c_tdc);
                 my_first = __reduce_min_sync(0xffffffffu, (unsigned)my_first);
+                my_la = __reduce_min_sync(0xffffffffu, (unsigned)my_la);
                 if (lane == 0) {
-                    atomicAdd(&S.cnt[C_TDCS], (unsigned long long)c_tdc);
-                    atomicMin(&S.first_tdc, my_first);
+                    if (c_tdc) atomicAdd(&S.cnt[C_TDCS], (unsigned long long)c_tdc);
+                    if (my_first != INT_MAX) atomicMin(&S.first_tdc, my_first);
+                    if (my_la != INT_MAX) atomicMin(&S.la_first[0], my_la);
                 }
             }
         }
         __syncthreads();
 
+        TPX_PH(1);
         const int f = S.first_tdc;
 
-        // ---- look ahead past the tile up to the next TDC packet ----
-        int L = cnt;
+        // ---- look ahead past the window up to the next TDC packet, one
+        // barrier per chunk (the chunks' minima rotate over three slots: a
+        // slot is reset two chunks after it was read) ----
+        int L = f != INT_MAX ? cnt + lw : cnt;   // a tile without a TDC packet owns nothing
         bool term = false;
         if (f != INT_MAX) {
-            while (base + L < rend) {
-                const int room = C - L;
-                if (room <= 0) break;
-                const int chunk = (int)min((long long)min(NT, room), rend - (base + L));
-                bool is_t = false;
-                if (tid < chunk) {
-                    const uint64_t w = __ldcg(p.pk + base + L + tid);
-                    if (TPX_IN(L + tid, C)) S.buf[pad(L + tid)] = w;
-                    is_t = (w >> 60) == 0x6u;
+            const int lf0 = S.la_first[0];
+            if (lf0 != INT_MAX) {
+                L = lf0 + 1;
+                term = true;
+            } else {
+                for (int k = 1; base + L < rend; ++k) {
+                    const int room = C - L;
+                    if (room <= 0) break;
+                    const int chunk = (int)min((long long)min(NT, room), rend - (base + L));
+                    const int slot = k % 3;
+                    if (tid == 0) S.la_first[(k + 1) % 3] = INT_MAX;
+                    if (tid < chunk) {
+                        const uint64_t w = __ldcg(p.pk + base + L + tid);
+                        if (TPX_IN(L + tid, C)) S.buf[pad(L + tid)] = w;
+                        if ((w >> 60) == 0x6u) atomicMin(&S.la_first[slot], tid);
+                    }
+                    __syncthreads();
+                    const int lf = S.la_first[slot];
+                    if (lf != INT_MAX) { L += lf + 1; term = true; break; }
+                    L += chunk;
                 }
-                if (tid == 0) S.la_first = INT_MAX;
-                __syncthreads();
-                if (is_t) atomicMin(&S.la_first, tid);
-                __syncthreads();
-                const int lf = S.la_first;
-                __syncthreads();
-                if (lf != INT_MAX) { L += lf + 1; term = true; break; }
-                L += chunk;
             }
             if (!term && base + L < rend && tid == 0) atomicOr(&S.status, ST_CAPACITY);
         }
 
+        TPX_PH(2);
         // ---- walk 2: wrap steps and TDC counts over [0, L) ----
         // [0, L) is split evenly over all threads, in thread order (every
         // later per-thread walk and scan uses the same contiguous chunks). A
@@ -638,12 +695,19 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         const int li0 = (int)(pk_ex >> 16);              // TDC packets before the chunk
         const int ntdc = (int)(pk_tot >> 16);            // in [0, L)
         const int jp_ex = (int)(short)(pk_ex & 0xFFFFu); // pixel wraps between the range's first pixel and the chunk
+        TPX_PH(3);
         const GAgg E = S.E;
         // a call sees only its own triggers: "earlier" means earlier in this call
         const long long trig_base = (!BATCH && p.E0) ? p.E0->tdc.n : 0;
         const bool prev_global = E.tdc.n > trig_base;
         const int nseg = min(ntdc, MAXSEG);
-        if (ntdc > MAXSEG && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+        if (tid == 0) {
+            if (ntdc > MAXSEG) atomicOr(&S.status, ST_CAPACITY);
+            // the step into the range's first pixel, read while the buffer
+            // still holds packets (walk 4 overwrites them with records)
+            const int fp = S.first_pix;
+            S.j0 = (fp != INT_MAX && E.pix.n > 0) ? jump(pix_raw(S.buf[pad(fp)]) - E.pix.last, tp) : 0;
+        }
         // ---- TDC packets of the range in stream order, then their unwrapped
         // times (one warp, a scan of the wrap steps) ----
         if (ntd) {
@@ -692,14 +756,13 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         __syncthreads();
 
+        TPX_PH(4);
         // ---- walk 4: pixels -> shot, cut, timewalk, packed record ----
         {
             // wraps at the chunk's first pixel: before the range, the step from
             // the last pixel before it to the range's first pixel, the steps
             // inside the range before the chunk
-            const int fp = S.first_pix;
-            const long long j0 = (fp != INT_MAX && E.pix.n > 0) ? jump(pix_raw(S.buf[pad(fp)]) - E.pix.last, tp) : 0;
-            long long ep = E.pix.sum + j0 + jp_ex;
+            long long ep = E.pix.sum + S.j0 + jp_ex;
             bool has = false;
             long long last = 0;
             int seg = li0 - 1;
@@ -758,6 +821,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         __syncthreads();   // records written per contiguous chunk are read strided below
 
+        TPX_PH(5);
         // a batch tile whose range the tiles cannot hold: its run is redone by
         // the general path, so it clusters nothing (its counts still flow)
         const bool skip = BATCH && (S.status & (ST_CAPACITY | ST_EXCEPTION)) != 0;
@@ -787,6 +851,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         __syncthreads();
 
+        TPX_PH(6);
         // ---- neighbour pass: each adjacent pair once (Sec. V.A box rule) ----
         // The warp walks 32 consecutive positions at a time; each lane gathers
         // its pixel's partners in the forward half of the box -- a strict order
@@ -887,6 +952,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         __syncthreads();
 
+        TPX_PH(7);
         int ncl = 0;
         if (MODE == TPX_MODE_CC) {
             // compress: every pixel points to the root of its tree
@@ -896,6 +962,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 sh_st(pbase + 4 * q, (w & 0xFFFF0000u) | find_hw(pbase, w & 0xFFFFu));
             }
             __syncthreads();
+            TPX_PH(8);
             // unions of the second partners, warp-synchronous: each trip
             // advances every active lane by one find hop (path halving) or one
             // link attempt, the larger root position linked under the smaller.
@@ -938,12 +1005,14 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 }
             }
             __syncthreads();
+            TPX_PH(9);
             // roots; the hash is free now: member-list heads, cleared
             for (int q = R0 + tid; q < R1; q += NT) {
                 S.u1.mhead[q] = EMPTY;
                 if (S.buf[pad(q)] != INVALID) S.u2.rootof[q] = (uint16_t)find_ro(pbase, (uint32_t)q);
             }
             __syncthreads();
+            TPX_PH(10);
             // member lists: each kept pixel joins its root's list (the links
             // take the first half of the union-find array); the roots are
             // appended to the root list (its second half) in any order, and
@@ -966,6 +1035,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 if (is_root && TPX_IN(at, C)) rootpos[at] = (uint16_t)q;
             }
             __syncthreads();
+            TPX_PH(11);
             ncl = S.nroot;
             if (STAGED) {
                 // The last warp copies the previous tile's staged records out
@@ -994,6 +1064,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     }
                 }
                 __syncthreads();
+                TPX_PH(12);
                 // the labels' ranks: one warp scans the bitmap's counts
                 if (tid < 32) {
                     constexpr int WPL = C / 32 / 32;   // bitmap words per lane
@@ -1080,6 +1151,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             }
         }
 
+        TPX_PH(13);
         // ---- record offsets: publish this tile's count now, look back later ----
         if (tid == 0 && tile + 1 != p.hold) {
             if (tile > 0) {
@@ -1229,6 +1301,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 dst[i] = o;
             }
         }
+        TPX_PH(14);
         if (BATCH) {   // this tile's trigger times wait with its records
             const int nt = min((int)S.cnt[C_TDCS], MAXSEG);
             long long *ts = p.bt.tstage + (long long)blockIdx.x * T;
@@ -1246,10 +1319,17 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
             }
         }
         __syncthreads();
-        if (tid < C_NUM) S.acc[tid] += tid == C_PACKETS ? (unsigned long long)cnt : S.cnt[tid];
-        // the next tile and its unwrap state
+        TPX_PH(15);
+        // the tile's counters join the CTA's, and the per-tile fields are
+        // reset for the next tile (which starts with a barrier)
+        if (tid < C_NUM) {
+            S.acc[tid] += tid == C_PACKETS ? (unsigned long long)cnt : S.cnt[tid];
+            S.cnt[tid] = 0;
+        }
+        // the next tile and its unwrap state, by warp 0 alone: no other warp
+        // reads S.tile or S.E before the next barrier
         if (tid == 0) S.next_tile = (long long)claim;
-        __syncthreads();
+        __syncwarp();
         if (tid < 8 && S.next_tile < p.n_tiles)
             reinterpret_cast<long long *>(&S.E)[tid] =
                 __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[S.next_tile]) + tid);
@@ -1261,6 +1341,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 st = (st & ~(ST_CAPACITY | ST_EXCEPTION)) | ST_RUN_REDO;
             }
             if (st) atomicOr(&p.ctl->status, st);
+            S.status = 0;
+            S.first_tdc = INT_MAX;
+            S.first_pix = INT_MAX;
+            S.nroot = 0;
+            S.la_first[0] = S.la_first[1] = S.la_first[2] = INT_MAX;
         }
     }
 }

@@ -56,6 +56,24 @@ def test_library_loads_and_host_calls(libpath):
     assert L.tpx_create(ctypes.byref(h), ctypes.byref(bad), 10, None) == tpx.EINVAL
 
 
+def test_phase_counters_and_flags_without_a_gpu(libpath):
+    L = tpx.load(libpath)
+    arr = (ctypes.c_uint64 * 32)(*([7] * 32))
+    # the normal build has no phase counters: unsupported, zeros
+    assert L.tpx_debug_phase_times(tpx.TILE_2048, arr, 0) == tpx.EUNSUPPORTED
+    assert list(arr) == [0] * 32
+    assert L.tpx_debug_phase_times(5, arr, 0) == tpx.EINVAL
+    assert L.tpx_kernel_timing(None, 1) == tpx.EINVAL
+    assert L.tpx_kernel_times(None, None, None, None) == tpx.EINVAL
+    # the configuration accepts the two flags and nothing else
+    assert tpx.Config(labels32=True, host_direct=True).flags() == tpx.FLAG_LABELS32 | tpx.FLAG_HOST_DIRECT
+    bad = tpx._CConfig()
+    L.tpx_config_default(ctypes.byref(bad))
+    bad.flags = 16
+    h = ctypes.c_void_p()
+    assert L.tpx_create(ctypes.byref(h), ctypes.byref(bad), 10, None) == tpx.EINVAL
+
+
 def test_build_targets_sm103a_only():
     assert tbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 

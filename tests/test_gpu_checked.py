@@ -50,3 +50,46 @@ def test_checked_build_reports_no_violation_and_matches_the_oracle():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1500)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     assert r.stdout.count("ok ") == 6
+
+
+PHASE_SCRIPT = r"""
+import sys
+sys.path[:0] = [ROOT, HERE]
+import paper_2603_04942_gb300 as tpx
+from paper_2603_04942_gb300 import build
+tpx.load(build.build(phases=True))
+import synth
+from gpu_common import assert_parity, gpu_run, oracle_run
+# across the first pixel wrap: the wrap step into a range's first pixel
+pk = synth.generate(synth.large(n_shots=2000))[0]
+for tile in (tpx.TILE_2048, tpx.TILE_4096):
+    g = gpu_run(pk, tile=tile)
+    assert g["status"] == 0 and g["counters"]["redone"] == 0, (tile, g["status"], g["counters"])
+    assert_parity(g, oracle_run(pk))
+    print("ok", tile, flush=True)
+"""
+
+
+def test_phase_timing_build_matches_the_oracle_without_a_redo():
+    """The instrumented build's timers shift the warps' timing: it once
+    exposed a read of a packet another thread had already replaced by its
+    record (the wrap step into a range's first pixel). Its results must equal
+    the oracle's with no call handed to the general path."""
+    code = f"ROOT = {ROOT!r}\nHERE = {HERE!r}\n" + PHASE_SCRIPT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+    assert r.stdout.count("ok ") == 2
+
+
+def test_phase_timing_build_counts_every_phase():
+    """The instrumented build (-DTPX_PHASE_TIMING) runs the same kernel with
+    per-phase cycle counters; every phase of a tile is counted once."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--phase-shares", "3000", "--tile", "2048"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    sh = d["shares"]
+    assert abs(sum(sh.values()) - 1.0) < 1e-3
+    for k in ("neighbour pass", "walk 4 (records)", "unions", "tile load"):
+        assert sh[k] > 0, k
