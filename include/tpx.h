@@ -461,12 +461,14 @@ int tpx_cnn_train_step(tpx_ctx *ctx, float *d_params, float *d_adam_m, float *d_
 /* Inference on the tensor cores (tcgen05, fp32 accumulation in tensor
    memory): tpx_cnn_pack writes a bf16 copy of the weights (and fp32 biases)
    to d_packed (tpx_cnn_packed_bytes() bytes, 256-byte aligned);
-   tpx_cnn_infer runs the five layers as implicit GEMMs over n <= 2^30
-   patches d_x [n x 162] bf16 (16-byte aligned; tpx_refine_patches_bf16),
-   each hidden activation rounded to bf16 after its ReLU, into d_out [n x 6]
-   floats.  d_work: tpx_cnn_infer_work_bytes(n) bytes, 16-byte aligned (the
-   bf16 activations between layers).  Asynchronous; a tensor-core wait that
-   runs out sets the context's status (TPX_EDEVTIMEOUT at tpx_sync). */
+   tpx_cnn_infer runs the five layers over n <= 2^30 patches d_x [n x 162]
+   bf16 (16-byte aligned; tpx_refine_patches_bf16) in one kernel: groups of
+   48 patches per CTA, the layers as implicit GEMMs whose activations stay in
+   shared memory, each hidden activation rounded to bf16 after its ReLU, into
+   d_out [n x 6] floats.  d_work is not used (tpx_cnn_infer_work_bytes is
+   kept for the interface: 256 bytes for n > 0); it may be NULL.
+   Asynchronous; a tensor-core wait that runs out sets the context's status
+   (TPX_EDEVTIMEOUT at tpx_sync). */
 int64_t tpx_cnn_packed_bytes(void);
 int tpx_cnn_pack(tpx_ctx *ctx, const float *d_params, void *d_packed);
 int64_t tpx_cnn_infer_work_bytes(int64_t n);

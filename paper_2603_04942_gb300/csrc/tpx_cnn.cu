@@ -17,12 +17,13 @@
 // output positions of all patches; columns: input channel, kernel row,
 // kernel column) with the weights; the backward pass uses the same matrices
 // (weight gradients as split-K GEMMs over the rows, input gradients gathered
-// back from the column gradients). Inference: each layer is an implicit GEMM
-// on the fifth-generation tensor cores -- the im2col tile of 128 output
-// positions is gathered straight into shared memory, one thread issues
-// tcgen05.mma (bf16 operands, fp32 accumulator in tensor memory), the
-// epilogue reads the accumulator with tcgen05.ld, adds the bias, applies the
-// ReLU and rounds the activation to bf16 for the next layer.
+// back from the column gradients). Inference: one kernel runs all five layers
+// on the fifth-generation tensor cores for groups of patches -- implicit GEMMs
+// whose A operands are the layers' input maps in shared memory, read through
+// shifted descriptors (no im2col copy); one thread issues tcgen05.mma (bf16
+// operands, fp32 accumulators in tensor memory), the epilogue reads the
+// accumulators with tcgen05.ld, adds the bias, applies the ReLU and rounds
+// the activation to bf16 into the next layer's input map.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -266,22 +267,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-template <int CIN, int HIN, int N, int HO, int KK, int KP, bool IN_CHW, bool OUT_F32, int COUT>
-struct TcLayer {
-    static constexpr int K = CIN * KK * KK;   // real reduction length
-    static constexpr int ROWS = HO * HO;      // output positions per patch
-    static constexpr int TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));   // TMEM columns
-    // layers with several output positions per patch stage the inputs of the
-    // tile's patches in shared memory first (coalesced), then gather from there
-    static constexpr bool STAGE = HO > 1;
-    static constexpr int PIN = CIN * HIN * HIN;                      // input elements per patch
-    static constexpr int PPT = STAGE ? (127 + ROWS - 1) / ROWS + 1 : 0;   // patches a tile can span
-    static constexpr size_t A_BYTES = (size_t)128 * KP * 2, B_BYTES = (size_t)N * KP * 2;
-    static constexpr size_t IN_BYTES = (((size_t)PPT * PIN * 2 + 15) / 16) * 16;
-    static constexpr size_t SMEM = A_BYTES + B_BYTES + IN_BYTES + 64 + 1024;   // + barrier, TMEM address, alignment
-    static_assert(KP % 16 == 0 && KP >= K && N % 16 == 0 && N >= 16 && N <= 256 && COUT <= N, "tcgen05 shape");
-};
-
 // byte offset of element (r, k) of a core-matrix tile with KP columns
 __device__ __forceinline__ uint32_t core_off(int r, int k, int kp) {
     return (uint32_t)((((r >> 3) * (kp >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
@@ -301,175 +286,9 @@ __device__ __forceinline__ void cp_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
-template <int CIN, int HIN, int N, int HO, int KK, int KP, bool IN_CHW, bool OUT_F32, int COUT>
-__global__ void __launch_bounds__(128) k_conv_tc(const __nv_bfloat16 *__restrict__ in, long long n_rows,
-                                                 const __nv_bfloat16 *__restrict__ w, const float *__restrict__ bias,
-                                                 void *__restrict__ out, unsigned *status) {
-    using G = TcLayer<CIN, HIN, N, HO, KK, KP, IN_CHW, OUT_F32, COUT>;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *As = base;
-    unsigned char *Bs = base + G::A_BYTES;
-    __nv_bfloat16 *Sin = reinterpret_cast<__nv_bfloat16 *>(Bs + G::B_BYTES);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + G::B_BYTES + G::IN_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    // the weights, once: [N][KP] bf16 rows into the core-matrix layout
-    for (int i = tid; i < N * (KP / 8); i += 128) {
-        const int r = i / (KP / 8), c = i % (KP / 8);
-        *reinterpret_cast<uint4 *>(Bs + core_off(r, c * 8, KP)) = *reinterpret_cast<const uint4 *>(w + (size_t)r * KP + c * 8);
-    }
-    if (tid == 0) mbar_init(smem_u32(bar), 1);
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)G::TCOLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-    constexpr uint32_t SBO = (KP / 8) * 128;
-    uint32_t phase = 0;
-
-    const long long tiles = (n_rows + 127) / 128;
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        bool failed = false;
-        // ---- the im2col tile: 128 output positions x KP reduction columns ----
-        const long long r0 = tile * 128;
-        const long long n_pat = (n_rows + G::ROWS - 1) / G::ROWS;
-        const long long pf = r0 / G::ROWS;   // the tile's first patch
-        if (G::STAGE) {   // the inputs of the tile's patches, coalesced, into shared memory
-            const long long pl = min(n_pat, (r0 + 127) / G::ROWS + 1);
-            const int elems = (int)((pl - pf) * G::PIN);
-            const __nv_bfloat16 *src = in + pf * G::PIN;
-            if (G::PIN % 8 == 0) {
-                for (int i = tid; i < elems / 8; i += 128) cp16(Sin + 8 * i, src + 8 * i, true);
-            } else {      // PIN is even: 4-byte words
-                for (int i = tid; i < elems / 2; i += 128) cp4(Sin + 2 * i, src + 2 * i);
-            }
-            cp_wait_all();
-            __syncthreads();
-        }
-        if (G::STAGE) {   // one thread per row: the taps' offsets are compile-time constants
-            const int r = tid;
-            const long long row = r0 + r;
-            const bool valid = row < n_rows;
-            const int p = valid ? (int)(row / G::ROWS - pf) : 0;
-            const int pos = valid ? (int)(row % G::ROWS) : 0, oy = pos / HO, ox = pos % HO;
-            unsigned char *arow = As + core_off(r, 0, KP);
-            if (IN_CHW) {   // conv1: channel-major patch rows of 162, two k at a time
-                const __nv_bfloat16 *src = Sin + p * G::PIN + oy * HIN + ox;
-#pragma unroll
-                for (int k = 0; k < KP; k += 2) {
-                    __nv_bfloat16 v[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int kk = k + u, ci = kk / (KK * KK), t = kk % (KK * KK);
-                        v[u] = (valid && kk < G::K) ? src[ci * HIN * HIN + (t / KK) * HIN + (t % KK)] : __float2bfloat16_rn(0.f);
-                    }
-                    *reinterpret_cast<__nv_bfloat162 *>(arow + (((k >> 3) << 7) + ((k & 7) << 1))) = __halves2bfloat162(v[0], v[1]);
-                }
-            } else {        // channel-minor activations: 8 channels of a tap per 16-byte chunk
-                static_assert(IN_CHW || CIN % 8 == 0, "16-byte gathers");
-                const __nv_bfloat16 *src = Sin + p * G::PIN + (oy * HIN + ox) * CIN;
-#pragma unroll
-                for (int c8 = 0; c8 < KP; c8 += 8) {
-                    const int t = c8 / CIN, ci = c8 % CIN;
-                    uint4 v = make_uint4(0, 0, 0, 0);
-                    if (valid && c8 < G::K) v = *reinterpret_cast<const uint4 *>(src + ((t / KK) * HIN + (t % KK)) * CIN + ci);
-                    *reinterpret_cast<uint4 *>(arow + ((c8 >> 3) << 7)) = v;
-                }
-            }
-        } else {        // one output position per patch: the row is the patch's activations, copied
-            for (int i = tid; i < 128 * (KP / 8); i += 128) {
-                const int r = i / (KP / 8), c8 = (i % (KP / 8)) * 8;
-                const long long row = r0 + r;
-                const bool ok = row < n_rows && c8 < G::K;
-                cp16(As + core_off(r, c8, KP), ok ? in + row * G::K + c8 : in, ok);
-            }
-            cp_wait_all();
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // ---- one thread issues the MMAs over the reduction, then commits ----
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-            for (int s = 0; s < KP / 16; ++s) {
-                const uint64_t ad = sdesc(a_base + 256 * s, 128, SBO);
-                const uint64_t bd = sdesc(b_base + 256 * s, 128, SBO);
-                const uint32_t acc = s > 0 ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc_bf16(N)), "r"(acc)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                         : "memory");
-        }
-        // ---- wait for the accumulator (bounded; a wait that runs out sets the
-        // status and every thread leaves the loop, then frees the TMEM) ----
-        long long spins = 0;
-        while (!mbar_try_wait(smem_u32(bar), phase)) {
-            if (++spins > kSpin) { failed = true; break; }
-        }
-        if (__syncthreads_or(failed ? 1 : 0)) {
-            if (tid == 0) atomicOr(status, tpxk::ST_DEVTIMEOUT);
-            break;
-        }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- epilogue: warp w reads accumulator lanes 32w..32w+31 (its rows) ----
-        const long long row = r0 + 32 * warp + lane;
-#pragma unroll
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < n_rows) {
-                if (OUT_F32) {
-                    float *o = reinterpret_cast<float *>(out) + row * COUT;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < COUT) o[c0 + j] = __uint_as_float(v[j]) + bias[c0 + j];
-                } else {
-                    __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out) + row * COUT + c0;
-                    uint32_t pk[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float lo = fmaxf(__uint_as_float(v[2 * j]) + bias[c0 + 2 * j], 0.f);
-                        const float hi = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[c0 + 2 * j + 1], 0.f);
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-                        pk[j] = *reinterpret_cast<uint32_t *>(&b2);
-                    }
-                    reinterpret_cast<uint4 *>(o)[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    reinterpret_cast<uint4 *>(o)[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // the accumulator and the A tile are free again
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)G::TCOLS)
-                     : "memory");
-}
-
 // packed inference weights: per layer [N][KP] bf16 with column k = tap * cin +
-// ci (8 channels of a tap per 16-byte chunk; conv1: ci * 9 + tap), zero
-// padded; then the biases (fp32, padded to N)
+// ci (8 channels of a tap per 16-byte chunk; conv1: ky * 8 + kx * 2 + ci, one
+// chunk per kernel row), zero padded; then the biases (fp32, padded to N)
 struct Packed {
     static constexpr int N1 = 16, KP1 = 32, N2 = 16, KP2 = 144, N3 = 32, KP3 = 144, N4 = 144, KP4 = 288, N5 = 16,
                          KP5 = 144;
@@ -505,32 +324,363 @@ __global__ void k_cnn_pack(const float *P, __nv_bfloat16 *wt, float *bias) {
         else { L = 4; o = i - Q::w5; r = (int)(o / Q::KP5); k = (int)(o % Q::KP5); }
         const Conv C = layer_of(L);
         const int kk2 = C.kk * C.kk, K = C.cin * kk2;
-        if (r < C.cout && k < K) {
-            int ci, t;
-            if (L == 0) { ci = k / kk2; t = k % kk2; }   // conv1 gathers channel-major
-            else { t = k / C.cin; ci = k % C.cin; }
+        if (L == 0) {   // conv1: one 8-wide chunk per kernel row, [c0, c1] at kx = 0, 1, 2, two zeros
+            const int ky = k / 8, kx = (k % 8) / 2, ci = k % 2;
+            if (r < C.cout && ky < 3 && k % 8 < 6) v = P[C.ow + (long long)r * K + ci * kk2 + ky * 3 + kx];
+        } else if (r < C.cout && k < K) {   // k = tap * cin + ci: 8 channels of a tap per chunk
+            const int t = k / C.cin, ci = k % C.cin;
             v = P[C.ow + (long long)r * K + ci * kk2 + t];   // [cout][cin][tap]
         }
         wt[i] = __float2bfloat16_rn(v);
     }
 }
 
-template <int CIN, int HIN, int N, int HO, int KK, int KP, bool IN_CHW, bool OUT_F32, int COUT>
-int launch_tc(tpx_ctx *c, const __nv_bfloat16 *in, long long n_rows, const __nv_bfloat16 *w, const float *bias, void *out) {
-    using G = TcLayer<CIN, HIN, N, HO, KK, KP, IN_CHW, OUT_F32, COUT>;
-    auto kern = k_conv_tc<CIN, HIN, N, HO, KK, KP, IN_CHW, OUT_F32, COUT>;
-    if (ck(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM))) return TPX_ECUDA;
-    // CTAs per SM: by shared memory (227 KB, 1 KB reserved per CTA), by
-    // threads (16 of 128), and by tensor memory (each holds TCOLS of 512 columns)
-    int per_sm = (int)((227 * 1024) / (G::SMEM + 1024));
-    if (per_sm > 16) per_sm = 16;
-    if (per_sm > 512 / G::TCOLS) per_sm = 512 / G::TCOLS;
-    if (per_sm < 1) per_sm = 1;
-    const long long tiles = (n_rows + 127) / 128;
-    long long grid = (long long)c->num_sms * per_sm;
-    if (grid > tiles) grid = tiles;
-    if (grid < 1) return TPX_OK;
-    kern<<<(unsigned)grid, 128, G::SMEM, c->stream>>>(in, n_rows, w, bias, out, &c->ctl->status);
+// ---------------------------------------------------------------- fused inference
+// One persistent CTA per SM carries groups of FP patches through all five
+// layers: the activations stay in one shared-memory region X (each layer's
+// input is dead once its MMAs completed, so the next layer's input takes its
+// place), the accumulators in tensor memory, the weights in shared memory for
+// the whole launch. The convolutions are implicit GEMMs with no im2col copy:
+// a layer's input map is stored as planes of 8 channels with one 16-byte row
+// per input position, and the layer computes an output row for every position
+// of its input grid (the rows outside the valid window are computed and
+// dropped), so the A operand of kernel tap (ky, kx) is the map itself shifted
+// by ky * W + kx rows -- a descriptor with its start moved, leading offset the
+// plane stride, stride offset one core matrix (8 rows). conv1's two channels
+// are packed with those of the two right-hand neighbours into one row
+// ([c0, c1] at x, x + 1, x + 2, then two zeros), so a k chunk is a kernel row.
+// Rows past the valid ones read stale (finite) contents of X; X starts zeroed.
+constexpr int FP = 48;                                // patches per group
+constexpr int R1 = FP * 81, T1 = (R1 + 127) / 128;    // conv1: rows of the 9 x 9 grid, MMA tiles
+constexpr int R2 = FP * 49, T2 = (R2 + 127) / 128;    // conv2: 7 x 7 grid
+constexpr int R3 = FP * 25, T3 = (R3 + 127) / 128;    // conv3: 5 x 5 grid
+constexpr int M1_ROWS = T1 * 128 + 27;                // conv1 reads up to the largest shift (18, then +9)
+constexpr int P1_ROWS = T2 * 128 + 16;                // conv2 input plane (shifts up to 2 * 7 + 2)
+constexpr int P2_ROWS = T3 * 128 + 12;                // conv3 input plane (shifts up to 2 * 5 + 2)
+constexpr int PLB = FP * 16;                          // dense-layer input plane: one row per patch
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t X_BYTES =
+    ((cmax(cmax((size_t)M1_ROWS * 16, (size_t)2 * P1_ROWS * 16),
+           cmax((size_t)2 * P2_ROWS * 16, cmax((size_t)(35 * FP + 128) * 16, (size_t)(17 * FP + 128) * 16))) +
+      127) / 128) * 128;
+constexpr size_t W1B = 16 * 32 * 2, W2B = 16 * 144 * 2, W3B = 32 * 144 * 2, W4B = 144 * 288 * 2, W5B = 16 * 144 * 2;
+constexpr size_t W_BYTES = W1B + W2B + W3B + W4B + W5B;
+constexpr size_t RAW_BYTES = (size_t)FP * 162 * 2;    // one group of bf16 patches
+constexpr size_t FUSED_SMEM = 1024 + W_BYTES + X_BYTES + 2 * RAW_BYTES + 64;
+static_assert(T1 * 16 <= 512 && T2 * 16 <= 512 && T3 * 32 <= 512 && FP <= 128, "tensor memory of a group");
+static_assert(FUSED_SMEM <= 227 * 1024, "shared memory of the fused kernel");
+static_assert(RAW_BYTES % 16 == 0 && W_BYTES % 128 == 0, "16-byte copies");
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, bool acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc ? 1u : 0u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t *v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// 32 consecutive accumulator columns of the warp's 32 lanes, no wait
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t ta, uint32_t *v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(ta));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 16 accumulators + bias, ReLU, rounded to bf16: two 16-byte rows of 8 channels
+__device__ __forceinline__ void relu_bf16x16(const uint32_t *v, const float *bias, uint4 *lo, uint4 *hi) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float a = fmaxf(__uint_as_float(v[2 * j]) + __ldg(bias + 2 * j), 0.f);
+        const float b = fmaxf(__uint_as_float(v[2 * j + 1]) + __ldg(bias + 2 * j + 1), 0.f);
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(a, b);
+        pk[j] = *reinterpret_cast<uint32_t *>(&b2);
+    }
+    *lo = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *hi = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+// [N][KP] bf16 rows of the packed weights into the canonical core-matrix layout
+__device__ __forceinline__ void load_weights(unsigned char *dst, const __nv_bfloat16 *w, int n, int kp) {
+    for (int i = threadIdx.x; i < n * (kp / 8); i += blockDim.x) {
+        const int r = i / (kp / 8), c = i % (kp / 8);
+        *reinterpret_cast<uint4 *>(dst + core_off(r, c * 8, kp)) = *reinterpret_cast<const uint4 *>(w + (size_t)r * kp + c * 8);
+    }
+}
+
+// the bf16 patches of group g (zero past the last patch), 16-byte copies
+__device__ __forceinline__ void load_group(unsigned char *raw, const __nv_bfloat16 *x, long long n, long long g) {
+    const long long b0 = g * (long long)RAW_BYTES, bend = n * 324;
+    const unsigned char *src = reinterpret_cast<const unsigned char *>(x);
+    for (int i = threadIdx.x; i < (int)(RAW_BYTES / 16); i += blockDim.x) {
+        const long long o = b0 + 16LL * i;
+        const long long rem = bend - o;
+        const int bytes = rem >= 16 ? 16 : (rem > 0 ? (int)rem : 0);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(raw + 16 * i)),
+                     "l"(src + (bytes ? o : 0)), "r"(bytes)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+constexpr int CNN_THREADS = 512;   // 16 warps: four per tensor-memory lane quadrant
+
+__global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat16 *__restrict__ x, long long n,
+                                                      const __nv_bfloat16 *__restrict__ wt,
+                                                      const float *__restrict__ bias, float *__restrict__ out,
+                                                      unsigned *status) {
+    using Q = Packed;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *W1 = base, *W2 = W1 + W1B, *W3 = W2 + W2B, *W4 = W3 + W3B, *W5 = W4 + W4B;
+    unsigned char *X = W5 + W5B;
+    unsigned char *RAW[2] = {X + X_BYTES, X + X_BYTES + RAW_BYTES};
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + X_BYTES + 2 * RAW_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, sub = warp >> 2;   // accumulator lanes 32 * quad.., and which share of the columns
+    const long long groups = (n + FP - 1) / FP;
+
+    load_weights(W1, wt + Q::w1, 16, 32);
+    load_weights(W2, wt + Q::w2, 16, 144);
+    load_weights(W3, wt + Q::w3, 32, 144);
+    load_weights(W4, wt + Q::w4, 144, 288);
+    load_weights(W5, wt + Q::w5, 16, 144);
+    for (int i = tid; i < (int)(X_BYTES / 16); i += CNN_THREADS) reinterpret_cast<uint4 *>(X)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) mbar_init(smem_u32(bar), 1);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    long long g = blockIdx.x;
+    if (g < groups) load_group(RAW[0], x, n, g);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t xs = smem_u32(X);
+    const uint32_t lane_off = (uint32_t)(32 * quad) << 16;   // this warp's accumulator lanes
+    uint32_t phase = 0;
+    bool failed = false;
+
+    // the layer's A operand is in X: make it visible to the tensor cores, then
+    // one thread issues the MMAs and commits; everyone waits (bounded)
+    auto run_layer = [&](auto issue) -> bool {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            issue();
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                         : "memory");
+        }
+        long long spins = 0;
+        bool bad = false;
+        while (!mbar_try_wait(smem_u32(bar), phase)) {
+            if (++spins > kSpin) { bad = true; break; }
+        }
+        phase ^= 1u;
+        if (__syncthreads_or(bad ? 1 : 0)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return true;
+    };
+
+    for (int it = 0; g < groups; g += gridDim.x, ++it) {
+        unsigned char *raw = RAW[it & 1];
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        // the next group's patches come in while this one runs
+        if (g + gridDim.x < groups) load_group(RAW[(it + 1) & 1], x, n, g + gridDim.x);
+        // ---- conv1 input map: row (patch, y * 9 + x) = [c0, c1] at x, x + 1, x + 2, 0, 0 ----
+        {
+            const __nv_bfloat16 *pr = reinterpret_cast<const __nv_bfloat16 *>(raw);
+            for (int r = tid; r < R1; r += CNN_THREADS) {
+                const int pp = r / 81, pos = r % 81, xx = pos % 9;
+                const __nv_bfloat16 *c0 = pr + pp * 162 + pos, *c1 = c0 + 81;
+                const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+                __nv_bfloat162 v0 = __halves2bfloat162(c0[0], c1[0]);
+                __nv_bfloat162 v1 = xx + 1 < 9 ? __halves2bfloat162(c0[1], c1[1]) : __halves2bfloat162(z, z);
+                __nv_bfloat162 v2 = xx + 2 < 9 ? __halves2bfloat162(c0[2], c1[2]) : __halves2bfloat162(z, z);
+                __nv_bfloat162 v3 = __halves2bfloat162(z, z);
+                uint4 row;
+                row.x = *reinterpret_cast<uint32_t *>(&v0);
+                row.y = *reinterpret_cast<uint32_t *>(&v1);
+                row.z = *reinterpret_cast<uint32_t *>(&v2);
+                row.w = *reinterpret_cast<uint32_t *>(&v3);
+                reinterpret_cast<uint4 *>(X)[r] = row;
+            }
+        }
+        // ---- conv1: 2 MMAs per tile (kernel rows 0-1, then row 2 and a zero chunk) ----
+        if (!run_layer([&] {
+                // a descriptor's start field counts 16-byte units: one row, or
+                // 256 bytes = 16 for the next two k chunks of the weights
+                const uint32_t id = idesc_bf16(16);
+                const uint64_t da = sdesc(xs, 144, 128), db = sdesc(smem_u32(W1), 128, 512);
+                // the tiles' accumulators are independent: consecutive MMAs go to
+                // different tiles, so a tile's accumulation chain does not stall the pipe
+                for (int t = 0; t < T1; ++t) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128), db, id, false);
+                for (int t = 0; t < T1; ++t) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + 18), db + 16, id, true);
+            })) { failed = true; break; }
+        // epilogue: the 7 x 7 window -> conv2 input planes; a warp takes two
+        // tiles (32 accumulator columns) of its lane quadrant per load
+        for (int t0 = 2 * sub; t0 < T1; t0 += 8) {
+            uint32_t v[32];
+            tmem_ld32_nowait(tmem + lane_off + 16 * t0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = t0 + u;
+                const int r = t * 128 + 32 * quad + lane;
+                const int pp = r / 81, pos = r % 81, yy = pos / 9, xx = pos % 9;
+                if (t < T1 && pp < FP && yy < 7 && xx < 7) {
+                    uint4 lo, hi;
+                    relu_bf16x16(v + 16 * u, bias + Q::b1, &lo, &hi);
+                    const int o = pp * 49 + yy * 7 + xx;
+                    reinterpret_cast<uint4 *>(X)[o] = lo;
+                    reinterpret_cast<uint4 *>(X + (size_t)P1_ROWS * 16)[o] = hi;
+                }
+            }
+        }
+        // ---- conv2: one MMA per tap (16 channels = the two planes) ----
+        if (!run_layer([&] {
+                const uint32_t id = idesc_bf16(16);
+                const uint64_t da = sdesc(xs, P1_ROWS * 16, 128), db = sdesc(smem_u32(W2), 128, 18 * 128);
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    for (int t = 0; t < T2; ++t)
+                        mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + (k / 3) * 7 + k % 3), db + 16 * k, id, k > 0);
+            })) { failed = true; break; }
+        for (int t0 = 2 * sub; t0 < T2; t0 += 8) {
+            uint32_t v[32];
+            tmem_ld32_nowait(tmem + lane_off + 16 * t0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = t0 + u;
+                const int r = t * 128 + 32 * quad + lane;
+                const int pp = r / 49, pos = r % 49, yy = pos / 7, xx = pos % 7;
+                if (t < T2 && pp < FP && yy < 5 && xx < 5) {
+                    uint4 lo, hi;
+                    relu_bf16x16(v + 16 * u, bias + Q::b2, &lo, &hi);
+                    const int o = pp * 25 + yy * 5 + xx;
+                    reinterpret_cast<uint4 *>(X)[o] = lo;
+                    reinterpret_cast<uint4 *>(X + (size_t)P2_ROWS * 16)[o] = hi;
+                }
+            }
+        }
+        // ---- conv3 ----
+        if (!run_layer([&] {
+                const uint32_t id = idesc_bf16(32);
+                const uint64_t da = sdesc(xs, P2_ROWS * 16, 128), db = sdesc(smem_u32(W3), 128, 18 * 128);
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    for (int t = 0; t < T3; ++t)
+                        mma_bf16(tmem + 32 * t, da + (uint64_t)(t * 128 + (k / 3) * 5 + k % 3), db + 16 * k, id, k > 0);
+            })) { failed = true; break; }
+        // epilogue: the 3 x 3 window -> fc1 input, one row per patch, plane (pos * 4 + channel / 8)
+        for (int t = sub; t < T3; t += 4) {
+            uint32_t v[32];
+            tmem_ld32_nowait(tmem + lane_off + 32 * t, v);
+            tmem_wait_ld();
+            const int r = t * 128 + 32 * quad + lane;
+            const int pp = r / 25, pos = r % 25, yy = pos / 5, xx = pos % 5;
+            if (pp < FP && yy < 3 && xx < 3) {
+                uint4 a0, a1, a2, a3;
+                relu_bf16x16(v, bias + Q::b3, &a0, &a1);
+                relu_bf16x16(v + 16, bias + Q::b3 + 16, &a2, &a3);
+                const int j = (yy * 3 + xx) * 4;
+                *reinterpret_cast<uint4 *>(X + (size_t)(j + 0) * PLB + 16 * pp) = a0;
+                *reinterpret_cast<uint4 *>(X + (size_t)(j + 1) * PLB + 16 * pp) = a1;
+                *reinterpret_cast<uint4 *>(X + (size_t)(j + 2) * PLB + 16 * pp) = a2;
+                *reinterpret_cast<uint4 *>(X + (size_t)(j + 3) * PLB + 16 * pp) = a3;
+            }
+        }
+        // ---- fc1: 18 MMAs over K = 288 (rows past the group's patches are dropped) ----
+        if (!run_layer([&] {
+                const uint32_t id = idesc_bf16(144);
+                const uint64_t da = sdesc(xs, PLB, 128), db = sdesc(smem_u32(W4), 128, 36 * 128);
+                // three accumulators (columns 0, 160, 320) over interleaved k
+                // steps, summed in the epilogue: three short chains, not one long
+#pragma unroll
+                for (int k = 0; k < 18; ++k)
+                    mma_bf16(tmem + 160 * (k % 3), da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
+            })) { failed = true; break; }
+        {
+            const int pp = 32 * quad + lane;
+#pragma unroll 1
+            for (int c0 = 32 * sub; c0 < 144; c0 += 128) {   // 32 columns of each of the three accumulators per wait
+                uint32_t v[32], u[32], w[32];
+                tmem_ld32_nowait(tmem + lane_off + c0, v);
+                tmem_ld32_nowait(tmem + lane_off + 160 + c0, u);
+                tmem_ld32_nowait(tmem + lane_off + 320 + c0, w);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(u[j]) + __uint_as_float(w[j]));
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + 16 * h;
+                    if (c < 144 && pp < FP) {
+                        uint4 lo, hi;
+                        relu_bf16x16(v + 16 * h, bias + Q::b4 + c, &lo, &hi);
+                        *reinterpret_cast<uint4 *>(X + (size_t)(c / 8) * PLB + 16 * pp) = lo;
+                        *reinterpret_cast<uint4 *>(X + (size_t)(c / 8 + 1) * PLB + 16 * pp) = hi;
+                    }
+                }
+            }
+        }
+        // ---- fc2: 9 MMAs over K = 144, fp32 outputs ----
+        if (!run_layer([&] {
+                const uint32_t id = idesc_bf16(16);
+                const uint64_t da = sdesc(xs, PLB, 128), db = sdesc(smem_u32(W5), 128, 18 * 128);
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    mma_bf16(tmem + 16 * (k % 3), da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
+            })) { failed = true; break; }
+        if (sub == 0) {
+            uint32_t v[32], u[16];
+            tmem_ld32_nowait(tmem + lane_off, v);        // accumulators 0 and 1
+            tmem_ld16(tmem + lane_off + 32, u);          // accumulator 2 (and the wait)
+            const int pp = 32 * quad + lane;
+            const long long row = g * FP + pp;
+            if (pp < FP && row < n) {
+#pragma unroll
+                for (int j = 0; j < NOUT; ++j)
+                    out[row * NOUT + j] = __uint_as_float(v[j]) + __uint_as_float(v[16 + j]) + __uint_as_float(u[j]) +
+                                          __ldg(bias + Q::b5 + j);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    if (failed && tid == 0) atomicOr(status, tpxk::ST_DEVTIMEOUT);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+int launch_fused_cnn(tpx_ctx *c, const __nv_bfloat16 *x, long long n, const __nv_bfloat16 *wt, const float *bias,
+                     float *out) {
+    if (ck(cudaFuncSetAttribute(k_cnn_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FUSED_SMEM))) return TPX_ECUDA;
+    const long long groups = (n + FP - 1) / FP;
+    long long grid = c->num_sms;   // one CTA per SM: its shared memory and all of tensor memory
+    if (grid > groups) grid = groups;
+    k_cnn_fused<<<(unsigned)grid, CNN_THREADS, FUSED_SMEM, c->stream>>>(x, n, wt, bias, out, &c->ctl->status);
     return ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
 }
 
@@ -594,29 +744,16 @@ int tpx_cnn_pack(tpx_ctx *c, const float *d_params, void *d_packed) {
     return ck(cudaGetLastError()) ? TPX_ECUDA : TPX_OK;
 }
 
-int64_t tpx_cnn_infer_work_bytes(int64_t n) {
-    if (n <= 0) return 0;
-    return n * (int64_t)(49 * 16 + 25 * 16 + 9 * 32 + 144) * 2 + 1024;
-}
+int64_t tpx_cnn_infer_work_bytes(int64_t n) { return n > 0 ? 256 : 0; }
 
 int tpx_cnn_infer(tpx_ctx *c, const void *d_packed, const uint16_t *d_x, int64_t n, void *d_work, float *d_out) {
-    if (!c || n < 0 || (n > 0 && (!d_packed || !d_x || !d_work || !d_out)) || n > (1LL << 30)) return TPX_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(d_packed) & 255) || (reinterpret_cast<uintptr_t>(d_x) & 15) ||
-        (reinterpret_cast<uintptr_t>(d_work) & 15))
-        return TPX_EINVAL;
+    if (!c || n < 0 || (n > 0 && (!d_packed || !d_x || !d_out)) || n > (1LL << 30)) return TPX_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_packed) & 255) || (reinterpret_cast<uintptr_t>(d_x) & 15)) return TPX_EINVAL;
+    (void)d_work;
     if (n == 0) return TPX_OK;
-    using Q = Packed;
     const __nv_bfloat16 *wt = static_cast<const __nv_bfloat16 *>(d_packed);
-    const float *bias = reinterpret_cast<const float *>(static_cast<const char *>(d_packed) + Q::boff);
-    __nv_bfloat16 *a1 = static_cast<__nv_bfloat16 *>(d_work);
-    __nv_bfloat16 *a2 = a1 + n * 49 * 16, *a3 = a2 + n * 25 * 16, *a4 = a3 + n * 9 * 32;
-    const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(d_x);
-    int rc;
-    if ((rc = launch_tc<2, 9, 16, 7, 3, 32, true, false, 16>(c, x, n * 49, wt + Q::w1, bias + Q::b1, a1))) return rc;
-    if ((rc = launch_tc<16, 7, 16, 5, 3, 144, false, false, 16>(c, a1, n * 25, wt + Q::w2, bias + Q::b2, a2))) return rc;
-    if ((rc = launch_tc<16, 5, 32, 3, 3, 144, false, false, 32>(c, a2, n * 9, wt + Q::w3, bias + Q::b3, a3))) return rc;
-    if ((rc = launch_tc<32, 3, 144, 1, 3, 288, false, false, 144>(c, a3, n, wt + Q::w4, bias + Q::b4, a4))) return rc;
-    return launch_tc<144, 1, 16, 1, 1, 144, false, true, NOUT>(c, a4, n, wt + Q::w5, bias + Q::b5, d_out);
+    const float *bias = reinterpret_cast<const float *>(static_cast<const char *>(d_packed) + Packed::boff);
+    return launch_fused_cnn(c, reinterpret_cast<const __nv_bfloat16 *>(d_x), n, wt, bias, d_out);
 }
 
 }  // extern "C"
