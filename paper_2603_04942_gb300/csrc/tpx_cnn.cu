@@ -366,7 +366,8 @@ constexpr size_t X_BYTES =
 constexpr size_t W1B = 16 * 32 * 2, W2B = 16 * 144 * 2, W3B = 32 * 144 * 2, W4B = 144 * 288 * 2, W5B = 16 * 144 * 2;
 constexpr size_t W_BYTES = W1B + W2B + W3B + W4B + W5B;
 constexpr size_t RAW_BYTES = (size_t)FP * 162 * 2;    // one group of bf16 patches
-constexpr size_t FUSED_SMEM = 1024 + W_BYTES + X_BYTES + 2 * RAW_BYTES + 64;
+constexpr size_t BIAS_BYTES = ((Packed::bend * 4 + 127) / 128) * 128;
+constexpr size_t FUSED_SMEM = 1024 + W_BYTES + X_BYTES + 2 * RAW_BYTES + BIAS_BYTES + 64;
 static_assert(T1 * 16 <= 512 && T2 * 16 <= 512 && T3 * 32 <= 512 && FP <= 128, "tensor memory of a group");
 static_assert(FUSED_SMEM <= 227 * 1024, "shared memory of the fused kernel");
 static_assert(RAW_BYTES % 16 == 0 && W_BYTES % 128 == 0, "16-byte copies");
@@ -402,8 +403,8 @@ __device__ __forceinline__ void relu_bf16x16(const uint32_t *v, const float *bia
     uint32_t pk[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const float a = fmaxf(__uint_as_float(v[2 * j]) + __ldg(bias + 2 * j), 0.f);
-        const float b = fmaxf(__uint_as_float(v[2 * j + 1]) + __ldg(bias + 2 * j + 1), 0.f);
+        const float a = fmaxf(__uint_as_float(v[2 * j]) + bias[2 * j], 0.f);
+        const float b = fmaxf(__uint_as_float(v[2 * j + 1]) + bias[2 * j + 1], 0.f);
         __nv_bfloat162 b2 = __floats2bfloat162_rn(a, b);
         pk[j] = *reinterpret_cast<uint32_t *>(&b2);
     }
@@ -446,7 +447,8 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
     unsigned char *W1 = base, *W2 = W1 + W1B, *W3 = W2 + W2B, *W4 = W3 + W3B, *W5 = W4 + W4B;
     unsigned char *X = W5 + W5B;
     unsigned char *RAW[2] = {X + X_BYTES, X + X_BYTES + RAW_BYTES};
-    uint64_t *bar = reinterpret_cast<uint64_t *>(X + X_BYTES + 2 * RAW_BYTES);
+    float *SB = reinterpret_cast<float *>(X + X_BYTES + 2 * RAW_BYTES);   // the biases
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + X_BYTES + 2 * RAW_BYTES + BIAS_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, sub = warp >> 2;   // accumulator lanes 32 * quad.., and which share of the columns
@@ -458,7 +460,8 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
     load_weights(W4, wt + Q::w4, 144, 288);
     load_weights(W5, wt + Q::w5, 16, 144);
     for (int i = tid; i < (int)(X_BYTES / 16); i += CNN_THREADS) reinterpret_cast<uint4 *>(X)[i] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) mbar_init(smem_u32(bar), 1);
+    for (int i = tid; i < (int)Q::bend; i += CNN_THREADS) SB[i] = bias[i];
+    if (tid == 0) mbar_init(smem_u32(bar), 4);   // four issuing threads commit per layer
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
@@ -477,14 +480,16 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
     bool failed = false;
 
     // the layer's A operand is in X: make it visible to the tensor cores, then
-    // one thread issues the MMAs and commits; everyone waits (bounded)
+    // lane 0 of warps 0-3 (one per scheduler) each issue a share of the MMAs
+    // and commit them to the barrier (four arrivals); everyone waits (bounded)
+    const int issuer = (lane == 0 && warp < 4) ? warp : -1;
     auto run_layer = [&](auto issue) -> bool {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (issuer >= 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            issue();
+            issue(issuer);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                          : "memory");
         }
@@ -525,15 +530,16 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
             }
         }
         // ---- conv1: 2 MMAs per tile (kernel rows 0-1, then row 2 and a zero chunk) ----
-        if (!run_layer([&] {
+        if (!run_layer([&](int q) {
                 // a descriptor's start field counts 16-byte units: one row, or
                 // 256 bytes = 16 for the next two k chunks of the weights
                 const uint32_t id = idesc_bf16(16);
                 const uint64_t da = sdesc(xs, 144, 128), db = sdesc(smem_u32(W1), 128, 512);
-                // the tiles' accumulators are independent: consecutive MMAs go to
-                // different tiles, so a tile's accumulation chain does not stall the pipe
-                for (int t = 0; t < T1; ++t) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128), db, id, false);
-                for (int t = 0; t < T1; ++t) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + 18), db + 16, id, true);
+                // issuer q takes tiles q, q + 4, ...; the tiles' accumulators are
+                // independent, so consecutive MMAs go to different tiles and a
+                // tile's accumulation chain does not stall the pipe
+                for (int t = q; t < T1; t += 4) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128), db, id, false);
+                for (int t = q; t < T1; t += 4) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + 18), db + 16, id, true);
             })) { failed = true; break; }
         // epilogue: the 7 x 7 window -> conv2 input planes; a warp takes two
         // tiles (32 accumulator columns) of its lane quadrant per load
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 const int pp = r / 81, pos = r % 81, yy = pos / 9, xx = pos % 9;
                 if (t < T1 && pp < FP && yy < 7 && xx < 7) {
                     uint4 lo, hi;
-                    relu_bf16x16(v + 16 * u, bias + Q::b1, &lo, &hi);
+                    relu_bf16x16(v + 16 * u, SB + Q::b1, &lo, &hi);
                     const int o = pp * 49 + yy * 7 + xx;
                     reinterpret_cast<uint4 *>(X)[o] = lo;
                     reinterpret_cast<uint4 *>(X + (size_t)P1_ROWS * 16)[o] = hi;
@@ -556,12 +562,12 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
             }
         }
         // ---- conv2: one MMA per tap (16 channels = the two planes) ----
-        if (!run_layer([&] {
+        if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(16);
                 const uint64_t da = sdesc(xs, P1_ROWS * 16, 128), db = sdesc(smem_u32(W2), 128, 18 * 128);
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
-                    for (int t = 0; t < T2; ++t)
+                    for (int t = q; t < T2; t += 4)
                         mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + (k / 3) * 7 + k % 3), db + 16 * k, id, k > 0);
             })) { failed = true; break; }
         for (int t0 = 2 * sub; t0 < T2; t0 += 8) {
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 const int pp = r / 49, pos = r % 49, yy = pos / 7, xx = pos % 7;
                 if (t < T2 && pp < FP && yy < 5 && xx < 5) {
                     uint4 lo, hi;
-                    relu_bf16x16(v + 16 * u, bias + Q::b2, &lo, &hi);
+                    relu_bf16x16(v + 16 * u, SB + Q::b2, &lo, &hi);
                     const int o = pp * 25 + yy * 5 + xx;
                     reinterpret_cast<uint4 *>(X)[o] = lo;
                     reinterpret_cast<uint4 *>(X + (size_t)P2_ROWS * 16)[o] = hi;
@@ -583,12 +589,12 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
             }
         }
         // ---- conv3 ----
-        if (!run_layer([&] {
+        if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(32);
                 const uint64_t da = sdesc(xs, P2_ROWS * 16, 128), db = sdesc(smem_u32(W3), 128, 18 * 128);
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
-                    for (int t = 0; t < T3; ++t)
+                    for (int t = q; t < T3; t += 4)
                         mma_bf16(tmem + 32 * t, da + (uint64_t)(t * 128 + (k / 3) * 5 + k % 3), db + 16 * k, id, k > 0);
             })) { failed = true; break; }
         // epilogue: the 3 x 3 window -> fc1 input, one row per patch, plane (pos * 4 + channel / 8)
@@ -600,8 +606,8 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
             const int pp = r / 25, pos = r % 25, yy = pos / 5, xx = pos % 5;
             if (pp < FP && yy < 3 && xx < 3) {
                 uint4 a0, a1, a2, a3;
-                relu_bf16x16(v, bias + Q::b3, &a0, &a1);
-                relu_bf16x16(v + 16, bias + Q::b3 + 16, &a2, &a3);
+                relu_bf16x16(v, SB + Q::b3, &a0, &a1);
+                relu_bf16x16(v + 16, SB + Q::b3 + 16, &a2, &a3);
                 const int j = (yy * 3 + xx) * 4;
                 *reinterpret_cast<uint4 *>(X + (size_t)(j + 0) * PLB + 16 * pp) = a0;
                 *reinterpret_cast<uint4 *>(X + (size_t)(j + 1) * PLB + 16 * pp) = a1;
@@ -610,14 +616,16 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
             }
         }
         // ---- fc1: 18 MMAs over K = 288 (rows past the group's patches are dropped) ----
-        if (!run_layer([&] {
+        if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(144);
                 const uint64_t da = sdesc(xs, PLB, 128), db = sdesc(smem_u32(W4), 128, 36 * 128);
                 // three accumulators (columns 0, 160, 320) over interleaved k
-                // steps, summed in the epilogue: three short chains, not one long
+                // steps, summed in the epilogue: three short chains, one per
+                // issuer (the fourth issues nothing)
+                if (q < 3)
 #pragma unroll
-                for (int k = 0; k < 18; ++k)
-                    mma_bf16(tmem + 160 * (k % 3), da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
+                    for (int k = q; k < 18; k += 3)
+                        mma_bf16(tmem + 160 * q, da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
             })) { failed = true; break; }
         {
             const int pp = 32 * quad + lane;
@@ -636,7 +644,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                     const int c = c0 + 16 * h;
                     if (c < 144 && pp < FP) {
                         uint4 lo, hi;
-                        relu_bf16x16(v + 16 * h, bias + Q::b4 + c, &lo, &hi);
+                        relu_bf16x16(v + 16 * h, SB + Q::b4 + c, &lo, &hi);
                         *reinterpret_cast<uint4 *>(X + (size_t)(c / 8) * PLB + 16 * pp) = lo;
                         *reinterpret_cast<uint4 *>(X + (size_t)(c / 8 + 1) * PLB + 16 * pp) = hi;
                     }
@@ -644,12 +652,13 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
             }
         }
         // ---- fc2: 9 MMAs over K = 144, fp32 outputs ----
-        if (!run_layer([&] {
+        if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(16);
                 const uint64_t da = sdesc(xs, PLB, 128), db = sdesc(smem_u32(W5), 128, 18 * 128);
+                if (q < 3)
 #pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    mma_bf16(tmem + 16 * (k % 3), da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
+                    for (int k = q; k < 9; k += 3)
+                        mma_bf16(tmem + 16 * q, da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
             })) { failed = true; break; }
         if (sub == 0) {
             uint32_t v[32], u[16];
@@ -661,7 +670,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
 #pragma unroll
                 for (int j = 0; j < NOUT; ++j)
                     out[row * NOUT + j] = __uint_as_float(v[j]) + __uint_as_float(v[16 + j]) + __uint_as_float(u[j]) +
-                                          __ldg(bias + Q::b5 + j);
+                                          SB[Q::b5 + j];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
