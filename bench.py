@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--phase-shares", type=int, default=0, metavar="SHOTS",
                     help="per-phase cycle shares of the fused kernel (instrumented build) on SHOTS shots of the "
                          "large recipe, --tile geometry (2048 when default)")
+    ap.add_argument("--cnn-phase-shares", type=int, default=0, metavar="N",
+                    help="per-phase cycle shares of the CNN inference kernel (instrumented build) on N patches")
     ap.add_argument("--cnn-infer-only", type=int, default=0, metavar="N",
                     help="time only the CNN refiner's tcgen05 inference on N random bf16 patches (random weights)")
     ap.add_argument("--batch-runs", type=int, default=4096)
@@ -574,7 +576,7 @@ def phase_bench(shots: int, tile: str) -> dict:
 CNN_FLOPS_PER_PATCH = 2 * (49 * 18 * 16 + 25 * 144 * 16 + 9 * 144 * 32 + 288 * 144 + 144 * 6)
 
 
-def cnn_infer_bench(n: int, steps: int, warmup: int) -> dict:
+def cnn_infer_bench(n: int, steps: int, warmup: int, phases: bool = False) -> dict:
     """The CNN refiner's inference alone: n patches of bf16 values in [0, 2),
     weights N(0, 0.1), both seeded; `steps` timed calls after `warmup`."""
     import numpy as np
@@ -592,6 +594,8 @@ def cnn_infer_bench(n: int, steps: int, warmup: int) -> dict:
     for _ in range(max(1, warmup)):
         ctx.tpx_cnn_infer(packed, x, n, work=work, out=out)
     torch.cuda.synchronize()
+    if phases:
+        tpx.cnn_phase_times(clear=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
     for _ in range(steps):
@@ -601,6 +605,11 @@ def cnn_infer_bench(n: int, steps: int, warmup: int) -> dict:
     ms = e0.elapsed_time(e1) / steps
     rc, _ = ctx.tpx_sync(check=False)
     ctx.close()
+    if phases:
+        cyc = tpx.cnn_phase_times(clear=True).astype(np.float64)
+        return {"metric": "CNN inference phase shares (thread 0 cycles per CTA)", "patches": n,
+                "shares": {nm: round(float(c / cyc.sum()), 4) for nm, c in zip(tpx.CNN_PHASE_NAMES, cyc)},
+                "cycles_per_group": float(cyc.sum() / ((n + 47) // 48) / steps), "status": rc}
     return {"metric": "CNN refiner inference", "patches": n, "ms_per_call": ms, "patches_per_s": n / (ms / 1e3),
             "tflops": CNN_FLOPS_PER_PATCH * n / (ms / 1e3) / 1e12, "status": rc, "steps": steps, "warmup": warmup}
 
@@ -797,6 +806,15 @@ def main():
         import paper_2603_04942_gb300 as tpx
         tpx.load(tbuild.build(phases=True))
         print(json.dumps(phase_bench(args.phase_shares, args.tile)), flush=True)
+        return 0
+    if args.cnn_phase_shares:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2603_04942_gb300 import build as tbuild
+        import paper_2603_04942_gb300 as tpx
+        tpx.load(tbuild.build(phases=True))
+        res = cnn_infer_bench(args.cnn_phase_shares, 1, max(1, args.warmup), phases=True)
+        print(json.dumps(res), flush=True)
         return 0
     if args.cnn_infer_only:
         import torch

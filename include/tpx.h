@@ -472,6 +472,15 @@ int tpx_cnn_train_step(tpx_ctx *ctx, float *d_params, float *d_adam_m, float *d_
 int64_t tpx_cnn_packed_bytes(void);
 int tpx_cnn_pack(tpx_ctx *ctx, const float *d_params, void *d_packed);
 int64_t tpx_cnn_infer_work_bytes(int64_t n);
+/* Per-phase cycle counters of tpx_cnn_infer's kernel in the instrumented
+   build (libtpx_phases.so, -DTPX_PHASE_TIMING): thread 0 of each CTA adds
+   the clock64 cycles of each phase of each group of patches.  Synchronises
+   the device, copies the 16 counters to h_cycles[16] (zeroing them when
+   `clear` is nonzero).  Phases: 0 wait for the group's patches, 1 their
+   conversion into the conv1 input map, then MMAs and epilogue of conv1 (2,
+   3), conv2 (4, 5), conv3 (6, 7), fc1 (8, 9), fc2 (10, 11).  The normal
+   build returns TPX_EUNSUPPORTED (zeros); TPX_EINVAL for a NULL pointer. */
+int tpx_debug_cnn_phase_times(uint64_t *h_cycles, int clear);
 int tpx_cnn_infer(tpx_ctx *ctx, const void *d_packed, const uint16_t *d_x, int64_t n, void *d_work, float *d_out);
 
 /* tpx_refine_patches writing the patches as bf16 [capacity x 162] (the patch

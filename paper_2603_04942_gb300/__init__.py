@@ -47,7 +47,7 @@ EXPORTED_SYMBOLS = ("tpx_config_default", "tpx_create", "tpx_reserve", "tpx_dest
                     "tpx_stream_submit", "tpx_stream_finish", "tpx_stream_poll", "tpx_stream_destroy",
                     "tpx_stream_snapshot_bytes", "tpx_stream_snapshot", "tpx_stream_restore",
                     "tpx_cnn_params", "tpx_cnn_work_floats", "tpx_cnn_forward", "tpx_cnn_train_step",
-                    "tpx_cnn_packed_bytes", "tpx_cnn_pack", "tpx_cnn_infer_work_bytes", "tpx_cnn_infer",
+                    "tpx_cnn_packed_bytes", "tpx_cnn_pack", "tpx_cnn_infer_work_bytes", "tpx_cnn_infer", "tpx_debug_cnn_phase_times",
                     "tpx_refine_patches_bf16", "tpx_strerror", "tpx_version")
 
 
@@ -147,6 +147,8 @@ def load(path: str | None = None):
         L.tpx_kernel_timing.argtypes = [vp, i32]
         L.tpx_debug_phase_times.argtypes = [i32, ctypes.POINTER(ctypes.c_uint64), i32]
         L.tpx_debug_phase_times.restype = i32
+        L.tpx_debug_cnn_phase_times.argtypes = [ctypes.POINTER(ctypes.c_uint64), i32]
+        L.tpx_debug_cnn_phase_times.restype = i32
         L.tpx_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]
         L.tpx_strerror.argtypes = [i32]
@@ -223,6 +225,20 @@ PHASE_NAMES = ("tile start", "tile load", "look-ahead", "walk 2 and its scan", "
                "walk 4 (records)", "hash insert", "neighbour pass", "compression", "unions", "roots",
                "member lists", "member-list walks (and the previous tile's copy-out)",
                "label ranks and staged stores", "labels and offsets", "tail", "CTA end")
+
+
+CNN_PHASE_NAMES = ("wait for the patches", "conversion to the conv1 map", "conv1 MMAs", "conv1 epilogue",
+                   "conv2 MMAs", "conv2 epilogue", "conv3 MMAs", "conv3 epilogue", "fc1 MMAs", "fc1 epilogue",
+                   "fc2 MMAs", "fc2 epilogue")
+
+
+def cnn_phase_times(clear: bool = True) -> np.ndarray:
+    """The CNN inference kernel's per-phase cycle counters (instrumented build only)."""
+    arr = (ctypes.c_uint64 * 16)()
+    rc = lib().tpx_debug_cnn_phase_times(arr, 1 if clear else 0)
+    if rc:
+        raise TpxError(rc, "tpx_debug_cnn_phase_times")
+    return np.array(arr[:len(CNN_PHASE_NAMES)], dtype=np.uint64)
 
 
 def phase_times(tile_geometry: int, clear: bool = True) -> np.ndarray:

@@ -437,6 +437,21 @@ __device__ __forceinline__ void load_group(unsigned char *raw, const __nv_bfloat
 
 constexpr int CNN_THREADS = 512;   // 16 warps: four per tensor-memory lane quadrant
 
+// Phase timing (-DTPX_PHASE_TIMING, the libtpx_phases.so build): thread 0 of
+// every CTA adds the clock64 cycles since its previous mark to the phase's
+// counter (read with tpx_debug_cnn_phase_times); compiled away otherwise.
+#ifdef TPX_PHASE_TIMING
+__device__ unsigned long long g_cnn_phase[16];
+#define CNN_PH(k)                                                                                       \
+    do {                                                                                                \
+        const long long ph_now = clock64();                                                             \
+        if (threadIdx.x == 0) atomicAdd(&g_cnn_phase[k], (unsigned long long)(ph_now - ph_t));           \
+        ph_t = ph_now;                                                                                  \
+    } while (0)
+#else
+#define CNN_PH(k) do {} while (0)
+#endif
+
 __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat16 *__restrict__ x, long long n,
                                                       const __nv_bfloat16 *__restrict__ wt,
                                                       const float *__restrict__ bias, float *__restrict__ out,
@@ -478,6 +493,9 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
     const uint32_t lane_off = (uint32_t)(32 * quad) << 16;   // this warp's accumulator lanes
     uint32_t phase = 0;
     bool failed = false;
+#ifdef TPX_PHASE_TIMING
+    long long ph_t = clock64();
+#endif
 
     // the layer's A operand is in X: make it visible to the tensor cores, then
     // lane 0 of warps 0-3 (one per scheduler) each issue a share of the MMAs
@@ -508,6 +526,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
         unsigned char *raw = RAW[it & 1];
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
+        CNN_PH(0);
         // the next group's patches come in while this one runs
         if (g + gridDim.x < groups) load_group(RAW[(it + 1) & 1], x, n, g + gridDim.x);
         // ---- conv1 input map: row (patch, y * 9 + x) = [c0, c1] at x, x + 1, x + 2, 0, 0 ----
@@ -529,6 +548,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 reinterpret_cast<uint4 *>(X)[r] = row;
             }
         }
+        CNN_PH(1);
         // ---- conv1: 2 MMAs per tile (kernel rows 0-1, then row 2 and a zero chunk) ----
         if (!run_layer([&](int q) {
                 // a descriptor's start field counts 16-byte units: one row, or
@@ -541,6 +561,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 for (int t = q; t < T1; t += 4) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128), db, id, false);
                 for (int t = q; t < T1; t += 4) mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + 18), db + 16, id, true);
             })) { failed = true; break; }
+        CNN_PH(2);
         // epilogue: the 7 x 7 window -> conv2 input planes; a warp takes two
         // tiles (32 accumulator columns) of its lane quadrant per load
         for (int t0 = 2 * sub; t0 < T1; t0 += 8) {
@@ -561,6 +582,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 }
             }
         }
+        CNN_PH(3);
         // ---- conv2: one MMA per tap (16 channels = the two planes) ----
         if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(16);
@@ -570,6 +592,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                     for (int t = q; t < T2; t += 4)
                         mma_bf16(tmem + 16 * t, da + (uint64_t)(t * 128 + (k / 3) * 7 + k % 3), db + 16 * k, id, k > 0);
             })) { failed = true; break; }
+        CNN_PH(4);
         for (int t0 = 2 * sub; t0 < T2; t0 += 8) {
             uint32_t v[32];
             tmem_ld32_nowait(tmem + lane_off + 16 * t0, v);
@@ -588,6 +611,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 }
             }
         }
+        CNN_PH(5);
         // ---- conv3 ----
         if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(32);
@@ -597,6 +621,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                     for (int t = q; t < T3; t += 4)
                         mma_bf16(tmem + 32 * t, da + (uint64_t)(t * 128 + (k / 3) * 5 + k % 3), db + 16 * k, id, k > 0);
             })) { failed = true; break; }
+        CNN_PH(6);
         // epilogue: the 3 x 3 window -> fc1 input, one row per patch, plane (pos * 4 + channel / 8)
         for (int t = sub; t < T3; t += 4) {
             uint32_t v[32];
@@ -615,6 +640,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 *reinterpret_cast<uint4 *>(X + (size_t)(j + 3) * PLB + 16 * pp) = a3;
             }
         }
+        CNN_PH(7);
         // ---- fc1: 18 MMAs over K = 288 (rows past the group's patches are dropped) ----
         if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(144);
@@ -627,6 +653,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                     for (int k = q; k < 18; k += 3)
                         mma_bf16(tmem + 160 * q, da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
             })) { failed = true; break; }
+        CNN_PH(8);
         {
             const int pp = 32 * quad + lane;
 #pragma unroll 1
@@ -651,6 +678,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                 }
             }
         }
+        CNN_PH(9);
         // ---- fc2: 9 MMAs over K = 144, fp32 outputs ----
         if (!run_layer([&](int q) {
                 const uint32_t id = idesc_bf16(16);
@@ -660,6 +688,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                     for (int k = q; k < 9; k += 3)
                         mma_bf16(tmem + 16 * q, da + (uint64_t)(2 * k * (PLB / 16)), db + 16 * k, id, k >= 3);
             })) { failed = true; break; }
+        CNN_PH(10);
         if (sub == 0) {
             uint32_t v[32], u[16];
             tmem_ld32_nowait(tmem + lane_off, v);        // accumulators 0 and 1
@@ -673,6 +702,7 @@ __global__ void __launch_bounds__(CNN_THREADS, 1) k_cnn_fused(const __nv_bfloat1
                                           SB[Q::b5 + j];
             }
         }
+        CNN_PH(11);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     if (failed && tid == 0) atomicOr(status, tpxk::ST_DEVTIMEOUT);
@@ -754,6 +784,23 @@ int tpx_cnn_pack(tpx_ctx *c, const float *d_params, void *d_packed) {
 }
 
 int64_t tpx_cnn_infer_work_bytes(int64_t n) { return n > 0 ? 256 : 0; }
+
+int tpx_debug_cnn_phase_times(uint64_t *h_cycles, int clear) {
+    if (!h_cycles) return TPX_EINVAL;
+#ifdef TPX_PHASE_TIMING
+    if (cudaDeviceSynchronize() != cudaSuccess) return TPX_ECUDA;
+    cudaError_t e = cudaMemcpyFromSymbol(h_cycles, g_cnn_phase, 16 * 8);
+    if (e == cudaSuccess && clear) {
+        static const unsigned long long zero[16] = {0};
+        e = cudaMemcpyToSymbol(g_cnn_phase, zero, 16 * 8);
+    }
+    return e == cudaSuccess ? TPX_OK : TPX_ECUDA;
+#else
+    (void)clear;
+    for (int i = 0; i < 16; ++i) h_cycles[i] = 0;
+    return TPX_EUNSUPPORTED;
+#endif
+}
 
 int tpx_cnn_infer(tpx_ctx *c, const void *d_packed, const uint16_t *d_x, int64_t n, void *d_work, float *d_out) {
     if (!c || n < 0 || (n > 0 && (!d_packed || !d_x || !d_out)) || n > (1LL << 30)) return TPX_EINVAL;

@@ -77,6 +77,7 @@ struct tpx_ctx {
     tpxk::GAgg *d_state;      // [2]
     int cur;                  // d_state[cur]: state for the next call
     bool state_once;          // tpx_set_state was called for the next call
+    bool packets_on_host;     // the next calls read mapped host packets (no L2 prefetch of them)
     bool lab32_outer;         // int32 labels of the next calls are relative to lab32_base
     int64_t lab32_base;       // (the pieces of one pipelined host call), not to their own base
     tpxk::GAgg h_state;       // host staging for tpx_set_state / tpx_get_state

@@ -95,6 +95,7 @@ struct Params {
     long long idx_base;
     long long *labels;
     int *labels32;            // TPX_FLAG_LABELS32: labels minus lab32_base, as int32 (labels NULL)
+    int l2_prefetch;          // the packets are in device memory: prefetch the next tile into L2
     long long lab32_base;
     uint8_t *is_peak;
     tpx_record *clusters;

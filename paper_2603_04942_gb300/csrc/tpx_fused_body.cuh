@@ -531,7 +531,19 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         const long long tile = S.tile;
         // the next tile is claimed now; its number is needed only at the end
         unsigned long long claim = 0;
-        if (tid == 0 && tile < p.n_tiles) claim = atomicAdd(&p.ctl->tile_counter, 1u);
+        if (tid == 0 && tile < p.n_tiles) {
+            claim = atomicAdd(&p.ctl->tile_counter, 1u);
+            // the claimed tile's packets (and its look-ahead window) start
+            // moving into L2 now, a tile ahead of their loads (one bulk
+            // prefetch; the start is 16-byte aligned, the size a multiple of 16)
+            if (!BATCH && p.l2_prefetch && claim < (unsigned long long)p.n_tiles) {
+                const long long b = (long long)claim * T;
+                const long long m = min((long long)(T + LA0), p.n - b) & ~1LL;
+                if (m > 0)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p.pk + b), "r"((unsigned)(8 * m))
+                                 : "memory");
+            }
+        }
         if (tile >= p.n_tiles) {
             if (STAGED) {
                 if (tid < 32) flush_pending_warp<BATCH>(S, p, seq);

@@ -97,17 +97,27 @@ __global__ void __launch_bounds__(AW * 32) k_tile_aggs(const Params p, int T) {
         WarpChain cp{0, 0, 0, 0, false}, ct{0, 0, 0, 0, false};
         const uint64_t *src = p.pk + sp.base;
         const bool vec = (sp.base & 1) == 0;
-        for (int q0 = 0; q0 < sp.cnt; q0 += 64) {
+        // the lane's two packets of step q0 (zero past the tile)
+        auto load2 = [&](int q0, uint64_t &a, uint64_t &b) {
             const int q = q0 + 2 * lane;
-            uint64_t w0 = 0, w1 = 0;
+            a = 0;
+            b = 0;
             if (vec && q + 1 < sp.cnt) {
                 const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(src + q));
-                w0 = v.x;
-                w1 = v.y;
+                a = v.x;
+                b = v.y;
             } else {
-                if (q < sp.cnt) w0 = __ldcs(src + q);
-                if (q + 1 < sp.cnt) w1 = __ldcs(src + q + 1);
+                if (q < sp.cnt) a = __ldcs(src + q);
+                if (q + 1 < sp.cnt) b = __ldcs(src + q + 1);
             }
+        };
+        // one step ahead: the next 64 packets are in flight while these are combined
+        uint64_t nx0, nx1;
+        load2(0, nx0, nx1);
+        for (int q0 = 0; q0 < sp.cnt; q0 += 64) {
+            const int q = q0 + 2 * lane;
+            const uint64_t w0 = nx0, w1 = nx1;
+            if (q0 + 64 < sp.cnt) load2(q0 + 64, nx0, nx1);
             const bool in0 = q < sp.cnt, in1 = q + 1 < sp.cnt;
             const unsigned h0 = (unsigned)(w0 >> 60), h1 = (unsigned)(w1 >> 60);
             const bool p0 = in0 && h0 == 0xBu, p1 = in1 && h1 == 0xBu;

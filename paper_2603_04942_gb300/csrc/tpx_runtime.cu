@@ -143,6 +143,18 @@ int tune_pick(const tpx_ctx *c, int64_t n) {
     return c->tune.issued[tpxk::GEO_T2048 - 1] <= c->tune.issued[tpxk::GEO_T4096 - 1] ? tpxk::GEO_T2048 : tpxk::GEO_T4096;
 }
 
+// device memory (not mapped host or managed memory): the fused kernel may
+// prefetch such packets into L2 with the bulk-copy engine
+bool device_memory(const void *ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice;
+}
+
 // kernel timing: add the oldest recorded launch's pre-pass and fused-kernel
 // times to the sums (waits for it)
 int ktime_collect_one(tpx_ctx *c) {
@@ -391,6 +403,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.labels = l32 ? nullptr : reinterpret_cast<long long *>(d_labels);
     p.labels32 = l32 ? reinterpret_cast<int *>(d_labels) : nullptr;
     p.lab32_base = l32_base;
+    p.l2_prefetch = (!c->packets_on_host && device_memory(d_packets)) ? 1 : 0;
     p.is_peak = d_is_peak;
     p.clusters = d_clusters;
     p.cl_cap = cl_cap;
@@ -932,8 +945,10 @@ static int process_host_direct(tpx_ctx *c, const uint64_t *h_packets, int64_t n,
         return 1;
     int rc = grow(&c->st_counts, &c->st_counts_cap, 2);
     if (rc) return rc;
+    c->packets_on_host = true;
     rc = tpx_process(c, h_packets, n, idx_base, h_labels, h_is_peak, h_clusters, cl_cap, c->st_counts, h_trig, trig_cap,
                      c->st_counts + 1);
+    c->packets_on_host = false;
     if (rc) return rc;
     rc = tpx_sync(c, nullptr);
     int64_t cnt[2] = {0, 0};

@@ -63,6 +63,10 @@ def test_phase_counters_and_flags_without_a_gpu(libpath):
     assert L.tpx_debug_phase_times(tpx.TILE_2048, arr, 0) == tpx.EUNSUPPORTED
     assert list(arr) == [0] * 32
     assert L.tpx_debug_phase_times(5, arr, 0) == tpx.EINVAL
+    arr16 = (ctypes.c_uint64 * 16)(*([7] * 16))
+    assert L.tpx_debug_cnn_phase_times(arr16, 0) == tpx.EUNSUPPORTED
+    assert list(arr16) == [0] * 16
+    assert L.tpx_debug_cnn_phase_times(None, 0) == tpx.EINVAL
     assert L.tpx_kernel_timing(None, 1) == tpx.EINVAL
     assert L.tpx_kernel_times(None, None, None, None) == tpx.EINVAL
     # the configuration accepts the two flags and nothing else

@@ -56,6 +56,37 @@ def test_stream_small_config_in_random_chunks():
     assert all(b >= a for a, b in zip(first, first[1:]))
 
 
+def test_stream_several_chunks_in_flight_equal_the_oracle():
+    """Up to `slots` chunks are submitted before any result is polled; each
+    ticket's records come back in submission order and their union is the
+    oracle's result over the whole stream."""
+    pk = synth.generate(synth.small(n_shots=400, pair_frac=0.05))[0]
+    whole = oracle_run(pk)
+    rng = np.random.default_rng(7)
+    sizes = chunks_for(pk.size, rng, 1, 20_000)
+    st = tpx.Stream(tpx.Config(), max_chunk_packets=max(sizes), max_hold_packets=1 << 20, hold_triggers=2, slots=4)
+    try:
+        recs, trig, pos, i = [], [], 0, 0
+        while i < len(sizes):
+            tickets = []
+            for c in sizes[i:i + 4]:
+                tickets.append(st.submit(pk[pos:pos + c]))
+                pos += c
+            i += len(tickets)
+            for t in tickets:
+                r = st.poll(t)
+                assert r["status"] == 0
+                recs.append(r["clusters"])
+                trig.append(r["triggers"])
+        r = st.poll(st.finish())
+        recs.append(r["clusters"])
+        trig.append(r["triggers"])
+    finally:
+        st.close()
+    assert np.array_equal(np.concatenate(trig), whole["triggers"])
+    assert_clusters_equal(np.concatenate(recs), whole["clusters"])
+
+
 def test_stream_high_rate_full_period():
     """10 Mhit/s ion-like stream, ToF cut = the whole period: shots hold ~10k
     pixels and their late pixels follow the next trigger packet."""
