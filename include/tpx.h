@@ -610,16 +610,25 @@ typedef struct tpx_stream_result {
    Errors: TPX_EINVAL, TPX_ENOMEM, TPX_EAGAIN (budget). */
 int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda_stream);
 
-/* Submit a chunk (host memory; pinned for best latency).  Returns a ticket.
-   TPX_EAGAIN when every slot holds results not yet polled (admission);
-   TPX_EINVAL when n_packets exceeds max_chunk_packets. */
+/* Submit a chunk (host memory; pinned for best latency).  Returns a ticket at
+   once: the chunk is queued in a free result slot and the stream's worker
+   thread processes the queued chunks in order, so up to `slots` chunks are in
+   flight.  The chunk's memory must stay valid and unchanged until its ticket
+   has been polled.  TPX_EAGAIN when every slot holds a chunk not yet polled
+   (admission); TPX_EINVAL when n_packets exceeds max_chunk_packets or after
+   tpx_stream_finish.  Errors of the processing itself (TPX_EOVERFLOW when
+   the open shots outgrow max_hold_packets, TPX_ECORRUPT for decreasing
+   trigger times, TPX_ECUDA) are returned by the ticket's poll. */
 int tpx_stream_submit(tpx_stream *st, const uint64_t *h_chunk, int64_t n_packets, uint64_t *ticket);
 
 /* End of the stream: emit every held shot (returns a ticket like submit). */
 int tpx_stream_finish(tpx_stream *st, uint64_t *ticket);
 
 /* Wait up to timeout_us (negative: forever) for a ticket's results.
-   TPX_ETIMEOUT if not ready in time, TPX_EINVAL for an unknown ticket. */
+   TPX_ETIMEOUT if not ready in time, TPX_EINVAL for an unknown ticket; the
+   processing error of a failed chunk (its slot is freed).  The result's
+   buffers belong to the slot and stay valid until the slot is reused by a
+   later submit. */
 int tpx_stream_poll(tpx_stream *st, uint64_t ticket, tpx_stream_result *out, int32_t timeout_us);
 
 int tpx_stream_destroy(tpx_stream *st);

@@ -686,14 +686,17 @@ class Stream:
             raise TpxError(rc, "tpx_stream_create")
         self._h = h
         self._keep = cfg
+        self._chunks = {}   # ticket -> chunk: the library reads it until the ticket is polled
 
     def submit(self, chunk: np.ndarray) -> int:
-        """Returns the ticket; raises TpxError (EAGAIN when all slots await poll)."""
+        """Queue a chunk; returns the ticket at once (raises TpxError, EAGAIN
+        when all slots await poll). The chunk is held until its poll."""
         chunk = np.ascontiguousarray(chunk, dtype=np.uint64)
         t = ctypes.c_uint64()
         rc = lib().tpx_stream_submit(self._h, chunk.ctypes.data if chunk.size else None, chunk.size, ctypes.byref(t))
         if rc:
             raise TpxError(rc, "tpx_stream_submit")
+        self._chunks[t.value] = chunk
         return t.value
 
     def finish(self) -> int:
@@ -706,6 +709,8 @@ class Stream:
     def poll(self, ticket: int, timeout_us: int = -1) -> dict:
         r = _CStreamResult()
         rc = lib().tpx_stream_poll(self._h, ticket, ctypes.byref(r), int(timeout_us))
+        if rc != ETIMEOUT:
+            self._chunks.pop(ticket, None)
         if rc:
             raise TpxError(rc, "tpx_stream_poll")
         n = r.n_clusters
@@ -737,8 +742,9 @@ class Stream:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().tpx_stream_destroy(self._h)
+            lib().tpx_stream_destroy(self._h)   # processes what is queued first
             self._h = None
+        self._chunks = {}
 
     def __del__(self):
         try:

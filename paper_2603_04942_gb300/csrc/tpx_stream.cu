@@ -1,25 +1,31 @@
 // tpx_stream.cu -- streaming: acquisition chunks in, closed shots' records out.
 //
-// Per submit: the held (open) packets plus the new chunk are decoded by the
-// general path starting from the unwrap state at the held part's start
-// (device-resident); the hits are sorted and clustered, and records are
-// written for the shots that closed (all but the last `hold_triggers`); the
-// unwrap state at the first open shot's trigger packet is computed on the
-// device and the open part is moved to the front of the other pending buffer
-// for the next chunk.  Two host round trips per submit: one for the counts
-// after decoding, one for the record count.  Independent streams run on
-// their own CUDA streams, so chunks of different acquisitions overlap on the
-// GPU.
+// A submit takes a free result slot and queues the chunk; it returns at once.
+// The stream's worker thread processes the queued chunks in order: the held
+// (open) packets plus the chunk are decoded by the general path starting from
+// the unwrap state at the held part's start (device-resident); the hits are
+// sorted and clustered, and records are written for the shots that closed
+// (all but the last `hold_triggers`); the unwrap state at the first open
+// shot's trigger packet is computed on the device and the open part is moved
+// to the front of the other pending buffer for the next chunk. Two host
+// round trips per chunk inside the worker: one for the counts after decoding,
+// one for the record count. A poll waits for its chunk's slot. Independent
+// streams run on their own CUDA streams and workers, so chunks of different
+// acquisitions overlap on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "tpx.h"
@@ -44,7 +50,9 @@ std::mutex g_budget_mu;
 int64_t g_budget_used = 0;
 
 struct Slot {
-    bool busy = false;
+    bool busy = false;              // holds a queued, running or unpolled chunk
+    bool ready = false;             // the worker is done with it (status in rc)
+    int rc = 0;
     uint64_t ticket = 0;
     cudaEvent_t done = nullptr;
     tpx_record *h_cl = nullptr;
@@ -54,6 +62,13 @@ struct Slot {
     int64_t n_cl = 0, first_shot = 0, n_shots = 0, processed = 0;
     int32_t status = 0;
     Clock::time_point t_submit;
+};
+
+struct Job {                        // a queued submit or finish
+    Slot *sl;
+    const uint64_t *h;
+    int64_t n;
+    bool finishing;
 };
 
 struct Probe {                      // k_state_at scratch
@@ -84,6 +99,18 @@ struct tpx_stream {
     uint64_t next_ticket = 1;
     int64_t bytes = 0;
     bool finished = false;
+    // the worker: queued chunks, processed in order on the stream's CUDA stream
+    int device = 0;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;     // a job was queued, a job finished, or stop
+    std::deque<Job> q;
+    bool busy_worker = false;       // processing a job now
+    bool stop = false;
+    // the same facts without the lock, for the short spins that keep a
+    // thread wake-up out of a chunk's latency
+    std::atomic<int> queued{0};
+    std::atomic<uint64_t> done_ticket_max{0};   // tickets complete in order: every one up to this
 };
 
 namespace tpxs {
@@ -175,12 +202,8 @@ int grow_pinned(Slot &sl, int64_t ncl, int64_t ntr) {
     return TPX_OK;
 }
 
-int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, uint64_t *ticket) {
-    Slot *sl = nullptr;
-    for (auto &x : S->slots)
-        if (!x.busy) { sl = &x; break; }
-    if (!sl) return TPX_EAGAIN;
-    const auto t0 = Clock::now();
+// one chunk, in the worker thread (the slot and ticket were taken at submit)
+int process_job(tpx_stream *S, Slot *sl, const uint64_t *h_chunk, int64_t n, bool finishing) {
     cudaStream_t s = S->s;
     tpx_ctx *c = S->ctx;
     int rc = TPX_OK;
@@ -251,12 +274,66 @@ int process(tpx_stream *S, const uint64_t *h_chunk, int64_t n, bool finishing, u
     sl->n_cl = n_cl;
     sl->processed = P;
     sl->status = 0;
-    sl->t_submit = t0;
-    sl->ticket = S->next_ticket++;
-    sl->busy = true;
     if (cks(cudaEventRecord(sl->done, s))) return TPX_ECUDA;
-    *ticket = sl->ticket;
     return TPX_OK;
+}
+
+// spins before sleeping: about 0.2 ms of polling, then the condition variable
+constexpr auto kSpinFor = std::chrono::microseconds(200);
+
+void worker_loop(tpx_stream *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        Job j;
+        {
+            const auto t0 = Clock::now();
+            while (S->queued.load(std::memory_order_acquire) == 0 && Clock::now() - t0 < kSpinFor)
+                std::this_thread::yield();
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->stop || !S->q.empty(); });
+            if (S->q.empty()) return;   // stop, nothing left
+            j = S->q.front();
+            S->q.pop_front();
+            S->queued.fetch_sub(1, std::memory_order_acq_rel);
+            S->busy_worker = true;
+        }
+        const int rc = process_job(S, j.sl, j.h, j.n, j.finishing);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            j.sl->rc = rc;
+            j.sl->ready = true;
+            S->busy_worker = false;
+            S->done_ticket_max.store(j.sl->ticket, std::memory_order_release);
+        }
+        S->cv.notify_all();
+    }
+}
+
+// queue a chunk (or the finish) into a free slot
+int enqueue(tpx_stream *S, const uint64_t *h, int64_t n, bool finishing, uint64_t *ticket) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->finished) return TPX_EINVAL;
+    Slot *sl = nullptr;
+    for (auto &x : S->slots)
+        if (!x.busy) { sl = &x; break; }
+    if (!sl) return TPX_EAGAIN;
+    sl->busy = true;
+    sl->ready = false;
+    sl->rc = 0;
+    sl->ticket = S->next_ticket++;
+    sl->t_submit = Clock::now();
+    S->q.push_back(Job{sl, h, n, finishing});
+    S->queued.fetch_add(1, std::memory_order_acq_rel);
+    if (finishing) S->finished = true;
+    *ticket = sl->ticket;
+    S->cv.notify_all();
+    return TPX_OK;
+}
+
+// wait until the worker has nothing queued or running
+void drain(tpx_stream *S) {
+    std::unique_lock<std::mutex> lk(S->mu);
+    S->cv.wait(lk, [&] { return S->q.empty() && !S->busy_worker; });
 }
 
 }  // namespace tpxs
@@ -330,29 +407,53 @@ int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda
             tpx_stream_destroy(S);
             return TPX_ECUDA;
         }
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        cudaGetLastError();
+        tpx_stream_destroy(S);
+        return TPX_ECUDA;
+    }
+    try {
+        S->worker = std::thread(tpxs::worker_loop, S);
+    } catch (...) {
+        tpx_stream_destroy(S);
+        return TPX_ENOMEM;
+    }
     *out = S;
     return TPX_OK;
 }
 
 int tpx_stream_submit(tpx_stream *S, const uint64_t *h_chunk, int64_t n, uint64_t *ticket) {
-    if (!S || !ticket || n < 0 || (n > 0 && !h_chunk) || n > S->cfg.max_chunk_packets || S->finished) return TPX_EINVAL;
-    return tpxs::process(S, h_chunk, n, false, ticket);
+    if (!S || !ticket || n < 0 || (n > 0 && !h_chunk) || n > S->cfg.max_chunk_packets) return TPX_EINVAL;
+    return tpxs::enqueue(S, h_chunk, n, false, ticket);
 }
 
 int tpx_stream_finish(tpx_stream *S, uint64_t *ticket) {
-    if (!S || !ticket || S->finished) return TPX_EINVAL;
-    const int rc = tpxs::process(S, nullptr, 0, true, ticket);
-    if (!rc) S->finished = true;
-    return rc;
+    if (!S || !ticket) return TPX_EINVAL;
+    return tpxs::enqueue(S, nullptr, 0, true, ticket);
 }
 
 int tpx_stream_poll(tpx_stream *S, uint64_t ticket, tpx_stream_result *out, int32_t timeout_us) {
     if (!S || !out) return TPX_EINVAL;
     Slot *sl = nullptr;
-    for (auto &x : S->slots)
-        if (x.busy && x.ticket == ticket) { sl = &x; break; }
-    if (!sl) return TPX_EINVAL;
     const auto start = Clock::now();
+    // a short spin first (tickets complete in order)
+    while (S->done_ticket_max.load(std::memory_order_acquire) < ticket && Clock::now() - start < tpxs::kSpinFor &&
+           (timeout_us < 0 || Clock::now() - start < std::chrono::microseconds(timeout_us)))
+        std::this_thread::yield();
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        for (auto &x : S->slots)
+            if (x.busy && x.ticket == ticket) { sl = &x; break; }
+        if (!sl) return TPX_EINVAL;
+        auto done = [&] { return sl->ready; };
+        if (timeout_us < 0) S->cv.wait(lk, done);
+        else if (!S->cv.wait_for(lk, std::chrono::microseconds(timeout_us), done)) return TPX_ETIMEOUT;
+        if (sl->rc) {   // the chunk failed: the slot is free again, the status goes to the caller
+            const int rc = sl->rc;
+            sl->busy = false;
+            return rc;
+        }
+    }
     for (;;) {
         const cudaError_t e = cudaEventQuery(sl->done);
         if (e == cudaSuccess) break;
@@ -371,6 +472,7 @@ int tpx_stream_poll(tpx_stream *S, uint64_t ticket, tpx_stream_result *out, int3
     out->clusters = sl->h_cl;
     out->packets_processed = sl->processed;
     out->latency_us = std::chrono::duration<double, std::micro>(Clock::now() - sl->t_submit).count();
+    std::lock_guard<std::mutex> lk(S->mu);
     sl->busy = false;
     return TPX_OK;
 }
@@ -393,11 +495,13 @@ void snap_cfg(const tpx_stream *S, SnapHeader &h) {
 
 int64_t tpx_stream_snapshot_bytes(tpx_stream *S) {
     if (!S) return 0;
+    tpxs::drain(S);
     return (int64_t)sizeof(SnapHeader) + 8 * S->held;
 }
 
 int tpx_stream_snapshot(tpx_stream *S, void *h_buf, int64_t capacity, int64_t *written) {
     if (!S || !h_buf || !written) return TPX_EINVAL;
+    tpxs::drain(S);
     const int64_t need = tpx_stream_snapshot_bytes(S);
     *written = need;
     if (capacity < need) return TPX_EOVERFLOW;
@@ -424,6 +528,7 @@ int tpx_stream_snapshot(tpx_stream *S, void *h_buf, int64_t capacity, int64_t *w
 
 int tpx_stream_restore(tpx_stream *S, const void *h_buf, int64_t n) {
     if (!S || !h_buf || n < (int64_t)sizeof(SnapHeader)) return TPX_EINVAL;
+    tpxs::drain(S);
     SnapHeader hd;
     std::memcpy(&hd, h_buf, sizeof hd);
     if (hd.magic != kSnapMagic || hd.held < 0 || n != (int64_t)sizeof hd + 8 * hd.held) return TPX_EINVAL;
@@ -451,6 +556,14 @@ int tpx_stream_restore(tpx_stream *S, const void *h_buf, int64_t n) {
 
 int tpx_stream_destroy(tpx_stream *S) {
     if (!S) return TPX_EINVAL;
+    if (S->worker.joinable()) {   // the queued chunks are processed first
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stop = true;
+        }
+        S->cv.notify_all();
+        S->worker.join();
+    }
     if (S->s) cudaStreamSynchronize(S->s);
     for (auto &sl : S->slots) {
         if (sl.done) cudaEventDestroy(sl.done);
