@@ -951,15 +951,20 @@ def main():
         # pipelined copies, or TPX_FLAG_HOST_DIRECT (the kernels read the
         # pinned packets and write the pinned outputs in place over the host
         # link); labels as int64 stream indices or int32 (TPX_FLAG_LABELS32)
-        modes = [("staged through device memory, pipelined copies", False, False),
-                 ("staged through device memory, pipelined copies, int32 labels (TPX_FLAG_LABELS32)", False, True),
-                 ("TPX_FLAG_HOST_DIRECT: kernels on the pinned host buffers in place, no copies", True, False),
-                 ("TPX_FLAG_HOST_DIRECT + TPX_FLAG_LABELS32: in place, int32 labels", True, True)]
+        modes = [("staged through device memory, pipelined copies", False, False, False),
+                 ("staged through device memory, pipelined copies, int32 labels (TPX_FLAG_LABELS32)", False, True, False),
+                 ("staged, pipelined, int32 labels, 64-byte records (TPX_FLAG_RECORDS64)", False, True, True),
+                 ("TPX_FLAG_HOST_DIRECT: kernels on the pinned host buffers in place, no copies", True, False, False),
+                 ("TPX_FLAG_HOST_DIRECT + TPX_FLAG_LABELS32: in place, int32 labels", True, True, False),
+                 ("TPX_FLAG_HOST_DIRECT + TPX_FLAG_LABELS32 + TPX_FLAG_RECORDS64: in place, compact outputs", True, True,
+                  True)]
         results = []
-        for mode, direct, l32 in modes:
+        for mode, direct, l32, r64 in modes:
             a_lab = h_lab.numpy().view(np.int32)[:n] if l32 else h_lab.numpy()
+            rdt = tpx.CLUSTER64_DTYPE if r64 else tpx.CLUSTER_DTYPE
+            a_cl = h_cl.numpy()[: cl_cap * rdt.itemsize].view(rdt)
             hctx = tpx.Context(tpx.Config(tile_geometry=tuning["tile_geometry"] or tpx.TILE_2048, host_direct=direct,
-                                          labels32=l32), max_packets=n)
+                                          labels32=l32, records64=r64), max_packets=n)
             try:
                 def host_step():
                     if state is not None:
@@ -985,7 +990,7 @@ def main():
             results.append({"value": float(h_all.item()) / float(e_t.item()), "unit": UNIT,
                             # in place, the pre-pass and the fused kernel each read the packets
                             "h2d_bytes_per_step": 8 * n * (2 if direct else 1),
-                            "d2h_bytes_per_step": lab_b + CLUSTER_BYTES * ncl_h + 8 * ntr_h + 16,
+                            "d2h_bytes_per_step": lab_b + (64 if r64 else CLUSTER_BYTES) * ncl_h + 8 * ntr_h + 16,
                             "ms_per_step": 1e3 * statistics.mean(tim), "mode": mode,
                             "step_ms": {"min": 1e3 * min(tim), "median": 1e3 * statistics.median(tim),
                                         "max": 1e3 * max(tim)}})

@@ -105,6 +105,14 @@ typedef struct tpx_config {
    labels would not fit 31 bits is rejected (TPX_EINVAL), as is a batch call
    with labels. */
 #define TPX_FLAG_LABELS32 8
+/* TPX_FLAG_RECORDS64 -- tpx_process, tpx_process_host and
+   tpx_process_noalloc write the clusters as tpx_record64 (64 bytes: the
+   record without the derived x, y and tof, which follow from the exact sums
+   as x = s_x / s_tot, y = s_y / s_tot, tof = (t0 - t_trig[shot]) +
+   s_t / s_tot); the d_clusters / h_clusters argument then points to cl_cap
+   tpx_record64 (the pointer type stays tpx_record *).  A batch call is
+   rejected (TPX_EINVAL). */
+#define TPX_FLAG_RECORDS64 16
 
 #define TPX_TILE_DEFAULT 0
 #define TPX_TILE_4096 1
@@ -129,6 +137,12 @@ typedef struct tpx_record {
     double y;        /* s_y / s_tot                                          */
     double tof;      /* (t0 - t_trig[shot]) + s_t / s_tot, ticks             */
 } tpx_record;        /* 88 bytes */
+
+/* The compact record of TPX_FLAG_RECORDS64: the first 64 bytes of tpx_record. */
+typedef struct tpx_record64 {
+    int64_t label, shot, t0, s_tot, s_x, s_y, s_t;
+    int32_t n, n_peaks;
+} tpx_record64;      /* 64 bytes */
 
 typedef struct tpx_counters {
     int64_t packets, pixels, tdcs, corrupt, dropped_pre_trigger, dropped_background,

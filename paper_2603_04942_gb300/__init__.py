@@ -25,6 +25,7 @@ MODE_PAPER = 1
 TILE_DEFAULT, TILE_4096, TILE_2048 = 0, 1, 2
 FLAG_HOST_DIRECT = 4
 FLAG_LABELS32 = 8
+FLAG_RECORDS64 = 16
 TICK_NS = 1.5625
 
 OK, EINVAL, ENOMEM, EOVERFLOW, ECORRUPT, EAGAIN, ETIMEOUT, EDEVTIMEOUT, ECUDA, EUNSUPPORTED = \
@@ -35,6 +36,10 @@ CLUSTER_DTYPE = np.dtype([("label", "<i8"), ("shot", "<i8"), ("t0", "<i8"), ("s_
                           ("s_x", "<i8"), ("s_y", "<i8"), ("s_t", "<i8"), ("n", "<i4"),
                           ("n_peaks", "<i4"), ("x", "<f8"), ("y", "<f8"), ("tof", "<f8")])
 assert CLUSTER_DTYPE.itemsize == 88
+# tpx_record64 (TPX_FLAG_RECORDS64): the record without the derived x, y, tof
+CLUSTER64_DTYPE = np.dtype([("label", "<i8"), ("shot", "<i8"), ("t0", "<i8"), ("s_tot", "<i8"),
+                            ("s_x", "<i8"), ("s_y", "<i8"), ("s_t", "<i8"), ("n", "<i4"), ("n_peaks", "<i4")])
+assert CLUSTER64_DTYPE.itemsize == 64
 
 COUNTER_FIELDS = ("packets", "pixels", "tdcs", "corrupt", "dropped_pre_trigger", "dropped_background",
                   "kept", "clusters", "peaks", "status_bits", "redone")
@@ -116,9 +121,14 @@ class Config:
     tile_geometry: int = 0             # TILE_DEFAULT, TILE_4096 or TILE_2048 (speed only)
     host_direct: bool = False          # tpx_process_host on mapped pinned host buffers in place
     labels32: bool = False             # per-packet labels as int32, relative to the call's index base
+    records64: bool = False            # 64-byte records (CLUSTER64_DTYPE: no x, y, tof)
 
     def flags(self) -> int:
-        return (FLAG_HOST_DIRECT if self.host_direct else 0) | (FLAG_LABELS32 if self.labels32 else 0)
+        return ((FLAG_HOST_DIRECT if self.host_direct else 0) | (FLAG_LABELS32 if self.labels32 else 0) |
+                (FLAG_RECORDS64 if self.records64 else 0))
+
+    def record_dtype(self) -> np.dtype:
+        return CLUSTER64_DTYPE if self.records64 else CLUSTER_DTYPE
 
 
 _lock = threading.Lock()
@@ -337,11 +347,11 @@ class Context:
             labels=torch.empty(n_packets, dtype=torch.int32 if self.cfg.labels32 else torch.int64,
                                device=dev) if labels else None,
             is_peak=torch.empty(n_packets, dtype=torch.uint8, device=dev) if is_peak else None,
-            clusters=torch.empty(cl_cap * CLUSTER_DTYPE.itemsize, dtype=torch.uint8, device=dev),
+            clusters=torch.empty(cl_cap * self.cfg.record_dtype().itemsize, dtype=torch.uint8, device=dev),
             n_clusters=torch.zeros(1, dtype=torch.int64, device=dev),
             trig=torch.empty(tr_cap, dtype=torch.int64, device=dev),
             n_trig=torch.zeros(1, dtype=torch.int64, device=dev),
-            cluster_capacity=cl_cap, trig_capacity=tr_cap)
+            cluster_capacity=cl_cap, trig_capacity=tr_cap, record_dtype=self.cfg.record_dtype())
 
     def tpx_process(self, packets, out: dict, index_base: int = 0, n_packets: int | None = None):
         n = int(packets.numel() if n_packets is None else n_packets)
@@ -424,8 +434,9 @@ class Context:
         ncl = int(out["n_clusters"].item())
         ntr = int(out["n_trig"].item())
         m = min(ncl, out["cluster_capacity"])
-        raw = out["clusters"][: m * CLUSTER_DTYPE.itemsize].cpu().numpy()
-        clusters = np.frombuffer(raw.tobytes(), CLUSTER_DTYPE).copy() if m else np.zeros(0, CLUSTER_DTYPE)
+        dt = out.get("record_dtype", CLUSTER_DTYPE)
+        raw = out["clusters"][: m * dt.itemsize].cpu().numpy()
+        clusters = np.frombuffer(raw.tobytes(), dt).copy() if m else np.zeros(0, dt)
         return dict(status=rc, counters=counters, clusters=clusters, n_clusters=ncl, n_trig=ntr,
                     triggers=out["trig"][: min(ntr, out["trig_capacity"])].cpu().numpy(),
                     labels=None if out["labels"] is None else out["labels"].cpu().numpy(),
@@ -436,6 +447,7 @@ class Context:
                          clusters: np.ndarray, triggers: np.ndarray, index_base: int = 0) -> tuple[int, int, int]:
         assert packets.dtype == np.uint64 and packets.flags.c_contiguous
         assert labels is None or labels.dtype == (np.int32 if self.cfg.labels32 else np.int64)
+        assert clusters.dtype == self.cfg.record_dtype()
         n_cl = ctypes.c_int64()
         n_tr = ctypes.c_int64()
         rc = lib().tpx_process_host(self._h, packets.ctypes.data, packets.size, int(index_base),

@@ -96,6 +96,7 @@ struct Params {
     long long *labels;
     int *labels32;            // TPX_FLAG_LABELS32: labels minus lab32_base, as int32 (labels NULL)
     int l2_prefetch;          // the packets are in device memory: prefetch the next tile into L2
+    int rec64;                // TPX_FLAG_RECORDS64: clusters holds 64-byte records (no x, y, tof)
     long long lab32_base;
     uint8_t *is_peak;
     tpx_record *clusters;

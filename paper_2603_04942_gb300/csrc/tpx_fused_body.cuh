@@ -421,8 +421,23 @@ __device__ void flush_pending_warp(Smem &S, const Params &p, unsigned seq) {
     const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
     constexpr int WPR = (int)(sizeof(tpx_record) / 8);
     const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
+    if (p.rec64) {   // 64-byte records: the first 8 words of each staged record
+        unsigned long long *d64 = reinterpret_cast<unsigned long long *>(p.clusters) + O * 8;
+        const long long nw = keep * 8;
+        for (long long w0 = lane; w0 < nw; w0 += 32 * 8) {
+            unsigned long long v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const long long w = w0 + 32 * u;
+                v[u] = w < nw ? __ldcg(src + (w >> 3) * WPR + (w & 7)) : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (w0 + 32 * u < nw) d64[w0 + 32 * u] = v[u];
+        }
+    }
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
-    const long long nw = keep * WPR;
+    const long long nw = p.rec64 ? 0 : keep * WPR;
     for (long long w0 = lane; w0 < nw; w0 += 32 * 8) {
         unsigned long long v[8];
 #pragma unroll
@@ -487,6 +502,19 @@ __device__ __forceinline__ void put_record(tpx_record *dst, const Moments &m, co
     o.n = m.n; o.n_peaks = m.npk;
     com_from_moments(m.s_x, m.s_y, s_t, m.s_tot, tofc0, &o.x, &o.y, &o.tof);
     *dst = o;
+}
+
+// a record at position idx of the caller's buffer (88 bytes, or its first 64
+// with TPX_FLAG_RECORDS64)
+__device__ __forceinline__ void out_record(const Params &p, long long idx, const tpx_record &o) {
+    if (p.rec64) {
+        const unsigned long long *w = reinterpret_cast<const unsigned long long *>(&o);
+        unsigned long long *d = reinterpret_cast<unsigned long long *>(p.clusters) + idx * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[k] = w[k];
+    } else {
+        p.clusters[idx] = o;
+    }
 }
 
 // rank of label position lp among the tile's labels (after the bitmap scan)
@@ -1252,7 +1280,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
                 o.n = n; o.n_peaks = npk;
                 com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                dst[i] = o;
+                out_record(p, S.clo + i, o);   // unstaged: straight to its offset
             }
         } else {
             unsigned long long c_pk = 0;
@@ -1310,7 +1338,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y; o.s_t = s_t;
                 o.n = (int)n; o.n_peaks = 1;
                 com_from_moments(s_x, s_y, s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
-                dst[i] = o;
+                if (STAGED) dst[i] = o;
+                else out_record(p, S.clo + i, o);
             }
         }
         TPX_PH(14);

@@ -1452,6 +1452,11 @@ __global__ void k_packet_labels32(tpx_hits h, const long long *hl, long long nh,
 __global__ void k_fill_i32(int *p, long long n, int v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
 }
+__global__ void k_records64(const tpx_record *src, const long long *n, long long cap, tpx_record64 *dst) {
+    const long long m = min(*n, cap);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = *reinterpret_cast<const tpx_record64 *>(src + i);
+}
 __global__ void k_fill_ll(long long *p, long long n, long long v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -1493,7 +1498,24 @@ int redo_last(tpx_ctx *c) {
     unsigned status = 0;
     if (!rc) rc = ck(cudaMemcpy(&status, &c->ctl->status, 4, cudaMemcpyDeviceToHost));
     if (!rc && !(status & (ST_TRIG_ORDER | ST_TRIG_CAP))) {
-        rc = cluster_all(c, h, nh, reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, -1, L.cl, L.cl_cap, L.n_cl);
+        // TPX_FLAG_RECORDS64: the full records go to a scratch array first,
+        // then their first 64 bytes to the caller's buffer
+        const bool r64 = (c->cfg.flags & TPX_FLAG_RECORDS64) != 0 && L.cl_cap > 0;
+        const int64_t cap64 = r64 ? std::min<int64_t>(L.cl_cap, std::max<long long>(nh, 1)) : 0;
+        tpx_record *out = L.cl;
+        void *tmp = nullptr;
+        if (r64) {
+            if (cudaMalloc(&tmp, sizeof(tpx_record) * (size_t)cap64) != cudaSuccess) { cudaGetLastError(); rc = TPX_ENOMEM; }
+            out = static_cast<tpx_record *>(tmp);
+        }
+        if (!rc) rc = cluster_all(c, h, nh, reinterpret_cast<int64_t *>(hl), hp, LLONG_MAX, -1, out, r64 ? cap64 : L.cl_cap,
+                                  L.n_cl);
+        if (!rc && r64) {
+            k_records64<<<grid_for(cap64), GT, 0, s>>>(static_cast<const tpx_record *>(tmp), reinterpret_cast<const long long *>(L.n_cl),
+                                                     cap64, reinterpret_cast<tpx_record64 *>(L.cl));
+            rc = ck(cudaStreamSynchronize(s));
+        }
+        if (tmp) cudaFree(tmp);
         if (!rc && (L.labels || L.is_peak)) {
             long long *l64 = L.lab32 ? nullptr : reinterpret_cast<long long *>(L.labels);
             int *l32 = L.lab32 ? reinterpret_cast<int *>(L.labels) : nullptr;

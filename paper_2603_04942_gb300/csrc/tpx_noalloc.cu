@@ -135,6 +135,7 @@ extern "C" int tpx_process_noalloc(const tpx_config *cfg, void *cuda_stream, con
         p.labels = l32 ? nullptr : reinterpret_cast<long long *>(d_labels);
         p.labels32 = l32 ? reinterpret_cast<int *>(d_labels) : nullptr;
         p.lab32_base = idx_base;
+        p.rec64 = (cfg->flags & TPX_FLAG_RECORDS64) ? 1 : 0;
         p.is_peak = d_is_peak;
         p.clusters = d_clusters;
         p.cl_cap = cl_cap;

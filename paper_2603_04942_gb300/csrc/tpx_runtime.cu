@@ -43,7 +43,7 @@ int check_cfg(const tpx_config *c) {
     if (c->wrap_thr_pix_ticks <= 0 || c->wrap_thr_tdc_ticks <= 0) return TPX_EINVAL;
     if (c->tile_geometry != TPX_TILE_DEFAULT && c->tile_geometry != TPX_TILE_4096 && c->tile_geometry != TPX_TILE_2048)
         return TPX_EINVAL;
-    if (c->flags & ~(TPX_FLAG_HOST_DIRECT | TPX_FLAG_LABELS32)) return TPX_EINVAL;
+    if (c->flags & ~(TPX_FLAG_HOST_DIRECT | TPX_FLAG_LABELS32 | TPX_FLAG_RECORDS64)) return TPX_EINVAL;
     return TPX_OK;
 }
 
@@ -404,6 +404,7 @@ int tpx_process(tpx_ctx *c, const uint64_t *d_packets, int64_t n, int64_t idx_ba
     p.labels32 = l32 ? reinterpret_cast<int *>(d_labels) : nullptr;
     p.lab32_base = l32_base;
     p.l2_prefetch = (!c->packets_on_host && device_memory(d_packets)) ? 1 : 0;
+    p.rec64 = (c->cfg.flags & TPX_FLAG_RECORDS64) ? 1 : 0;
     p.is_peak = d_is_peak;
     p.clusters = d_clusters;
     p.cl_cap = cl_cap;
@@ -475,6 +476,7 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
         return TPX_EINVAL;
     if (h_run_offsets[0] != 0) return TPX_EINVAL;
     if ((c->cfg.flags & TPX_FLAG_LABELS32) && d_labels) return TPX_EINVAL;   // batch labels are int64
+    if (c->cfg.flags & TPX_FLAG_RECORDS64) return TPX_EINVAL;                // batch records are 88 bytes
     for (int64_t r = 0; r < n_runs; ++r)
         if (h_run_offsets[r + 1] < h_run_offsets[r]) return TPX_EINVAL;
     const int64_t n = h_run_offsets[n_runs];
@@ -822,6 +824,7 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
     if (h_is_peak && (rc = grow(&c->st_peak, &c->st_peak_cap, n))) return rc;
     // int32 labels (TPX_FLAG_LABELS32) stay relative to the whole call
     const size_t les = (c->cfg.flags & TPX_FLAG_LABELS32) ? 4 : 8;
+    const size_t rsz = (c->cfg.flags & TPX_FLAG_RECORDS64) ? sizeof(tpx_record64) : sizeof(tpx_record);
     char *st_lab = reinterpret_cast<char *>(c->st_labels);
     char *h_lab = reinterpret_cast<char *>(h_labels);
     cudaStream_t sc = c->stream;
@@ -852,8 +855,8 @@ static int process_host_pipelined(tpx_ctx *c, const uint64_t *h_packets, int64_t
         const int64_t ccl = std::max<int64_t>(0, std::min(ncl, cl_cap - rec_off));
         const int64_t ctr = std::max<int64_t>(0, std::min(ntr, trig_cap - trig_off));
         if (!failed && ccl > 0 &&
-            ckr(cudaMemcpyAsync(h_clusters + rec_off, P.cl[k & 1], sizeof(tpx_record) * ccl, cudaMemcpyDeviceToHost,
-                                P.s_out)))
+            ckr(cudaMemcpyAsync(reinterpret_cast<char *>(h_clusters) + rsz * rec_off, P.cl[k & 1], rsz * ccl,
+                                cudaMemcpyDeviceToHost, P.s_out)))
             return TPX_ECUDA;
         if (!failed && ctr > 0 &&
             ckr(cudaMemcpyAsync(h_trig + trig_off, P.trig[k & 1], sizeof(int64_t) * ctr, cudaMemcpyDeviceToHost, P.s_out)))
@@ -995,7 +998,8 @@ int tpx_process_host(tpx_ctx *c, const uint64_t *h_packets, int64_t n, int64_t i
     if (ckr(cudaStreamSynchronize(s))) return TPX_ECUDA;
     const int64_t ncl = counts[0] < cl_cap ? counts[0] : cl_cap;
     const int64_t ntr = counts[1] < trig_cap ? counts[1] : trig_cap;
-    if (ncl > 0 && cudaMemcpyAsync(h_clusters, c->st_cl, sizeof(tpx_record) * ncl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    const size_t rsz = (c->cfg.flags & TPX_FLAG_RECORDS64) ? sizeof(tpx_record64) : sizeof(tpx_record);
+    if (ncl > 0 && cudaMemcpyAsync(h_clusters, c->st_cl, rsz * ncl, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;
     if (ntr > 0 && cudaMemcpyAsync(h_trig, c->st_trig, sizeof(int64_t) * ntr, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return TPX_ECUDA;

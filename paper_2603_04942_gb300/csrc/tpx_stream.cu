@@ -347,6 +347,7 @@ int tpx_stream_create(tpx_stream **out, const tpx_stream_config *cfg, void *cuda
     *out = nullptr;
     if (cfg->max_chunk_packets <= 0 || cfg->max_hold_packets < 0 || cfg->hold_triggers < 1 || cfg->slots < 1)
         return TPX_EINVAL;
+    if (cfg->cfg.flags & (TPX_FLAG_LABELS32 | TPX_FLAG_RECORDS64)) return TPX_EINVAL;   // results are 88-byte records
     tpx_stream *S = new (std::nothrow) tpx_stream;
     if (!S) return TPX_ENOMEM;
     S->cfg = *cfg;

@@ -71,9 +71,11 @@ def test_phase_counters_and_flags_without_a_gpu(libpath):
     assert L.tpx_kernel_times(None, None, None, None) == tpx.EINVAL
     # the configuration accepts the two flags and nothing else
     assert tpx.Config(labels32=True, host_direct=True).flags() == tpx.FLAG_LABELS32 | tpx.FLAG_HOST_DIRECT
+    assert tpx.Config(records64=True).flags() == tpx.FLAG_RECORDS64
+    assert tpx.CLUSTER64_DTYPE.names == tpx.CLUSTER_DTYPE.names[:9]
     bad = tpx._CConfig()
     L.tpx_config_default(ctypes.byref(bad))
-    bad.flags = 16
+    bad.flags = 32
     h = ctypes.c_void_p()
     assert L.tpx_create(ctypes.byref(h), ctypes.byref(bad), 10, None) == tpx.EINVAL
 

@@ -176,3 +176,32 @@ def test_labels32_equal_the_oracle():
     ncl = int(n_cl.item())
     g = np.frombuffer(clusters[: ncl * tpx.CLUSTER_DTYPE.itemsize].cpu().numpy().tobytes(), tpx.CLUSTER_DTYPE)
     assert_clusters_equal(g, ref["clusters"])
+
+
+def test_records64_equal_the_oracle():
+    import torch
+    tpx, L = _lib()
+    pk = synth.generate(synth.small(shot_begin=0, n_shots=300))[0]
+    ref = oracle_run(pk)
+    cfg = tpx._CConfig()
+    L.tpx_config_default(ctypes.byref(cfg))
+    cfg.flags = tpx.FLAG_RECORDS64
+    n = pk.size
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    labels = torch.full((n,), -7, dtype=torch.int64, device="cuda")
+    clusters = torch.zeros(n * 64, dtype=torch.uint8, device="cuda")
+    trig = torch.zeros(n, dtype=torch.int64, device="cuda")
+    n_cl = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n_tr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = tpx._CCounters()
+    torch.cuda.synchronize()
+    rc = L.tpx_process_noalloc(ctypes.byref(cfg), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                               d.data_ptr(), n, 0, labels.data_ptr(), None, clusters.data_ptr(), n,
+                               n_cl.data_ptr(), trig.data_ptr(), n, n_tr.data_ptr(), ctypes.byref(cnt))
+    assert rc == 0
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    ncl = int(n_cl.item())
+    g = np.frombuffer(clusters[: ncl * 64].cpu().numpy().tobytes(), tpx.CLUSTER64_DTYPE)
+    assert g.size == ref["clusters"].size
+    for f in tpx.CLUSTER64_DTYPE.names:
+        assert np.array_equal(g[f], ref["clusters"][f]), f
