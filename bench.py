@@ -70,6 +70,8 @@ def parse():
                     help="time only the CNN refiner's tcgen05 inference on N random bf16 patches (random weights)")
     ap.add_argument("--batch-runs", type=int, default=4096)
     ap.add_argument("--batch-only", action="store_true")
+    ap.add_argument("--batch-phase-shares", type=int, default=0, metavar="RUNS",
+                    help="per-phase cycle shares of the batch kernel on the first RUNS runs (instrumented build)")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed whole calls of the batch (each ~5 s)")
     ap.add_argument("--stream-only", action="store_true")
     ap.add_argument("--stream-chunks", type=int, default=150)
@@ -573,6 +575,44 @@ def phase_bench(shots: int, tile: str) -> dict:
             "shares": {nm: round(float(c / cyc.sum()), 4) for nm, c in zip(tpx.PHASE_NAMES, cyc)}}
 
 
+def batch_phase_bench(n_runs: int) -> dict:
+    """Per-phase cycle shares of the batch kernel on the first `n_runs` runs
+    of the uneven batch (the instrumented library must be loaded): one
+    untimed call, then one call whose counters are read."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    runs = synth.batched(n_runs=n_runs)
+    pks = [synth.generate(p)[0] for p in runs]
+    offs = np.zeros(len(pks) + 1, np.int64)
+    offs[1:] = np.cumsum([x.size for x in pks])
+    pk = np.concatenate(pks)
+    del pks
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+    shots = sum(p.n_shots for p in runs)
+    expect = sum(p.n_shots * p.particles_per_shot for p in runs)
+    out = ctx.alloc_batch_outputs(pk.size, len(runs), labels=False, is_peak=False,
+                                  cluster_capacity=int(1.3 * expect) + (1 << 20), trig_capacity=shots + 16)
+    ctx.tpx_process_batch(d, offs, out)
+    rc, cnt = ctx.tpx_sync(check=False)
+    tpx.phase_times(tpx.TILE_4096, clear=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.tpx_process_batch(d, offs, out)
+    rc, cnt = ctx.tpx_sync(check=False)
+    wall = time.perf_counter() - t0
+    cyc = tpx.phase_times(tpx.TILE_4096, clear=True).astype(np.float64)
+    ctx.close()
+    main, sub = cyc[:20], cyc[20:len(tpx.PHASE_NAMES)]   # the big-range steps lie inside phase 17
+    return {"metric": "batch-kernel phase shares (warp cycles, barrier waits included)", "runs": n_runs,
+            "packets": int(pk.size), "status": rc, "redone": cnt["redone"], "wall_s_instrumented": round(wall, 3),
+            "shares": {nm: round(float(c / main.sum()), 4) for nm, c in zip(tpx.PHASE_NAMES[:20], main)},
+            "big_range_steps": {nm: round(float(c / max(main[17], 1.0)), 4)
+                                for nm, c in zip(tpx.PHASE_NAMES[20:], sub)}}
+
+
 CNN_FLOPS_PER_PATCH = 2 * (49 * 18 * 16 + 25 * 144 * 16 + 9 * 144 * 32 + 288 * 144 + 144 * 6)
 
 
@@ -806,6 +846,14 @@ def main():
         import paper_2603_04942_gb300 as tpx
         tpx.load(tbuild.build(phases=True))
         print(json.dumps(phase_bench(args.phase_shares, args.tile)), flush=True)
+        return 0
+    if args.batch_phase_shares:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2603_04942_gb300 import build as tbuild
+        import paper_2603_04942_gb300 as tpx
+        tpx.load(tbuild.build(phases=True))
+        print(json.dumps(batch_phase_bench(args.batch_phase_shares)), flush=True)
         return 0
     if args.cnn_phase_shares:
         import torch

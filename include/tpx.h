@@ -510,9 +510,19 @@ int tpx_refine_patches_bf16(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_p
    h_run_offsets[r+1]).  One persistent launch of the fused kernel works
    through a device queue of tiles of all runs; every run is a stream of its
    own (unwrap state and trigger count start from zero at its first packet),
-   the context's configuration applies to all.  Runs whose shots do not fit
-   the tiles' ranges are redone exactly by the general path at tpx_sync
-   (counters.redone = the number of such runs) and spliced into the outputs.
+   the context's configuration applies to all.  In CC mode a tile whose
+   range (its shots up to the next trigger packet) is longer than the tile
+   can hold on chip clusters it in the same launch with the big-range path:
+   the whole range decoded into the CTA's global scratch, its kept pixels
+   sorted by (shot, time bin), each pixel compared with its own and the
+   previous bin (the same results as the tile's path).  A range even that
+   cannot hold (more than 65,535 packets, more kept pixels than its shared
+   scratch: 38,720, or 24,960 with 2048-packet tiles, more than 256 trigger
+   packets), any range in PAPER mode, and a pixel whose trigger lies
+   outside its range send the run to the general path: such runs are redone
+   exactly at tpx_sync (counters.redone = the number of such runs) and
+   spliced into the outputs.  The big-range scratch takes 9.5 MB per CTA of
+   the grid (5.3 MB with 2048-packet tiles) of the batch scratch.
      h_run_offsets   host [n_runs + 1], h_run_offsets[0] = 0, non-decreasing
      d_labels, d_is_peak  per packet of the whole buffer, or NULL; labels are
                      positions in the whole buffer

@@ -234,7 +234,10 @@ def lib():
 PHASE_NAMES = ("tile start", "tile load", "look-ahead", "walk 2 and its scan", "trigger times",
                "walk 4 (records)", "hash insert", "neighbour pass", "compression", "unions", "roots",
                "member lists", "member-list walks (and the previous tile's copy-out)",
-               "label ranks and staged stores", "labels and offsets", "tail", "CTA end")
+               "staged stores", "labels and offsets", "tail", "CTA end",
+               "big ranges (batches: the sorted-window path)", "big ranges: the previous tile's copy-out",
+               "label ranks (bitmap scan)", "big: range end, walk 2, triggers", "big: walk 4", "big: bins and sort",
+               "big: neighbour pass", "big: compression and roots", "big: moments", "big: labels, records, outputs")
 
 
 CNN_PHASE_NAMES = ("wait for the patches", "conversion to the conv1 map", "conv1 MMAs", "conv1 epilogue",

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <climits>
+#include <cstddef>
 #include <cstdint>
 
 #include "tpx_common.cuh"
@@ -31,6 +32,7 @@ int fused_threads(int geo) { return geo == GEO_T2048 ? geo_t2048::NT : geo_t4096
 int fused_range_capacity(int geo) { return geo == GEO_T2048 ? geo_t2048::C : geo_t4096::C; }
 int fused_ctas_per_sm(int geo) { return geo == GEO_T2048 ? geo_t2048::MINB : geo_t4096::MINB; }
 int fused_smem_bytes(int geo) { return geo == GEO_T2048 ? geo_t2048::smem_bytes() : geo_t4096::smem_bytes(); }
+size_t fused_big_scratch_bytes(int geo) { return geo == GEO_T2048 ? geo_t2048::BR_STRIDE : geo_t4096::BR_STRIDE; }
 
 cudaError_t launch_fused(const Params &p, int mode, int geo, int grid, cudaStream_t s, cudaEvent_t mid) {
     cudaError_t e = launch_unwrap_prepass(p, fused_tile_packets(geo), grid, s);

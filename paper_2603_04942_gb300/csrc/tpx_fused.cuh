@@ -35,6 +35,7 @@ namespace tpxk {
 constexpr int64_t kPixPeriod = 1LL << 34;
 constexpr int64_t kTdcPeriod = 1LL << 36;
 constexpr int kTofBias = 32768;            // tof_c + bias >= 1 for int16 timewalk shifts
+constexpr int kBatchRing = 4;              // staged tiles per CTA of a batch launch (records, triggers)
 
 // status bits latched in Ctl::status
 enum : unsigned {
@@ -47,6 +48,7 @@ enum : unsigned {
     ST_DEVTIMEOUT = 1u << 6,   // a look-back wait ran out
     ST_RUN_REDO = 1u << 7,     // batch: a run needs the general path (see run_failed)
     ST_BOUNDS = 1u << 8,       // checked build: an index outside its array (the access was skipped)
+    ST_BIG = 1u << 9,          // a tile's range exceeds the capacity: the big-range path (never reported)
 };
 
 enum CounterIdx {
@@ -85,7 +87,7 @@ struct BatchTable {
     long long *run_trig_off;      // [runs + 1] out: trigger offsets
     unsigned *run_failed;         // [runs] out: 1 = a range the tiles cannot hold
     long long *tcagg, *tcpre;     // [tiles] trigger-count chain
-    long long *tstage;            // [grid * tile packets] trigger staging
+    long long *tstage;            // [grid * kBatchRing * tile packets] trigger staging
     long long n_runs;
 };
 
@@ -114,11 +116,13 @@ struct Params {
     TileScratch ts;
     Ctl *ctl;
     tpx_record *stage;       // per-CTA record staging (range-capacity records per
-                             // CTA of the grid, in label order), or NULL: inline
-                             // offset look-back
+                             // CTA of the grid, kBatchRing slots of them in a batch,
+                             // in label order), or NULL: inline offset look-back
     BatchTable bt;           // batch of runs (tile_run == NULL: one stream)
     long long hold;          // tile + 1 whose look-back flags stay unpublished (0: none): lets a
                              // test run its successors' bounded waits out (TPX_EDEVTIMEOUT)
+    unsigned char *big;      // big-range scratch, fused_big_scratch_bytes per CTA of the grid (NULL:
+                             // a range past the capacity sends its run to the general path)
     const GAgg *E0;          // unwrap state before the call (NULL: stream start)
     GAgg *state_out;         // state after the call, written by the pre-pass (or NULL)
 };
@@ -134,6 +138,8 @@ int fused_smem_bytes(int geo);
 int fused_threads(int geo);
 int fused_range_capacity(int geo);
 int fused_ctas_per_sm(int geo);
+// global scratch of the big-range path per CTA (batches in CC mode)
+size_t fused_big_scratch_bytes(int geo);
 // the unwrap pre-pass (tpx_prepass.cu): ts.pre[tile] = the state before each
 // tile, *state_out = the state after the call; adds the pixel, TDC and
 // corrupt-packet counters. launch_fused runs it before the fused kernel.

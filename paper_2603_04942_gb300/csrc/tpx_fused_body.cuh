@@ -133,13 +133,15 @@ struct __align__(16) Smem {
     long long next_tile;          // claimed while the current tile runs
     long long tile;
     long long clo;
-    long long pend_tile;          // staged records awaiting their offset (-1: none)
-    long long pend_ntr;
     long long tlo;                // trigger offset of a batch tile
-    int pend_ncl;
-    int pend_ntdc;                // batch: the pending tile's triggers, its run,
-    int pend_run;                 // and whether it is the run's first tile
-    bool pend_first;
+    // staged tiles awaiting their offsets: a ring, entry k staged in slot k
+    // (one entry for a single stream, RING in a batch)
+    struct Pend {
+        long long tile, ntr;      // the tile; its trigger total (single streams)
+        int ncl, ntdc, run;       // its records and triggers; its run
+        bool first, big;          // the run's first tile; records in the big-range slot
+    } pend[4];
+    int pend_head, pend_count;
     int first_tdc;
     int first_pix;                // first pixel of the range
     int la_first[3];              // first TDC packet past the tile (window, then rotating chunk slots)
@@ -153,6 +155,46 @@ struct __align__(16) Smem {
 // MINB CTAs per SM within the SM's 228 KB of shared memory (1 KB of it is
 // reserved per CTA)
 static_assert(MINB * (sizeof(Smem) + 1024) <= 228 * 1024, "shared memory of the tile geometry");
+
+// a batch keeps up to RING staged tiles per CTA waiting for their offsets (a
+// tile behind a big range need not wait for it); a single stream keeps one
+constexpr int RING = kBatchRing;
+static_assert(RING >= 1 && RING <= 4, "the ring of staged tiles");
+
+// ---------------------------------------------------- big-range constants
+// (the path itself is described at big_range below)
+constexpr int BR_L = 65535;          // positions of a big range (16-bit)
+constexpr int BR_LW = (BR_L + 1) / 32;
+constexpr int BR_S = 256;            // shots (trigger packets) of a big range
+// sort keys (time bin, 16-column stripe) shared out over its shots
+constexpr int BR_BINS = C >= 8192 ? 8192 : 4096;
+constexpr int BR_NS = 16;            // x stripes of 16 columns (one stripe when rx > 16)
+struct BrMom { unsigned long long s_tot, s_x, s_y, s_tt, best; unsigned n, npk; };
+static_assert(sizeof(BrMom) == 48, "moment record");
+// shared scratch: the tile arrays in front of the trigger tables
+constexpr int BR_REGION = (int)offsetof(Smem, tdc_t);
+// the neighbour pass reads the sorted records through shared memory, BR_CH
+// pixels at a time with the records before them that they can reach
+constexpr int BR_CH = 2 * NT;
+constexpr int BR_SB = 2 * BR_CH;
+constexpr int BR_FIXED = 4 * (BR_BINS + 4) + 4 * BR_LW + 2 * BR_LW + 4 * 5 * BR_S + 4 * 16 + 8 * BR_SB;
+// kept pixels: a 16-bit parent and a local-maximum bit each
+constexpr int BR_N0 = ((BR_REGION - BR_FIXED) * 8 / 17) & ~63;
+constexpr int BR_N = BR_N0 < 65472 ? BR_N0 : 65472;
+static_assert(BR_N > C && BR_N % 64 == 0, "a big range holds more pixels than a tile");
+static_assert(2 * BR_N + BR_N / 8 + BR_FIXED <= BR_REGION, "big-range shared scratch");
+static_assert(BR_BINS % NT == 0 && BR_LW % NT == 0, "bins and label words split evenly over the CTA");
+// per-CTA global scratch: records by position, sorted records and their
+// positions, moments by root, and the staged cluster records (a big range
+// may hold up to one cluster per kept pixel)
+constexpr size_t BR_REC_OFF = ((size_t)8 * (BR_L + 1) + (size_t)58 * BR_N + 255) & ~(size_t)255;
+// One record slot per ring entry: a big range's records wait in its entry's
+// slot while the CTA goes on.
+constexpr size_t BR_STRIDE = (BR_REC_OFF + RING * sizeof(tpx_record) * (size_t)BR_N + 255) & ~(size_t)255;
+__device__ __forceinline__ tpx_record *br_stage(const Params &p, int slot) {
+    return reinterpret_cast<tpx_record *>(p.big + (size_t)blockIdx.x * BR_STRIDE + BR_REC_OFF) + (size_t)slot * BR_N;
+}
+
 
 // block exclusive scan in thread order of two 16-bit halves added
 // separately (__vadd2); each half's sums must fit it. Total in *total.
@@ -270,7 +312,8 @@ __device__ __forceinline__ LbScan lb_scan(const unsigned *flags, long long hi, l
 // Decoupled look-back over the record counts of the tiles (and, in a batch,
 // their trigger counts: .y), over all tiles of the call.
 template <bool BATCH>
-__device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status) {
+__device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsigned seq, unsigned *status,
+                                         bool block = true, bool *ready = nullptr) {
     const int lane = threadIdx.x & 31;
     longlong2 acc = make_longlong2(0, 0);
     for (long long hi = tile - 1; hi >= 0; hi -= 32 * LBC) {
@@ -279,6 +322,7 @@ __device__ longlong2 lookback_count_warp(const Params &p, long long tile, unsign
         for (;;) {
             sc = lb_scan<LBC>(p.ts.cflags, hi, 0, seq);
             if (__all_sync(0xffffffffu, sc.ok)) break;
+            if (!block) { *ready = false; return acc; }   // not yet: the caller tries again later
             if (++spins > MAX_SPIN || timed_out(p)) {
                 if (lane == 0) atomicOr(&p.ctl->status, ST_DEVTIMEOUT);
                 *status |= ST_DEVTIMEOUT;
@@ -371,12 +415,16 @@ __device__ void rewalk_unite(const Smem &S, const Params &p, uint32_t pbase, int
 // for the last tile, the call's totals; the offset is left in S.clo. In a
 // batch the chain also carries the tile's nt triggers (offset in S.tlo), and a
 // run's first tile records the run's record and trigger offsets.
+// Without `block`, gives up (false, nothing published) when a predecessor's
+// count is not out yet.
 template <bool BATCH>
-__device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr, int nt,
-                               int run, bool run_first) {
+__device__ bool resolve_offset(Smem &S, const Params &p, unsigned seq, long long tl, int nc, long long ntr, int nt,
+                               int run, bool run_first, bool block = true) {
     unsigned st2 = 0;
     longlong2 Ow = make_longlong2(0, 0);
-    if (tl > 0) Ow = lookback_count_warp<BATCH>(p, tl, seq, &st2);
+    bool ready = true;
+    if (tl > 0) Ow = lookback_count_warp<BATCH>(p, tl, seq, &st2, block, &ready);
+    if (!ready) return false;
     if ((threadIdx.x & 31) == 0) {
         if (tl > 0 && tl + 1 != p.hold) {
             __stcg(&p.ts.cpre[tl], Ow.x + (long long)nc);
@@ -402,58 +450,74 @@ __device__ void resolve_offset(Smem &S, const Params &p, unsigned seq, long long
             if (nt_all > p.trig_cap) atomicOr(&p.ctl->status, ST_TRIG_CAP);
         }
     }
+    return true;
 }
 
 // Staged output: a tile's records (in label order) and, in a batch, its
-// trigger times wait in the CTA's staging slot until the CTA's next tile (or
-// the end of the kernel) resolves their offset, when the predecessors' counts
-// are long published; then one warp copies them out, coalesced, eight loads
-// in flight per lane. Called by one whole warp.
+// trigger times wait in a staging slot of the CTA until a later tile of the
+// CTA (or the end of the kernel) resolves their offset, when the
+// predecessors' counts are long published; then one warp copies them out,
+// coalesced, eight loads in flight per lane. The staged tiles form a ring
+// (one entry for a single stream, RING in a batch): the oldest entries go out
+// in order while their offsets resolve; the warp waits for the oldest only
+// when the ring is full (the CTA needs the slot) or with `all` (the kernel's
+// end). Called by one whole warp.
 template <bool BATCH>
-__device__ void flush_pending_warp(Smem &S, const Params &p, unsigned seq) {
-    const long long pt = S.pend_tile;
-    if (pt < 0) return;
+__device__ void flush_ring_warp(Smem &S, const Params &p, unsigned seq, bool all) {
+    constexpr int NP = BATCH ? RING : 1;
     const int lane = threadIdx.x & 31;
-    const int nc = S.pend_ncl, nt = S.pend_ntdc;
-    resolve_offset<BATCH>(S, p, seq, pt, nc, S.pend_ntr, nt, S.pend_run, S.pend_first);
-    __syncwarp();
-    const long long O = S.clo;
-    const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
     constexpr int WPR = (int)(sizeof(tpx_record) / 8);
-    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p.stage + (long long)blockIdx.x * C);
-    if (p.rec64) {   // 64-byte records: the first 8 words of each staged record
-        unsigned long long *d64 = reinterpret_cast<unsigned long long *>(p.clusters) + O * 8;
-        const long long nw = keep * 8;
+    for (;;) {
+        const int cnt = S.pend_count;
+        if (cnt == 0) break;
+        const int slot = S.pend_head;
+        const long long pt = S.pend[slot].tile, ntr = S.pend[slot].ntr;
+        const int nc = S.pend[slot].ncl, nt = S.pend[slot].ntdc, run = S.pend[slot].run;
+        const bool first = S.pend[slot].first, big = S.pend[slot].big;
+        if (!resolve_offset<BATCH>(S, p, seq, pt, nc, ntr, nt, run, first, all || cnt == NP)) break;
+        __syncwarp();
+        const long long O = S.clo;
+        const long long keep = min((long long)nc, max(0LL, p.cl_cap - O));
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(
+            (BATCH && big) ? br_stage(p, slot) : p.stage + ((long long)blockIdx.x * NP + slot) * C);
+        if (p.rec64) {   // 64-byte records: the first 8 words of each staged record
+            unsigned long long *d64 = reinterpret_cast<unsigned long long *>(p.clusters) + O * 8;
+            const long long nw = keep * 8;
+            for (long long w0 = lane; w0 < nw; w0 += 32 * 8) {
+                unsigned long long v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const long long w = w0 + 32 * u;
+                    v[u] = w < nw ? __ldcg(src + (w >> 3) * WPR + (w & 7)) : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (w0 + 32 * u < nw) d64[w0 + 32 * u] = v[u];
+            }
+        }
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
+        const long long nw = p.rec64 ? 0 : keep * WPR;
         for (long long w0 = lane; w0 < nw; w0 += 32 * 8) {
             unsigned long long v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const long long w = w0 + 32 * u;
-                v[u] = w < nw ? __ldcg(src + (w >> 3) * WPR + (w & 7)) : 0ull;
-            }
+            for (int u = 0; u < 8; ++u) v[u] = w0 + 32 * u < nw ? __ldcg(src + w0 + 32 * u) : 0ull;
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-                if (w0 + 32 * u < nw) d64[w0 + 32 * u] = v[u];
+                if (w0 + 32 * u < nw) dst[w0 + 32 * u] = v[u];
         }
+        if (BATCH) {
+            const long long TO = S.tlo;
+            const long long tkeep = min((long long)nt, max(0LL, p.trig_cap - TO));
+            const long long *ts = p.bt.tstage + ((long long)blockIdx.x * NP + slot) * T;
+            for (long long i = lane; i < tkeep; i += 32) p.trig[TO + i] = __ldcg(ts + i);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            S.pend_head = (slot + 1) % NP;
+            S.pend_count = cnt - 1;
+        }
+        __syncwarp();
     }
-    unsigned long long *dst = reinterpret_cast<unsigned long long *>(p.clusters + O);
-    const long long nw = p.rec64 ? 0 : keep * WPR;
-    for (long long w0 = lane; w0 < nw; w0 += 32 * 8) {
-        unsigned long long v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = w0 + 32 * u < nw ? __ldcg(src + w0 + 32 * u) : 0ull;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (w0 + 32 * u < nw) dst[w0 + 32 * u] = v[u];
-    }
-    if (BATCH) {
-        const long long TO = S.tlo;
-        const long long tkeep = min((long long)nt, max(0LL, p.trig_cap - TO));
-        const long long *ts = p.bt.tstage + (long long)blockIdx.x * T;
-        for (long long i = lane; i < tkeep; i += 32) p.trig[TO + i] = __ldcg(ts + i);
-    }
-    __syncwarp();
-    if (lane == 0) S.pend_tile = -1;
 }
 
 // the exact integer moments of one cluster from its member list (Sec. V.C)
@@ -522,6 +586,576 @@ __device__ __forceinline__ int label_rank(const Smem &S, uint32_t lp) {
     return (int)S.lpre[lp >> 5] + __popc(S.lbits[lp >> 5] & ((1u << (lp & 31)) - 1u));
 }
 
+// ------------------------------------------------------------- big ranges
+// A range longer than the range capacity C (in CC mode: a shot of more pixels
+// than a tile holds) stays in the launch. The CTA decodes the whole range
+// into its own global scratch (the tile's unwrap, binning and cut, Sec.
+// IV.A-C), sorts the kept pixels by (shot, time bin, 16-column x stripe)
+// with bins at least dt + 1 ticks wide, and compares each pixel with the
+// pixels of the keys before its own that can hold a neighbour: the previous
+// bin's three stripes around its own, its own bin's stripe to the left, and
+// its own key up to itself. Two adjacent pixels (Sec. V.A: same shot, box
+// neighbours, |dt| within the radius) lie in the same or consecutive bins
+// and stripes, so every adjacent pair is seen once, as in the tile's
+// neighbour pass. Union-find over the sorted order runs in shared
+// memory (16-bit parents, roots linked by a hashed priority). The
+// exact integer moments of each cluster (Sec. V.C) are gathered with
+// warp-aggregated atomics, and the records are staged in label order in the
+// scratch (copied out like a tile's). A range this cannot hold either goes
+// back to the general path with its run: more than BR_L positions, BR_N
+// kept pixels or BR_S shots.
+// 16-bit parents addressed in the shared window (pb: the array's shared
+// address), as the tile's union-find addresses its words
+__device__ __forceinline__ unsigned br_ld(uint32_t pb, unsigned x) {
+    unsigned short v;
+    asm volatile("ld.volatile.shared.u16 %0, [%1];" : "=h"(v) : "r"(pb + 2 * x) : "memory");
+    return v;
+}
+__device__ __forceinline__ void br_st(uint32_t pb, unsigned x, unsigned v) {
+    asm volatile("st.volatile.shared.u16 [%0], %1;" ::"r"(pb + 2 * x), "h"((unsigned short)v) : "memory");
+}
+__device__ __forceinline__ unsigned br_cas(uint32_t pb, unsigned x, unsigned cmp, unsigned v) {
+    unsigned short o;
+    asm volatile("atom.shared.cas.b16 %0, [%1], %2, %3;"
+                 : "=h"(o) : "r"(pb + 2 * x), "h"((unsigned short)cmp), "h"((unsigned short)v) : "memory");
+    return o;
+}
+__device__ __forceinline__ void br_or(uint32_t a, unsigned v) {
+    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned br_find(uint32_t pb, unsigned x) {
+    for (;;) {
+        const unsigned px = br_ld(pb, x);
+        if (px == x) return x;
+        const unsigned g = br_ld(pb, px);
+        if (g == px) return px;
+        br_st(pb, x, g);   // path halving: g is an ancestor of x
+        x = g;
+    }
+}
+// The root of a big-range cluster need not be any particular pixel (its
+// label comes from its moments), so roots are linked by a hashed priority,
+// the lower under the higher: the sorted order puts a cluster's pixels on
+// consecutive slots, and linking by slot would chain them. Links always rise
+// in (priority, slot) order, so the forest stays acyclic.
+__device__ __forceinline__ unsigned br_prio(unsigned x) { return ((x * 0x9E3779B1u) & 0xFFFF0000u) | x; }
+__device__ __forceinline__ void br_unite(uint32_t pb, unsigned a, unsigned b) {
+    for (;;) {
+        a = br_find(pb, a);
+        b = br_find(pb, b);
+        if (a == b) return;
+        const bool a_low = br_prio(a) < br_prio(b);
+        const unsigned child = a_low ? a : b, up = a_low ? b : a;
+        const unsigned old = br_cas(pb, child, child, up);
+        if (old == child) return;
+        if (a_low) a = old; else b = old;   // the child was linked meanwhile
+    }
+}
+
+// The range of the tile at stream position `base` (first trigger packet at
+// f): its cluster count, or -1 with a status bit set when it goes back to
+// the general path. Called by every thread of the CTA after the tile's
+// staging slot is free; writes the labels, local-maximum flags and staged
+// records, and replaces the tile's keep / drop counts by the whole range's.
+#ifdef TPX_PHASE_TIMING
+#define BR_PH(k)                                                                          \
+    do {                                                                                  \
+        const long long ph_now = clock64();                                               \
+        if ((threadIdx.x & 31) == 0) atomicAdd(&S.ph[k], (unsigned long long)(ph_now - br_t)); \
+        br_t = ph_now;                                                                    \
+    } while (0)
+#else
+#define BR_PH(k) do {} while (0)
+#endif
+template <bool BATCH>
+__device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, long long rend, int f,
+                                      bool prev_global) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#ifdef TPX_PHASE_TIMING
+    long long br_t = clock64();
+#endif
+    const long long tp = p.thr_pix, tt = p.thr_tdc;
+    unsigned char *R = reinterpret_cast<unsigned char *>(&S);
+    uint16_t *par = reinterpret_cast<uint16_t *>(R);
+    unsigned *npk = reinterpret_cast<unsigned *>(R + 2 * BR_N);
+    unsigned *bins = npk + BR_N / 32;
+    unsigned *lbits = bins + BR_BINS + 4;
+    uint16_t *lpre = reinterpret_cast<uint16_t *>(lbits + BR_LW);
+    int *sg_n = reinterpret_cast<int *>(lpre + BR_LW);
+    int *sg_lo = sg_n + BR_S, *sg_hi = sg_lo + BR_S, *sg_b0 = sg_hi + BR_S, *sg_w = sg_b0 + BR_S;
+    // misc: [0..2] range-end slots, [3] first pixel, [4] kept, [5] dropped
+    // before a trigger, [6] background, [7] failure bits, [8] clusters, [9] peaks
+    int *misc = sg_w + BR_S;
+    uint64_t *sbuf = reinterpret_cast<uint64_t *>(misc + 16);   // [BR_SB] staged sorted records
+    unsigned char *G = p.big + (size_t)blockIdx.x * BR_STRIDE;
+    uint64_t *g_rec = reinterpret_cast<uint64_t *>(G);
+    uint64_t *g_srec = g_rec + (BR_L + 1);
+    uint16_t *g_spos = reinterpret_cast<uint16_t *>(g_srec + BR_N);
+    BrMom *g_mom = reinterpret_cast<BrMom *>(g_spos + BR_N);
+    const GAgg E = S.E;
+    const uint32_t pb = (uint32_t)__cvta_generic_to_shared(par);      // shared addresses
+    const uint32_t nb_sh = (uint32_t)__cvta_generic_to_shared(npk);
+    const int rx = p.rx, ry = p.ry, dtr = p.dt;
+    __syncthreads();
+    if (tid < 16) misc[tid] = tid < 4 ? INT_MAX : 0;
+    __syncthreads();
+
+    // ---- the range end: the first TDC packet at or past C (the tile
+    // searched the positions below C); four packets per thread per step, the
+    // steps' minima rotating over three slots as in the tile's look-ahead ----
+    int L = 0;
+    bool term = false;
+    {
+        constexpr int STEP = 4 * NT;
+        long long q0 = C;
+        for (int k = 0;; ++k) {
+            const long long lim = min((long long)BR_L, rend - base);
+            if (q0 >= lim) { L = (int)lim; break; }
+            if (tid == 0) misc[(k + 1) % 3] = INT_MAX;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long q = q0 + u * NT + tid;
+                if (q < lim && (__ldcg(p.pk + base + q) >> 60) == 0x6u) atomicMin(&misc[k % 3], (int)q);
+            }
+            __syncthreads();
+            const int lf = misc[k % 3];
+            if (lf != INT_MAX) { L = lf + 1; term = true; break; }
+            q0 += STEP;
+        }
+    }
+    // not terminated before the position limit while the run goes on
+    if (!term && base + L < rend) { if (tid == 0) atomicOr(&S.status, ST_CAPACITY); return -1; }
+
+    // ---- walk 2 over [0, L): wrap steps and TDC counts per contiguous chunk ----
+    const int kpd = (L + NT - 1) / NT;
+    const int p0 = tid * kpd;
+    int ntd = 0, jp = 0;
+    {
+        int lpx = -1, fpx = INT_MAX;
+        long long lr = 0;
+        for (int j = 0; j < kpd; ++j) {
+            const int q = p0 + j;
+            if (q >= L) break;
+            const uint64_t w = __ldg(p.pk + base + q);
+            const unsigned h = (unsigned)(w >> 60);
+            if (h == 0xBu) {
+                const long long r = pix_raw(w);
+                if (lpx >= 0) jp += (int)jump(r - lr, tp); else fpx = q;
+                lpx = q;
+                lr = r;
+            } else if (h == 0x6u) {
+                ++ntd;
+            }
+        }
+        if (lpx >= 0) {
+            for (int q = p0 + kpd; q < L; ++q) {
+                const uint64_t w = __ldg(p.pk + base + q);
+                if ((w >> 60) == 0xBu) { jp += (int)jump(pix_raw(w) - lr, tp); break; }
+            }
+        }
+        const int fw = (int)__reduce_min_sync(0xffffffffu, (unsigned)fpx);
+        if (lane == 0 && fw != INT_MAX) atomicMin(&misc[3], fw);
+    }
+    unsigned pk_tot;
+    const unsigned pk_ex = block_scan_vadd2(S, ((unsigned)ntd << 16) | ((unsigned)jp & 0xFFFFu), &pk_tot);
+    const int li0 = (int)(pk_ex >> 16);
+    const int nseg = (int)(pk_tot >> 16);
+    const int jp_ex = (int)(short)(pk_ex & 0xFFFFu);
+    if (nseg > BR_S || nseg > MAXSEG) { if (tid == 0) atomicOr(&S.status, ST_CAPACITY); return -1; }
+    if (tid == 0) {
+        const int fp = misc[3];
+        S.j0 = (fp != INT_MAX && E.pix.n > 0) ? jump(pix_raw(__ldcg(p.pk + base + fp)) - E.pix.last, tp) : 0;
+    }
+    if (ntd) {
+        int li = li0;
+        for (int j = 0; j < kpd; ++j) {
+            const int q = p0 + j;
+            if (q >= L) break;
+            if ((__ldg(p.pk + base + q) >> 60) != 0x6u) continue;
+            S.tdc_pos[li] = (uint16_t)q;
+            ++li;
+        }
+    }
+    for (int s = tid; s < nseg; s += NT) { sg_n[s] = 0; sg_lo[s] = INT_MAX; sg_hi[s] = INT_MIN; }
+    __syncthreads();
+    // the trigger times (one warp, a scan of the TDC wrap steps)
+    if (tid < 32) {
+        bool has = E.tdc.n > 0;
+        long long last = E.tdc.last, ep = E.tdc.sum, t_last = 0;
+        for (int i0 = 0; i0 < nseg; i0 += 32) {
+            const int i = i0 + lane;
+            long long r = 0;
+            if (i < nseg) r = tdc_raw(__ldcg(p.pk + base + S.tdc_pos[i]));
+            const long long rp = __shfl_up_sync(0xffffffffu, r, 1);
+            int st = 0;
+            if (i < nseg && (lane > 0 || has)) st = (int)jump(r - (lane > 0 ? rp : last), tt);
+            int inc = st;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            const long long t = r + (ep + inc) * kTdcPeriod;
+            const long long tp_ = __shfl_up_sync(0xffffffffu, t, 1);
+            if (i < nseg) {
+                S.tdc_t[i] = t;
+                if ((lane > 0 || i0 > 0) && t < (lane > 0 ? tp_ : t_last)) atomicOr(&p.ctl->status, ST_TRIG_ORDER);
+            }
+            const int lastl = min(31, nseg - 1 - i0);
+            ep += __shfl_sync(0xffffffffu, inc, lastl);
+            last = __shfl_sync(0xffffffffu, r, lastl);
+            t_last = __shfl_sync(0xffffffffu, t, lastl);
+            has = true;
+        }
+    }
+    __syncthreads();
+
+    BR_PH(20);
+    // ---- walk 4 over [0, L): shot, cut, timewalk, packed record per position
+    // (the tile's rule), and each shot's kept count and ToF span ----
+    {
+        long long ep = E.pix.sum + S.j0 + jp_ex;
+        bool has = false;
+        long long last = 0;
+        int seg = li0 - 1;
+        const long long t_prev_global = E.tdc.last + E.tdc.sum * kTdcPeriod;
+        int c_keep = 0, c_pre = 0, c_bg = 0;
+        bool exc = false;
+        int cs = -1, cn = 0, clo = INT_MAX, chi = INT_MIN;   // the current shot's running stats
+        for (int j = 0; j < kpd; ++j) {
+            const int q = p0 + j;
+            if (q >= L) break;
+            const uint64_t w = __ldg(p.pk + base + q);
+            const unsigned h = (unsigned)(w >> 60);
+            uint64_t rec = INVALID;
+            if (h == 0x6u) {
+                ++seg;
+            } else if (h == 0xBu) {
+                const long long r = pix_raw(w);
+                if (has) ep += jump(r - last, tp);
+                has = true;
+                last = r;
+                const long long t = r + ep * kPixPeriod;
+                if (seg < 0) {
+                    if (!prev_global) ++c_pre;
+                } else if (seg < nseg) {
+                    const long long t_lo = S.tdc_t[seg];
+                    const bool has_hi = seg + 1 < nseg;
+                    int verdict;                      // 0 keep, 1 bg, 2 pre, 3 undecidable here
+                    if (has_hi && t >= S.tdc_t[seg + 1]) verdict = 3;
+                    else if (t >= t_lo) verdict = (t - t_lo > p.tof_max) ? 1 : 0;
+                    else {
+                        const bool hp = seg > 0 || prev_global;
+                        const long long tprev = seg > 0 ? S.tdc_t[seg - 1] : t_prev_global;
+                        if (!hp) verdict = 2;
+                        else if (t >= tprev) verdict = (t - tprev > p.tof_max) ? 1 : 3;
+                        else verdict = 3;
+                    }
+                    if (verdict == 0) {
+                        const int tot = pix_tot(w);
+                        const long long tc = t - (p.lut ? (long long)p.lut[tot] : 0LL);
+                        const int tofb = (int)(tc - t_lo + kTofBias);
+                        rec = mkrec((uint32_t)tofb, (uint32_t)seg, (uint32_t)tot, (uint32_t)pix_x(w), (uint32_t)pix_y(w));
+                        ++c_keep;
+                        if (seg != cs) {
+                            if (cs >= 0) { atomicAdd(&sg_n[cs], cn); atomicMin(&sg_lo[cs], clo); atomicMax(&sg_hi[cs], chi); }
+                            cs = seg; cn = 0; clo = INT_MAX; chi = INT_MIN;
+                        }
+                        ++cn;
+                        clo = min(clo, tofb);
+                        chi = max(chi, tofb);
+                    } else if (verdict == 1) ++c_bg;
+                    else if (verdict == 2) ++c_pre;
+                    else exc = true;
+                }
+            }
+            g_rec[q] = rec;
+        }
+        if (cs >= 0) { atomicAdd(&sg_n[cs], cn); atomicMin(&sg_lo[cs], clo); atomicMax(&sg_hi[cs], chi); }
+        c_keep = (int)warp_sum((unsigned long long)c_keep);
+        c_pre = (int)warp_sum((unsigned long long)c_pre);
+        c_bg = (int)warp_sum((unsigned long long)c_bg);
+        if (lane == 0) {
+            atomicAdd(&misc[4], c_keep);
+            atomicAdd(&misc[5], c_pre);
+            atomicAdd(&misc[6], c_bg);
+        }
+        if (exc) atomicOr(&misc[7], (int)ST_EXCEPTION);
+    }
+    __syncthreads();
+    const int N = misc[4];
+    if (misc[7] || N > BR_N) {
+        if (tid == 0) atomicOr(&S.status, misc[7] ? (unsigned)misc[7] : ST_CAPACITY);
+        return -1;
+    }
+
+    BR_PH(21);
+    // ---- time bins: each shot gets a share of the bins by its kept count,
+    // each bin at least dt + 1 ticks wide (one warp); a key is a (bin,
+    // stripe) pair ----
+    const int NS = rx <= 256 / BR_NS ? BR_NS : 1;
+    const int TB = BR_BINS / NS;   // time bins over all shots
+    if (wid == 0) {
+        constexpr int SPL = BR_S / 32;   // shots per lane
+        int nb[SPL], tot = 0;
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            const int s = lane * SPL + k;
+            const int n = s < nseg ? sg_n[s] : 0;
+            nb[k] = s < nseg ? (n > 0 ? 1 + (int)(((long long)(TB - nseg) * n) / N) : 1) : 0;
+            tot += nb[k];
+        }
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        int b0 = incl - tot;
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+            const int s = lane * SPL + k;
+            if (s < nseg) {
+                sg_b0[s] = b0;
+                const long long span = sg_n[s] > 0 ? (long long)sg_hi[s] - sg_lo[s] + 1 : 1;
+                sg_w[s] = (int)max((long long)dtr + 1, (span + nb[k] - 1) / nb[k]);
+                if (sg_n[s] == 0) sg_lo[s] = 0;
+            }
+            b0 += nb[k];
+        }
+    }
+    for (int b = tid; b < BR_BINS; b += NT) bins[b] = 0u;
+    __syncthreads();
+    auto bin_of = [&](uint64_t r) -> int {
+        const int s = r_seg(r);
+        return (sg_b0[s] + (r_tof(r) - sg_lo[s]) / sg_w[s]) * NS + (NS > 1 ? r_x(r) / (256 / BR_NS) : 0);
+    };
+    // ---- counting sort of the kept pixels by bin ----
+    for (int q = tid; q < L; q += NT) {
+        const uint64_t r = g_rec[q];
+        if (r != INVALID) atomicAdd(&bins[bin_of(r)], 1u);
+    }
+    __syncthreads();
+    {
+        constexpr int BPT = BR_BINS / NT;   // bins per thread, contiguous
+        unsigned c[BPT], s = 0;
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) { c[k] = bins[tid * BPT + k]; s += c[k]; }
+        int total;
+        unsigned run = (unsigned)block_scan_int(S, (int)s, &total);
+#pragma unroll
+        for (int k = 0; k < BPT; ++k) { bins[tid * BPT + k] = run; run += c[k]; }
+    }
+    __syncthreads();
+    for (int q = tid; q < L; q += NT) {
+        const uint64_t r = g_rec[q];
+        if (r == INVALID) continue;
+        const unsigned slot = atomicAdd(&bins[bin_of(r)], 1u);
+        if (!TPX_IN(slot, N)) continue;
+        g_srec[slot] = r;
+        g_spos[slot] = (uint16_t)q;
+    }
+    // bins[b] is now the end of bin b (the start of bin b + 1)
+    for (int i = tid; i < N; i += NT) par[i] = (uint16_t)i;
+    for (int w = tid; w < BR_N / 32; w += NT) npk[w] = 0u;
+    for (int w = tid; w < BR_LW; w += NT) lbits[w] = 0u;
+    __syncthreads();
+
+    BR_PH(22);
+    // ---- neighbour pass: one thread per pixel of the sorted order scans
+    // the keys that can hold its earlier neighbours, checks the box rule
+    // (Sec. V.A), updates the local-maximum flags (Sec. V.B, equal ToT goes
+    // to the later pixel) and unites. The sorted records are read through
+    // shared memory: BR_CH pixels at a time, staged with the records before
+    // them from the start of the first one's previous time bin (or straight
+    // from the scratch when those do not fit) ----
+    for (int a = 0; a < N; a += BR_CH) {
+        const int e = min(N, a + BR_CH);
+        int lo;
+        {
+            const uint64_t ra = g_srec[a];
+            const int s = r_seg(ra);
+            const int tbin = sg_b0[s] + (r_tof(ra) - sg_lo[s]) / sg_w[s];
+            const int k0 = (tbin > sg_b0[s] ? tbin - 1 : tbin) * NS;
+            lo = k0 > 0 ? (int)bins[k0 - 1] : 0;
+        }
+        const bool fits = e - lo <= BR_SB;
+        if (fits)
+            for (int j = lo + tid; j < e; j += NT) sbuf[j - lo] = g_srec[j];
+        __syncthreads();
+        auto rec_at = [&](int j) -> uint64_t { return fits ? sbuf[j - lo] : g_srec[j]; };
+        for (int i = a + tid; i < e; i += NT) {
+            const uint64_t ri = rec_at(i);
+            const int s = r_seg(ri), x = r_x(ri), y = r_y(ri), tb = r_tof(ri), tot = r_tot(ri);
+            const int tbin = sg_b0[s] + (tb - sg_lo[s]) / sg_w[s];
+            const int st = NS > 1 ? x / (256 / BR_NS) : 0;
+            const int key = tbin * NS + st;
+            int pos = -1;   // read on the first ToT tie
+            bool dim = false;
+            for (int db = tbin > sg_b0[s] ? -1 : 0; db <= 0; ++db) {
+                for (int ds = -1; ds <= 1; ++ds) {
+                    const int s2 = st + ds;
+                    if (s2 < 0 || s2 >= NS) continue;
+                    const int k2 = (tbin + db) * NS + s2;
+                    if (k2 > key) continue;
+                    const int j1 = k2 == key ? i : (int)bins[k2];
+                    for (int j = k2 > 0 ? (int)bins[k2 - 1] : 0; j < j1; ++j) {
+                        const uint64_t rj = rec_at(j);
+                        const int dx = r_x(rj) - x, dy = r_y(rj) - y;
+                        if (dx < -rx || dx > rx || dy < -ry || dy > ry || !within(r_tof(rj) - tb, dtr)) continue;
+                        const int tj = r_tot(rj);
+                        if (tj == tot && pos < 0) pos = g_spos[i];
+                        if (tj > tot || (tj == tot && (int)g_spos[j] > pos)) dim = true;
+                        else br_or(nb_sh + 4 * (j >> 5), 1u << (j & 31));
+                        br_unite(pb, (unsigned)i, (unsigned)j);
+                    }
+                }
+            }
+            if (dim) br_or(nb_sh + 4 * (i >> 5), 1u << (i & 31));
+        }
+        __syncthreads();
+    }
+    BR_PH(23);
+    // compress: every pixel points to its root
+    for (int i = tid; i < N; i += NT) br_st(pb, (unsigned)i, br_find(pb, (unsigned)i));
+    __syncthreads();
+    // roots: their moment records cleared, counted
+    {
+        int k = 0;
+        for (int i = tid; i < N; i += NT) {
+            if (par[i] != i) continue;
+            ++k;
+            unsigned long long *m = reinterpret_cast<unsigned long long *>(&g_mom[i]);
+#pragma unroll
+            for (int u = 0; u < 5; ++u) __stcg(m + u, u == 4 ? ~0ull : 0ull);
+            __stcg(m + 5, 0ull);
+        }
+        k = (int)warp_sum((unsigned long long)k);
+        if (lane == 0 && k) atomicAdd(&misc[8], k);
+    }
+    __syncthreads();
+    const int K = misc[8];
+
+    BR_PH(24);
+    // ---- moments: a warp's lanes sharing a root add up among themselves, one
+    // lane per root adds to its record ----
+    for (int i0 = wid * 32; i0 < N; i0 += NT) {
+        const int i = i0 + lane;
+        const bool v = i < N;
+        const unsigned r = v ? par[i] : 0xFFFFFFFFu;
+        const uint64_t ri = v ? g_srec[i] : 0ull;
+        const unsigned pos = v ? g_spos[i] : 0u;
+        const unsigned tot = (unsigned)r_tot(ri), tofb = (unsigned)r_tof(ri);
+        const unsigned ux = tot * (unsigned)r_x(ri), uy = tot * (unsigned)r_y(ri);
+        const unsigned long long utt = (unsigned long long)tot * tofb;
+        const bool pk = v && !((npk[i >> 5] >> (i & 31)) & 1u);
+        unsigned act = __ballot_sync(0xffffffffu, v);
+        unsigned c_pk = 0;
+        while (act) {
+            const int ld = __ffs(act) - 1;
+            const unsigned r0 = __shfl_sync(0xffffffffu, r, ld);
+            const bool mine = v && r == r0;
+            const unsigned grp = __ballot_sync(0xffffffffu, mine);
+            const unsigned a_tot = __reduce_add_sync(0xffffffffu, mine ? tot : 0u);
+            const unsigned a_x = __reduce_add_sync(0xffffffffu, mine ? ux : 0u);
+            const unsigned a_y = __reduce_add_sync(0xffffffffu, mine ? uy : 0u);
+            const unsigned a_tl = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(utt & 0xFFFFFFu) : 0u);
+            const unsigned a_th = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(utt >> 24) : 0u);
+            const unsigned m_t = __reduce_min_sync(0xffffffffu, mine ? tofb : 0xFFFFFFFFu);
+            const unsigned m_p = __reduce_min_sync(0xffffffffu, (mine && tofb == m_t) ? pos : 0xFFFFFFFFu);
+            const unsigned n_pk = __popc(__ballot_sync(0xffffffffu, mine && pk));
+            if (lane == ld && TPX_IN(r0, N)) {
+                BrMom &M = g_mom[r0];
+                atomicAdd(&M.s_tot, (unsigned long long)a_tot);
+                atomicAdd(&M.s_x, (unsigned long long)a_x);
+                atomicAdd(&M.s_y, (unsigned long long)a_y);
+                atomicAdd(&M.s_tt, ((unsigned long long)a_th << 24) + a_tl);
+                atomicMin(&M.best, ((unsigned long long)m_t << 16) | m_p);
+                atomicAdd(&M.n, (unsigned)__popc(grp));
+                atomicAdd(&M.npk, n_pk);
+            }
+            c_pk += n_pk;
+            act &= ~grp;
+        }
+        if (lane == 0 && c_pk) atomicAdd(&misc[9], (int)c_pk);
+    }
+    __syncthreads();
+    BR_PH(25);
+    // ---- the labels (each cluster's earliest pixel in (time, position)
+    // order) marked in the bitmap, then their ranks ----
+    for (int i = tid; i < N; i += NT) {
+        if (par[i] != i) continue;
+        const unsigned lp = (unsigned)(__ldcg(&g_mom[i].best) & 0xFFFFu);
+        atomicOr(&lbits[lp >> 5], 1u << (lp & 31));
+    }
+    __syncthreads();
+    {
+        constexpr int WPT = BR_LW / NT;
+        unsigned c[WPT], s = 0;
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) { c[k] = (unsigned)__popc(lbits[tid * WPT + k]); s += c[k]; }
+        int total;
+        unsigned run = (unsigned)block_scan_int(S, (int)s, &total);
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) { lpre[tid * WPT + k] = (uint16_t)run; run += c[k]; }
+    }
+    __syncthreads();
+    // ---- records, staged in label order ----
+    tpx_record *dst = br_stage(p, (S.pend_head + S.pend_count) % RING);   // the ring entry this tile takes
+    for (int i = tid; i < N; i += NT) {
+        if (par[i] != i) continue;
+        const unsigned long long *m = reinterpret_cast<const unsigned long long *>(&g_mom[i]);
+        const long long s_tot = (long long)__ldcg(m), s_x = (long long)__ldcg(m + 1), s_y = (long long)__ldcg(m + 2);
+        const long long s_tt = (long long)__ldcg(m + 3);
+        const unsigned long long best = __ldcg(m + 4), nn = __ldcg(m + 5);
+        const unsigned lp = (unsigned)(best & 0xFFFFu);
+        const int tofb0 = (int)(best >> 16);
+        const int k = (int)lpre[lp >> 5] + __popc(lbits[lp >> 5] & ((1u << (lp & 31)) - 1u));
+        if (!TPX_IN(k, K) || !TPX_IN(lp, L)) continue;
+        const int seg = r_seg(g_rec[lp]);
+        const long long tofc0 = (long long)tofb0 - kTofBias;
+        tpx_record o;
+        o.label = p.idx_base + base + lp;
+        o.shot = E.tdc.n + seg;
+        o.t0 = S.tdc_t[seg] + tofc0;
+        o.s_tot = s_tot; o.s_x = s_x; o.s_y = s_y;
+        o.s_t = s_tt - (long long)tofb0 * s_tot;
+        o.n = (int)(nn & 0xFFFFFFFFu);
+        o.n_peaks = (int)(nn >> 32);
+        com_from_moments(o.s_x, o.s_y, o.s_t, s_tot, tofc0, &o.x, &o.y, &o.tof);
+        dst[k] = o;
+    }
+    // ---- per-packet outputs over the range's label span ----
+    if (p.labels || p.labels32 || p.is_peak) {
+        for (int i = tid; i < N; i += NT) {
+            const long long q = g_spos[i];
+            const unsigned lp = (unsigned)(__ldcg(&g_mom[par[i]].best) & 0xFFFFu);
+            const uint8_t pk = ((npk[i >> 5] >> (i & 31)) & 1u) ? 0 : 1;
+            if (!TPX_IN(base + q, rend)) continue;
+            if (p.labels) p.labels[base + q] = p.idx_base + base + lp;
+            else if (p.labels32) p.labels32[base + q] = (int)(p.idx_base - p.lab32_base + base + lp);
+            if (p.is_peak) p.is_peak[base + q] = pk;
+        }
+        const int W0 = prev_global ? f : 0, W1 = term ? L - 1 : L;
+        for (int q = W0 + tid; q < W1; q += NT) {
+            if (g_rec[q] != INVALID || !TPX_IN(base + q, rend)) continue;
+            if (p.labels) p.labels[base + q] = -1LL;
+            else if (p.labels32) p.labels32[base + q] = -1;
+            if (p.is_peak) p.is_peak[base + q] = 0;
+        }
+    }
+    __syncthreads();
+    BR_PH(26);
+    if (tid == 0) {
+        S.cnt[C_KEPT] = (unsigned long long)misc[4];
+        S.cnt[C_DROP_PRE] = (unsigned long long)misc[5];
+        S.cnt[C_DROP_BG] = (unsigned long long)misc[6];
+        S.cnt[C_PEAKS] += (unsigned long long)misc[9];
+    }
+    __syncthreads();
+    return K;
+}
+
 // ------------------------------------------------------------------- kernel
 template <int MODE, bool STAGED, bool BATCH>
 __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
@@ -531,8 +1165,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
     const long long tp = p.thr_pix, tt = p.thr_tdc;
     const unsigned seq = p.seq & 0x3FFFFFFFu;
     const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(S.parent);
+    // ranges past the capacity go through the big-range path (CC mode, batches)
+    constexpr bool BIGR = BATCH && STAGED && MODE == TPX_MODE_CC;
+    constexpr int NP = BATCH ? RING : 1;   // staged tiles a CTA may hold
     if (tid == 0) {
-        S.pend_tile = -1;
+        S.pend_head = 0;
+        S.pend_count = 0;
         S.tile = atomicAdd(&p.ctl->tile_counter, 1u);
         S.first_tdc = INT_MAX;
         S.first_pix = INT_MAX;
@@ -574,7 +1212,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         }
         if (tile >= p.n_tiles) {
             if (STAGED) {
-                if (tid < 32) flush_pending_warp<BATCH>(S, p, seq);
+                if (tid < 32) flush_ring_warp<BATCH>(S, p, seq, true);
                 __syncthreads();
                 if (tid == 0 && S.status) atomicOr(&p.ctl->status, S.status);
             }
@@ -689,7 +1327,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     L += chunk;
                 }
             }
-            if (!term && base + L < rend && tid == 0) atomicOr(&S.status, ST_CAPACITY);
+            // a range past the capacity: the big-range path, or its run goes back
+            if (!term && base + L < rend && tid == 0) atomicOr(&S.status, (BIGR && p.big) ? ST_BIG : ST_CAPACITY);
         }
 
         TPX_PH(2);
@@ -864,7 +1503,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         TPX_PH(5);
         // a batch tile whose range the tiles cannot hold: its run is redone by
         // the general path, so it clusters nothing (its counts still flow)
-        const bool skip = BATCH && (S.status & (ST_CAPACITY | ST_EXCEPTION)) != 0;
+        // (a big range clusters nothing here either: it has a path of its own)
+        const bool skip = BATCH && (S.status & (ST_CAPACITY | ST_EXCEPTION | ST_BIG)) != 0;
+        // a big range: its path runs before the previous tile is copied out
+        // (that copy may wait for other CTAs' big ranges)
+        const bool big_tile = BIGR && (S.status & ST_BIG) && !(S.status & (ST_CAPACITY | ST_EXCEPTION));
         // the range this CTA owns: [R0, R1)
         const int R0 = (f == INT_MAX || skip) ? 0 : f;
         const int R1 = (f == INT_MAX || skip) ? 0 : (term ? L - 1 : L);
@@ -1089,7 +1732,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 constexpr int NWALK = NT - 32;
                 Moments held{0, 0, 0, 0, 0, 0, 0, 0};
                 if (tid >= NWALK) {
-                    flush_pending_warp<BATCH>(S, p, seq);
+                    flush_ring_warp<BATCH>(S, p, seq, false);
                 } else {
                     for (int i = tid; i < ncl; i += NWALK) {
                         if (!TPX_IN(i, C)) break;
@@ -1125,7 +1768,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                     }
                 }
                 __syncthreads();
-                tpx_record *dst = p.stage + (long long)blockIdx.x * C;
+                TPX_PH(19);
+                tpx_record *dst = p.stage + ((long long)blockIdx.x * NP + (S.pend_head + S.pend_count) % NP) * C;
                 if (tid < NWALK && tid < ncl && held.n > 0) {
                     const int k = label_rank(S, held.best_lo);
                     if (TPX_IN(k, C)) put_record(dst + k, held, S, p, base, E.tdc.n);
@@ -1190,6 +1834,20 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 }
             }
         }
+        bool big_done = false;   // this tile's records wait in the big-range scratch
+        if constexpr (BIGR) {
+            // a big range takes its own path once the staging slot is free
+            // (the previous tile's records were copied out above)
+            if (big_tile) {
+                const int k = big_range<BATCH>(S, p, base, rend, f, prev_global);
+                ncl = k > 0 ? k : 0;
+                big_done = k >= 0;
+                TPX_PH(17);
+                if (tid < 32) flush_ring_warp<BATCH>(S, p, seq, false);
+                __syncthreads();
+                TPX_PH(18);
+            }
+        }
 
         TPX_PH(13);
         // ---- record offsets: publish this tile's count now, look back later ----
@@ -1209,10 +1867,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         // offset after an inline look-back
         auto record_target = [&](long long *lim) -> tpx_record * {
             if (STAGED) {
-                if (tid < 32) flush_pending_warp<BATCH>(S, p, seq);
+                if (tid < 32) flush_ring_warp<BATCH>(S, p, seq, false);
                 __syncthreads();   // the peak list is complete
                 *lim = C;
-                return p.stage + (long long)blockIdx.x * C;
+                return p.stage + ((long long)blockIdx.x * NP + (S.pend_head + S.pend_count) % NP) * C;
             }
             if (tid < 32) resolve_offset<false>(S, p, seq, tile, ncl, ntr_here, 0, 0, false);
             __syncthreads();
@@ -1345,18 +2003,28 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
         TPX_PH(14);
         if (BATCH) {   // this tile's trigger times wait with its records
             const int nt = min((int)S.cnt[C_TDCS], MAXSEG);
-            long long *ts = p.bt.tstage + (long long)blockIdx.x * T;
+            long long *ts = p.bt.tstage + ((long long)blockIdx.x * NP + (S.pend_head + S.pend_count) % NP) * T;
             for (int i = tid; i < nt; i += NT) ts[i] = S.tdc_t[i];
+            __syncthreads();   // every thread has its slot before the tile joins the ring
         }
         if (tid == 0) {
             S.cnt[C_CLUSTERS] = (unsigned long long)ncl;
             if (STAGED) {
-                S.pend_tile = tile;
-                S.pend_ncl = ncl;
-                S.pend_ntr = ntr_here;
-                S.pend_ntdc = (int)S.cnt[C_TDCS];
-                S.pend_run = run;
-                S.pend_first = tile == tile0;
+                // a tile with nothing to write (no records, no triggers; not
+                // a run's first tile nor the call's last) needs no offset: its
+                // count is published, and the successors' look-backs add it up
+                const bool first = tile == tile0;
+                if (ncl != 0 || S.cnt[C_TDCS] != 0 || (BATCH && first) || tile == p.n_tiles - 1) {
+                    const int e = (S.pend_head + S.pend_count) % NP;
+                    S.pend[e].tile = tile;
+                    S.pend[e].ncl = ncl;
+                    S.pend[e].ntr = ntr_here;
+                    S.pend[e].ntdc = (int)S.cnt[C_TDCS];
+                    S.pend[e].run = run;
+                    S.pend[e].first = first;
+                    S.pend[e].big = big_done;
+                    S.pend_count += 1;
+                }
             }
         }
         __syncthreads();
@@ -1376,7 +2044,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_kernel(const Params p) {
                 __ldcg(reinterpret_cast<const long long *>(&p.ts.pre[S.next_tile]) + tid);
         if (tid == 0) {
             S.tile = S.next_tile;
-            unsigned st = S.status;
+            unsigned st = S.status & ~ST_BIG;
             if (BATCH && (st & (ST_CAPACITY | ST_EXCEPTION))) {   // only this run is redone
                 p.bt.run_failed[run] = 1u;
                 st = (st & ~(ST_CAPACITY | ST_EXCEPTION)) | ST_RUN_REDO;

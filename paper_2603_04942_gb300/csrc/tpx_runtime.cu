@@ -504,12 +504,18 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     if (grid > n_tiles) grid = n_tiles;
     if (grid < 1) return TPX_EINVAL;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    // CC mode: a range past the capacity goes through the big-range path,
+    // with global scratch per CTA of the grid
+    const size_t big_bytes = c->cfg.mode == TPX_MODE_CC ? (size_t)grid * tpxk::fused_big_scratch_bytes(geo) : 0;
+    // a batch CTA holds up to kBatchRing staged tiles (records and triggers)
+    constexpr int64_t RG = tpxk::kBatchRing;
+    const size_t stage_bytes = sizeof(tpx_record) * (size_t)(grid * RG * C);
     // device scratch of the batch
     auto &B = c->batch;
     const size_t need_dev = al(4 * (size_t)n_tiles) + al(8 * (size_t)n_runs) + al(8 * (size_t)(n_runs + 1)) +
-                            al(4 * (size_t)n_runs) + 4 * al(8 * (size_t)n_tiles) + al(8 * (size_t)(grid * T)) +
+                            al(4 * (size_t)n_runs) + 4 * al(8 * (size_t)n_tiles) + al(8 * (size_t)(grid * T * RG)) +
                             al(tpxk::unwrap_prepass_scratch_bytes(n_tiles)) + al(4 * (size_t)n_tiles) +
-                            2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles);
+                            2 * al(sizeof(tpxk::GAgg) * (size_t)n_tiles) + al(big_bytes) + al(stage_bytes);
     const size_t need_host = 8 * (size_t)(n_runs + 1) + 8 * (size_t)n_runs + 4 * (size_t)n_tiles + 64;
     // a call captured into a CUDA graph (relaxed capture mode) gets its own
     // device tables and pinned host tables, kept for the graph's replays
@@ -565,11 +571,13 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     bt.tcpre = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
     B.ts.cagg = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
     B.ts.cpre = reinterpret_cast<long long *>(take(8 * (size_t)n_tiles));
-    bt.tstage = reinterpret_cast<long long *>(take(8 * (size_t)(grid * T)));
+    bt.tstage = reinterpret_cast<long long *>(take(8 * (size_t)(grid * T * RG)));
     B.ts.blk = reinterpret_cast<tpxk::GAgg *>(take(tpxk::unwrap_prepass_scratch_bytes(n_tiles)));
     B.ts.cflags = reinterpret_cast<unsigned *>(take(4 * (size_t)n_tiles));
     B.ts.agg = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg) * (size_t)n_tiles));
     B.ts.pre = reinterpret_cast<tpxk::GAgg *>(take(sizeof(tpxk::GAgg) * (size_t)n_tiles));
+    unsigned char *big = big_bytes ? reinterpret_cast<unsigned char *>(take(big_bytes)) : nullptr;
+    tpx_record *bstage = reinterpret_cast<tpx_record *>(take(stage_bytes));
     bt.run_rec_off = reinterpret_cast<long long *>(d_run_clusters);
     bt.run_trig_off = reinterpret_cast<long long *>(d_run_trig);
     bt.n_runs = n_runs;
@@ -630,8 +638,9 @@ int tpx_process_batch(tpx_ctx *c, const uint64_t *d_packets, const int64_t *h_ru
     p.seq = c->seq;
     p.ts = B.ts;
     p.ctl = c->ctl;
-    p.stage = c->stage;
+    p.stage = bstage;
     p.bt = bt;
+    p.big = big;
     cudaEvent_t *kte = ktime_begin(c, s);
     if (ckr(tpxk::launch_fused(p, c->cfg.mode, geo, (int)grid, s, kte ? kte[1] : nullptr))) return TPX_ECUDA;
     ktime_end(c, kte, s);

@@ -1,8 +1,10 @@
 """Batched runs in one launch (tpx_process_batch) against the oracle run on
 each run alone: every run is a stream of its own; records and triggers come
-run after run with per-run offsets; runs the tiles cannot hold (one shot
-longer than a range) are redone exactly; empty runs, one-packet runs, runs
-starting at odd packets and runs crossing the pixel wrap are covered."""
+run after run with per-run offsets; in CC mode a shot longer than a tile's
+range stays in the launch (the big-range path), and runs even that cannot
+hold (a range past 65,535 positions; PAPER mode) are redone exactly; empty
+runs, one-packet runs, runs starting at odd packets and runs crossing the
+pixel wrap are covered."""
 import numpy as np
 import pytest
 
@@ -15,25 +17,31 @@ from streams import StreamBuilder
 pytestmark = pytest.mark.gpu
 
 
-def _long_shot_run(rng, pixels=9000):
+def _long_shot_run(rng, pixels=9000, spread=50_000):
+    """Three shots; the middle one holds `pixels` pixels at random places,
+    their ToF spread over `spread` ticks (the first shot's tile range holds
+    two shots)."""
     b = StreamBuilder()
     t = 50_000_000
     for s in range(3):
         b.tdc(t + s * 640_000)
         for _ in range(pixels if s == 1 else 300):
             b.pix(rng.integers(0, 256), rng.integers(0, 256), rng.integers(1, 400),
-                  t + s * 640_000 + 800 + rng.integers(0, 50_000))
+                  t + s * 640_000 + 800 + rng.integers(0, spread))
     return b.packets()
 
 
-def make_batch(n_runs=20, seed=5, long_shot=True):
+BEYOND_BIG = 66_000   # pixels of a shot past the big-range path's 65,535 positions
+
+
+def make_batch(n_runs=20, seed=5, long_shot=True, long_pixels=9000):
     runs = [synth.generate(p)[0] for p in synth.batched(n_runs=n_runs, seed=seed, shots_hi=150, particles_hi=40)]
     rng = np.random.default_rng(seed)
     runs.insert(3, np.zeros(0, np.uint64))                 # an empty run
     runs.insert(5, runs[4][:1].copy())                     # a one-packet run (odd offsets after it)
     runs.insert(8, runs[7][: 2 * 4096 + 3].copy())         # a run cut mid-shot
     if long_shot:
-        runs.insert(11, _long_shot_run(rng))               # needs the general path
+        runs.insert(11, _long_shot_run(rng, long_pixels))  # a shot past a tile's range
     offs = np.zeros(len(runs) + 1, np.int64)
     offs[1:] = np.cumsum([r.size for r in runs])
     pk = np.concatenate(runs) if offs[-1] else np.zeros(0, np.uint64)
@@ -73,19 +81,20 @@ def check_against_oracle(g, pk, offs, mode=0):
 def test_batch_matches_each_run_alone(mode):
     pk, offs = make_batch()
     g = run_batch(pk, offs, mode=mode)
-    assert g["counters"]["redone"] == 1          # the long-shot run
+    # the long-shot run: the big-range path in CC mode, the general path in PAPER mode
+    assert g["counters"]["redone"] == (0 if mode == 0 else 1)
     check_against_oracle(g, pk, offs, mode)
 
 
 def test_several_redone_runs_share_one_clustering_pass():
-    """Three runs with shots longer than a range, between ordinary runs: they
-    are redone together (shots kept apart per run) and spliced back in run
-    order, with per-packet labels."""
+    """Three runs with shots past even the big-range path (more than 65,535
+    positions), between ordinary runs: they are redone together (shots kept
+    apart per run) and spliced back in run order, with per-packet labels."""
     rng = np.random.default_rng(21)
     pk, offs = make_batch(n_runs=12, seed=8, long_shot=False)
     runs = [pk[offs[r]:offs[r + 1]] for r in range(offs.size - 1)]
     for k, at in enumerate((2, 6, 9)):
-        runs.insert(at, _long_shot_run(rng, pixels=8500 + 700 * k))
+        runs.insert(at, _long_shot_run(rng, pixels=BEYOND_BIG + 700 * k))
     offs = np.zeros(len(runs) + 1, np.int64)
     offs[1:] = np.cumsum([r.size for r in runs])
     pk = np.concatenate(runs)
@@ -143,7 +152,7 @@ def test_batch_captured_in_a_cuda_graph_replays_exactly():
     tpx_sync) gives the eager call's outputs, and eager calls still work
     after the capture."""
     import torch
-    pk, offs = make_batch(n_runs=24, seed=9)
+    pk, offs = make_batch(n_runs=24, seed=9, long_pixels=BEYOND_BIG)
     s = torch.cuda.Stream()
     ctx = tpx.Context(tpx.Config(tile_geometry=tpx.TILE_4096), max_packets=pk.size, stream=s)
     try:
@@ -175,3 +184,84 @@ def test_batch_captured_in_a_cuda_graph_replays_exactly():
         assert rc == 0 and np.array_equal(ctx.collect_batch(ref_out, rc, cnt)["labels"], ref["labels"])
     finally:
         ctx.close()
+
+
+def _ion_runs(seed, n_runs, particles, shots=(4, 12)):
+    """Ion-like runs (sigma 1.2 px, ToF 1-20 us, ~36 px per particle) whose
+    shots hold `particles` Poisson particles: 10k-20k pixels per shot for
+    300-550 particles."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for r in range(n_runs):
+        pp = float(particles[r % len(particles)])
+        p = synth.Params(n_shots=int(rng.integers(*shots)), seed=seed * 1000 + r, poisson=True,
+                         particles_per_shot=pp, t_start_ticks=int(rng.integers(0, synth.PIX_PERIOD_TICKS)),
+                         **synth.ION)
+        runs.append(synth.generate(p)[0])
+    return runs
+
+
+def _concat(runs):
+    offs = np.zeros(len(runs) + 1, np.int64)
+    offs[1:] = np.cumsum([r.size for r in runs])
+    return (np.concatenate(runs) if offs[-1] else np.zeros(0, np.uint64)), offs
+
+
+def _check_counters(g, pk, offs, **okw):
+    tot = dict.fromkeys(("kept", "dropped_pre_trigger", "dropped_background", "clusters", "peaks"), 0)
+    for r in range(offs.size - 1):
+        o = oracle_run(pk[offs[r]:offs[r + 1]], **okw)
+        for k in tot:
+            tot[k] += int(o["counters"][k])
+    for k, v in tot.items():
+        assert g["counters"][k] == v, (k, g["counters"][k], v)
+
+
+@pytest.mark.parametrize("tile", [tpx.TILE_4096, tpx.TILE_2048])
+def test_big_shots_stay_in_the_launch(tile):
+    """Runs whose shots hold 10k-20k pixels (ion-like, 300-550 particles per
+    shot) between ordinary runs: every range past a tile's capacity takes the
+    big-range path in the same launch, nothing is redone, and records, labels,
+    local maxima, triggers and counters equal the oracle's run by run."""
+    runs = _ion_runs(31, 6, (300, 420, 550))
+    small = [synth.generate(p)[0] for p in synth.batched(n_runs=6, seed=12, shots_hi=80, particles_hi=40)]
+    mixed = [x for pair in zip(runs, small) for x in pair]
+    pk, offs = _concat(mixed)
+    g = run_batch(pk, offs, tile=tile)
+    assert g["counters"]["redone"] == 0
+    check_against_oracle(g, pk, offs)
+    _check_counters(g, pk, offs)
+
+
+def test_big_shots_with_a_wider_box_and_radius():
+    """The big-range path under rx = ry = 2 and a 64-tick time radius."""
+    runs = _ion_runs(33, 3, (350, 500), shots=(3, 6))
+    pk, offs = _concat(runs)
+    ctx = tpx.Context(tpx.Config(rx=2, ry=2, dt_ticks=64), max_packets=pk.size)
+    try:
+        out = ctx.alloc_batch_outputs(pk.size, offs.size - 1, labels=True, is_peak=True,
+                                      cluster_capacity=pk.size, trig_capacity=pk.size)
+        ctx.tpx_process_batch(to_device(pk), offs, out)
+        rc, cnt = ctx.tpx_sync(check=False)
+        g = ctx.collect_batch(out, rc, cnt)
+    finally:
+        ctx.close()
+    assert g["counters"]["redone"] == 0
+    for r in range(offs.size - 1):
+        a, b = int(offs[r]), int(offs[r + 1])
+        o = oracle_run(pk[a:b], rx=2, ry=2, dt=64, index_base=a)
+        assert_clusters_equal(g["clusters"][g["run_clusters"][r]: g["run_clusters"][r + 1]], o["clusters"])
+        assert np.array_equal(g["labels"][a:b], o["labels"]) and np.array_equal(g["is_peak"][a:b], o["is_peak"])
+
+
+def test_big_shot_with_dense_time_bins_and_a_run_past_the_limit():
+    """A 12k-pixel shot within 300 ticks (a few wide-open bins: long
+    windows), a big shot beside a small one in one tile's range, and a shot
+    past the big-range path's limit (that run alone is redone)."""
+    rng = np.random.default_rng(41)
+    runs = [_long_shot_run(rng, 12_000, spread=300), _long_shot_run(rng, 15_000),
+            _long_shot_run(rng, BEYOND_BIG), _ion_runs(35, 1, (450,), shots=(5, 6))[0]]
+    pk, offs = _concat(runs)
+    g = run_batch(pk, offs)
+    assert g["counters"]["redone"] == 1
+    check_against_oracle(g, pk, offs)
