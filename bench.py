@@ -70,6 +70,8 @@ def parse():
                     help="time only the CNN refiner's tcgen05 inference on N random bf16 patches (random weights)")
     ap.add_argument("--batch-runs", type=int, default=4096)
     ap.add_argument("--batch-only", action="store_true")
+    ap.add_argument("--big-shot-batch", type=int, default=0, metavar="RUNS",
+                    help="time one batch of RUNS ion runs whose shots all take the big-range path")
     ap.add_argument("--batch-phase-shares", type=int, default=0, metavar="RUNS",
                     help="per-phase cycle shares of the batch kernel on the first RUNS runs (instrumented build)")
     ap.add_argument("--batch-steps", type=int, default=3, help="timed whole calls of the batch (each ~5 s)")
@@ -575,6 +577,41 @@ def phase_bench(shots: int, tile: str) -> dict:
             "shares": {nm: round(float(c / cyc.sum()), 4) for nm, c in zip(tpx.PHASE_NAMES, cyc)}}
 
 
+def big_shot_batch(n_runs: int) -> dict:
+    """A batch of ion-like runs whose shots all hold 14k-19k pixels (60 shots
+    per run, 400-520 Poisson particles per shot): every range goes through
+    the big-range path. One untimed call, then one timed call (wall clock,
+    device synchronised)."""
+    import torch
+
+    import paper_2603_04942_gb300 as tpx
+    import synth
+    rng = np.random.default_rng(3)
+    pks = []
+    for r in range(n_runs):
+        p = synth.Params(n_shots=60, seed=77 + r, poisson=True, particles_per_shot=float(400 + 40 * (r % 4)),
+                         t_start_ticks=int(rng.integers(0, synth.PIX_PERIOD_TICKS)), **synth.ION)
+        pks.append(synth.generate(p)[0])
+    offs = np.zeros(len(pks) + 1, np.int64)
+    offs[1:] = np.cumsum([x.size for x in pks])
+    pk = np.concatenate(pks)
+    d = torch.from_numpy(pk.view(np.int64)).cuda()
+    ctx = tpx.Context(tpx.Config(), max_packets=pk.size)
+    out = ctx.alloc_batch_outputs(pk.size, n_runs, labels=False, is_peak=False, cluster_capacity=pk.size // 4,
+                                  trig_capacity=1 << 16)
+    ctx.tpx_process_batch(d, offs, out)
+    rc, cnt = ctx.tpx_sync(check=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.tpx_process_batch(d, offs, out)
+    rc, cnt = ctx.tpx_sync(check=False)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return {"metric": "pixel hits/s, big-shot batch", "runs": n_runs, "packets": int(pk.size), "status": rc,
+            "redone": cnt["redone"], "clusters": cnt["clusters"], "ms": round(dt * 1e3, 3),
+            "hits_per_s": cnt["pixels"] / dt}
+
+
 def batch_phase_bench(n_runs: int) -> dict:
     """Per-phase cycle shares of the batch kernel on the first `n_runs` runs
     of the uneven batch (the instrumented library must be loaded): one
@@ -846,6 +883,11 @@ def main():
         import paper_2603_04942_gb300 as tpx
         tpx.load(tbuild.build(phases=True))
         print(json.dumps(phase_bench(args.phase_shares, args.tile)), flush=True)
+        return 0
+    if args.big_shot_batch:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(big_shot_batch(args.big_shot_batch)), flush=True)
         return 0
     if args.batch_phase_shares:
         import torch
