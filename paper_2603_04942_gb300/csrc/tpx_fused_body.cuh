@@ -962,13 +962,14 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
     __syncthreads();
 
     BR_PH(22);
-    // ---- neighbour pass: one thread per pixel of the sorted order scans
-    // the keys that can hold its earlier neighbours, checks the box rule
-    // (Sec. V.A), updates the local-maximum flags (Sec. V.B, equal ToT goes
-    // to the later pixel) and unites. The sorted records are read through
-    // shared memory: BR_CH pixels at a time, staged with the records before
-    // them from the start of the first one's previous time bin (or straight
-    // from the scratch when those do not fit) ----
+    // ---- neighbour pass: every pixel of the sorted order is checked against
+    // the keys that can hold its earlier neighbours (the box rule, Sec. V.A);
+    // an adjacent pair clears the loser's local-maximum flag (Sec. V.B: the
+    // larger ToT wins, equal ToT goes to the later pixel) and unites. The
+    // sorted records are read through shared memory: BR_CH pixels at a time,
+    // staged with the records before them from the start of the first one's
+    // previous time bin (or straight from the scratch when those do not fit) ----
+    auto kstart = [&](int k) -> int { return k > 0 ? (int)bins[k - 1] : 0; };   // a key's first slot
     for (int a = 0; a < N; a += BR_CH) {
         const int e = min(N, a + BR_CH);
         int lo;
@@ -984,34 +985,59 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
             for (int j = lo + tid; j < e; j += NT) sbuf[j - lo] = g_srec[j];
         __syncthreads();
         auto rec_at = [&](int j) -> uint64_t { return fits ? sbuf[j - lo] : g_srec[j]; };
-        for (int i = a + tid; i < e; i += NT) {
-            const uint64_t ri = rec_at(i);
-            const int s = r_seg(ri), x = r_x(ri), y = r_y(ri), tb = r_tof(ri), tot = r_tot(ri);
-            const int tbin = sg_b0[s] + (tb - sg_lo[s]) / sg_w[s];
-            const int st = NS > 1 ? x / (256 / BR_NS) : 0;
-            const int key = tbin * NS + st;
-            int pos = -1;   // read on the first ToT tie
-            bool dim = false;
-            for (int db = tbin > sg_b0[s] ? -1 : 0; db <= 0; ++db) {
-                for (int ds = -1; ds <= 1; ++ds) {
-                    const int s2 = st + ds;
-                    if (s2 < 0 || s2 >= NS) continue;
-                    const int k2 = (tbin + db) * NS + s2;
-                    if (k2 > key) continue;
-                    const int j1 = k2 == key ? i : (int)bins[k2];
-                    for (int j = k2 > 0 ? (int)bins[k2 - 1] : 0; j < j1; ++j) {
-                        const uint64_t rj = rec_at(j);
-                        const int dx = r_x(rj) - x, dy = r_y(rj) - y;
-                        if (dx < -rx || dx > rx || dy < -ry || dy > ry || !within(r_tof(rj) - tb, dtr)) continue;
-                        const int tj = r_tot(rj);
-                        if (tj == tot && pos < 0) pos = g_spos[i];
-                        if (tj > tot || (tj == tot && (int)g_spos[j] > pos)) dim = true;
-                        else br_or(nb_sh + 4 * (j >> 5), 1u << (j & 31));
-                        br_unite(pb, (unsigned)i, (unsigned)j);
-                    }
+        // A warp takes 32 consecutive pixels. A pixel's candidates are two
+        // runs of consecutive slots: the previous bin's stripes around its own
+        // (consecutive keys), and its own bin's left stripe with its own key up
+        // to itself. The warp spreads all its (pixel, candidate) pairs evenly
+        // over its lanes: a prefix of the pixels' candidate counts, and each
+        // lane finds the pixel of its pair by a search over the lanes.
+        for (int i0 = a + wid * 32; i0 < e; i0 += NT) {
+            const int i = i0 + lane;
+            int a0 = 0, la = 0, b0 = 0, lb = 0;
+            if (i < e) {
+                const uint64_t ri = rec_at(i);
+                const int s = r_seg(ri);
+                const int tbin = sg_b0[s] + (r_tof(ri) - sg_lo[s]) / sg_w[s];
+                const int st = NS > 1 ? r_x(ri) / (256 / BR_NS) : 0;
+                if (tbin > sg_b0[s]) {
+                    a0 = kstart((tbin - 1) * NS + max(st - 1, 0));
+                    la = (int)bins[(tbin - 1) * NS + min(st + 1, NS - 1)] - a0;
                 }
+                b0 = kstart(tbin * NS + max(st - 1, 0));
+                lb = i - b0;
             }
-            if (dim) br_or(nb_sh + 4 * (i >> 5), 1u << (i & 31));
+            const int n = la + lb;
+            int incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            const int off = incl - n;
+            const int W = __shfl_sync(0xffffffffu, incl, 31);
+            for (int wb = 0; wb < W; wb += 32) {
+                const int w = wb + lane;
+                int q = 0;   // the last lane whose pairs start at or before w
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int o = __shfl_sync(0xffffffffu, off, q + step);
+                    if (o <= w) q += step;
+                }
+                const int qa0 = __shfl_sync(0xffffffffu, a0, q), qla = __shfl_sync(0xffffffffu, la, q);
+                const int qb0 = __shfl_sync(0xffffffffu, b0, q), qoff = __shfl_sync(0xffffffffu, off, q);
+                if (w >= W) continue;
+                const int c = w - qoff;
+                const int ip = i0 + q;
+                const int j = c < qla ? qa0 + c : qb0 + (c - qla);
+                const uint64_t rp = rec_at(ip), rj = rec_at(j);
+                const int dx = r_x(rj) - r_x(rp), dy = r_y(rj) - r_y(rp);
+                if (dx < -rx || dx > rx || dy < -ry || dy > ry || !within(r_tof(rj) - r_tof(rp), dtr)) continue;
+                const int tj = r_tot(rj), tp = r_tot(rp);
+                const bool j_wins = tj > tp || (tj == tp && g_spos[j] > g_spos[ip]);
+                const int loser = j_wins ? ip : j;
+                br_or(nb_sh + 4 * (loser >> 5), 1u << (loser & 31));
+                br_unite(pb, (unsigned)ip, (unsigned)j);
+            }
         }
         __syncthreads();
     }
