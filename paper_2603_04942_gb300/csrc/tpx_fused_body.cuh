@@ -166,9 +166,9 @@ static_assert(RING >= 1 && RING <= 4, "the ring of staged tiles");
 constexpr int BR_L = 65535;          // positions of a big range (16-bit)
 constexpr int BR_LW = (BR_L + 1) / 32;
 constexpr int BR_S = 256;            // shots (trigger packets) of a big range
-// sort keys (time bin, 16-column stripe) shared out over its shots
+// sort keys (time bin, x stripe) shared out over its shots
 constexpr int BR_BINS = C >= 8192 ? 8192 : 4096;
-constexpr int BR_NS = 16;            // x stripes of 16 columns (one stripe when rx > 16)
+constexpr int BR_NS = 32;            // x stripes of 8 columns (16 when rx > 8, one when rx > 16)
 struct BrMom { unsigned long long s_tot, s_x, s_y, s_tt, best; unsigned n, npk; };
 static_assert(sizeof(BrMom) == 48, "moment record");
 // shared scratch: the tile arrays in front of the trigger tables
@@ -590,7 +590,7 @@ __device__ __forceinline__ int label_rank(const Smem &S, uint32_t lp) {
 // A range longer than the range capacity C (in CC mode: a shot of more pixels
 // than a tile holds) stays in the launch. The CTA decodes the whole range
 // into its own global scratch (the tile's unwrap, binning and cut, Sec.
-// IV.A-C), sorts the kept pixels by (shot, time bin, 16-column x stripe)
+// IV.A-C), sorts the kept pixels by (shot, time bin, 8-column x stripe)
 // with bins at least dt + 1 ticks wide, and compares each pixel with the
 // pixels of the keys before its own that can hold a neighbour: the previous
 // bin's three stripes around its own, its own bin's stripe to the left, and
@@ -893,7 +893,11 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
     // ---- time bins: each shot gets a share of the bins by its kept count,
     // each bin at least dt + 1 ticks wide (one warp); a key is a (bin,
     // stripe) pair ----
-    const int NS = rx <= 256 / BR_NS ? BR_NS : 1;
+    // stripes at least rx wide; fewer when the shots need the time bins
+    // (every shot takes at least one)
+    int NS = rx <= 256 / BR_NS ? BR_NS : (rx <= 2 * 256 / BR_NS ? BR_NS / 2 : 1);
+    while (NS > 1 && BR_BINS / NS < 2 * nseg) NS = NS > BR_NS / 2 ? BR_NS / 2 : 1;
+    const int SW = 256 / NS;   // stripe width (columns)
     const int TB = BR_BINS / NS;   // time bins over all shots
     if (wid == 0) {
         constexpr int SPL = BR_S / 32;   // shots per lane
@@ -928,7 +932,7 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
     __syncthreads();
     auto bin_of = [&](uint64_t r) -> int {
         const int s = r_seg(r);
-        return (sg_b0[s] + (r_tof(r) - sg_lo[s]) / sg_w[s]) * NS + (NS > 1 ? r_x(r) / (256 / BR_NS) : 0);
+        return (sg_b0[s] + (r_tof(r) - sg_lo[s]) / sg_w[s]) * NS + r_x(r) / SW;
     };
     // ---- counting sort of the kept pixels by bin ----
     for (int q = tid; q < L; q += NT) {
@@ -998,7 +1002,7 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
                 const uint64_t ri = rec_at(i);
                 const int s = r_seg(ri);
                 const int tbin = sg_b0[s] + (r_tof(ri) - sg_lo[s]) / sg_w[s];
-                const int st = NS > 1 ? r_x(ri) / (256 / BR_NS) : 0;
+                const int st = r_x(ri) / SW;
                 if (tbin > sg_b0[s]) {
                     a0 = kstart((tbin - 1) * NS + max(st - 1, 0));
                     la = (int)bins[(tbin - 1) * NS + min(st + 1, NS - 1)] - a0;
