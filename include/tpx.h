@@ -517,7 +517,7 @@ int tpx_refine_patches_bf16(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_p
    sorted by (shot, time bin), each pixel compared with its own and the
    previous bin (the same results as the tile's path).  A range even that
    cannot hold (more than 65,535 packets, more kept pixels than its shared
-   scratch: 38,720, or 24,960 with 2048-packet tiles, more than 256 trigger
+   scratch: 31,040, or 24,960 with 2048-packet tiles, more than 256 trigger
    packets), any range in PAPER mode, and a pixel whose trigger lies
    outside its range send the run to the general path: such runs are redone
    exactly at tpx_sync (counters.redone = the number of such runs) and

@@ -167,7 +167,7 @@ constexpr int BR_L = 65535;          // positions of a big range (16-bit)
 constexpr int BR_LW = (BR_L + 1) / 32;
 constexpr int BR_S = 256;            // shots (trigger packets) of a big range
 // sort keys (time bin, x stripe) shared out over its shots
-constexpr int BR_BINS = C >= 8192 ? 8192 : 4096;
+constexpr int BR_BINS = C >= 8192 ? 12288 : 4096;
 constexpr int BR_NS = 32;            // x stripes of 8 columns (16 when rx > 8, one when rx > 16)
 struct BrMom { unsigned long long s_tot, s_x, s_y, s_tt, best; unsigned n, npk; };
 static_assert(sizeof(BrMom) == 48, "moment record");
