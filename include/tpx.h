@@ -521,8 +521,8 @@ int tpx_refine_patches_bf16(tpx_ctx *ctx, const uint64_t *d_packets, int64_t n_p
    packets), any range in PAPER mode, and a pixel whose trigger lies
    outside its range send the run to the general path: such runs are redone
    exactly at tpx_sync (counters.redone = the number of such runs) and
-   spliced into the outputs.  The big-range scratch takes 9.5 MB per CTA of
-   the grid (5.3 MB with 2048-packet tiles) of the batch scratch.
+   spliced into the outputs.  The big-range scratch takes 13.3 MB per CTA of
+   the grid (10.8 MB with 2048-packet tiles) of the batch scratch.
      h_run_offsets   host [n_runs + 1], h_run_offsets[0] = 0, non-decreasing
      d_labels, d_is_peak  per packet of the whole buffer, or NULL; labels are
                      positions in the whole buffer
