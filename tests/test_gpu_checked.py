@@ -93,3 +93,31 @@ def test_phase_timing_build_counts_every_phase():
     assert abs(sum(sh.values()) - 1.0) < 1e-3
     for k in ("neighbour pass", "walk 4 (records)", "unions", "tile load"):
         assert sh[k] > 0, k
+
+
+BATCH_SCRIPT = r"""
+import sys
+sys.path[:0] = [ROOT, HERE]
+import paper_2603_04942_gb300 as tpx
+from paper_2603_04942_gb300 import build
+tpx.load(build.build(checked=True))
+from test_gpu_batch import _concat, _ion_runs, check_against_oracle, run_batch
+ST_BOUNDS = 1 << 8
+pk, offs = _concat(_ion_runs(51, 3, (350, 500), shots=(3, 6)))
+for tile in (tpx.TILE_4096, tpx.TILE_2048):
+    g = run_batch(pk, offs, tile=tile)
+    assert g["counters"]["redone"] == 0, g["counters"]
+    assert not (g["counters"]["status_bits"] & ST_BOUNDS), tile
+    check_against_oracle(g, pk, offs)
+    print("ok", tile, flush=True)
+"""
+
+
+def test_checked_build_big_ranges_in_a_batch():
+    """The big-range path of a batch (shots of 12k-18k pixels, both tile
+    geometries) under the checked build: no index outside its array, nothing
+    redone, results equal to the oracle's run by run."""
+    code = f"ROOT = {ROOT!r}\nHERE = {HERE!r}\n" + BATCH_SCRIPT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1500)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+    assert r.stdout.count("ok ") == 2
