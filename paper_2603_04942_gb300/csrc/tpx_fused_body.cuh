@@ -684,7 +684,8 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
     int *sg_n = reinterpret_cast<int *>(lpre + BR_LW);
     int *sg_lo = sg_n + BR_S, *sg_hi = sg_lo + BR_S, *sg_b0 = sg_hi + BR_S, *sg_w = sg_b0 + BR_S;
     // misc: [0..2] range-end slots, [3] first pixel, [4] kept, [5] dropped
-    // before a trigger, [6] background, [7] failure bits, [8] clusters, [9] peaks
+    // before a trigger, [6] background, [7] failure bits, [8] clusters, [9]
+    // peaks, [12] the neighbour pass's task counter
     int *misc = sg_w + BR_S;
     uint64_t *sbuf = reinterpret_cast<uint64_t *>(misc + 16);   // [BR_SB] staged sorted records
     unsigned char *G = p.big + (size_t)blockIdx.x * BR_STRIDE;
@@ -985,17 +986,26 @@ __device__ __noinline__ int big_range(Smem &S, const Params &p, long long base, 
             lo = k0 > 0 ? (int)bins[k0 - 1] : 0;
         }
         const bool fits = e - lo <= BR_SB;
+        if (tid == 0) misc[12] = 0;   // the chunk's task counter
         if (fits)
             for (int j = lo + tid; j < e; j += NT) sbuf[j - lo] = g_srec[j];
         __syncthreads();
         auto rec_at = [&](int j) -> uint64_t { return fits ? sbuf[j - lo] : g_srec[j]; };
-        // A warp takes 32 consecutive pixels. A pixel's candidates are two
-        // runs of consecutive slots: the previous bin's stripes around its own
-        // (consecutive keys), and its own bin's left stripe with its own key up
-        // to itself. The warp spreads all its (pixel, candidate) pairs evenly
-        // over its lanes: a prefix of the pixels' candidate counts, and each
-        // lane finds the pixel of its pair by a search over the lanes.
-        for (int i0 = a + wid * 32; i0 < e; i0 += NT) {
+        // A warp takes 32 consecutive pixels at a time, the next task from the
+        // chunk's counter (dense stretches take longer). A pixel's candidates
+        // are two runs of consecutive slots: the previous bin's stripes around
+        // its own (consecutive keys), and its own bin's left stripe with its
+        // own key up to itself. The warp spreads all its (pixel, candidate)
+        // pairs evenly over its lanes: a prefix of the pixels' candidate
+        // counts, and each lane finds the pixel of its pair by a search over
+        // the lanes.
+        const int ntask = (e - a + 31) >> 5;
+        for (;;) {
+            int task = 0;
+            if (lane == 0) task = atomicAdd(&misc[12], 1);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (task >= ntask) break;
+            const int i0 = a + 32 * task;
             const int i = i0 + lane;
             int a0 = 0, la = 0, b0 = 0, lb = 0;
             if (i < e) {
