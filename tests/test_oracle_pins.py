@@ -415,3 +415,45 @@ def test_literal_tie_break_diverges_only_past_position_1000():
     r = oracle.run(pk)
     assert r["labels"][1500] >= 0 and r["labels"][1501] == r["labels"][1500]
     assert r["is_peak"][1500] == 1 and r["is_peak"][1501] == 0
+
+
+@pytest.mark.parametrize("rx,ry,dt", [(1, 1, 32), (2, 1, 8)])
+def test_bruteforce_large_dense_shot(rx, ry, dt):
+    """One shot of 4,000 pixels crowded into 40 x 40 pixels and 3,000 ticks
+    (long adjacency chains, crowded time windows: the regime of a shot longer
+    than a tile's range). The oracle's components, canonical labels (the
+    stream index of each component's earliest pixel in (time, index) order)
+    and per-cluster counts and sums equal the connected components of the
+    dense pairwise adjacency matrix (Sec. V.A box rule), found by scipy."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    sparse = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(77 + rx)
+    n, t0 = 4000, 1_000_000
+    xs = rng.integers(100, 140, n)
+    ys = rng.integers(100, 140, n)
+    tots = rng.integers(1, 200, n)
+    ts = t0 + 700 + rng.integers(0, 3000, n)
+    b = StreamBuilder()
+    b.tdc(t0)
+    for i in range(n):
+        b.pix(int(xs[i]), int(ys[i]), int(tots[i]), int(ts[i]))
+    b.tdc(t0 + 640_000)
+    got = oracle.run(b.packets(), oracle.Config(rx=rx, ry=ry, dt_ticks=dt))
+    assert got["status"] == 0
+    adj = ((np.abs(xs[:, None] - xs[None, :]) <= rx) & (np.abs(ys[:, None] - ys[None, :]) <= ry)
+           & (np.abs(ts[:, None] - ts[None, :]) <= dt))
+    ncomp, comp = csgraph.connected_components(sparse.csr_matrix(adj), directed=False)
+    pos = np.arange(n) + 1                      # stream index of pixel i (after the first trigger)
+    first = np.lexsort((pos, ts))               # (time, index) order
+    label = np.full(ncomp, -1, np.int64)
+    for i in first:
+        if label[comp[i]] < 0:
+            label[comp[i]] = pos[i]
+    assert np.array_equal(got["labels"][1:n + 1], label[comp])
+    cl = got["clusters"]
+    assert cl.size == ncomp
+    order = np.argsort(label)
+    assert np.array_equal(cl["label"], label[order])
+    w = tots.astype(np.int64)
+    for f, vals in (("n", np.ones(n, np.int64)), ("s_tot", w), ("s_x", w * xs), ("s_y", w * ys)):
+        assert np.array_equal(cl[f], np.bincount(comp, weights=vals, minlength=ncomp).astype(np.int64)[order]), f
